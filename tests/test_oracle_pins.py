@@ -1,0 +1,384 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by the mathematics.
+
+Each test checks the oracle against something other than itself: closed forms,
+exact symbolic integration, textbook results, invariants, and the paper's
+qualitative statements (Sec. 3.1 remark on Jacobi, Sec. 3.1 single-block
+case, Additive-Schwarz lemma of Sec. 3.1/3.2).  No GPU is needed.
+"""
+import numpy as np
+import numpy.polynomial.legendre as npleg
+import pytest
+
+from oracle import oracle as O
+from paper_1809_00828_gb300 import inputs as I
+
+
+# ---------------------------------------------------------------- basis + rule
+def test_gauss_legendre_exact_for_polynomials():
+    for n in (1, 2, 3, 4, 5, 8):
+        x, w = O.gauss(n)
+        for k in range(2 * n):
+            exact = 0.0 if k % 2 else 2.0 / (k + 1)
+            assert abs(np.dot(w, x ** k) - exact) < 1e-14
+        # and not exact one degree higher (a wrong rule could be "too good" only by accident)
+        k = 2 * n
+        assert abs(np.dot(w, x ** k) - 2.0 / (k + 1)) > 1e-6
+
+
+def _leg_series_1d(p):
+    """Lattice-ordered 1D shape functions as Legendre series (independent of the oracle)."""
+    out = []
+    out.append(np.array([0.5, -0.5]))                # N0 = (1 - xi)/2
+    for a in range(1, p):
+        j = a + 1
+        c = np.zeros(j + 1)
+        c[j] = 1.0
+        c[j - 2] -= 1.0
+        out.append(c / np.sqrt(2.0 * (2 * j - 1)))
+    out.append(np.array([0.5, 0.5]))                 # N1 = (1 + xi)/2
+    return out
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_shape_functions_integrated_legendre(p):
+    fs = _leg_series_1d(p)
+    for xi in (-0.9, -0.31, 0.0, 0.42, 0.77):
+        f, df = O.shape1d(p, xi)
+        for a in range(p + 1):
+            assert abs(f[a] - npleg.legval(xi, fs[a])) < 1e-14
+            assert abs(df[a] - npleg.legval(xi, npleg.legder(fs[a]))) < 1e-13
+    # vertex functions interpolate, bubbles vanish at the ends
+    for xi, want in ((-1.0, 0), (1.0, p)):
+        f, _ = O.shape1d(p, xi)
+        for a in range(p + 1):
+            assert abs(f[a] - (1.0 if a == want else 0.0)) < 1e-14
+    # closed form: int phi_i' phi_j' dxi = delta_ij for the bubbles (Szabo normalisation)
+    if p >= 2:
+        xg, wg = npleg.leggauss(p + 2)
+        D = np.array([[np.sum(wg * np.array([O.shape1d(p, t)[1][i] * O.shape1d(p, t)[1][j] for t in xg]))
+                       for j in range(1, p)] for i in range(1, p)])
+        assert np.allclose(D, np.eye(p - 1), atol=1e-13)
+
+
+# ------------------------------------------------------------ element matrices
+def _kron_element(p, h, E, nu, zrange=(-1.0, 1.0)):
+    """Uncut (or z-truncated) element stiffness from 1D integrals and Kronecker products.
+
+    G_jl[I,J] = int d_j N_I d_l N_J dx factorises per axis; K^{ab} = lam G_ab + mu delta_ab tr G + mu G_ba.
+    """
+    fs = _leg_series_1d(p)
+    q = p + 1
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+
+    def m1(axis, di, dj, rng=(-1.0, 1.0)):
+        M = np.zeros((q, q))
+        for i in range(q):
+            for j in range(q):
+                fi = npleg.legder(fs[i]) * (2.0 / h[axis]) if di else fs[i]
+                fj = npleg.legder(fs[j]) * (2.0 / h[axis]) if dj else fs[j]
+                prod = npleg.legmul(fi, fj)
+                anti = npleg.legint(prod)
+                M[i, j] = (npleg.legval(rng[1], anti) - npleg.legval(rng[0], anti)) * h[axis] / 2.0
+        return M
+
+    G = {}
+    for j in range(3):
+        for l in range(3):
+            mats = [m1(ax, ax == j, ax == l, zrange if ax == 2 else (-1.0, 1.0)) for ax in range(3)]
+            G[j, l] = np.kron(mats[2], np.kron(mats[1], mats[0]))
+    n = q ** 3
+    K = np.zeros((3 * n, 3 * n))
+    tr = G[0, 0] + G[1, 1] + G[2, 2]
+    for a in range(3):
+        for b in range(3):
+            blk = lam * G[a, b] + mu * G[b, a] + (mu * tr if a == b else 0.0)
+            K[a::3, b::3] = blk
+    return K
+
+
+def test_element_p1_equals_exact_symbolic_integration():
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z")
+    h = (sp.Rational(1, 4), sp.Rational(1, 2), sp.Integer(1))
+    E, nu = sp.Integer(1), sp.Rational(3, 10)
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+
+    def box_int(e):
+        P = sp.Poly(sp.expand(e), x, y, z)
+        return sum(c * h[0] ** (a + 1) / (a + 1) * h[1] ** (b + 1) / (b + 1) * h[2] ** (g + 1) / (g + 1)
+                   for (a, b, g), c in P.terms())
+
+    Ns = []
+    for iz in range(2):
+        for iy in range(2):
+            for ix in range(2):
+                fx = (1 - x / h[0]) if ix == 0 else x / h[0]
+                fy = (1 - y / h[1]) if iy == 0 else y / h[1]
+                fz = (1 - z / h[2]) if iz == 0 else z / h[2]
+                Ns.append(fx * fy * fz)
+    grads = [[sp.diff(N, v) for v in (x, y, z)] for N in Ns]
+    K = np.zeros((24, 24))
+    for Ii in range(8):
+        for a in range(3):
+            for J in range(8):
+                for b in range(3):
+                    e = lam * grads[Ii][a] * grads[J][b] + mu * (
+                        (1 if a == b else 0) * sum(grads[Ii][k] * grads[J][k] for k in range(3))
+                        + grads[Ii][b] * grads[J][a])
+                    K[3 * Ii + a, 3 * J + b] = float(box_int(e))
+    d, keep = O.make_desc((1, 1, 1), 1, 1e-3, I.uncut(), hi=(0.25, 0.5, 1.0))
+    Ko, eta = O.cell_matrix(d, (0, 0, 0))
+    assert eta == pytest.approx(1.0, abs=1e-14)
+    assert np.abs(Ko - K).max() < 1e-14 * np.abs(K).max() * 10
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_uncut_element_equals_kronecker_formula(p):
+    h = (0.3, 0.5, 0.7)
+    d, keep = O.make_desc((2, 2, 2), p, 1e-6, I.uncut(), E=2.5, nu=0.27, hi=(0.6, 1.0, 1.4))
+    Ko, eta = O.cell_matrix(d, (1, 0, 1))
+    Kk = _kron_element(p, h, 2.5, 0.27)
+    assert eta == pytest.approx(1.0, abs=1e-13)
+    assert np.abs(Ko - Kk).max() < 1e-12 * np.abs(Kk).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_cut_cell_is_alpha_blend_of_full_and_solid_part(p):
+    # solid iff z < 0.35 inside a cell spanning z in [0, 0.7]: the octree resolves the half exactly
+    alpha = 0.1
+    g = I.halfspace(0.0, 0.0, 1.0, 0.35, octree_depth=2)
+    d, keep = O.make_desc((1, 1, 1), p, alpha, g, hi=(0.3, 0.5, 0.7))
+    Ko, eta = O.cell_matrix(d, (0, 0, 0))
+    h = (0.3, 0.5, 0.7)
+    Kfull = _kron_element(p, h, 1.0, 0.3)
+    Klow = _kron_element(p, h, 1.0, 0.3, zrange=(-1.0, 0.0))
+    want = alpha * Kfull + (1 - alpha) * Klow
+    assert eta == pytest.approx(0.5, abs=1e-14)
+    assert np.abs(Ko - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_alpha_one_makes_cut_cells_equal_uncut():
+    # with alpha = 1 the octree quadrature must integrate the full cell exactly, cut or not
+    g = I.single_sphere_void(3, 0.3, 0.05, octree_depth=3)
+    d, keep = O.make_desc((4, 4, 4), 2, 1.0, g)
+    K0, _ = O.cell_matrix(d, (0, 0, 0))
+    for c in [(1, 1, 1), (2, 1, 1), (1, 2, 2)]:
+        dc, keepc = O.make_desc((4, 4, 4), 2, 1e-8, g)
+        assert O.cell_matrix(dc, c, want_K=False)[1] < 1.0   # these cells are cut
+        Kc, _ = O.cell_matrix(d, c)
+        assert np.abs(Kc - K0).max() < 1e-13 * np.abs(K0).max()
+
+
+# ---------------------------------------------------------- global invariants
+def _vertex_coords(P, desc):
+    """Physical coordinates of lattice nodes that are grid vertices (else None)."""
+    p = desc.p
+    M = [p * desc.n[a] + 1 for a in range(3)]
+    node = P.free_lat // 3
+    idx = [node % M[0], (node // M[0]) % M[1], node // (M[0] * M[1])]
+    is_vertex = np.ones(len(node), dtype=bool)
+    X = np.zeros((len(node), 3))
+    for a in range(3):
+        is_vertex &= idx[a] % p == 0
+        h = (desc.hi[a] - desc.lo[a]) / desc.n[a]
+        X[:, a] = desc.lo[a] + (idx[a] // p) * h
+    return is_vertex, X, P.free_lat % 3
+
+
+def test_rigid_body_modes_in_null_space_before_bcs():
+    g = I.random_sphere_voids(5, 6, 0.1, 0.25, octree_depth=2)
+    w = I.Workload("rbm", (3, 3, 3), 2, 1e-6, g, 1e-8, bc=-1)
+    d, keep = O.desc_for(w)
+    P = O.Problem(d, keep)
+    K = P.csr()
+    isv, X, comp = _vertex_coords(P, d)
+    modes = []
+    for a in range(3):
+        modes.append(np.where(isv & (comp == a), 1.0, 0.0))
+    for omega in np.eye(3):
+        u = np.cross(omega, X)          # rotation field omega x X, sampled at the vertices
+        modes.append(np.where(isv, u[np.arange(len(comp)), comp], 0.0))
+    Kn = abs(K).sum(axis=1).max()
+    for m in modes:
+        assert np.abs(K @ m).max() < 1e-12 * Kn * np.abs(m).max()
+    # and K is symmetric with a positive diagonal
+    assert abs(K - K.T).max() < 1e-15 * Kn
+    assert K.diagonal().min() > 0
+
+
+def test_patch_test_uniaxial_stress_is_reproduced_exactly():
+    # rollers on x=0, y=0, z=0; uniform traction sigma on z=hi; others traction free
+    sigma, E, nu = 0.7, 2.0, 0.25
+    w = I.Workload("patch", (2, 3, 2), 2, 1e-6, I.uncut(), 1e-12, E=E, nu=nu, traction=(0.0, 0.0, sigma),
+                   bc=1, hi=(1.5, 1.2, 0.8))
+    d, keep = O.desc_for(w)
+    P = O.Problem(d, keep)
+    K = P.csr().toarray()
+    x = np.linalg.solve(K, P.rhs())
+    isv, X, comp = _vertex_coords(P, d)
+    exact_field = np.stack([-nu * sigma * X[:, 0] / E, -nu * sigma * X[:, 1] / E, sigma * X[:, 2] / E], axis=1)
+    want = np.where(isv, exact_field[np.arange(len(comp)), comp], 0.0)
+    assert np.abs(x - want).max() < 1e-12
+    # the iterative solve gets there too
+    P.precond_build(0)
+    xi, its, _ = P.pcg(tol=1e-12)
+    assert its > 0 and np.abs(xi - want).max() < 1e-10
+
+
+def test_volume_fraction_converges_to_sphere_volume():
+    g = I.Geometry(I.GEOM_SPHERE_VOIDS, spheres=np.array([[0.5, 0.5, 0.5, 0.3]]))
+    exact = 1.0 - 4.0 / 3.0 * np.pi * 0.3 ** 3
+    errs = []
+    for depth in (0, 3, 5):
+        d, keep = O.make_desc((4, 4, 4), 2, 1e-8, g, depth=depth)
+        vol = sum(O.cell_matrix(d, (cx, cy, cz), want_K=False)[1] / 64
+                  for cz in range(4) for cy in range(4) for cx in range(4))
+        errs.append(abs(vol - exact))
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 2e-5
+
+
+def test_traction_resultant_equals_load_times_solid_area():
+    # the four vertex functions of a top face sum to one there, so their loads sum to the resultant
+    t = (0.2, -0.3, -1.0)
+    p, n = 3, 4
+    q = p + 1
+    cz, r = 0.9, 0.25
+    cases = [(I.uncut(), 1.0, 1e-13),
+             (I.Geometry(I.GEOM_SPHERE_VOIDS, spheres=np.array([[0.45, 0.55, cz, r]]), octree_depth=6),
+              1.0 - np.pi * (r * r - (1.0 - cz) ** 2), 2e-3)]
+    corner = [3 * (ix + q * (iy + q * p)) for iy in (0, p) for ix in (0, p)]
+    for geom, area, rel in cases:
+        d, keep = O.make_desc((n, n, n), p, 1e-8, geom, traction=t)
+        tot = np.zeros(3)
+        for cy in range(n):
+            for cx in range(n):
+                be = O.cell_traction(d, (cx, cy, n - 1))
+                for a in range(3):
+                    tot[a] += sum(be[c + a] for c in corner)
+        for a in range(3):
+            assert tot[a] == pytest.approx(t[a] * area, rel=rel)
+    # a cell below the top layer carries no load
+    assert not O.cell_traction(d, (0, 0, n - 2)).any()
+
+
+def test_dof_count_closed_form():
+    # all cells active: 3 (pN+1)^3 lattice DOFs, minus the clamped z=0 plane
+    w = I.workload_single_void(0)
+    P = O.Problem.from_workload(w)
+    m = 2 * 4 + 1
+    assert P.nlat == 3 * m ** 3
+    assert P.nfree == 3 * (m ** 3 - m ** 2) == 1944
+
+
+# ------------------------------------------------------------- pseudo inverse
+def test_pseudo_inverse_matches_spectral_definition():
+    rng = np.random.default_rng(7)
+    n = 12
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.array([10.0, 3.0, 1.0, 0.5, 0.2, 1e-2, 1e-4, 1e-6, 1e-6, 5e-13, -3e-11, -1e-10])
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    F, cond, nneg, nfilt = O.pseudo_inverse(A, 1e-13)
+    keep = lam > 1e-13 * lam.max()
+    want = (Q[:, keep] / lam[keep]) @ Q[:, keep].T
+    assert np.abs(F - want).max() < 1e-8 * np.abs(want).max()
+    assert nfilt == 3 and nneg == 2
+    assert cond == pytest.approx(10.0 / 1e-6, rel=1e-6)
+    lj, V, _ = O.jacobi_eig(A)
+    assert np.allclose(np.sort(lj), np.sort(np.linalg.eigvalsh(A)), atol=1e-14)
+    # unstabilised inverse (S*): the negative roundoff eigenvalue is inverted too
+    Fs, _, _, _ = O.pseudo_inverse(A, -1.0)
+    ev = np.linalg.eigvalsh(0.5 * (Fs + Fs.T))
+    assert ev.min() < -1e10 and ev.max() > 1e12
+
+
+# ------------------------------------------------------------------- solver
+@pytest.fixture(scope="module")
+def single_void():
+    w = I.workload_single_void(0)
+    P = O.Problem.from_workload(w)
+    return w, P
+
+
+def test_config_single_void_pcg_matches_dense_solve(single_void):
+    w, P = single_void
+    P.precond_build(0)
+    K = P.csr().toarray()
+    xd = np.linalg.solve(K, P.rhs())
+    x, its, hist = P.pcg(tol=w.tol)
+    assert 0 < its < 500
+    assert hist[-1] <= w.tol
+    assert P.energy_error(xd, x) < 1e-8
+
+
+def test_single_block_with_every_dof_converges_in_one_iteration():
+    g = I.single_sphere_void(2, 0.3, 0.05, octree_depth=2)
+    P = O.Problem.from_workload(I.Workload("tiny", (2, 2, 2), 2, 1e-8, g, 1e-10))
+    P.precond_build(1)
+    assert P.nblocks() == 1
+    x, its, hist = P.pcg(tol=1e-10)
+    assert its == 1
+
+
+def test_size_one_blocks_are_jacobi(single_void):
+    w, P = single_void
+    P.precond_build(2)
+    r = I.random_vector(3, P.nfree)
+    z = P.apply_S(r)
+    assert np.allclose(z, r / P.csr().diagonal(), rtol=4e-16, atol=0.0)
+
+
+def test_vertex_patch_membership_and_overlap(single_void):
+    w, P = single_void
+    P.precond_build(0)
+    nb = P.nblocks()
+    assert nb == 5 ** 3
+    count = np.zeros(P.nfree, dtype=int)
+    sizes = []
+    for b in range(nb):
+        idx, F, info = P.block(b)
+        count[idx] += 1
+        sizes.append(len(idx))
+        assert np.allclose(F, F.T, atol=1e-12 * np.abs(F).max())
+    assert max(sizes) == 3 * (2 * w.p - 1) ** 3 == 81
+    assert count.min() >= 1 and count.max() == 8
+    # overlap = 2^(number of axes on which the function is a bubble)
+    M = 2 * 4 + 1
+    node = P.free_lat // 3
+    ijk = [node % M, (node // M) % M, node // (M * M)]
+    nbub = sum((c % w.p != 0).astype(int) for c in ijk)
+    assert np.array_equal(count, 2 ** nbub)
+
+
+def test_schwarz_spectrum_bounded_by_number_of_colours():
+    # Additive-Schwarz lemma: with 8 colours of disjoint blocks, lambda_max(S A) <= 8; S A is positive
+    g = I.single_sphere_void(1, 0.3, 0.05, octree_depth=2)
+    w = I.Workload("tiny", (2, 2, 2), 2, 1e-6, g, 1e-8)
+    P = O.Problem.from_workload(w)
+    P.precond_build(0)
+    K = P.csr().toarray()
+    S = np.stack([P.apply_S(e) for e in np.eye(P.nfree)], axis=1)
+    assert np.abs(S - S.T).max() < 1e-9 * np.abs(S).max()
+    lam = np.linalg.eigvals(S @ K).real
+    assert lam.max() <= 8.0 + 1e-8
+    assert lam.min() > 0.0
+    assert lam.max() > 2.0
+
+
+def test_jacobi_degrades_with_small_cuts_schwarz_stays_bounded():
+    # Sec. 3.1 remark / Sec. 5.2: diagonal scaling is not robust to small cut cells, the blocks are
+    its = {}
+    for eta in (0.3, 0.03):
+        g = I.halfspace(1.0, 0.0, 0.0, 0.75 + 0.25 * eta, octree_depth=5)
+        w = I.Workload("sliver", (4, 4, 4), 2, 1e-12, g, 1e-8)
+        P = O.Problem.from_workload(w)
+        for rule in (0, 2):
+            P.precond_build(rule)
+            _, n, _ = P.pcg(tol=1e-8, maxit=20000)
+            its[eta, rule] = n
+    assert its[0.03, 2] > 3 * its[0.3, 2]
+    assert its[0.03, 0] <= 1.2 * its[0.3, 0] + 2
+    assert its[0.03, 0] * 20 < its[0.03, 2]
