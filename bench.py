@@ -1,0 +1,351 @@
+"""Benchmark: PCG time-to-solution of the finite cell Schwarz-PCG on one GB300.
+
+A step is one complete preconditioned CG solve (x0 = 0 to ||S r|| / ||S b|| <=
+tol) of the 32^3-cell, p=3 porous cube (40 seeded spherical voids, alpha 1e-10,
+octree depth 4) with the set-up and the preconditioner built once beforehand.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcm|reference]
+                  [--workload NAME] [--precision fp64|mixed]
+
+N > 1 runs independent replicas (one per GPU, launched by torchrun); the
+solve has no data-path collective.  `--impl reference` times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-solution (s) and GB/s vs HBM roofline at 1e-8, learned/mixed vs plain FP64"
+DEFAULT_WORKLOAD = "porous40_32_p3"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 pipe of one SM: 2 fused multiply-adds per clock (64x below the 128 FP32
+# lanes), i.e. 152 SMs x 2070 MHz x 4 flop = 1.26 TFLOP/s, the nominal GB300 FP64 rate.
+FP64_FLOP_PER_CLK_PER_SM = 4
+N_SM = 152
+
+
+def fp64_peak_tflops(sm_mhz):
+    return N_SM * sm_mhz * 1e6 * FP64_FLOP_PER_CLK_PER_SM / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(name):
+    from paper_1809_00828_gb300 import inputs
+    return inputs.WORKLOADS[name]()
+
+
+def oracle_sample(w, gpu_iterations, sapply_fmas, kapply_fmas, min_seconds=10.0):
+    """Time the CPU oracle's PCG on a bounded window of the same workload and scale it.
+
+    The window is the 2x2x2-cell corner [0, 2h]^3 of the same geometry, order,
+    alpha and octree depth (27 vertex patches).  The oracle's per-iteration time
+    is scaled by the ratio of per-iteration multiply-adds (K entries + sum of
+    block sizes squared) of the full workload to the window, times the full
+    workload's iteration count.
+    """
+    from oracle import oracle as O
+    from paper_1809_00828_gb300 import inputs
+    h = [(w.hi[a] - w.lo[a]) / w.n[a] for a in range(3)]
+    win = inputs.Workload(w.name + "_window", (2, 2, 2), w.p, w.alpha, w.geometry, w.tol, E=w.E, nu=w.nu,
+                          traction=w.traction, bc=w.bc, lo=w.lo,
+                          hi=tuple(w.lo[a] + 2 * h[a] for a in range(3)))
+    P = O.Problem.from_workload(win)
+    P.precond_build(0)
+    nnz = P.csr().nnz
+    blocks = sum(P.block(b)[0].size ** 2 for b in range(P.nblocks()))
+    per_iter = []
+    t_total = 0.0
+    while t_total < min_seconds:
+        t0 = time.perf_counter()
+        _, its, _ = P.pcg(tol=w.tol, maxit=20000)
+        dt = time.perf_counter() - t0
+        t_total += dt
+        per_iter.append(dt / max(its, 1))
+    t_iter = statistics.median(per_iter)
+    scale = (kapply_fmas + sapply_fmas) / float(nnz + blocks)
+    value = t_iter * scale * gpu_iterations
+    sample = (f"oracle PCG on the 2x2x2-cell corner window of {w.name} ({P.nfree} DOFs, {P.nblocks()} blocks), "
+              f"{len(per_iter)} solves in {t_total:.1f} s; {t_iter * 1e3:.3f} ms/iteration scaled by per-iteration multiply-adds x{scale:.1f} "
+              f"and {gpu_iterations} iterations")
+    return value, sample, t_total
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = _workload(args.workload)
+    # the full workload's iteration count and per-iteration work come from the problem sizes,
+    # not from the GPU: counted on the host from the oracle's own block rule
+    gpu_like_iters = args.ref_iterations
+    kf, sf = _host_work_counts(w)
+    steps = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        v, sample, _ = oracle_sample(w, gpu_like_iters, sf, kf, min_seconds=2.0 if i < args.warmup else 10.0)
+        if i >= args.warmup:
+            steps.append(v)
+    value = statistics.median(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _describe(w), "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _host_work_counts(w):
+    """Per-iteration multiply-adds of K (active cells x ne^2) and S (sum of box sizes^2), counted on the host."""
+    p = w.p
+    ne = 3 * (p + 1) ** 3
+    ncells = w.n[0] * w.n[1] * w.n[2]
+    kf = ncells * ne * ne
+    sf = 0
+    dims = []
+    for a in range(3):
+        M = p * w.n[a] + 1
+        d = []
+        for v in range(w.n[a] + 1):
+            lo = max(0, p * v - (p - 1))
+            hi = min(M - 1, p * v + (p - 1))
+            d.append(hi - lo + 1)
+        dims.append(np.array(d, dtype=np.int64))
+    box = 3 * dims[0][None, None, :] * dims[1][None, :, None] * dims[2][:, None, None]
+    sf = int((box.astype(np.int64) ** 2).sum())
+    return kf, sf
+
+
+def _describe(w):
+    return (f"{w.name}: {w.n[0]}x{w.n[1]}x{w.n[2]} cells, p={w.p}, alpha={w.alpha:g}, "
+            f"{0 if w.geometry.spheres is None else len(w.geometry.spheres)} spherical voids, "
+            f"octree depth {w.geometry.octree_depth}, tol {w.tol:g}, E={w.E:g}, nu={w.nu:g}, z=0 clamped, "
+            f"unit traction on z=1, vertex-patch blocks, eps=1e-13")
+
+
+def run_fcm(args, rank, world, local_rank):
+    import torch
+    from paper_1809_00828_gb300 import fcm
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    w = _workload(args.workload)
+    s = fcm.Solver(w)
+    s.precond_build(precision=args.precision)
+    info = s.info
+    b = s.rhs()
+    u = s.empty()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=u)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    per = []
+    iters = []
+    for _ in range(args.steps):
+        _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=u)
+        li = s.last_solve()
+        per.append(li["seconds"])
+        iters.append(its)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_per_step = elapsed / args.steps * 1e3
+    last = s.last_solve()
+
+    # dominant kernel: the Schwarz block apply (8 colour launches), timed live on the stream
+    r = b.clone()
+    z = s.empty()
+    for _ in range(3):
+        s.apply_S(r, out=z)
+    torch.cuda.synchronize()
+    reps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.apply_S(r, out=z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_s = e0.elapsed_time(e1) / 1e3 / reps
+    e0.record(stream)
+    for _ in range(reps):
+        s.apply_K(r, out=z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_k = e0.elapsed_time(e1) / 1e3 / reps
+
+    peaks, peak_kind = _peaks()
+    n = info["n_lattice"]
+    s_flops = 2.0 * info["sapply_fmas"]
+    # algorithmic HBM bytes of one S apply: distinct stored factors + gather of r + read-modify-write of z
+    s_bytes = info["factor_bytes"] + 8.0 * n * 3
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = fp64_peak_tflops(sm_mhz)
+    achieved_tf = s_flops / t_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_peak, "traffic": None,
+                "kernel": "schwarz_apply_kernel<3> (8 colour launches per S apply)",
+                "peak_source": f"FP64: {N_SM} SMs x {FP64_FLOP_PER_CLK_PER_SM} flop/clk x median SM clock {sm_mhz:.0f} MHz",
+                "hbm_achieved_gbs": s_bytes / t_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": s_bytes / t_s / 1e9 / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind,
+                "s_apply_ms": t_s * 1e3, "k_apply_ms": t_k * 1e3,
+                "k_apply_tflops": 2.0 * info["kapply_fmas"] / t_k / 1e12}
+
+    # end to end through the host-buffer entry point (pinned buffers, copies inside the timed region)
+    b_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    b_host.copy_(b)
+    u_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bh = b_host.numpy()
+    uh = u_host.numpy()
+    s.pcg_solve_host(bh, w.tol, args.maxit, out=uh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        s.pcg_solve_host(bh, w.tol, args.maxit, out=uh)
+    e2e = (time.perf_counter() - t0) / e2e_steps
+
+    its_med = int(statistics.median(iters))
+    graph_launches = -(-its_med // 8)
+    launches_per_solve = 13 + 10 + graph_launches * 8 * (1 + 8 + 2 + 1 + 8 + 2)
+    line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {"workload": _describe(w), "precision": args.precision, "n_free": info["n_free"],
+                       "iterations": its_med, "relres": rel, "true_relres": last["true_relres"],
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": f"inputs larger than L2: factor pool {info['factor_bytes'] / 2**30:.2f} GiB, "
+                             f"element matrices {info['element_bytes'] / 2**30:.2f} GiB",
+                       "n_blocks": info["n_blocks"], "n_factors": info["n_factors"],
+                       "setup_s": info["setup_seconds"], "precond_s": info["precond_seconds"],
+                       "device_seconds_median": statistics.median(per)},
+            "roofline": roofline,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": launches_per_solve * args.steps,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        kf, sf = info["kapply_fmas"], info["sapply_fmas"]
+        v, sample, _ = oracle_sample(w, its_med, sf, kf)
+        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--ref-iterations", type=int, default=None,
+                    help="iteration count used to scale the reference arm (default: a GPU-free estimate)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if args.ref_iterations is None:
+            args.ref_iterations = 250
+        return run_reference(args, rank, world)
+    return run_fcm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

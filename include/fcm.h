@@ -1,0 +1,197 @@
+/*
+ * fcm.h -- C ABI of the GB300 finite cell Schwarz-PCG solver (libfcm.so).
+ *
+ * The library solves the finite cell stiffness system of 3D linear elasticity
+ * (Jomo et al., arXiv:1809.00828, Sec. 2.1 Eq. (1)) on a Cartesian grid with an
+ * integrated-Legendre basis of order p, cut cells integrated by octree
+ * partitioning (Sec. 5.1 setup) and a fictitious-domain stiffness alpha, by
+ * conjugate gradients preconditioned with the overlapping Additive-Schwarz
+ * operator S = sum_B R_B^T A_B+^-1 R_B (Sec. 3.1 Eq. (5)) built from
+ * eigenvalue-filtered pseudo inverses (Sec. 3.2 Eqs. (11)-(13), Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Vectors (right-hand sides, solutions, K/S inputs and outputs) are FP64
+ * arrays of length fcm_info.n_lattice in "lattice" layout:
+ *   M_a = p * n[a] + 1 lattice nodes per axis, node (i,j,k) -> i + M_0 (j + M_1 k),
+ *   DOF = 3 * node + component (components interleaved).
+ * Along an axis, cell c owns lattice indices p*c .. p*c+p: p*c is its left
+ * grid vertex, p*c+p its right one, p*c+a (0<a<p) the integrated Legendre
+ * function phi_{a+1} = (P_{a+1} - P_{a-1}) / sqrt(2(2a+1)) of that cell.
+ * Entries that are not free (on no active cell, or Dirichlet-fixed) are
+ * ignored on input and written as 0 on output.
+ *
+ * Pointers named *_dev are CUDA device pointers on the current device; the
+ * caller owns them.  Everything reachable from an fcm_ctx is owned by the
+ * library and released by fcm_destroy.  No C++ exception crosses this ABI.
+ * All device work is ordered on the stream passed to fcm_setup; functions
+ * that return results to host memory synchronise that stream.
+ * On error a function returns a nonzero fcm_status and leaves a message in
+ * fcm_last_error(ctx) (or fcm_last_error(NULL) when no context exists).
+ */
+#ifndef FCM_H
+#define FCM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fcm_ctx fcm_ctx;
+
+typedef enum {
+    FCM_OK = 0,
+    FCM_EINVAL = 1,      /* invalid argument (sizes, NaN inputs, null pointers)      */
+    FCM_ENOMEM = 2,      /* device or host allocation failed                         */
+    FCM_ECUDA = 3,       /* a CUDA / cuSOLVER / cuBLAS call failed                   */
+    FCM_ENOTCONV = 4,    /* maxit reached; the last iterate is returned              */
+    FCM_EBREAKDOWN = 5,  /* p^T K p <= 0 or a non-finite scalar in CG                */
+    FCM_ETIMEOUT = 6,    /* a bounded device wait gave up                            */
+    FCM_ESTATE = 7       /* call out of order (e.g. solve before fcm_precond_build)  */
+} fcm_status;
+
+/* Cartesian grid: n[a] cells on [lo[a], hi[a]] per axis. */
+typedef struct {
+    int n[3];
+    double lo[3], hi[3];
+} fcm_grid;
+
+enum { FCM_GEOM_SPHERE_VOIDS = 0, FCM_GEOM_VOXELS = 1, FCM_GEOM_HALFSPACE = 2 };
+
+/* Physical domain Omega_phys (Sec. 2.1).  Host arrays, copied by fcm_setup.
+ *   kind 0: the grid box minus the union of open balls sph[4*s..4*s+3] = (cx, cy, cz, r)
+ *   kind 1: voxel image vox (vdim[0] fastest) over the grid box; solid where vox != 0
+ *   kind 2: half-space {x : plane[0] x + plane[1] y + plane[2] z < plane[3]}
+ * octree_depth: partition depth of cut cells relative to the cell size (Sec. 5.1). */
+typedef struct {
+    int kind;
+    int nsph;
+    const double *sph;
+    int vdim[3];
+    const unsigned char *vox;
+    double plane[4];
+    int octree_depth;
+} fcm_geometry;
+
+enum { FCM_BC_NONE = -1, FCM_BC_CLAMP_ZLO = 0, FCM_BC_ROLLERS = 1 };
+
+/* Material and boundary conditions.  bc: FCM_BC_CLAMP_ZLO fixes every
+ * component on the face z = lo[2]; FCM_BC_ROLLERS fixes u_x on x = lo[0],
+ * u_y on y = lo[1], u_z on z = lo[2]; FCM_BC_NONE fixes nothing (K then has
+ * the rigid-body modes in its null space).  Dirichlet data is homogeneous and
+ * imposed strongly on the grid-aligned faces.  traction: surface load on the
+ * face z = hi[2] where it lies in Omega_phys (load case 0). */
+typedef struct {
+    double E, nu;
+    int bc;
+    double traction[3];
+} fcm_bc;
+
+/* Sizes of a set-up problem. */
+typedef struct {
+    int64_t n_lattice;        /* length of every vector, 3 * prod(M_a)                 */
+    int64_t n_free;           /* free DOFs                                             */
+    int64_t n_cells_active;   /* cells with eta_T > 0                                  */
+    int64_t n_cells_cut;      /* active cells with their own element matrix            */
+    int64_t n_patches;        /* vertex patches (blocks), (n0+1)(n1+1)(n2+1)           */
+    int64_t n_factors;        /* distinct stored block factors after deduplication     */
+    int64_t factor_bytes;     /* device bytes of the stored block factors              */
+    int64_t element_bytes;    /* device bytes of the stored element matrices           */
+    int max_block;            /* largest block, 3 (2p-1)^3                              */
+    int p;
+    double setup_seconds;     /* host+device time of fcm_setup                         */
+    double precond_seconds;   /* time of the last fcm_precond_build                    */
+    int64_t n_blocks;         /* vertex patches with at least one free DOF             */
+    int64_t n_blocks_fp32;    /* of the stored factors, those kept in FP32             */
+    int64_t kapply_fmas;      /* multiply-adds of one K apply (sum over active cells)  */
+    int64_t sapply_fmas;      /* multiply-adds of one S apply (sum of block box sizes^2) */
+    double max_block_cond;    /* largest retained condition number of a block          */
+} fcm_info_t;
+
+enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1 };
+
+/* Preconditioner options (Algorithm 1).
+ *   eps: pseudo-inverse threshold, eigenvalues <= eps * lambda_max are dropped
+ *        (Sec. 3.2 Eq. (13); the paper uses 1e-13).  eps < 0 gives the
+ *        unstabilised inverse S* (every nonzero eigenvalue inverted).
+ *   precision: FCM_PREC_FP64 stores and applies every factor in FP64;
+ *        FCM_PREC_MIXED stores factors in FP32 except blocks whose retained
+ *        condition number exceeds cond_fp64 (kept in FP64).
+ *   cond_fp64: threshold for FCM_PREC_MIXED (default 1e7). */
+typedef struct {
+    double eps;
+    int precision;
+    double cond_fp64;
+} fcm_precond_opts;
+
+/* Solver result details. */
+typedef struct {
+    int iterations;            /* K applications performed                          */
+    double relres;             /* ||S r_i|| / ||S b||, Eq. (14)                      */
+    double true_relres;        /* ||b - K x_i|| / ||b|| recomputed at exit           */
+    int status;                /* fcm_status of the solve                           */
+    double seconds;            /* device time of the solve                          */
+} fcm_solve_info;
+
+/* Set up the problem: classify cells by octree quadrature, compute eta_T,
+ * the element matrices, the free-DOF mask and the load (Sec. 2.1 Eq. (1),
+ * Sec. 5.1).  p in [1, 4].  alpha in (0, 1].  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) used for every later call on this context.
+ * Returns FCM_EINVAL for bad sizes, FCM_ECUDA/FCM_ENOMEM for device failures. */
+fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, double alpha,
+                     const fcm_bc *bc, void *cuda_stream, fcm_ctx **out);
+
+/* Copy the problem sizes into *out. */
+fcm_status fcm_info(const fcm_ctx *ctx, fcm_info_t *out);
+
+/* Write load case load_case into b_dev (n_lattice FP64, device).
+ *   0: traction of fcm_bc on the top face (Sec. 2.1 Eq. (1), Neumann term). */
+fcm_status fcm_rhs(const fcm_ctx *ctx, int load_case, double *b_dev);
+
+/* Build the Additive-Schwarz preconditioner (Algorithm 1) with vertex-patch
+ * blocks: for each grid vertex v, the free functions carried by v and by the
+ * edges, faces and cells whose closure contains v.  Extracts A_B = K[B,B],
+ * computes its eigendecomposition, keeps lambda_k > eps * max lambda and
+ * stores A_B+^-1.  Identical blocks (patches of uncut cells with the same
+ * boundary pattern) share one stored factor.  opts may be NULL (eps 1e-13,
+ * FP64). */
+fcm_status fcm_precond_build(fcm_ctx *ctx, const fcm_precond_opts *opts);
+
+/* Preconditioned CG, x0 = 0, stopping when ||S r_i|| / ||S b|| <= tol
+ * (Sec. 5 Eq. (14)) or after maxit iterations.  rhs_dev / u_dev: nrhs
+ * vectors of n_lattice FP64 each, stored one after another (device).
+ * iterations / final_relres may be NULL; with nrhs > 1 they receive the
+ * largest count and residual over the right-hand sides.
+ * Returns FCM_ESTATE before fcm_precond_build, FCM_EINVAL for a non-finite
+ * rhs, FCM_ENOTCONV after maxit (u_dev holds the last iterate),
+ * FCM_EBREAKDOWN when p^T K p <= 0 or a scalar becomes non-finite. */
+fcm_status fcm_pcg_solve(fcm_ctx *ctx, const double *rhs_dev, int nrhs, double tol, int maxit,
+                         double *u_dev, int *iterations, double *final_relres);
+
+/* Same as fcm_pcg_solve with host buffers: rhs_host is copied to the device,
+ * solved, and the solution copied back into u_host before returning. */
+fcm_status fcm_pcg_solve_host(fcm_ctx *ctx, const double *rhs_host, int nrhs, double tol, int maxit,
+                              double *u_host, int *iterations, double *final_relres);
+
+/* Details of the last solve (all right-hand sides folded as in fcm_pcg_solve). */
+fcm_status fcm_last_solve(const fcm_ctx *ctx, fcm_solve_info *out);
+
+/* y_dev = K x_dev (Sec. 2.1 Eq. (1), left-hand side), lattice layout, device. */
+fcm_status fcm_apply_K(fcm_ctx *ctx, const double *x_dev, double *y_dev);
+
+/* z_dev = S r_dev, S = sum_B R_B^T A_B+^-1 R_B (Sec. 3.1 Eq. (5)); device.
+ * FCM_ESTATE before fcm_precond_build. */
+fcm_status fcm_apply_S(fcm_ctx *ctx, const double *r_dev, double *z_dev);
+
+/* Message of the last failure on ctx (ctx may be NULL for setup failures). */
+const char *fcm_last_error(const fcm_ctx *ctx);
+
+/* Release every device and host resource of ctx (NULL is a no-op). */
+void fcm_destroy(fcm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCM_H */

@@ -1,0 +1,452 @@
+// extern "C" entry points of libfcm (declared in include/fcm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fcm_device.cuh"
+
+using fcm::CgScalars;
+using fcm::CgWork;
+
+namespace {
+
+thread_local std::string g_setup_error;
+constexpr int kItersPerGraph = 8;
+
+#define API_CUDA(C, call)                                                                              \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            (C)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                             \
+            return e_ == cudaErrorMemoryAllocation ? FCM_ENOMEM : FCM_ECUDA;                           \
+        }                                                                                              \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(count, 1));
+}
+
+CgWork work_of(fcm_ctx *C)
+{
+    CgWork w;
+    w.x = C->d_x;
+    w.r = C->d_r;
+    w.z = C->d_z;
+    w.p = C->d_p;
+    w.q = C->d_q;
+    w.b = C->d_b;
+    w.partial = C->d_partial;
+    w.counter = C->d_counter;
+    w.s = C->d_s;
+    w.n = C->nlat;
+    w.red_blocks = C->red_blocks;
+    return w;
+}
+
+// The library works on its own stream; every call is ordered after the
+// caller's stream on entry, and the caller's stream after the library's on exit.
+struct StreamScope {
+    fcm_ctx *C;
+    explicit StreamScope(fcm_ctx *c) : C(c)
+    {
+        cudaEventRecord(C->ev_in, C->ustream);
+        cudaStreamWaitEvent(C->stream, C->ev_in, 0);
+    }
+    ~StreamScope()
+    {
+        cudaEventRecord(C->ev_out, C->stream);
+        cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
+    }
+};
+
+void apply_K_dev(fcm_ctx *C, const double *x, double *y, const int *done)
+{
+    fcm::launch_zero(y, C->nlat, done, C->stream);
+    fcm::launch_ebe_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->d_cells, C->cell_colour_off, done, C->stream);
+}
+
+void apply_S_dev(fcm_ctx *C, const double *r, double *z, const int *done)
+{
+    fcm::launch_zero(z, C->nlat, done, C->stream);
+    fcm::launch_schwarz_apply(C->p, C->g, r, z, C->d_f64, C->d_f32, C->d_patches, C->patch_colour_off, done, C->stream);
+}
+
+void destroy_graph(fcm_ctx *C)
+{
+    if (C->graph) cudaGraphExecDestroy(C->graph);
+    C->graph = nullptr;
+}
+
+fcm_status build_graph(fcm_ctx *C)
+{
+    destroy_graph(C);
+    const CgWork w = work_of(C);
+    const int *done = &C->d_s->done;
+    API_CUDA(C, cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < kItersPerGraph; ++it) {
+        apply_K_dev(C, C->d_p, C->d_q, done);
+        fcm::cg_after_K(w, C->stream);
+        apply_S_dev(C, C->d_r, C->d_z, done);
+        fcm::cg_after_S(w, C->stream);
+    }
+    cudaGraph_t graph = nullptr;
+    API_CUDA(C, cudaStreamEndCapture(C->stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&C->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        C->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        C->graph = nullptr;
+        return FCM_ECUDA;
+    }
+    C->graph_iters = kItersPerGraph;
+    return FCM_OK;
+}
+
+// One right-hand side, rhs and u on the device (rhs may alias the context's scratch vector).
+fcm_status solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, double *u, fcm_solve_info &info)
+{
+    const CgWork w = work_of(C);
+    cudaStream_t st = C->stream;
+    fcm::launch_mask_copy(rhs, C->d_b, C->d_mask, C->nlat, st);
+    fcm::cg_residual_norms(w, C->d_b, C->d_b, C->d_out2, st);
+    double bb[2];
+    API_CUDA(C, cudaMemcpyAsync(bb, C->d_out2, sizeof bb, cudaMemcpyDeviceToHost, st));
+    API_CUDA(C, cudaStreamSynchronize(st));
+    if (!std::isfinite(bb[1])) {
+        C->err = "right-hand side has non-finite entries";
+        return FCM_EINVAL;
+    }
+    CgScalars &h = *C->h_s;
+    std::memset(&h, 0, sizeof h);
+    h.tol = tol;
+    h.maxit = maxit;
+    API_CUDA(C, cudaMemcpyAsync(C->d_s, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    API_CUDA(C, cudaEventRecord(C->ev_t0, st));
+    fcm::cg_init_kernels(w, st);
+    apply_S_dev(C, C->d_r, C->d_z, nullptr);
+    fcm::cg_after_first_S(w, st);
+    API_CUDA(C, cudaGetLastError());
+    if (!C->graph) {
+        fcm_status s = build_graph(C);
+        if (s != FCM_OK) return s;
+    }
+    for (;;) {
+        API_CUDA(C, cudaMemcpyAsync(&h, C->d_s, sizeof h, cudaMemcpyDeviceToHost, st));
+        API_CUDA(C, cudaStreamSynchronize(st));
+        if (h.done) break;
+        API_CUDA(C, cudaGraphLaunch(C->graph, st));
+    }
+    API_CUDA(C, cudaEventRecord(C->ev_t1, st));
+    API_CUDA(C, cudaMemcpyAsync(u, C->d_x, sizeof(double) * C->nlat, cudaMemcpyDeviceToDevice, st));
+    // true residual ||b - K x|| / ||b||
+    apply_K_dev(C, C->d_x, C->d_q, nullptr);
+    fcm::cg_residual_norms(w, C->d_q, C->d_b, C->d_out2, st);
+    API_CUDA(C, cudaMemcpyAsync(bb, C->d_out2, sizeof bb, cudaMemcpyDeviceToHost, st));
+    API_CUDA(C, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, C->ev_t0, C->ev_t1);
+    info.iterations = h.it;
+    info.relres = h.relres;
+    info.true_relres = bb[1] > 0.0 ? std::sqrt(bb[0] / bb[1]) : 0.0;
+    info.status = h.status;
+    info.seconds = ms * 1e-3;
+    return (fcm_status)h.status;
+}
+
+void free_ctx(fcm_ctx *C)
+{
+    if (!C) return;
+    destroy_graph(C);
+    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_f64, C->d_f32, C->d_patches,
+                    C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
+                    C->d_out2};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (C->h_s) cudaFreeHost(C->h_s);
+    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1};
+    for (auto e : evs)
+        if (e) cudaEventDestroy(e);
+    if (C->stream) cudaStreamDestroy(C->stream);
+    delete C;
+}
+
+}  // namespace
+
+extern "C" {
+
+fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, double alpha, const fcm_bc *bc,
+                     void *cuda_stream, fcm_ctx **out)
+{
+    if (!out || !grid || !geom || !bc) {
+        g_setup_error = "fcm_setup: null argument";
+        return FCM_EINVAL;
+    }
+    *out = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    fcm_ctx *C = new (std::nothrow) fcm_ctx();
+    if (!C) {
+        g_setup_error = "fcm_setup: out of host memory";
+        return FCM_ENOMEM;
+    }
+    std::string e;
+    try {
+        e = fcm::build_host_problem(*grid, *geom, p, alpha, *bc, C->hp);
+    } catch (const std::bad_alloc &) {
+        e = "out of host memory";
+    } catch (...) {
+        e = "host set-up failed";
+    }
+    if (!e.empty()) {
+        g_setup_error = "fcm_setup: " + e;
+        free_ctx(C);
+        return e == "out of host memory" ? FCM_ENOMEM : FCM_EINVAL;
+    }
+    fcm::HostProblem &hp = C->hp;
+    C->p = p;
+    C->ne = hp.ne;
+    C->nlat = hp.nlat;
+    for (int a = 0; a < 3; ++a) {
+        C->g.n[a] = hp.n[a];
+        C->g.M[a] = hp.M[a];
+    }
+    C->ustream = (cudaStream_t)cuda_stream;
+    auto fail = [&](cudaError_t ce, const char *what) {
+        g_setup_error = std::string("fcm_setup: ") + what + ": " + cudaGetErrorString(ce);
+        free_ctx(C);
+        return ce == cudaErrorMemoryAllocation ? FCM_ENOMEM : FCM_ECUDA;
+    };
+#define SETUP_CUDA(call)                          \
+    do {                                          \
+        cudaError_t ce_ = (call);                 \
+        if (ce_ != cudaSuccess) return fail(ce_, #call); \
+    } while (0)
+    SETUP_CUDA(cudaStreamCreateWithFlags(&C->stream, cudaStreamNonBlocking));
+    SETUP_CUDA(cudaEventCreateWithFlags(&C->ev_in, cudaEventDisableTiming));
+    SETUP_CUDA(cudaEventCreateWithFlags(&C->ev_out, cudaEventDisableTiming));
+    SETUP_CUDA(cudaEventCreate(&C->ev_t0));
+    SETUP_CUDA(cudaEventCreate(&C->ev_t1));
+    const size_t ne2 = (size_t)hp.ne * hp.ne;
+    const int64_t nelem = 1 + hp.ncut;
+    SETUP_CUDA(dalloc(&C->d_elem, ne2 * nelem));
+    SETUP_CUDA(dalloc(&C->d_cell_elem, hp.ncells));
+    SETUP_CUDA(dalloc(&C->d_mask, hp.nlat));
+    SETUP_CUDA(dalloc(&C->d_rhs, hp.nlat));
+    cudaStream_t st = C->stream;
+    SETUP_CUDA(cudaMemcpyAsync(C->d_elem, hp.Kref.data(), sizeof(double) * ne2, cudaMemcpyHostToDevice, st));
+    if (hp.ncut > 0)
+        SETUP_CUDA(cudaMemcpyAsync(C->d_elem + ne2, hp.Kcut.data(), sizeof(double) * ne2 * hp.ncut, cudaMemcpyHostToDevice, st));
+    SETUP_CUDA(cudaMemcpyAsync(C->d_cell_elem, hp.cell_elem.data(), sizeof(int32_t) * hp.ncells, cudaMemcpyHostToDevice, st));
+    SETUP_CUDA(cudaMemcpyAsync(C->d_mask, hp.mask.data(), hp.nlat, cudaMemcpyHostToDevice, st));
+    SETUP_CUDA(cudaMemcpyAsync(C->d_rhs, hp.rhs.data(), sizeof(double) * hp.nlat, cudaMemcpyHostToDevice, st));
+    C->element_bytes = (int64_t)(sizeof(double) * ne2 * nelem);
+    // active cells grouped by parity colour
+    std::vector<int2> cells;
+    cells.reserve(hp.nactive);
+    C->cell_colour_off[0] = 0;
+    for (int col = 0; col < 8; ++col) {
+        for (int64_t ci = 0; ci < hp.ncells; ++ci) {
+            if (hp.cell_elem[ci] < 0) continue;
+            const int cx = (int)(ci % hp.n[0]), cy = (int)((ci / hp.n[0]) % hp.n[1]), cz = (int)(ci / ((int64_t)hp.n[0] * hp.n[1]));
+            if ((cx & 1) + 2 * (cy & 1) + 4 * (cz & 1) != col) continue;
+            cells.push_back(make_int2((int)ci, hp.cell_elem[ci]));
+        }
+        C->cell_colour_off[col + 1] = (int)cells.size();
+    }
+    SETUP_CUDA(dalloc(&C->d_cells, cells.size()));
+    SETUP_CUDA(cudaMemcpyAsync(C->d_cells, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice, st));
+    // solver workspace
+    double **vecs[] = {&C->d_x, &C->d_r, &C->d_z, &C->d_p, &C->d_q, &C->d_b, &C->d_t};
+    for (double **v : vecs) {
+        SETUP_CUDA(dalloc(v, hp.nlat));
+        SETUP_CUDA(cudaMemsetAsync(*v, 0, sizeof(double) * hp.nlat, st));
+    }
+    int64_t rb = (hp.nlat + 255) / 256;
+    C->red_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(rb, 152 * 8));
+    SETUP_CUDA(dalloc(&C->d_partial, 2 * (size_t)C->red_blocks));
+    SETUP_CUDA(dalloc(&C->d_counter, 1));
+    SETUP_CUDA(cudaMemsetAsync(C->d_counter, 0, sizeof(unsigned), st));
+    SETUP_CUDA(dalloc(&C->d_s, 1));
+    SETUP_CUDA(cudaMemsetAsync(C->d_s, 0, sizeof(CgScalars), st));
+    SETUP_CUDA(dalloc(&C->d_out2, 2));
+    SETUP_CUDA(cudaMallocHost((void **)&C->h_s, sizeof(CgScalars)));
+    SETUP_CUDA(cudaStreamSynchronize(st));
+#undef SETUP_CUDA
+    // the element matrices now live on the device only
+    std::vector<double>().swap(hp.Kcut);
+    C->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = C;
+    return FCM_OK;
+}
+
+fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
+{
+    if (!C || !out) return FCM_EINVAL;
+    const fcm::HostProblem &hp = C->hp;
+    out->n_lattice = hp.nlat;
+    out->n_free = hp.nfree;
+    out->n_cells_active = hp.nactive;
+    out->n_cells_cut = hp.ncut;
+    out->n_patches = (int64_t)(hp.n[0] + 1) * (hp.n[1] + 1) * (hp.n[2] + 1);
+    out->n_factors = C->n_factors;
+    out->factor_bytes = C->factor_bytes;
+    out->element_bytes = C->element_bytes;
+    out->max_block = 3 * (2 * hp.p - 1) * (2 * hp.p - 1) * (2 * hp.p - 1);
+    out->p = hp.p;
+    out->setup_seconds = C->setup_seconds;
+    out->precond_seconds = C->precond_seconds;
+    out->n_blocks = C->n_blocks;
+    out->n_blocks_fp32 = C->n_fp32_factors;
+    out->kapply_fmas = (int64_t)hp.nactive * hp.ne * hp.ne;
+    out->sapply_fmas = C->sapply_fmas;
+    out->max_block_cond = C->max_cond;
+    return FCM_OK;
+}
+
+fcm_status fcm_rhs(const fcm_ctx *Cc, int load_case, double *b_dev)
+{
+    fcm_ctx *C = const_cast<fcm_ctx *>(Cc);
+    if (!C || !b_dev) return FCM_EINVAL;
+    if (load_case != 0) {
+        C->err = "fcm_rhs: unknown load case";
+        return FCM_EINVAL;
+    }
+    StreamScope sc(C);
+    API_CUDA(C, cudaMemcpyAsync(b_dev, C->d_rhs, sizeof(double) * C->nlat, cudaMemcpyDeviceToDevice, C->stream));
+    return FCM_OK;
+}
+
+fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
+{
+    if (!C) return FCM_EINVAL;
+    fcm_precond_opts o;
+    o.eps = 1e-13;
+    o.precision = FCM_PREC_FP64;
+    o.cond_fp64 = 1e7;
+    if (opts) o = *opts;
+    if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED) || !(o.cond_fp64 > 0.0)) {
+        C->err = "fcm_precond_build: invalid options";
+        return FCM_EINVAL;
+    }
+    StreamScope sc(C);
+    destroy_graph(C);
+    C->have_precond = false;
+    std::string e;
+    try {
+        e = fcm::build_preconditioner(C, o);
+    } catch (const std::bad_alloc &) {
+        e = "out of host memory";
+    }
+    if (!e.empty()) {
+        C->err = "fcm_precond_build: " + e;
+        return e.find("out of memory") != std::string::npos ? FCM_ENOMEM : FCM_ECUDA;
+    }
+    return FCM_OK;
+}
+
+static fcm_status solve_many(fcm_ctx *C, const double *rhs, int nrhs, double tol, int maxit, double *u, bool host,
+                             int *iterations, double *final_relres)
+{
+    if (!C || !rhs || !u || nrhs < 1 || !(tol > 0.0) || maxit < 1) {
+        if (C) C->err = "fcm_pcg_solve: invalid argument";
+        return FCM_EINVAL;
+    }
+    if (!C->have_precond) {
+        C->err = "fcm_pcg_solve: call fcm_precond_build first";
+        return FCM_ESTATE;
+    }
+    StreamScope sc(C);
+    fcm_solve_info agg = {};
+    agg.status = FCM_OK;
+    fcm_status worst = FCM_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        const double *b = rhs + (size_t)k * C->nlat;
+        double *x = u + (size_t)k * C->nlat;
+        if (host) {
+            API_CUDA(C, cudaMemcpyAsync(C->d_t, b, sizeof(double) * C->nlat, cudaMemcpyHostToDevice, C->stream));
+            b = C->d_t;
+        }
+        fcm_solve_info one = {};
+        fcm_status s = solve_one(C, b, tol, maxit, host ? C->d_t : x, one);
+        if (host) {
+            API_CUDA(C, cudaMemcpyAsync(x, C->d_t, sizeof(double) * C->nlat, cudaMemcpyDeviceToHost, C->stream));
+            API_CUDA(C, cudaStreamSynchronize(C->stream));
+        }
+        if (s == FCM_EINVAL || s == FCM_ECUDA || s == FCM_ENOMEM) return s;
+        agg.iterations = std::max(agg.iterations, one.iterations);
+        agg.relres = std::max(agg.relres, one.relres);
+        agg.true_relres = std::max(agg.true_relres, one.true_relres);
+        agg.seconds += one.seconds;
+        if (s != FCM_OK && worst == FCM_OK) worst = s;
+    }
+    agg.status = worst;
+    C->last = agg;
+    if (iterations) *iterations = agg.iterations;
+    if (final_relres) *final_relres = agg.relres;
+    if (worst == FCM_ENOTCONV) C->err = "fcm_pcg_solve: maxit reached";
+    if (worst == FCM_EBREAKDOWN) C->err = "fcm_pcg_solve: CG breakdown (p^T K p <= 0 or non-finite scalar)";
+    return worst;
+}
+
+fcm_status fcm_pcg_solve(fcm_ctx *C, const double *rhs_dev, int nrhs, double tol, int maxit, double *u_dev,
+                         int *iterations, double *final_relres)
+{
+    return solve_many(C, rhs_dev, nrhs, tol, maxit, u_dev, false, iterations, final_relres);
+}
+
+fcm_status fcm_pcg_solve_host(fcm_ctx *C, const double *rhs_host, int nrhs, double tol, int maxit, double *u_host,
+                              int *iterations, double *final_relres)
+{
+    return solve_many(C, rhs_host, nrhs, tol, maxit, u_host, true, iterations, final_relres);
+}
+
+fcm_status fcm_last_solve(const fcm_ctx *C, fcm_solve_info *out)
+{
+    if (!C || !out) return FCM_EINVAL;
+    *out = C->last;
+    return FCM_OK;
+}
+
+fcm_status fcm_apply_K(fcm_ctx *C, const double *x_dev, double *y_dev)
+{
+    if (!C || !x_dev || !y_dev) return FCM_EINVAL;
+    StreamScope sc(C);
+    fcm::launch_mask_copy(x_dev, C->d_t, C->d_mask, C->nlat, C->stream);
+    apply_K_dev(C, C->d_t, y_dev, nullptr);
+    API_CUDA(C, cudaGetLastError());
+    return FCM_OK;
+}
+
+fcm_status fcm_apply_S(fcm_ctx *C, const double *r_dev, double *z_dev)
+{
+    if (!C || !r_dev || !z_dev) return FCM_EINVAL;
+    if (!C->have_precond) {
+        C->err = "fcm_apply_S: call fcm_precond_build first";
+        return FCM_ESTATE;
+    }
+    StreamScope sc(C);
+    fcm::launch_mask_copy(r_dev, C->d_t, C->d_mask, C->nlat, C->stream);
+    apply_S_dev(C, C->d_t, z_dev, nullptr);
+    API_CUDA(C, cudaGetLastError());
+    return FCM_OK;
+}
+
+const char *fcm_last_error(const fcm_ctx *C)
+{
+    return C ? C->err.c_str() : g_setup_error.c_str();
+}
+
+void fcm_destroy(fcm_ctx *C)
+{
+    if (!C) return;
+    cudaStreamSynchronize(C->stream);
+    free_ctx(C);
+}
+
+}  // extern "C"

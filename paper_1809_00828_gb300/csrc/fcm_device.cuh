@@ -1,0 +1,104 @@
+// Device-side context and kernel launchers of libfcm (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fcm_internal.h"
+
+struct fcm_ctx;
+
+namespace fcm {
+
+// One vertex patch (Schwarz block) as seen by the block-apply kernel.
+struct PatchRec {
+    int64_t off;   // element offset of the block factor in the factor pool
+    int32_t v;     // linear vertex index v_x + (n_x+1)(v_y + (n_y+1) v_z)
+    int32_t prec;  // 0: factor stored in FP64, 1: FP32
+};
+
+// CG scalars kept on the device for the whole solve (no host round trip per iteration).
+struct CgScalars {
+    double rz, pq, zz, zz0, alpha, beta, relres, tol;
+    int it, maxit, done, status;
+};
+
+struct Grid3 {
+    int n[3];   // cells
+    int M[3];   // lattice nodes per axis
+};
+
+// Launchers (all asynchronous on `s`).  `done` may be null.
+void launch_ebe_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
+                      const int2 *cells, const int *colour_off, const int *done, cudaStream_t s);
+void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
+                          const float *fpool32, const PatchRec *patches, const int *colour_off, const int *done,
+                          cudaStream_t s);
+void launch_mask_copy(const double *in, double *out, const uint8_t *mask, int64_t n, cudaStream_t s);
+void launch_zero(double *v, int64_t n, const int *done, cudaStream_t s);
+
+// CG building blocks (fcm_solver.cu)
+struct CgWork {
+    double *x, *r, *z, *p, *q, *b;
+    double *partial;      // reduction partials
+    unsigned *counter;    // last-block ticket
+    CgScalars *s;         // device scalars
+    int64_t n;
+    int red_blocks;
+};
+void cg_init_kernels(const CgWork &w, cudaStream_t s);                  // x=0, r=b
+void cg_after_first_S(const CgWork &w, cudaStream_t s);                 // rz, zz0, p = z
+void cg_after_K(const CgWork &w, cudaStream_t s);                       // pq, alpha, x, r
+void cg_after_S(const CgWork &w, cudaStream_t s);                       // rz, zz, convergence, beta, p
+void cg_residual_norms(const CgWork &w, const double *res, const double *b, double *out2, cudaStream_t s);
+
+// fcm_precond.cu
+std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o);
+
+}  // namespace fcm
+
+struct fcm_ctx {
+    std::string err;
+    cudaStream_t ustream = nullptr;  // caller's stream (ordering with the caller)
+    cudaStream_t stream = nullptr;   // the library's own work stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    fcm::HostProblem hp;
+    fcm::Grid3 g;
+    int p = 0, ne = 0;
+    int64_t nlat = 0;
+    // problem on the device
+    double *d_elem = nullptr;        // [Kref | Kcut_1 | ...], ne*ne each, row-major (symmetric)
+    int32_t *d_cell_elem = nullptr;  // per cell
+    uint8_t *d_mask = nullptr;       // per lattice DOF
+    double *d_rhs = nullptr;         // load case 0
+    int2 *d_cells = nullptr;         // active cells by colour: (cell, element id)
+    int cell_colour_off[9] = {0};
+    int64_t element_bytes = 0;
+    double setup_seconds = 0.0;
+    // preconditioner
+    bool have_precond = false;
+    double *d_f64 = nullptr;         // FP64 factor pool
+    float *d_f32 = nullptr;          // FP32 factor pool (mixed precision)
+    fcm::PatchRec *d_patches = nullptr;
+    int patch_colour_off[9] = {0};
+    int64_t n_factors = 0, factor_bytes = 0, n_fp32_factors = 0;
+    double max_cond = 0.0;
+    int64_t n_blocks = 0, sapply_fmas = 0;
+    int max_block = 0;
+    double precond_seconds = 0.0;
+    // solver workspace
+    double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr,
+           *d_t = nullptr;
+    double *d_partial = nullptr;
+    unsigned *d_counter = nullptr;
+    fcm::CgScalars *d_s = nullptr;
+    fcm::CgScalars *h_s = nullptr;   // pinned
+    double *d_out2 = nullptr;
+    int red_blocks = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    fcm_solve_info last = {};
+};

@@ -1,0 +1,56 @@
+// Internal declarations of libfcm (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fcm.h"
+
+namespace fcm {
+
+// Host-side description of a set-up finite cell problem.  Produced by
+// build_host_problem() from the ABI inputs; uploaded to the device by the
+// context.  Lattice layout as documented in fcm.h.
+struct HostProblem {
+    // grid, order, material
+    int n[3];
+    double lo[3], hi[3], h[3];
+    int p;
+    double alpha;
+    double E, nu;
+    int bc;
+    double traction[3];
+    // geometry
+    int gkind;
+    std::vector<double> sph;       // 4 per sphere
+    int vdim[3];
+    std::vector<uint8_t> vox;
+    double plane[4];
+    int depth;
+    // sizes
+    int M[3];
+    int64_t nnodes, nlat;
+    int ne;                         // 3 (p+1)^3, rows of an element matrix
+    int64_t ncells;
+    // results
+    std::vector<int32_t> cell_elem; // -1 inactive, 0 uncut (reference matrix), 1+k k-th cut cell
+    std::vector<double> eta;        // volume fraction per cell
+    std::vector<double> Kref;       // ne x ne
+    std::vector<double> Kcut;       // ncut x ne x ne
+    int64_t ncut = 0;
+    int64_t nactive = 0;
+    std::vector<uint8_t> mask;      // per lattice DOF: 1 = free
+    int64_t nfree = 0;
+    std::vector<double> rhs;        // load case 0, lattice layout
+};
+
+// Builds everything on the host.  Returns an empty string on success, else
+// the error message.  nthreads <= 0 uses the hardware concurrency.
+std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, int p, double alpha,
+                               const fcm_bc &bc, HostProblem &out, int nthreads = 0);
+
+// Gauss-Legendre rule with n points on [-1, 1].
+void gauss_legendre(int n, double *x, double *w);
+
+}  // namespace fcm

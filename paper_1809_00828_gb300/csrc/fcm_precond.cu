@@ -1,0 +1,493 @@
+// Additive-Schwarz preconditioner set-up (Algorithm 1 of Jomo et al.,
+// arXiv:1809.00828): getBlocks -> extractSubMatrix -> computePseudoInverse ->
+// store, with the eigenvalue filter of Sec. 3.2 Eqs. (11)-(13).
+//
+// Blocks are vertex patches: for grid vertex v the free functions carried by v
+// and by the edges, faces and cells whose closure contains v.  In lattice
+// terms this is the box [p v - (p-1), p v + (p-1)] per axis (clipped at the
+// domain), so a block is stored densely over its box, with zero rows and
+// columns for box DOFs that are not free.  Patches whose cells are all uncut
+// (or inactive) and that share the same clipping and activity pattern have
+// identical blocks and share one stored factor.
+//
+// Device pipeline per group of equal-size blocks: assemble A_B from the element
+// matrices of the (up to 8) patch cells, pad the diagonal of non-free rows
+// with max_i A_ii (which leaves lambda_max and the filtered set unchanged),
+// batched symmetric eigensolve (cuSOLVER), filter/invert the eigenvalues,
+// F = V diag(lambda+^-1) V^T (cuBLAS batched GEMM), symmetrise, zero the
+// non-free rows/columns.  Mixed precision keeps factors whose retained
+// condition number exceeds cond_fp64 in FP64 and stores the rest in FP32.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fcm_device.cuh"
+
+namespace fcm {
+
+namespace {
+
+#define PC_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return std::string(#call) + ": " + cudaGetErrorString(e_);              \
+    } while (0)
+#define PC_SOLVER(call)                                                                                \
+    do {                                                                                               \
+        cusolverStatus_t e_ = (call);                                                                  \
+        if (e_ != CUSOLVER_STATUS_SUCCESS) return std::string(#call) + ": cusolver status " + std::to_string((int)e_); \
+    } while (0)
+#define PC_BLAS(call)                                                                                  \
+    do {                                                                                               \
+        cublasStatus_t e_ = (call);                                                                    \
+        if (e_ != CUBLAS_STATUS_SUCCESS) return std::string(#call) + ": cublas status " + std::to_string((int)e_); \
+    } while (0)
+
+struct BoxInfo {
+    int lo[3], d[3], n;
+};
+
+__host__ __device__ inline BoxInfo patch_box(int p, const Grid3 &g, int vx, int vy, int vz)
+{
+    BoxInfo b;
+    const int v[3] = {vx, vy, vz};
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = v[a] * p - (p - 1);
+        if (b.lo[a] < 0) b.lo[a] = 0;
+        int hi = v[a] * p + (p - 1);
+        if (hi > g.M[a] - 1) hi = g.M[a] - 1;
+        b.d[a] = hi - b.lo[a] + 1;
+    }
+    b.n = 3 * b.d[0] * b.d[1] * b.d[2];
+    return b;
+}
+
+// A_B[i][j] = K[g_i][g_j] summed over the active cells of the patch (0 if i or j is not free).
+__global__ void assemble_kernel(int p, Grid3 g, const int *__restrict__ rep, int n, double *__restrict__ A,
+                                const double *__restrict__ elem, const int32_t *__restrict__ cell_elem,
+                                const uint8_t *__restrict__ mask)
+{
+    const int b = blockIdx.y;
+    const int nv0 = g.n[0] + 1, nv1 = g.n[1] + 1;
+    const int v = rep[b];
+    const int vx = v % nv0, vy = (v / nv0) % nv1, vz = v / (nv0 * nv1);
+    const BoxInfo bx = patch_box(p, g, vx, vy, vz);
+    const int q = p + 1, ne = 3 * q * q * q;
+    double *Ab = A + (size_t)b * n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        int Li[3], Lj[3];
+        const int ni = i / 3, nj = j / 3, ci = i % 3, cj = j % 3;
+        Li[0] = bx.lo[0] + ni % bx.d[0];
+        Li[1] = bx.lo[1] + (ni / bx.d[0]) % bx.d[1];
+        Li[2] = bx.lo[2] + ni / (bx.d[0] * bx.d[1]);
+        Lj[0] = bx.lo[0] + nj % bx.d[0];
+        Lj[1] = bx.lo[1] + (nj / bx.d[0]) % bx.d[1];
+        Lj[2] = bx.lo[2] + nj / (bx.d[0] * bx.d[1]);
+        const int64_t gi = 3 * (Li[0] + (int64_t)g.M[0] * (Li[1] + (int64_t)g.M[1] * Li[2])) + ci;
+        const int64_t gj = 3 * (Lj[0] + (int64_t)g.M[0] * (Lj[1] + (int64_t)g.M[1] * Lj[2])) + cj;
+        double s = 0.0;
+        if (mask[gi] && mask[gj]) {
+            for (int t = 0; t < 8; ++t) {
+                int c[3] = {vx - 1 + (t & 1), vy - 1 + ((t >> 1) & 1), vz - 1 + ((t >> 2) & 1)};
+                if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= g.n[0] || c[1] >= g.n[1] || c[2] >= g.n[2]) continue;
+                const int el = cell_elem[c[0] + (int64_t)g.n[0] * (c[1] + (int64_t)g.n[1] * c[2])];
+                if (el < 0) continue;
+                int li[3], lj[3];
+                bool in = true;
+                for (int a = 0; a < 3; ++a) {
+                    li[a] = Li[a] - p * c[a];
+                    lj[a] = Lj[a] - p * c[a];
+                    in = in && li[a] >= 0 && li[a] <= p && lj[a] >= 0 && lj[a] <= p;
+                }
+                if (!in) continue;
+                const int Ii = li[0] + q * (li[1] + q * li[2]), Ij = lj[0] + q * (lj[1] + q * lj[2]);
+                s += elem[(size_t)el * ne * ne + (size_t)(3 * Ii + ci) * ne + 3 * Ij + cj];
+            }
+        }
+        Ab[e] = s;
+    }
+}
+
+// Non-free diagonal entries get max_i A_ii: decoupled eigenpairs that neither
+// raise lambda_max nor fall under the filter; removed again in finalize.
+__global__ void pad_kernel(double *A, int n)
+{
+    double *Ab = A + (size_t)blockIdx.x * n * n;
+    __shared__ double smax[256];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, Ab[(size_t)i * n + i]);
+    smax[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double d = smax[0] > 0.0 ? smax[0] : 1.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        bool zero_row = true;
+        for (int j = 0; j < n && zero_row; ++j) zero_row = Ab[(size_t)i * n + j] == 0.0;
+        if (zero_row) Ab[(size_t)i * n + i] = d;
+    }
+}
+
+// U = V diag(lambda+^-1), lambda+^-1 = 1/lambda for lambda > eps * lambda_max, else 0
+// (eps < 0: every nonzero eigenvalue inverted, the unstabilised inverse).
+__global__ void invert_kernel(const double *V, const double *W, double *U, int n, double eps, double *cond,
+                              int *nfilt)
+{
+    const int b = blockIdx.x;
+    const double *w = W + (size_t)b * n;
+    const double lmax = w[n - 1];  // ascending order
+    const double thr = eps * lmax;
+    __shared__ double smin[256];
+    __shared__ int sfilt[256];
+    double lmin = INFINITY;
+    int filt = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        if (eps < 0.0 || w[k] > thr) {
+            if (w[k] > 0.0) lmin = fmin(lmin, w[k]);
+        } else {
+            ++filt;
+        }
+    }
+    smin[threadIdx.x] = lmin;
+    sfilt[threadIdx.x] = filt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+            sfilt[threadIdx.x] += sfilt[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        cond[b] = lmax / smin[0];
+        nfilt[b] = sfilt[0];
+    }
+    const double *Vb = V + (size_t)b * n * n;
+    double *Ub = U + (size_t)b * n * n;
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+        const int k = (int)(e / n);  // column-major: e = i + k n
+        const double lk = w[k];
+        double inv = 0.0;
+        if (eps < 0.0) inv = lk != 0.0 ? 1.0 / lk : 0.0;
+        else if (lk > thr) inv = 1.0 / lk;
+        Ub[e] = Vb[e] * inv;
+    }
+}
+
+// F = sym(C) on free rows/columns, 0 elsewhere; written to the FP64 pool.
+__global__ void finalize_kernel(const double *C, int n, const int *rep, const int64_t *off, double *pool, int p,
+                                Grid3 g, const uint8_t *mask)
+{
+    const int b = blockIdx.y;
+    const int nv0 = g.n[0] + 1, nv1 = g.n[1] + 1;
+    const int v = rep[b];
+    const BoxInfo bx = patch_box(p, g, v % nv0, (v / nv0) % nv1, v / (nv0 * nv1));
+    const double *Cb = C + (size_t)b * n * n;
+    double *F = pool + off[b];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        auto gidx = [&](int t) {
+            const int nl = t / 3;
+            const int x = bx.lo[0] + nl % bx.d[0], y = bx.lo[1] + (nl / bx.d[0]) % bx.d[1], z = bx.lo[2] + nl / (bx.d[0] * bx.d[1]);
+            return 3 * (x + (int64_t)g.M[0] * (y + (int64_t)g.M[1] * z)) + t % 3;
+        };
+        const bool on = mask[gidx(i)] && mask[gidx(j)];
+        F[e] = on ? 0.5 * (Cb[(size_t)i + (size_t)j * n] + Cb[(size_t)j + (size_t)i * n]) : 0.0;
+    }
+}
+
+__global__ void to_f32_kernel(const double *in, float *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+struct FactorInfo {
+    int rep;      // representative vertex
+    int n;        // box size
+    int64_t off;  // offset in the FP64 staging pool
+    double cond;
+    int nfilt;
+};
+
+}  // namespace
+
+std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const HostProblem &hp = C->hp;
+    const int p = C->p;
+    const Grid3 g = C->g;
+    const int nv[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
+    const int64_t npatch = (int64_t)nv[0] * nv[1] * nv[2];
+    cudaStream_t st = C->stream;
+
+    // ---- getBlocks: vertex patches, deduplicated by signature
+    std::vector<int> patch_factor(npatch, -1);
+    std::vector<FactorInfo> fac;
+    std::map<uint64_t, int> regular;
+    for (int vz = 0; vz < nv[2]; ++vz)
+        for (int vy = 0; vy < nv[1]; ++vy)
+            for (int vx = 0; vx < nv[0]; ++vx) {
+                const int v = vx + nv[0] * (vy + nv[1] * vz);
+                const BoxInfo bx = patch_box(p, g, vx, vy, vz);
+                bool any_free = false;
+                for (int t = 0; t < bx.n && !any_free; ++t) {
+                    const int nl = t / 3;
+                    const int x = bx.lo[0] + nl % bx.d[0], y = bx.lo[1] + (nl / bx.d[0]) % bx.d[1], z = bx.lo[2] + nl / (bx.d[0] * bx.d[1]);
+                    any_free = hp.mask[3 * (x + (int64_t)g.M[0] * (y + (int64_t)g.M[1] * z)) + t % 3] != 0;
+                }
+                if (!any_free) continue;
+                bool cut = false;
+                uint64_t key = 0;
+                for (int t = 0; t < 8; ++t) {
+                    const int c[3] = {vx - 1 + (t & 1), vy - 1 + ((t >> 1) & 1), vz - 1 + ((t >> 2) & 1)};
+                    int el = -2;
+                    if (c[0] >= 0 && c[1] >= 0 && c[2] >= 0 && c[0] < g.n[0] && c[1] < g.n[1] && c[2] < g.n[2])
+                        el = hp.cell_elem[c[0] + (int64_t)g.n[0] * (c[1] + (int64_t)g.n[1] * c[2])];
+                    if (el > 0) cut = true;
+                    key |= (uint64_t)(el == 0) << t;
+                }
+                int fid;
+                if (!cut) {
+                    const int cl[3] = {(vx == 0) + 2 * (vx == g.n[0]), (vy == 0) + 2 * (vy == g.n[1]), (vz == 0) + 2 * (vz == g.n[2])};
+                    key |= (uint64_t)(cl[0] + 4 * cl[1] + 16 * cl[2]) << 8;
+                    auto it = regular.find(key);
+                    if (it != regular.end()) {
+                        patch_factor[v] = it->second;
+                        continue;
+                    }
+                    fid = (int)fac.size();
+                    regular[key] = fid;
+                } else {
+                    fid = (int)fac.size();
+                }
+                fac.push_back({v, bx.n, 0, 0.0, 0});
+                patch_factor[v] = fid;
+            }
+
+    // ---- group by size, staging offsets
+    std::map<int, std::vector<int>> groups;
+    for (int f = 0; f < (int)fac.size(); ++f) groups[fac[f].n].push_back(f);
+    int64_t total = 0;
+    int maxn = 0;
+    for (auto &kv : groups)
+        for (int f : kv.second) {
+            fac[f].off = total;
+            total += (int64_t)kv.first * kv.first;
+            maxn = std::max(maxn, kv.first);
+        }
+
+    double *stage = nullptr;
+    PC_CUDA(cudaMalloc(&stage, sizeof(double) * std::max<int64_t>(total, 1)));
+    struct Guard {
+        std::vector<void *> ptrs;
+        ~Guard()
+        {
+            for (void *q : ptrs) cudaFree(q);
+        }
+    } guard;
+    guard.ptrs.push_back(stage);
+
+    cusolverDnHandle_t sh = nullptr;
+    cublasHandle_t bh = nullptr;
+    cusolverDnParams_t params = nullptr;
+    PC_SOLVER(cusolverDnCreate(&sh));
+    struct HGuard {
+        cusolverDnHandle_t s;
+        cublasHandle_t b;
+        cusolverDnParams_t p;
+        ~HGuard()
+        {
+            if (p) cusolverDnDestroyParams(p);
+            if (s) cusolverDnDestroy(s);
+            if (b) cublasDestroy(b);
+        }
+    } hguard{sh, nullptr, nullptr};
+    PC_BLAS(cublasCreate(&bh));
+    hguard.b = bh;
+    PC_SOLVER(cusolverDnCreateParams(&params));
+    hguard.p = params;
+    PC_SOLVER(cusolverDnSetStream(sh, st));
+    PC_BLAS(cublasSetStream(bh, st));
+
+    for (auto &kv : groups) {
+        const int n = kv.first;
+        const std::vector<int> &ids = kv.second;
+        const size_t n2 = (size_t)n * n;
+        int chunk = (int)std::max<size_t>(1, std::min<size_t>(ids.size(), (size_t)(1536ull << 20) / (3 * n2 * sizeof(double))));
+        double *dA = nullptr, *dU = nullptr, *dC = nullptr, *dW = nullptr, *dcond = nullptr;
+        int *dinfo = nullptr, *drep = nullptr, *dfilt = nullptr;
+        int64_t *doff = nullptr;
+        PC_CUDA(cudaMalloc(&dA, sizeof(double) * n2 * chunk));
+        guard.ptrs.push_back(dA);
+        PC_CUDA(cudaMalloc(&dU, sizeof(double) * n2 * chunk));
+        guard.ptrs.push_back(dU);
+        PC_CUDA(cudaMalloc(&dC, sizeof(double) * n2 * chunk));
+        guard.ptrs.push_back(dC);
+        PC_CUDA(cudaMalloc(&dW, sizeof(double) * n * chunk));
+        guard.ptrs.push_back(dW);
+        PC_CUDA(cudaMalloc(&dcond, sizeof(double) * chunk));
+        guard.ptrs.push_back(dcond);
+        PC_CUDA(cudaMalloc(&dinfo, sizeof(int) * chunk));
+        guard.ptrs.push_back(dinfo);
+        PC_CUDA(cudaMalloc(&dfilt, sizeof(int) * chunk));
+        guard.ptrs.push_back(dfilt);
+        PC_CUDA(cudaMalloc(&drep, sizeof(int) * chunk));
+        guard.ptrs.push_back(drep);
+        PC_CUDA(cudaMalloc(&doff, sizeof(int64_t) * chunk));
+        guard.ptrs.push_back(doff);
+
+        // eigen workspace: batched API if it accepts this size, else one matrix at a time
+        bool batched = true;
+        size_t dws = 0, hws = 0;
+        if (cusolverDnXsyevBatched_bufferSize(sh, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F,
+                                              dA, n, CUDA_R_64F, dW, CUDA_R_64F, &dws, &hws, chunk) != CUSOLVER_STATUS_SUCCESS)
+            batched = false;
+        if (!batched) {
+            PC_SOLVER(cusolverDnXsyevd_bufferSize(sh, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F,
+                                                  dA, n, CUDA_R_64F, dW, CUDA_R_64F, &dws, &hws));
+        }
+        void *dwork = nullptr;
+        std::vector<char> hwork(std::max<size_t>(hws, 1));
+        PC_CUDA(cudaMalloc(&dwork, std::max<size_t>(dws, 16)));
+        guard.ptrs.push_back(dwork);
+
+        std::vector<int> hrep(chunk), hinfo(chunk), hfilt(chunk);
+        std::vector<int64_t> hoff(chunk);
+        std::vector<double> hcond(chunk);
+        for (size_t s0 = 0; s0 < ids.size(); s0 += chunk) {
+            const int B = (int)std::min<size_t>(chunk, ids.size() - s0);
+            for (int b = 0; b < B; ++b) {
+                hrep[b] = fac[ids[s0 + b]].rep;
+                hoff[b] = fac[ids[s0 + b]].off;
+            }
+            PC_CUDA(cudaMemcpyAsync(drep, hrep.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+            PC_CUDA(cudaMemcpyAsync(doff, hoff.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, st));
+            const int gx = (int)std::min<int64_t>(((int64_t)n2 + 255) / 256, 64);
+            assemble_kernel<<<dim3(gx, B), 256, 0, st>>>(p, g, drep, n, dA, C->d_elem, C->d_cell_elem, C->d_mask);
+            pad_kernel<<<B, 256, 0, st>>>(dA, n);
+            PC_CUDA(cudaGetLastError());
+            if (batched) {
+                PC_SOLVER(cusolverDnXsyevBatched(sh, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, dA,
+                                                 n, CUDA_R_64F, dW, CUDA_R_64F, dwork, dws, hwork.data(), hws, dinfo, B));
+            } else {
+                for (int b = 0; b < B; ++b)
+                    PC_SOLVER(cusolverDnXsyevd(sh, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F,
+                                               dA + n2 * b, n, CUDA_R_64F, dW + (size_t)n * b, CUDA_R_64F, dwork, dws,
+                                               hwork.data(), hws, dinfo + b));
+            }
+            invert_kernel<<<B, 256, 0, st>>>(dA, dW, dU, n, o.eps, dcond, dfilt);
+            PC_CUDA(cudaGetLastError());
+            const double one = 1.0, zero = 0.0;
+            // C = U V^T (column-major): C(i,j) = sum_k U(i,k) V(j,k)
+            PC_BLAS(cublasDgemmStridedBatched(bh, CUBLAS_OP_N, CUBLAS_OP_T, n, n, n, &one, dU, n, (long long)n2, dA, n,
+                                              (long long)n2, &zero, dC, n, (long long)n2, B));
+            finalize_kernel<<<dim3(gx, B), 256, 0, st>>>(dC, n, drep, doff, stage, p, g, C->d_mask);
+            PC_CUDA(cudaGetLastError());
+            PC_CUDA(cudaMemcpyAsync(hinfo.data(), dinfo, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+            PC_CUDA(cudaMemcpyAsync(hcond.data(), dcond, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+            PC_CUDA(cudaMemcpyAsync(hfilt.data(), dfilt, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+            PC_CUDA(cudaStreamSynchronize(st));
+            for (int b = 0; b < B; ++b) {
+                if (hinfo[b] != 0) return "eigensolver failed for a block (info " + std::to_string(hinfo[b]) + ")";
+                fac[ids[s0 + b]].cond = hcond[b];
+                fac[ids[s0 + b]].nfilt = hfilt[b];
+            }
+        }
+    }
+
+    // ---- final pools (FP64 only, or FP32 + FP64 for the ill-conditioned blocks)
+    const bool mixed = o.precision == FCM_PREC_MIXED;
+    std::vector<int> prec(fac.size(), 0);
+    std::vector<int64_t> off(fac.size(), 0);
+    int64_t n64 = 0, n32 = 0;
+    for (size_t f = 0; f < fac.size(); ++f) {
+        const int64_t sz = (int64_t)fac[f].n * fac[f].n;
+        if (mixed && fac[f].cond <= o.cond_fp64) {
+            prec[f] = 1;
+            off[f] = n32;
+            n32 += sz;
+        } else {
+            off[f] = n64;
+            n64 += sz;
+        }
+    }
+    if (C->d_f64) cudaFree(C->d_f64);
+    if (C->d_f32) cudaFree(C->d_f32);
+    C->d_f64 = nullptr;
+    C->d_f32 = nullptr;
+    if (!mixed) {
+        C->d_f64 = stage;  // staging layout is final
+        guard.ptrs.erase(std::find(guard.ptrs.begin(), guard.ptrs.end(), (void *)stage));
+    } else {
+        if (n64 > 0) PC_CUDA(cudaMalloc(&C->d_f64, sizeof(double) * n64));
+        if (n32 > 0) PC_CUDA(cudaMalloc(&C->d_f32, sizeof(float) * n32));
+        for (size_t f = 0; f < fac.size(); ++f) {
+            const int64_t sz = (int64_t)fac[f].n * fac[f].n;
+            if (prec[f] == 1)
+                to_f32_kernel<<<(int)std::min<int64_t>((sz + 255) / 256, 1024), 256, 0, st>>>(stage + fac[f].off, C->d_f32 + off[f], sz);
+            else
+                PC_CUDA(cudaMemcpyAsync(C->d_f64 + off[f], stage + fac[f].off, sizeof(double) * sz, cudaMemcpyDeviceToDevice, st));
+        }
+        PC_CUDA(cudaGetLastError());
+        PC_CUDA(cudaStreamSynchronize(st));
+    }
+    if (!mixed)
+        for (size_t f = 0; f < fac.size(); ++f) off[f] = fac[f].off;
+
+    // ---- patch records, grouped by colour (vertex parity)
+    std::vector<PatchRec> recs[8];
+    for (int vz = 0; vz < nv[2]; ++vz)
+        for (int vy = 0; vy < nv[1]; ++vy)
+            for (int vx = 0; vx < nv[0]; ++vx) {
+                const int v = vx + nv[0] * (vy + nv[1] * vz);
+                const int f = patch_factor[v];
+                if (f < 0) continue;
+                recs[(vx & 1) + 2 * (vy & 1) + 4 * (vz & 1)].push_back({off[f], v, prec[f]});
+            }
+    std::vector<PatchRec> all;
+    C->n_blocks = 0;
+    C->sapply_fmas = 0;
+    for (int c = 0; c < 8; ++c)
+        for (const PatchRec &r : recs[c]) {
+            const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
+            const BoxInfo bx = patch_box(p, g, r.v % nvx, (r.v / nvx) % nvy, r.v / (nvx * nvy));
+            C->n_blocks += 1;
+            C->sapply_fmas += (int64_t)bx.n * bx.n;
+        }
+    C->patch_colour_off[0] = 0;
+    for (int c = 0; c < 8; ++c) {
+        all.insert(all.end(), recs[c].begin(), recs[c].end());
+        C->patch_colour_off[c + 1] = (int)all.size();
+    }
+    if (C->d_patches) cudaFree(C->d_patches);
+    C->d_patches = nullptr;
+    PC_CUDA(cudaMalloc(&C->d_patches, sizeof(PatchRec) * std::max<size_t>(all.size(), 1)));
+    PC_CUDA(cudaMemcpyAsync(C->d_patches, all.data(), sizeof(PatchRec) * all.size(), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    C->n_factors = (int64_t)fac.size();
+    C->factor_bytes = n64 * 8 + n32 * 4;
+    C->max_block = maxn;
+    C->n_fp32_factors = 0;
+    C->max_cond = 0.0;
+    for (size_t f = 0; f < fac.size(); ++f) {
+        C->n_fp32_factors += prec[f];
+        if (std::isfinite(fac[f].cond)) C->max_cond = std::max(C->max_cond, fac[f].cond);
+    }
+    C->have_precond = true;
+    C->precond_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return std::string();
+}
+
+}  // namespace fcm

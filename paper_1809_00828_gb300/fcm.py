@@ -1,0 +1,211 @@
+"""Python binding of libfcm.so (the C ABI in include/fcm.h).
+
+Argument marshalling only: every step of the set-up and the solve runs in the
+library.  PyTorch provides device memory and the current CUDA stream.  The
+binding fails loudly when the library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfcm.so")
+
+FCM_OK, FCM_EINVAL, FCM_ENOMEM, FCM_ECUDA, FCM_ENOTCONV, FCM_EBREAKDOWN, FCM_ETIMEOUT, FCM_ESTATE = range(8)
+STATUS_NAMES = ["FCM_OK", "FCM_EINVAL", "FCM_ENOMEM", "FCM_ECUDA", "FCM_ENOTCONV", "FCM_EBREAKDOWN",
+                "FCM_ETIMEOUT", "FCM_ESTATE"]
+PREC_FP64, PREC_MIXED = 0, 1
+
+# Every symbol include/fcm.h declares (checked by the tests).
+EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_solve", "fcm_pcg_solve_host",
+            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_last_error", "fcm_destroy")
+
+
+class FcmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {message}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nsph", ctypes.c_int), ("sph", ctypes.POINTER(ctypes.c_double)),
+                ("vdim", ctypes.c_int * 3), ("vox", ctypes.POINTER(ctypes.c_ubyte)), ("plane", ctypes.c_double * 4),
+                ("octree_depth", ctypes.c_int)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("bc", ctypes.c_int), ("traction", ctypes.c_double * 3)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_lattice", ctypes.c_int64), ("n_free", ctypes.c_int64), ("n_cells_active", ctypes.c_int64),
+                ("n_cells_cut", ctypes.c_int64), ("n_patches", ctypes.c_int64), ("n_factors", ctypes.c_int64),
+                ("factor_bytes", ctypes.c_int64), ("element_bytes", ctypes.c_int64), ("max_block", ctypes.c_int),
+                ("p", ctypes.c_int), ("setup_seconds", ctypes.c_double), ("precond_seconds", ctypes.c_double),
+                ("n_blocks", ctypes.c_int64), ("n_blocks_fp32", ctypes.c_int64), ("kapply_fmas", ctypes.c_int64),
+                ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double)]
+
+
+class PrecondOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("cond_fp64", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("relres", ctypes.c_double), ("true_relres", ctypes.c_double),
+                ("status", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfcm.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.fcm_setup.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Geometry), ctypes.c_int, ctypes.c_double,
+                            ctypes.POINTER(BC), P, ctypes.POINTER(P)]
+    L.fcm_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.fcm_rhs.argtypes = [P, ctypes.c_int, P]
+    L.fcm_precond_build.argtypes = [P, ctypes.POINTER(PrecondOpts)]
+    L.fcm_pcg_solve.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, ip, dp]
+    L.fcm_pcg_solve_host.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, ip, dp]
+    L.fcm_last_solve.argtypes = [P, ctypes.POINTER(SolveInfo)]
+    L.fcm_apply_K.argtypes = [P, P, P]
+    L.fcm_apply_S.argtypes = [P, P, P]
+    L.fcm_last_error.argtypes = [P]
+    L.fcm_last_error.restype = ctypes.c_char_p
+    L.fcm_destroy.argtypes = [P]
+    for f in EXPORTED:
+        if f not in ("fcm_last_error", "fcm_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+    L.fcm_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One finite cell problem on the current CUDA device (libfcm context)."""
+
+    def __init__(self, workload, stream=None):
+        import torch
+
+        self._torch = torch
+        L = load()
+        w = workload
+        g = Grid()
+        g.n[:] = list(w.n)
+        g.lo[:] = list(w.lo)
+        g.hi[:] = list(w.hi)
+        geo = Geometry()
+        geo.kind = w.geometry.kind
+        self._sph = w.geometry.sphere_array()
+        geo.nsph = self._sph.shape[0]
+        geo.sph = self._sph.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if w.geometry.voxels is not None:
+            self._vox = np.ascontiguousarray(w.geometry.voxels, dtype=np.uint8)
+            geo.vdim[:] = [self._vox.shape[2], self._vox.shape[1], self._vox.shape[0]]
+            geo.vox = self._vox.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        geo.plane[:] = list(w.geometry.plane)
+        geo.octree_depth = w.geometry.octree_depth
+        bc = BC()
+        bc.E, bc.nu, bc.bc = w.E, w.nu, w.bc
+        bc.traction[:] = list(w.traction)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.ctx = ctypes.c_void_p()
+        st = L.fcm_setup(ctypes.byref(g), ctypes.byref(geo), w.p, w.alpha, ctypes.byref(bc), ctypes.c_void_p(stream),
+                         ctypes.byref(self.ctx))
+        if st != FCM_OK:
+            raise FcmError(st, L.fcm_last_error(None).decode())
+        self.workload = w
+        self.info = self.get_info()
+        self.n = self.info["n_lattice"]
+
+    def _check(self, st):
+        if st != FCM_OK:
+            raise FcmError(st, load().fcm_last_error(self.ctx).decode())
+
+    def get_info(self):
+        inf = Info()
+        self._check(load().fcm_info(self.ctx, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def empty(self, nrhs=1):
+        return self._torch.zeros(nrhs * self.n, dtype=self._torch.float64, device="cuda")
+
+    def rhs(self, load_case=0):
+        b = self.empty()
+        self._check(load().fcm_rhs(self.ctx, load_case, _ptr(b)))
+        return b
+
+    def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7):
+        o = PrecondOpts()
+        o.eps = eps
+        o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        o.cond_fp64 = cond_fp64
+        self._check(load().fcm_precond_build(self.ctx, ctypes.byref(o)))
+        self.info = self.get_info()
+
+    def pcg_solve(self, b, tol, maxit=100000, out=None, check=True):
+        nrhs = b.numel() // self.n
+        u = out if out is not None else self.empty(nrhs)
+        its = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = load().fcm_pcg_solve(self.ctx, _ptr(b), nrhs, tol, maxit, _ptr(u), ctypes.byref(its), ctypes.byref(rel))
+        if check:
+            self._check(st)
+        return u, its.value, rel.value, st
+
+    def pcg_solve_host(self, b_host: np.ndarray, tol, maxit=100000, out: np.ndarray | None = None):
+        nrhs = b_host.size // self.n
+        u = out if out is not None else np.empty_like(b_host)
+        its = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = load().fcm_pcg_solve_host(self.ctx, ctypes.c_void_p(b_host.ctypes.data), nrhs, tol, maxit,
+                                       ctypes.c_void_p(u.ctypes.data), ctypes.byref(its), ctypes.byref(rel))
+        self._check(st)
+        return u, its.value, rel.value
+
+    def last_solve(self):
+        s = SolveInfo()
+        self._check(load().fcm_last_solve(self.ctx, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in SolveInfo._fields_}
+
+    def apply_K(self, x, out=None):
+        y = out if out is not None else self.empty()
+        self._check(load().fcm_apply_K(self.ctx, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_S(self, r, out=None):
+        z = out if out is not None else self.empty()
+        self._check(load().fcm_apply_S(self.ctx, _ptr(r), _ptr(z)))
+        return z
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            load().fcm_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances:
+  * K x: the element matrices of both sides integrate the same polynomials
+    on the same octree leaves; they differ by rounding only, so entries agree
+    to ~1e-13 of max|K_e| and K x to 1e-12 relative (max-norm).
+  * S r: each block factor is a pseudo inverse computed by a different
+    eigensolver.  Perturbation theory bounds the relative error of an
+    inverted eigenpair by ~ n eps_mach cond(A_B); the comparison is therefore
+    made in the energy norm of K (directions with small eigenvalues, where S
+    is large, weigh little) and bounded by 1e-9, and in the max norm by
+    max_B cond(A_B) * 1e-13.
+  * PCG: the relative energy-norm error against the oracle's dense solve
+    (Eq. (15)) must be below 1e-6 (1e-8 where the tolerance allows), and the
+    iteration count must equal the oracle's within 2.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1809_00828_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _solver(w):
+    from paper_1809_00828_gb300 import fcm
+    return fcm.Solver(w)
+
+
+def _lat(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module")
+def single():
+    w = I.workload_single_void(0)
+    P = O.Problem.from_workload(w)
+    P.precond_build(0)
+    s = _solver(w)
+    s.precond_build()
+    yield w, P, s
+    s.close()
+
+
+def test_rhs_and_free_dofs_match(single):
+    w, P, s = single
+    b = s.rhs().cpu().numpy()
+    assert s.info["n_free"] == P.nfree == 1944
+    nz = np.zeros(s.n, dtype=bool)
+    nz[P.free_lat] = True
+    assert not b[~nz].any()
+    assert np.abs(b[P.free_lat] - P.rhs()).max() <= 1e-14 * np.abs(P.rhs()).max()
+
+
+def test_apply_K_matches_oracle(single):
+    w, P, s = single
+    x = I.random_vector(101, s.n)
+    y = s.apply_K(_lat(x)).cpu().numpy()
+    y_ref = P.apply_K(x[P.free_lat])
+    assert np.abs(y[P.free_lat] - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+    mask = np.zeros(s.n, dtype=bool)
+    mask[P.free_lat] = True
+    assert not y[~mask].any()
+
+
+def test_apply_S_matches_oracle(single):
+    w, P, s = single
+    r = I.random_vector(202, s.n)
+    z = s.apply_S(_lat(r)).cpu().numpy()[P.free_lat]
+    z_ref = P.apply_S(r[P.free_lat])
+    K = P.csr()
+    d = z - z_ref
+    e_energy = np.sqrt(abs(d @ (K @ d)) / (z_ref @ (K @ z_ref)))
+    assert e_energy < 1e-9
+    cond = max(P.block(b)[2][0] for b in range(P.nblocks()))
+    assert np.abs(d).max() <= max(1e-12, cond * 1e-13) * np.abs(z_ref).max()
+
+
+def test_pcg_matches_oracle_and_dense_solve(single):
+    w, P, s = single
+    b = s.rhs()
+    u, its, rel, st = s.pcg_solve(b, w.tol, 2000)
+    x = u.cpu().numpy()[P.free_lat]
+    x_dense = np.linalg.solve(P.csr().toarray(), P.rhs())
+    assert rel <= w.tol
+    assert P.energy_error(x_dense, x) < 1e-8
+    _, its_ref, _ = P.pcg(tol=w.tol, maxit=2000)
+    assert abs(its - its_ref) <= 2
+    info = s.last_solve()
+    assert info["status"] == 0 and info["true_relres"] < 1e-8
+
+
+def test_pcg_host_buffers_match_device(single):
+    w, P, s = single
+    b = s.rhs()
+    u_dev, its_d, _, _ = s.pcg_solve(b, w.tol, 2000)
+    u_host, its_h, _ = s.pcg_solve_host(b.cpu().numpy(), w.tol, 2000)
+    assert its_h == its_d
+    assert np.array_equal(u_host, u_dev.cpu().numpy())
+
+
+def test_solve_is_deterministic(single):
+    w, P, s = single
+    b = s.rhs()
+    u1, i1, r1, _ = s.pcg_solve(b, w.tol, 2000)
+    u2, i2, r2, _ = s.pcg_solve(b, w.tol, 2000)
+    assert i1 == i2 and r1 == r2 and torch.equal(u1, u2)
+
+
+def test_error_statuses(single):
+    from paper_1809_00828_gb300 import fcm
+    w, P, s = single
+    b = s.rhs()
+    bad = b.clone()
+    bad[int(P.free_lat[5])] = float("nan")
+    _, _, _, st = s.pcg_solve(bad, w.tol, 100, check=False)
+    assert st == fcm.FCM_EINVAL
+    u, its, rel, st = s.pcg_solve(b, w.tol, 3, check=False)
+    assert st == fcm.FCM_ENOTCONV and its == 3 and rel > w.tol
+    assert torch.isfinite(u).all() and u.abs().max() > 0
+    fresh = _solver(w)
+    _, _, _, st = fresh.pcg_solve(b, w.tol, 10, check=False)
+    assert st == fcm.FCM_ESTATE
+    fresh.close()
+
+
+@pytest.mark.parametrize("p,n", [(1, (3, 2, 2)), (3, (2, 2, 3)), (4, (2, 1, 2))])
+def test_apply_K_and_S_other_orders(p, n):
+    g = I.random_sphere_voids(9, 3, 0.15, 0.3, octree_depth=2)
+    w = I.Workload("orders", n, p, 1e-6, g, 1e-9, hi=(0.3 * n[0], 0.25 * n[1], 0.2 * n[2]))
+    P = O.Problem.from_workload(w)
+    P.precond_build(0)
+    s = _solver(w)
+    s.precond_build()
+    x = I.random_vector(7 + p, s.n)
+    y = s.apply_K(_lat(x)).cpu().numpy()[P.free_lat]
+    y_ref = P.apply_K(x[P.free_lat])
+    assert np.abs(y - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+    z = s.apply_S(_lat(x)).cpu().numpy()[P.free_lat]
+    z_ref = P.apply_S(x[P.free_lat])
+    K = P.csr()
+    d = z - z_ref
+    assert np.sqrt(abs(d @ (K @ d)) / (z_ref @ (K @ z_ref))) < 1e-9
+    u, its, rel, st = s.pcg_solve(s.rhs(), 1e-9, 3000)
+    x_dense = np.linalg.solve(K.toarray(), P.rhs())
+    assert P.energy_error(x_dense, u.cpu().numpy()[P.free_lat]) < 1e-7
+    s.close()
+
+
+def test_porous_8_cells_iterations_and_energy_error():
+    # 8^3 cells, p=2, 40 voids, alpha 1e-10: a small member of the porous family
+    w = I.workload_porous(12, 8, 2, 40, 1e-10, 3, 1e-8)
+    P = O.Problem.from_workload(w)
+    P.precond_build(0)
+    x_ref, its_ref, _ = P.pcg(tol=1e-12, maxit=5000)
+    _, its_o, _ = P.pcg(tol=w.tol, maxit=5000)
+    s = _solver(w)
+    s.precond_build()
+    u, its, rel, st = s.pcg_solve(s.rhs(), w.tol, 5000)
+    assert abs(its - its_o) <= 2
+    assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
+    s.close()
