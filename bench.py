@@ -312,6 +312,16 @@ def run_fcm(args, rank, world, local_rank):
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
             "gpu_launches": launches_per_solve * args.steps,
             "clocks": clk}
+    if args.precision != "fp64":
+        # accuracy of this form: relative energy-norm error (Eq. (15)) against the plain FP64 solve
+        x = u.clone()
+        s.precond_build(precision="fp64")
+        x64, its64, _, _ = s.pcg_solve(b, w.tol, args.maxit)
+        e = x - x64
+        num = torch.dot(e, s.apply_K(e)).item()
+        den = torch.dot(x64, s.apply_K(x64)).item()
+        line["config"]["energy_error_vs_fp64"] = (abs(num) / den) ** 0.5
+        line["config"]["fp64_iterations"] = its64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         kf, sf = info["kapply_fmas"], info["sapply_fmas"]
         v, sample, _ = oracle_sample(w, its_med, sf, kf)

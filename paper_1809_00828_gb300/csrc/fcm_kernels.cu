@@ -15,10 +15,12 @@ namespace fcm {
 namespace {
 
 constexpr int round32(int v) { return (v + 31) / 32 * 32; }
+// One thread per row up to 512 rows; larger blocks loop over rows.
+constexpr int threads_for(int rows) { return round32(rows) < 512 ? round32(rows) : 512; }
 
 // y += K_e x_e over the active cells of one colour; rows that are not free stay untouched.
 template <int P>
-__global__ void __launch_bounds__(round32(3 * (P + 1) * (P + 1) * (P + 1)))
+__global__ void __launch_bounds__(threads_for(3 * (P + 1) * (P + 1) * (P + 1)))
     ebe_apply_kernel(const double *__restrict__ x, double *__restrict__ y, const uint8_t *__restrict__ mask,
                      const double *__restrict__ elem, const int2 *__restrict__ cells, Grid3 g,
                      const int *__restrict__ done)
@@ -37,8 +39,7 @@ __global__ void __launch_bounds__(round32(3 * (P + 1) * (P + 1) * (P + 1)))
     for (int t = threadIdx.x; t < NE; t += blockDim.x) xe[t] = x[3 * node[t / 3] + t % 3];
     __syncthreads();
     const double *__restrict__ K = elem + (size_t)ce.y * NE * NE;
-    const int t = threadIdx.x;
-    if (t < NE) {
+    for (int t = threadIdx.x; t < NE; t += blockDim.x) {
         double s = 0.0;
 #pragma unroll 8
         for (int j = 0; j < NE; ++j) s = fma(__ldg(K + (size_t)j * NE + t), xe[j], s);
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(round32(3 * (P + 1) * (P + 1) * (P + 1)))
 // z += F_B r_B for the patches of one colour.  F_B is the dense symmetric
 // pseudo inverse over the patch box (zero rows/columns for DOFs outside B).
 template <int P>
-__global__ void __launch_bounds__(round32(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
+__global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
     schwarz_apply_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ f64,
                          const float *__restrict__ f32, const PatchRec *__restrict__ patches, Grid3 g,
                          const int *__restrict__ done)
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(round32(3 * (2 * P - 1) * (2 * P - 1) * (2 * P
     constexpr int W = 2 * P - 1, NB = 3 * W * W * W;
     if (done && *done) return;
     __shared__ double rb[NB];
+    __shared__ float rbf[NB];
     __shared__ int64_t gidx[NB];
     const PatchRec pr = patches[blockIdx.x];
     const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
@@ -74,11 +76,12 @@ __global__ void __launch_bounds__(round32(3 * (2 * P - 1) * (2 * P - 1) * (2 * P
         const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
         const int64_t gi = 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + comp;
         gidx[t] = gi;
-        rb[t] = r[gi];
+        const double v = r[gi];
+        rb[t] = v;
+        rbf[t] = (float)v;
     }
     __syncthreads();
-    const int t = threadIdx.x;
-    if (t < n) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
         double s = 0.0;
         if (pr.prec == 0) {
             const double *__restrict__ F = f64 + pr.off;
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(round32(3 * (2 * P - 1) * (2 * P - 1) * (2 * P
             const float *__restrict__ F = f32 + pr.off;
             float acc = 0.0f;
 #pragma unroll 8
-            for (int j = 0; j < n; ++j) acc = fmaf(__ldg(F + (size_t)j * n + t), (float)rb[j], acc);
+            for (int j = 0; j < n; ++j) acc = fmaf(__ldg(F + (size_t)j * n + t), rbf[j], acc);
             s = acc;
         }
         z[gidx[t]] += s;
@@ -116,7 +119,7 @@ void ebe_launch(const Grid3 &g, const double *x, double *y, const uint8_t *mask,
     constexpr int NE = 3 * (P + 1) * (P + 1) * (P + 1);
     for (int c = 0; c < 8; ++c) {
         const int cnt = off[c + 1] - off[c];
-        if (cnt > 0) ebe_apply_kernel<P><<<cnt, round32(NE), 0, s>>>(x, y, mask, elem, cells + off[c], g, done);
+        if (cnt > 0) ebe_apply_kernel<P><<<cnt, threads_for(NE), 0, s>>>(x, y, mask, elem, cells + off[c], g, done);
     }
 }
 
@@ -127,7 +130,7 @@ void schwarz_launch(const Grid3 &g, const double *r, double *z, const double *f6
     constexpr int NB = 3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1);
     for (int c = 0; c < 8; ++c) {
         const int cnt = off[c + 1] - off[c];
-        if (cnt > 0) schwarz_apply_kernel<P><<<cnt, round32(NB), 0, s>>>(r, z, f64, f32, patches + off[c], g, done);
+        if (cnt > 0) schwarz_apply_kernel<P><<<cnt, threads_for(NB), 0, s>>>(r, z, f64, f32, patches + off[c], g, done);
     }
 }
 

@@ -155,4 +155,6 @@ WORKLOADS = {
     "porous40_32_p3": lambda: workload_porous(11, 32, 3, 40, 1e-10, 4, 1e-8),
     # ~6.4M DOFs: 40 voids, 64^3 cells, p=2 (mixed precision family)
     "porous40_64_p2": lambda: workload_porous(12, 64, 2, 40, 1e-10, 3, 1e-8),
+    # ~0.35M DOFs: the 32^3 family at 16^3 cells (profiling-sized: ~1.5 GB of block factors)
+    "porous40_16_p3": lambda: workload_porous(11, 16, 3, 40, 1e-10, 4, 1e-8),
 }

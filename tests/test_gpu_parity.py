@@ -149,16 +149,45 @@ def test_apply_K_and_S_other_orders(p, n):
     s.close()
 
 
-def test_porous_8_cells_iterations_and_energy_error():
+@pytest.fixture(scope="module")
+def porous8():
     # 8^3 cells, p=2, 40 voids, alpha 1e-10: a small member of the porous family
     w = I.workload_porous(12, 8, 2, 40, 1e-10, 3, 1e-8)
     P = O.Problem.from_workload(w)
     P.precond_build(0)
-    x_ref, its_ref, _ = P.pcg(tol=1e-12, maxit=5000)
+    x_ref, _, _ = P.pcg(tol=1e-12, maxit=5000)
     _, its_o, _ = P.pcg(tol=w.tol, maxit=5000)
+    return w, P, x_ref, its_o
+
+
+def test_porous_8_cells_iterations_and_energy_error(porous8):
+    w, P, x_ref, its_o = porous8
     s = _solver(w)
     s.precond_build()
     u, its, rel, st = s.pcg_solve(s.rhs(), w.tol, 5000)
     assert abs(its - its_o) <= 2
+    assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
+    s.close()
+
+
+def test_mixed_precision_factors_keep_energy_error_below_1e6(single):
+    # FP32 block factors (FP64 for blocks with retained condition number > 1e7)
+    w, P, s0 = single
+    s = _solver(w)
+    s.precond_build(precision="mixed")
+    assert s.info["n_blocks_fp32"] > 0
+    u, its, rel, st = s.pcg_solve(s.rhs(), w.tol, 2000)
+    x_dense = np.linalg.solve(P.csr().toarray(), P.rhs())
+    assert P.energy_error(x_dense, u.cpu().numpy()[P.free_lat]) < 1e-6
+    _, its64, _, _ = s0.pcg_solve(s0.rhs(), w.tol, 2000)
+    assert its <= its64 * 1.2 + 5
+    s.close()
+
+
+def test_mixed_precision_porous_8_cells(porous8):
+    w, P, x_ref, _ = porous8
+    s = _solver(w)
+    s.precond_build(precision="mixed", cond_fp64=1e7)
+    u, its, rel, st = s.pcg_solve(s.rhs(), w.tol, 5000)
     assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
     s.close()
