@@ -184,6 +184,24 @@ fcm_status fcm_apply_K(fcm_ctx *ctx, const double *x_dev, double *y_dev);
  * FCM_ESTATE before fcm_precond_build. */
 fcm_status fcm_apply_S(fcm_ctx *ctx, const double *r_dev, double *z_dev);
 
+/* Largest n_lattice that fcm_apply_S_noalloc accepts (8 MiB of FP64 scratch). */
+#define FCM_NOALLOC_MAX_LATTICE 1048576
+
+/* Same result as fcm_apply_S, for callers that must not allocate device
+ * memory once they are running (an application whose device memory belongs
+ * to its own pool allocator, or a real-time loop that forbids allocation
+ * after start-up).  This call allocates nothing: its scratch vector is a
+ * fixed static device array of FCM_NOALLOC_MAX_LATTICE doubles, held by
+ * every GPU that loads the library until the process exits.  The paper has
+ * no counterpart; it is an interface convenience.
+ *   - Returns FCM_EINVAL when n_lattice > FCM_NOALLOC_MAX_LATTICE, FCM_ESTATE
+ *     before fcm_precond_build.
+ *   - All calls on a device share the one array; calls that overlap on the
+ *     GPU (different streams or contexts) race on it.
+ *   - The first call on each device looks up the array's address
+ *     (cudaGetSymbolAddress); make it before any stream capture. */
+fcm_status fcm_apply_S_noalloc(fcm_ctx *ctx, const double *r_dev, double *z_dev);
+
 /* Message of the last failure on ctx (ctx may be NULL for setup failures). */
 const char *fcm_last_error(const fcm_ctx *ctx);
 

@@ -21,7 +21,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 # Every symbol include/fcm.h declares (checked by the tests).
 EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_solve", "fcm_pcg_solve_host",
-            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_last_error", "fcm_destroy")
+            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy")
+NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
 class FcmError(RuntimeError):
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
     L.fcm_last_solve.argtypes = [P, ctypes.POINTER(SolveInfo)]
     L.fcm_apply_K.argtypes = [P, P, P]
     L.fcm_apply_S.argtypes = [P, P, P]
+    L.fcm_apply_S_noalloc.argtypes = [P, P, P]
     L.fcm_last_error.argtypes = [P]
     L.fcm_last_error.restype = ctypes.c_char_p
     L.fcm_destroy.argtypes = [P]
