@@ -132,6 +132,8 @@ typedef struct {
     double true_relres;        /* ||b - K x_i|| / ||b|| recomputed at exit           */
     int status;                /* fcm_status of the solve                           */
     double seconds;            /* device time of the solve                          */
+    int flexible_iterations;   /* fcm_fpcg_solve: iterations with the learned term  */
+    int fallback;              /* fcm_fpcg_solve: 1 if it fell back to plain PCG    */
 } fcm_solve_info;
 
 /* Set up the problem: classify cells by octree quadrature, compute eta_T,
@@ -183,6 +185,63 @@ fcm_status fcm_apply_K(fcm_ctx *ctx, const double *x_dev, double *y_dev);
 /* z_dev = S r_dev, S = sum_B R_B^T A_B+^-1 R_B (Sec. 3.1 Eq. (5)); device.
  * FCM_ESTATE before fcm_precond_build. */
 fcm_status fcm_apply_S(fcm_ctx *ctx, const double *r_dev, double *z_dev);
+
+/* ------------------------------------------------------------------------ */
+/* Learned coarse correction (not in the paper: the paper's preconditioner   */
+/* has no coarse space, Sec. 6; this adds one, learned).                     */
+/* ------------------------------------------------------------------------ */
+
+/* 3D U-Net on the cell grid: `levels` resolution levels with channels
+ * base * 2^l capped at 4 * base, two 3x3x3 convolutions + ReLU per level and
+ * decoder stage, average pooling, nearest upsampling with skip
+ * concatenation, and a final 3x3x3 convolution to out_ch channels.
+ * Weights are stored in BF16 for the forward pass (FP32 master copy and
+ * Adam moments for training); activations and accumulation are FP32.
+ * Tensors are float, layout [batch][channel][z][y][x] (x fastest), device.
+ * Spatial sizes must be divisible by 2^(levels-1). */
+typedef struct fcm_unet fcm_unet;
+typedef struct {
+    int in_ch, out_ch, base, levels;
+    uint64_t seed;            /* SplitMix64 seed of the Kaiming-uniform initial weights */
+} fcm_unet_desc;
+
+fcm_status fcm_unet_create(const fcm_unet_desc *desc, void *cuda_stream, fcm_unet **out);
+/* Number of parameters (all weights then all biases, layer by layer). */
+fcm_status fcm_unet_params(const fcm_unet *net, int64_t *count);
+/* Copy the FP32 master parameters (and, if g_host != NULL, their gradients) to host memory. */
+fcm_status fcm_unet_get(fcm_unet *net, float *w_host, float *g_host);
+/* Replace the FP32 master parameters from host memory (BF16 copies are refreshed). */
+fcm_status fcm_unet_set(fcm_unet *net, const float *w_host);
+/* out_dev[batch][out_ch][nz][ny][nx] = U-Net(in_dev[batch][in_ch][nz][ny][nx]); keeps the activations
+ * for a following fcm_unet_backward. */
+fcm_status fcm_unet_forward(fcm_unet *net, const float *in_dev, int batch, int nx, int ny, int nz, float *out_dev);
+/* Back-propagates dL/d(out) of the last forward: accumulates parameter gradients; writes
+ * dL/d(in) to din_dev unless it is NULL. */
+fcm_status fcm_unet_backward(fcm_unet *net, const float *dout_dev, float *din_dev);
+fcm_status fcm_unet_zero_grad(fcm_unet *net);
+/* One Adam step (Kingma & Ba 2015) on the FP32 master parameters; step counts from 1. */
+fcm_status fcm_unet_adam(fcm_unet *net, float lr, float beta1, float beta2, float eps, int step);
+void fcm_unet_destroy(fcm_unet *net);
+
+/* Restriction of a lattice vector to the cell grid: cells_dev[c][cell] = s * mean of
+ * v at the (up to 8) vertex nodes of the cell, component c (3 x n_cells floats, cell
+ * index x fastest).  With eta_channel != 0 a 4th channel receives eta_T of each cell.
+ * The transpose of fcm_coarse_prolong up to the factor s. */
+fcm_status fcm_coarse_restrict(fcm_ctx *ctx, const double *v_dev, float s, int eta_channel, float *cells_dev);
+/* Prolongation: y_dev (lattice) = s * P cells_dev, where P puts on each free vertex DOF
+ * 1/8 of the sum of the cell values of the cells that contain the vertex; higher-order
+ * DOFs get 0. */
+fcm_status fcm_coarse_prolong(fcm_ctx *ctx, const float *cells_dev, double s, double *y_dev);
+
+/* Flexible PCG (Notay's FCG(1): beta = -(z.Kp)/(p.Kp), alpha = (p.r)/(p.Kp)) with the
+ * nonlinear preconditioner z = S r + gamma sigma P N(R r / sigma, eta), N the U-Net,
+ * sigma the RMS of R r.  Convergence is judged by the plain Schwarz residual
+ * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the judged residual grows 100-fold over
+ * its best value or a scalar breaks down, the solve falls back to plain Schwarz-PCG
+ * restarted from the current iterate (fcm_last_solve reports it).  iterations counts
+ * K applications of both phases. */
+fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, const double *rhs_dev, double tol, int maxit,
+                          double *u_dev, int *iterations, double *final_relres);
 
 /* Largest n_lattice that fcm_apply_S_noalloc accepts (8 MiB of FP64 scratch). */
 #define FCM_NOALLOC_MAX_LATTICE 1048576

@@ -69,13 +69,13 @@ struct StreamScope {
 void apply_K_dev(fcm_ctx *C, const double *x, double *y, const int *done)
 {
     fcm::launch_zero(y, C->nlat, done, C->stream);
-    fcm::launch_ebe_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->d_cells, C->cell_colour_off, done, C->stream);
+    fcm::launch_k_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->kc, done, C->stream);
 }
 
 void apply_S_dev(fcm_ctx *C, const double *r, double *z, const int *done)
 {
     fcm::launch_zero(z, C->nlat, done, C->stream);
-    fcm::launch_schwarz_apply(C->p, C->g, r, z, C->d_f64, C->d_f32, C->d_patches, C->patch_colour_off, done, C->stream);
+    fcm::launch_schwarz_apply(C->p, C->g, r, z, C->d_f64, C->d_f32, C->plan, done, C->stream);
 }
 
 void destroy_graph(fcm_ctx *C)
@@ -164,7 +164,7 @@ void free_ctx(fcm_ctx *C)
 {
     if (!C) return;
     destroy_graph(C);
-    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_f64, C->d_f32, C->d_patches,
+    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32, C->d_patches, C->d_batches, C->d_eta,
                     C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
                     C->d_out2};
     for (void *q : ptrs)
@@ -178,6 +178,18 @@ void free_ctx(fcm_ctx *C)
 }
 
 }  // namespace
+
+// errors of calls without a context (set-up, U-Net) are reported by fcm_last_error(NULL)
+std::string &fcm_unet_last_error() { return g_setup_error; }
+
+namespace fcm {
+void ctx_apply_K(fcm_ctx *C, const double *x, double *y) { apply_K_dev(C, x, y, nullptr); }
+void ctx_apply_S(fcm_ctx *C, const double *r, double *z) { apply_S_dev(C, r, z, nullptr); }
+fcm_status ctx_solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, double *u, fcm_solve_info &info)
+{
+    return solve_one(C, rhs, tol, maxit, u, info);
+}
+}  // namespace fcm
 
 extern "C" {
 
@@ -238,6 +250,7 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     SETUP_CUDA(dalloc(&C->d_cell_elem, hp.ncells));
     SETUP_CUDA(dalloc(&C->d_mask, hp.nlat));
     SETUP_CUDA(dalloc(&C->d_rhs, hp.nlat));
+    SETUP_CUDA(dalloc(&C->d_eta, hp.ncells));
     cudaStream_t st = C->stream;
     SETUP_CUDA(cudaMemcpyAsync(C->d_elem, hp.Kref.data(), sizeof(double) * ne2, cudaMemcpyHostToDevice, st));
     if (hp.ncut > 0)
@@ -245,22 +258,37 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     SETUP_CUDA(cudaMemcpyAsync(C->d_cell_elem, hp.cell_elem.data(), sizeof(int32_t) * hp.ncells, cudaMemcpyHostToDevice, st));
     SETUP_CUDA(cudaMemcpyAsync(C->d_mask, hp.mask.data(), hp.nlat, cudaMemcpyHostToDevice, st));
     SETUP_CUDA(cudaMemcpyAsync(C->d_rhs, hp.rhs.data(), sizeof(double) * hp.nlat, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<float> eta_f(hp.eta.begin(), hp.eta.end());
+        SETUP_CUDA(cudaMemcpyAsync(C->d_eta, eta_f.data(), sizeof(float) * hp.ncells, cudaMemcpyHostToDevice, st));
+        SETUP_CUDA(cudaStreamSynchronize(st));
+    }
     C->element_bytes = (int64_t)(sizeof(double) * ne2 * nelem);
-    // active cells grouped by parity colour
+    // active cells grouped by parity colour: uncut (matrix-free) and cut (own element matrix)
     std::vector<int2> cells;
-    cells.reserve(hp.nactive);
-    C->cell_colour_off[0] = 0;
+    std::vector<int> uncut;
+    cells.reserve(hp.ncut);
+    uncut.reserve(hp.nactive);
+    C->kc.cut_off[0] = 0;
+    C->kc.uncut_off[0] = 0;
     for (int col = 0; col < 8; ++col) {
         for (int64_t ci = 0; ci < hp.ncells; ++ci) {
             if (hp.cell_elem[ci] < 0) continue;
             const int cx = (int)(ci % hp.n[0]), cy = (int)((ci / hp.n[0]) % hp.n[1]), cz = (int)(ci / ((int64_t)hp.n[0] * hp.n[1]));
             if ((cx & 1) + 2 * (cy & 1) + 4 * (cz & 1) != col) continue;
-            cells.push_back(make_int2((int)ci, hp.cell_elem[ci]));
+            if (hp.cell_elem[ci] == 0) uncut.push_back((int)ci);
+            else cells.push_back(make_int2((int)ci, hp.cell_elem[ci]));
         }
-        C->cell_colour_off[col + 1] = (int)cells.size();
+        C->kc.cut_off[col + 1] = (int)cells.size();
+        C->kc.uncut_off[col + 1] = (int)uncut.size();
     }
     SETUP_CUDA(dalloc(&C->d_cells, cells.size()));
     SETUP_CUDA(cudaMemcpyAsync(C->d_cells, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice, st));
+    SETUP_CUDA(dalloc(&C->d_uncut, uncut.size()));
+    SETUP_CUDA(cudaMemcpyAsync(C->d_uncut, uncut.data(), sizeof(int) * uncut.size(), cudaMemcpyHostToDevice, st));
+    C->kc.cut = C->d_cells;
+    C->kc.uncut = C->d_uncut;
+    fcm::make_sf_tables(hp, C->kc.sf);
     // solver workspace
     double **vecs[] = {&C->d_x, &C->d_r, &C->d_z, &C->d_p, &C->d_q, &C->d_b, &C->d_t};
     for (double **v : vecs) {
@@ -303,7 +331,12 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->precond_seconds = C->precond_seconds;
     out->n_blocks = C->n_blocks;
     out->n_blocks_fp32 = C->n_fp32_factors;
-    out->kapply_fmas = (int64_t)hp.nactive * hp.ne * hp.ne;
+    {
+        // cut cells: dense ne x ne; uncut cells: 3 components x (8 forward + 8 transposed) contractions of
+        // Q^3 points x Q terms, plus ~21 multiply-adds of the stress per point
+        const int64_t q = hp.p + 1;
+        out->kapply_fmas = hp.ncut * (int64_t)hp.ne * hp.ne + (hp.nactive - hp.ncut) * (48 * q * q * q * q + 21 * q * q * q);
+    }
     out->sapply_fmas = C->sapply_fmas;
     out->max_block_cond = C->max_cond;
     return FCM_OK;

@@ -31,12 +31,39 @@ struct Grid3 {
     int M[3];   // lattice nodes per axis
 };
 
+// Active cells of the K apply, grouped by parity colour: uncut cells (matrix-free,
+// sum-factorised) and cut cells (their own dense element matrix).
+struct KCells {
+    const int *uncut;     // cell ids
+    const int2 *cut;      // (cell id, element id)
+    int uncut_off[9];
+    int cut_off[9];
+    SfTables sf;
+};
+
+// Launch plan of the Schwarz apply.  Patches are grouped into batches that
+// share one stored factor (up to 8 patches, same colour and precision) or
+// hold a single patch; a segment is a run of batches launched together.
+// Segments are ordered by colour, so the colours run one after another.
+struct SchwarzSeg {
+    int colour;   // vertex parity colour 0..7
+    int prec;     // 0 FP64 factors, 1 FP32 factors
+    int G;        // 8: shared-factor batches, 1: single patches
+    int first;    // first batch of the segment
+    int count;    // batches in the segment
+};
+struct SchwarzPlan {
+    const PatchRec *patches;  // patch records, batch by batch
+    const int2 *batches;      // (first patch, patch count)
+    int nseg;
+    SchwarzSeg seg[32];
+};
+
 // Launchers (all asynchronous on `s`).  `done` may be null.
-void launch_ebe_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
-                      const int2 *cells, const int *colour_off, const int *done, cudaStream_t s);
+void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
+                    const KCells &kc, const int *done, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
-                          const float *fpool32, const PatchRec *patches, const int *colour_off, const int *done,
-                          cudaStream_t s);
+                          const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
 void launch_mask_copy(const double *in, double *out, const uint8_t *mask, int64_t n, cudaStream_t s);
 void launch_zero(double *v, int64_t n, const int *done, cudaStream_t s);
 
@@ -58,7 +85,17 @@ void cg_residual_norms(const CgWork &w, const double *res, const double *b, doub
 // fcm_precond.cu
 std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o);
 
+// fcm_capi.cu: operators and the plain PCG on a context's own work stream
+void ctx_apply_K(fcm_ctx *C, const double *x, double *y);
+void ctx_apply_S(fcm_ctx *C, const double *r, double *z);
+fcm_status ctx_solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, double *u, fcm_solve_info &info);
+
+// fcm_unet.cu: redirect a network's launches to stream s; returns the previous stream
+cudaStream_t unet_set_stream(fcm_unet *N, cudaStream_t s);
+
 }  // namespace fcm
+
+std::string &fcm_unet_last_error();
 
 struct fcm_ctx {
     std::string err;
@@ -74,8 +111,10 @@ struct fcm_ctx {
     int32_t *d_cell_elem = nullptr;  // per cell
     uint8_t *d_mask = nullptr;       // per lattice DOF
     double *d_rhs = nullptr;         // load case 0
-    int2 *d_cells = nullptr;         // active cells by colour: (cell, element id)
-    int cell_colour_off[9] = {0};
+    float *d_eta = nullptr;          // volume fraction per cell
+    int2 *d_cells = nullptr;         // cut cells by colour: (cell, element id)
+    int *d_uncut = nullptr;          // uncut cells by colour
+    fcm::KCells kc = {};
     int64_t element_bytes = 0;
     double setup_seconds = 0.0;
     // preconditioner
@@ -83,7 +122,8 @@ struct fcm_ctx {
     double *d_f64 = nullptr;         // FP64 factor pool
     float *d_f32 = nullptr;          // FP32 factor pool (mixed precision)
     fcm::PatchRec *d_patches = nullptr;
-    int patch_colour_off[9] = {0};
+    int2 *d_batches = nullptr;
+    fcm::SchwarzPlan plan = {};
     int64_t n_factors = 0, factor_bytes = 0, n_fp32_factors = 0;
     double max_cond = 0.0;
     int64_t n_blocks = 0, sapply_fmas = 0;

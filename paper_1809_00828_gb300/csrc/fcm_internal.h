@@ -45,6 +45,18 @@ struct HostProblem {
     std::vector<double> rhs;        // load case 0, lattice layout
 };
 
+// 1D tables for the sum-factorised stiffness apply of an uncut cell: shape
+// functions and their physical derivatives at the p+1 Gauss points of each
+// axis (exact for the uncut integrand, whose degree is <= 2p per axis).
+struct SfTables {
+    double B[5][5];     // B[q][i] = f_i(xi_q)
+    double D[3][5][5];  // D[a][q][i] = f_i'(xi_q) * 2 / h_a
+    double W[5];        // Gauss weights on [-1, 1]
+    double detJ;        // h_0 h_1 h_2 / 8
+    double lam, mu;     // Lame parameters
+};
+void make_sf_tables(const HostProblem &P, SfTables &T);
+
 // Builds everything on the host.  Returns an empty string on success, else
 // the error message.  nthreads <= 0 uses the hardware concurrency.
 std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, int p, double alpha,

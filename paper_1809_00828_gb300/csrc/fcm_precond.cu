@@ -446,36 +446,58 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     if (!mixed)
         for (size_t f = 0; f < fac.size(); ++f) off[f] = fac[f].off;
 
-    // ---- patch records, grouped by colour (vertex parity)
-    std::vector<PatchRec> recs[8];
+    // ---- launch plan: per colour (vertex parity) and precision, batches of patches sharing a
+    // factor (up to 8; 4 for FP64 at p = 4) and single patches with their own factor
+    std::vector<int> users(fac.size(), 0);
+    std::vector<std::vector<int>> by_colour_factor[8];
+    for (int c = 0; c < 8; ++c) by_colour_factor[c].resize(fac.size());
+    C->n_blocks = 0;
+    C->sapply_fmas = 0;
     for (int vz = 0; vz < nv[2]; ++vz)
         for (int vy = 0; vy < nv[1]; ++vy)
             for (int vx = 0; vx < nv[0]; ++vx) {
                 const int v = vx + nv[0] * (vy + nv[1] * vz);
                 const int f = patch_factor[v];
                 if (f < 0) continue;
-                recs[(vx & 1) + 2 * (vy & 1) + 4 * (vz & 1)].push_back({off[f], v, prec[f]});
+                by_colour_factor[(vx & 1) + 2 * (vy & 1) + 4 * (vz & 1)][f].push_back(v);
+                C->n_blocks += 1;
+                C->sapply_fmas += (int64_t)fac[f].n * fac[f].n;
             }
     std::vector<PatchRec> all;
-    C->n_blocks = 0;
-    C->sapply_fmas = 0;
+    std::vector<int2> batches;
+    SchwarzPlan plan = {};
     for (int c = 0; c < 8; ++c)
-        for (const PatchRec &r : recs[c]) {
-            const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
-            const BoxInfo bx = patch_box(p, g, r.v % nvx, (r.v / nvx) % nvy, r.v / (nvx * nvy));
-            C->n_blocks += 1;
-            C->sapply_fmas += (int64_t)bx.n * bx.n;
-        }
-    C->patch_colour_off[0] = 0;
-    for (int c = 0; c < 8; ++c) {
-        all.insert(all.end(), recs[c].begin(), recs[c].end());
-        C->patch_colour_off[c + 1] = (int)all.size();
-    }
+        for (int pr = 0; pr < 2; ++pr)
+            for (int shared = 1; shared >= 0; --shared) {
+                SchwarzSeg sg = {c, pr, shared ? 8 : 1, (int)batches.size(), 0};
+                const int cap = shared ? ((p == 4 && pr == 0) ? 4 : 8) : 1;
+                for (size_t f = 0; f < fac.size(); ++f) {
+                    const std::vector<int> &vs = by_colour_factor[c][f];
+                    if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
+                    for (size_t s0 = 0; s0 < vs.size(); s0 += cap) {
+                        const int cnt = (int)std::min<size_t>(cap, vs.size() - s0);
+                        batches.push_back(make_int2((int)all.size(), cnt));
+                        for (int k = 0; k < cnt; ++k) all.push_back({off[f], vs[s0 + k], prec[f]});
+                    }
+                }
+                sg.count = (int)batches.size() - sg.first;
+                if (sg.count > 0) {
+                    if (plan.nseg >= 32) return "launch plan has too many segments";
+                    plan.seg[plan.nseg++] = sg;
+                }
+            }
     if (C->d_patches) cudaFree(C->d_patches);
+    if (C->d_batches) cudaFree(C->d_batches);
     C->d_patches = nullptr;
+    C->d_batches = nullptr;
     PC_CUDA(cudaMalloc(&C->d_patches, sizeof(PatchRec) * std::max<size_t>(all.size(), 1)));
+    PC_CUDA(cudaMalloc(&C->d_batches, sizeof(int2) * std::max<size_t>(batches.size(), 1)));
     PC_CUDA(cudaMemcpyAsync(C->d_patches, all.data(), sizeof(PatchRec) * all.size(), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
     PC_CUDA(cudaStreamSynchronize(st));
+    plan.patches = C->d_patches;
+    plan.batches = C->d_batches;
+    C->plan = plan;
     C->n_factors = (int64_t)fac.size();
     C->factor_bytes = n64 * 8 + n32 * 4;
     C->max_block = maxn;

@@ -439,6 +439,26 @@ void gauss_legendre(int n, double *x, double *w)
     }
 }
 
+void make_sf_tables(const HostProblem &P, SfTables &T)
+{
+    std::memset(&T, 0, sizeof T);
+    const int q = P.p + 1;
+    double x[kMaxQ], w[kMaxQ];
+    gauss_legendre(q, x, w);
+    for (int k = 0; k < q; ++k) {
+        double f[kMaxQ], df[kMaxQ];
+        shape_1d(P.p, x[k], f, df);
+        T.W[k] = w[k];
+        for (int i = 0; i < q; ++i) {
+            T.B[k][i] = f[i];
+            for (int a = 0; a < 3; ++a) T.D[a][k][i] = df[i] * 2.0 / P.h[a];
+        }
+    }
+    T.detJ = P.h[0] * P.h[1] * P.h[2] / 8.0;
+    T.lam = P.E * P.nu / ((1.0 + P.nu) * (1.0 - 2.0 * P.nu));
+    T.mu = P.E / (2.0 * (1.0 + P.nu));
+}
+
 std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, int p, double alpha,
                                const fcm_bc &bc, HostProblem &P, int nthreads)
 {

@@ -21,7 +21,10 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 # Every symbol include/fcm.h declares (checked by the tests).
 EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_solve", "fcm_pcg_solve_host",
-            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy")
+            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy",
+            "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
+            "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
+            "fcm_coarse_prolong", "fcm_fpcg_solve")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -60,7 +63,8 @@ class PrecondOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("relres", ctypes.c_double), ("true_relres", ctypes.c_double),
-                ("status", ctypes.c_int), ("seconds", ctypes.c_double)]
+                ("status", ctypes.c_int), ("seconds", ctypes.c_double), ("flexible_iterations", ctypes.c_int),
+                ("fallback", ctypes.c_int)]
 
 
 _lib = None
@@ -92,7 +96,7 @@ def load(path: str = LIB_PATH):
     L.fcm_last_error.restype = ctypes.c_char_p
     L.fcm_destroy.argtypes = [P]
     for f in EXPORTED:
-        if f not in ("fcm_last_error", "fcm_destroy"):
+        if f not in ("fcm_last_error", "fcm_destroy", "fcm_unet_destroy"):
             getattr(L, f).restype = ctypes.c_int
     L.fcm_destroy.restype = None
     _lib = L
@@ -211,3 +215,144 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------------------------
+# Learned coarse correction (U-Net on the cell grid) and the flexible PCG that uses it.
+# ----------------------------------------------------------------------------------------------
+class UNetDesc(ctypes.Structure):
+    _fields_ = [("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int), ("base", ctypes.c_int), ("levels", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+_unet_bound = False
+
+
+def _bind_unet(L):
+    global _unet_bound
+    if _unet_bound:
+        return
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.fcm_unet_create.argtypes = [ctypes.POINTER(UNetDesc), P, ctypes.POINTER(P)]
+    L.fcm_unet_params.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.fcm_unet_get.argtypes = [P, P, P]
+    L.fcm_unet_set.argtypes = [P, P]
+    L.fcm_unet_forward.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    L.fcm_unet_backward.argtypes = [P, P, P]
+    L.fcm_unet_zero_grad.argtypes = [P]
+    L.fcm_unet_adam.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int]
+    L.fcm_unet_destroy.argtypes = [P]
+    L.fcm_unet_destroy.restype = None
+    L.fcm_coarse_restrict.argtypes = [P, P, ctypes.c_float, ctypes.c_int, P]
+    L.fcm_coarse_prolong.argtypes = [P, P, ctypes.c_double, P]
+    L.fcm_fpcg_solve.argtypes = [P, P, ctypes.c_double, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
+    for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
+              "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
+              "fcm_fpcg_solve"):
+        getattr(L, f).restype = ctypes.c_int
+    _unet_bound = True
+
+
+def _unet_check(st):
+    if st != FCM_OK:
+        raise FcmError(st, load().fcm_last_error(None).decode())
+
+
+class UNet:
+    """The U-Net of the learned coarse correction (device weights, our own kernels)."""
+
+    def __init__(self, in_ch=4, out_ch=3, base=16, levels=4, seed=0, stream=None):
+        import torch
+
+        self._torch = torch
+        L = load()
+        _bind_unet(L)
+        d = UNetDesc(in_ch, out_ch, base, levels, seed)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.h = ctypes.c_void_p()
+        _unet_check(L.fcm_unet_create(ctypes.byref(d), ctypes.c_void_p(stream), ctypes.byref(self.h)))
+        self.desc = (in_ch, out_ch, base, levels)
+        n = ctypes.c_int64(0)
+        _unet_check(L.fcm_unet_params(self.h, ctypes.byref(n)))
+        self.nparam = n.value
+
+    def get(self, with_grad=False):
+        w = np.zeros(self.nparam, dtype=np.float32)
+        g = np.zeros(self.nparam, dtype=np.float32) if with_grad else None
+        _unet_check(load().fcm_unet_get(self.h, ctypes.c_void_p(w.ctypes.data),
+                                        ctypes.c_void_p(g.ctypes.data) if with_grad else None))
+        return (w, g) if with_grad else w
+
+    def set(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.nparam
+        _unet_check(load().fcm_unet_set(self.h, ctypes.c_void_p(w.ctypes.data)))
+
+    def forward(self, x, out=None):
+        B, C, Z, Y, X = x.shape
+        if out is None:
+            out = self._torch.empty((B, self.desc[1], Z, Y, X), dtype=self._torch.float32, device=x.device)
+        _unet_check(load().fcm_unet_forward(self.h, _ptr(x), B, X, Y, Z, _ptr(out)))
+        return out
+
+    def backward(self, gout, want_din=False):
+        din = None
+        if want_din:
+            shp = list(gout.shape)
+            shp[1] = self.desc[0]
+            din = self._torch.empty(shp, dtype=self._torch.float32, device=gout.device)
+        _unet_check(load().fcm_unet_backward(self.h, _ptr(gout), _ptr(din) if want_din else None))
+        return din
+
+    def zero_grad(self):
+        _unet_check(load().fcm_unet_zero_grad(self.h))
+
+    def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+        _unet_check(load().fcm_unet_adam(self.h, lr, beta1, beta2, eps, step))
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().fcm_unet_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _solver_coarse_restrict(self, v, s=1.0, eta_channel=True, out=None):
+    _bind_unet(load())
+    nc = self.workload.n[0] * self.workload.n[1] * self.workload.n[2]
+    if out is None:
+        out = self._torch.empty((4 if eta_channel else 3) * nc, dtype=self._torch.float32, device="cuda")
+    self._check(load().fcm_coarse_restrict(self.ctx, _ptr(v), s, 1 if eta_channel else 0, _ptr(out)))
+    return out
+
+
+def _solver_coarse_prolong(self, cells, s=1.0, out=None):
+    _bind_unet(load())
+    y = out if out is not None else self.empty()
+    self._check(load().fcm_coarse_prolong(self.ctx, _ptr(cells), s, _ptr(y)))
+    return y
+
+
+def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=True):
+    _bind_unet(load())
+    u = out if out is not None else self.empty()
+    its = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = load().fcm_fpcg_solve(self.ctx, net.h, gamma, _ptr(b), tol, maxit, _ptr(u), ctypes.byref(its),
+                               ctypes.byref(rel))
+    if check:
+        self._check(st)
+    return u, its.value, rel.value, st
+
+
+Solver.coarse_restrict = _solver_coarse_restrict
+Solver.coarse_prolong = _solver_coarse_prolong
+Solver.fpcg_solve = _solver_fpcg_solve
