@@ -148,7 +148,11 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
 fcm_status fcm_info(const fcm_ctx *ctx, fcm_info_t *out);
 
 /* Write load case load_case into b_dev (n_lattice FP64, device).
- *   0: traction of fcm_bc on the top face (Sec. 2.1 Eq. (1), Neumann term). */
+ *   0: traction of fcm_bc on the top face (Sec. 2.1 Eq. (1), Neumann term).
+ *   1..6: unit-strain load cases b_k(v) = -int alpha eps(v) : C : E_k dOmega, E_k the
+ *         Voigt unit strains xx, yy, zz, yz, xz, xy (engineering shears), i.e. the load
+ *         that a prescribed uniform strain E_k exerts through the alpha-weighted
+ *         stiffness of Eq. (1) (equal to -K u_k for the linear field u_k = E_k x). */
 fcm_status fcm_rhs(const fcm_ctx *ctx, int load_case, double *b_dev);
 
 /* Build the Additive-Schwarz preconditioner (Algorithm 1) with vertex-patch
@@ -237,9 +241,10 @@ fcm_status fcm_coarse_prolong(fcm_ctx *ctx, const float *cells_dev, double s, do
  * nonlinear preconditioner z = S r + gamma sigma P N(R r / sigma, eta), N the U-Net,
  * sigma the RMS of R r.  Convergence is judged by the plain Schwarz residual
  * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the judged residual grows 100-fold over
- * its best value or a scalar breaks down, the solve falls back to plain Schwarz-PCG
- * restarted from the current iterate (fcm_last_solve reports it).  iterations counts
- * K applications of both phases. */
+ * its best value, has not halved within 100 iterations, or a scalar breaks down, the
+ * solve falls back to plain Schwarz-PCG on the remaining residual, from the current
+ * iterate (fcm_last_solve reports it).  iterations counts K applications of both
+ * phases.  gamma scales the network output (gamma = 0 gives plain flexible CG). */
 fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, const double *rhs_dev, double tol, int maxit,
                           double *u_dev, int *iterations, double *final_relres);
 

@@ -209,6 +209,7 @@ typedef struct {
     double gx[64], gw[64];
     double D[6][6];
     double *K;          /* ndof x ndof, or NULL */
+    double *Fs;         /* 6 x ndof unit-strain loads, or NULL */
     double solid_vol;
     /* scratch */
     double *B;          /* 6 x ndof */
@@ -244,7 +245,7 @@ static void leaf_quadrature(cell_integrator *ci, const double *blo, const double
                 double w = ci->gw[kx] * ci->gw[ky] * ci->gw[kz] * vol / 8.0;
                 int solid = ora_solid_at(d, x);
                 ci->solid_vol += w * solid;
-                if (!ci->K) continue;
+                if (!ci->K && !ci->Fs) continue;
                 double al = solid ? 1.0 : d->alpha;
                 for (int a = 0; a < 3; ++a) ora_shape1d(p, xi[a], f[a], df[a]);
                 /* B: 6 x ndof, Voigt order xx, yy, zz, yz, xz, xy (engineering shears) */
@@ -273,6 +274,11 @@ static void leaf_quadrature(cell_integrator *ci, const double *blo, const double
                         ci->DB[r * n + j] = s;
                     }
                 double wa = w * al;
+                /* unit-strain load k: -(B^T D e_k) = -(D B)[k][.] since D is symmetric */
+                if (ci->Fs)
+                    for (int k = 0; k < 6; ++k)
+                        for (int i = 0; i < n; ++i) ci->Fs[k * n + i] -= wa * ci->DB[k * n + i];
+                if (!ci->K) continue;
                 for (int i = 0; i < n; ++i)
                     for (int j = i; j < n; ++j) {
                         double s = 0.0;
@@ -311,8 +317,17 @@ static void cell_box(const ora_desc *d, const int *c, double *clo, double *chi, 
 }
 
 /* Element matrix (3(p+1)^3 square, row-major, local DOF = 3*I + comp with
- * I = ix + (p+1)(iy + (p+1) iz)) and volume fraction of cell c.  Ke may be NULL. */
+ * I = ix + (p+1)(iy + (p+1) iz)), the six unit-strain loads of the cell
+ * Fs[k][i] = -int alpha (B^T D e_k)_i (e_k the k-th Voigt unit strain, engineering
+ * shears) and the volume fraction of cell c.  Ke and Fs may be NULL. */
+int ora_cell_matrix_ex(const ora_desc *d, const int *c, double *Ke, double *Fs, double *eta);
+
 int ora_cell_matrix(const ora_desc *d, const int *c, double *Ke, double *eta)
+{
+    return ora_cell_matrix_ex(d, c, Ke, NULL, eta);
+}
+
+int ora_cell_matrix_ex(const ora_desc *d, const int *c, double *Ke, double *Fs, double *eta)
 {
     cell_integrator ci;
     memset(&ci, 0, sizeof ci);
@@ -325,18 +340,19 @@ int ora_cell_matrix(const ora_desc *d, const int *c, double *Ke, double *eta)
     ora_gauss(q, ci.gx, ci.gw);
     material_D(d->E, d->nu, ci.D);
     ci.K = Ke;
-    if (Ke) {
-        memset(Ke, 0, sizeof(double) * ci.ndof * ci.ndof);
+    ci.Fs = Fs;
+    if (Ke) memset(Ke, 0, sizeof(double) * ci.ndof * ci.ndof);
+    if (Fs) memset(Fs, 0, sizeof(double) * 6 * ci.ndof);
+    if (Ke || Fs) {
         ci.B = malloc(sizeof(double) * 6 * ci.ndof);
         ci.DB = malloc(sizeof(double) * 6 * ci.ndof);
     }
     octree(&ci, ci.clo, chi, 0);
-    if (Ke) {
+    if (Ke)
         for (int i = 0; i < ci.ndof; ++i)
             for (int j = 0; j < i; ++j) Ke[(size_t)i * ci.ndof + j] = Ke[(size_t)j * ci.ndof + i];
-        free(ci.B);
-        free(ci.DB);
-    }
+    free(ci.B);
+    free(ci.DB);
     if (eta) *eta = ci.solid_vol / ((chi[0] - ci.clo[0]) * (chi[1] - ci.clo[1]) * (chi[2] - ci.clo[2]));
     return ci.ndof;
 }
@@ -426,6 +442,7 @@ typedef struct {
     int64_t *col;
     double *val;
     double *b;
+    double *bs[6];          /* unit-strain load cases 1..6 (per free DOF) */
     /* preconditioner */
     int nblocks;
     ora_block *blocks;
@@ -472,13 +489,16 @@ ora_problem *ora_problem_build(const ora_desc *din)
     P->eta = calloc(P->ncells, sizeof(double));
     P->active = calloc(P->ncells, 1);
     double **Ke = calloc(P->ncells, sizeof(double *));
+    double **Fcell = calloc(P->ncells, sizeof(double *));
     for (int cz = 0; cz < d->n[2]; ++cz)
         for (int cy = 0; cy < d->n[1]; ++cy)
             for (int cx = 0; cx < d->n[0]; ++cx) {
                 int c[3] = {cx, cy, cz};
                 int ci = cx + d->n[0] * (cy + d->n[1] * cz);
                 double *K = malloc(sizeof(double) * ndof * ndof);
-                ora_cell_matrix(d, c, K, &P->eta[ci]);
+                double *Fs = malloc(sizeof(double) * 6 * ndof);
+                ora_cell_matrix_ex(d, c, K, Fs, &P->eta[ci]);
+                Fcell[ci] = Fs;
                 P->active[ci] = P->eta[ci] > 0.0;
                 if (P->active[ci]) Ke[ci] = K;
                 else free(K);
@@ -519,6 +539,7 @@ ora_problem *ora_problem_build(const ora_desc *din)
     coo_entry *coo = malloc(sizeof(coo_entry) * (cap > 0 ? cap : 1));
     int64_t nz = 0;
     P->b = calloc(P->nfree > 0 ? P->nfree : 1, sizeof(double));
+    for (int k = 0; k < 6; ++k) P->bs[k] = calloc(P->nfree > 0 ? P->nfree : 1, sizeof(double));
     int64_t *g = malloc(sizeof(int64_t) * ndof);
     double *be = malloc(sizeof(double) * ndof);
     for (int cz = 0; cz < d->n[2]; ++cz)
@@ -547,11 +568,18 @@ ora_problem *ora_problem_build(const ora_desc *din)
                 ora_cell_traction(d, c, be);
                 for (int i = 0; i < ndof; ++i)
                     if (g[i] >= 0) P->b[g[i]] += be[i];
+                for (int k = 0; k < 6; ++k)
+                    for (int i = 0; i < ndof; ++i)
+                        if (g[i] >= 0) P->bs[k][g[i]] += Fcell[ci][k * ndof + i];
             }
     free(g);
     free(be);
-    for (int ci = 0; ci < P->ncells; ++ci) free(Ke[ci]);
+    for (int ci = 0; ci < P->ncells; ++ci) {
+        free(Ke[ci]);
+        free(Fcell[ci]);
+    }
     free(Ke);
+    free(Fcell);
     qsort(coo, nz, sizeof(coo_entry), coo_cmp);
     P->rowptr = calloc(P->nfree + 1, sizeof(int64_t));
     P->col = malloc(sizeof(int64_t) * (nz > 0 ? nz : 1));
@@ -579,6 +607,7 @@ void ora_problem_free(ora_problem *P)
     free(P->blocks); free(P->jac); free(P->covered);
     free(P->eta); free(P->active); free(P->free_lat); free(P->lat_free);
     free(P->rowptr); free(P->col); free(P->val); free(P->b);
+    for (int k = 0; k < 6; ++k) free(P->bs[k]);
     free(P->sph_copy); free(P->vox_copy);
     free(P);
 }
@@ -589,6 +618,14 @@ int64_t ora_nlat(const ora_problem *P) { return P->nlat; }
 int ora_ncells(const ora_problem *P) { return P->ncells; }
 void ora_get_free_lat(const ora_problem *P, int64_t *out) { memcpy(out, P->free_lat, sizeof(int64_t) * P->nfree); }
 void ora_get_rhs(const ora_problem *P, double *out) { memcpy(out, P->b, sizeof(double) * P->nfree); }
+/* load case 0: traction; 1..6: unit Voigt strains (xx, yy, zz, yz, xz, xy) */
+int ora_get_load(const ora_problem *P, int load_case, double *out)
+{
+    if (load_case == 0) { memcpy(out, P->b, sizeof(double) * P->nfree); return 0; }
+    if (load_case < 1 || load_case > 6) return -1;
+    memcpy(out, P->bs[load_case - 1], sizeof(double) * P->nfree);
+    return 0;
+}
 void ora_get_eta(const ora_problem *P, double *out) { memcpy(out, P->eta, sizeof(double) * P->ncells); }
 void ora_get_csr(const ora_problem *P, int64_t *rowptr, int64_t *col, double *val)
 {

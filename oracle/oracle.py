@@ -79,6 +79,7 @@ def lib():
         L.ora_ncells.argtypes = [P]
         L.ora_get_free_lat.argtypes = [P, lp]
         L.ora_get_rhs.argtypes = [P, dp]
+        L.ora_get_load.argtypes = [P, ctypes.c_int, dp]
         L.ora_get_eta.argtypes = [P, dp]
         L.ora_get_csr.argtypes = [P, lp, lp, dp]
         L.ora_apply_K.argtypes = [P, dp, dp]
@@ -225,6 +226,13 @@ class Problem:
     def rhs(self):
         b = np.zeros(self.nfree)
         lib().ora_get_rhs(self.h, _dp(b))
+        return b
+
+    def load(self, load_case):
+        """Load case 0 (traction) or 1..6 (unit Voigt strains xx, yy, zz, yz, xz, xy)."""
+        b = np.zeros(self.nfree)
+        if lib().ora_get_load(self.h, load_case, _dp(b)) != 0:
+            raise ValueError("load case must be in 0..6")
         return b
 
     def eta(self):

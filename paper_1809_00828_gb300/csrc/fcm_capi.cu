@@ -170,6 +170,9 @@ void free_ctx(fcm_ctx *C)
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (C->h_s) cudaFreeHost(C->h_s);
+    if (C->d_m) cudaFree(C->d_m);
+    if (C->d_ms) cudaFree(C->d_ms);
+    if (C->h_ms) cudaFreeHost(C->h_ms);
     cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1};
     for (auto e : evs)
         if (e) cudaEventDestroy(e);
@@ -346,12 +349,19 @@ fcm_status fcm_rhs(const fcm_ctx *Cc, int load_case, double *b_dev)
 {
     fcm_ctx *C = const_cast<fcm_ctx *>(Cc);
     if (!C || !b_dev) return FCM_EINVAL;
-    if (load_case != 0) {
-        C->err = "fcm_rhs: unknown load case";
+    if (load_case < 0 || load_case > 6) {
+        C->err = "fcm_rhs: load case must be in 0..6";
         return FCM_EINVAL;
     }
     StreamScope sc(C);
-    API_CUDA(C, cudaMemcpyAsync(b_dev, C->d_rhs, sizeof(double) * C->nlat, cudaMemcpyDeviceToDevice, C->stream));
+    if (load_case == 0) {
+        API_CUDA(C, cudaMemcpyAsync(b_dev, C->d_rhs, sizeof(double) * C->nlat, cudaMemcpyDeviceToDevice, C->stream));
+    } else {
+        // host copy of the set-up; synchronous so that the host buffer may be reused at once
+        API_CUDA(C, cudaMemcpyAsync(b_dev, C->hp.rhs_strain.data() + (size_t)(load_case - 1) * C->nlat,
+                                    sizeof(double) * C->nlat, cudaMemcpyHostToDevice, C->stream));
+        API_CUDA(C, cudaStreamSynchronize(C->stream));
+    }
     return FCM_OK;
 }
 
@@ -383,6 +393,94 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     return FCM_OK;
 }
 
+// nr independent PCG recurrences (one per right-hand side) that share every Schwarz launch: the block
+// factors are read once per iteration for all nr residuals.  K is applied per right-hand side; each
+// recurrence stops on its own ||S r|| / ||S b|| <= tol (its kernels then return at once).
+static fcm_status solve_multi(fcm_ctx *C, const double *rhs, int nr, double tol, int maxit, double *u,
+                              fcm_solve_info &agg)
+{
+    const int64_t n = C->nlat;
+    cudaStream_t st = C->stream;
+    if (C->m_nr != nr) {
+        if (C->d_m) cudaFree(C->d_m);
+        if (C->d_ms) cudaFree(C->d_ms);
+        if (C->h_ms) cudaFreeHost(C->h_ms);
+        C->d_m = nullptr;
+        C->d_ms = nullptr;
+        C->h_ms = nullptr;
+        C->m_nr = 0;
+        API_CUDA(C, cudaMalloc(&C->d_m, sizeof(double) * 6 * (size_t)nr * n));
+        API_CUDA(C, cudaMalloc(&C->d_ms, sizeof(CgScalars) * nr));
+        API_CUDA(C, cudaMallocHost((void **)&C->h_ms, sizeof(CgScalars) * nr));
+        C->m_nr = nr;
+    }
+    double *X = C->d_m, *R = X + (size_t)nr * n, *Z = R + (size_t)nr * n, *Pd = Z + (size_t)nr * n,
+           *Q = Pd + (size_t)nr * n, *B = Q + (size_t)nr * n;
+    std::vector<CgWork> w(nr);
+    double bb[2];
+    for (int k = 0; k < nr; ++k) {
+        w[k] = work_of(C);
+        w[k].x = X + (size_t)k * n;
+        w[k].r = R + (size_t)k * n;
+        w[k].z = Z + (size_t)k * n;
+        w[k].p = Pd + (size_t)k * n;
+        w[k].q = Q + (size_t)k * n;
+        w[k].b = B + (size_t)k * n;
+        w[k].s = C->d_ms + k;
+        fcm::launch_mask_copy(rhs + (size_t)k * n, w[k].b, C->d_mask, n, st);
+        fcm::cg_residual_norms(w[k], w[k].b, w[k].b, C->d_out2, st);
+        API_CUDA(C, cudaMemcpyAsync(bb, C->d_out2, sizeof bb, cudaMemcpyDeviceToHost, st));
+        API_CUDA(C, cudaStreamSynchronize(st));
+        if (!std::isfinite(bb[1])) {
+            C->err = "right-hand side has non-finite entries";
+            return FCM_EINVAL;
+        }
+        std::memset(C->h_ms + k, 0, sizeof(CgScalars));
+        C->h_ms[k].tol = tol;
+        C->h_ms[k].maxit = maxit;
+    }
+    API_CUDA(C, cudaMemcpyAsync(C->d_ms, C->h_ms, sizeof(CgScalars) * nr, cudaMemcpyHostToDevice, st));
+    API_CUDA(C, cudaEventRecord(C->ev_t0, st));
+    for (int k = 0; k < nr; ++k) fcm::cg_init_kernels(w[k], st);
+    fcm::launch_zero(Z, (int64_t)nr * n, nullptr, st);
+    fcm::launch_schwarz_apply_multi(C->p, C->g, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, nullptr, st);
+    for (int k = 0; k < nr; ++k) fcm::cg_after_first_S(w[k], st);
+    for (int it = 0;; ++it) {
+        if (it % 8 == 0) {
+            API_CUDA(C, cudaMemcpyAsync(C->h_ms, C->d_ms, sizeof(CgScalars) * nr, cudaMemcpyDeviceToHost, st));
+            API_CUDA(C, cudaStreamSynchronize(st));
+            bool all = true;
+            for (int k = 0; k < nr; ++k) all = all && C->h_ms[k].done;
+            if (all) break;
+        }
+        for (int k = 0; k < nr; ++k) apply_K_dev(C, w[k].p, w[k].q, &C->d_ms[k].done);
+        for (int k = 0; k < nr; ++k) fcm::cg_after_K(w[k], st);
+        fcm::launch_zero(Z, (int64_t)nr * n, nullptr, st);
+        fcm::launch_schwarz_apply_multi(C->p, C->g, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, nullptr, st);
+        for (int k = 0; k < nr; ++k) fcm::cg_after_S(w[k], st);
+        API_CUDA(C, cudaGetLastError());
+    }
+    API_CUDA(C, cudaEventRecord(C->ev_t1, st));
+    API_CUDA(C, cudaMemcpyAsync(u, X, sizeof(double) * (size_t)nr * n, cudaMemcpyDeviceToDevice, st));
+    fcm_status worst = FCM_OK;
+    for (int k = 0; k < nr; ++k) {
+        apply_K_dev(C, w[k].x, C->d_q, nullptr);
+        fcm::cg_residual_norms(w[k], C->d_q, w[k].b, C->d_out2, st);
+        API_CUDA(C, cudaMemcpyAsync(bb, C->d_out2, sizeof bb, cudaMemcpyDeviceToHost, st));
+        API_CUDA(C, cudaStreamSynchronize(st));
+        const CgScalars &h = C->h_ms[k];
+        agg.iterations = std::max(agg.iterations, h.it);
+        agg.relres = std::max(agg.relres, h.relres);
+        agg.true_relres = std::max(agg.true_relres, bb[1] > 0.0 ? std::sqrt(bb[0] / bb[1]) : 0.0);
+        if (h.status != FCM_OK && worst == FCM_OK) worst = (fcm_status)h.status;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, C->ev_t0, C->ev_t1);
+    agg.seconds = ms * 1e-3;
+    agg.status = worst;
+    return worst;
+}
+
 static fcm_status solve_many(fcm_ctx *C, const double *rhs, int nrhs, double tol, int maxit, double *u, bool host,
                              int *iterations, double *final_relres)
 {
@@ -398,6 +496,12 @@ static fcm_status solve_many(fcm_ctx *C, const double *rhs, int nrhs, double tol
     fcm_solve_info agg = {};
     agg.status = FCM_OK;
     fcm_status worst = FCM_OK;
+    const bool fp64_p4 = C->p == 4 && C->d_f64;
+    if (!host && nrhs > 1 && nrhs <= 8 && !fp64_p4) {
+        worst = solve_multi(C, rhs, nrhs, tol, maxit, u, agg);
+        if (worst == FCM_EINVAL || worst == FCM_ECUDA || worst == FCM_ENOMEM) return worst;
+        nrhs = 0;  // done
+    }
     for (int k = 0; k < nrhs; ++k) {
         const double *b = rhs + (size_t)k * C->nlat;
         double *x = u + (size_t)k * C->nlat;

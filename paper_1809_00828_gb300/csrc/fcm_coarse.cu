@@ -8,15 +8,16 @@
 //
 // The preconditioner of the flexible PCG is z = S r + gamma sigma P N(R r /
 // sigma, eta), with S the Additive-Schwarz operator (Sec. 3.1 Eq. (5)) and N
-// the U-Net.  Because N is nonlinear, the search directions are
-// K-orthogonalised explicitly (Notay's flexible CG with one previous
-// direction).  Convergence is judged on ||S r|| / ||S b|| (Sec. 5 Eq. (14))
+// the U-Net.  Because N is nonlinear, each new search direction is
+// K-orthogonalised explicitly against the last four (truncated flexible CG,
+// Notay, SIAM J. Sci. Comput. 22, 2000).  Convergence is judged on ||S r|| / ||S b|| (Sec. 5 Eq. (14))
 // with the plain Schwarz part, so the judge is the same as for plain PCG.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "fcm_device.cuh"
 
@@ -154,6 +155,16 @@ __global__ void add_kernel(double *z, const double *a, const double *b, int64_t 
 __global__ void xpby_kernel(double *p, const double *z, int64_t n, double beta)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
+}
+
+// y += a u (+ b v when v is non-null)
+__global__ void xpby_acc_kernel(double *y, const double *u, double a, const double *v, double b, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double t = fma(a, u[i], y[i]);
+        if (v) t = fma(b, v[i], t);
+        y[i] = t;
+    }
 }
 
 // r = b - q (explicit residual)
@@ -302,26 +313,49 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double 
     ctx_apply_S(C, r, zS);
     if ((s = dot2(C, zS, zS, nullptr, nullptr, h2)) != FCM_OK) return s;
     const double judge0 = std::sqrt(h2[0]);
-    double rel = 0.0, best = 1.0;
-    int it = 0;
+    double rel = 0.0, best = 1.0, mark = 1.0;
+    int it = 0, mark_it = 0;
+    constexpr int kStallWindow = 100;
     bool converged = judge0 == 0.0, fallback = false;
+    // truncated flexible CG, FCG(m) (Notay 2000): each new direction is K-orthogonalised
+    // against the last kTrunc ones; ring of kTrunc + 1 direction slots (slot 0 = C->d_p/d_q)
+    constexpr int kTrunc = 4, kRing = kTrunc + 1;
+    double *P[kRing], *Q[kRing], pqs[kRing] = {0.0};
+    P[0] = p;
+    Q[0] = q;
+    std::vector<double *> extra;
+    struct FreeRing {
+        std::vector<double *> &v;
+        ~FreeRing()
+        {
+            for (double *a : v) cudaFree(a);
+        }
+    } free_ring{extra};
+    for (int k = 1; k < kRing; ++k) {
+        CO_CUDA(C, cudaMalloc(&P[k], sizeof(double) * n));
+        extra.push_back(P[k]);
+        CO_CUDA(C, cudaMalloc(&Q[k], sizeof(double) * n));
+        extra.push_back(Q[k]);
+    }
     if (!converged) {
         if ((s = coarse_correction(C, net, gamma, r, ws, ws.c)) != FCM_OK) return s;
-        add_kernel<<<nblk(n), 256, 0, st>>>(ws.z, zS, ws.c, n);
-        CO_CUDA(C, cudaMemcpyAsync(p, ws.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        add_kernel<<<nblk(n), 256, 0, st>>>(P[0], zS, ws.c, n);
         rel = 1.0;
     }
     while (!converged && !fallback && it < maxit) {
-        ctx_apply_K(C, p, q);
-        if ((s = dot2(C, p, q, p, r, h2)) != FCM_OK) return s;
+        const int cur = it % kRing;
+        double *pc = P[cur], *qc = Q[cur];
+        ctx_apply_K(C, pc, qc);
+        if ((s = dot2(C, pc, qc, pc, r, h2)) != FCM_OK) return s;
         const double pq = h2[0], pr = h2[1];
+        pqs[cur] = pq;
         ++it;
         if (!(pq > 0.0) || !std::isfinite(pr)) {
             fallback = true;
             break;
         }
         const double alpha = pr / pq;
-        axpy2_kernel<<<nblk(n), 256, 0, st>>>(x, r, p, q, n, alpha);
+        axpy2_kernel<<<nblk(n), 256, 0, st>>>(x, r, pc, qc, n, alpha);
         ctx_apply_S(C, r, zS);
         if ((s = dot2(C, zS, zS, nullptr, nullptr, h2)) != FCM_OK) return s;
         rel = std::sqrt(h2[0]) / judge0;
@@ -334,15 +368,29 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double 
             converged = true;
             break;
         }
-        if (rel > 100.0 * best) {
+        if (rel <= 0.5 * mark) {
+            mark = rel;
+            mark_it = it;
+        }
+        // a harmful or useless correction: growth, or no halving within kStallWindow iterations
+        if (rel > 100.0 * best || it - mark_it >= kStallWindow) {
             fallback = true;
             break;
         }
         if ((s = coarse_correction(C, net, gamma, r, ws, ws.c)) != FCM_OK) return s;
         add_kernel<<<nblk(n), 256, 0, st>>>(ws.z, zS, ws.c, n);
-        if ((s = dot2(C, ws.z, q, nullptr, nullptr, h2)) != FCM_OK) return s;
-        const double beta = -h2[0] / pq;
-        xpby_kernel<<<nblk(n), 256, 0, st>>>(p, ws.z, n, beta);
+        // p_new = z - sum_j (z.q_j / p_j.q_j) p_j over the last min(it, kTrunc) directions
+        const int nxt = it % kRing;
+        CO_CUDA(C, cudaMemcpyAsync(P[nxt], ws.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        const int nprev = std::min(it, kTrunc);
+        for (int j0 = 0; j0 < nprev; j0 += 2) {
+            const int a = (it - 1 - j0 + kRing) % kRing;
+            const int b2 = (it - 2 - j0 + kRing) % kRing;
+            const bool two = j0 + 1 < nprev;
+            if ((s = dot2(C, ws.z, Q[a], two ? ws.z : nullptr, two ? Q[b2] : nullptr, h2)) != FCM_OK) return s;
+            xpby_acc_kernel<<<nblk(n), 256, 0, st>>>(P[nxt], P[a], -h2[0] / pqs[a], two ? P[b2] : nullptr,
+                                                      two ? -h2[1] / pqs[b2] : 0.0, n);
+        }
     }
     int total = it;
     fcm_status status = converged ? FCM_OK : FCM_ENOTCONV;

@@ -64,6 +64,10 @@ void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uin
                     const KCells &kc, const int *done, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
                           const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
+// nr <= 8 right-hand sides stored nlat apart (p = 4 needs FP32 factors)
+void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,
+                                const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
+                                cudaStream_t s);
 void launch_mask_copy(const double *in, double *out, const uint8_t *mask, int64_t n, cudaStream_t s);
 void launch_zero(double *v, int64_t n, const int *done, cudaStream_t s);
 
@@ -141,4 +145,8 @@ struct fcm_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     fcm_solve_info last = {};
+    // multi-RHS workspace: x, r, z, p, q, b for m_nr right-hand sides, and their CG scalars
+    double *d_m = nullptr;
+    fcm::CgScalars *d_ms = nullptr, *h_ms = nullptr;
+    int m_nr = 0;
 };

@@ -43,6 +43,7 @@ struct HostProblem {
     std::vector<uint8_t> mask;      // per lattice DOF: 1 = free
     int64_t nfree = 0;
     std::vector<double> rhs;        // load case 0, lattice layout
+    std::vector<double> rhs_strain; // load cases 1..6 (unit Voigt strains), 6 x nlat
 };
 
 // 1D tables for the sum-factorised stiffness apply of an uncut cell: shape

@@ -188,28 +188,29 @@ __global__ void __launch_bounds__(256)
             if (mask[3 * node + c]) y[3 * node + c] += out[c];
 }
 
-// z += F_B r_B for one batch of patches of one colour that share the stored
-// factor F (G = 8), or for one patch with its own factor (G = 1).  F is the
-// dense symmetric pseudo inverse over the patch box (zero rows/columns for
-// box DOFs outside the block), stored in T = double or float.  Each thread
-// owns rows of the box; one load of F[j][t] feeds G multiply-adds, so a
-// shared factor is read once per batch instead of once per patch.  The
-// gathered residuals of the batch sit in shared memory as rbT[j][g] so that
-// one vector load returns the G values a row step needs.
-template <int P, int G, typename T>
-__global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
-    schwarz_batch_kernel(const double *__restrict__ r, double *__restrict__ z, const T *__restrict__ pool,
-                         const PatchRec *__restrict__ patches, const int2 *__restrict__ batches, Grid3 g,
-                         const int *__restrict__ done)
+// Work kinds of the Schwarz apply, stored in bits 8.. of a batch's .y (bits 0..7: patch count).
+enum { kF32Shared = 0, kF32Single = 1, kF64Shared = 2, kF64Single = 3 };
+
+// z += F r_B for the `count` patches of one batch, which share the stored
+// factor F (shared batches, up to G patches) or have their own (G = 1).  F is
+// the dense symmetric pseudo inverse over the patch box (zero rows/columns
+// for box DOFs outside the block), stored in T = double or float.  Each
+// thread owns rows of the box; one load of F[j][t] feeds G multiply-adds, so
+// a shared factor is read once per batch instead of once per patch.  The
+// gathered residuals sit in shared memory as rbT[j][g], so one vector load
+// returns the G values a row step needs.  UNROLL sets the loads in flight
+// per thread (cut patches stream their factor from DRAM and are latency-bound).
+template <int P, int G, typename T, int UNROLL>
+__device__ __forceinline__ void apply_batch(const double *__restrict__ r, double *__restrict__ z,
+                                            const T *__restrict__ pool, const PatchRec *__restrict__ patches,
+                                            int first, int count, const Grid3 &g, unsigned char *smem)
 {
     constexpr int W = 2 * P - 1, NB = 3 * W * W * W;
-    if (done && *done) return;
-    __shared__ __align__(16) T rbT[NB][G];
-    __shared__ int vtx[G];
-    const int2 bt = batches[blockIdx.x];
+    T(*rbT)[G] = reinterpret_cast<T(*)[G]>(smem);
+    int *vtx = reinterpret_cast<int *>(smem + sizeof(T) * NB * G);
     const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
-    const PatchRec p0 = patches[bt.x];
-    if (threadIdx.x < G) vtx[threadIdx.x] = threadIdx.x < bt.y ? patches[bt.x + threadIdx.x].v : -1;
+    const PatchRec p0 = patches[first];
+    if (threadIdx.x < G) vtx[threadIdx.x] = (int)threadIdx.x < count ? patches[first + threadIdx.x].v : -1;
     // the patches of a batch share the factor, hence the box shape; the origin differs
     int d[3];
     {
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2
         T acc[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) acc[k] = (T)0;
-#pragma unroll 4
+#pragma unroll UNROLL
         for (int j = 0; j < n; ++j) {
             const T f = __ldg(F + (size_t)j * n + t);
 #pragma unroll
@@ -248,6 +249,95 @@ __global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2
 #pragma unroll
         for (int k = 0; k < G; ++k)
             if (vtx[k] >= 0) z[gidx(vtx[k], t)] += (double)acc[k];
+    }
+}
+
+// Several right-hand sides (nr <= 8, vectors nlat apart): z_k += F r_k,B for each patch of
+// the work item, one patch after the other; one load of F[j][t] feeds nr multiply-adds.
+template <int P, typename T, int UNROLL>
+__device__ __forceinline__ void apply_multi(const double *__restrict__ r, double *__restrict__ z, int64_t nlat, int nr,
+                                            const T *__restrict__ pool, const PatchRec *__restrict__ patches,
+                                            int first, int count, const Grid3 &g, unsigned char *smem)
+{
+    constexpr int W = 2 * P - 1, NB = 3 * W * W * W, MR = 8;
+    T(*rbT)[MR] = reinterpret_cast<T(*)[MR]>(smem);
+    const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
+    for (int b = 0; b < count; ++b) {
+        const PatchRec pr = patches[first + b];
+        const int v[3] = {pr.v % nvx, (pr.v / nvx) % nvy, pr.v / (nvx * nvy)};
+        int lo[3], d[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = max(0, P * v[a] - (P - 1));
+            d[a] = min(g.M[a] - 1, P * v[a] + (P - 1)) - lo[a] + 1;
+        }
+        const int n = 3 * d[0] * d[1] * d[2];
+        auto gidx = [&](int t) -> int64_t {
+            const int nl = t / 3;
+            const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
+            return 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + t % 3;
+        };
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * MR; e += blockDim.x) {
+            const int t = e / MR, k = e % MR;
+            rbT[t][k] = k < nr ? (T)r[(int64_t)k * nlat + gidx(t)] : (T)0;
+        }
+        __syncthreads();
+        const T *__restrict__ F = pool + pr.off;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            T acc[MR];
+#pragma unroll
+            for (int k = 0; k < MR; ++k) acc[k] = (T)0;
+#pragma unroll UNROLL
+            for (int j = 0; j < n; ++j) {
+                const T f = __ldg(F + (size_t)j * n + t);
+#pragma unroll
+                for (int k = 0; k < MR; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
+            }
+            const int64_t gi = gidx(t);
+            for (int k = 0; k < nr; ++k) z[(int64_t)k * nlat + gi] += (double)acc[k];
+        }
+    }
+}
+
+// One colour of the Schwarz apply for nr right-hand sides at once (multi-RHS solves).
+template <int P>
+__global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
+    schwarz_multi_kernel(const double *__restrict__ r, double *__restrict__ z, int64_t nlat, int nr,
+                         const double *__restrict__ f64, const float *__restrict__ f32,
+                         const PatchRec *__restrict__ patches, const int2 *__restrict__ batches, Grid3 g,
+                         const int *__restrict__ done)
+{
+    constexpr int W = 2 * P - 1, NB = 3 * W * W * W;
+    __shared__ __align__(16) unsigned char smem[NB * 8 * (P == 4 ? 4 : 8)];
+    if (done && *done) return;
+    const int2 bt = batches[blockIdx.x];
+    const int count = bt.y & 255, kind = bt.y >> 8;
+    if (kind == kF32Shared || kind == kF32Single)
+        apply_multi<P, float, 8>(r, z, nlat, nr, f32, patches, bt.x, count, g, smem);
+    else if (P < 4)
+        apply_multi<P, double, 8>(r, z, nlat, nr, f64, patches, bt.x, count, g, smem);
+}
+
+// One colour of the Schwarz apply (Sec. 3.1 Eq. (5)): each CTA takes one work
+// item (a shared-factor batch or a single patch, FP32 or FP64 factor).  The
+// patches of one colour are DOF-disjoint, so the scatter needs no atomics.
+template <int P>
+__global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
+    schwarz_colour_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ f64,
+                          const float *__restrict__ f32, const PatchRec *__restrict__ patches,
+                          const int2 *__restrict__ batches, Grid3 g, const int *__restrict__ done)
+{
+    constexpr int W = 2 * P - 1, NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8);
+    constexpr int ROW = (GD * 8 > 8 * 4 ? GD * 8 : 8 * 4);  // bytes of one rbT row, largest variant
+    __shared__ __align__(16) unsigned char smem[NB * ROW + 64];
+    if (done && *done) return;
+    const int2 bt = batches[blockIdx.x];
+    const int count = bt.y & 255, kind = bt.y >> 8;
+    switch (kind) {
+    case kF32Shared: apply_batch<P, 8, float, 4>(r, z, f32, patches, bt.x, count, g, smem); break;
+    case kF32Single: apply_batch<P, 1, float, 16>(r, z, f32, patches, bt.x, count, g, smem); break;
+    case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, smem); break;
+    default: apply_batch<P, 1, double, 16>(r, z, f64, patches, bt.x, count, g, smem); break;
     }
 }
 
@@ -286,20 +376,24 @@ void schwarz_launch(const Grid3 &g, const double *r, double *z, const double *f6
                     const SchwarzPlan &plan, const int *done, cudaStream_t s)
 {
     constexpr int NB = 3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1);
-    constexpr int TH = threads_for(NB);
     for (int i = 0; i < plan.nseg; ++i) {
         const SchwarzSeg &sg = plan.seg[i];
-        if (sg.count <= 0) continue;
-        const int2 *b = plan.batches + sg.first;
-        // shared-factor batches hold 8 patches (4 for FP64 at p = 4, to stay within static shared memory)
-        if (sg.prec == 1 && sg.G > 1)
-            schwarz_batch_kernel<P, 8, float><<<sg.count, TH, 0, s>>>(r, z, f32, plan.patches, b, g, done);
-        else if (sg.prec == 1)
-            schwarz_batch_kernel<P, 1, float><<<sg.count, TH, 0, s>>>(r, z, f32, plan.patches, b, g, done);
-        else if (sg.G > 1)
-            schwarz_batch_kernel<P, (P == 4 ? 4 : 8), double><<<sg.count, TH, 0, s>>>(r, z, f64, plan.patches, b, g, done);
-        else
-            schwarz_batch_kernel<P, 1, double><<<sg.count, TH, 0, s>>>(r, z, f64, plan.patches, b, g, done);
+        if (sg.count > 0)
+            schwarz_colour_kernel<P><<<sg.count, threads_for(NB), 0, s>>>(r, z, f64, f32, plan.patches,
+                                                                         plan.batches + sg.first, g, done);
+    }
+}
+
+template <int P>
+void schwarz_multi_launch(const Grid3 &g, const double *r, double *z, int64_t nlat, int nr, const double *f64,
+                          const float *f32, const SchwarzPlan &plan, const int *done, cudaStream_t s)
+{
+    constexpr int NB = 3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1);
+    for (int i = 0; i < plan.nseg; ++i) {
+        const SchwarzSeg &sg = plan.seg[i];
+        if (sg.count > 0)
+            schwarz_multi_kernel<P><<<sg.count, threads_for(NB), 0, s>>>(r, z, nlat, nr, f64, f32, plan.patches,
+                                                                        plan.batches + sg.first, g, done);
     }
 }
 
@@ -332,6 +426,19 @@ void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, con
     case 2: schwarz_launch<2>(g, r, z, f64, f32, plan, done, s); break;
     case 3: schwarz_launch<3>(g, r, z, f64, f32, plan, done, s); break;
     case 4: schwarz_launch<4>(g, r, z, f64, f32, plan, done, s); break;
+    default: break;
+    }
+}
+
+void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,
+                                const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
+                                cudaStream_t s)
+{
+    switch (p) {
+    case 1: schwarz_multi_launch<1>(g, r, z, nlat, nr, f64, f32, plan, done, s); break;
+    case 2: schwarz_multi_launch<2>(g, r, z, nlat, nr, f64, f32, plan, done, s); break;
+    case 3: schwarz_multi_launch<3>(g, r, z, nlat, nr, f64, f32, plan, done, s); break;
+    case 4: schwarz_multi_launch<4>(g, r, z, nlat, nr, f64, f32, plan, done, s); break;
     default: break;
     }
 }

@@ -463,29 +463,32 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
                 C->n_blocks += 1;
                 C->sapply_fmas += (int64_t)fac[f].n * fac[f].n;
             }
+    // One launch per colour.  Work items, heaviest first so that the tail of the launch is short:
+    // FP64 shared-factor batches, FP64 single patches, FP32 single patches (DRAM-bound), FP32 batches.
+    // Kinds as in fcm_kernels.cu: 0 FP32 shared, 1 FP32 single, 2 FP64 shared, 3 FP64 single.
     std::vector<PatchRec> all;
     std::vector<int2> batches;
     SchwarzPlan plan = {};
-    for (int c = 0; c < 8; ++c)
-        for (int pr = 0; pr < 2; ++pr)
-            for (int shared = 1; shared >= 0; --shared) {
-                SchwarzSeg sg = {c, pr, shared ? 8 : 1, (int)batches.size(), 0};
-                const int cap = shared ? ((p == 4 && pr == 0) ? 4 : 8) : 1;
-                for (size_t f = 0; f < fac.size(); ++f) {
-                    const std::vector<int> &vs = by_colour_factor[c][f];
-                    if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
-                    for (size_t s0 = 0; s0 < vs.size(); s0 += cap) {
-                        const int cnt = (int)std::min<size_t>(cap, vs.size() - s0);
-                        batches.push_back(make_int2((int)all.size(), cnt));
-                        for (int k = 0; k < cnt; ++k) all.push_back({off[f], vs[s0 + k], prec[f]});
-                    }
-                }
-                sg.count = (int)batches.size() - sg.first;
-                if (sg.count > 0) {
-                    if (plan.nseg >= 32) return "launch plan has too many segments";
-                    plan.seg[plan.nseg++] = sg;
+    const int order[4][2] = {{0, 1}, {0, 0}, {1, 0}, {1, 1}};  // (precision 0 = FP64 / 1 = FP32, shared?)
+    for (int c = 0; c < 8; ++c) {
+        SchwarzSeg sg = {c, -1, 0, (int)batches.size(), 0};
+        for (const auto &o : order) {
+            const int pr = o[0], shared = o[1];
+            const int kind = pr == 1 ? (shared ? 0 : 1) : (shared ? 2 : 3);
+            const int cap = shared ? ((p == 4 && pr == 0) ? 4 : 8) : 1;
+            for (size_t f = 0; f < fac.size(); ++f) {
+                const std::vector<int> &vs = by_colour_factor[c][f];
+                if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
+                for (size_t s0 = 0; s0 < vs.size(); s0 += cap) {
+                    const int cnt = (int)std::min<size_t>(cap, vs.size() - s0);
+                    batches.push_back(make_int2((int)all.size(), cnt | (kind << 8)));
+                    for (int k = 0; k < cnt; ++k) all.push_back({off[f], vs[s0 + k], prec[f]});
                 }
             }
+        }
+        sg.count = (int)batches.size() - sg.first;
+        if (sg.count > 0) plan.seg[plan.nseg++] = sg;
+    }
     if (C->d_patches) cudaFree(C->d_patches);
     if (C->d_batches) cudaFree(C->d_batches);
     C->d_patches = nullptr;

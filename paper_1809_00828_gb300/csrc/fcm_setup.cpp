@@ -157,6 +157,8 @@ struct Tables {
     double coef[4][kMaxQ][kMaxQ][kMaxL];
     // face[a][m]: Legendre coefficient m of f_a
     double face[kMaxQ][kMaxL];
+    // dface[a][m]: Legendre coefficient m of f_a'
+    double dface[kMaxQ][kMaxL];
 };
 
 void make_tables(int p, Tables &T)
@@ -170,6 +172,7 @@ void make_tables(int p, Tables &T)
     gauss_legendre(ng, x, w);
     std::memset(T.coef, 0, sizeof T.coef);
     std::memset(T.face, 0, sizeof T.face);
+    std::memset(T.dface, 0, sizeof T.dface);
     for (int g = 0; g < ng; ++g) {
         double f[kMaxQ], df[kMaxQ], P[kMaxL + 2];
         shape_1d(p, x[g], f, df);
@@ -178,6 +181,7 @@ void make_tables(int p, Tables &T)
             const double s = w[g] * P[m] * (2 * m + 1) * 0.5;
             for (int a = 0; a <= p; ++a) {
                 T.face[a][m] += s * f[a];
+                T.dface[a][m] += s * df[a];
                 for (int b = 0; b <= p; ++b) {
                     T.coef[0][a][b][m] += s * f[a] * f[b];
                     T.coef[1][a][b][m] += s * df[a] * f[b];
@@ -333,6 +337,51 @@ void element_from_moments(const Setup &S, const double *mu, double *K)
             K[(size_t)r * ne + c] = v;
             K[(size_t)c * ne + r] = v;
         }
+}
+
+// Unit-strain loads of one cell from the moments of the alpha-weighted measure:
+// G1[j][I] = int alpha d_j N_I, and load case k (Voigt unit strain e_k, engineering
+// shears) gives be[k][3I + a] = -sum_j sigma_k[a][j] G1[j][I] with sigma_k = C : E_k.
+void strain_loads_from_moments(const Setup &S, const double *mu, double *be)
+{
+    const HostProblem &P = *S.P;
+    const int q = S.T.q, L = S.T.L, nl = q * q * q, ne = 3 * nl;
+    const double vol = P.h[0] * P.h[1] * P.h[2] / 8.0;
+    const double lam = P.E * P.nu / ((1.0 + P.nu) * (1.0 - 2.0 * P.nu));
+    const double mus = P.E / (2.0 * (1.0 + P.nu));
+    std::vector<double> G1(3 * (size_t)nl);
+    for (int j = 0; j < 3; ++j)
+        for (int i2 = 0; i2 < q; ++i2)
+            for (int i1 = 0; i1 < q; ++i1)
+                for (int i0 = 0; i0 < q; ++i0) {
+                    const double *e0 = j == 0 ? S.T.dface[i0] : S.T.face[i0];
+                    const double *e1 = j == 1 ? S.T.dface[i1] : S.T.face[i1];
+                    const double *e2 = j == 2 ? S.T.dface[i2] : S.T.face[i2];
+                    double s = 0.0;
+                    for (int m0 = 0; m0 < L; ++m0)
+                        for (int m1 = 0; m1 < L; ++m1) {
+                            const double t = e0[m0] * e1[m1];
+                            for (int m2 = 0; m2 < L; ++m2) s += t * e2[m2] * mu[(m0 * L + m1) * L + m2];
+                        }
+                    G1[(size_t)j * nl + i0 + q * (i1 + q * i2)] = vol * (2.0 / P.h[j]) * s;
+                }
+    static const int voigt[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+    for (int k = 0; k < 6; ++k) {
+        double sig[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const int a0 = voigt[k][0], b0 = voigt[k][1];
+        if (a0 == b0) {
+            for (int a = 0; a < 3; ++a) sig[a][a] = lam;
+            sig[a0][a0] += 2.0 * mus;
+        } else {
+            sig[a0][b0] = sig[b0][a0] = mus;  // engineering shear strain 1
+        }
+        for (int I = 0; I < nl; ++I)
+            for (int a = 0; a < 3; ++a) {
+                double v = 0.0;
+                for (int j = 0; j < 3; ++j) v += sig[a][j] * G1[(size_t)j * nl + I];
+                be[(size_t)k * ne + 3 * I + a] = -v;
+            }
+    }
 }
 
 // Solid-part 2D Legendre moments of the top face of a cell (reference square measure).
@@ -567,22 +616,27 @@ std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, i
     // 2. element matrices: the uncut reference and one per crossed cell
     const size_t ne2 = (size_t)P.ne * P.ne;
     P.Kref.assign(ne2, 0.0);
+    std::vector<double> be_ref;
     {
         std::vector<double> mu(L3, 0.0);
         mu[0] = 8.0;
         element_from_moments(S, mu.data(), P.Kref.data());
+        be_ref.assign(6 * (size_t)P.ne, 0.0);
+        strain_loads_from_moments(S, mu.data(), be_ref.data());
     }
     P.Kcut.assign(ne2 * ncut, 0.0);
     std::vector<int64_t> cut_cells;
     cut_cells.reserve(ncut);
     for (int64_t ci = 0; ci < P.ncells; ++ci)
         if (kind[ci] == 2) cut_cells.push_back(ci);
+    std::vector<double> be_cut(6 * (size_t)P.ne * ncut);
     parallel_for(ncut, nthreads, [&](int64_t k) {
         const int64_t ci = cut_cells[k];
         std::vector<double> mu(moments[ci]);
         for (int m = 0; m < L3; ++m) mu[m] *= (1.0 - P.alpha);
         mu[0] += 8.0 * P.alpha;
         element_from_moments(S, mu.data(), P.Kcut.data() + ne2 * k);
+        strain_loads_from_moments(S, mu.data(), be_cut.data() + 6 * (size_t)P.ne * k);
         std::vector<double>().swap(moments[ci]);
     });
 
@@ -610,6 +664,25 @@ std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, i
                 ++P.nfree;
             }
         }
+    }
+
+    // 4a. unit-strain load cases 1..6
+    P.rhs_strain.assign(6 * (size_t)P.nlat, 0.0);
+    for (int64_t ci = 0; ci < P.ncells; ++ci) {
+        const int32_t el = P.cell_elem[ci];
+        if (el < 0) continue;
+        const double *be = el == 0 ? be_ref.data() : be_cut.data() + 6 * (size_t)P.ne * (el - 1);
+        const int c[3] = {(int)(ci % P.n[0]), (int)((ci / P.n[0]) % P.n[1]), (int)(ci / ((int64_t)P.n[0] * P.n[1]))};
+        for (int iz = 0; iz <= p; ++iz)
+            for (int iy = 0; iy <= p; ++iy)
+                for (int ix = 0; ix <= p; ++ix) {
+                    const int I = ix + q * (iy + q * iz);
+                    const int64_t node = (p * c[0] + ix) + (int64_t)P.M[0] * ((p * c[1] + iy) + (int64_t)P.M[1] * (p * c[2] + iz));
+                    for (int a = 0; a < 3; ++a) {
+                        if (!P.mask[3 * node + a]) continue;
+                        for (int k = 0; k < 6; ++k) P.rhs_strain[(size_t)k * P.nlat + 3 * node + a] += be[(size_t)k * P.ne + 3 * I + a];
+                    }
+                }
     }
 
     // 4. traction on the top faces of active top-layer cells

@@ -100,6 +100,57 @@ def uncut() -> Geometry:
     return Geometry(GEOM_SPHERE_VOIDS, spheres=np.zeros((0, 4)), octree_depth=0)
 
 
+def splitmix_uniforms(seed: int, n: int) -> np.ndarray:
+    """n doubles in [0, 1) from the SplitMix64 stream of `seed` (vectorised, same stream as `uniform`)."""
+    k = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _MASK64) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def gaussian_random_field_voxels(seed: int, m: int = 128, corr_len: float = 0.05, solid_fraction: float = 0.25,
+                                 octree_depth: int = 3) -> Geometry:
+    """Trabecular-like voxel image on the unit cube (a synthetic stand-in for a bone micro-CT).
+
+    White noise N(0,1) on m^3 voxels (Box-Muller on SplitMix64 uniforms), smoothed
+    periodically with a Gaussian of standard deviation corr_len / sqrt(2) (so the
+    field's covariance is exp(-d^2 / (2 corr_len^2))), thresholded so that the top
+    `solid_fraction` of the values is solid, and restricted to the solid voxels that
+    are 6-connected to the face z = 0 (floating islands would only carry the
+    fictitious stiffness).  Array layout [z][y][x].
+    """
+    u = splitmix_uniforms(seed, m ** 3 + (m ** 3) % 2)
+    u1, u2 = u[0::2], u[1::2]
+    rad = np.sqrt(-2.0 * np.log(1.0 - u1))
+    noise = np.concatenate([rad * np.cos(2 * np.pi * u2), rad * np.sin(2 * np.pi * u2)])[: m ** 3].reshape(m, m, m)
+    sigma_vox = corr_len / np.sqrt(2.0) * m
+    k = np.fft.fftfreq(m)
+    g1 = np.exp(-2.0 * (np.pi * k * sigma_vox) ** 2)
+    kern = g1[:, None, None] * g1[None, :, None] * g1[None, None, :]
+    field = np.real(np.fft.ifftn(np.fft.fftn(noise) * kern))
+    thr = np.quantile(field, 1.0 - solid_fraction)
+    solid = field > thr
+    # keep the solid voxels 6-connected to z = 0 (breadth-first flood fill)
+    keep = np.zeros_like(solid)
+    frontier = np.zeros_like(solid)
+    frontier[0] = solid[0]
+    keep |= frontier
+    while frontier.any():
+        nxt = np.zeros_like(solid)
+        nxt[1:] |= frontier[:-1]
+        nxt[:-1] |= frontier[1:]
+        nxt[:, 1:] |= frontier[:, :-1]
+        nxt[:, :-1] |= frontier[:, 1:]
+        nxt[:, :, 1:] |= frontier[:, :, :-1]
+        nxt[:, :, :-1] |= frontier[:, :, 1:]
+        frontier = nxt & solid & ~keep
+        keep |= frontier
+    return Geometry(GEOM_VOXELS, voxels=keep.astype(np.uint8), octree_depth=octree_depth)
+
+
 def random_vector(seed: int, n: int) -> np.ndarray:
     """n doubles uniform in [-1, 1) from SplitMix64, vectorised (same stream as `uniform`)."""
     # Vectorised SplitMix64: state_k = seed + k * gamma (mod 2^64), k = 1..n.
@@ -157,4 +208,15 @@ WORKLOADS = {
     "porous40_64_p2": lambda: workload_porous(12, 64, 2, 40, 1e-10, 3, 1e-8),
     # ~0.35M DOFs: the 32^3 family at 16^3 cells (profiling-sized: ~1.5 GB of block factors)
     "porous40_16_p3": lambda: workload_porous(11, 16, 3, 40, 1e-10, 4, 1e-8),
+    # trabecular-like voxel domain (Gaussian random field, volume fraction 0.25), 48^3 cells, p=3, 6 strain loads
+    "trabecular_48_p3": lambda: workload_trabecular(13, 48, 3),
+    # the same family at 24^3 cells (test-sized)
+    "trabecular_24_p3": lambda: workload_trabecular(13, 24, 3),
 }
+
+
+def workload_trabecular(seed: int = 13, n: int = 48, p: int = 3, alpha: float = 1e-10, depth: int = 3,
+                        tol: float = 1e-8) -> Workload:
+    """Gaussian-random-field voxel domain (128^3 voxels, correlation length 0.05, solid fraction 0.25)."""
+    geo = gaussian_random_field_voxels(seed, 128, 0.05, 0.25, octree_depth=depth)
+    return Workload(f"trabecular_{n}^3_p{p}", (n, n, n), p, alpha, geo, tol)

@@ -191,3 +191,28 @@ def test_mixed_precision_porous_8_cells(porous8):
     u, its, rel, st = s.pcg_solve(s.rhs(), w.tol, 5000)
     assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
     s.close()
+
+
+def test_unit_strain_loads_match_oracle(single):
+    w, P, s = single
+    for k in range(1, 7):
+        b = s.rhs(k).cpu().numpy()
+        ref = P.load(k)
+        assert np.abs(b[P.free_lat] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_multi_rhs_solve_matches_separate_solves(single):
+    # six unit-strain load cases in one call: the recurrences share every Schwarz launch
+    w, P, s = single
+    B = torch.cat([s.rhs(k) for k in range(1, 7)])
+    U, its, rel, st = s.pcg_solve(B, 1e-10, 3000)
+    K = P.csr().toarray()
+    its_each = []
+    for k in range(6):
+        u1, i1, r1, _ = s.pcg_solve(s.rhs(k + 1), 1e-10, 3000)
+        its_each.append(i1)
+        uk = U[k * s.n:(k + 1) * s.n]
+        assert torch.allclose(uk, u1, rtol=0, atol=1e-12 * float(u1.abs().max()))
+        x_dense = np.linalg.solve(K, P.load(k + 1))
+        assert P.energy_error(x_dense, uk.cpu().numpy()[P.free_lat]) < 1e-8
+    assert its == max(its_each) and rel <= 1e-10

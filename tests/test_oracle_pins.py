@@ -382,3 +382,26 @@ def test_jacobi_degrades_with_small_cuts_schwarz_stays_bounded():
     assert its[0.03, 2] > 3 * its[0.3, 2]
     assert its[0.03, 0] <= 1.2 * its[0.3, 0] + 2
     assert its[0.03, 0] * 20 < its[0.03, 2]
+
+
+def test_unit_strain_loads_equal_minus_K_times_the_linear_field():
+    # b_k(v) = -int alpha eps(v):C:E_k, and the linear field u = E_k x has eps(u) = E_k everywhere, so
+    # b_k = -K u_k exactly (u_k = vertex interpolation of E_k x, bubbles 0), for any geometry and alpha.
+    g = I.random_sphere_voids(5, 5, 0.15, 0.3, octree_depth=2)
+    w = I.Workload("strain", (3, 2, 3), 2, 1e-3, g, 1e-8, bc=-1, hi=(0.9, 0.5, 0.8))
+    d, keep = O.desc_for(w)
+    P = O.Problem(d, keep)
+    K = P.csr()
+    isv, X, comp = _vertex_coords(P, d)
+    voigt = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    for k, (i, j) in enumerate(voigt):
+        E = np.zeros((3, 3))
+        if i == j:
+            E[i, i] = 1.0
+        else:
+            E[i, j] = E[j, i] = 0.5          # engineering shear strain 1
+        U = X @ E.T                          # u(X) = E X
+        u = np.where(isv, U[np.arange(len(comp)), comp], 0.0)
+        b = P.load(k + 1)
+        assert np.abs(b + K @ u).max() < 1e-12 * np.abs(b).max()
+        assert np.abs(b).max() > 0
