@@ -237,16 +237,32 @@ fcm_status fcm_coarse_restrict(fcm_ctx *ctx, const double *v_dev, float s, int e
  * DOFs get 0. */
 fcm_status fcm_coarse_prolong(fcm_ctx *ctx, const float *cells_dev, double s, double *y_dev);
 
-/* Flexible PCG (Notay's FCG(1): beta = -(z.Kp)/(p.Kp), alpha = (p.r)/(p.Kp)) with the
- * nonlinear preconditioner z = S r + gamma sigma P N(R r / sigma, eta), N the U-Net,
- * sigma the RMS of R r.  Convergence is judged by the plain Schwarz residual
- * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the judged residual grows 100-fold over
- * its best value, has not halved within 100 iterations, or a scalar breaks down, the
- * solve falls back to plain Schwarz-PCG on the remaining residual, from the current
- * iterate (fcm_last_solve reports it).  iterations counts K applications of both
- * phases.  gamma scales the network output (gamma = 0 gives plain flexible CG). */
-fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, const double *rhs_dev, double tol, int maxit,
-                          double *u_dev, int *iterations, double *final_relres);
+/* Galerkin coarse operator on the cell grid: y_cells = K_H x_cells with
+ * K_H = P^T K P (P as in fcm_coarse_prolong, K the FCM stiffness of Sec. 2).
+ * Cell vectors are 3 * n_cells floats, component-major (a * n_cells + cell).
+ * K_H is assembled on the first call by probing K with 375 coloured cell
+ * vectors (each cell couples with the cells of its 5x5x5 neighbourhood) and
+ * is kept in FP32 on the context (n_cells * 125 * 9 floats).  Returns
+ * FCM_ENOMEM if it does not fit. */
+fcm_status fcm_coarse_apply(fcm_ctx *ctx, const float *x_cells_dev, float *y_cells_dev);
+
+/* Flexible PCG with a coarse correction: z = S r + P y, S the Additive-Schwarz
+ * operator (Eq. (5)) and y an approximation of K_H^-1 R r.  y starts from the
+ * U-Net's prediction gamma sigma N(R r / sigma, eta) (sigma the RMS of R r;
+ * zero when net is NULL) and is refined by coarse_iters steps of block-Jacobi
+ * CG on K_H (coarse_iters = 0: the prediction alone; net == NULL needs
+ * coarse_iters >= 1).  Since z depends nonlinearly on r, every new direction
+ * is K-orthogonalised against the previous four (truncated flexible CG,
+ * FCG(4), Notay 2000).  Convergence is judged by the plain Schwarz residual
+ * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the judged residual grows
+ * 100-fold over its best value, has not halved within 100 iterations, or a
+ * scalar breaks down, the solve falls back to plain Schwarz-PCG on the
+ * remaining residual, from the current iterate (fcm_last_solve reports it).
+ * iterations counts K applications of both phases on the fine lattice.
+ * Returns FCM_EINVAL on bad arguments, FCM_ESTATE before fcm_precond_build,
+ * FCM_ENOTCONV when maxit is reached. */
+fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, int coarse_iters, const double *rhs_dev,
+                          double tol, int maxit, double *u_dev, int *iterations, double *final_relres);
 
 /* Largest n_lattice that fcm_apply_S_noalloc accepts (8 MiB of FP64 scratch). */
 #define FCM_NOALLOC_MAX_LATTICE 1048576

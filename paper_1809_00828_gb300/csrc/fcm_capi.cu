@@ -173,6 +173,7 @@ void free_ctx(fcm_ctx *C)
     if (C->d_m) cudaFree(C->d_m);
     if (C->d_ms) cudaFree(C->d_ms);
     if (C->h_ms) cudaFreeHost(C->h_ms);
+    fcm::coarse_free(C->coarse);
     cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1};
     for (auto e : evs)
         if (e) cudaEventDestroy(e);

@@ -184,7 +184,7 @@ namespace {
 
 struct CoarseWs {
     double *z = nullptr, *c = nullptr, *red = nullptr;
-    float *cin = nullptr, *cout = nullptr;
+    float *cin = nullptr, *cout = nullptr, *f = nullptr;
 };
 
 #define CO_CUDA(C, call)                                                                        \
@@ -204,28 +204,38 @@ fcm_status dot2(fcm_ctx *C, const double *a, const double *b, const double *c, c
     return FCM_OK;
 }
 
-// c = gamma sigma P N(R r / sigma, eta); returns FCM_OK and c = 0 when R r = 0
-fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, const double *r, CoarseWs &ws, double *c)
+// c = P y with y ~ K_H^-1 R r: the initial guess is gamma sigma N(R r / sigma, eta) (zero without a
+// network), refined by `iters` coarse CG steps (iters = 0: the network's prediction alone).
+fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, int iters, const double *r, CoarseWs &ws,
+                             double *c)
 {
     const int64_t ncell = C->hp.ncells;
-    restrict_kernel<<<nblk(ncell), 256, 0, C->stream>>>(r, C->d_mask, C->d_eta, ws.cin, C->g, C->p, 1.0f, 1, ncell);
-    sumsq_kernel<<<1, RT, 0, C->stream>>>(ws.cin, 3 * ncell, ws.red);
-    double ss = 0.0;
-    CO_CUDA(C, cudaMemcpyAsync(&ss, ws.red, sizeof(double), cudaMemcpyDeviceToHost, C->stream));
-    CO_CUDA(C, cudaStreamSynchronize(C->stream));
-    const double sigma = std::sqrt(ss / (3.0 * ncell));
-    if (!(sigma > 0.0) || !std::isfinite(sigma)) {
-        CO_CUDA(C, cudaMemsetAsync(c, 0, sizeof(double) * C->nlat, C->stream));
-        return FCM_OK;
+    cudaStream_t st = C->stream;
+    restrict_kernel<<<nblk(ncell), 256, 0, st>>>(r, C->d_mask, C->d_eta, ws.cin, C->g, C->p, 1.0f, 1, ncell);
+    if (net) {
+        sumsq_kernel<<<1, RT, 0, st>>>(ws.cin, 3 * ncell, ws.red);
+        double ss = 0.0;
+        CO_CUDA(C, cudaMemcpyAsync(&ss, ws.red, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CO_CUDA(C, cudaStreamSynchronize(st));
+        const double sigma = std::sqrt(ss / (3.0 * ncell));
+        if (!(sigma > 0.0) || !std::isfinite(sigma)) {
+            CO_CUDA(C, cudaMemsetAsync(c, 0, sizeof(double) * C->nlat, st));
+            return FCM_OK;
+        }
+        CO_CUDA(C, cudaMemcpyAsync(ws.f, ws.cin, sizeof(float) * 3 * ncell, cudaMemcpyDeviceToDevice, st));
+        scale_f_kernel<<<nblk(3 * ncell), 256, 0, st>>>(ws.cin, 3 * ncell, (float)(1.0 / sigma));
+        fcm_status s = fcm_unet_forward(net, ws.cin, 1, C->g.n[0], C->g.n[1], C->g.n[2], ws.cout);
+        if (s != FCM_OK) {
+            C->err = "fcm_fpcg_solve: " + fcm_unet_last_error();
+            return s;
+        }
+        scale_f_kernel<<<nblk(3 * ncell), 256, 0, st>>>(ws.cout, 3 * ncell, (float)(gamma * sigma));
+    } else {
+        CO_CUDA(C, cudaMemcpyAsync(ws.f, ws.cin, sizeof(float) * 3 * ncell, cudaMemcpyDeviceToDevice, st));
+        CO_CUDA(C, cudaMemsetAsync(ws.cout, 0, sizeof(float) * 3 * ncell, st));
     }
-    scale_f_kernel<<<nblk(3 * ncell), 256, 0, C->stream>>>(ws.cin, 3 * ncell, (float)(1.0 / sigma));
-    fcm_status st = fcm_unet_forward(net, ws.cin, 1, C->g.n[0], C->g.n[1], C->g.n[2], ws.cout);
-    if (st != FCM_OK) {
-        C->err = "fcm_fpcg_solve: " + fcm_unet_last_error();
-        return st;
-    }
-    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, C->stream>>>(ws.cout, C->d_mask, c, C->g, C->p, gamma * sigma, nullptr,
-                                                            C->nlat / 3);
+    if (iters > 0) coarse_solve(C, ws.f, ws.cout, iters);
+    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, st>>>(ws.cout, C->d_mask, c, C->g, C->p, 1.0, nullptr, C->nlat / 3);
     CO_CUDA(C, cudaGetLastError());
     return FCM_OK;
 }
@@ -259,10 +269,12 @@ fcm_status fcm_coarse_prolong(fcm_ctx *C, const float *cells, double s, double *
     return FCM_OK;
 }
 
-fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double *rhs, double tol, int maxit, double *u,
+fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_iters, const double *rhs, double tol,
+                          int maxit, double *u,
                           int *iterations, double *final_relres)
 {
-    if (!C || !net || !rhs || !u || !(tol > 0.0) || maxit < 1 || !std::isfinite(gamma)) {
+    if (!C || !rhs || !u || !(tol > 0.0) || maxit < 1 || !std::isfinite(gamma) || coarse_iters < 0 ||
+        (!net && coarse_iters == 0)) {
         if (C) C->err = "fcm_fpcg_solve: invalid argument";
         return FCM_EINVAL;
     }
@@ -284,6 +296,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double 
             cudaFree(w.red);
             cudaFree(w.cin);
             cudaFree(w.cout);
+            cudaFree(w.f);
         }
     } freer{ws};
     CO_CUDA(C, cudaMalloc(&ws.z, sizeof(double) * n));
@@ -291,12 +304,20 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double 
     CO_CUDA(C, cudaMalloc(&ws.red, sizeof(double) * 2));
     CO_CUDA(C, cudaMalloc(&ws.cin, sizeof(float) * 4 * ncell));
     CO_CUDA(C, cudaMalloc(&ws.cout, sizeof(float) * 3 * ncell));
+    CO_CUDA(C, cudaMalloc(&ws.f, sizeof(float) * 3 * ncell));
+    if (coarse_iters > 0) {
+        fcm_status se = coarse_ensure(C);
+        if (se != FCM_OK) return se;
+    }
     // the network runs on the solver's stream for the duration of the solve
     struct Restore {
         fcm_unet *n;
         cudaStream_t s;
-        ~Restore() { unet_set_stream(n, s); }
-    } restore{net, unet_set_stream(net, st)};
+        ~Restore()
+        {
+            if (n) unet_set_stream(n, s);
+        }
+    } restore{net, net ? unet_set_stream(net, st) : nullptr};
 
     cudaEventRecord(C->ev_t0, st);
     double *x = C->d_x, *r = C->d_r, *zS = C->d_z, *p = C->d_p, *q = C->d_q, *b = C->d_b;
@@ -338,7 +359,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double 
         extra.push_back(Q[k]);
     }
     if (!converged) {
-        if ((s = coarse_correction(C, net, gamma, r, ws, ws.c)) != FCM_OK) return s;
+        if ((s = coarse_correction(C, net, gamma, coarse_iters, r, ws, ws.c)) != FCM_OK) return s;
         add_kernel<<<nblk(n), 256, 0, st>>>(P[0], zS, ws.c, n);
         rel = 1.0;
     }
@@ -377,7 +398,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, const double 
             fallback = true;
             break;
         }
-        if ((s = coarse_correction(C, net, gamma, r, ws, ws.c)) != FCM_OK) return s;
+        if ((s = coarse_correction(C, net, gamma, coarse_iters, r, ws, ws.c)) != FCM_OK) return s;
         add_kernel<<<nblk(n), 256, 0, st>>>(ws.z, zS, ws.c, n);
         // p_new = z - sum_j (z.q_j / p_j.q_j) p_j over the last min(it, kTrunc) directions
         const int nxt = it % kRing;

@@ -97,6 +97,13 @@ fcm_status ctx_solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, d
 // fcm_unet.cu: redirect a network's launches to stream s; returns the previous stream
 cudaStream_t unet_set_stream(fcm_unet *N, cudaStream_t s);
 
+// fcm_coarse_op.cu: Galerkin coarse operator K_H = P^T K P on the cell grid
+struct CoarseOp;
+fcm_status coarse_ensure(fcm_ctx *C);
+void coarse_free(CoarseOp *op);
+void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters);
+void coarse_apply(fcm_ctx *C, const float *x, float *y);
+
 }  // namespace fcm
 
 std::string &fcm_unet_last_error();
@@ -149,4 +156,6 @@ struct fcm_ctx {
     double *d_m = nullptr;
     fcm::CgScalars *d_ms = nullptr, *h_ms = nullptr;
     int m_nr = 0;
+    // coarse operator of the learned correction (built on first use)
+    fcm::CoarseOp *coarse = nullptr;
 };

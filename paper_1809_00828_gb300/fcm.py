@@ -24,7 +24,7 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy",
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
-            "fcm_coarse_prolong", "fcm_fpcg_solve")
+            "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -247,10 +247,11 @@ def _bind_unet(L):
     L.fcm_unet_destroy.restype = None
     L.fcm_coarse_restrict.argtypes = [P, P, ctypes.c_float, ctypes.c_int, P]
     L.fcm_coarse_prolong.argtypes = [P, P, ctypes.c_double, P]
-    L.fcm_fpcg_solve.argtypes = [P, P, ctypes.c_double, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
+    L.fcm_coarse_apply.argtypes = [P, P, P]
+    L.fcm_fpcg_solve.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
     for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
               "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
-              "fcm_fpcg_solve"):
+              "fcm_coarse_apply", "fcm_fpcg_solve"):
         getattr(L, f).restype = ctypes.c_int
     _unet_bound = True
 
@@ -341,13 +342,22 @@ def _solver_coarse_prolong(self, cells, s=1.0, out=None):
     return y
 
 
-def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=True):
+def _solver_coarse_apply(self, x, out=None):
+    """y = K_H x on cell vectors (3 * n_cells floats, component-major)."""
+    _bind_unet(load())
+    y = out if out is not None else self._torch.empty_like(x)
+    self._check(load().fcm_coarse_apply(self.ctx, _ptr(x), _ptr(y)))
+    return y
+
+
+def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=True, coarse_iters=0):
+    """Flexible PCG with the coarse correction; net may be None when coarse_iters >= 1."""
     _bind_unet(load())
     u = out if out is not None else self.empty()
     its = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
-    st = load().fcm_fpcg_solve(self.ctx, net.h, gamma, _ptr(b), tol, maxit, _ptr(u), ctypes.byref(its),
-                               ctypes.byref(rel))
+    st = load().fcm_fpcg_solve(self.ctx, net.h if net is not None else None, gamma, coarse_iters, _ptr(b), tol,
+                               maxit, _ptr(u), ctypes.byref(its), ctypes.byref(rel))
     if check:
         self._check(st)
     return u, its.value, rel.value, st
@@ -355,4 +365,5 @@ def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=T
 
 Solver.coarse_restrict = _solver_coarse_restrict
 Solver.coarse_prolong = _solver_coarse_prolong
+Solver.coarse_apply = _solver_coarse_apply
 Solver.fpcg_solve = _solver_fpcg_solve
