@@ -2,10 +2,20 @@
 
 A step is one complete preconditioned CG solve (x0 = 0 to ||S r|| / ||S b|| <=
 tol) of the 32^3-cell, p=3 porous cube (40 seeded spherical voids, alpha 1e-10,
-octree depth 4) with the set-up and the preconditioner built once beforehand.
+octree depth 4) with the set-up, the preconditioner and the coarse operator
+built once beforehand.  Forms:
+
+  coarse (default): flexible CG, z = S r + P y with y from `--coarse-iters`
+                    coarse CG steps on K_H = P^T K P (optionally started from a
+                    trained U-Net, `--net`), FP32 block factors (`--precision`)
+  pcg:              plain Schwarz-PCG
+
+The same run also times plain FP64 Schwarz-PCG and reports the energy-norm
+error of this form against it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcm|reference]
-                  [--workload NAME] [--precision fp64|mixed]
+                  [--workload NAME] [--form coarse|pcg] [--precision fp64|mixed]
+                  [--coarse-iters K] [--net CHECKPOINT]
 
 N > 1 runs independent replicas (one per GPU, launched by torchrun); the
 solve has no data-path collective.  `--impl reference` times the CPU oracle.
@@ -197,6 +207,36 @@ def _describe(w):
             f"unit traction on z=1, vertex-patch blocks, eps=1e-13")
 
 
+def _form(args, net):
+    if args.form == "pcg":
+        return "plain Schwarz-PCG"
+    start = "trained U-Net prediction scaled by the coarse line search" if net is not None else "zero"
+    return (f"flexible CG(4), z = S r + P y, y from {args.coarse_iters} block-Jacobi CG steps on the Galerkin "
+            f"coarse operator K_H = P^T K P starting from {start}")
+
+
+def _launches_per_solve(args, its, net):
+    """Kernels of one solve (device-side loop, so the count follows the iterations)."""
+    k_apply = 1 + 2 * 8        # zero q, uncut and cut launches of the 8 colours
+    s_apply = 1 + 8            # zero z, one launch per colour
+    if args.form == "pcg":
+        graphs = -(-its // 8)
+        return 4 + s_apply + 1 + graphs * 8 * (k_apply + 2 + s_apply + 2) + k_apply + 1
+    k = args.coarse_iters
+    coarse = 1 + (1 + 2 * k) + 1                        # restrict, coarse start + 2 per step, prolong
+    if net is not None:
+        coarse += 2 + 1 + 2 + _unet_launches(net)       # sigma, prep, post, start apply + line search
+    per_it = k_apply + 2 + s_apply + 1 + coarse + 2    # pq, xr, conv, dots, newp
+    graphs = -(-its // 4)
+    return 1 + s_apply + 1 + coarse + 1 + graphs * 4 * per_it + k_apply + 3
+
+
+def _unet_launches(net):
+    L = net.desc[3]
+    # per level: pool (l > 0), 2 x (conv, relu); per decoder level: up, copy, 2 x (conv, relu); output conv
+    return (L - 1) + 4 * L + 6 * (L - 1) + 1
+
+
 def run_fcm(args, rank, world, local_rank):
     import torch
     from paper_1809_00828_gb300 import fcm
@@ -209,12 +249,24 @@ def run_fcm(args, rank, world, local_rank):
     w = _workload(args.workload)
     s = fcm.Solver(w)
     s.precond_build(precision=args.precision)
-    info = s.info
     b = s.rhs()
     u = s.empty()
     stream = torch.cuda.current_stream()
+    net, gamma = None, 0.0
+    if args.form == "coarse" and args.net:
+        from paper_1809_00828_gb300 import learned
+        net, gamma = learned.load(args.net)
+
+    def solve(out):
+        if args.form == "coarse":
+            _, its, rel, _ = s.fpcg_solve(net, gamma, b, w.tol, args.maxit, out=out, coarse_iters=args.coarse_iters)
+        else:
+            _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=out)
+        return its, rel
+
     for _ in range(args.warmup):
-        _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=u)
+        its, rel = solve(u)
+    info = s.get_info()
     clocks = ClockSampler(local_rank)
     clocks.start()
     if dist:
@@ -226,7 +278,7 @@ def run_fcm(args, rank, world, local_rank):
     per = []
     iters = []
     for _ in range(args.steps):
-        _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=u)
+        its, rel = solve(u)
         li = s.last_solve()
         per.append(li["seconds"])
         iters.append(its)
@@ -289,6 +341,25 @@ def run_fcm(args, rank, world, local_rank):
                     "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": kernel,
                     "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "fp64_tflops_equivalent": achieved_tf, "fp64_peak_tflops": fp64_peak}
+    if args.form == "coarse":
+        # the coarse operator apply (one kh_kernel launch), timed live; algorithmic bytes: the
+        # stored half of K_H once plus the input and output cell vectors
+        nc = w.n[0] * w.n[1] * w.n[2]
+        xc = torch.ones(3 * nc, dtype=torch.float32, device="cuda")
+        yc = torch.empty_like(xc)
+        for _ in range(3):
+            s.coarse_apply(xc, out=yc)
+        e0.record(stream)
+        for _ in range(reps):
+            s.coarse_apply(xc, out=yc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_h = e0.elapsed_time(e1) / 1e3 / reps
+        kh_bytes = nc * (63 * 9 * 4 + 2 * 3 * 4)
+        roofline.update({"kh_apply_us": t_h * 1e6, "kh_algorithmic_bytes": kh_bytes,
+                         "kh_achieved_gbs": kh_bytes / t_h / 1e9,
+                         "kh_note": "K_H (74 MB at 32^3 cells) stays in L2 (129 MB) across a coarse solve, "
+                                    "so this rate can exceed the HBM copy peak"})
     roofline.update({"s_apply_ms": t_s * 1e3, "k_apply_ms": t_k * 1e3,
                      "k_apply_fp64_tflops": 2.0 * info["kapply_fmas"] / t_k / 1e12,
                      "k_apply_fp64_frac": 2.0 * info["kapply_fmas"] / t_k / 1e12 / fp64_peak,
@@ -300,41 +371,58 @@ def run_fcm(args, rank, world, local_rank):
     u_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
     bh = b_host.numpy()
     uh = u_host.numpy()
-    s.pcg_solve_host(bh, w.tol, args.maxit, out=uh)
+    def solve_host():
+        if args.form == "coarse":
+            s.fpcg_solve_host(net, gamma, bh, w.tol, args.maxit, out=uh, coarse_iters=args.coarse_iters)
+        else:
+            s.pcg_solve_host(bh, w.tol, args.maxit, out=uh)
+
+    solve_host()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
-        s.pcg_solve_host(bh, w.tol, args.maxit, out=uh)
+        solve_host()
     e2e = (time.perf_counter() - t0) / e2e_steps
 
     its_med = int(statistics.median(iters))
-    graph_launches = -(-its_med // 8)
-    # per iteration: zero q, 8 x (uncut + cut K kernels), pq, xr, zero z, 8 Schwarz colours, rz, p
-    launches_per_solve = 13 + 18 + graph_launches * 8 * (1 + 16 + 2 + 1 + 8 + 2)
+    launches_per_solve = _launches_per_solve(args, its_med, net)
     line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-            "config": {"workload": _describe(w), "precision": args.precision, "n_free": info["n_free"],
+            "config": {"workload": _describe(w), "form": _form(args, net), "precision": args.precision,
+                       "n_free": info["n_free"],
                        "iterations": its_med, "relres": rel, "true_relres": last["true_relres"],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"inputs larger than L2: factor pool {info['factor_bytes'] / 2**30:.2f} GiB, "
                              f"element matrices {info['element_bytes'] / 2**30:.2f} GiB",
                        "n_blocks": info["n_blocks"], "n_factors": info["n_factors"],
                        "setup_s": info["setup_seconds"], "precond_s": info["precond_seconds"],
+                       "coarse_operator_s": info["coarse_seconds"],
                        "device_seconds_median": statistics.median(per)},
             "roofline": roofline,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
             "gpu_launches": launches_per_solve * args.steps,
             "clocks": clk}
-    if args.precision != "fp64":
-        # the plain FP64 Schwarz-PCG on the same GPU: its time-to-solution for the comparison the
-        # metric names, and the relative energy-norm error (Eq. (15)) of this form against it
+    its64 = its_med
+    if args.form != "pcg" or args.precision != "fp64":
+        # plain Schwarz-PCG on the same GPU (mixed factors, then FP64 factors): their times-to-solution
+        # for the comparison the metric names, and the relative energy-norm error (Eq. (15)) of this
+        # form against the plain FP64 solve
         x = u.clone()
+        nrep = max(1, min(args.steps, 3))
+        if args.form != "pcg" and args.precision == "mixed":
+            s.pcg_solve(b, w.tol, args.maxit)
+            tm = []
+            for _ in range(nrep):
+                _, itsm, _, _ = s.pcg_solve(b, w.tol, args.maxit)
+                tm.append(s.last_solve()["seconds"])
+            line["config"]["plain_mixed"] = {"seconds": statistics.median(tm), "iterations": itsm,
+                                             "speedup_of_this_form": statistics.median(tm) / (ms_per_step / 1e3)}
         s.precond_build(precision="fp64")
         x64, its64, _, _ = s.pcg_solve(b, w.tol, args.maxit)
         t64 = []
-        for _ in range(max(1, min(args.steps, 3))):
+        for _ in range(nrep):
             s.pcg_solve(b, w.tol, args.maxit, out=x64)
             t64.append(s.last_solve()["seconds"])
         e = x - x64
@@ -344,10 +432,13 @@ def run_fcm(args, rank, world, local_rank):
         line["config"]["plain_fp64"] = {"seconds": statistics.median(t64), "iterations": its64,
                                         "speedup_of_this_form": statistics.median(t64) / (ms_per_step / 1e3)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle runs plain FP64 Schwarz-PCG: scaled to that method's iteration count
         kf = info["n_cells_active"] * (3 * (w.p + 1) ** 3) ** 2
         sf = info["sapply_fmas"]
-        v, sample, _ = oracle_sample(w, its_med, sf, kf)
+        v, sample, _ = oracle_sample(w, its64, sf, kf)
         line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+    if net is not None:
+        net.close()
     s.close()
     if rank == 0:
         print(json.dumps(line))
@@ -365,6 +456,10 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="mixed: FP32 block factors (FP64 for cond > 1e7), compared with plain FP64 in the same run")
+    ap.add_argument("--form", default="coarse", choices=["coarse", "pcg"],
+                    help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
+    ap.add_argument("--coarse-iters", type=int, default=20)
+    ap.add_argument("--net", default=None, help="U-Net checkpoint whose prediction starts the coarse solve")
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--ref-iterations", type=int, default=None,
                     help="iteration count used to scale the reference arm (default: a GPU-free estimate)")

@@ -107,6 +107,7 @@ typedef struct {
     int64_t kapply_fmas;      /* multiply-adds of one K apply (sum over active cells)  */
     int64_t sapply_fmas;      /* multiply-adds of one S apply (sum of block box sizes^2) */
     double max_block_cond;    /* largest retained condition number of a block          */
+    double coarse_seconds;    /* assembly time of the coarse operator K_H (0 until built) */
 } fcm_info_t;
 
 enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1 };
@@ -263,6 +264,12 @@ fcm_status fcm_coarse_apply(fcm_ctx *ctx, const float *x_cells_dev, float *y_cel
  * FCM_ENOTCONV when maxit is reached. */
 fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, int coarse_iters, const double *rhs_dev,
                           double tol, int maxit, double *u_dev, int *iterations, double *final_relres);
+
+/* Same as fcm_fpcg_solve with host buffers: rhs_host (n_lattice doubles) is
+ * copied to the device, solved, and the solution copied back into u_host
+ * before returning (pinned host memory makes the copies asynchronous DMA). */
+fcm_status fcm_fpcg_solve_host(fcm_ctx *ctx, fcm_unet *net, double gamma, int coarse_iters, const double *rhs_host,
+                               double tol, int maxit, double *u_host, int *iterations, double *final_relres);
 
 /* Largest n_lattice that fcm_apply_S_noalloc accepts (8 MiB of FP64 scratch). */
 #define FCM_NOALLOC_MAX_LATTICE 1048576

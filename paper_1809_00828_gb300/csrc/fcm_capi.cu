@@ -173,6 +173,7 @@ void free_ctx(fcm_ctx *C)
     if (C->d_m) cudaFree(C->d_m);
     if (C->d_ms) cudaFree(C->d_ms);
     if (C->h_ms) cudaFreeHost(C->h_ms);
+    fcm::fcg_free(C->fcg);
     fcm::coarse_free(C->coarse);
     cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1};
     for (auto e : evs)
@@ -189,6 +190,8 @@ std::string &fcm_unet_last_error() { return g_setup_error; }
 namespace fcm {
 void ctx_apply_K(fcm_ctx *C, const double *x, double *y) { apply_K_dev(C, x, y, nullptr); }
 void ctx_apply_S(fcm_ctx *C, const double *r, double *z) { apply_S_dev(C, r, z, nullptr); }
+void ctx_apply_K_flag(fcm_ctx *C, const double *x, double *y, const int *stop) { apply_K_dev(C, x, y, stop); }
+void ctx_apply_S_flag(fcm_ctx *C, const double *r, double *z, const int *stop) { apply_S_dev(C, r, z, stop); }
 fcm_status ctx_solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, double *u, fcm_solve_info &info)
 {
     return solve_one(C, rhs, tol, maxit, u, info);
@@ -343,6 +346,7 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     }
     out->sapply_fmas = C->sapply_fmas;
     out->max_block_cond = C->max_cond;
+    out->coarse_seconds = fcm::coarse_seconds(C->coarse);
     return FCM_OK;
 }
 

@@ -1,35 +1,97 @@
 // Coarse transfer between lattice DOFs and the cell grid, and the flexible
-// PCG that uses the learned coarse correction.
+// PCG that uses the coarse correction.
 //
 // R (restriction): cell value = mean of the vector at the 8 vertex nodes of
 // the cell, per component.  P (prolongation) = R^T: a free vertex DOF
 // receives 1/8 of the sum of the values of the cells that contain the vertex;
 // higher-order DOFs receive nothing.
 //
-// The preconditioner of the flexible PCG is z = S r + gamma sigma P N(R r /
-// sigma, eta), with S the Additive-Schwarz operator (Sec. 3.1 Eq. (5)) and N
-// the U-Net.  Because N is nonlinear, each new search direction is
+// The preconditioner of the flexible PCG is z = S r + P y, with S the
+// Additive-Schwarz operator (Sec. 3.1 Eq. (5)) and y an approximation of
+// K_H^-1 R r (K_H = P^T K P): the U-Net's prediction gamma sigma N(R r / sigma,
+// eta) (sigma the RMS of R r), scaled by the coarse energy-minimising step,
+// refined by a few coarse CG steps (or those steps from zero without a
+// network).  z depends nonlinearly on r, so each new search direction is
 // K-orthogonalised explicitly against the last four (truncated flexible CG,
-// Notay, SIAM J. Sci. Comput. 22, 2000).  Convergence is judged on ||S r|| / ||S b|| (Sec. 5 Eq. (14))
-// with the plain Schwarz part, so the judge is the same as for plain PCG.
+// FCG(4), Notay, SIAM J. Sci. Comput. 22, 2000).  Convergence is judged on
+// ||S r|| / ||S b|| (Sec. 5 Eq. (14)) with the plain Schwarz part, so the
+// judge is the same as for plain PCG.
+//
+// The iteration runs on the device: every scalar (alpha, the
+// orthogonalisation coefficients, the convergence and stall tests) is
+// computed by the last CTA of a deterministic two-level reduction, and every
+// kernel returns at once when the device flag `stop` is set.  Four
+// iterations are captured in one CUDA graph, kept on the context between
+// solves; the host polls the flag once per graph launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <cstring>
 #include <string>
 #include <vector>
 
 #include "fcm_device.cuh"
 
-
 namespace fcm {
+
+constexpr int kM = 4;          // FCG(m): directions kept for the explicit K-orthogonalisation
+constexpr int kFcgChunk = 4;   // iterations per captured graph
+constexpr int kStallWindow = 100;
+
+struct FcgScalars {
+    double pq[kM];     // p_j . K p_j, by ring slot
+    double beta[kM];   // z . K p_j / pq_j for the j-th previous direction
+    double alpha, judge0, rel, best, mark, tol, sigma;
+    int it, maxit, mark_it, window, stop, status, fallback, pad;
+};
+
+struct FcgState {
+    int64_t n = 0, ncell = 0;
+    double *ring = nullptr;      // kM direction slots P, then kM slots Q = K P
+    double *c = nullptr;         // P y on the lattice
+    double *partial = nullptr;   // kM partials per CTA
+    unsigned *counter = nullptr;
+    float *cin = nullptr, *cout = nullptr, *f = nullptr;
+    FcgScalars *d = nullptr, *h = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    // what the graph was captured for
+    uint64_t net_serial = 0, net_gen = 0;
+    const fcm_unet *net = nullptr;
+    double gamma = 0.0;
+    int coarse_iters = -1;
+};
+
+// device address of the stop flag
+const int *stop_flag(const FcgState *F)
+{
+    return reinterpret_cast<const int *>(reinterpret_cast<const char *>(F->d) + offsetof(FcgScalars, stop));
+}
+
+void fcg_free(FcgState *F)
+{
+    if (!F) return;
+    if (F->graph) cudaGraphExecDestroy(F->graph);
+    void *ps[] = {F->ring, F->c, F->partial, F->counter, F->cin, F->cout, F->f, F->d};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    if (F->h) cudaFreeHost(F->h);
+    delete F;
+}
+
 namespace {
 
 constexpr int RT = 256;
 
+#define STOP_RETURN \
+    if (stop && *stop) return
+
 __global__ void restrict_kernel(const double *__restrict__ v, const uint8_t *__restrict__ mask, const float *__restrict__ eta,
-                                float *__restrict__ out, Grid3 g, int p, float s, int with_eta, int64_t ncell)
+                                float *__restrict__ out, Grid3 g, int p, float s, int with_eta, int64_t ncell,
+                                const int *stop)
 {
+    STOP_RETURN;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
         const int cx = (int)(c % g.n[0]), cy = (int)((c / g.n[0]) % g.n[1]), cz = (int)(c / ((int64_t)g.n[0] * g.n[1]));
         double acc[3] = {0.0, 0.0, 0.0};
@@ -44,11 +106,11 @@ __global__ void restrict_kernel(const double *__restrict__ v, const uint8_t *__r
     }
 }
 
-// y = s * P cells (scale s from host, or from *s_dev when non-null)
+// y = s * P cells
 __global__ void prolong_kernel(const float *__restrict__ cells, const uint8_t *__restrict__ mask, double *__restrict__ y,
-                               Grid3 g, int p, double s, const double *__restrict__ s_dev, int64_t nnode)
+                               Grid3 g, int p, double s, int64_t nnode, const int *stop)
 {
-    const double sc = s_dev ? *s_dev : s;
+    STOP_RETURN;
     const int64_t ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nnode;
          node += (int64_t)gridDim.x * blockDim.x) {
@@ -63,7 +125,7 @@ __global__ void prolong_kernel(const float *__restrict__ cells, const uint8_t *_
                 for (int a = 0; a < 3; ++a) acc[a] += cells[a * ncell + c];
             }
         }
-        for (int a = 0; a < 3; ++a) y[3 * node + a] = mask[3 * node + a] ? 0.125 * sc * acc[a] : 0.0;
+        for (int a = 0; a < 3; ++a) y[3 * node + a] = mask[3 * node + a] ? 0.125 * s * acc[a] : 0.0;
     }
 }
 
@@ -74,6 +136,7 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Sum over the CTA; valid in thread 0.
 __device__ double block_sum(double v, double *sh)
 {
     v = warp_sum(v);
@@ -85,86 +148,237 @@ __device__ double block_sum(double v, double *sh)
     return v;
 }
 
-// out[0] = a.b, out[1] = c.d (c may be null); deterministic two-level reduction.
-__global__ void __launch_bounds__(RT) dot2_kernel(const double *a, const double *b, const double *c, const double *d,
-                                                   int64_t n, double *partial, unsigned *counter, double *out)
+// K sums over the grid in a fixed order: every CTA publishes its partials, the last CTA
+// to arrive adds them up (thread 0 then holds the totals) and returns true.
+template <int K>
+__device__ bool grid_sums(double (&v)[K], double *partial, unsigned *counter)
 {
     __shared__ double sh[RT / 32];
     __shared__ bool last;
-    double x = 0.0, y = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
-        x = fma(a[i], b[i], x);
-        if (c) y = fma(c[i], d[i], y);
-    }
-    x = block_sum(x, sh);
-    y = block_sum(y, sh);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = block_sum(v[k], sh);
     if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = x;
-        partial[2 * blockIdx.x + 1] = y;
+#pragma unroll
+        for (int k = 0; k < K; ++k) partial[K * blockIdx.x + k] = v[k];
         __threadfence();
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
-    x = 0.0;
-    y = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += RT) {
-        x += __ldcg(partial + 2 * i);
-        y += __ldcg(partial + 2 * i + 1);
+    if (!last) return false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += RT) x += __ldcg(partial + K * i + k);
+        v[k] = block_sum(x, sh);
     }
-    x = block_sum(x, sh);
-    y = block_sum(y, sh);
-    if (threadIdx.x == 0) {
-        out[0] = x;
-        out[1] = y;
-        *counter = 0u;
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// judge0 = ||S b||; resets the iteration state
+__global__ void __launch_bounds__(RT) fk_first_kernel(const double *zS, int64_t n, double *partial, unsigned *counter,
+                                                       FcgScalars *F)
+{
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) v[0] = fma(zS[i], zS[i], v[0]);
+    if (!grid_sums<1>(v, partial, counter) || threadIdx.x) return;
+    const double j0 = sqrt(v[0]);
+    F->judge0 = j0;
+    F->it = 0;
+    F->rel = 1.0;
+    F->best = 1.0;
+    F->mark = 1.0;
+    F->mark_it = 0;
+    F->fallback = 0;
+    F->status = FCM_OK;
+    F->stop = 0;
+    F->sigma = 0.0;
+    if (!isfinite(j0)) {
+        F->status = FCM_EBREAKDOWN;
+        F->stop = 1;
+    } else if (j0 == 0.0) {
+        F->rel = 0.0;
+        F->stop = 1;
     }
 }
 
-// sum of squares of a float array into out[0] (single block, fixed order)
-__global__ void __launch_bounds__(RT) sumsq_kernel(const float *a, int64_t n, double *out)
+// pq = p.q, alpha = p.r / pq; stores p and q in the ring slot of this iteration
+__global__ void __launch_bounds__(RT) fk_pq_kernel(const double *p, const double *q, const double *r, double *ring, int64_t n,
+                                                    double *partial, unsigned *counter, FcgScalars *F)
 {
-    __shared__ double sh[RT / 32];
-    double x = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += RT) x += (double)a[i] * a[i];
-    x = block_sum(x, sh);
-    if (threadIdx.x == 0) out[0] = x;
-}
-
-__global__ void scale_f_kernel(float *a, int64_t n, float s)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] *= s;
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    const int slot = F->it % kM;
+    double *Ps = ring + (int64_t)slot * n, *Qs = ring + (int64_t)(kM + slot) * n;
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        const double pi = p[i], qi = q[i];
+        v[0] = fma(pi, qi, v[0]);
+        v[1] = fma(pi, r[i], v[1]);
+        Ps[i] = pi;
+        Qs[i] = qi;
+    }
+    if (!grid_sums<2>(v, partial, counter) || threadIdx.x) return;
+    F->pq[slot] = v[0];
+    const double alpha = v[1] / v[0];
+    F->alpha = alpha;
+    if (!(v[0] > 0.0) || !isfinite(alpha)) {
+        F->fallback = 1;
+        F->stop = 1;
+    }
 }
 
 // x += alpha p, r -= alpha q
-__global__ void axpy2_kernel(double *x, double *r, const double *p, const double *q, int64_t n, double alpha)
+__global__ void __launch_bounds__(RT) fk_xr_kernel(double *x, double *r, const double *p, const double *q, int64_t n,
+                                                    const FcgScalars *F)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    const double alpha = F->alpha;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
         x[i] = fma(alpha, p[i], x[i]);
         r[i] = fma(-alpha, q[i], r[i]);
     }
+}
+
+// judged residual ||S r|| / ||S b|| (Eq. (14)); convergence, growth, stall and iteration-limit tests
+__global__ void __launch_bounds__(RT) fk_conv_kernel(const double *zS, int64_t n, double *partial, unsigned *counter,
+                                                      FcgScalars *F)
+{
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) v[0] = fma(zS[i], zS[i], v[0]);
+    if (!grid_sums<1>(v, partial, counter) || threadIdx.x) return;
+    const int it = F->it + 1;
+    F->it = it;
+    const double rel = sqrt(v[0]) / F->judge0;
+    F->rel = rel;
+    if (!isfinite(rel)) {
+        F->fallback = 1;
+        F->stop = 1;
+        return;
+    }
+    F->best = fmin(F->best, rel);
+    if (rel <= F->tol) {
+        F->status = FCM_OK;
+        F->stop = 1;
+        return;
+    }
+    if (rel <= 0.5 * F->mark) {
+        F->mark = rel;
+        F->mark_it = it;
+    }
+    // a harmful or useless correction: growth, or no halving within `window` iterations
+    if (rel > 100.0 * F->best || it - F->mark_it >= F->window) {
+        F->fallback = 1;
+        F->stop = 1;
+    } else if (it >= F->maxit) {
+        F->status = FCM_ENOTCONV;
+        F->stop = 1;
+    }
+}
+
+// beta_j = (zS + c) . q_j / pq_j over the last min(it, kM) directions
+__global__ void __launch_bounds__(RT) fk_dots_kernel(const double *zS, const double *c, const double *ring, int64_t n,
+                                                      double *partial, unsigned *counter, FcgScalars *F)
+{
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    const int it = F->it, np = min(it, kM);
+    const double *Q[kM];
+#pragma unroll
+    for (int j = 0; j < kM; ++j) Q[j] = ring + (int64_t)(kM + (it - 1 - j + 2 * kM) % kM) * n;
+    double v[kM] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        const double z = zS[i] + c[i];
+#pragma unroll
+        for (int j = 0; j < kM; ++j)
+            if (j < np) v[j] = fma(z, Q[j][i], v[j]);
+    }
+    if (!grid_sums<kM>(v, partial, counter) || threadIdx.x) return;
+#pragma unroll
+    for (int j = 0; j < kM; ++j) F->beta[j] = j < np ? v[j] / F->pq[(it - 1 - j + 2 * kM) % kM] : 0.0;
+}
+
+// p = zS + c - sum_j beta_j p_j
+__global__ void __launch_bounds__(RT) fk_newp_kernel(double *p, const double *zS, const double *c, const double *ring,
+                                                      int64_t n, const FcgScalars *F)
+{
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    const int it = F->it, np = min(it, kM);
+    const double *P[kM];
+    double b[kM];
+#pragma unroll
+    for (int j = 0; j < kM; ++j) {
+        P[j] = ring + (int64_t)((it - 1 - j + 2 * kM) % kM) * n;
+        b[j] = j < np ? F->beta[j] : 0.0;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        double z = zS[i] + c[i];
+#pragma unroll
+        for (int j = 0; j < kM; ++j)
+            if (j < np) z = fma(-b[j], P[j][i], z);
+        p[i] = z;
+    }
+}
+
+// sigma = RMS of the 3 residual channels of the network input
+__global__ void __launch_bounds__(RT) fk_sigma_kernel(const float *cin, int64_t n3, double *partial, unsigned *counter,
+                                                       FcgScalars *F)
+{
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n3; i += (int64_t)gridDim.x * RT)
+        v[0] += (double)cin[i] * cin[i];
+    if (!grid_sums<1>(v, partial, counter) || threadIdx.x) return;
+    const double s = sqrt(v[0] / (double)n3);
+    F->sigma = isfinite(s) ? s : 0.0;
+}
+
+// f = R r (unscaled); the network input channels become R r / sigma
+__global__ void fk_prep_kernel(float *cin, float *f, int64_t n3, const FcgScalars *F)
+{
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    const float inv = F->sigma > 0.0 ? (float)(1.0 / F->sigma) : 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = cin[i];
+        f[i] = v;
+        cin[i] = v * inv;
+    }
+}
+
+// network output times gamma sigma
+__global__ void fk_post_kernel(float *cout, int64_t n3, double gamma, const FcgScalars *F)
+{
+    const int *stop = &F->stop;
+    STOP_RETURN;
+    const float s = (float)(gamma * F->sigma);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+        cout[i] *= s;
+}
+
+// out = a.b, c.d (c may be null); deterministic
+__global__ void __launch_bounds__(RT) dot2_kernel(const double *a, const double *b, const double *c, const double *d,
+                                                   int64_t n, double *partial, unsigned *counter, double *out)
+{
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        v[0] = fma(a[i], b[i], v[0]);
+        if (c) v[1] = fma(c[i], d[i], v[1]);
+    }
+    if (!grid_sums<2>(v, partial, counter) || threadIdx.x) return;
+    out[0] = v[0];
+    out[1] = v[1];
 }
 
 // z = a + b
 __global__ void add_kernel(double *z, const double *a, const double *b, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) z[i] = a[i] + b[i];
-}
-
-// p = z + beta p
-__global__ void xpby_kernel(double *p, const double *z, int64_t n, double beta)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
-}
-
-// y += a u (+ b v when v is non-null)
-__global__ void xpby_acc_kernel(double *y, const double *u, double a, const double *v, double b, int64_t n)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double t = fma(a, u[i], y[i]);
-        if (v) t = fma(b, v[i], t);
-        y[i] = t;
-    }
 }
 
 // r = b - q (explicit residual)
@@ -182,11 +396,6 @@ using namespace fcm;
 
 namespace {
 
-struct CoarseWs {
-    double *z = nullptr, *c = nullptr, *red = nullptr;
-    float *cin = nullptr, *cout = nullptr, *f = nullptr;
-};
-
 #define CO_CUDA(C, call)                                                                        \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \
@@ -198,45 +407,118 @@ struct CoarseWs {
 
 fcm_status dot2(fcm_ctx *C, const double *a, const double *b, const double *c, const double *d, double *h2)
 {
-    dot2_kernel<<<C->red_blocks, RT, 0, C->stream>>>(a, b, c, d, C->nlat, C->d_partial, C->d_counter, C->d_out2);
+    FcgState *F = C->fcg;
+    dot2_kernel<<<C->red_blocks, RT, 0, C->stream>>>(a, b, c, d, C->nlat, F->partial, F->counter, C->d_out2);
     CO_CUDA(C, cudaMemcpyAsync(h2, C->d_out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
     CO_CUDA(C, cudaStreamSynchronize(C->stream));
     return FCM_OK;
 }
 
-// c = P y with y ~ K_H^-1 R r: the initial guess is gamma sigma N(R r / sigma, eta) (zero without a
-// network), refined by `iters` coarse CG steps (iters = 0: the network's prediction alone).
-fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, int iters, const double *r, CoarseWs &ws,
-                             double *c)
+fcm_status fcg_ensure(fcm_ctx *C)
 {
-    const int64_t ncell = C->hp.ncells;
+    if (C->fcg) return FCM_OK;
+    FcgState *F = new FcgState();
+    F->n = C->nlat;
+    F->ncell = C->hp.ncells;
+    auto fail = [&](cudaError_t e) {
+        C->err = std::string("flexible PCG workspace: ") + cudaGetErrorString(e);
+        fcg_free(F);
+        return e == cudaErrorMemoryAllocation ? FCM_ENOMEM : FCM_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&F->ring, sizeof(double) * 2 * kM * F->n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->c, sizeof(double) * F->n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->partial, sizeof(double) * kM * 152 * 8)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->cin, sizeof(float) * 4 * F->ncell)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->cout, sizeof(float) * 3 * F->ncell)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->f, sizeof(float) * 3 * F->ncell)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&F->d, sizeof(FcgScalars))) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&F->h, sizeof(FcgScalars))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(F->counter, 0, sizeof(unsigned), C->stream)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(F->d, 0, sizeof(FcgScalars), C->stream)) != cudaSuccess) return fail(e);
+    C->fcg = F;
+    return FCM_OK;
+}
+
+// c = P y, y ~ K_H^-1 R r (see the file comment); every launch is stream-ordered and capturable
+fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
+{
+    FcgState *F = C->fcg;
+    const int64_t ncell = F->ncell, n3 = 3 * ncell;
     cudaStream_t st = C->stream;
-    restrict_kernel<<<nblk(ncell), 256, 0, st>>>(r, C->d_mask, C->d_eta, ws.cin, C->g, C->p, 1.0f, 1, ncell);
+    const int *stop = stop_flag(F);
     if (net) {
-        sumsq_kernel<<<1, RT, 0, st>>>(ws.cin, 3 * ncell, ws.red);
-        double ss = 0.0;
-        CO_CUDA(C, cudaMemcpyAsync(&ss, ws.red, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CO_CUDA(C, cudaStreamSynchronize(st));
-        const double sigma = std::sqrt(ss / (3.0 * ncell));
-        if (!(sigma > 0.0) || !std::isfinite(sigma)) {
-            CO_CUDA(C, cudaMemsetAsync(c, 0, sizeof(double) * C->nlat, st));
-            return FCM_OK;
-        }
-        CO_CUDA(C, cudaMemcpyAsync(ws.f, ws.cin, sizeof(float) * 3 * ncell, cudaMemcpyDeviceToDevice, st));
-        scale_f_kernel<<<nblk(3 * ncell), 256, 0, st>>>(ws.cin, 3 * ncell, (float)(1.0 / sigma));
-        fcm_status s = fcm_unet_forward(net, ws.cin, 1, C->g.n[0], C->g.n[1], C->g.n[2], ws.cout);
+        restrict_kernel<<<nblk(ncell), 256, 0, st>>>(C->d_r, C->d_mask, C->d_eta, F->cin, C->g, C->p, 1.0f, 1, ncell, stop);
+        fk_sigma_kernel<<<nblk(n3), RT, 0, st>>>(F->cin, n3, F->partial, F->counter, F->d);
+        fk_prep_kernel<<<nblk(n3), 256, 0, st>>>(F->cin, F->f, n3, F->d);
+        fcm_status s = fcm_unet_forward(net, F->cin, 1, C->g.n[0], C->g.n[1], C->g.n[2], F->cout);
         if (s != FCM_OK) {
             C->err = "fcm_fpcg_solve: " + fcm_unet_last_error();
             return s;
         }
-        scale_f_kernel<<<nblk(3 * ncell), 256, 0, st>>>(ws.cout, 3 * ncell, (float)(gamma * sigma));
+        fk_post_kernel<<<nblk(n3), 256, 0, st>>>(F->cout, n3, gamma, F->d);
+        coarse_solve(C, F->f, F->cout, iters, 2, stop);
     } else {
-        CO_CUDA(C, cudaMemcpyAsync(ws.f, ws.cin, sizeof(float) * 3 * ncell, cudaMemcpyDeviceToDevice, st));
-        CO_CUDA(C, cudaMemsetAsync(ws.cout, 0, sizeof(float) * 3 * ncell, st));
+        restrict_kernel<<<nblk(ncell), 256, 0, st>>>(C->d_r, C->d_mask, C->d_eta, F->f, C->g, C->p, 1.0f, 0, ncell, stop);
+        coarse_solve(C, F->f, F->cout, iters, 0, stop);
     }
-    if (iters > 0) coarse_solve(C, ws.f, ws.cout, iters);
-    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, st>>>(ws.cout, C->d_mask, c, C->g, C->p, 1.0, nullptr, C->nlat / 3);
-    CO_CUDA(C, cudaGetLastError());
+    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, st>>>(F->cout, C->d_mask, F->c, C->g, C->p, 1.0, C->nlat / 3, stop);
+    return FCM_OK;
+}
+
+// one iteration: q = K p, x and r, zS = S r and the judge, c = P y, the next direction
+fcm_status fcg_iteration(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
+{
+    FcgState *F = C->fcg;
+    cudaStream_t st = C->stream;
+    const int64_t n = C->nlat;
+    const int rb = C->red_blocks;
+    const int *stop = stop_flag(F);
+    ctx_apply_K_flag(C, C->d_p, C->d_q, stop);
+    fk_pq_kernel<<<rb, RT, 0, st>>>(C->d_p, C->d_q, C->d_r, F->ring, n, F->partial, F->counter, F->d);
+    fk_xr_kernel<<<rb, RT, 0, st>>>(C->d_x, C->d_r, C->d_p, C->d_q, n, F->d);
+    ctx_apply_S_flag(C, C->d_r, C->d_z, stop);
+    fk_conv_kernel<<<rb, RT, 0, st>>>(C->d_z, n, F->partial, F->counter, F->d);
+    fcm_status s = coarse_correction(C, net, gamma, iters);
+    if (s != FCM_OK) return s;
+    fk_dots_kernel<<<rb, RT, 0, st>>>(C->d_z, F->c, F->ring, n, F->partial, F->counter, F->d);
+    fk_newp_kernel<<<rb, RT, 0, st>>>(C->d_p, C->d_z, F->c, F->ring, n, F->d);
+    return FCM_OK;
+}
+
+fcm_status fcg_graph(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
+{
+    FcgState *F = C->fcg;
+    uint64_t serial = 0, gen = 0;
+    unet_identity(net, &serial, &gen);
+    if (F->graph && F->net == net && F->net_serial == serial && F->net_gen == gen && F->gamma == gamma &&
+        F->coarse_iters == iters)
+        return FCM_OK;
+    if (F->graph) cudaGraphExecDestroy(F->graph);
+    F->graph = nullptr;
+    CO_CUDA(C, cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal));
+    fcm_status s = FCM_OK;
+    for (int k = 0; k < kFcgChunk && s == FCM_OK; ++k) s = fcg_iteration(C, net, gamma, iters);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(C->stream, &graph);
+    if (s != FCM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    CO_CUDA(C, e);
+    e = cudaGraphInstantiate(&F->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        F->graph = nullptr;
+        C->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return FCM_ECUDA;
+    }
+    F->net = net;
+    F->net_serial = serial;
+    F->net_gen = gen;
+    F->gamma = gamma;
+    F->coarse_iters = iters;
     return FCM_OK;
 }
 
@@ -250,7 +532,8 @@ fcm_status fcm_coarse_restrict(fcm_ctx *C, const double *v, float s, int eta_cha
     cudaEventRecord(C->ev_in, C->ustream);
     cudaStreamWaitEvent(C->stream, C->ev_in, 0);
     const int64_t ncell = C->hp.ncells;
-    restrict_kernel<<<nblk(ncell), 256, 0, C->stream>>>(v, C->d_mask, C->d_eta, cells, C->g, C->p, s, eta_channel, ncell);
+    restrict_kernel<<<nblk(ncell), 256, 0, C->stream>>>(v, C->d_mask, C->d_eta, cells, C->g, C->p, s, eta_channel, ncell,
+                                                        nullptr);
     cudaEventRecord(C->ev_out, C->stream);
     cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
     CO_CUDA(C, cudaGetLastError());
@@ -262,7 +545,7 @@ fcm_status fcm_coarse_prolong(fcm_ctx *C, const float *cells, double s, double *
     if (!C || !cells || !y) return FCM_EINVAL;
     cudaEventRecord(C->ev_in, C->ustream);
     cudaStreamWaitEvent(C->stream, C->ev_in, 0);
-    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, C->stream>>>(cells, C->d_mask, y, C->g, C->p, s, nullptr, C->nlat / 3);
+    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, C->stream>>>(cells, C->d_mask, y, C->g, C->p, s, C->nlat / 3, nullptr);
     cudaEventRecord(C->ev_out, C->stream);
     cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
     CO_CUDA(C, cudaGetLastError());
@@ -270,8 +553,7 @@ fcm_status fcm_coarse_prolong(fcm_ctx *C, const float *cells, double s, double *
 }
 
 fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_iters, const double *rhs, double tol,
-                          int maxit, double *u,
-                          int *iterations, double *final_relres)
+                          int maxit, double *u, int *iterations, double *final_relres)
 {
     if (!C || !rhs || !u || !(tol > 0.0) || maxit < 1 || !std::isfinite(gamma) || coarse_iters < 0 ||
         (!net && coarse_iters == 0)) {
@@ -284,31 +566,12 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     }
     cudaEventRecord(C->ev_in, C->ustream);
     cudaStreamWaitEvent(C->stream, C->ev_in, 0);
+    fcm_status s;
+    if ((s = fcg_ensure(C)) != FCM_OK) return s;
+    if ((s = coarse_ensure(C)) != FCM_OK) return s;
+    FcgState *F = C->fcg;
     cudaStream_t st = C->stream;
-    const int64_t n = C->nlat, ncell = C->hp.ncells;
-    CoarseWs ws;
-    struct Free {
-        CoarseWs &w;
-        ~Free()
-        {
-            cudaFree(w.z);
-            cudaFree(w.c);
-            cudaFree(w.red);
-            cudaFree(w.cin);
-            cudaFree(w.cout);
-            cudaFree(w.f);
-        }
-    } freer{ws};
-    CO_CUDA(C, cudaMalloc(&ws.z, sizeof(double) * n));
-    CO_CUDA(C, cudaMalloc(&ws.c, sizeof(double) * n));
-    CO_CUDA(C, cudaMalloc(&ws.red, sizeof(double) * 2));
-    CO_CUDA(C, cudaMalloc(&ws.cin, sizeof(float) * 4 * ncell));
-    CO_CUDA(C, cudaMalloc(&ws.cout, sizeof(float) * 3 * ncell));
-    CO_CUDA(C, cudaMalloc(&ws.f, sizeof(float) * 3 * ncell));
-    if (coarse_iters > 0) {
-        fcm_status se = coarse_ensure(C);
-        if (se != FCM_OK) return se;
-    }
+    const int64_t n = C->nlat;
     // the network runs on the solver's stream for the duration of the solve
     struct Restore {
         fcm_unet *n;
@@ -319,129 +582,72 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
         }
     } restore{net, net ? unet_set_stream(net, st) : nullptr};
 
-    cudaEventRecord(C->ev_t0, st);
-    double *x = C->d_x, *r = C->d_r, *zS = C->d_z, *p = C->d_p, *q = C->d_q, *b = C->d_b;
+    double *x = C->d_x, *r = C->d_r, *zS = C->d_z, *q = C->d_q, *b = C->d_b;
     launch_mask_copy(rhs, b, C->d_mask, n, st);
-    CO_CUDA(C, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-    CO_CUDA(C, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     double h2[2];
-    fcm_status s;
     if ((s = dot2(C, b, b, nullptr, nullptr, h2)) != FCM_OK) return s;
     if (!std::isfinite(h2[0])) {
         C->err = "fcm_fpcg_solve: right-hand side has non-finite entries";
         return FCM_EINVAL;
     }
-    ctx_apply_S(C, r, zS);
-    if ((s = dot2(C, zS, zS, nullptr, nullptr, h2)) != FCM_OK) return s;
-    const double judge0 = std::sqrt(h2[0]);
-    double rel = 0.0, best = 1.0, mark = 1.0;
-    int it = 0, mark_it = 0;
-    constexpr int kStallWindow = 100;
-    bool converged = judge0 == 0.0, fallback = false;
-    // truncated flexible CG, FCG(m) (Notay 2000): each new direction is K-orthogonalised
-    // against the last kTrunc ones; ring of kTrunc + 1 direction slots (slot 0 = C->d_p/d_q)
-    constexpr int kTrunc = 4, kRing = kTrunc + 1;
-    double *P[kRing], *Q[kRing], pqs[kRing] = {0.0};
-    P[0] = p;
-    Q[0] = q;
-    std::vector<double *> extra;
-    struct FreeRing {
-        std::vector<double *> &v;
-        ~FreeRing()
-        {
-            for (double *a : v) cudaFree(a);
-        }
-    } free_ring{extra};
-    for (int k = 1; k < kRing; ++k) {
-        CO_CUDA(C, cudaMalloc(&P[k], sizeof(double) * n));
-        extra.push_back(P[k]);
-        CO_CUDA(C, cudaMalloc(&Q[k], sizeof(double) * n));
-        extra.push_back(Q[k]);
+    FcgScalars &h = *F->h;
+    std::memset(&h, 0, sizeof h);
+    h.tol = tol;
+    h.maxit = maxit;
+    h.window = kStallWindow;
+    CO_CUDA(C, cudaMemcpyAsync(F->d, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    CO_CUDA(C, cudaEventRecord(C->ev_t0, st));
+    CO_CUDA(C, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CO_CUDA(C, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    ctx_apply_S_flag(C, r, zS, nullptr);
+    fk_first_kernel<<<C->red_blocks, RT, 0, st>>>(zS, n, F->partial, F->counter, F->d);
+    // first direction p = S r + c (also the warm-up of the network's buffers before any capture)
+    if ((s = coarse_correction(C, net, gamma, coarse_iters)) != FCM_OK) return s;
+    fk_newp_kernel<<<C->red_blocks, RT, 0, st>>>(C->d_p, zS, F->c, F->ring, n, F->d);
+    CO_CUDA(C, cudaGetLastError());
+    if ((s = fcg_graph(C, net, gamma, coarse_iters)) != FCM_OK) return s;
+    for (;;) {
+        CO_CUDA(C, cudaMemcpyAsync(&h, F->d, sizeof h, cudaMemcpyDeviceToHost, st));
+        CO_CUDA(C, cudaStreamSynchronize(st));
+        if (h.stop) break;
+        CO_CUDA(C, cudaGraphLaunch(F->graph, st));
     }
-    if (!converged) {
-        if ((s = coarse_correction(C, net, gamma, coarse_iters, r, ws, ws.c)) != FCM_OK) return s;
-        add_kernel<<<nblk(n), 256, 0, st>>>(P[0], zS, ws.c, n);
-        rel = 1.0;
-    }
-    while (!converged && !fallback && it < maxit) {
-        const int cur = it % kRing;
-        double *pc = P[cur], *qc = Q[cur];
-        ctx_apply_K(C, pc, qc);
-        if ((s = dot2(C, pc, qc, pc, r, h2)) != FCM_OK) return s;
-        const double pq = h2[0], pr = h2[1];
-        pqs[cur] = pq;
-        ++it;
-        if (!(pq > 0.0) || !std::isfinite(pr)) {
-            fallback = true;
-            break;
-        }
-        const double alpha = pr / pq;
-        axpy2_kernel<<<nblk(n), 256, 0, st>>>(x, r, pc, qc, n, alpha);
-        ctx_apply_S(C, r, zS);
-        if ((s = dot2(C, zS, zS, nullptr, nullptr, h2)) != FCM_OK) return s;
-        rel = std::sqrt(h2[0]) / judge0;
-        if (!std::isfinite(rel)) {
-            fallback = true;
-            break;
-        }
-        best = std::min(best, rel);
-        if (rel <= tol) {
-            converged = true;
-            break;
-        }
-        if (rel <= 0.5 * mark) {
-            mark = rel;
-            mark_it = it;
-        }
-        // a harmful or useless correction: growth, or no halving within kStallWindow iterations
-        if (rel > 100.0 * best || it - mark_it >= kStallWindow) {
-            fallback = true;
-            break;
-        }
-        if ((s = coarse_correction(C, net, gamma, coarse_iters, r, ws, ws.c)) != FCM_OK) return s;
-        add_kernel<<<nblk(n), 256, 0, st>>>(ws.z, zS, ws.c, n);
-        // p_new = z - sum_j (z.q_j / p_j.q_j) p_j over the last min(it, kTrunc) directions
-        const int nxt = it % kRing;
-        CO_CUDA(C, cudaMemcpyAsync(P[nxt], ws.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        const int nprev = std::min(it, kTrunc);
-        for (int j0 = 0; j0 < nprev; j0 += 2) {
-            const int a = (it - 1 - j0 + kRing) % kRing;
-            const int b2 = (it - 2 - j0 + kRing) % kRing;
-            const bool two = j0 + 1 < nprev;
-            if ((s = dot2(C, ws.z, Q[a], two ? ws.z : nullptr, two ? Q[b2] : nullptr, h2)) != FCM_OK) return s;
-            xpby_acc_kernel<<<nblk(n), 256, 0, st>>>(P[nxt], P[a], -h2[0] / pqs[a], two ? P[b2] : nullptr,
-                                                      two ? -h2[1] / pqs[b2] : 0.0, n);
-        }
-    }
+    const int it = h.it;
+    const bool fallback = h.fallback != 0;
+    const double judge0 = h.judge0;
+    double rel = h.rel;
     int total = it;
-    fcm_status status = converged ? FCM_OK : FCM_ENOTCONV;
+    fcm_status status = (fcm_status)h.status;
     if (fallback && it < maxit) {
         // plain Schwarz-PCG on K dx = b - K x, to the same absolute judged residual
-        ctx_apply_K(C, x, q);
-        sub_kernel<<<nblk(n), 256, 0, st>>>(ws.c, b, q, n);  // ws.c = explicit residual
-        ctx_apply_S(C, ws.c, zS);
+        double *res = F->c, *keep = F->ring;
+        ctx_apply_K_flag(C, x, q, nullptr);
+        sub_kernel<<<nblk(n), 256, 0, st>>>(res, b, q, n);
+        ctx_apply_S_flag(C, res, zS, nullptr);
         if ((s = dot2(C, zS, zS, nullptr, nullptr, h2)) != FCM_OK) return s;
         const double jr = std::sqrt(h2[0]);
-        CO_CUDA(C, cudaMemcpyAsync(ws.z, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));  // keep x
+        CO_CUDA(C, cudaMemcpyAsync(keep, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         fcm_solve_info inner = {};
         const double tol2 = jr > 0.0 ? std::min(1.0, tol * judge0 / jr) : 1.0;
-        // the plain solve consumes its right-hand side first, so ws.c also receives dx
-        fcm_status s2 = ctx_solve_one(C, ws.c, tol2, maxit - it, ws.c, inner);
+        // the plain solve copies its right-hand side first, so `res` also receives dx
+        fcm_status s2 = ctx_solve_one(C, res, tol2, maxit - it, res, inner);
         if (s2 == FCM_EINVAL || s2 == FCM_ECUDA || s2 == FCM_ENOMEM) return s2;
-        add_kernel<<<nblk(n), 256, 0, st>>>(x, ws.z, ws.c, n);
+        add_kernel<<<nblk(n), 256, 0, st>>>(x, keep, res, n);
         total += inner.iterations;
         rel = inner.relres * (jr / judge0);
         status = (fcm_status)inner.status;
-        // ctx_solve_one left b = masked ws.c; restore the caller's b for the true residual
+        // the plain solve left b = masked res; restore the caller's b for the true residual
         launch_mask_copy(rhs, b, C->d_mask, n, st);
+    } else if (fallback) {
+        status = FCM_ENOTCONV;
     }
     cudaEventRecord(C->ev_t1, st);
     CO_CUDA(C, cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    ctx_apply_K(C, x, q);
+    ctx_apply_K_flag(C, x, q, nullptr);
     if ((s = dot2(C, b, b, nullptr, nullptr, h2)) != FCM_OK) return s;
     const double bb = h2[0];
-    sub_kernel<<<nblk(n), 256, 0, st>>>(ws.c, b, q, n);
-    if ((s = dot2(C, ws.c, ws.c, nullptr, nullptr, h2)) != FCM_OK) return s;
+    sub_kernel<<<nblk(n), 256, 0, st>>>(F->c, b, q, n);
+    if ((s = dot2(C, F->c, F->c, nullptr, nullptr, h2)) != FCM_OK) return s;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, C->ev_t0, C->ev_t1);
     C->last.iterations = total;
@@ -457,6 +663,32 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
     if (status == FCM_ENOTCONV) C->err = "fcm_fpcg_solve: maxit reached";
     return status;
+}
+
+fcm_status fcm_fpcg_solve_host(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_iters, const double *rhs_host,
+                               double tol, int maxit, double *u_host, int *iterations, double *final_relres)
+{
+    if (!C || !rhs_host || !u_host) {
+        if (C) C->err = "fcm_fpcg_solve_host: invalid argument";
+        return FCM_EINVAL;
+    }
+    if (!C->have_precond) {
+        C->err = "fcm_fpcg_solve_host: call fcm_precond_build first";
+        return FCM_ESTATE;
+    }
+    cudaEventRecord(C->ev_in, C->ustream);
+    cudaStreamWaitEvent(C->stream, C->ev_in, 0);
+    // the coarse operator's assembly uses the scratch vector d_t: build it before the rhs goes there
+    fcm_status s;
+    if ((s = fcg_ensure(C)) != FCM_OK) return s;
+    if ((s = coarse_ensure(C)) != FCM_OK) return s;
+    CO_CUDA(C, cudaMemcpyAsync(C->d_t, rhs_host, sizeof(double) * C->nlat, cudaMemcpyHostToDevice, C->stream));
+    // the device solve reads its right-hand side before it writes the solution, so both may be d_t
+    s = fcm_fpcg_solve(C, net, gamma, coarse_iters, C->d_t, tol, maxit, C->d_t, iterations, final_relres);
+    if (s == FCM_EINVAL || s == FCM_ECUDA || s == FCM_ENOMEM || s == FCM_ESTATE) return s;
+    CO_CUDA(C, cudaMemcpyAsync(u_host, C->d_t, sizeof(double) * C->nlat, cudaMemcpyDeviceToHost, C->stream));
+    CO_CUDA(C, cudaStreamSynchronize(C->stream));
+    return s;
 }
 
 }  // extern "C"

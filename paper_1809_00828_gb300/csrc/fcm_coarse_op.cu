@@ -12,9 +12,17 @@
 //
 // The coarse system K_H y = R r is solved approximately by a fixed number of
 // block-Jacobi-preconditioned CG steps whose scalars stay on the device, from
-// an initial guess (the learned network's prediction, or zero).  Storage and
-// arithmetic are FP32 with FP64 dot products: the coarse solve is part of a
-// preconditioner inside flexible CG, which tolerates its inexactness.
+// an initial guess: zero, or the learned network's prediction scaled by the
+// step t = f.y0 / y0.K_H y0 that minimises the coarse energy along y0 (so the
+// start is never worse than zero in the K_H norm).  Storage and arithmetic are
+// FP32 with FP64 dot products: the coarse solve is part of a preconditioner
+// inside flexible CG, which tolerates its inexactness.  K_H is symmetric, so
+// only the 63 blocks of the offsets from (0,0,0) on (in z, y, x order) are
+// stored, as structure of arrays, KH[(s * 9 + 3 a + b) * n_cells + cell], so
+// that consecutive threads (cells) read consecutive words; at 32^3 cells the
+// 74 MB stay in L2 across the steps of a coarse solve.  Every kernel returns at
+// once when the device flag `stop` (may be null) is set, so the solve can be
+// captured in a CUDA graph that runs past the end of the outer iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,20 +35,28 @@ namespace fcm {
 
 struct CoarseOp {
     int64_t ncell = 0;
-    float *KH = nullptr;     // [cell][125][3][3]
+    float *KH = nullptr;     // [63 * 9][cell]: the blocks of offsets 0..62 (see kStored)
     float *Dinv = nullptr;   // [cell][3][3] inverse of the diagonal block (0 where singular)
-    float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;  // 3 x ncell each, [comp][cell]
+    float *r = nullptr, *z = nullptr, *q = nullptr, *p[2] = {nullptr, nullptr};  // 3 x ncell each, [comp][cell]
     double *partial = nullptr;
+    int64_t npartial = 0;
     unsigned *counter = nullptr;
-    double *sc = nullptr;    // rz, pq, alpha, beta
+    double *sc = nullptr;    // rz, pq, alpha, beta, t
+    double seconds = 0.0;    // assembly time
 };
 
 namespace {
 
 constexpr int RT = 256;
-constexpr int NOFF = 125;
+constexpr int kCenter = 62;               // offset index of (0, 0, 0) in the 5x5x5 stencil
+constexpr int kStored = 63;               // offsets kCenter..124 are stored; the others by symmetry
+constexpr int kTileCells = 32;            // cells per CTA of the K_H apply (one per lane)
+constexpr int kTileWarps = RT / 32;       // warps of that CTA, splitting the offsets
 
 int nb(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+#define STOP_RETURN \
+    if (stop && *stop) return
 
 // e[b][c] = 1 for the cells of class (ox, oy, oz) (c mod 5 per axis) and component b, else 0 (double cells)
 __global__ void probe_cells_kernel(double *e, Grid3 g, int ox, int oy, int oz, int b, int64_t ncell)
@@ -74,7 +90,8 @@ __global__ void prolong_d_kernel(const double *__restrict__ cells, const uint8_t
     }
 }
 
-// KH[c'][off][a][b] = (R K P e)[a][c'] for the probed cell c within distance 2 of c'
+// KH[s][a][b][c'] = (R K P e)[a][c'] for the probed cell c = c' + off within distance 2 of c',
+// kept for the offsets with index kCenter + s, s >= 0
 __global__ void probe_scatter_kernel(const double *__restrict__ v, const uint8_t *__restrict__ mask, float *KH, Grid3 g,
                                      int p, int ox, int oy, int oz, int b, int64_t ncell)
 {
@@ -90,7 +107,8 @@ __global__ void probe_scatter_kernel(const double *__restrict__ v, const uint8_t
             const int t = cc[ax] + d;
             ok = ok && t >= 0 && t < g.n[ax];
         }
-        if (!ok) continue;
+        const int oi = (off[0] + 2) + 5 * ((off[1] + 2) + 5 * (off[2] + 2));
+        if (!ok || oi < kCenter) continue;
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < 8; ++k) {
             const int64_t node = (int64_t)p * (cc[0] + (k & 1)) +
@@ -98,15 +116,16 @@ __global__ void probe_scatter_kernel(const double *__restrict__ v, const uint8_t
             for (int a = 0; a < 3; ++a)
                 if (mask[3 * node + a]) acc[a] += v[3 * node + a];
         }
-        const int oi = (off[0] + 2) + 5 * ((off[1] + 2) + 5 * (off[2] + 2));
-        for (int a = 0; a < 3; ++a) KH[((c * NOFF + oi) * 3 + a) * 3 + b] = (float)(0.125 * acc[a]);
+        const int s = oi - kCenter;
+        for (int a = 0; a < 3; ++a) KH[(int64_t)(s * 9 + 3 * a + b) * ncell + c] = (float)(0.125 * acc[a]);
     }
 }
 
 __global__ void diag_inverse_kernel(const float *KH, float *Dinv, int64_t ncell)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-        const float *A = KH + (c * NOFF + 62) * 9;  // offset (0,0,0)
+        double A[9];
+        for (int t = 0; t < 9; ++t) A[t] = KH[(int64_t)t * ncell + c];  // s = 0: offset (0,0,0)
         const double a = A[0], b = A[1], d = A[2], e = A[3], f = A[4], h = A[5], k = A[6], l = A[7], m = A[8];
         const double c00 = f * m - h * l, c01 = -(e * m - h * k), c02 = e * l - f * k;
         const double det = a * c00 + b * c01 + d * c02;
@@ -129,44 +148,6 @@ __global__ void diag_inverse_kernel(const float *KH, float *Dinv, int64_t ncell)
     }
 }
 
-// y = K_H x (FP32, [comp][cell])
-__global__ void kh_apply_kernel(const float *__restrict__ KH, const float *__restrict__ x, float *__restrict__ y, Grid3 g,
-                                int64_t ncell)
-{
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-        const int cx = (int)(c % g.n[0]), cy = (int)((c / g.n[0]) % g.n[1]), cz = (int)(c / ((int64_t)g.n[0] * g.n[1]));
-        float acc[3] = {0.f, 0.f, 0.f};
-        const float *A = KH + c * NOFF * 9;
-        for (int dz = -2; dz <= 2; ++dz) {
-            const int zz = cz + dz;
-            if (zz < 0 || zz >= g.n[2]) continue;
-            for (int dy = -2; dy <= 2; ++dy) {
-                const int yy = cy + dy;
-                if (yy < 0 || yy >= g.n[1]) continue;
-                for (int dx = -2; dx <= 2; ++dx) {
-                    const int xx = cx + dx;
-                    if (xx < 0 || xx >= g.n[0]) continue;
-                    const int64_t nc = xx + (int64_t)g.n[0] * (yy + (int64_t)g.n[1] * zz);
-                    const float *B = A + ((dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2))) * 9;
-                    const float x0 = x[nc], x1 = x[ncell + nc], x2 = x[2 * ncell + nc];
-                    for (int a = 0; a < 3; ++a) acc[a] = fmaf(B[3 * a], x0, fmaf(B[3 * a + 1], x1, fmaf(B[3 * a + 2], x2, acc[a])));
-                }
-            }
-        }
-        for (int a = 0; a < 3; ++a) y[a * ncell + c] = acc[a];
-    }
-}
-
-// z = Dinv r
-__global__ void jacobi_kernel(const float *Dinv, const float *r, float *z, int64_t ncell)
-{
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-        const float *D = Dinv + c * 9;
-        const float r0 = r[c], r1 = r[ncell + c], r2 = r[2 * ncell + c];
-        for (int a = 0; a < 3; ++a) z[a * ncell + c] = D[3 * a] * r0 + D[3 * a + 1] * r1 + D[3 * a + 2] * r2;
-    }
-}
-
 __device__ __forceinline__ double wsum(double v)
 {
 #pragma unroll
@@ -185,63 +166,195 @@ __device__ double bsum(double v, double *sh)
     return v;
 }
 
-// mode 0: sc[0] = a.b (rz of the start);  mode 1: pq = a.b, alpha = rz / pq;
-// mode 2: rz' = a.b, beta = rz' / rz, rz = rz'.  Deterministic two-level reduction.
-__global__ void __launch_bounds__(RT) cdot_kernel(const float *a, const float *b, int64_t n, double *partial,
-                                                   unsigned *counter, double *sc, int mode)
+// Two sums over the grid in a fixed order; true in the last CTA, whose thread 0 then holds the totals.
+__device__ bool grid_sums2(double &x, double &y, double *partial, unsigned *counter)
 {
     __shared__ double sh[RT / 32];
     __shared__ bool last;
-    double x = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) x += (double)a[i] * b[i];
     x = bsum(x, sh);
+    y = bsum(y, sh);
     if (threadIdx.x == 0) {
-        partial[blockIdx.x] = x;
+        partial[2 * blockIdx.x] = x;
+        partial[2 * blockIdx.x + 1] = y;
         __threadfence();
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
-    x = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += RT) x += __ldcg(partial + i);
-    x = bsum(x, sh);
-    if (threadIdx.x == 0) {
-        *counter = 0u;
-        if (mode == 0) {
-            sc[0] = x;
-        } else if (mode == 1) {
-            sc[1] = x;
-            sc[2] = (x > 0.0 && isfinite(sc[0] / x)) ? sc[0] / x : 0.0;
-        } else {
-            sc[3] = (sc[0] > 0.0 && isfinite(x / sc[0])) ? x / sc[0] : 0.0;
-            sc[0] = x;
+    if (!last) return false;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += RT) {
+        a += __ldcg(partial + 2 * i);
+        b += __ldcg(partial + 2 * i + 1);
+    }
+    x = bsum(a, sh);
+    y = bsum(b, sh);
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// y = K_H v over a tile of 32 cells per CTA; the 8 warps split the 63 stored offsets, each
+// stored block used twice: directly (row cell c, column cell c + off) and transposed for the
+// mirrored offset (row c, column c - off), since K_H is symmetric.
+//   mode 0: v = x
+//   mode 1: v = x + beta xb (beta = sc[3]); v is written to pout; pq = v.y, alpha = rz / pq
+//   mode 2: v = x;                          v is written to pout; pq = v.y, alpha = rz / pq
+__global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, const float *__restrict__ x,
+                                                 const float *__restrict__ xb, float *__restrict__ pout,
+                                                 float *__restrict__ y, Grid3 g, int64_t ncell, int mode,
+                                                 double *partial, unsigned *counter, double *sc, const int *stop)
+{
+    STOP_RETURN;
+    __shared__ float red[kTileWarps][3][kTileCells];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kTileCells + lane;
+    const bool live = c < ncell;
+    const float beta = mode == 1 ? (float)sc[3] : 0.f;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int cx = live ? (int)(c % nx) : 0, cy = live ? (int)((c / nx) % ny) : 0,
+              cz = live ? (int)(c / ((int64_t)nx * ny)) : 0;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (live) {
+        for (int s = w; s < kStored; s += kTileWarps) {
+            const int oi = kCenter + s, dx = oi % 5 - 2, dy = (oi / 5) % 5 - 2, dz = oi / 25 - 2;
+            const int64_t d = dx + (int64_t)nx * (dy + (int64_t)ny * dz);
+            const float *B = KH + (int64_t)s * 9 * ncell;
+            if (cx + dx >= 0 && cx + dx < nx && cy + dy >= 0 && cy + dy < ny && cz + dz >= 0 && cz + dz < nz) {
+                const int64_t n = c + d;
+                float v0 = __ldg(x + n), v1 = __ldg(x + ncell + n), v2 = __ldg(x + 2 * ncell + n);
+                if (mode == 1) {
+                    v0 = fmaf(beta, __ldg(xb + n), v0);
+                    v1 = fmaf(beta, __ldg(xb + ncell + n), v1);
+                    v2 = fmaf(beta, __ldg(xb + 2 * ncell + n), v2);
+                }
+                const float *Bc = B + c;
+                a0 = fmaf(__ldg(Bc), v0, fmaf(__ldg(Bc + ncell), v1, fmaf(__ldg(Bc + 2 * ncell), v2, a0)));
+                a1 = fmaf(__ldg(Bc + 3 * ncell), v0, fmaf(__ldg(Bc + 4 * ncell), v1, fmaf(__ldg(Bc + 5 * ncell), v2, a1)));
+                a2 = fmaf(__ldg(Bc + 6 * ncell), v0, fmaf(__ldg(Bc + 7 * ncell), v1, fmaf(__ldg(Bc + 8 * ncell), v2, a2)));
+            }
+            if (s > 0 && cx - dx >= 0 && cx - dx < nx && cy - dy >= 0 && cy - dy < ny && cz - dz >= 0 && cz - dz < nz) {
+                const int64_t m = c - d;
+                float v0 = __ldg(x + m), v1 = __ldg(x + ncell + m), v2 = __ldg(x + 2 * ncell + m);
+                if (mode == 1) {
+                    v0 = fmaf(beta, __ldg(xb + m), v0);
+                    v1 = fmaf(beta, __ldg(xb + ncell + m), v1);
+                    v2 = fmaf(beta, __ldg(xb + 2 * ncell + m), v2);
+                }
+                const float *Bm = B + m;
+                a0 = fmaf(__ldg(Bm), v0, fmaf(__ldg(Bm + 3 * ncell), v1, fmaf(__ldg(Bm + 6 * ncell), v2, a0)));
+                a1 = fmaf(__ldg(Bm + ncell), v0, fmaf(__ldg(Bm + 4 * ncell), v1, fmaf(__ldg(Bm + 7 * ncell), v2, a1)));
+                a2 = fmaf(__ldg(Bm + 2 * ncell), v0, fmaf(__ldg(Bm + 5 * ncell), v1, fmaf(__ldg(Bm + 8 * ncell), v2, a2)));
+            }
         }
     }
-}
-
-// y += alpha p, r -= alpha q
-__global__ void cupd_kernel(float *y, float *r, const float *p, const float *q, int64_t n, const double *sc)
-{
-    const float al = (float)sc[2];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        y[i] = fmaf(al, p[i], y[i]);
-        r[i] = fmaf(-al, q[i], r[i]);
+    red[w][0][lane] = a0;
+    red[w][1][lane] = a1;
+    red[w][2][lane] = a2;
+    __syncthreads();
+    double dot = 0.0, unused = 0.0;
+    if (w < 3) {
+        // warp w finishes component w of the 32 cells
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTileWarps; ++k) acc += red[k][w][lane];
+        if (live) {
+            y[w * ncell + c] = acc;
+            if (mode != 0) {
+                float v = x[w * ncell + c];
+                if (mode == 1) v = fmaf(beta, xb[w * ncell + c], v);
+                pout[w * ncell + c] = v;
+                dot = (double)v * acc;
+            }
+        }
     }
+    if (mode == 0) return;
+    if (!grid_sums2(dot, unused, partial, counter) || threadIdx.x) return;
+    sc[1] = dot;
+    sc[2] = (dot > 0.0 && isfinite(sc[0] / dot)) ? sc[0] / dot : 0.0;
 }
 
-// p = z + beta p (beta = 0 on the first call: p = z)
-__global__ void cp_kernel(float *p, const float *z, int64_t n, const double *sc, int first)
+// line search t = f.y / y.q (0 when y.q <= 0), into sc[4]
+__global__ void __launch_bounds__(RT) line_kernel(const float *f, const float *y, const float *q, int64_t n,
+                                                   double *partial, unsigned *counter, double *sc, const int *stop)
 {
-    const float be = first ? 0.f : (float)sc[3];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = first ? z[i] : fmaf(be, p[i], z[i]);
+    STOP_RETURN;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        a += (double)f[i] * y[i];
+        b += (double)y[i] * q[i];
+    }
+    if (!grid_sums2(a, b, partial, counter) || threadIdx.x) return;
+    sc[4] = (b > 0.0 && isfinite(a / b)) ? a / b : 0.0;
 }
 
-// r = f - r  (r holds K_H y on entry)
-__global__ void csub_kernel(const float *f, float *r, int64_t n)
+// Start of the coarse CG, one thread per cell:
+//   start 0: y = 0, r = f;  start 1: r = f - q (q = K_H y);  start 2: y *= t, r = f - t q.
+// With want_z: z = Dinv r and rz = r.z into sc[0].
+__global__ void __launch_bounds__(RT) cstart_kernel(const float *f, float *y, float *r, float *z, const float *q,
+                                                     const float *Dinv, int64_t ncell, int start, int want_z,
+                                                     double *partial, unsigned *counter, double *sc, const int *stop)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) r[i] = f[i] - r[i];
+    STOP_RETURN;
+    const float t = start == 2 ? (float)sc[4] : 1.f;
+    double dot = 0.0, unused = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)RT + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * RT) {
+        float rv[3];
+        for (int a = 0; a < 3; ++a) {
+            const int64_t i = a * ncell + c;
+            if (start == 0) {
+                y[i] = 0.f;
+                rv[a] = f[i];
+            } else {
+                y[i] *= t;
+                rv[a] = fmaf(-t, q[i], f[i]);
+            }
+            r[i] = rv[a];
+        }
+        if (want_z) {
+            const float *D = Dinv + c * 9;
+            for (int a = 0; a < 3; ++a) {
+                const float zv = D[3 * a] * rv[0] + D[3 * a + 1] * rv[1] + D[3 * a + 2] * rv[2];
+                z[a * ncell + c] = zv;
+                dot += (double)rv[a] * zv;
+            }
+        }
+    }
+    if (!want_z) return;
+    if (!grid_sums2(dot, unused, partial, counter) || threadIdx.x) return;
+    sc[0] = dot;
 }
+
+// y += alpha p, r -= alpha q; unless last: z = Dinv r, rz' = r.z, beta = rz' / rz, rz = rz'
+__global__ void __launch_bounds__(RT) cupd_kernel(float *y, float *r, float *z, const float *p, const float *q,
+                                                   const float *Dinv, int64_t ncell, int last_step, double *partial,
+                                                   unsigned *counter, double *sc, const int *stop)
+{
+    STOP_RETURN;
+    const float al = (float)sc[2];
+    double dot = 0.0, unused = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)RT + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * RT) {
+        float rv[3];
+        for (int a = 0; a < 3; ++a) {
+            const int64_t i = a * ncell + c;
+            y[i] = fmaf(al, p[i], y[i]);
+            rv[a] = fmaf(-al, q[i], r[i]);
+            r[i] = rv[a];
+        }
+        if (!last_step) {
+            const float *D = Dinv + c * 9;
+            for (int a = 0; a < 3; ++a) {
+                const float zv = D[3 * a] * rv[0] + D[3 * a + 1] * rv[1] + D[3 * a + 2] * rv[2];
+                z[a * ncell + c] = zv;
+                dot += (double)rv[a] * zv;
+            }
+        }
+    }
+    if (last_step) return;
+    if (!grid_sums2(dot, unused, partial, counter) || threadIdx.x) return;
+    sc[3] = (sc[0] > 0.0 && isfinite(dot / sc[0])) ? dot / sc[0] : 0.0;
+    sc[0] = dot;
+}
+
+int tiles(int64_t ncell) { return (int)((ncell + kTileCells - 1) / kTileCells); }
 
 }  // namespace
 
@@ -258,17 +371,24 @@ fcm_status coarse_ensure(fcm_ctx *C)
         return e == cudaErrorMemoryAllocation ? FCM_ENOMEM : FCM_ECUDA;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&op->KH, sizeof(float) * ncell * NOFF * 9)) != cudaSuccess) return fail(e);
+    const size_t kh_words = (size_t)ncell * kStored * 9;
+    if ((e = cudaMalloc(&op->KH, sizeof(float) * kh_words)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&op->Dinv, sizeof(float) * ncell * 9)) != cudaSuccess) return fail(e);
-    float **vs[] = {&op->r, &op->z, &op->p, &op->q};
+    float **vs[] = {&op->r, &op->z, &op->q, &op->p[0], &op->p[1]};
     for (float **v : vs)
         if ((e = cudaMalloc(v, sizeof(float) * n3)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&op->partial, sizeof(double) * 152 * 8)) != cudaSuccess) return fail(e);
+    op->npartial = std::max<int64_t>(tiles(ncell), 152 * 8);
+    if ((e = cudaMalloc(&op->partial, sizeof(double) * 2 * op->npartial)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&op->counter, sizeof(unsigned))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&op->sc, sizeof(double) * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&op->sc, sizeof(double) * 8)) != cudaSuccess) return fail(e);
     cudaStream_t st = C->stream;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, st);
     cudaMemsetAsync(op->counter, 0, sizeof(unsigned), st);
-    cudaMemsetAsync(op->KH, 0, sizeof(float) * ncell * NOFF * 9, st);
+    cudaMemsetAsync(op->sc, 0, sizeof(double) * 8, st);
+    cudaMemsetAsync(op->KH, 0, sizeof(float) * kh_words, st);
     double *ecell = nullptr;
     if ((e = cudaMalloc(&ecell, sizeof(double) * n3)) != cudaSuccess) return fail(e);
     // lattice scratch: the context's d_t (probe) and d_q (K times probe)
@@ -283,7 +403,13 @@ fcm_status coarse_ensure(fcm_ctx *C)
                                                                      ncell);
                 }
     diag_inverse_kernel<<<nb(ncell), 256, 0, st>>>(op->KH, op->Dinv, ncell);
+    cudaEventRecord(t1, st);
     e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    op->seconds = ms * 1e-3;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
     cudaFree(ecell);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return fail(e);
     C->coarse = op;
@@ -293,39 +419,45 @@ fcm_status coarse_ensure(fcm_ctx *C)
 void coarse_free(CoarseOp *op)
 {
     if (!op) return;
-    void *ps[] = {op->KH, op->Dinv, op->r, op->z, op->p, op->q, op->partial, op->counter, op->sc};
+    void *ps[] = {op->KH, op->Dinv, op->r, op->z, op->q, op->p[0], op->p[1], op->partial, op->counter, op->sc};
     for (void *q : ps)
         if (q) cudaFree(q);
     delete op;
 }
 
-// y <- approximate solution of K_H y = f after `iters` block-Jacobi CG steps from the given y
-// (FP32 cells, [comp][cell]); asynchronous on the context's stream.
-void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters)
+double coarse_seconds(const CoarseOp *op) { return op ? op->seconds : 0.0; }
+
+// y <- approximate solution of K_H y = f after `iters` block-Jacobi CG steps (FP32 cells,
+// [comp][cell]) from the start `start` (0 zero, 1 the given y, 2 the given y scaled by the
+// energy-minimising step); asynchronous on the context's stream, capturable.  Two launches
+// per step: the K_H apply (which also forms the new direction and alpha) and the update
+// (which also applies Dinv and forms beta).
+void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, const int *stop)
 {
     CoarseOp *op = C->coarse;
-    const int64_t n3 = 3 * op->ncell;
+    const int64_t n3 = 3 * op->ncell, nc = op->ncell;
     cudaStream_t st = C->stream;
-    const int rb = nb(n3);
-    kh_apply_kernel<<<nb(op->ncell), 256, 0, st>>>(op->KH, y, op->r, C->g, op->ncell);
-    csub_kernel<<<nb(n3), 256, 0, st>>>(f, op->r, n3);
-    jacobi_kernel<<<nb(op->ncell), 256, 0, st>>>(op->Dinv, op->r, op->z, op->ncell);
-    cp_kernel<<<nb(n3), 256, 0, st>>>(op->p, op->z, n3, op->sc, 1);
-    cdot_kernel<<<rb, RT, 0, st>>>(op->r, op->z, n3, op->partial, op->counter, op->sc, 0);
+    if (start != 0)
+        kh_kernel<<<tiles(nc), RT, 0, st>>>(op->KH, y, nullptr, nullptr, op->q, C->g, nc, 0, op->partial, op->counter,
+                                            op->sc, stop);
+    if (start == 2) line_kernel<<<nb(n3), RT, 0, st>>>(f, y, op->q, n3, op->partial, op->counter, op->sc, stop);
+    cstart_kernel<<<nb(nc), RT, 0, st>>>(f, y, op->r, op->z, op->q, op->Dinv, nc, start, iters > 0 ? 1 : 0, op->partial,
+                                         op->counter, op->sc, stop);
     for (int i = 0; i < iters; ++i) {
-        kh_apply_kernel<<<nb(op->ncell), 256, 0, st>>>(op->KH, op->p, op->q, C->g, op->ncell);
-        cdot_kernel<<<rb, RT, 0, st>>>(op->p, op->q, n3, op->partial, op->counter, op->sc, 1);
-        cupd_kernel<<<nb(n3), 256, 0, st>>>(y, op->r, op->p, op->q, n3, op->sc);
-        if (i + 1 == iters) break;
-        jacobi_kernel<<<nb(op->ncell), 256, 0, st>>>(op->Dinv, op->r, op->z, op->ncell);
-        cdot_kernel<<<rb, RT, 0, st>>>(op->r, op->z, n3, op->partial, op->counter, op->sc, 2);
-        cp_kernel<<<nb(n3), 256, 0, st>>>(op->p, op->z, n3, op->sc, 0);
+        float *pn = op->p[i & 1];
+        const float *po = op->p[(i + 1) & 1];
+        kh_kernel<<<tiles(nc), RT, 0, st>>>(op->KH, op->z, i == 0 ? nullptr : po, pn, op->q, C->g, nc, i == 0 ? 2 : 1,
+                                            op->partial, op->counter, op->sc, stop);
+        cupd_kernel<<<nb(nc), RT, 0, st>>>(y, op->r, op->z, pn, op->q, op->Dinv, nc, i + 1 == iters ? 1 : 0, op->partial,
+                                           op->counter, op->sc, stop);
     }
 }
 
 void coarse_apply(fcm_ctx *C, const float *x, float *y)
 {
-    kh_apply_kernel<<<nb(C->coarse->ncell), 256, 0, C->stream>>>(C->coarse->KH, x, y, C->g, C->coarse->ncell);
+    CoarseOp *op = C->coarse;
+    kh_kernel<<<tiles(op->ncell), RT, 0, C->stream>>>(op->KH, x, nullptr, nullptr, y, C->g, op->ncell, 0, op->partial,
+                                                      op->counter, op->sc, nullptr);
 }
 
 }  // namespace fcm

@@ -92,17 +92,28 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o);
 // fcm_capi.cu: operators and the plain PCG on a context's own work stream
 void ctx_apply_K(fcm_ctx *C, const double *x, double *y);
 void ctx_apply_S(fcm_ctx *C, const double *r, double *z);
+// the same, skipped on the device while *stop != 0 (stop may be null)
+void ctx_apply_K_flag(fcm_ctx *C, const double *x, double *y, const int *stop);
+void ctx_apply_S_flag(fcm_ctx *C, const double *r, double *z, const int *stop);
 fcm_status ctx_solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, double *u, fcm_solve_info &info);
 
 // fcm_unet.cu: redirect a network's launches to stream s; returns the previous stream
 cudaStream_t unet_set_stream(fcm_unet *N, cudaStream_t s);
+// identity of a network and of its current activation buffers (changes when they are reallocated)
+void unet_identity(const fcm_unet *N, uint64_t *serial, uint64_t *gen);
 
 // fcm_coarse_op.cu: Galerkin coarse operator K_H = P^T K P on the cell grid
 struct CoarseOp;
 fcm_status coarse_ensure(fcm_ctx *C);
 void coarse_free(CoarseOp *op);
-void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters);
+// start: 0 from zero, 1 from the given y, 2 from the given y scaled by the energy-minimising step
+void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, const int *stop);
 void coarse_apply(fcm_ctx *C, const float *x, float *y);
+double coarse_seconds(const CoarseOp *op);
+
+// fcm_coarse.cu: workspace and captured graph of the flexible PCG, kept between solves
+struct FcgState;
+void fcg_free(FcgState *f);
 
 }  // namespace fcm
 
@@ -158,4 +169,5 @@ struct fcm_ctx {
     int m_nr = 0;
     // coarse operator of the learned correction (built on first use)
     fcm::CoarseOp *coarse = nullptr;
+    fcm::FcgState *fcg = nullptr;
 };

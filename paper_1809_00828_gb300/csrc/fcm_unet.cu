@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -269,6 +270,8 @@ struct fcm_unet {
     std::vector<int64_t> S;   // voxels per level
     std::vector<int> dim;     // nx >> l etc. (cube not required: stored per axis below)
     std::vector<int> lx, ly, lz;
+    // identity of this network and of its activation buffers, for graphs that captured its launches
+    uint64_t serial = 0, act_gen = 0;
     int ch(int l) const { return std::min(base << l, 4 * base); }
     int enc_a(int l) const { return 2 * l; }
     int enc_b(int l) const { return 2 * l + 1; }
@@ -297,6 +300,7 @@ cudaError_t ensure_shape(fcm_unet *N, int B, int nx, int ny, int nz)
 {
     if (N->B == B && N->n[0] == nx && N->n[1] == ny && N->n[2] == nz) return cudaSuccess;
     free_acts(N);
+    ++N->act_gen;
     const int L = N->levels;
     auto resize = [&](std::vector<float *> &v) { v.assign(L, nullptr); };
     for (auto *v : {&N->xin, &N->ea, &N->eA, &N->eb, &N->eB, &N->cat, &N->da, &N->dA, &N->db, &N->dB, &N->gxin, &N->gea,
@@ -399,6 +403,12 @@ uint64_t splitmix(uint64_t &s)
 
 
 namespace fcm {
+void unet_identity(const fcm_unet *N, uint64_t *serial, uint64_t *gen)
+{
+    *serial = N ? N->serial : 0;
+    *gen = N ? N->act_gen : 0;
+}
+
 cudaStream_t unet_set_stream(fcm_unet *N, cudaStream_t s)
 {
     cudaStream_t old = N->stream;
@@ -427,6 +437,8 @@ fcm_status fcm_unet_create(const fcm_unet_desc *d, void *cuda_stream, fcm_unet *
     }
     *out = nullptr;
     fcm_unet *N = new fcm_unet();
+    static std::atomic<uint64_t> next_serial{1};
+    N->serial = next_serial++;
     N->stream = (cudaStream_t)cuda_stream;
     N->in_ch = d->in_ch;
     N->out_ch = d->out_ch;

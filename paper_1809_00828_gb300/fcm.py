@@ -24,7 +24,7 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy",
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
-            "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve")
+            "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -54,7 +54,8 @@ class Info(ctypes.Structure):
                 ("factor_bytes", ctypes.c_int64), ("element_bytes", ctypes.c_int64), ("max_block", ctypes.c_int),
                 ("p", ctypes.c_int), ("setup_seconds", ctypes.c_double), ("precond_seconds", ctypes.c_double),
                 ("n_blocks", ctypes.c_int64), ("n_blocks_fp32", ctypes.c_int64), ("kapply_fmas", ctypes.c_int64),
-                ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double)]
+                ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double),
+                ("coarse_seconds", ctypes.c_double)]
 
 
 class PrecondOpts(ctypes.Structure):
@@ -249,9 +250,11 @@ def _bind_unet(L):
     L.fcm_coarse_prolong.argtypes = [P, P, ctypes.c_double, P]
     L.fcm_coarse_apply.argtypes = [P, P, P]
     L.fcm_fpcg_solve.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
+    L.fcm_fpcg_solve_host.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ip,
+                                      dp]
     for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
               "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
-              "fcm_coarse_apply", "fcm_fpcg_solve"):
+              "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host"):
         getattr(L, f).restype = ctypes.c_int
     _unet_bound = True
 
@@ -363,7 +366,23 @@ def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=T
     return u, its.value, rel.value, st
 
 
+def _solver_fpcg_solve_host(self, net, gamma, b_host, tol, maxit=100000, out=None, check=True, coarse_iters=0):
+    """fpcg_solve with host numpy buffers (float64, n_lattice); copies are inside the call."""
+    _bind_unet(load())
+    b_host = np.ascontiguousarray(b_host, dtype=np.float64)
+    u = out if out is not None else np.empty_like(b_host)
+    its = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = load().fcm_fpcg_solve_host(self.ctx, net.h if net is not None else None, gamma, coarse_iters,
+                                    ctypes.c_void_p(b_host.ctypes.data), tol, maxit, ctypes.c_void_p(u.ctypes.data),
+                                    ctypes.byref(its), ctypes.byref(rel))
+    if check:
+        self._check(st)
+    return u, its.value, rel.value, st
+
+
 Solver.coarse_restrict = _solver_coarse_restrict
 Solver.coarse_prolong = _solver_coarse_prolong
 Solver.coarse_apply = _solver_coarse_apply
 Solver.fpcg_solve = _solver_fpcg_solve
+Solver.fpcg_solve_host = _solver_fpcg_solve_host

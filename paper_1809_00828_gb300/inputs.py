@@ -208,6 +208,11 @@ WORKLOADS = {
     "porous40_64_p2": lambda: workload_porous(12, 64, 2, 40, 1e-10, 3, 1e-8),
     # ~0.35M DOFs: the 32^3 family at 16^3 cells (profiling-sized: ~1.5 GB of block factors)
     "porous40_16_p3": lambda: workload_porous(11, 16, 3, 40, 1e-10, 4, 1e-8),
+    # ~0.8M DOFs: 40 voids, 32^3 cells, p=2 (the size of the learned correction's training cubes;
+    # profiling-sized for the coarse operator: 74 MB of K_H, ~1 GB of FP32 block factors)
+    "porous40_32_p2": lambda: workload_porous(7, 32, 2, 40, 1e-10, 3, 1e-8),
+    # ~12.4M DOFs: 300 voids, 80^3 cells, p=2 (the learned correction's evaluation cube)
+    "porous300_80_p2": lambda: workload_porous(21, 80, 2, 300, 1e-10, 3, 1e-8),
     # trabecular-like voxel domain (Gaussian random field, volume fraction 0.25), 48^3 cells, p=3, 6 strain loads
     "trabecular_48_p3": lambda: workload_trabecular(13, 48, 3),
     # the same family at 24^3 cells (test-sized)

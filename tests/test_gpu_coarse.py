@@ -97,6 +97,15 @@ def test_fpcg_network_start_plus_coarse_cg(porous8):
     x_ref = spla.spsolve(P.csr().tocsc(), P.rhs())
     assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
     net.close()
+    # a second network of another depth: the solver's captured iteration must be rebuilt for it
+    net2 = fcm.UNet(in_ch=4, out_ch=3, base=3, levels=3, seed=10)
+    u2, its2, rel2, st2 = s.fpcg_solve(net2, 1.0, b, w.tol, 4000, coarse_iters=5)
+    assert st2 == 0 and rel2 <= w.tol * 1.0001
+    assert P.energy_error(x_ref, u2.cpu().numpy()[P.free_lat]) < 1e-6
+    net2.close()
+    # and back to no network, same coarse steps
+    u3, its3, rel3, st3 = s.fpcg_solve(None, 0.0, b, w.tol, 4000, coarse_iters=5)
+    assert st3 == 0 and P.energy_error(x_ref, u3.cpu().numpy()[P.free_lat]) < 1e-6
 
 
 def test_fpcg_rejects_no_network_and_no_coarse_steps(porous8):
