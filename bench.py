@@ -15,7 +15,8 @@ error of this form against it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcm|reference]
                   [--workload NAME] [--form coarse|pcg] [--precision fp64|mixed]
-                  [--coarse-iters K] [--net CHECKPOINT]
+                  [--coarse-iters K] [--net CHECKPOINT] [--loads traction|strain6]
+                  [--blocks vertex|element] [--eta-bar X]
 
 N > 1 runs independent replicas (one per GPU, launched by torchrun); the
 solve has no data-path collective.  `--impl reference` times the CPU oracle.
@@ -158,8 +159,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     w = _workload(args.workload)
-    # the full workload's iteration count and per-iteration work come from the problem sizes,
-    # not from the GPU: counted on the host from the oracle's own block rule
+    # per-iteration work is counted on the host from the problem sizes; the iteration count that
+    # scales the per-iteration time is --ref-iterations (a full oracle solve at this size would
+    # take hours)
     gpu_like_iters = args.ref_iterations
     kf, sf = _host_work_counts(w)
     steps = []
@@ -172,7 +174,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": _describe(w), "precision": "fp64"},
+            "config": {"workload": _describe(w, args), "precision": "fp64"},
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -200,11 +202,22 @@ def _host_work_counts(w):
     return kf, sf
 
 
-def _describe(w):
-    return (f"{w.name}: {w.n[0]}x{w.n[1]}x{w.n[2]} cells, p={w.p}, alpha={w.alpha:g}, "
-            f"{0 if w.geometry.spheres is None else len(w.geometry.spheres)} spherical voids, "
+def _describe(w, args):
+    g = w.geometry
+    shape = (f"{len(g.spheres)} spherical voids" if g.spheres is not None else
+             f"voxel image {'x'.join(str(v) for v in g.voxels.shape)} (solid fraction {g.voxels.mean():.2f})"
+             if g.voxels is not None else "no voids")
+    return (f"{w.name}: {w.n[0]}x{w.n[1]}x{w.n[2]} cells, p={w.p}, alpha={w.alpha:g}, {shape}, "
             f"octree depth {w.geometry.octree_depth}, tol {w.tol:g}, E={w.E:g}, nu={w.nu:g}, z=0 clamped, "
-            f"unit traction on z=1, vertex-patch blocks, eps=1e-13")
+            f"{'unit traction on z=1' if args.loads == 'traction' else 'six unit-strain load cases'}, "
+            f"{_blocks(args)}, eps=1e-13")
+
+
+def _blocks(args):
+    if args.blocks == "element":
+        return (f"element blocks for the cells with eta_T < {args.eta_bar:g} and diagonal scaling of the DOFs "
+                f"in no block")
+    return "vertex-patch blocks"
 
 
 def _form(args, net):
@@ -248,9 +261,13 @@ def run_fcm(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = _workload(args.workload)
     s = fcm.Solver(w)
-    s.precond_build(precision=args.precision)
-    b = s.rhs()
-    u = s.empty()
+    s.precond_build(precision=args.precision, blocks=args.blocks, eta_bar=args.eta_bar)
+    n = s.n
+    # load cases: 0 = traction on z = 1; 1..6 = unit Voigt strains (one solve of all six)
+    cases = [0] if args.loads == "traction" else [1, 2, 3, 4, 5, 6]
+    nrhs = len(cases)
+    b = torch.cat([s.rhs(k) for k in cases])
+    u = s.empty(nrhs)
     stream = torch.cuda.current_stream()
     net, gamma = None, 0.0
     if args.form == "coarse" and args.net:
@@ -258,8 +275,13 @@ def run_fcm(args, rank, world, local_rank):
         net, gamma = learned.load(args.net)
 
     def solve(out):
+        """One step: every right-hand side solved; returns the largest iteration count and residual."""
         if args.form == "coarse":
-            _, its, rel, _ = s.fpcg_solve(net, gamma, b, w.tol, args.maxit, out=out, coarse_iters=args.coarse_iters)
+            its, rel = 0, 0.0
+            for k in range(nrhs):
+                _, i, r, _ = s.fpcg_solve(net, gamma, b[k * n:(k + 1) * n], w.tol, args.maxit,
+                                          out=out[k * n:(k + 1) * n], coarse_iters=args.coarse_iters)
+                its, rel = max(its, i), max(rel, r)
         else:
             _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=out)
         return its, rel
@@ -275,12 +297,9 @@ def run_fcm(args, rank, world, local_rank):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    per = []
     iters = []
     for _ in range(args.steps):
         its, rel = solve(u)
-        li = s.last_solve()
-        per.append(li["seconds"])
         iters.append(its)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -296,7 +315,7 @@ def run_fcm(args, rank, world, local_rank):
     last = s.last_solve()
 
     # dominant kernel: the Schwarz block apply (8 colour launches), timed live on the stream
-    r = b.clone()
+    r = b[:n].clone()
     z = s.empty()
     for _ in range(3):
         s.apply_S(r, out=z)
@@ -318,7 +337,6 @@ def run_fcm(args, rank, world, local_rank):
     t_k = e0.elapsed_time(e1) / 1e3 / reps
 
     peaks, peak_kind = _peaks()
-    n = info["n_lattice"]
     s_flops = 2.0 * info["sapply_fmas"]
     # algorithmic HBM bytes of one S apply: distinct stored factors + gather of r + read-modify-write of z
     s_bytes = info["factor_bytes"] + 8.0 * n * 3
@@ -326,7 +344,7 @@ def run_fcm(args, rank, world, local_rank):
     fp64_peak = fp64_peak_tflops(sm_mhz)
     achieved_tf = s_flops / t_s / 1e12
     achieved_gbs = s_bytes / t_s / 1e9
-    kernel = "schwarz_colour_kernel<3> (8 colour launches per S apply)"
+    kernel = f"schwarz_colour_kernel<{w.p}> (8 colour launches per S apply)"
     if args.precision == "fp64":
         # FP64 factors: one FP64 multiply-add per 8-byte entry; the FP64 pipe saturates first
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -358,22 +376,25 @@ def run_fcm(args, rank, world, local_rank):
         kh_bytes = nc * (63 * 9 * 4 + 2 * 3 * 4)
         roofline.update({"kh_apply_us": t_h * 1e6, "kh_algorithmic_bytes": kh_bytes,
                          "kh_achieved_gbs": kh_bytes / t_h / 1e9,
-                         "kh_note": "K_H (74 MB at 32^3 cells) stays in L2 (129 MB) across a coarse solve, "
-                                    "so this rate can exceed the HBM copy peak"})
+                         "kh_note": f"K_H ({nc * 63 * 9 * 4 / 1e6:.0f} MB) "
+                                    + ("stays in L2 (129 MB) across a coarse solve, so this rate can exceed the "
+                                       "HBM copy peak" if nc * 63 * 9 * 4 < 100e6 else "streams from HBM")})
     roofline.update({"s_apply_ms": t_s * 1e3, "k_apply_ms": t_k * 1e3,
                      "k_apply_fp64_tflops": 2.0 * info["kapply_fmas"] / t_k / 1e12,
                      "k_apply_fp64_frac": 2.0 * info["kapply_fmas"] / t_k / 1e12 / fp64_peak,
                      "algorithmic_bytes_per_s_apply": s_bytes})
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside the timed region)
-    b_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    b_host = torch.empty(n * nrhs, dtype=torch.float64, pin_memory=True)
     b_host.copy_(b)
-    u_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    u_host = torch.empty(n * nrhs, dtype=torch.float64, pin_memory=True)
     bh = b_host.numpy()
     uh = u_host.numpy()
     def solve_host():
         if args.form == "coarse":
-            s.fpcg_solve_host(net, gamma, bh, w.tol, args.maxit, out=uh, coarse_iters=args.coarse_iters)
+            for k in range(nrhs):
+                s.fpcg_solve_host(net, gamma, bh[k * n:(k + 1) * n], w.tol, args.maxit,
+                                  out=uh[k * n:(k + 1) * n], coarse_iters=args.coarse_iters)
         else:
             s.pcg_solve_host(bh, w.tol, args.maxit, out=uh)
 
@@ -386,22 +407,25 @@ def run_fcm(args, rank, world, local_rank):
     e2e = (time.perf_counter() - t0) / e2e_steps
 
     its_med = int(statistics.median(iters))
-    launches_per_solve = _launches_per_solve(args, its_med, net)
+    launches_per_solve = _launches_per_solve(args, its_med, net) * (nrhs if args.form == "coarse" else 1)
     line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-            "config": {"workload": _describe(w), "form": _form(args, net), "precision": args.precision,
-                       "n_free": info["n_free"],
+            "config": {"workload": _describe(w, args), "loads": args.loads, "form": _form(args, net),
+                       "precision": args.precision, "n_free": info["n_free"],
                        "iterations": its_med, "relres": rel, "true_relres": last["true_relres"],
+                       "fell_back_to_plain_pcg": bool(last["fallback"]) if args.form == "coarse" else None,
+                       "flexible_iterations": last["flexible_iterations"] if args.form == "coarse" else None,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"inputs larger than L2: factor pool {info['factor_bytes'] / 2**30:.2f} GiB, "
                              f"element matrices {info['element_bytes'] / 2**30:.2f} GiB",
                        "n_blocks": info["n_blocks"], "n_factors": info["n_factors"],
+                       "n_factors_fp32": info["n_blocks_fp32"], "n_jacobi_dofs": info["n_jacobi"],
                        "setup_s": info["setup_seconds"], "precond_s": info["precond_seconds"],
                        "coarse_operator_s": info["coarse_seconds"],
-                       "device_seconds_median": statistics.median(per)},
+                       "load_cases": cases},
             "roofline": roofline,
-            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs},
             "gpu_launches": launches_per_solve * args.steps,
             "clocks": clk}
     its64 = its_med
@@ -416,19 +440,22 @@ def run_fcm(args, rank, world, local_rank):
             tm = []
             for _ in range(nrep):
                 _, itsm, _, _ = s.pcg_solve(b, w.tol, args.maxit)
-                tm.append(s.last_solve()["seconds"])
+                tm.append(s.last_solve()["seconds"])  # device time of the call (all right-hand sides)
             line["config"]["plain_mixed"] = {"seconds": statistics.median(tm), "iterations": itsm,
                                              "speedup_of_this_form": statistics.median(tm) / (ms_per_step / 1e3)}
-        s.precond_build(precision="fp64")
+        s.precond_build(precision="fp64", blocks=args.blocks, eta_bar=args.eta_bar)
         x64, its64, _, _ = s.pcg_solve(b, w.tol, args.maxit)
         t64 = []
         for _ in range(nrep):
             s.pcg_solve(b, w.tol, args.maxit, out=x64)
             t64.append(s.last_solve()["seconds"])
-        e = x - x64
-        num = torch.dot(e, s.apply_K(e)).item()
-        den = torch.dot(x64, s.apply_K(x64)).item()
-        line["config"]["energy_error_vs_fp64"] = (abs(num) / den) ** 0.5
+        errs = []
+        for k in range(nrhs):
+            e = x[k * n:(k + 1) * n] - x64[k * n:(k + 1) * n]
+            num = torch.dot(e, s.apply_K(e)).item()
+            den = torch.dot(x64[k * n:(k + 1) * n], s.apply_K(x64[k * n:(k + 1) * n])).item()
+            errs.append((abs(num) / den) ** 0.5)
+        line["config"]["energy_error_vs_fp64"] = max(errs)
         line["config"]["plain_fp64"] = {"seconds": statistics.median(t64), "iterations": its64,
                                         "speedup_of_this_form": statistics.median(t64) / (ms_per_step / 1e3)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -436,6 +463,9 @@ def run_fcm(args, rank, world, local_rank):
         kf = info["n_cells_active"] * (3 * (w.p + 1) ** 3) ** 2
         sf = info["sapply_fmas"]
         v, sample, _ = oracle_sample(w, its64, sf, kf)
+        if nrhs > 1:
+            v *= nrhs
+            sample += f"; times {nrhs} right-hand sides"
         line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
     if net is not None:
         net.close()
@@ -461,8 +491,15 @@ def main():
     ap.add_argument("--coarse-iters", type=int, default=20)
     ap.add_argument("--net", default=None, help="U-Net checkpoint whose prediction starts the coarse solve")
     ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--loads", default="traction", choices=["traction", "strain6"],
+                    help="traction: the z = 1 traction load; strain6: the six unit-strain load cases in one step")
+    ap.add_argument("--blocks", default="vertex", choices=["vertex", "element"],
+                    help="Schwarz blocks: vertex patches, or the paper's element blocks with --eta-bar")
+    ap.add_argument("--eta-bar", type=float, default=1.0,
+                    help="element blocks for the cells with volume fraction below this; the rest diagonal")
     ap.add_argument("--ref-iterations", type=int, default=None,
-                    help="iteration count used to scale the reference arm (default: a GPU-free estimate)")
+                    help="iteration count that scales the reference arm's per-iteration time (default 877, the plain "
+                         "FP64 Schwarz-PCG count of porous40_32_p3, which the oracle's algorithm shares)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -102,15 +102,18 @@ typedef struct {
     int p;
     double setup_seconds;     /* host+device time of fcm_setup                         */
     double precond_seconds;   /* time of the last fcm_precond_build                    */
-    int64_t n_blocks;         /* vertex patches with at least one free DOF             */
+    int64_t n_blocks;         /* blocks (patches or elements) with at least one free DOF */
     int64_t n_blocks_fp32;    /* of the stored factors, those kept in FP32             */
     int64_t kapply_fmas;      /* multiply-adds of one K apply (sum over active cells)  */
     int64_t sapply_fmas;      /* multiply-adds of one S apply (sum of block box sizes^2) */
     double max_block_cond;    /* largest retained condition number of a block          */
     double coarse_seconds;    /* assembly time of the coarse operator K_H (0 until built) */
+    int64_t n_jacobi;         /* free DOFs in no block (diagonal part of S), last build   */
 } fcm_info_t;
 
 enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1 };
+
+enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
 
 /* Preconditioner options (Algorithm 1).
  *   eps: pseudo-inverse threshold, eigenvalues <= eps * lambda_max are dropped
@@ -119,11 +122,24 @@ enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1 };
  *   precision: FCM_PREC_FP64 stores and applies every factor in FP64;
  *        FCM_PREC_MIXED stores factors in FP32 except blocks whose retained
  *        condition number exceeds cond_fp64 (kept in FP64).
- *   cond_fp64: threshold for FCM_PREC_MIXED (default 1e7). */
+ *   cond_fp64: threshold for FCM_PREC_MIXED (default 1e7).
+ *   block_rule: FCM_BLOCKS_VERTEX (0, default): one block per grid vertex,
+ *        the free functions carried by the vertex and by the edges, faces and
+ *        cells whose closure contains it (every free DOF is covered).
+ *        FCM_BLOCKS_ELEMENT (3): the paper's element blocks (Sec. 3.2,
+ *        "Optimizing the number of blocks"): for every active cell with volume
+ *        fraction eta_T < eta_bar, all functions supported on the cell; the free
+ *        DOFs in no block get Algorithm 1's diagonal scaling 1 / K_ll.
+ *        eta_bar = 0 gives pure Jacobi; eta_bar > 1 blocks every active cell.
+ *   eta_bar: threshold of FCM_BLOCKS_ELEMENT (ignored by FCM_BLOCKS_VERTEX).
+ * A zero-initialised struct with eps, precision and cond_fp64 set selects
+ * vertex patches. */
 typedef struct {
     double eps;
     int precision;
     double cond_fp64;
+    int block_rule;
+    double eta_bar;
 } fcm_precond_opts;
 
 /* Solver result details. */
@@ -156,13 +172,16 @@ fcm_status fcm_info(const fcm_ctx *ctx, fcm_info_t *out);
  *         stiffness of Eq. (1) (equal to -K u_k for the linear field u_k = E_k x). */
 fcm_status fcm_rhs(const fcm_ctx *ctx, int load_case, double *b_dev);
 
-/* Build the Additive-Schwarz preconditioner (Algorithm 1) with vertex-patch
- * blocks: for each grid vertex v, the free functions carried by v and by the
- * edges, faces and cells whose closure contains v.  Extracts A_B = K[B,B],
- * computes its eigendecomposition, keeps lambda_k > eps * max lambda and
- * stores A_B+^-1.  Identical blocks (patches of uncut cells with the same
- * boundary pattern) share one stored factor.  opts may be NULL (eps 1e-13,
- * FP64). */
+/* Build the Additive-Schwarz preconditioner (Algorithm 1) with the blocks of
+ * opts->block_rule (vertex patches by default, or the paper's element blocks
+ * with the eta_bar threshold and diagonal scaling of uncovered DOFs).
+ * Extracts A_B = K[B,B], computes its eigendecomposition, keeps
+ * lambda_k > eps * max lambda and stores A_B+^-1.  Identical blocks (blocks of
+ * uncut cells with the same boundary pattern) share one stored factor.  opts
+ * may be NULL (eps 1e-13, FP64, vertex patches).  Returns FCM_EINVAL for an
+ * unknown rule or precision or a negative or NaN eta_bar.  Invalidates the
+ * captured solver graphs of the context (they are captured again by the next
+ * solve). */
 fcm_status fcm_precond_build(fcm_ctx *ctx, const fcm_precond_opts *opts);
 
 /* Preconditioned CG, x0 = 0, stopping when ||S r_i|| / ||S b|| <= tol

@@ -74,7 +74,6 @@ void apply_K_dev(fcm_ctx *C, const double *x, double *y, const int *done)
 
 void apply_S_dev(fcm_ctx *C, const double *r, double *z, const int *done)
 {
-    fcm::launch_zero(z, C->nlat, done, C->stream);
     fcm::launch_schwarz_apply(C->p, C->g, r, z, C->d_f64, C->d_f32, C->plan, done, C->stream);
 }
 
@@ -164,7 +163,7 @@ void free_ctx(fcm_ctx *C)
 {
     if (!C) return;
     destroy_graph(C);
-    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32, C->d_patches, C->d_batches, C->d_eta,
+    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32, C->d_patches, C->d_batches, C->d_eta, C->d_jac,
                     C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
                     C->d_out2};
     for (void *q : ptrs)
@@ -313,7 +312,26 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     SETUP_CUDA(cudaMallocHost((void **)&C->h_s, sizeof(CgScalars)));
     SETUP_CUDA(cudaStreamSynchronize(st));
 #undef SETUP_CUDA
-    // the element matrices now live on the device only
+    // diagonal of K (Algorithm 1's diagonal scaling for DOFs in no block), then the element
+    // matrices live on the device only
+    hp.kdiag.assign(hp.nlat, 0.0);
+    {
+        const int q = hp.p + 1, ne = hp.ne;
+        for (int64_t ci = 0; ci < hp.ncells; ++ci) {
+            const int el = hp.cell_elem[ci];
+            if (el < 0) continue;
+            const double *Ke = el == 0 ? hp.Kref.data() : hp.Kcut.data() + (size_t)(el - 1) * ne * ne;
+            const int cx = (int)(ci % hp.n[0]), cy = (int)((ci / hp.n[0]) % hp.n[1]),
+                      cz = (int)(ci / ((int64_t)hp.n[0] * hp.n[1]));
+            for (int iz = 0; iz < q; ++iz)
+                for (int iy = 0; iy < q; ++iy)
+                    for (int ix = 0; ix < q; ++ix) {
+                        const int I = ix + q * (iy + q * iz);
+                        const int64_t node = (hp.p * cx + ix) + (int64_t)hp.M[0] * ((hp.p * cy + iy) + (int64_t)hp.M[1] * (hp.p * cz + iz));
+                        for (int a = 0; a < 3; ++a) hp.kdiag[3 * node + a] += Ke[(size_t)(3 * I + a) * ne + 3 * I + a];
+                    }
+        }
+    }
     std::vector<double>().swap(hp.Kcut);
     C->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = C;
@@ -347,6 +365,7 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->sapply_fmas = C->sapply_fmas;
     out->max_block_cond = C->max_cond;
     out->coarse_seconds = fcm::coarse_seconds(C->coarse);
+    out->n_jacobi = C->n_jacobi;
     return FCM_OK;
 }
 
@@ -377,13 +396,19 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     o.eps = 1e-13;
     o.precision = FCM_PREC_FP64;
     o.cond_fp64 = 1e7;
+    o.block_rule = FCM_BLOCKS_VERTEX;
+    o.eta_bar = 1.0;
     if (opts) o = *opts;
-    if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED) || !(o.cond_fp64 > 0.0)) {
+    if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED) || !(o.cond_fp64 > 0.0) ||
+        (o.block_rule != FCM_BLOCKS_VERTEX && o.block_rule != FCM_BLOCKS_ELEMENT) ||
+        (o.block_rule == FCM_BLOCKS_ELEMENT && !(o.eta_bar >= 0.0))) {
         C->err = "fcm_precond_build: invalid options";
         return FCM_EINVAL;
     }
     StreamScope sc(C);
+    // captured graphs hold the addresses of the plan and factor pools being replaced
     destroy_graph(C);
+    fcm::fcg_forget_graph(C->fcg);
     C->have_precond = false;
     std::string e;
     try {
@@ -447,7 +472,6 @@ static fcm_status solve_multi(fcm_ctx *C, const double *rhs, int nr, double tol,
     API_CUDA(C, cudaMemcpyAsync(C->d_ms, C->h_ms, sizeof(CgScalars) * nr, cudaMemcpyHostToDevice, st));
     API_CUDA(C, cudaEventRecord(C->ev_t0, st));
     for (int k = 0; k < nr; ++k) fcm::cg_init_kernels(w[k], st);
-    fcm::launch_zero(Z, (int64_t)nr * n, nullptr, st);
     fcm::launch_schwarz_apply_multi(C->p, C->g, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, nullptr, st);
     for (int k = 0; k < nr; ++k) fcm::cg_after_first_S(w[k], st);
     for (int it = 0;; ++it) {
@@ -460,7 +484,6 @@ static fcm_status solve_multi(fcm_ctx *C, const double *rhs, int nr, double tol,
         }
         for (int k = 0; k < nr; ++k) apply_K_dev(C, w[k].p, w[k].q, &C->d_ms[k].done);
         for (int k = 0; k < nr; ++k) fcm::cg_after_K(w[k], st);
-        fcm::launch_zero(Z, (int64_t)nr * n, nullptr, st);
         fcm::launch_schwarz_apply_multi(C->p, C->g, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, nullptr, st);
         for (int k = 0; k < nr; ++k) fcm::cg_after_S(w[k], st);
         API_CUDA(C, cudaGetLastError());

@@ -69,6 +69,14 @@ const int *stop_flag(const FcgState *F)
     return reinterpret_cast<const int *>(reinterpret_cast<const char *>(F->d) + offsetof(FcgScalars, stop));
 }
 
+void fcg_forget_graph(FcgState *F)
+{
+    if (!F) return;
+    if (F->graph) cudaGraphExecDestroy(F->graph);
+    F->graph = nullptr;
+    F->coarse_iters = -1;
+}
+
 void fcg_free(FcgState *F)
 {
     if (!F) return;

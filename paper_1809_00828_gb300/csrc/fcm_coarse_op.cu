@@ -194,7 +194,9 @@ __device__ bool grid_sums2(double &x, double &y, double *partial, unsigned *coun
 
 // y = K_H v over a tile of 32 cells per CTA; the 8 warps split the 63 stored offsets, each
 // stored block used twice: directly (row cell c, column cell c + off) and transposed for the
-// mirrored offset (row c, column c - off), since K_H is symmetric.
+// mirrored offset (row c, column c - off), since K_H is symmetric.  The loads carry no
+// branches: a neighbour outside the grid is replaced by the cell itself (an in-bounds address)
+// and its vector value weighted by 0, so all 24 loads of an offset can be in flight at once.
 //   mode 0: v = x
 //   mode 1: v = x + beta xb (beta = sc[3]); v is written to pout; pq = v.y, alpha = rz / pq
 //   mode 2: v = x;                          v is written to pout; pq = v.y, alpha = rz / pq
@@ -206,44 +208,54 @@ __global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, co
     STOP_RETURN;
     __shared__ float red[kTileWarps][3][kTileCells];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * kTileCells + lane;
-    const bool live = c < ncell;
+    const int64_t c0 = (int64_t)blockIdx.x * kTileCells + lane;
+    const bool live = c0 < ncell;
+    const int64_t c = live ? c0 : ncell - 1;
     const float beta = mode == 1 ? (float)sc[3] : 0.f;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int cx = live ? (int)(c % nx) : 0, cy = live ? (int)((c / nx) % ny) : 0,
-              cz = live ? (int)(c / ((int64_t)nx * ny)) : 0;
+    const int cx = (int)(c % nx), cy = (int)((c / nx) % ny), cz = (int)(c / ((int64_t)nx * ny));
+    // bit d + 2 set when the coordinate + d lies in the grid, d = -2..2
+    unsigned mx = 0, my = 0, mz = 0;
+#pragma unroll
+    for (int d = -2; d <= 2; ++d) {
+        mx |= (unsigned)(cx + d >= 0 && cx + d < nx) << (d + 2);
+        my |= (unsigned)(cy + d >= 0 && cy + d < ny) << (d + 2);
+        mz |= (unsigned)(cz + d >= 0 && cz + d < nz) << (d + 2);
+    }
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     if (live) {
+#pragma unroll 2
         for (int s = w; s < kStored; s += kTileWarps) {
             const int oi = kCenter + s, dx = oi % 5 - 2, dy = (oi / 5) % 5 - 2, dz = oi / 25 - 2;
             const int64_t d = dx + (int64_t)nx * (dy + (int64_t)ny * dz);
-            const float *B = KH + (int64_t)s * 9 * ncell;
-            if (cx + dx >= 0 && cx + dx < nx && cy + dy >= 0 && cy + dy < ny && cz + dz >= 0 && cz + dz < nz) {
-                const int64_t n = c + d;
-                float v0 = __ldg(x + n), v1 = __ldg(x + ncell + n), v2 = __ldg(x + 2 * ncell + n);
-                if (mode == 1) {
-                    v0 = fmaf(beta, __ldg(xb + n), v0);
-                    v1 = fmaf(beta, __ldg(xb + ncell + n), v1);
-                    v2 = fmaf(beta, __ldg(xb + 2 * ncell + n), v2);
-                }
-                const float *Bc = B + c;
-                a0 = fmaf(__ldg(Bc), v0, fmaf(__ldg(Bc + ncell), v1, fmaf(__ldg(Bc + 2 * ncell), v2, a0)));
-                a1 = fmaf(__ldg(Bc + 3 * ncell), v0, fmaf(__ldg(Bc + 4 * ncell), v1, fmaf(__ldg(Bc + 5 * ncell), v2, a1)));
-                a2 = fmaf(__ldg(Bc + 6 * ncell), v0, fmaf(__ldg(Bc + 7 * ncell), v1, fmaf(__ldg(Bc + 8 * ncell), v2, a2)));
+            const bool vd = (mx >> (dx + 2)) & (my >> (dy + 2)) & (mz >> (dz + 2)) & 1u;
+            const bool vm = s > 0 && ((mx >> (2 - dx)) & (my >> (2 - dy)) & (mz >> (2 - dz)) & 1u);
+            const int64_t n = vd ? c + d : c, m = vm ? c - d : c;
+            const float wd = vd ? 1.f : 0.f, wm = vm ? 1.f : 0.f;
+            const float *Bc = KH + (int64_t)s * 9 * ncell + c;
+            const float *Bm = KH + (int64_t)s * 9 * ncell + m;
+            float u0 = __ldg(x + n), u1 = __ldg(x + ncell + n), u2 = __ldg(x + 2 * ncell + n);
+            float v0 = __ldg(x + m), v1 = __ldg(x + ncell + m), v2 = __ldg(x + 2 * ncell + m);
+            if (mode == 1) {
+                u0 = fmaf(beta, __ldg(xb + n), u0);
+                u1 = fmaf(beta, __ldg(xb + ncell + n), u1);
+                u2 = fmaf(beta, __ldg(xb + 2 * ncell + n), u2);
+                v0 = fmaf(beta, __ldg(xb + m), v0);
+                v1 = fmaf(beta, __ldg(xb + ncell + m), v1);
+                v2 = fmaf(beta, __ldg(xb + 2 * ncell + m), v2);
             }
-            if (s > 0 && cx - dx >= 0 && cx - dx < nx && cy - dy >= 0 && cy - dy < ny && cz - dz >= 0 && cz - dz < nz) {
-                const int64_t m = c - d;
-                float v0 = __ldg(x + m), v1 = __ldg(x + ncell + m), v2 = __ldg(x + 2 * ncell + m);
-                if (mode == 1) {
-                    v0 = fmaf(beta, __ldg(xb + m), v0);
-                    v1 = fmaf(beta, __ldg(xb + ncell + m), v1);
-                    v2 = fmaf(beta, __ldg(xb + 2 * ncell + m), v2);
-                }
-                const float *Bm = B + m;
-                a0 = fmaf(__ldg(Bm), v0, fmaf(__ldg(Bm + 3 * ncell), v1, fmaf(__ldg(Bm + 6 * ncell), v2, a0)));
-                a1 = fmaf(__ldg(Bm + ncell), v0, fmaf(__ldg(Bm + 4 * ncell), v1, fmaf(__ldg(Bm + 7 * ncell), v2, a1)));
-                a2 = fmaf(__ldg(Bm + 2 * ncell), v0, fmaf(__ldg(Bm + 5 * ncell), v1, fmaf(__ldg(Bm + 8 * ncell), v2, a2)));
-            }
+            u0 *= wd;
+            u1 *= wd;
+            u2 *= wd;
+            v0 *= wm;
+            v1 *= wm;
+            v2 *= wm;
+            a0 = fmaf(__ldg(Bc), u0, fmaf(__ldg(Bc + ncell), u1, fmaf(__ldg(Bc + 2 * ncell), u2, a0)));
+            a1 = fmaf(__ldg(Bc + 3 * ncell), u0, fmaf(__ldg(Bc + 4 * ncell), u1, fmaf(__ldg(Bc + 5 * ncell), u2, a1)));
+            a2 = fmaf(__ldg(Bc + 6 * ncell), u0, fmaf(__ldg(Bc + 7 * ncell), u1, fmaf(__ldg(Bc + 8 * ncell), u2, a2)));
+            a0 = fmaf(__ldg(Bm), v0, fmaf(__ldg(Bm + 3 * ncell), v1, fmaf(__ldg(Bm + 6 * ncell), v2, a0)));
+            a1 = fmaf(__ldg(Bm + ncell), v0, fmaf(__ldg(Bm + 4 * ncell), v1, fmaf(__ldg(Bm + 7 * ncell), v2, a1)));
+            a2 = fmaf(__ldg(Bm + 2 * ncell), v0, fmaf(__ldg(Bm + 5 * ncell), v1, fmaf(__ldg(Bm + 8 * ncell), v2, a2)));
         }
     }
     red[w][0][lane] = a0;

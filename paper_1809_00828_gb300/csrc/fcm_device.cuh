@@ -13,10 +13,11 @@ struct fcm_ctx;
 
 namespace fcm {
 
-// One vertex patch (Schwarz block) as seen by the block-apply kernel.
+// One Schwarz block as seen by the block-apply kernel.
 struct PatchRec {
     int64_t off;   // element offset of the block factor in the factor pool
-    int32_t v;     // linear vertex index v_x + (n_x+1)(v_y + (n_y+1) v_z)
+    int32_t v;     // vertex patches: linear vertex index v_x + (n_x+1)(v_y + (n_y+1) v_z);
+                   // element blocks: linear cell index c_x + n_x (c_y + n_y c_z)
     int32_t prec;  // 0: factor stored in FP64, 1: FP32
 };
 
@@ -41,12 +42,13 @@ struct KCells {
     SfTables sf;
 };
 
-// Launch plan of the Schwarz apply.  Patches are grouped into batches that
-// share one stored factor (up to 8 patches, same colour and precision) or
-// hold a single patch; a segment is a run of batches launched together.
-// Segments are ordered by colour, so the colours run one after another.
+// Launch plan of the Schwarz apply.  Blocks are grouped into batches that
+// share one stored factor (up to 8 blocks, same colour and precision); a block
+// with its own factor is split into row tiles, one work item each.  A segment
+// is a run of work items launched together; segments are ordered by colour,
+// so the colours run one after another.
 struct SchwarzSeg {
-    int colour;   // vertex parity colour 0..7
+    int colour;   // parity colour 0..7 of the vertex or cell
     int prec;     // 0 FP64 factors, 1 FP32 factors
     int G;        // 8: shared-factor batches, 1: single patches
     int first;    // first batch of the segment
@@ -54,16 +56,23 @@ struct SchwarzSeg {
 };
 struct SchwarzPlan {
     const PatchRec *patches;  // patch records, batch by batch
-    const int2 *batches;      // (first patch, patch count)
+    const int2 *batches;      // (first block, count or row tile | kind << 8)
     int nseg;
     SchwarzSeg seg[32];
+    int rule;                 // 0 vertex patches, 3 element blocks (FCM_BLOCKS_*)
+    int rows;                 // rows per work item of a block with its own factor (row tiles)
+    const double *jac;        // 1 / K_ll for the free DOFs in no block, 0 elsewhere (lattice); null if none
 };
 
-// Launchers (all asynchronous on `s`).  `done` may be null.
+// Launchers (all asynchronous on `s`).  `done` may be null.  The Schwarz launchers overwrite z
+// with S r (its diagonal part first, then the blocks colour by colour).
 void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
                     const KCells &kc, const int *done, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
                           const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
+// Rows per work item when a block with its own factor is split into row tiles (fixed by the
+// launch shape of the Schwarz kernels for degree p and block rule).
+int schwarz_rows_per_item(int p, int rule);
 // nr <= 8 right-hand sides stored nlat apart (p = 4 needs FP32 factors)
 void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,
                                 const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
@@ -114,6 +123,8 @@ double coarse_seconds(const CoarseOp *op);
 // fcm_coarse.cu: workspace and captured graph of the flexible PCG, kept between solves
 struct FcgState;
 void fcg_free(FcgState *f);
+// drop the captured flexible-CG graph (it holds the addresses of the Schwarz plan and factors)
+void fcg_forget_graph(FcgState *f);
 
 }  // namespace fcm
 
@@ -145,6 +156,8 @@ struct fcm_ctx {
     float *d_f32 = nullptr;          // FP32 factor pool (mixed precision)
     fcm::PatchRec *d_patches = nullptr;
     int2 *d_batches = nullptr;
+    double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
+    int64_t n_jacobi = 0;
     fcm::SchwarzPlan plan = {};
     int64_t n_factors = 0, factor_bytes = 0, n_fp32_factors = 0;
     double max_cond = 0.0;

@@ -37,7 +37,8 @@ struct HostProblem {
     std::vector<int32_t> cell_elem; // -1 inactive, 0 uncut (reference matrix), 1+k k-th cut cell
     std::vector<double> eta;        // volume fraction per cell
     std::vector<double> Kref;       // ne x ne
-    std::vector<double> Kcut;       // ncut x ne x ne
+    std::vector<double> Kcut;       // ncut x ne x ne (released once uploaded)
+    std::vector<double> kdiag;      // diagonal of K per lattice DOF (sum over the active cells)
     int64_t ncut = 0;
     int64_t nactive = 0;
     std::vector<uint8_t> mask;      // per lattice DOF: 1 = free

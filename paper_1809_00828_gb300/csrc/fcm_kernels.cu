@@ -2,10 +2,11 @@
 //  * element-by-element stiffness apply y = K x (Sec. 2.1 Eq. (1)), one CTA
 //    per active cell, cells processed in 8 parity colours so that cells of one
 //    launch share no lattice DOF and the scatter needs no atomics;
-//  * Additive-Schwarz apply z = sum_B R_B^T A_B+^-1 R_B r (Sec. 3.1 Eq. (5)):
-//    gather r over the vertex patch box, dense symmetric block apply, scatter
-//    into z, patches processed in 8 parity colours (patches of one colour are
-//    DOF-disjoint).
+//  * Additive-Schwarz apply z = D r + sum_B R_B^T A_B+^-1 R_B r (Sec. 3.1
+//    Eq. (5), Algorithm 1): diagonal part D for the DOFs in no block, then
+//    gather r over the block box, dense symmetric block apply, scatter into z,
+//    blocks (vertex patches or element blocks) processed in 8 parity colours
+//    (blocks of one colour are DOF-disjoint).
 #include <cuda_runtime.h>
 
 #include "fcm_device.cuh"
@@ -17,6 +18,36 @@ namespace {
 __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
 // One thread per row up to 512 rows; larger blocks loop over rows.
 __host__ __device__ constexpr int threads_for(int rows) { return round32(rows) < 512 ? round32(rows) : 512; }
+
+// Lattice width of the largest block box: vertex patches span 2p - 1 nodes per axis, element
+// blocks p + 1 (the wider of the two at p = 1).
+__host__ __device__ constexpr int box_width(int P) { return 2 * P - 1 > P + 1 ? 2 * P - 1 : P + 1; }
+
+// Threads of a Schwarz CTA: one per row of the largest block of the rule.
+__host__ __device__ constexpr int schwarz_threads(int P, int rule)
+{
+    return rule == 3 ? threads_for(3 * (P + 1) * (P + 1) * (P + 1)) : threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1));
+}
+
+// Lattice box of block `id`: rule 0, the vertex patch of vertex id, [p v - (p-1), p v + (p-1)]
+// clipped to the lattice; rule 3, the element block of cell id, [p c, p c + p].
+__device__ __forceinline__ void block_box(int rule, int P, const Grid3 &g, int id, int lo[3], int d[3])
+{
+    if (rule == 3) {
+        const int c[3] = {id % g.n[0], (id / g.n[0]) % g.n[1], id / (g.n[0] * g.n[1])};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = P * c[a];
+            d[a] = P + 1;
+        }
+    } else {
+        const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
+        const int v[3] = {id % nvx, (id / nvx) % nvy, id / (nvx * nvy)};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = max(0, P * v[a] - (P - 1));
+            d[a] = min(g.M[a] - 1, P * v[a] + (P - 1)) - lo[a] + 1;
+        }
+    }
+}
 
 // y += K_e x_e over the active cells of one colour; rows that are not free stay untouched.
 template <int P>
@@ -188,51 +219,50 @@ __global__ void __launch_bounds__(256)
             if (mask[3 * node + c]) y[3 * node + c] += out[c];
 }
 
-// Work kinds of the Schwarz apply, stored in bits 8.. of a batch's .y (bits 0..7: patch count).
+// Work kinds of the Schwarz apply, stored in bits 8.. of a work item's .y.  Bits 0..7 hold the
+// block count of a shared-factor batch, or the row tile index of a block with its own factor.
 enum { kF32Shared = 0, kF32Single = 1, kF64Shared = 2, kF64Single = 3 };
 
-// z += F r_B for the `count` patches of one batch, which share the stored
-// factor F (shared batches, up to G patches) or have their own (G = 1).  F is
-// the dense symmetric pseudo inverse over the patch box (zero rows/columns
-// for box DOFs outside the block), stored in T = double or float.  Each
-// thread owns rows of the box; one load of F[j][t] feeds G multiply-adds, so
-// a shared factor is read once per batch instead of once per patch.  The
-// gathered residuals sit in shared memory as rbT[j][g], so one vector load
-// returns the G values a row step needs.  UNROLL sets the loads in flight
-// per thread (cut patches stream their factor from DRAM and are latency-bound).
+// z += F r_B for the `count` blocks of one batch, which share the stored factor F
+// (up to G blocks).  F is the dense symmetric pseudo inverse over the block box (zero
+// rows/columns for box DOFs outside the block), stored in T = double or float.  Each
+// thread owns rows of the box; one load of F[j][t] feeds G multiply-adds, so a shared
+// factor is read once per batch instead of once per block.  The gathered residuals sit in
+// shared memory as rbT[j][g], so one vector load returns the G values a row step needs.
+// The blocks of a batch have the same box shape, so a box entry's lattice index is the
+// block's base plus an offset common to the batch: both are tabulated once per CTA.
 template <int P, int G, typename T, int UNROLL>
 __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double *__restrict__ z,
                                             const T *__restrict__ pool, const PatchRec *__restrict__ patches,
-                                            int first, int count, const Grid3 &g, unsigned char *smem)
+                                            int first, int count, const Grid3 &g, int rule, unsigned char *smem)
 {
-    constexpr int W = 2 * P - 1, NB = 3 * W * W * W;
+    constexpr int W = box_width(P), NB = 3 * W * W * W;
     T(*rbT)[G] = reinterpret_cast<T(*)[G]>(smem);
-    int *vtx = reinterpret_cast<int *>(smem + sizeof(T) * NB * G);
-    const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
+    int64_t *base = reinterpret_cast<int64_t *>(smem + sizeof(T) * NB * G);  // G entries, -1: no block
+    int *rel = reinterpret_cast<int *>(base + G);                            // NB entries
     const PatchRec p0 = patches[first];
-    if (threadIdx.x < G) vtx[threadIdx.x] = (int)threadIdx.x < count ? patches[first + threadIdx.x].v : -1;
-    // the patches of a batch share the factor, hence the box shape; the origin differs
-    int d[3];
-    {
-        const int v[3] = {p0.v % nvx, (p0.v / nvx) % nvy, p0.v / (nvx * nvy)};
-        for (int a = 0; a < 3; ++a) {
-            const int lo = max(0, P * v[a] - (P - 1));
-            d[a] = min(g.M[a] - 1, P * v[a] + (P - 1)) - lo + 1;
-        }
-    }
+    int lo0[3], d[3];
+    block_box(rule, P, g, p0.v, lo0, d);
     const int n = 3 * d[0] * d[1] * d[2];
-    __syncthreads();
-    auto gidx = [&](int vv, int t) -> int64_t {
-        const int v0 = vv % nvx, v1 = (vv / nvx) % nvy, v2 = vv / (nvx * nvy);
-        const int l0 = max(0, P * v0 - (P - 1)), l1 = max(0, P * v1 - (P - 1)), l2 = max(0, P * v2 - (P - 1));
+    if (threadIdx.x < G) {
+        int64_t b = -1;
+        if ((int)threadIdx.x < count) {
+            int l[3], dd[3];
+            block_box(rule, P, g, patches[first + threadIdx.x].v, l, dd);
+            b = 3 * (l[0] + (int64_t)g.M[0] * (l[1] + (int64_t)g.M[1] * l[2]));
+        }
+        base[threadIdx.x] = b;
+    }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const int nl = t / 3;
         const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
-        return 3 * ((l0 + ix) + (int64_t)g.M[0] * ((l1 + iy) + (int64_t)g.M[1] * (l2 + iz))) + t % 3;
-    };
+        rel[t] = 3 * (ix + g.M[0] * (iy + g.M[1] * iz)) + t % 3;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < n * G; e += blockDim.x) {
         const int t = e / G, k = e % G;
-        const int vv = vtx[k];
-        rbT[t][k] = vv >= 0 ? (T)r[gidx(vv, t)] : (T)0;
+        const int64_t b = base[k];
+        rbT[t][k] = b >= 0 ? (T)r[b + rel[t]] : (T)0;
     }
     __syncthreads();
     const T *__restrict__ F = pool + p0.off;
@@ -246,30 +276,156 @@ __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double
 #pragma unroll
             for (int k = 0; k < G; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
         }
+        const int rt = rel[t];
 #pragma unroll
         for (int k = 0; k < G; ++k)
-            if (vtx[k] >= 0) z[gidx(vtx[k], t)] += (double)acc[k];
+            if (base[k] >= 0) z[base[k] + rt] += (double)acc[k];
     }
 }
 
-// Several right-hand sides (nr <= 8, vectors nlat apart): z_k += F r_k,B for each patch of
-// the work item, one patch after the other; one load of F[j][t] feeds nr multiply-adds.
+// Rows [row0, row0 + rows) of z_B += F r_B for a block with its own factor (cut blocks stream
+// their factor from DRAM).  The factor is symmetric, so row t of F is the contiguous column t
+// of the stored matrix: each warp takes 4 rows at a time and its lanes split the columns, so
+// one warp load reads 32 consecutive entries of a row and a lane keeps 16 loads in flight.
+// The row sums are finished by warp shuffles.  Splitting a block into row tiles gives the
+// launch many equal work items, so the DRAM stream does not wait on a few long blocks.
+template <int P, typename T>
+__device__ __forceinline__ void apply_rows(const double *__restrict__ r, double *__restrict__ z,
+                                           const T *__restrict__ pool, const PatchRec *__restrict__ patches,
+                                           int first, int row0, int rows, const Grid3 &g, int rule,
+                                           unsigned char *smem)
+{
+    T *rb = reinterpret_cast<T *>(smem);
+    const PatchRec pr = patches[first];
+    int lo[3], d[3];
+    block_box(rule, P, g, pr.v, lo, d);
+    const int n = 3 * d[0] * d[1] * d[2];
+    auto gidx = [&](int t) -> int64_t {
+        const int nl = t / 3;
+        const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
+        return 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + t % 3;
+    };
+    for (int t = threadIdx.x; t < n; t += blockDim.x) rb[t] = (T)r[gidx(t)];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int row1 = min(n, row0 + rows);
+    const T *__restrict__ F = pool + pr.off;
+    for (int t = row0 + 4 * w; t < row1; t += 4 * nw) {
+        // rows past row1 repeat the last row (in bounds) and are not written
+        const T *f0 = F + (size_t)t * n;
+        const T *f1 = F + (size_t)min(t + 1, row1 - 1) * n;
+        const T *f2 = F + (size_t)min(t + 2, row1 - 1) * n;
+        const T *f3 = F + (size_t)min(t + 3, row1 - 1) * n;
+        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+        for (int j0 = 0; j0 < n; j0 += 128) {
+            T v0[4], v1[4], v2[4], v3[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + 32 * u + lane;
+                const bool in = j < n;
+                v0[u] = in ? __ldg(f0 + j) : (T)0;
+                v1[u] = in ? __ldg(f1 + j) : (T)0;
+                v2[u] = in ? __ldg(f2 + j) : (T)0;
+                v3[u] = in ? __ldg(f3 + j) : (T)0;
+                x[u] = in ? rb[j] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a0 = fma(v0[u], x[u], a0);
+                a1 = fma(v1[u], x[u], a1);
+                a2 = fma(v2[u], x[u], a2);
+                a3 = fma(v3[u], x[u], a3);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        }
+        if (lane < 4 && t + lane < row1) {
+            const T a = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
+            z[gidx(t + lane)] += (double)a;
+        }
+    }
+}
+
+// Rows [row0, row0 + rows) of z_k,B += F r_k,B for nr <= 8 right-hand sides (vectors nlat
+// apart) of a block with its own factor: warp-per-row as in apply_rows, two rows at a time,
+// each lane holding nr partial sums per row; one load of F feeds nr multiply-adds.
+template <int P, typename T>
+__device__ __forceinline__ void apply_multi_rows(const double *__restrict__ r, double *__restrict__ z, int64_t nlat,
+                                                 int nr, const T *__restrict__ pool,
+                                                 const PatchRec *__restrict__ patches, int first, int row0, int rows,
+                                                 const Grid3 &g, int rule, unsigned char *smem)
+{
+    constexpr int MR = 8;
+    T(*rbT)[MR] = reinterpret_cast<T(*)[MR]>(smem);
+    const PatchRec pr = patches[first];
+    int lo[3], d[3];
+    block_box(rule, P, g, pr.v, lo, d);
+    const int n = 3 * d[0] * d[1] * d[2];
+    auto gidx = [&](int t) -> int64_t {
+        const int nl = t / 3;
+        const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
+        return 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + t % 3;
+    };
+    for (int e = threadIdx.x; e < n * MR; e += blockDim.x) {
+        const int t = e / MR, k = e % MR;
+        rbT[t][k] = k < nr ? (T)r[(int64_t)k * nlat + gidx(t)] : (T)0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int row1 = min(n, row0 + rows);
+    const T *__restrict__ F = pool + pr.off;
+    for (int t = row0 + 2 * w; t < row1; t += 2 * nw) {
+        const T *f0 = F + (size_t)t * n;
+        const T *f1 = F + (size_t)min(t + 1, row1 - 1) * n;
+        T a[2][MR];
+#pragma unroll
+        for (int k = 0; k < MR; ++k) a[0][k] = a[1][k] = (T)0;
+#pragma unroll 2
+        for (int j = lane; j < n; j += 32) {
+            const T g0 = __ldg(f0 + j), g1 = __ldg(f1 + j);
+#pragma unroll
+            for (int k = 0; k < MR; ++k) {
+                a[0][k] = fma(g0, rbT[j][k], a[0][k]);
+                a[1][k] = fma(g1, rbT[j][k], a[1][k]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < MR; ++k) {
+                a[0][k] += __shfl_xor_sync(0xffffffffu, a[0][k], o);
+                a[1][k] += __shfl_xor_sync(0xffffffffu, a[1][k], o);
+            }
+        // lane 8 h + k writes row t + h, right-hand side k
+        const int h = lane >> 3, k = lane & 7;
+        if (h < 2 && k < nr && t + h < row1) {
+            T v = (T)0;
+#pragma unroll
+            for (int kk = 0; kk < MR; ++kk)
+                if (kk == k) v = h == 0 ? a[0][kk] : a[1][kk];
+            z[(int64_t)k * nlat + gidx(t + h)] += (double)v;
+        }
+    }
+}
+
+// Several right-hand sides (nr <= 8, vectors nlat apart): z_k += F r_k,B for each block of a
+// shared-factor batch, one block after the other; one load of F[j][t] feeds nr multiply-adds.
 template <int P, typename T, int UNROLL>
 __device__ __forceinline__ void apply_multi(const double *__restrict__ r, double *__restrict__ z, int64_t nlat, int nr,
                                             const T *__restrict__ pool, const PatchRec *__restrict__ patches,
-                                            int first, int count, const Grid3 &g, unsigned char *smem)
+                                            int first, int count, const Grid3 &g, int rule, unsigned char *smem)
 {
-    constexpr int W = 2 * P - 1, NB = 3 * W * W * W, MR = 8;
+    constexpr int MR = 8;
     T(*rbT)[MR] = reinterpret_cast<T(*)[MR]>(smem);
-    const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
     for (int b = 0; b < count; ++b) {
         const PatchRec pr = patches[first + b];
-        const int v[3] = {pr.v % nvx, (pr.v / nvx) % nvy, pr.v / (nvx * nvy)};
         int lo[3], d[3];
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = max(0, P * v[a] - (P - 1));
-            d[a] = min(g.M[a] - 1, P * v[a] + (P - 1)) - lo[a] + 1;
-        }
+        block_box(rule, P, g, pr.v, lo, d);
         const int n = 3 * d[0] * d[1] * d[2];
         auto gidx = [&](int t) -> int64_t {
             const int nl = t / 3;
@@ -301,44 +457,64 @@ __device__ __forceinline__ void apply_multi(const double *__restrict__ r, double
 
 // One colour of the Schwarz apply for nr right-hand sides at once (multi-RHS solves).
 template <int P>
-__global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
+__global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * box_width(P)))
     schwarz_multi_kernel(const double *__restrict__ r, double *__restrict__ z, int64_t nlat, int nr,
                          const double *__restrict__ f64, const float *__restrict__ f32,
-                         const PatchRec *__restrict__ patches, const int2 *__restrict__ batches, Grid3 g,
-                         const int *__restrict__ done)
+                         const PatchRec *__restrict__ patches, const int2 *__restrict__ batches, Grid3 g, int rule,
+                         int rows, const int *__restrict__ done)
 {
-    constexpr int W = 2 * P - 1, NB = 3 * W * W * W;
+    constexpr int W = box_width(P), NB = 3 * W * W * W;
     __shared__ __align__(16) unsigned char smem[NB * 8 * (P == 4 ? 4 : 8)];
     if (done && *done) return;
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
-    if (kind == kF32Shared || kind == kF32Single)
-        apply_multi<P, float, 8>(r, z, nlat, nr, f32, patches, bt.x, count, g, smem);
+    // single-factor items carry a row tile index in place of the block count
+    if (kind == kF32Single)
+        apply_multi_rows<P, float>(r, z, nlat, nr, f32, patches, bt.x, count * rows, rows, g, rule, smem);
+    else if (kind == kF64Single && P < 4)
+        apply_multi_rows<P, double>(r, z, nlat, nr, f64, patches, bt.x, count * rows, rows, g, rule, smem);
+    else if (kind == kF32Shared)
+        apply_multi<P, float, 8>(r, z, nlat, nr, f32, patches, bt.x, count, g, rule, smem);
     else if (P < 4)
-        apply_multi<P, double, 8>(r, z, nlat, nr, f64, patches, bt.x, count, g, smem);
+        apply_multi<P, double, 8>(r, z, nlat, nr, f64, patches, bt.x, count, g, rule, smem);
 }
 
-// One colour of the Schwarz apply (Sec. 3.1 Eq. (5)): each CTA takes one work
-// item (a shared-factor batch or a single patch, FP32 or FP64 factor).  The
-// patches of one colour are DOF-disjoint, so the scatter needs no atomics.
+// One colour of the Schwarz apply (Sec. 3.1 Eq. (5)): each CTA takes one work item (a
+// shared-factor batch, or a row tile of a block with its own factor; FP32 or FP64 factor).
+// The blocks of one colour are DOF-disjoint, so the scatter needs no atomics.
 template <int P>
-__global__ void __launch_bounds__(threads_for(3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1)))
+__global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * box_width(P)))
     schwarz_colour_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ f64,
                           const float *__restrict__ f32, const PatchRec *__restrict__ patches,
-                          const int2 *__restrict__ batches, Grid3 g, const int *__restrict__ done)
+                          const int2 *__restrict__ batches, Grid3 g, int rule, int rows,
+                          const int *__restrict__ done)
 {
-    constexpr int W = 2 * P - 1, NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8);
+    constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8);
     constexpr int ROW = (GD * 8 > 8 * 4 ? GD * 8 : 8 * 4);  // bytes of one rbT row, largest variant
-    __shared__ __align__(16) unsigned char smem[NB * ROW + 64];
+    // rbT, then the batch's block bases (8 x int64) and box offsets (NB x int)
+    __shared__ __align__(16) unsigned char smem[NB * ROW + 64 + 4 * NB];
     if (done && *done) return;
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
     switch (kind) {
-    case kF32Shared: apply_batch<P, 8, float, 4>(r, z, f32, patches, bt.x, count, g, smem); break;
-    case kF32Single: apply_batch<P, 1, float, 16>(r, z, f32, patches, bt.x, count, g, smem); break;
-    case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, smem); break;
-    default: apply_batch<P, 1, double, 16>(r, z, f64, patches, bt.x, count, g, smem); break;
+    case kF32Shared: apply_batch<P, 8, float, 4>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
+    // single-factor items carry a row tile index in place of the block count
+    case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows, rows, g, rule, smem); break;
+    case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, rule, smem); break;
+    default: apply_rows<P, double>(r, z, f64, patches, bt.x, count * rows, rows, g, rule, smem); break;
     }
+}
+
+// Start of z = S r for nr vectors nlat apart: z = D r with D = 1 / K_ll for the DOFs in no
+// block (Algorithm 1's diagonal part) and 0 elsewhere, or z = 0 when the blocks cover every
+// free DOF (jac == nullptr).
+__global__ void schwarz_init_kernel(const double *__restrict__ r, double *__restrict__ z,
+                                    const double *__restrict__ jac, int64_t nlat, int64_t n,
+                                    const int *__restrict__ done)
+{
+    if (done && *done) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = jac ? jac[i % nlat] * r[i] : 0.0;
 }
 
 __global__ void mask_copy_kernel(const double *__restrict__ in, double *__restrict__ out,
@@ -375,12 +551,12 @@ template <int P>
 void schwarz_launch(const Grid3 &g, const double *r, double *z, const double *f64, const float *f32,
                     const SchwarzPlan &plan, const int *done, cudaStream_t s)
 {
-    constexpr int NB = 3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1);
+    const int threads = schwarz_threads(P, plan.rule);
     for (int i = 0; i < plan.nseg; ++i) {
         const SchwarzSeg &sg = plan.seg[i];
         if (sg.count > 0)
-            schwarz_colour_kernel<P><<<sg.count, threads_for(NB), 0, s>>>(r, z, f64, f32, plan.patches,
-                                                                         plan.batches + sg.first, g, done);
+            schwarz_colour_kernel<P><<<sg.count, threads, 0, s>>>(r, z, f64, f32, plan.patches, plan.batches + sg.first,
+                                                                  g, plan.rule, plan.rows, done);
     }
 }
 
@@ -388,12 +564,12 @@ template <int P>
 void schwarz_multi_launch(const Grid3 &g, const double *r, double *z, int64_t nlat, int nr, const double *f64,
                           const float *f32, const SchwarzPlan &plan, const int *done, cudaStream_t s)
 {
-    constexpr int NB = 3 * (2 * P - 1) * (2 * P - 1) * (2 * P - 1);
+    const int threads = schwarz_threads(P, plan.rule);
     for (int i = 0; i < plan.nseg; ++i) {
         const SchwarzSeg &sg = plan.seg[i];
         if (sg.count > 0)
-            schwarz_multi_kernel<P><<<sg.count, threads_for(NB), 0, s>>>(r, z, nlat, nr, f64, f32, plan.patches,
-                                                                        plan.batches + sg.first, g, done);
+            schwarz_multi_kernel<P><<<sg.count, threads, 0, s>>>(r, z, nlat, nr, f64, f32, plan.patches,
+                                                                 plan.batches + sg.first, g, plan.rule, plan.rows, done);
     }
 }
 
@@ -418,9 +594,13 @@ void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uin
     }
 }
 
+int schwarz_rows_per_item(int p, int rule) { return 4 * (schwarz_threads(p, rule) / 32); }
+
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *f64, const float *f32,
                           const SchwarzPlan &plan, const int *done, cudaStream_t s)
 {
+    const int64_t nlat = 3 * (int64_t)g.M[0] * g.M[1] * g.M[2];
+    schwarz_init_kernel<<<grid_for(nlat, 256), 256, 0, s>>>(r, z, plan.jac, nlat, nlat, done);
     switch (p) {
     case 1: schwarz_launch<1>(g, r, z, f64, f32, plan, done, s); break;
     case 2: schwarz_launch<2>(g, r, z, f64, f32, plan, done, s); break;
@@ -434,6 +614,7 @@ void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *
                                 const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
                                 cudaStream_t s)
 {
+    schwarz_init_kernel<<<grid_for(nlat * nr, 256), 256, 0, s>>>(r, z, plan.jac, nlat, nlat * nr, done);
     switch (p) {
     case 1: schwarz_multi_launch<1>(g, r, z, nlat, nr, f64, f32, plan, done, s); break;
     case 2: schwarz_multi_launch<2>(g, r, z, nlat, nr, f64, f32, plan, done, s); break;

@@ -76,7 +76,6 @@ extern "C" fcm_status fcm_apply_S_noalloc(fcm_ctx *C, const double *r_dev, doubl
     cudaEventRecord(C->ev_in, C->ustream);
     cudaStreamWaitEvent(C->stream, C->ev_in, 0);
     fcm::launch_mask_copy(r_dev, scratch, C->d_mask, C->nlat, C->stream);
-    fcm::launch_zero(z_dev, C->nlat, nullptr, C->stream);
     fcm::launch_schwarz_apply(C->p, C->g, scratch, z_dev, C->d_f64, C->d_f32, C->plan,
                               nullptr, C->stream);
     e = cudaGetLastError();

@@ -2,16 +2,20 @@
 // arXiv:1809.00828): getBlocks -> extractSubMatrix -> computePseudoInverse ->
 // store, with the eigenvalue filter of Sec. 3.2 Eqs. (11)-(13).
 //
-// Blocks are vertex patches: for grid vertex v the free functions carried by v
-// and by the edges, faces and cells whose closure contains v.  In lattice
-// terms this is the box [p v - (p-1), p v + (p-1)] per axis (clipped at the
-// domain), so a block is stored densely over its box, with zero rows and
-// columns for box DOFs that are not free.  Patches whose cells are all uncut
-// (or inactive) and that share the same clipping and activity pattern have
-// identical blocks and share one stored factor.
+// Two block rules.  Vertex patches (rule 0): for grid vertex v the free
+// functions carried by v and by the edges, faces and cells whose closure
+// contains v; in lattice terms the box [p v - (p-1), p v + (p-1)] per axis
+// (clipped at the domain).  Element blocks (rule 3, the paper's rule, Sec. 3.2
+// "Optimizing the number of blocks"): for each active cell with volume
+// fraction eta_T < eta_bar, every function supported on the cell, the box
+// [p c, p c + p]; the free DOFs in no block get Algorithm 1's diagonal
+// scaling 1 / K_ll.  A block is stored densely over its box, with zero rows
+// and columns for box DOFs that are not free.  Blocks whose contributing cells
+// are all uncut (or inactive, or outside the grid) in the same pattern have
+// identical matrices and share one stored factor.
 //
 // Device pipeline per group of equal-size blocks: assemble A_B from the element
-// matrices of the (up to 8) patch cells, pad the diagonal of non-free rows
+// matrices of the cells around the block (8 for a patch, 27 for an element block), pad the diagonal of non-free rows
 // with max_i A_ii (which leaves lambda_max and the filtered set unchanged),
 // batched symmetric eigensolve (cuSOLVER), filter/invert the eigenvalues,
 // F = V diag(lambda+^-1) V^T (cuBLAS batched GEMM), symmetrise, zero the
@@ -52,6 +56,7 @@ namespace {
 
 struct BoxInfo {
     int lo[3], d[3], n;
+    int clo[3], chi[3];  // cells whose element matrices contribute to K[B,B]
 };
 
 __host__ __device__ inline BoxInfo patch_box(int p, const Grid3 &g, int vx, int vy, int vz)
@@ -66,19 +71,44 @@ __host__ __device__ inline BoxInfo patch_box(int p, const Grid3 &g, int vx, int 
         b.d[a] = hi - b.lo[a] + 1;
     }
     b.n = 3 * b.d[0] * b.d[1] * b.d[2];
+    for (int a = 0; a < 3; ++a) {
+        b.clo[a] = v[a] - 1;
+        b.chi[a] = v[a];
+    }
     return b;
 }
 
-// A_B[i][j] = K[g_i][g_j] summed over the active cells of the patch (0 if i or j is not free).
-__global__ void assemble_kernel(int p, Grid3 g, const int *__restrict__ rep, int n, double *__restrict__ A,
+// Element block of cell (cx, cy, cz): the box [p c, p c + p]; its DOFs on the cell's faces are
+// shared with the neighbours, so the 27 cells around contribute to K[B,B].
+__host__ __device__ inline BoxInfo element_box(int p, int cx, int cy, int cz)
+{
+    BoxInfo b;
+    const int c[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = p * c[a];
+        b.d[a] = p + 1;
+        b.clo[a] = c[a] - 1;
+        b.chi[a] = c[a] + 1;
+    }
+    b.n = 3 * (p + 1) * (p + 1) * (p + 1);
+    return b;
+}
+
+__host__ __device__ inline BoxInfo block_box_of(int rule, int p, const Grid3 &g, int id)
+{
+    if (rule == FCM_BLOCKS_ELEMENT)
+        return element_box(p, id % g.n[0], (id / g.n[0]) % g.n[1], id / (g.n[0] * g.n[1]));
+    const int nv0 = g.n[0] + 1, nv1 = g.n[1] + 1;
+    return patch_box(p, g, id % nv0, (id / nv0) % nv1, id / (nv0 * nv1));
+}
+
+// A_B[i][j] = K[g_i][g_j] summed over the active cells around the block (0 if i or j is not free).
+__global__ void assemble_kernel(int p, Grid3 g, int rule, const int *__restrict__ rep, int n, double *__restrict__ A,
                                 const double *__restrict__ elem, const int32_t *__restrict__ cell_elem,
                                 const uint8_t *__restrict__ mask)
 {
     const int b = blockIdx.y;
-    const int nv0 = g.n[0] + 1, nv1 = g.n[1] + 1;
-    const int v = rep[b];
-    const int vx = v % nv0, vy = (v / nv0) % nv1, vz = v / (nv0 * nv1);
-    const BoxInfo bx = patch_box(p, g, vx, vy, vz);
+    const BoxInfo bx = block_box_of(rule, p, g, rep[b]);
     const int q = p + 1, ne = 3 * q * q * q;
     double *Ab = A + (size_t)b * n * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -95,8 +125,9 @@ __global__ void assemble_kernel(int p, Grid3 g, const int *__restrict__ rep, int
         const int64_t gj = 3 * (Lj[0] + (int64_t)g.M[0] * (Lj[1] + (int64_t)g.M[1] * Lj[2])) + cj;
         double s = 0.0;
         if (mask[gi] && mask[gj]) {
-            for (int t = 0; t < 8; ++t) {
-                int c[3] = {vx - 1 + (t & 1), vy - 1 + ((t >> 1) & 1), vz - 1 + ((t >> 2) & 1)};
+            const int w0 = bx.chi[0] - bx.clo[0] + 1, w1 = bx.chi[1] - bx.clo[1] + 1, w2 = bx.chi[2] - bx.clo[2] + 1;
+            for (int t = 0; t < w0 * w1 * w2; ++t) {
+                int c[3] = {bx.clo[0] + t % w0, bx.clo[1] + (t / w0) % w1, bx.clo[2] + t / (w0 * w1)};
                 if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= g.n[0] || c[1] >= g.n[1] || c[2] >= g.n[2]) continue;
                 const int el = cell_elem[c[0] + (int64_t)g.n[0] * (c[1] + (int64_t)g.n[1] * c[2])];
                 if (el < 0) continue;
@@ -186,12 +217,10 @@ __global__ void invert_kernel(const double *V, const double *W, double *U, int n
 
 // F = sym(C) on free rows/columns, 0 elsewhere; written to the FP64 pool.
 __global__ void finalize_kernel(const double *C, int n, const int *rep, const int64_t *off, double *pool, int p,
-                                Grid3 g, const uint8_t *mask)
+                                Grid3 g, int rule, const uint8_t *mask)
 {
     const int b = blockIdx.y;
-    const int nv0 = g.n[0] + 1, nv1 = g.n[1] + 1;
-    const int v = rep[b];
-    const BoxInfo bx = patch_box(p, g, v % nv0, (v / nv0) % nv1, v / (nv0 * nv1));
+    const BoxInfo bx = block_box_of(rule, p, g, rep[b]);
     const double *Cb = C + (size_t)b * n * n;
     double *F = pool + off[b];
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -229,25 +258,70 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     const int p = C->p;
     const Grid3 g = C->g;
     const int nv[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
-    const int64_t npatch = (int64_t)nv[0] * nv[1] * nv[2];
+    const int rule = o.block_rule;
+    if (rule != FCM_BLOCKS_VERTEX && rule != FCM_BLOCKS_ELEMENT) return "unknown block rule";
+    // block ids: vertices (rule 0) or cells (rule 3)
+    const int nid[3] = {rule == FCM_BLOCKS_ELEMENT ? g.n[0] : nv[0], rule == FCM_BLOCKS_ELEMENT ? g.n[1] : nv[1],
+                        rule == FCM_BLOCKS_ELEMENT ? g.n[2] : nv[2]};
+    const int64_t npatch = (int64_t)nid[0] * nid[1] * nid[2];
     cudaStream_t st = C->stream;
+    auto box_has_free = [&](const BoxInfo &bx) {
+        for (int t = 0; t < bx.n; ++t) {
+            const int nl = t / 3;
+            const int x = bx.lo[0] + nl % bx.d[0], y = bx.lo[1] + (nl / bx.d[0]) % bx.d[1], z = bx.lo[2] + nl / (bx.d[0] * bx.d[1]);
+            if (hp.mask[3 * (x + (int64_t)g.M[0] * (y + (int64_t)g.M[1] * z)) + t % 3]) return true;
+        }
+        return false;
+    };
 
-    // ---- getBlocks: vertex patches, deduplicated by signature
+    // ---- getBlocks, deduplicated by signature
     std::vector<int> patch_factor(npatch, -1);
     std::vector<FactorInfo> fac;
     std::map<uint64_t, int> regular;
+    if (rule == FCM_BLOCKS_ELEMENT) {
+        for (int cz = 0; cz < g.n[2]; ++cz)
+            for (int cy = 0; cy < g.n[1]; ++cy)
+                for (int cx = 0; cx < g.n[0]; ++cx) {
+                    const int c = cx + g.n[0] * (cy + g.n[1] * cz);
+                    if (hp.cell_elem[c] < 0 || !(hp.eta[c] < o.eta_bar)) continue;
+                    const BoxInfo bx = element_box(p, cx, cy, cz);
+                    if (!box_has_free(bx)) continue;
+                    // 2 bits per contributing cell: 0 outside the grid, 1 inactive, 2 uncut; any cut
+                    // cell makes the block unique
+                    bool cut = false;
+                    uint64_t key = 0;
+                    for (int t = 0; t < 27; ++t) {
+                        const int n3[3] = {cx - 1 + t % 3, cy - 1 + (t / 3) % 3, cz - 1 + t / 9};
+                        uint64_t code = 0;
+                        if (n3[0] >= 0 && n3[1] >= 0 && n3[2] >= 0 && n3[0] < g.n[0] && n3[1] < g.n[1] && n3[2] < g.n[2]) {
+                            const int el = hp.cell_elem[n3[0] + (int64_t)g.n[0] * (n3[1] + (int64_t)g.n[1] * n3[2])];
+                            if (el > 0) cut = true;
+                            code = el < 0 ? 1 : 2;
+                        }
+                        key |= code << (2 * t);
+                    }
+                    int fid;
+                    if (!cut) {
+                        auto it = regular.find(key);
+                        if (it != regular.end()) {
+                            patch_factor[c] = it->second;
+                            continue;
+                        }
+                        fid = (int)fac.size();
+                        regular[key] = fid;
+                    } else {
+                        fid = (int)fac.size();
+                    }
+                    fac.push_back({c, bx.n, 0, 0.0, 0});
+                    patch_factor[c] = fid;
+                }
+    } else
     for (int vz = 0; vz < nv[2]; ++vz)
         for (int vy = 0; vy < nv[1]; ++vy)
             for (int vx = 0; vx < nv[0]; ++vx) {
                 const int v = vx + nv[0] * (vy + nv[1] * vz);
                 const BoxInfo bx = patch_box(p, g, vx, vy, vz);
-                bool any_free = false;
-                for (int t = 0; t < bx.n && !any_free; ++t) {
-                    const int nl = t / 3;
-                    const int x = bx.lo[0] + nl % bx.d[0], y = bx.lo[1] + (nl / bx.d[0]) % bx.d[1], z = bx.lo[2] + nl / (bx.d[0] * bx.d[1]);
-                    any_free = hp.mask[3 * (x + (int64_t)g.M[0] * (y + (int64_t)g.M[1] * z)) + t % 3] != 0;
-                }
-                if (!any_free) continue;
+                if (!box_has_free(bx)) continue;
                 bool cut = false;
                 uint64_t key = 0;
                 for (int t = 0; t < 8; ++t) {
@@ -375,7 +449,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
             PC_CUDA(cudaMemcpyAsync(drep, hrep.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
             PC_CUDA(cudaMemcpyAsync(doff, hoff.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, st));
             const int gx = (int)std::min<int64_t>(((int64_t)n2 + 255) / 256, 64);
-            assemble_kernel<<<dim3(gx, B), 256, 0, st>>>(p, g, drep, n, dA, C->d_elem, C->d_cell_elem, C->d_mask);
+            assemble_kernel<<<dim3(gx, B), 256, 0, st>>>(p, g, rule, drep, n, dA, C->d_elem, C->d_cell_elem, C->d_mask);
             pad_kernel<<<B, 256, 0, st>>>(dA, n);
             PC_CUDA(cudaGetLastError());
             if (batched) {
@@ -393,7 +467,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
             // C = U V^T (column-major): C(i,j) = sum_k U(i,k) V(j,k)
             PC_BLAS(cublasDgemmStridedBatched(bh, CUBLAS_OP_N, CUBLAS_OP_T, n, n, n, &one, dU, n, (long long)n2, dA, n,
                                               (long long)n2, &zero, dC, n, (long long)n2, B));
-            finalize_kernel<<<dim3(gx, B), 256, 0, st>>>(dC, n, drep, doff, stage, p, g, C->d_mask);
+            finalize_kernel<<<dim3(gx, B), 256, 0, st>>>(dC, n, drep, doff, stage, p, g, rule, C->d_mask);
             PC_CUDA(cudaGetLastError());
             PC_CUDA(cudaMemcpyAsync(hinfo.data(), dinfo, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
             PC_CUDA(cudaMemcpyAsync(hcond.data(), dcond, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
@@ -446,17 +520,18 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     if (!mixed)
         for (size_t f = 0; f < fac.size(); ++f) off[f] = fac[f].off;
 
-    // ---- launch plan: per colour (vertex parity) and precision, batches of patches sharing a
-    // factor (up to 8; 4 for FP64 at p = 4) and single patches with their own factor
+    // ---- launch plan: per colour and precision, batches of blocks sharing a factor (up to 8; 4
+    // for FP64 at p = 4) and row tiles of the blocks with their own factor
     std::vector<int> users(fac.size(), 0);
     std::vector<std::vector<int>> by_colour_factor[8];
     for (int c = 0; c < 8; ++c) by_colour_factor[c].resize(fac.size());
     C->n_blocks = 0;
     C->sapply_fmas = 0;
-    for (int vz = 0; vz < nv[2]; ++vz)
-        for (int vy = 0; vy < nv[1]; ++vy)
-            for (int vx = 0; vx < nv[0]; ++vx) {
-                const int v = vx + nv[0] * (vy + nv[1] * vz);
+    // colours: parity of the vertex (rule 0) or of the cell (rule 3); blocks of one colour are DOF-disjoint
+    for (int vz = 0; vz < nid[2]; ++vz)
+        for (int vy = 0; vy < nid[1]; ++vy)
+            for (int vx = 0; vx < nid[0]; ++vx) {
+                const int v = vx + nid[0] * (vy + nid[1] * vz);
                 const int f = patch_factor[v];
                 if (f < 0) continue;
                 by_colour_factor[(vx & 1) + 2 * (vy & 1) + 4 * (vz & 1)][f].push_back(v);
@@ -464,11 +539,13 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
                 C->sapply_fmas += (int64_t)fac[f].n * fac[f].n;
             }
     // One launch per colour.  Work items, heaviest first so that the tail of the launch is short:
-    // FP64 shared-factor batches, FP64 single patches, FP32 single patches (DRAM-bound), FP32 batches.
+    // FP64 shared-factor batches, FP64 single blocks, FP32 single blocks (DRAM-bound), FP32 batches.
     // Kinds as in fcm_kernels.cu: 0 FP32 shared, 1 FP32 single, 2 FP64 shared, 3 FP64 single.
     std::vector<PatchRec> all;
     std::vector<int2> batches;
     SchwarzPlan plan = {};
+    const int rows = schwarz_rows_per_item(p, rule);
+    plan.rows = rows;
     const int order[4][2] = {{0, 1}, {0, 0}, {1, 0}, {1, 1}};  // (precision 0 = FP64 / 1 = FP32, shared?)
     for (int c = 0; c < 8; ++c) {
         SchwarzSeg sg = {c, -1, 0, (int)batches.size(), 0};
@@ -481,7 +558,13 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
                 if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
                 for (size_t s0 = 0; s0 < vs.size(); s0 += cap) {
                     const int cnt = (int)std::min<size_t>(cap, vs.size() - s0);
-                    batches.push_back(make_int2((int)all.size(), cnt | (kind << 8)));
+                    if (shared) {
+                        batches.push_back(make_int2((int)all.size(), cnt | (kind << 8)));
+                    } else {
+                        // a block with its own factor is split into row tiles of `rows` rows; the
+                        // items carry the tile index in place of the count
+                        for (int t = 0; t * rows < fac[f].n; ++t) batches.push_back(make_int2((int)all.size(), t | (kind << 8)));
+                    }
                     for (int k = 0; k < cnt; ++k) all.push_back({off[f], vs[s0 + k], prec[f]});
                 }
             }
@@ -500,6 +583,34 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     PC_CUDA(cudaStreamSynchronize(st));
     plan.patches = C->d_patches;
     plan.batches = C->d_batches;
+    plan.rule = rule;
+
+    // ---- Algorithm 1's diagonal part: 1 / K_ll for the free DOFs in no block
+    std::vector<uint8_t> covered(hp.nlat, 0);
+    for (int64_t v = 0; v < npatch; ++v) {
+        if (patch_factor[v] < 0) continue;
+        const BoxInfo bx = block_box_of(rule, p, g, (int)v);
+        for (int t = 0; t < bx.n; ++t) {
+            const int nl = t / 3;
+            const int x = bx.lo[0] + nl % bx.d[0], y = bx.lo[1] + (nl / bx.d[0]) % bx.d[1], z = bx.lo[2] + nl / (bx.d[0] * bx.d[1]);
+            covered[3 * (x + (int64_t)g.M[0] * (y + (int64_t)g.M[1] * z)) + t % 3] = 1;
+        }
+    }
+    int64_t nuncovered = 0;
+    for (int64_t l = 0; l < hp.nlat; ++l) nuncovered += hp.mask[l] && !covered[l];
+    if (C->d_jac) cudaFree(C->d_jac);
+    C->d_jac = nullptr;
+    C->n_jacobi = nuncovered;
+    if (nuncovered > 0) {
+        const std::vector<double> &diag = hp.kdiag;  // K_ll, tabulated at set-up
+        std::vector<double> jac(hp.nlat, 0.0);
+        for (int64_t l = 0; l < hp.nlat; ++l)
+            if (hp.mask[l] && !covered[l] && diag[l] > 0.0) jac[l] = 1.0 / diag[l];
+        PC_CUDA(cudaMalloc(&C->d_jac, sizeof(double) * hp.nlat));
+        PC_CUDA(cudaMemcpyAsync(C->d_jac, jac.data(), sizeof(double) * hp.nlat, cudaMemcpyHostToDevice, st));
+        PC_CUDA(cudaStreamSynchronize(st));
+    }
+    plan.jac = C->d_jac;
     C->plan = plan;
     C->n_factors = (int64_t)fac.size();
     C->factor_bytes = n64 * 8 + n32 * 4;

@@ -55,11 +55,15 @@ class Info(ctypes.Structure):
                 ("p", ctypes.c_int), ("setup_seconds", ctypes.c_double), ("precond_seconds", ctypes.c_double),
                 ("n_blocks", ctypes.c_int64), ("n_blocks_fp32", ctypes.c_int64), ("kapply_fmas", ctypes.c_int64),
                 ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double),
-                ("coarse_seconds", ctypes.c_double)]
+                ("coarse_seconds", ctypes.c_double), ("n_jacobi", ctypes.c_int64)]
 
 
 class PrecondOpts(ctypes.Structure):
-    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("cond_fp64", ctypes.c_double)]
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("cond_fp64", ctypes.c_double),
+                ("block_rule", ctypes.c_int), ("eta_bar", ctypes.c_double)]
+
+
+BLOCKS_VERTEX, BLOCKS_ELEMENT = 0, 3
 
 
 class SolveInfo(ctypes.Structure):
@@ -163,11 +167,17 @@ class Solver:
         self._check(load().fcm_rhs(self.ctx, load_case, _ptr(b)))
         return b
 
-    def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7):
+    def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0):
+        """blocks: "vertex" (vertex patches) or "element" (element blocks of the cells with
+        eta_T < eta_bar, diagonal scaling for the DOFs in no block)."""
+        if blocks not in ("vertex", "element"):
+            raise ValueError(f"unknown block rule {blocks!r}")
         o = PrecondOpts()
         o.eps = eps
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
         o.cond_fp64 = cond_fp64
+        o.block_rule = BLOCKS_ELEMENT if blocks == "element" else BLOCKS_VERTEX
+        o.eta_bar = eta_bar
         self._check(load().fcm_precond_build(self.ctx, ctypes.byref(o)))
         self.info = self.get_info()
 

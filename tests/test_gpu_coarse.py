@@ -108,6 +108,22 @@ def test_fpcg_network_start_plus_coarse_cg(porous8):
     assert st3 == 0 and P.energy_error(x_ref, u3.cpu().numpy()[P.free_lat]) < 1e-6
 
 
+def test_fpcg_after_the_preconditioner_is_rebuilt(porous8):
+    # the flexible CG iteration is captured once and reused; rebuilding the Schwarz blocks
+    # (new factor pools and plan) must make the next solve capture it again
+    w, s, P = porous8
+    b = s.rhs()
+    x_ref = spla.spsolve(P.csr().tocsc(), P.rhs())
+    _, its0, _, st0 = s.fpcg_solve(None, 0.0, b, w.tol, 4000, coarse_iters=5)
+    assert st0 == 0
+    for prec in ("mixed", "fp64"):
+        s.precond_build(precision=prec)
+        u, its, rel, st = s.fpcg_solve(None, 0.0, b, w.tol, 4000, coarse_iters=5)
+        assert st == 0 and rel <= w.tol * 1.0001
+        assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
+    assert its == its0
+
+
 def test_fpcg_rejects_no_network_and_no_coarse_steps(porous8):
     from paper_1809_00828_gb300 import fcm
     w, s, P = porous8
