@@ -109,6 +109,10 @@ typedef struct {
     double max_block_cond;    /* largest retained condition number of a block          */
     double coarse_seconds;    /* assembly time of the coarse operator K_H (0 until built) */
     int64_t n_jacobi;         /* free DOFs in no block (diagonal part of S), last build   */
+    int rows32, rows64;       /* rows per work item of a cut block's FP32 / FP64 factor  */
+    double tune_seconds[4];   /* S-apply time of each tried row-tile size (0: not tried) */
+    int device_error;         /* 1 if a Schwarz kernel gave up waiting for its factor copy
+                                 since the last fcm_precond_build (its output is then wrong) */
 } fcm_info_t;
 
 enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1 };
@@ -132,14 +136,19 @@ enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
  *        DOFs in no block get Algorithm 1's diagonal scaling 1 / K_ll.
  *        eta_bar = 0 gives pure Jacobi; eta_bar > 1 blocks every active cell.
  *   eta_bar: threshold of FCM_BLOCKS_ELEMENT (ignored by FCM_BLOCKS_VERTEX).
+ *   fixed_tiles: 0 (default) lets the build time the Schwarz apply for up to
+ *        three row-tile sizes of the cut blocks (the rows of a factor handled
+ *        by one CTA) and keep the fastest; 1 keeps the default size.  The
+ *        result of S r does not depend on the tile size.
  * A zero-initialised struct with eps, precision and cond_fp64 set selects
- * vertex patches. */
+ * vertex patches and the autotuned tiles. */
 typedef struct {
     double eps;
     int precision;
     double cond_fp64;
     int block_rule;
     double eta_bar;
+    int fixed_tiles;
 } fcm_precond_opts;
 
 /* Solver result details. */

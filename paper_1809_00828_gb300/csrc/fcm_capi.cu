@@ -163,7 +163,7 @@ void free_ctx(fcm_ctx *C)
 {
     if (!C) return;
     destroy_graph(C);
-    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32, C->d_patches, C->d_batches, C->d_eta, C->d_jac,
+    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32, C->d_patches, C->d_batches, C->d_eta, C->d_jac, C->d_err,
                     C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
                     C->d_out2};
     for (void *q : ptrs)
@@ -366,6 +366,16 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->max_block_cond = C->max_cond;
     out->coarse_seconds = fcm::coarse_seconds(C->coarse);
     out->n_jacobi = C->n_jacobi;
+    out->rows32 = C->plan.rows;
+    out->rows64 = C->plan.rows64;
+    for (int k = 0; k < 4; ++k) out->tune_seconds[k] = C->tune_seconds[k];
+    out->device_error = 0;
+    if (C->d_err) {
+        int e = 0;
+        if (cudaMemcpyAsync(&e, C->d_err, sizeof(int), cudaMemcpyDeviceToHost, C->stream) == cudaSuccess &&
+            cudaStreamSynchronize(C->stream) == cudaSuccess)
+            out->device_error = e;
+    }
     return FCM_OK;
 }
 
@@ -398,6 +408,7 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     o.cond_fp64 = 1e7;
     o.block_rule = FCM_BLOCKS_VERTEX;
     o.eta_bar = 1.0;
+    o.fixed_tiles = 0;
     if (opts) o = *opts;
     if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED) || !(o.cond_fp64 > 0.0) ||
         (o.block_rule != FCM_BLOCKS_VERTEX && o.block_rule != FCM_BLOCKS_ELEMENT) ||

@@ -21,6 +21,15 @@ struct PatchRec {
     int32_t prec;  // 0: factor stored in FP64, 1: FP32
 };
 
+// Leading dimension of a stored block factor with n rows: rows are padded to a multiple of 16
+// bytes (zeros), so a row, or a run of rows, can be moved by one bulk copy and read as 16-byte
+// vectors.  Factor offsets in a pool are multiples of 16 bytes too.
+template <typename T>
+__host__ __device__ constexpr int factor_ld(int n)
+{
+    return (n + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
+}
+
 // CG scalars kept on the device for the whole solve (no host round trip per iteration).
 struct CgScalars {
     double rz, pq, zz, zz0, alpha, beta, relres, tol;
@@ -60,7 +69,10 @@ struct SchwarzPlan {
     int nseg;
     SchwarzSeg seg[32];
     int rule;                 // 0 vertex patches, 3 element blocks (FCM_BLOCKS_*)
-    int rows;                 // rows per work item of a block with its own factor (row tiles)
+    int rows;                 // rows per work item of a block with its own FP32 factor (row tiles)
+    int rows64;               // the same for FP64 factors
+    int smem;                 // dynamic shared memory of a Schwarz CTA (schwarz_smem_bytes)
+    int *err;                 // device flag, set to 1 by a bulk-copy wait that ran out
     const double *jac;        // 1 / K_ll for the free DOFs in no block, 0 elsewhere (lattice); null if none
 };
 
@@ -70,9 +82,14 @@ void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uin
                     const KCells &kc, const int *done, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
                           const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
-// Rows per work item when a block with its own factor is split into row tiles (fixed by the
-// launch shape of the Schwarz kernels for degree p and block rule).
-int schwarz_rows_per_item(int p, int rule);
+// Row tiles of the blocks with their own factor: default rows per work item for FP32 and FP64
+// factors (4 per warp of the launch, a tile of at most kTileBudget bytes), the dynamic shared
+// memory a Schwarz CTA needs for given row counts, and the kernel attributes for it (host
+// calls, outside stream capture).
+constexpr int kTileBudget = 72 * 1024;
+void schwarz_default_rows(int p, int rule, int *rows32, int *rows64);
+int schwarz_smem_bytes(int p, int rows32, int rows64);
+cudaError_t schwarz_prepare(int p, int smem_bytes);
 // nr <= 8 right-hand sides stored nlat apart (p = 4 needs FP32 factors)
 void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,
                                 const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
@@ -157,6 +174,8 @@ struct fcm_ctx {
     fcm::PatchRec *d_patches = nullptr;
     int2 *d_batches = nullptr;
     double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
+    int *d_err = nullptr;            // set by a Schwarz CTA whose bulk-copy wait ran out
+    double tune_seconds[4] = {0, 0, 0, 0};  // S-apply times of the row-tile sizes tried
     int64_t n_jacobi = 0;
     fcm::SchwarzPlan plan = {};
     int64_t n_factors = 0, factor_bytes = 0, n_fp32_factors = 0;

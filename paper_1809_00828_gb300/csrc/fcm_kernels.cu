@@ -9,6 +9,8 @@
 //    (blocks of one colour are DOF-disjoint).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fcm_device.cuh"
 
 namespace fcm {
@@ -266,13 +268,14 @@ __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double
     }
     __syncthreads();
     const T *__restrict__ F = pool + p0.off;
+    const int ld = factor_ld<T>(n);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         T acc[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) acc[k] = (T)0;
 #pragma unroll UNROLL
         for (int j = 0; j < n; ++j) {
-            const T f = __ldg(F + (size_t)j * n + t);
+            const T f = __ldg(F + (size_t)j * ld + t);
 #pragma unroll
             for (int k = 0; k < G; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
         }
@@ -283,70 +286,148 @@ __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double
     }
 }
 
+// ---- bulk copies (cp.async.bulk, global -> shared) completed on an mbarrier
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// the single arrival of the barrier's phase, announcing `bytes` of bulk copies
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// dst, src and bytes multiples of 16
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier; gives up (false) after a bounded number of tries.
+constexpr int kWaitTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitTries; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float dot(float4 a, float4 b, float c)
+    {
+        return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
+    }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double dot(double2 a, double2 b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
+};
+
+// Bytes in front of the factor tile in the Schwarz kernel's dynamic shared memory: the
+// mbarrier (16) and the gathered residual r_B in T, padded to the factor's row length.
+template <int P>
+__host__ __device__ constexpr int rows_tile_offset()
+{
+    return 16 + (factor_ld<double>(3 * box_width(P) * box_width(P) * box_width(P)) * 8 + 15) / 16 * 16;
+}
+
 // Rows [row0, row0 + rows) of z_B += F r_B for a block with its own factor (cut blocks stream
-// their factor from DRAM).  The factor is symmetric, so row t of F is the contiguous column t
-// of the stored matrix: each warp takes 4 rows at a time and its lanes split the columns, so
-// one warp load reads 32 consecutive entries of a row and a lane keeps 16 loads in flight.
-// The row sums are finished by warp shuffles.  Splitting a block into row tiles gives the
-// launch many equal work items, so the DRAM stream does not wait on a few long blocks.
+// their factor from DRAM).  The rows of the tile are contiguous in the factor pool (the
+// factor is symmetric, rows padded to 16 bytes), so one thread starts them on their way into
+// shared memory as bulk copies before the CTA gathers r_B; the CTA then waits on the
+// copies' mbarrier.  Each warp takes 4 rows at a time, its lanes split a row into 16-byte
+// vectors (r_B's vectors stay in registers across rows), and warp shuffles finish the sums.
+// Every CTA holds one tile in flight, so a colour's launch keeps the DRAM queue full without
+// per-thread loads.  A wait that runs out sets *err and the CTA returns without writing.
 template <int P, typename T>
 __device__ __forceinline__ void apply_rows(const double *__restrict__ r, double *__restrict__ z,
                                            const T *__restrict__ pool, const PatchRec *__restrict__ patches,
                                            int first, int row0, int rows, const Grid3 &g, int rule,
-                                           unsigned char *smem)
+                                           unsigned char *smem, int *err)
 {
-    T *rb = reinterpret_cast<T *>(smem);
+    using VT = typename Vec16<T>::type;
+    constexpr int W = box_width(P), NB = 3 * W * W * W, V = 16 / (int)sizeof(T);
+    constexpr int KV = (factor_ld<T>(NB) / V + 31) / 32;  // 16-byte vectors per lane and row
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *rb = reinterpret_cast<T *>(smem + 16);
+    T *tile = reinterpret_cast<T *>(smem + rows_tile_offset<P>());
     const PatchRec pr = patches[first];
     int lo[3], d[3];
     block_box(rule, P, g, pr.v, lo, d);
-    const int n = 3 * d[0] * d[1] * d[2];
+    const int n = 3 * d[0] * d[1] * d[2], ld = factor_ld<T>(n);
+    const int row1 = min(n, row0 + rows);
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)((row1 - row0) * ld * (int)sizeof(T));
+        const char *src = reinterpret_cast<const char *>(pool + pr.off + (size_t)row0 * ld);
+        mbar_init(bar);
+        mbar_expect(bar, bytes);
+        constexpr uint32_t kChunk = 16384;
+        for (uint32_t o = 0; o < bytes; o += kChunk)
+            bulk_load(reinterpret_cast<char *>(tile) + o, src + o, bytes - o < kChunk ? bytes - o : kChunk, bar);
+    }
     auto gidx = [&](int t) -> int64_t {
         const int nl = t / 3;
         const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
         return 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + t % 3;
     };
-    for (int t = threadIdx.x; t < n; t += blockDim.x) rb[t] = (T)r[gidx(t)];
-    __syncthreads();
+    for (int t = threadIdx.x; t < ld; t += blockDim.x) rb[t] = t < n ? (T)r[gidx(t)] : (T)0;
+    __syncthreads();  // r_B gathered; the barrier is initialised
+    if (!__syncthreads_and(mbar_wait(bar, 0))) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            mbar_wait(bar, 0);  // let the copies still in flight land before the CTA leaves
+        }
+        __syncthreads();
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int row1 = min(n, row0 + rows);
-    const T *__restrict__ F = pool + pr.off;
+    const int nv = ld / V;
+    const VT *rbv = reinterpret_cast<const VT *>(rb);
+    VT xr[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) xr[k] = lane + 32 * k < nv ? rbv[lane + 32 * k] : Vec16<T>::zero();
     for (int t = row0 + 4 * w; t < row1; t += 4 * nw) {
-        // rows past row1 repeat the last row (in bounds) and are not written
-        const T *f0 = F + (size_t)t * n;
-        const T *f1 = F + (size_t)min(t + 1, row1 - 1) * n;
-        const T *f2 = F + (size_t)min(t + 2, row1 - 1) * n;
-        const T *f3 = F + (size_t)min(t + 3, row1 - 1) * n;
-        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-        for (int j0 = 0; j0 < n; j0 += 128) {
-            T v0[4], v1[4], v2[4], v3[4], x[4];
+        T a[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = j0 + 32 * u + lane;
-                const bool in = j < n;
-                v0[u] = in ? __ldg(f0 + j) : (T)0;
-                v1[u] = in ? __ldg(f1 + j) : (T)0;
-                v2[u] = in ? __ldg(f2 + j) : (T)0;
-                v3[u] = in ? __ldg(f3 + j) : (T)0;
-                x[u] = in ? rb[j] : (T)0;
-            }
+        for (int q = 0; q < 4; ++q) {
+            // rows past row1 repeat the last row (in bounds) and are not written
+            const VT *fr = reinterpret_cast<const VT *>(tile + (size_t)(min(t + q, row1 - 1) - row0) * ld);
+            T acc = (T)0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a0 = fma(v0[u], x[u], a0);
-                a1 = fma(v1[u], x[u], a1);
-                a2 = fma(v2[u], x[u], a2);
-                a3 = fma(v3[u], x[u], a3);
-            }
+            for (int k = 0; k < KV; ++k)
+                if (lane + 32 * k < nv) acc = Vec16<T>::dot(fr[lane + 32 * k], xr[k], acc);
+            a[q] = acc;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
-        }
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
         if (lane < 4 && t + lane < row1) {
-            const T a = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
-            z[gidx(t + lane)] += (double)a;
+            const T v = lane == 0 ? a[0] : lane == 1 ? a[1] : lane == 2 ? a[2] : a[3];
+            z[gidx(t + lane)] += (double)v;
         }
     }
 }
@@ -379,9 +460,10 @@ __device__ __forceinline__ void apply_multi_rows(const double *__restrict__ r, d
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int row1 = min(n, row0 + rows);
     const T *__restrict__ F = pool + pr.off;
+    const int ld = factor_ld<T>(n);
     for (int t = row0 + 2 * w; t < row1; t += 2 * nw) {
-        const T *f0 = F + (size_t)t * n;
-        const T *f1 = F + (size_t)min(t + 1, row1 - 1) * n;
+        const T *f0 = F + (size_t)t * ld;
+        const T *f1 = F + (size_t)min(t + 1, row1 - 1) * ld;
         T a[2][MR];
 #pragma unroll
         for (int k = 0; k < MR; ++k) a[0][k] = a[1][k] = (T)0;
@@ -439,13 +521,14 @@ __device__ __forceinline__ void apply_multi(const double *__restrict__ r, double
         }
         __syncthreads();
         const T *__restrict__ F = pool + pr.off;
+        const int ld = factor_ld<T>(n);
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             T acc[MR];
 #pragma unroll
             for (int k = 0; k < MR; ++k) acc[k] = (T)0;
 #pragma unroll UNROLL
             for (int j = 0; j < n; ++j) {
-                const T f = __ldg(F + (size_t)j * n + t);
+                const T f = __ldg(F + (size_t)j * ld + t);
 #pragma unroll
                 for (int k = 0; k < MR; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
             }
@@ -461,7 +544,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     schwarz_multi_kernel(const double *__restrict__ r, double *__restrict__ z, int64_t nlat, int nr,
                          const double *__restrict__ f64, const float *__restrict__ f32,
                          const PatchRec *__restrict__ patches, const int2 *__restrict__ batches, Grid3 g, int rule,
-                         int rows, const int *__restrict__ done)
+                         int rows32, int rows64, const int *__restrict__ done)
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W;
     __shared__ __align__(16) unsigned char smem[NB * 8 * (P == 4 ? 4 : 8)];
@@ -470,9 +553,9 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     const int count = bt.y & 255, kind = bt.y >> 8;
     // single-factor items carry a row tile index in place of the block count
     if (kind == kF32Single)
-        apply_multi_rows<P, float>(r, z, nlat, nr, f32, patches, bt.x, count * rows, rows, g, rule, smem);
+        apply_multi_rows<P, float>(r, z, nlat, nr, f32, patches, bt.x, count * rows32, rows32, g, rule, smem);
     else if (kind == kF64Single && P < 4)
-        apply_multi_rows<P, double>(r, z, nlat, nr, f64, patches, bt.x, count * rows, rows, g, rule, smem);
+        apply_multi_rows<P, double>(r, z, nlat, nr, f64, patches, bt.x, count * rows64, rows64, g, rule, smem);
     else if (kind == kF32Shared)
         apply_multi<P, float, 8>(r, z, nlat, nr, f32, patches, bt.x, count, g, rule, smem);
     else if (P < 4)
@@ -481,27 +564,26 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
 
 // One colour of the Schwarz apply (Sec. 3.1 Eq. (5)): each CTA takes one work item (a
 // shared-factor batch, or a row tile of a block with its own factor; FP32 or FP64 factor).
-// The blocks of one colour are DOF-disjoint, so the scatter needs no atomics.
+// The blocks of one colour are DOF-disjoint, so the scatter needs no atomics.  Dynamic shared
+// memory: schwarz_smem_bytes(P, rows32, rows64).
 template <int P>
 __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * box_width(P)))
     schwarz_colour_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ f64,
                           const float *__restrict__ f32, const PatchRec *__restrict__ patches,
-                          const int2 *__restrict__ batches, Grid3 g, int rule, int rows,
+                          const int2 *__restrict__ batches, Grid3 g, int rule, int rows32, int rows64, int *err,
                           const int *__restrict__ done)
 {
-    constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8);
-    constexpr int ROW = (GD * 8 > 8 * 4 ? GD * 8 : 8 * 4);  // bytes of one rbT row, largest variant
-    // rbT, then the batch's block bases (8 x int64) and box offsets (NB x int)
-    __shared__ __align__(16) unsigned char smem[NB * ROW + 64 + 4 * NB];
+    constexpr int GD = (P == 4 ? 4 : 8);
+    extern __shared__ __align__(128) unsigned char smem[];
     if (done && *done) return;
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
     switch (kind) {
     case kF32Shared: apply_batch<P, 8, float, 4>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
     // single-factor items carry a row tile index in place of the block count
-    case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows, rows, g, rule, smem); break;
+    case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows32, rows32, g, rule, smem, err); break;
     case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, rule, smem); break;
-    default: apply_rows<P, double>(r, z, f64, patches, bt.x, count * rows, rows, g, rule, smem); break;
+    default: apply_rows<P, double>(r, z, f64, patches, bt.x, count * rows64, rows64, g, rule, smem, err); break;
     }
 }
 
@@ -555,8 +637,8 @@ void schwarz_launch(const Grid3 &g, const double *r, double *z, const double *f6
     for (int i = 0; i < plan.nseg; ++i) {
         const SchwarzSeg &sg = plan.seg[i];
         if (sg.count > 0)
-            schwarz_colour_kernel<P><<<sg.count, threads, 0, s>>>(r, z, f64, f32, plan.patches, plan.batches + sg.first,
-                                                                  g, plan.rule, plan.rows, done);
+            schwarz_colour_kernel<P><<<sg.count, threads, plan.smem, s>>>(
+                r, z, f64, f32, plan.patches, plan.batches + sg.first, g, plan.rule, plan.rows, plan.rows64, plan.err, done);
     }
 }
 
@@ -569,7 +651,7 @@ void schwarz_multi_launch(const Grid3 &g, const double *r, double *z, int64_t nl
         const SchwarzSeg &sg = plan.seg[i];
         if (sg.count > 0)
             schwarz_multi_kernel<P><<<sg.count, threads, 0, s>>>(r, z, nlat, nr, f64, f32, plan.patches,
-                                                                 plan.batches + sg.first, g, plan.rule, plan.rows, done);
+                                                                 plan.batches + sg.first, g, plan.rule, plan.rows, plan.rows64, done);
     }
 }
 
@@ -594,7 +676,59 @@ void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uin
     }
 }
 
-int schwarz_rows_per_item(int p, int rule) { return 4 * (schwarz_threads(p, rule) / 32); }
+namespace {
+
+// Batches: rbT, then the block bases and box offsets; row tiles: mbarrier, r_B, the tile.
+template <int P>
+int smem_bytes_p(int rows32, int rows64)
+{
+    constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
+    const int batch = NB * ROW + 64 + 4 * NB;
+    const int t32 = rows_tile_offset<P>() + rows32 * factor_ld<float>(NB) * 4;
+    const int t64 = rows_tile_offset<P>() + rows64 * factor_ld<double>(NB) * 8;
+    return std::max(batch, std::max(t32, t64));
+}
+
+template <int P>
+cudaError_t prepare_p(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(schwarz_colour_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(schwarz_colour_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+}  // namespace
+
+void schwarz_default_rows(int p, int rule, int *rows32, int *rows64)
+{
+    // 4 rows per warp of the launch, as long as a tile stays within kTileBudget bytes
+    const int nb = 3 * box_width(p) * box_width(p) * box_width(p);
+    const int full = 4 * (schwarz_threads(p, rule) / 32);
+    const int cap32 = kTileBudget / (factor_ld<float>(nb) * 4), cap64 = kTileBudget / (factor_ld<double>(nb) * 8);
+    *rows32 = std::max(4, std::min(full, cap32) / 4 * 4);
+    *rows64 = std::max(4, std::min(full, cap64) / 4 * 4);
+}
+
+int schwarz_smem_bytes(int p, int rows32, int rows64)
+{
+    switch (p) {
+    case 1: return smem_bytes_p<1>(rows32, rows64);
+    case 2: return smem_bytes_p<2>(rows32, rows64);
+    case 3: return smem_bytes_p<3>(rows32, rows64);
+    default: return smem_bytes_p<4>(rows32, rows64);
+    }
+}
+
+cudaError_t schwarz_prepare(int p, int smem_bytes)
+{
+    switch (p) {
+    case 1: return prepare_p<1>(smem_bytes);
+    case 2: return prepare_p<2>(smem_bytes);
+    case 3: return prepare_p<3>(smem_bytes);
+    default: return prepare_p<4>(smem_bytes);
+    }
+}
 
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *f64, const float *f32,
                           const SchwarzPlan &plan, const int *done, cudaStream_t s)

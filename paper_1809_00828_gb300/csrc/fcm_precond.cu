@@ -223,8 +223,13 @@ __global__ void finalize_kernel(const double *C, int n, const int *rep, const in
     const BoxInfo bx = block_box_of(rule, p, g, rep[b]);
     const double *Cb = C + (size_t)b * n * n;
     double *F = pool + off[b];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
+    const int ld = factor_ld<double>(n);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * ld; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        if (j >= n) {
+            F[e] = 0.0;  // row padding
+            continue;
+        }
         auto gidx = [&](int t) {
             const int nl = t / 3;
             const int x = bx.lo[0] + nl % bx.d[0], y = bx.lo[1] + (nl / bx.d[0]) % bx.d[1], z = bx.lo[2] + nl / (bx.d[0] * bx.d[1]);
@@ -235,16 +240,20 @@ __global__ void finalize_kernel(const double *C, int n, const int *rep, const in
     }
 }
 
-__global__ void to_f32_kernel(const double *in, float *out, int64_t n)
+// FP64 factor (rows padded to factor_ld<double>) -> FP32 factor (rows padded to factor_ld<float>)
+__global__ void to_f32_kernel(const double *in, float *out, int n)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (float)in[i];
+    const int ldi = factor_ld<double>(n), ldo = factor_ld<float>(n);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * ldo; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldo), j = (int)(e % ldo);
+        out[e] = j < n ? (float)in[(size_t)i * ldi + j] : 0.f;
+    }
 }
 
 struct FactorInfo {
     int rep;      // representative vertex
     int n;        // box size
-    int64_t off;  // offset in the FP64 staging pool
+    int64_t off;  // offset in the FP64 staging pool (16-byte aligned, rows padded to factor_ld<double>)
     double cond;
     int nfilt;
 };
@@ -357,8 +366,9 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     int maxn = 0;
     for (auto &kv : groups)
         for (int f : kv.second) {
+            total = (total + 1) / 2 * 2;  // 16-byte alignment
             fac[f].off = total;
-            total += (int64_t)kv.first * kv.first;
+            total += (int64_t)kv.first * factor_ld<double>(kv.first);
             maxn = std::max(maxn, kv.first);
         }
 
@@ -485,16 +495,20 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     const bool mixed = o.precision == FCM_PREC_MIXED;
     std::vector<int> prec(fac.size(), 0);
     std::vector<int64_t> off(fac.size(), 0);
-    int64_t n64 = 0, n32 = 0;
+    int64_t n64 = 0, n32 = 0, alg_bytes = 0;
     for (size_t f = 0; f < fac.size(); ++f) {
-        const int64_t sz = (int64_t)fac[f].n * fac[f].n;
+        const int n = fac[f].n;
         if (mixed && fac[f].cond <= o.cond_fp64) {
             prec[f] = 1;
+            n32 = (n32 + 3) / 4 * 4;
             off[f] = n32;
-            n32 += sz;
+            n32 += (int64_t)n * factor_ld<float>(n);
+            alg_bytes += (int64_t)n * n * 4;
         } else {
+            n64 = (n64 + 1) / 2 * 2;
             off[f] = n64;
-            n64 += sz;
+            n64 += (int64_t)n * factor_ld<double>(n);
+            alg_bytes += (int64_t)n * n * 8;
         }
     }
     if (C->d_f64) cudaFree(C->d_f64);
@@ -508,9 +522,9 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         if (n64 > 0) PC_CUDA(cudaMalloc(&C->d_f64, sizeof(double) * n64));
         if (n32 > 0) PC_CUDA(cudaMalloc(&C->d_f32, sizeof(float) * n32));
         for (size_t f = 0; f < fac.size(); ++f) {
-            const int64_t sz = (int64_t)fac[f].n * fac[f].n;
+            const int64_t sz = (int64_t)fac[f].n * factor_ld<double>(fac[f].n);
             if (prec[f] == 1)
-                to_f32_kernel<<<(int)std::min<int64_t>((sz + 255) / 256, 1024), 256, 0, st>>>(stage + fac[f].off, C->d_f32 + off[f], sz);
+                to_f32_kernel<<<(int)std::min<int64_t>((sz + 255) / 256, 1024), 256, 0, st>>>(stage + fac[f].off, C->d_f32 + off[f], fac[f].n);
             else
                 PC_CUDA(cudaMemcpyAsync(C->d_f64 + off[f], stage + fac[f].off, sizeof(double) * sz, cudaMemcpyDeviceToDevice, st));
         }
@@ -541,14 +555,16 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     // One launch per colour.  Work items, heaviest first so that the tail of the launch is short:
     // FP64 shared-factor batches, FP64 single blocks, FP32 single blocks (DRAM-bound), FP32 batches.
     // Kinds as in fcm_kernels.cu: 0 FP32 shared, 1 FP32 single, 2 FP64 shared, 3 FP64 single.
+    // `units` lists, colour by colour, a batch (first record, count) or a single block (record,
+    // rows); the work items follow from them once the row-tile sizes are chosen.
+    struct Unit {
+        int rec, kind, size;  // size: block count of a batch, rows of a single block
+    };
     std::vector<PatchRec> all;
-    std::vector<int2> batches;
-    SchwarzPlan plan = {};
-    const int rows = schwarz_rows_per_item(p, rule);
-    plan.rows = rows;
+    std::vector<Unit> units;
+    int unit_colour_end[8];
     const int order[4][2] = {{0, 1}, {0, 0}, {1, 0}, {1, 1}};  // (precision 0 = FP64 / 1 = FP32, shared?)
     for (int c = 0; c < 8; ++c) {
-        SchwarzSeg sg = {c, -1, 0, (int)batches.size(), 0};
         for (const auto &o : order) {
             const int pr = o[0], shared = o[1];
             const int kind = pr == 1 ? (shared ? 0 : 1) : (shared ? 2 : 3);
@@ -558,29 +574,111 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
                 if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
                 for (size_t s0 = 0; s0 < vs.size(); s0 += cap) {
                     const int cnt = (int)std::min<size_t>(cap, vs.size() - s0);
-                    if (shared) {
-                        batches.push_back(make_int2((int)all.size(), cnt | (kind << 8)));
-                    } else {
-                        // a block with its own factor is split into row tiles of `rows` rows; the
-                        // items carry the tile index in place of the count
-                        for (int t = 0; t * rows < fac[f].n; ++t) batches.push_back(make_int2((int)all.size(), t | (kind << 8)));
-                    }
+                    units.push_back({(int)all.size(), kind, shared ? cnt : fac[f].n});
                     for (int k = 0; k < cnt; ++k) all.push_back({off[f], vs[s0 + k], prec[f]});
                 }
             }
         }
-        sg.count = (int)batches.size() - sg.first;
-        if (sg.count > 0) plan.seg[plan.nseg++] = sg;
+        unit_colour_end[c] = (int)units.size();
     }
+    SchwarzPlan plan = {};
+    plan.rule = rule;
+    // a block with its own factor is split into row tiles of rows32 (FP32) or rows64 (FP64) rows;
+    // its items carry the tile index in place of the count
+    auto make_items = [&](int rows32, int rows64, std::vector<int2> &items, SchwarzPlan &pl) {
+        items.clear();
+        pl.nseg = 0;
+        int u = 0;
+        for (int c = 0; c < 8; ++c) {
+            SchwarzSeg sg = {c, -1, 0, (int)items.size(), 0};
+            for (; u < unit_colour_end[c]; ++u) {
+                const Unit &un = units[u];
+                if (un.kind == 0 || un.kind == 2) {
+                    items.push_back(make_int2(un.rec, un.size | (un.kind << 8)));
+                } else {
+                    const int rws = un.kind == 1 ? rows32 : rows64;
+                    for (int t = 0; t * rws < un.size; ++t) items.push_back(make_int2(un.rec, t | (un.kind << 8)));
+                }
+            }
+            sg.count = (int)items.size() - sg.first;
+            if (sg.count > 0) pl.seg[pl.nseg++] = sg;
+        }
+        pl.rows = rows32;
+        pl.rows64 = rows64;
+        pl.smem = schwarz_smem_bytes(p, rows32, rows64);
+    };
+    int rows32 = 0, rows64 = 0;
+    schwarz_default_rows(p, rule, &rows32, &rows64);
+    // candidate row-tile sizes: the default (4 rows per warp, tile within kTileBudget), half and a
+    // quarter of it (more, shorter work items)
+    std::vector<std::pair<int, int>> cand = {{rows32, rows64}};
+    if (!o.fixed_tiles)
+        for (int dv : {2, 4}) {
+            const std::pair<int, int> c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(4, rows64 / dv / 4 * 4)};
+            if (c2 != cand.back()) cand.push_back(c2);
+        }
+    std::vector<int2> batches;
+    size_t max_items = 0;
+    for (const auto &c2 : cand) {
+        make_items(c2.first, c2.second, batches, plan);
+        max_items = std::max(max_items, batches.size());
+    }
+    make_items(rows32, rows64, batches, plan);
+    if (!C->d_err) PC_CUDA(cudaMalloc(&C->d_err, sizeof(int)));
+    PC_CUDA(cudaMemsetAsync(C->d_err, 0, sizeof(int), st));
+    plan.err = C->d_err;
+    PC_CUDA(schwarz_prepare(p, schwarz_smem_bytes(p, rows32, rows64)));  // the largest tile of the candidates
     if (C->d_patches) cudaFree(C->d_patches);
     if (C->d_batches) cudaFree(C->d_batches);
     C->d_patches = nullptr;
     C->d_batches = nullptr;
     PC_CUDA(cudaMalloc(&C->d_patches, sizeof(PatchRec) * std::max<size_t>(all.size(), 1)));
-    PC_CUDA(cudaMalloc(&C->d_batches, sizeof(int2) * std::max<size_t>(batches.size(), 1)));
+    PC_CUDA(cudaMalloc(&C->d_batches, sizeof(int2) * std::max<size_t>(max_items, 1)));
     PC_CUDA(cudaMemcpyAsync(C->d_patches, all.data(), sizeof(PatchRec) * all.size(), cudaMemcpyHostToDevice, st));
     PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
     PC_CUDA(cudaStreamSynchronize(st));
+    plan.patches = C->d_patches;
+    plan.batches = C->d_batches;
+    for (int k = 0; k < 4; ++k) C->tune_seconds[k] = 0.0;
+    if (cand.size() > 1) {
+        // autotuner: S applied to the load vector (a field with the problem's own structure) into
+        // the z work vector, 2 warm-up and 5 timed applies per candidate on the context's stream
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        PC_CUDA(cudaEventCreate(&e0));
+        PC_CUDA(cudaEventCreate(&e1));
+        double best = 1e300;
+        size_t best_k = 0;
+        std::string fail;
+        for (size_t k = 0; k < cand.size() && fail.empty(); ++k) {
+            make_items(cand[k].first, cand[k].second, batches, plan);
+            if (cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
+                fail = "autotune upload";
+                break;
+            }
+            for (int w = 0; w < 2; ++w) launch_schwarz_apply(p, g, C->d_rhs, C->d_z, C->d_f64, C->d_f32, plan, nullptr, st);
+            cudaEventRecord(e0, st);
+            for (int w = 0; w < 5; ++w) launch_schwarz_apply(p, g, C->d_rhs, C->d_z, C->d_f64, C->d_f32, plan, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+                fail = "autotune run";
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            C->tune_seconds[k] = ms / 5e3;
+            if (C->tune_seconds[k] < best) {
+                best = C->tune_seconds[k];
+                best_k = k;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (!fail.empty()) return fail + ": " + cudaGetErrorString(cudaGetLastError());
+        make_items(cand[best_k].first, cand[best_k].second, batches, plan);
+        PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
+        PC_CUDA(cudaStreamSynchronize(st));
+    }
     plan.patches = C->d_patches;
     plan.batches = C->d_batches;
     plan.rule = rule;
@@ -613,7 +711,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     plan.jac = C->d_jac;
     C->plan = plan;
     C->n_factors = (int64_t)fac.size();
-    C->factor_bytes = n64 * 8 + n32 * 4;
+    C->factor_bytes = alg_bytes;  // n^2 entries per factor (the stored rows carry < 16 bytes of padding)
     C->max_block = maxn;
     C->n_fp32_factors = 0;
     C->max_cond = 0.0;

@@ -55,12 +55,14 @@ class Info(ctypes.Structure):
                 ("p", ctypes.c_int), ("setup_seconds", ctypes.c_double), ("precond_seconds", ctypes.c_double),
                 ("n_blocks", ctypes.c_int64), ("n_blocks_fp32", ctypes.c_int64), ("kapply_fmas", ctypes.c_int64),
                 ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double),
-                ("coarse_seconds", ctypes.c_double), ("n_jacobi", ctypes.c_int64)]
+                ("coarse_seconds", ctypes.c_double), ("n_jacobi", ctypes.c_int64),
+                ("rows32", ctypes.c_int), ("rows64", ctypes.c_int), ("tune_seconds", ctypes.c_double * 4),
+                ("device_error", ctypes.c_int)]
 
 
 class PrecondOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("cond_fp64", ctypes.c_double),
-                ("block_rule", ctypes.c_int), ("eta_bar", ctypes.c_double)]
+                ("block_rule", ctypes.c_int), ("eta_bar", ctypes.c_double), ("fixed_tiles", ctypes.c_int)]
 
 
 BLOCKS_VERTEX, BLOCKS_ELEMENT = 0, 3
@@ -157,7 +159,7 @@ class Solver:
     def get_info(self):
         inf = Info()
         self._check(load().fcm_info(self.ctx, ctypes.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in Info._fields_}
+        return {k: (list(getattr(inf, k)) if k == "tune_seconds" else getattr(inf, k)) for k, _ in Info._fields_}
 
     def empty(self, nrhs=1):
         return self._torch.zeros(nrhs * self.n, dtype=self._torch.float64, device="cuda")
@@ -167,9 +169,12 @@ class Solver:
         self._check(load().fcm_rhs(self.ctx, load_case, _ptr(b)))
         return b
 
-    def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0):
+    def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0,
+                      autotune=True):
         """blocks: "vertex" (vertex patches) or "element" (element blocks of the cells with
-        eta_T < eta_bar, diagonal scaling for the DOFs in no block)."""
+        eta_T < eta_bar, diagonal scaling for the DOFs in no block).  autotune: time the
+        Schwarz apply for a few row-tile sizes and keep the fastest (results do not depend
+        on the choice)."""
         if blocks not in ("vertex", "element"):
             raise ValueError(f"unknown block rule {blocks!r}")
         o = PrecondOpts()
@@ -178,6 +183,7 @@ class Solver:
         o.cond_fp64 = cond_fp64
         o.block_rule = BLOCKS_ELEMENT if blocks == "element" else BLOCKS_VERTEX
         o.eta_bar = eta_bar
+        o.fixed_tiles = 0 if autotune else 1
         self._check(load().fcm_precond_build(self.ctx, ctypes.byref(o)))
         self.info = self.get_info()
 

@@ -216,3 +216,23 @@ def test_multi_rhs_solve_matches_separate_solves(single):
         x_dense = np.linalg.solve(K, P.load(k + 1))
         assert P.energy_error(x_dense, uk.cpu().numpy()[P.free_lat]) < 1e-8
     assert its == max(its_each) and rel <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_row_tile_autotuner_leaves_S_unchanged(precision):
+    # p = 3 porous cube: cut patches stream their own factors in row tiles (FP32 and FP64 in the
+    # mixed build); the tile size the build picks by timing must not change S r by a bit
+    w = I.workload_porous(11, 6, 3, 10, 1e-10, 3, 1e-8)
+    s = _solver(w)
+    x = _lat(I.random_vector(5, s.n))
+    s.precond_build(precision=precision, autotune=False)
+    z0 = s.apply_S(x).clone()
+    info0 = s.get_info()
+    s.precond_build(precision=precision)
+    z1 = s.apply_S(x)
+    info1 = s.get_info()
+    assert torch.equal(z0, z1)
+    assert info0["tune_seconds"] == [0.0] * 4 and sum(t > 0 for t in info1["tune_seconds"]) >= 2
+    assert info0["device_error"] == 0 and info1["device_error"] == 0
+    assert info1["rows32"] <= info0["rows32"] and info1["rows64"] <= info0["rows64"]
+    s.close()
