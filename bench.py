@@ -215,7 +215,7 @@ def _describe(w, args):
 
 def _blocks(args):
     if args.blocks == "element":
-        return (f"element blocks for the cells with eta_T < {args.eta_bar:g} and diagonal scaling of the DOFs "
+        return (f"element blocks for the cells with eta_T <= {args.eta_bar:g} and diagonal scaling of the DOFs "
                 f"in no block")
     return "vertex-patch blocks"
 
@@ -496,7 +496,8 @@ def main():
     ap.add_argument("--blocks", default="vertex", choices=["vertex", "element"],
                     help="Schwarz blocks: vertex patches, or the paper's element blocks with --eta-bar")
     ap.add_argument("--eta-bar", type=float, default=1.0,
-                    help="element blocks for the cells with volume fraction below this; the rest diagonal")
+                    help="element blocks for the cells with volume fraction at most this (1: every cell); "
+                         "the DOFs in no block diagonal")
     ap.add_argument("--ref-iterations", type=int, default=None,
                     help="iteration count that scales the reference arm's per-iteration time (default 877, the plain "
                          "FP64 Schwarz-PCG count of porous40_32_p3, which the oracle's algorithm shares)")

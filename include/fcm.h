@@ -132,9 +132,10 @@ enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
  *        cells whose closure contains it (every free DOF is covered).
  *        FCM_BLOCKS_ELEMENT (3): the paper's element blocks (Sec. 3.2,
  *        "Optimizing the number of blocks"): for every active cell with volume
- *        fraction eta_T < eta_bar, all functions supported on the cell; the free
+ *        fraction eta_T <= eta_bar, all functions supported on the cell; the free
  *        DOFs in no block get Algorithm 1's diagonal scaling 1 / K_ll.
- *        eta_bar = 0 gives pure Jacobi; eta_bar > 1 blocks every active cell.
+ *        eta_bar = 0 gives pure Jacobi; eta_bar = 1 blocks every active cell
+ *        (Sec. 5.2's end points; eta_T is clamped to 1 against rounding).
  *   eta_bar: threshold of FCM_BLOCKS_ELEMENT (ignored by FCM_BLOCKS_VERTEX).
  *   fixed_tiles: 0 (default) lets the build time the Schwarz apply for up to
  *        three row-tile sizes of the cut blocks (the rows of a factor handled

@@ -768,7 +768,11 @@ static int add_block(ora_problem *P, int *cap, int n, int *idx)
  *   rule 1: one block with every free DOF (S = A^-1, Sec. 3.1)
  *   rule 2: no blocks (pure diagonal scaling, i.e. Jacobi)
  *   rule 3: element blocks (all functions supported on a cell) for active
- *           cells with eta_T < eta_bar (Sec. 3.2 "Optimizing the number of blocks") */
+ *           cells with eta_T <= eta_bar (Sec. 3.2 "Optimizing the number of
+ *           blocks"; the study of Sec. 5.2 fixes the end points: eta_bar = 1
+ *           gives a block for every element, eta_bar = 0 pure diagonal
+ *           scaling).  eta_T is a volume fraction, so it is clamped to 1
+ *           against the rounding of its quadrature. */
 int ora_precond_build(ora_problem *P, int rule, double eps, double eta_bar)
 {
     const ora_desc *d = &P->d;
@@ -801,7 +805,7 @@ int ora_precond_build(ora_problem *P, int rule, double eps, double eta_bar)
             for (int cy = 0; cy < d->n[1]; ++cy)
                 for (int cx = 0; cx < d->n[0]; ++cx) {
                     int ci = cx + d->n[0] * (cy + d->n[1] * cz);
-                    if (!P->active[ci] || !(P->eta[ci] < eta_bar)) continue;
+                    if (!P->active[ci] || !((P->eta[ci] < 1.0 ? P->eta[ci] : 1.0) <= eta_bar)) continue;
                     int n = 0;
                     for (int iz = 0; iz <= p; ++iz)
                         for (int iy = 0; iy <= p; ++iy)

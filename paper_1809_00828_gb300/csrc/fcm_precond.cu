@@ -7,7 +7,7 @@
 // contains v; in lattice terms the box [p v - (p-1), p v + (p-1)] per axis
 // (clipped at the domain).  Element blocks (rule 3, the paper's rule, Sec. 3.2
 // "Optimizing the number of blocks"): for each active cell with volume
-// fraction eta_T < eta_bar, every function supported on the cell, the box
+// fraction eta_T <= eta_bar, every function supported on the cell, the box
 // [p c, p c + p]; the free DOFs in no block get Algorithm 1's diagonal
 // scaling 1 / K_ll.  A block is stored densely over its box, with zero rows
 // and columns for box DOFs that are not free.  Blocks whose contributing cells
@@ -292,7 +292,8 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
             for (int cy = 0; cy < g.n[1]; ++cy)
                 for (int cx = 0; cx < g.n[0]; ++cx) {
                     const int c = cx + g.n[0] * (cy + g.n[1] * cz);
-                    if (hp.cell_elem[c] < 0 || !(hp.eta[c] < o.eta_bar)) continue;
+                    // eta_T is a volume fraction: clamped to 1 against the rounding of its quadrature
+                    if (hp.cell_elem[c] < 0 || !(std::min(hp.eta[c], 1.0) <= o.eta_bar)) continue;
                     const BoxInfo bx = element_box(p, cx, cy, cz);
                     if (!box_has_free(bx)) continue;
                     // 2 bits per contributing cell: 0 outside the grid, 1 inactive, 2 uncut; any cut

@@ -172,7 +172,7 @@ class Solver:
     def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0,
                       autotune=True):
         """blocks: "vertex" (vertex patches) or "element" (element blocks of the cells with
-        eta_T < eta_bar, diagonal scaling for the DOFs in no block).  autotune: time the
+        eta_T <= eta_bar, diagonal scaling for the DOFs in no block).  autotune: time the
         Schwarz apply for a few row-tile sizes and keep the fastest (results do not depend
         on the choice)."""
         if blocks not in ("vertex", "element"):

@@ -331,6 +331,27 @@ def test_size_one_blocks_are_jacobi(single_void):
     assert np.allclose(z, r / P.csr().diagonal(), rtol=4e-16, atol=0.0)
 
 
+def test_element_block_threshold_end_points(single_void):
+    # Sec. 5.2: eta_bar = 0 is diagonal scaling (Jacobi), eta_bar = 1 a block for every element;
+    # in between, exactly the cells with eta_T <= eta_bar get a block (Sec. 3.2).
+    w, P = single_void
+    r = I.random_vector(4, P.nfree)
+    P.precond_build(2)
+    z_jac = P.apply_S(r)
+    assert P.precond_build(3, 1e-13, 0.0) == 0
+    assert np.array_equal(P.apply_S(r), z_jac)
+    eta = P.eta()
+    active = eta > 0
+    assert P.precond_build(3, 1e-13, 1.0) == int(active.sum())
+    # with every element a block, every free DOF is in a block: S has no diagonal-only rows left,
+    # so S r differs from the Jacobi result in every entry with a nonzero neighbour coupling
+    z_all = P.apply_S(r)
+    assert np.count_nonzero(np.isclose(z_all, z_jac, rtol=1e-12, atol=0.0)) < P.nfree // 100
+    cut = active & (eta < 1.0 - 1e-12)
+    thr = float(np.median(eta[cut]))
+    assert P.precond_build(3, 1e-13, thr) == int((active & (np.minimum(eta, 1.0) <= thr)).sum())
+
+
 def test_vertex_patch_membership_and_overlap(single_void):
     w, P = single_void
     P.precond_build(0)
