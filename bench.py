@@ -270,6 +270,8 @@ def run_fcm(args, rank, world, local_rank):
     u = s.empty(nrhs)
     stream = torch.cuda.current_stream()
     net, gamma = None, 0.0
+    if args.form == "coarse":
+        s.set_stall_window(args.stall_window)
     if args.form == "coarse" and args.net:
         from paper_1809_00828_gb300 import learned
         net, gamma = learned.load(args.net)
@@ -489,6 +491,8 @@ def main():
     ap.add_argument("--form", default="coarse", choices=["coarse", "pcg"],
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
     ap.add_argument("--coarse-iters", type=int, default=20)
+    ap.add_argument("--stall-window", type=int, default=100,
+                    help="iterations without halving after which the flexible CG falls back to plain PCG")
     ap.add_argument("--net", default=None, help="U-Net checkpoint whose prediction starts the coarse solve")
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--loads", default="traction", choices=["traction", "strain6"],

@@ -285,7 +285,8 @@ fcm_status fcm_coarse_apply(fcm_ctx *ctx, const float *x_cells_dev, float *y_cel
  * is K-orthogonalised against the previous four (truncated flexible CG,
  * FCG(4), Notay 2000).  Convergence is judged by the plain Schwarz residual
  * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the judged residual grows
- * 100-fold over its best value, has not halved within 100 iterations, or a
+ * 100-fold over its best value, has not halved within the stall window
+ * (100 iterations unless set by fcm_fpcg_set_stall_window), or a
  * scalar breaks down, the solve falls back to plain Schwarz-PCG on the
  * remaining residual, from the current iterate (fcm_last_solve reports it).
  * iterations counts K applications of both phases on the fine lattice.
@@ -293,6 +294,13 @@ fcm_status fcm_coarse_apply(fcm_ctx *ctx, const float *x_cells_dev, float *y_cel
  * FCM_ENOTCONV when maxit is reached. */
 fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, int coarse_iters, const double *rhs_dev,
                           double tol, int maxit, double *u_dev, int *iterations, double *final_relres);
+
+/* Stall window of fcm_fpcg_solve: the flexible phase gives way to plain
+ * Schwarz-PCG when the judged residual has not halved within this many
+ * iterations (default 100).  The judged residual of CG is not monotone, so on
+ * slowly converging problems a longer window keeps the coarse correction in
+ * use through plateaus.  Returns FCM_EINVAL for window < 1. */
+fcm_status fcm_fpcg_set_stall_window(fcm_ctx *ctx, int window);
 
 /* Same as fcm_fpcg_solve with host buffers: rhs_host (n_lattice doubles) is
  * copied to the device, solved, and the solution copied back into u_host

@@ -38,7 +38,6 @@ namespace fcm {
 
 constexpr int kM = 4;          // FCG(m): directions kept for the explicit K-orthogonalisation
 constexpr int kFcgChunk = 4;   // iterations per captured graph
-constexpr int kStallWindow = 100;
 
 struct FcgScalars {
     double pq[kM];     // p_j . K p_j, by ring slot
@@ -560,6 +559,17 @@ fcm_status fcm_coarse_prolong(fcm_ctx *C, const float *cells, double s, double *
     return FCM_OK;
 }
 
+fcm_status fcm_fpcg_set_stall_window(fcm_ctx *C, int window)
+{
+    if (!C) return FCM_EINVAL;
+    if (window < 1) {
+        C->err = "fcm_fpcg_set_stall_window: window must be >= 1";
+        return FCM_EINVAL;
+    }
+    C->fcg_window = window;
+    return FCM_OK;
+}
+
 fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_iters, const double *rhs, double tol,
                           int maxit, double *u, int *iterations, double *final_relres)
 {
@@ -602,7 +612,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     std::memset(&h, 0, sizeof h);
     h.tol = tol;
     h.maxit = maxit;
-    h.window = kStallWindow;
+    h.window = C->fcg_window;
     CO_CUDA(C, cudaMemcpyAsync(F->d, &h, sizeof h, cudaMemcpyHostToDevice, st));
     CO_CUDA(C, cudaEventRecord(C->ev_t0, st));
     CO_CUDA(C, cudaMemsetAsync(x, 0, sizeof(double) * n, st));

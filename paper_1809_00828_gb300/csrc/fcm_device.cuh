@@ -175,6 +175,7 @@ struct fcm_ctx {
     int2 *d_batches = nullptr;
     double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
     int *d_err = nullptr;            // set by a Schwarz CTA whose bulk-copy wait ran out
+    int fcg_window = 100;            // stall window of the flexible CG (fcm_fpcg_set_stall_window)
     double tune_seconds[4] = {0, 0, 0, 0};  // S-apply times of the row-tile sizes tried
     int64_t n_jacobi = 0;
     fcm::SchwarzPlan plan = {};

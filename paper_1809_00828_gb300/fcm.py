@@ -24,7 +24,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy",
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
-            "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host")
+            "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
+            "fcm_fpcg_set_stall_window")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -268,9 +269,10 @@ def _bind_unet(L):
     L.fcm_fpcg_solve.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
     L.fcm_fpcg_solve_host.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ip,
                                       dp]
+    L.fcm_fpcg_set_stall_window.argtypes = [P, ctypes.c_int]
     for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
               "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
-              "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host"):
+              "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host", "fcm_fpcg_set_stall_window"):
         getattr(L, f).restype = ctypes.c_int
     _unet_bound = True
 
@@ -397,6 +399,13 @@ def _solver_fpcg_solve_host(self, net, gamma, b_host, tol, maxit=100000, out=Non
     return u, its.value, rel.value, st
 
 
+def _solver_set_stall_window(self, window):
+    """Iterations without halving of the judged residual after which fpcg_solve falls back."""
+    _bind_unet(load())
+    self._check(load().fcm_fpcg_set_stall_window(self.ctx, int(window)))
+
+
+Solver.set_stall_window = _solver_set_stall_window
 Solver.coarse_restrict = _solver_coarse_restrict
 Solver.coarse_prolong = _solver_coarse_prolong
 Solver.coarse_apply = _solver_coarse_apply
