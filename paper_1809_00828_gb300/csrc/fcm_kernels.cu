@@ -339,11 +339,13 @@ template <> struct Vec16<float> {
     {
         return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
     }
+    __device__ static float get(float4 a, int e) { return e == 0 ? a.x : e == 1 ? a.y : e == 2 ? a.z : a.w; }
 };
 template <> struct Vec16<double> {
     using type = double2;
     __device__ static double2 zero() { return make_double2(0.0, 0.0); }
     __device__ static double dot(double2 a, double2 b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
+    __device__ static double get(double2 a, int e) { return e == 0 ? a.x : a.y; }
 };
 
 // Bytes in front of the factor tile in the Schwarz kernel's dynamic shared memory: the
@@ -434,46 +436,52 @@ __device__ __forceinline__ void apply_rows(const double *__restrict__ r, double 
 
 // Rows [row0, row0 + rows) of z_k,B += F r_k,B for nr <= 8 right-hand sides (vectors nlat
 // apart) of a block with its own factor: warp-per-row as in apply_rows, two rows at a time,
-// each lane holding nr partial sums per row; one load of F feeds nr multiply-adds.
+// each lane holding nr partial sums per row; one load of F feeds nr multiply-adds.  A lane
+// visits the same 16-byte vectors of a row in the same order as apply_rows, so each
+// right-hand side gets exactly the single-vector result.
 template <int P, typename T>
 __device__ __forceinline__ void apply_multi_rows(const double *__restrict__ r, double *__restrict__ z, int64_t nlat,
                                                  int nr, const T *__restrict__ pool,
                                                  const PatchRec *__restrict__ patches, int first, int row0, int rows,
                                                  const Grid3 &g, int rule, unsigned char *smem)
 {
-    constexpr int MR = 8;
+    using VT = typename Vec16<T>::type;
+    constexpr int MR = 8, V = 16 / (int)sizeof(T);
     T(*rbT)[MR] = reinterpret_cast<T(*)[MR]>(smem);
     const PatchRec pr = patches[first];
     int lo[3], d[3];
     block_box(rule, P, g, pr.v, lo, d);
-    const int n = 3 * d[0] * d[1] * d[2];
+    const int n = 3 * d[0] * d[1] * d[2], ld = factor_ld<T>(n);
     auto gidx = [&](int t) -> int64_t {
         const int nl = t / 3;
         const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
         return 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + t % 3;
     };
-    for (int e = threadIdx.x; e < n * MR; e += blockDim.x) {
+    for (int e = threadIdx.x; e < ld * MR; e += blockDim.x) {
         const int t = e / MR, k = e % MR;
-        rbT[t][k] = k < nr ? (T)r[(int64_t)k * nlat + gidx(t)] : (T)0;
+        rbT[t][k] = (k < nr && t < n) ? (T)r[(int64_t)k * nlat + gidx(t)] : (T)0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int row1 = min(n, row0 + rows);
+    const int row1 = min(n, row0 + rows), nv = ld / V;
     const T *__restrict__ F = pool + pr.off;
-    const int ld = factor_ld<T>(n);
     for (int t = row0 + 2 * w; t < row1; t += 2 * nw) {
-        const T *f0 = F + (size_t)t * ld;
-        const T *f1 = F + (size_t)min(t + 1, row1 - 1) * ld;
+        const VT *f0 = reinterpret_cast<const VT *>(F + (size_t)t * ld);
+        const VT *f1 = reinterpret_cast<const VT *>(F + (size_t)min(t + 1, row1 - 1) * ld);
         T a[2][MR];
 #pragma unroll
         for (int k = 0; k < MR; ++k) a[0][k] = a[1][k] = (T)0;
-#pragma unroll 2
-        for (int j = lane; j < n; j += 32) {
-            const T g0 = __ldg(f0 + j), g1 = __ldg(f1 + j);
+        for (int c = lane; c < nv; c += 32) {
+            const VT g0 = __ldg(f0 + c), g1 = __ldg(f1 + c);
 #pragma unroll
-            for (int k = 0; k < MR; ++k) {
-                a[0][k] = fma(g0, rbT[j][k], a[0][k]);
-                a[1][k] = fma(g1, rbT[j][k], a[1][k]);
+            for (int e = 0; e < V; ++e) {
+                const int j = c * V + e;
+                const T v0 = Vec16<T>::get(g0, e), v1 = Vec16<T>::get(g1, e);
+#pragma unroll
+                for (int k = 0; k < MR; ++k) {
+                    a[0][k] = fma(v0, rbT[j][k], a[0][k]);
+                    a[1][k] = fma(v1, rbT[j][k], a[1][k]);
+                }
             }
         }
 #pragma unroll
@@ -533,7 +541,9 @@ __device__ __forceinline__ void apply_multi(const double *__restrict__ r, double
                 for (int k = 0; k < MR; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
             }
             const int64_t gi = gidx(t);
-            for (int k = 0; k < nr; ++k) z[(int64_t)k * nlat + gi] += (double)acc[k];
+#pragma unroll
+            for (int k = 0; k < MR; ++k)
+                if (k < nr) z[(int64_t)k * nlat + gi] += (double)acc[k];
         }
     }
 }
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
                          int rows32, int rows64, const int *__restrict__ done)
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W;
-    __shared__ __align__(16) unsigned char smem[NB * 8 * (P == 4 ? 4 : 8)];
+    __shared__ __align__(16) unsigned char smem[factor_ld<double>(NB) * 8 * (P == 4 ? 4 : 8)];
     if (done && *done) return;
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
