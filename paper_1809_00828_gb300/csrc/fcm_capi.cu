@@ -360,7 +360,7 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
         // cut cells: dense ne x ne; uncut cells: 3 components x (8 forward + 8 transposed) contractions of
         // Q^3 points x Q terms, plus ~21 multiply-adds of the stress per point
         const int64_t q = hp.p + 1;
-        out->kapply_fmas = hp.ncut * (int64_t)hp.ne * hp.ne + (hp.nactive - hp.ncut) * (48 * q * q * q * q + 21 * q * q * q);
+        out->kapply_fmas = hp.ncut * (int64_t)hp.ne * hp.ne + (hp.nactive - hp.ncut) * (36 * q * q * q * q + 21 * q * q * q);
     }
     out->sapply_fmas = C->sapply_fmas;
     out->max_block_cond = C->max_cond;

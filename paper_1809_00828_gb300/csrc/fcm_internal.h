@@ -53,6 +53,7 @@ struct HostProblem {
 struct SfTables {
     double B[5][5];     // B[q][i] = f_i(xi_q)
     double D[3][5][5];  // D[a][q][i] = f_i'(xi_q) * 2 / h_a
+    double G[3][5][5];  // G[a][q][k] = l_k'(xi_q) * 2 / h_a, l_k the Lagrange polynomials through the Gauss points
     double W[5];        // Gauss weights on [-1, 1]
     double detJ;        // h_0 h_1 h_2 / 8
     double lam, mu;     // Lame parameters

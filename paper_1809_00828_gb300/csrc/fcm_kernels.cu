@@ -81,14 +81,14 @@ __global__ void __launch_bounds__(threads_for(3 * (P + 1) * (P + 1) * (P + 1)))
     }
 }
 
-// y += K_ref x_e for uncut cells of one colour, without the matrix: the
-// displacement gradients at the (p+1)^3 Gauss points are obtained by
-// one-dimensional contractions along x, y, z (sum factorisation), the
-// weighted stress sigma = lam tr(eps) I + 2 mu eps is formed per point, and the
-// transposed contractions give the nodal forces.  Exact for the uncut
-// integrand (degree <= 2p per axis), so it equals K_ref x_e up to rounding
-// with (p+1)^3 * 24 * ... ~ 2.7x fewer FP64 multiply-adds than the dense
-// product at p = 3 and no matrix traffic.  Threads of a cell: one per point.
+// y += K_ref x_e for uncut cells of one colour, without the matrix.  Each displacement
+// component is interpolated to the (p+1)^3 Gauss points by one-dimensional contractions along
+// x, y, z (sum factorisation); its gradient there follows from the collocation derivative on
+// the Gauss points (exact: the field has degree <= p per axis).  The weighted stress
+// sigma = lam tr(eps) I + 2 mu eps is formed per point, and the transposed steps give the
+// nodal forces.  Exact for the uncut integrand (degree <= 2p per axis), so it equals
+// K_ref x_e up to rounding, with 36 (p+1)^4 FP64 multiply-adds per cell (the dense product
+// takes 9 (p+1)^6) and no matrix traffic.  Threads of a cell: one per point.
 template <int P>
 __global__ void __launch_bounds__(256)
     sf_apply_kernel(const double *__restrict__ x, double *__restrict__ y, const uint8_t *__restrict__ mask,
@@ -96,14 +96,13 @@ __global__ void __launch_bounds__(256)
 {
     constexpr int Q = P + 1, Q3 = Q * Q * Q, TPC = round32(Q3), CPC = 256 / TPC;
     if (done && *done) return;
-    __shared__ double sB[Q][Q], sD[3][Q][Q], sW[Q];
-    __shared__ double U[CPC][3][Q3];
-    __shared__ double S0[CPC][Q3], S1[CPC][Q3], S2[CPC][Q3];
-    __shared__ double R0[CPC][Q3], R1[CPC][Q3], R2[CPC][Q3];
+    __shared__ double sB[Q][Q], sG[3][Q][Q], sW[Q];
+    __shared__ double U[CPC][3][Q3];   // nodal values; then the point values per component
+    __shared__ double A[CPC][Q3], Bq[CPC][Q3];
     for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
         const int q = t / Q, i = t % Q;
         sB[q][i] = T.B[q][i];
-        for (int a = 0; a < 3; ++a) sD[a][q][i] = T.D[a][q][i];
+        for (int a = 0; a < 3; ++a) sG[a][q][i] = T.G[a][q][i];
     }
     if (threadIdx.x < Q) sW[threadIdx.x] = T.W[threadIdx.x];
     const int lc = threadIdx.x / TPC, t = threadIdx.x % TPC;
@@ -118,43 +117,44 @@ __global__ void __launch_bounds__(256)
         for (int c = 0; c < 3; ++c) U[lc][c][t] = x[3 * node + c];
     }
     __syncthreads();
-    double gr[3][3];
+    // interpolation to the points: (ix,iy,iz) -> (qx,iy,iz) -> (qx,qy,iz) -> (qx,qy,qz)
+    double uq[3];
     for (int c = 0; c < 3; ++c) {
-        if (on) {  // x: S0 = B u, S1 = D_x u at (qx, iy, iz)
-            double s0 = 0.0, s1 = 0.0;
+        if (on) {
+            double s0 = 0.0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const double u = U[lc][c][k + Q * (ty + Q * tz)];
-                s0 = fma(sB[tx][k], u, s0);
-                s1 = fma(sD[0][tx][k], u, s1);
-            }
-            S0[lc][t] = s0;
-            S1[lc][t] = s1;
+            for (int k = 0; k < Q; ++k) s0 = fma(sB[tx][k], U[lc][c][k + Q * (ty + Q * tz)], s0);
+            A[lc][t] = s0;
         }
         __syncthreads();
-        if (on) {  // y: R0 = B S0, R1 = D_y S0, R2 = B S1 at (qx, qy, iz)
-            double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+        if (on) {
+            double s1 = 0.0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const int id = tx + Q * (k + Q * tz);
-                const double a = S0[lc][id], b = S1[lc][id];
-                r0 = fma(sB[ty][k], a, r0);
-                r1 = fma(sD[1][ty][k], a, r1);
-                r2 = fma(sB[ty][k], b, r2);
-            }
-            R0[lc][t] = r0;
-            R1[lc][t] = r1;
-            R2[lc][t] = r2;
+            for (int k = 0; k < Q; ++k) s1 = fma(sB[ty][k], A[lc][tx + Q * (k + Q * tz)], s1);
+            Bq[lc][t] = s1;
         }
         __syncthreads();
-        if (on) {  // z: gradient of u_c at the point (qx, qy, qz)
+        if (on) {
+            double s2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) s2 = fma(sB[tz][k], Bq[lc][tx + Q * (ty + Q * k)], s2);
+            uq[c] = s2;
+        }
+    }
+    __syncthreads();  // every point has read the nodal values of its cell
+    if (on)
+        for (int c = 0; c < 3; ++c) U[lc][c][t] = uq[c];
+    __syncthreads();
+    // gradients at the point by the collocation derivative along each axis
+    double gr[3][3];
+    if (on) {
+        for (int c = 0; c < 3; ++c) {
             double gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                const int id = tx + Q * (ty + Q * k);
-                gx = fma(sB[tz][k], R2[lc][id], gx);
-                gy = fma(sB[tz][k], R1[lc][id], gy);
-                gz = fma(sD[2][tz][k], R0[lc][id], gz);
+                gx = fma(sG[0][tx][k], U[lc][c][k + Q * (ty + Q * tz)], gx);
+                gy = fma(sG[1][ty][k], U[lc][c][tx + Q * (k + Q * tz)], gy);
+                gz = fma(sG[2][tz][k], U[lc][c][tx + Q * (ty + Q * k)], gz);
             }
             gr[c][0] = gx;
             gr[c][1] = gy;
@@ -171,48 +171,39 @@ __global__ void __launch_bounds__(256)
     }
     double out[3];
     for (int c = 0; c < 3; ++c) {
+        __syncthreads();  // the previous readers of U and A are done
+        if (on)
+            for (int j = 0; j < 3; ++j) U[lc][j][t] = F[c][j];
         __syncthreads();
-        if (on) {
-            R0[lc][t] = F[c][0];
-            R1[lc][t] = F[c][1];
-            R2[lc][t] = F[c][2];
+        if (on) {  // transposed collocation derivative: point values of component c's force
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                v = fma(sG[0][k][tx], U[lc][0][k + Q * (ty + Q * tz)], v);
+                v = fma(sG[1][k][ty], U[lc][1][tx + Q * (k + Q * tz)], v);
+                v = fma(sG[2][k][tz], U[lc][2][tx + Q * (ty + Q * k)], v);
+            }
+            A[lc][t] = v;
         }
         __syncthreads();
         if (on) {  // z^T: (qx, qy, iz)
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            double s2 = 0.0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const int id = tx + Q * (ty + Q * k);
-                s0 = fma(sB[k][tz], R0[lc][id], s0);
-                s1 = fma(sB[k][tz], R1[lc][id], s1);
-                s2 = fma(sD[2][k][tz], R2[lc][id], s2);
-            }
-            S0[lc][t] = s0;
-            S1[lc][t] = s1;
-            S2[lc][t] = s2;
+            for (int k = 0; k < Q; ++k) s2 = fma(sB[k][tz], A[lc][tx + Q * (ty + Q * k)], s2);
+            Bq[lc][t] = s2;
         }
         __syncthreads();
         if (on) {  // y^T: (qx, iy, iz)
-            double r0 = 0.0, r1 = 0.0;
+            double s1 = 0.0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const int id = tx + Q * (k + Q * tz);
-                r0 = fma(sB[k][ty], S0[lc][id], r0);
-                r1 = fma(sD[1][k][ty], S1[lc][id], r1);
-                r1 = fma(sB[k][ty], S2[lc][id], r1);
-            }
-            R0[lc][t] = r0;
-            R1[lc][t] = r1;
+            for (int k = 0; k < Q; ++k) s1 = fma(sB[k][ty], Bq[lc][tx + Q * (k + Q * tz)], s1);
+            A[lc][t] = s1;
         }
         __syncthreads();
         if (on) {  // x^T: nodal force (ix, iy, iz)
             double o = 0.0;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const int id = k + Q * (ty + Q * tz);
-                o = fma(sD[0][k][tx], R0[lc][id], o);
-                o = fma(sB[k][tx], R1[lc][id], o);
-            }
+            for (int k = 0; k < Q; ++k) o = fma(sB[k][tx], A[lc][k + Q * (ty + Q * tz)], o);
             out[c] = o;
         }
     }

@@ -503,6 +503,24 @@ void make_sf_tables(const HostProblem &P, SfTables &T)
             for (int a = 0; a < 3; ++a) T.D[a][k][i] = df[i] * 2.0 / P.h[a];
         }
     }
+    // collocation derivative on the Gauss points (barycentric form): for a polynomial of degree
+    // <= p per axis, its values at the p+1 points give its derivative there exactly
+    double lam_b[kMaxQ];
+    for (int k = 0; k < q; ++k) {
+        lam_b[k] = 1.0;
+        for (int m = 0; m < q; ++m)
+            if (m != k) lam_b[k] /= (x[k] - x[m]);
+    }
+    for (int i = 0; i < q; ++i) {
+        double diag = 0.0;
+        for (int k = 0; k < q; ++k) {
+            if (k == i) continue;
+            const double v = (lam_b[k] / lam_b[i]) / (x[i] - x[k]);
+            diag -= v;
+            for (int a = 0; a < 3; ++a) T.G[a][i][k] = v * 2.0 / P.h[a];
+        }
+        for (int a = 0; a < 3; ++a) T.G[a][i][i] = diag * 2.0 / P.h[a];
+    }
     T.detJ = P.h[0] * P.h[1] * P.h[2] / 8.0;
     T.lam = P.E * P.nu / ((1.0 + P.nu) * (1.0 - 2.0 * P.nu));
     T.mu = P.E / (2.0 * (1.0 + P.nu));
