@@ -290,6 +290,16 @@ def run_fcm(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         its, rel = solve(u)
+    if args.profile_one_step:
+        # one step between cudaProfilerStart / Stop, for `ncu --profile-from-start off`; no JSON line
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        its, rel = solve(u)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"profiled one step: {its} iterations, relres {rel:.3e}")
+        s.close()
+        return 0
     info = s.get_info()
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -506,6 +516,8 @@ def main():
                     help="iteration count that scales the reference arm's per-iteration time (default 877, the plain "
                          "FP64 Schwarz-PCG count of porous40_32_p3, which the oracle's algorithm shares)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-one-step", action="store_true",
+                    help="after the warm-up, run one step between cudaProfilerStart/Stop and exit (for ncu)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
