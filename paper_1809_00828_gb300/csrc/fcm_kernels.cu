@@ -354,7 +354,7 @@ __host__ __device__ constexpr int rows_tile_offset()
 // copies' mbarrier.  Each warp takes 4 rows at a time, its lanes split a row into 16-byte
 // vectors (r_B's vectors stay in registers across rows), and warp shuffles finish the sums.
 // Every CTA holds one tile in flight, so a colour's launch keeps the DRAM queue full without
-// per-thread loads.  A wait that runs out sets *err and the CTA returns without writing.
+// per-thread loads.  (FP64 tiles: 2 rows per warp and pass, half as many rows per tile.)  A wait that runs out sets *err and the CTA returns without writing.
 template <int P, typename T>
 __device__ __forceinline__ void apply_rows(const double *__restrict__ r, double *__restrict__ z,
                                            const T *__restrict__ pool, const PatchRec *__restrict__ patches,
@@ -402,10 +402,11 @@ __device__ __forceinline__ void apply_rows(const double *__restrict__ r, double 
     VT xr[KV];
 #pragma unroll
     for (int k = 0; k < KV; ++k) xr[k] = lane + 32 * k < nv ? rbv[lane + 32 * k] : Vec16<T>::zero();
-    for (int t = row0 + 4 * w; t < row1; t += 4 * nw) {
-        T a[4];
+    constexpr int RPW = sizeof(T) == 8 ? 2 : 4;  // rows per warp and pass (FP64 tiles are half as tall)
+    for (int t = row0 + RPW * w; t < row1; t += RPW * nw) {
+        T a[RPW];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RPW; ++q) {
             // rows past row1 repeat the last row (in bounds) and are not written
             const VT *fr = reinterpret_cast<const VT *>(tile + (size_t)(min(t + q, row1 - 1) - row0) * ld);
             T acc = (T)0;
@@ -417,9 +418,12 @@ __device__ __forceinline__ void apply_rows(const double *__restrict__ r, double 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
-        if (lane < 4 && t + lane < row1) {
-            const T v = lane == 0 ? a[0] : lane == 1 ? a[1] : lane == 2 ? a[2] : a[3];
+            for (int q = 0; q < RPW; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+        if (lane < RPW && t + lane < row1) {
+            T v = a[0];
+#pragma unroll
+            for (int q = 1; q < RPW; ++q)
+                if (lane == q) v = a[q];
             z[gidx(t + lane)] += (double)v;
         }
     }
@@ -580,7 +584,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
     switch (kind) {
-    case kF32Shared: apply_batch<P, 8, float, 4>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
+    case kF32Shared: apply_batch<P, 8, float, 16>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
     // single-factor items carry a row tile index in place of the block count
     case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows32, rows32, g, rule, smem, err); break;
     case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, rule, smem); break;
@@ -703,12 +707,12 @@ cudaError_t prepare_p(int bytes)
 
 void schwarz_default_rows(int p, int rule, int *rows32, int *rows64)
 {
-    // 4 rows per warp of the launch, as long as a tile stays within kTileBudget bytes
+    // 4 (FP32) or 2 (FP64) rows per warp of the launch, as long as a tile stays within kTileBudget bytes
     const int nb = 3 * box_width(p) * box_width(p) * box_width(p);
-    const int full = 4 * (schwarz_threads(p, rule) / 32);
+    const int nw = schwarz_threads(p, rule) / 32;
     const int cap32 = kTileBudget / (factor_ld<float>(nb) * 4), cap64 = kTileBudget / (factor_ld<double>(nb) * 8);
-    *rows32 = std::max(4, std::min(full, cap32) / 4 * 4);
-    *rows64 = std::max(4, std::min(full, cap64) / 4 * 4);
+    *rows32 = std::max(4, std::min(4 * nw, cap32) / 4 * 4);
+    *rows64 = std::max(2, std::min(2 * nw, cap64) / 2 * 2);
 }
 
 int schwarz_smem_bytes(int p, int rows32, int rows64)

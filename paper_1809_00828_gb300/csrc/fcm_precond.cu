@@ -553,8 +553,8 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
                 C->n_blocks += 1;
                 C->sapply_fmas += (int64_t)fac[f].n * fac[f].n;
             }
-    // One launch per colour.  Work items, heaviest first so that the tail of the launch is short:
-    // FP64 shared-factor batches, FP64 single blocks, FP32 single blocks (DRAM-bound), FP32 batches.
+    // One launch per colour.  Units by kind, heaviest first: FP64 shared-factor batches, FP64 single
+    // blocks, FP32 single blocks (DRAM-bound), FP32 batches; their work items are interleaved below.
     // Kinds as in fcm_kernels.cu: 0 FP32 shared, 1 FP32 single, 2 FP64 shared, 3 FP64 single.
     // `units` lists, colour by colour, a batch (first record, count) or a single block (record,
     // rows); the work items follow from them once the row-tile sizes are chosen.
@@ -592,14 +592,35 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         int u = 0;
         for (int c = 0; c < 8; ++c) {
             SchwarzSeg sg = {c, -1, 0, (int)items.size(), 0};
+            // three streams of work items: FP64 (FP64 pipe), FP32 single-factor tiles (DRAM), FP32
+            // batches (FP32 pipe, factor in L2); each heaviest first
+            std::vector<int2> lists[3];
             for (; u < unit_colour_end[c]; ++u) {
                 const Unit &un = units[u];
+                const int li = un.kind >= 2 ? 0 : un.kind == 1 ? 1 : 2;
                 if (un.kind == 0 || un.kind == 2) {
-                    items.push_back(make_int2(un.rec, un.size | (un.kind << 8)));
+                    lists[li].push_back(make_int2(un.rec, un.size | (un.kind << 8)));
                 } else {
                     const int rws = un.kind == 1 ? rows32 : rows64;
-                    for (int t = 0; t * rws < un.size; ++t) items.push_back(make_int2(un.rec, t | (un.kind << 8)));
+                    for (int t = 0; t * rws < un.size; ++t) lists[li].push_back(make_int2(un.rec, t | (un.kind << 8)));
                 }
+            }
+            // interleaved by relative position, so that every part of the launch mixes the three
+            // kinds and the SMs run compute-bound and DRAM-bound items side by side
+            size_t pos[3] = {0, 0, 0};
+            for (;;) {
+                int best = -1;
+                double key = 2.0;
+                for (int l = 0; l < 3; ++l)
+                    if (pos[l] < lists[l].size()) {
+                        const double k = (pos[l] + 0.5) / (double)lists[l].size();
+                        if (k < key) {
+                            key = k;
+                            best = l;
+                        }
+                    }
+                if (best < 0) break;
+                items.push_back(lists[best][pos[best]++]);
             }
             sg.count = (int)items.size() - sg.first;
             if (sg.count > 0) pl.seg[pl.nseg++] = sg;
@@ -615,7 +636,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     std::vector<std::pair<int, int>> cand = {{rows32, rows64}};
     if (!o.fixed_tiles)
         for (int dv : {2, 4}) {
-            const std::pair<int, int> c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(4, rows64 / dv / 4 * 4)};
+            const std::pair<int, int> c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(2, rows64 / dv / 2 * 2)};
             if (c2 != cand.back()) cand.push_back(c2);
         }
     std::vector<int2> batches;
