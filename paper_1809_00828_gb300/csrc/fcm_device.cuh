@@ -89,6 +89,8 @@ void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, con
 constexpr int kTileBudget = 72 * 1024;
 void schwarz_default_rows(int p, int rule, int *rows32, int *rows64);
 int schwarz_smem_bytes(int p, int rows32, int rows64);
+// blocks per FP32 shared-factor batch (the register tiles of the batch kernel)
+int schwarz_f32_batch_cap(int p);
 cudaError_t schwarz_prepare(int p, int smem_bytes);
 // nr <= 8 right-hand sides stored nlat apart (p = 4 needs FP32 factors)
 void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,

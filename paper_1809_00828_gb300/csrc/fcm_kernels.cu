@@ -347,6 +347,87 @@ __host__ __device__ constexpr int rows_tile_offset()
     return 16 + (factor_ld<double>(3 * box_width(P) * box_width(P) * box_width(P)) * 8 + 15) / 16 * 16;
 }
 
+// Blocks per FP32 shared-factor batch: 32 (8 at p = 4, whose boxes are 3.7x larger).
+template <int P>
+__host__ __device__ constexpr int f32_batch_cap()
+{
+    return P == 4 ? 8 : 32;
+}
+
+// z += F r_B for the `count` <= f32_batch_cap<P>() blocks of an FP32 shared-factor batch, as a
+// small GEMM Z = F [r_B1 .. r_Bcount] with 4 x 4 register tiles: a thread owns 4 consecutive
+// rows for a group of 4 blocks, so one 16-byte load of F (4 rows of column j, by symmetry a
+// contiguous piece of row j) and one 16-byte shared load of the residuals feed 16
+// multiply-adds.  A factor is read once per 32 blocks.  Lattice indices are tabulated as in
+// apply_batch.
+template <int P>
+__device__ __forceinline__ void apply_batch_tiled(const double *__restrict__ r, double *__restrict__ z,
+                                                  const float *__restrict__ pool, const PatchRec *__restrict__ patches,
+                                                  int first, int count, const Grid3 &g, int rule, unsigned char *smem)
+{
+    constexpr int W = box_width(P), NB = 3 * W * W * W, G = f32_batch_cap<P>();
+    float(*rbT)[G] = reinterpret_cast<float(*)[G]>(smem);
+    int64_t *base = reinterpret_cast<int64_t *>(smem + sizeof(float) * NB * G);  // G entries, -1: no block
+    int *rel = reinterpret_cast<int *>(base + G);                                // NB entries
+    const PatchRec p0 = patches[first];
+    int lo0[3], d[3];
+    block_box(rule, P, g, p0.v, lo0, d);
+    const int n = 3 * d[0] * d[1] * d[2], ld = factor_ld<float>(n);
+    for (int k = threadIdx.x; k < G; k += blockDim.x) {
+        int64_t b = -1;
+        if (k < count) {
+            int l[3], dd[3];
+            block_box(rule, P, g, patches[first + k].v, l, dd);
+            b = 3 * (l[0] + (int64_t)g.M[0] * (l[1] + (int64_t)g.M[1] * l[2]));
+        }
+        base[k] = b;
+    }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int nl = t / 3;
+        const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
+        rel[t] = 3 * (ix + g.M[0] * (iy + g.M[1] * iz)) + t % 3;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * G; e += blockDim.x) {
+        const int t = e / G, k = e % G;
+        const int64_t b = base[k];
+        rbT[t][k] = b >= 0 ? (float)r[b + rel[t]] : 0.f;
+    }
+    __syncthreads();
+    const float *__restrict__ F = pool + p0.off;
+    const int ngr = (n + 3) / 4, npg = (count + 3) / 4;
+    for (int wi = threadIdx.x; wi < ngr * npg; wi += blockDim.x) {
+        const int t0 = 4 * (wi % ngr), k0 = 4 * (wi / ngr);
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+        // rows t0..t0+3 < ld (the padding columns of F are zero)
+        const float4 *Fc = reinterpret_cast<const float4 *>(F + t0);
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const float4 f = __ldg(Fc + (size_t)j * (ld / 4));
+            const float4 ra = *reinterpret_cast<const float4 *>(&rbT[j][k0]);
+            const float fr[4] = {f.x, f.y, f.z, f.w};
+            const float rr[4] = {ra.x, ra.y, ra.z, ra.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(fr[i], rr[k], acc[i][k]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int t = t0 + i;
+            if (t >= n) break;
+            const int rt = rel[t];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (base[k0 + k] >= 0) z[base[k0 + k] + rt] += (double)acc[i][k];
+        }
+    }
+}
+
 // Rows [row0, row0 + rows) of z_B += F r_B for a block with its own factor (cut blocks stream
 // their factor from DRAM).  The rows of the tile are contiguous in the factor pool (the
 // factor is symmetric, rows padded to 16 bytes), so one thread starts them on their way into
@@ -572,7 +653,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
 // The blocks of one colour are DOF-disjoint, so the scatter needs no atomics.  Dynamic shared
 // memory: schwarz_smem_bytes(P, rows32, rows64).
 template <int P>
-__global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * box_width(P)))
+__global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * box_width(P)), P == 3 ? 3 : 1)
     schwarz_colour_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ f64,
                           const float *__restrict__ f32, const PatchRec *__restrict__ patches,
                           const int2 *__restrict__ batches, Grid3 g, int rule, int rows32, int rows64, int *err,
@@ -584,7 +665,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
     switch (kind) {
-    case kF32Shared: apply_batch<P, 8, float, 16>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
+    case kF32Shared: apply_batch_tiled<P>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
     // single-factor items carry a row tile index in place of the block count
     case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows32, rows32, g, rule, smem, err); break;
     case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, rule, smem); break;
@@ -688,7 +769,7 @@ template <int P>
 int smem_bytes_p(int rows32, int rows64)
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
-    const int batch = NB * ROW + 64 + 4 * NB;
+    const int batch = std::max(NB * ROW + 64 + 4 * NB, NB * f32_batch_cap<P>() * 4 + 8 * f32_batch_cap<P>() + 4 * NB);
     const int t32 = rows_tile_offset<P>() + rows32 * factor_ld<float>(NB) * 4;
     const int t64 = rows_tile_offset<P>() + rows64 * factor_ld<double>(NB) * 8;
     return std::max(batch, std::max(t32, t64));
@@ -724,6 +805,8 @@ int schwarz_smem_bytes(int p, int rows32, int rows64)
     default: return smem_bytes_p<4>(rows32, rows64);
     }
 }
+
+int schwarz_f32_batch_cap(int p) { return p == 4 ? f32_batch_cap<4>() : f32_batch_cap<3>(); }
 
 cudaError_t schwarz_prepare(int p, int smem_bytes)
 {

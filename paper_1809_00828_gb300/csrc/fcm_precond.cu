@@ -569,7 +569,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         for (const auto &o : order) {
             const int pr = o[0], shared = o[1];
             const int kind = pr == 1 ? (shared ? 0 : 1) : (shared ? 2 : 3);
-            const int cap = shared ? ((p == 4 && pr == 0) ? 4 : 8) : 1;
+            const int cap = !shared ? 1 : pr == 1 ? schwarz_f32_batch_cap(p) : (p == 4 ? 4 : 8);
             for (size_t f = 0; f < fac.size(); ++f) {
                 const std::vector<int> &vs = by_colour_factor[c][f];
                 if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
