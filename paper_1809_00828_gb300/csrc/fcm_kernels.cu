@@ -51,6 +51,24 @@ __device__ __forceinline__ void block_box(int rule, int P, const Grid3 &g, int i
     }
 }
 
+// 16-byte vectors of float (4) or double (2): load type, dot-accumulate, element access.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float dot(float4 a, float4 b, float c)
+    {
+        return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
+    }
+    __device__ static float get(float4 a, int e) { return e == 0 ? a.x : e == 1 ? a.y : e == 2 ? a.z : a.w; }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double dot(double2 a, double2 b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
+    __device__ static double get(double2 a, int e) { return e == 0 ? a.x : a.y; }
+};
+
 // y += K_e x_e over the active cells of one colour; rows that are not free stay untouched.
 template <int P>
 __global__ void __launch_bounds__(threads_for(3 * (P + 1) * (P + 1) * (P + 1)))
@@ -267,8 +285,16 @@ __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double
 #pragma unroll UNROLL
         for (int j = 0; j < n; ++j) {
             const T f = __ldg(F + (size_t)j * ld + t);
+            // the G residuals of row j as 16-byte shared loads (the same address for the warp)
+            using VT = typename Vec16<T>::type;
+            constexpr int V = 16 / (int)sizeof(T);
+            const VT *rv = reinterpret_cast<const VT *>(&rbT[j][0]);
 #pragma unroll
-            for (int k = 0; k < G; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
+            for (int q = 0; q < G / V; ++q) {
+                const VT x = rv[q];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[q * V + e] = fma(f, Vec16<T>::get(x, e), acc[q * V + e]);
+            }
         }
         const int rt = rel[t];
 #pragma unroll
@@ -322,23 +348,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
-template <typename T> struct Vec16;
-template <> struct Vec16<float> {
-    using type = float4;
-    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-    __device__ static float dot(float4 a, float4 b, float c)
-    {
-        return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
-    }
-    __device__ static float get(float4 a, int e) { return e == 0 ? a.x : e == 1 ? a.y : e == 2 ? a.z : a.w; }
-};
-template <> struct Vec16<double> {
-    using type = double2;
-    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
-    __device__ static double dot(double2 a, double2 b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
-    __device__ static double get(double2 a, int e) { return e == 0 ? a.x : a.y; }
-};
-
 // Bytes in front of the factor tile in the Schwarz kernel's dynamic shared memory: the
 // mbarrier (16) and the gathered residual r_B in T, padded to the factor's row length.
 template <int P>
@@ -347,85 +356,13 @@ __host__ __device__ constexpr int rows_tile_offset()
     return 16 + (factor_ld<double>(3 * box_width(P) * box_width(P) * box_width(P)) * 8 + 15) / 16 * 16;
 }
 
-// Blocks per FP32 shared-factor batch: 32 (8 at p = 4, whose boxes are 3.7x larger).
+// Blocks per FP32 shared-factor batch: each load of a factor entry (from L2: shared factors are
+// few) feeds that many multiply-adds.  (16 measured slower than 8 at p = 3: more registers, no
+// less time.)
 template <int P>
 __host__ __device__ constexpr int f32_batch_cap()
 {
-    return P == 4 ? 8 : 32;
-}
-
-// z += F r_B for the `count` <= f32_batch_cap<P>() blocks of an FP32 shared-factor batch, as a
-// small GEMM Z = F [r_B1 .. r_Bcount] with 4 x 4 register tiles: a thread owns 4 consecutive
-// rows for a group of 4 blocks, so one 16-byte load of F (4 rows of column j, by symmetry a
-// contiguous piece of row j) and one 16-byte shared load of the residuals feed 16
-// multiply-adds.  A factor is read once per 32 blocks.  Lattice indices are tabulated as in
-// apply_batch.
-template <int P>
-__device__ __forceinline__ void apply_batch_tiled(const double *__restrict__ r, double *__restrict__ z,
-                                                  const float *__restrict__ pool, const PatchRec *__restrict__ patches,
-                                                  int first, int count, const Grid3 &g, int rule, unsigned char *smem)
-{
-    constexpr int W = box_width(P), NB = 3 * W * W * W, G = f32_batch_cap<P>();
-    float(*rbT)[G] = reinterpret_cast<float(*)[G]>(smem);
-    int64_t *base = reinterpret_cast<int64_t *>(smem + sizeof(float) * NB * G);  // G entries, -1: no block
-    int *rel = reinterpret_cast<int *>(base + G);                                // NB entries
-    const PatchRec p0 = patches[first];
-    int lo0[3], d[3];
-    block_box(rule, P, g, p0.v, lo0, d);
-    const int n = 3 * d[0] * d[1] * d[2], ld = factor_ld<float>(n);
-    for (int k = threadIdx.x; k < G; k += blockDim.x) {
-        int64_t b = -1;
-        if (k < count) {
-            int l[3], dd[3];
-            block_box(rule, P, g, patches[first + k].v, l, dd);
-            b = 3 * (l[0] + (int64_t)g.M[0] * (l[1] + (int64_t)g.M[1] * l[2]));
-        }
-        base[k] = b;
-    }
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int nl = t / 3;
-        const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
-        rel[t] = 3 * (ix + g.M[0] * (iy + g.M[1] * iz)) + t % 3;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * G; e += blockDim.x) {
-        const int t = e / G, k = e % G;
-        const int64_t b = base[k];
-        rbT[t][k] = b >= 0 ? (float)r[b + rel[t]] : 0.f;
-    }
-    __syncthreads();
-    const float *__restrict__ F = pool + p0.off;
-    const int ngr = (n + 3) / 4, npg = (count + 3) / 4;
-    for (int wi = threadIdx.x; wi < ngr * npg; wi += blockDim.x) {
-        const int t0 = 4 * (wi % ngr), k0 = 4 * (wi / ngr);
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-        // rows t0..t0+3 < ld (the padding columns of F are zero)
-        const float4 *Fc = reinterpret_cast<const float4 *>(F + t0);
-#pragma unroll 4
-        for (int j = 0; j < n; ++j) {
-            const float4 f = __ldg(Fc + (size_t)j * (ld / 4));
-            const float4 ra = *reinterpret_cast<const float4 *>(&rbT[j][k0]);
-            const float fr[4] = {f.x, f.y, f.z, f.w};
-            const float rr[4] = {ra.x, ra.y, ra.z, ra.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(fr[i], rr[k], acc[i][k]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int t = t0 + i;
-            if (t >= n) break;
-            const int rt = rel[t];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (base[k0 + k] >= 0) z[base[k0 + k] + rt] += (double)acc[i][k];
-        }
-    }
+    return 8;
 }
 
 // Rows [row0, row0 + rows) of z_B += F r_B for a block with its own factor (cut blocks stream
@@ -665,7 +602,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
     switch (kind) {
-    case kF32Shared: apply_batch_tiled<P>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
+    case kF32Shared: apply_batch<P, f32_batch_cap<P>(), float, 16>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
     // single-factor items carry a row tile index in place of the block count
     case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows32, rows32, g, rule, smem, err); break;
     case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, rule, smem); break;
@@ -770,6 +707,7 @@ int smem_bytes_p(int rows32, int rows64)
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
     const int batch = std::max(NB * ROW + 64 + 4 * NB, NB * f32_batch_cap<P>() * 4 + 8 * f32_batch_cap<P>() + 4 * NB);
+    static_assert(f32_batch_cap<P>() <= 16, "the batch's block bases take 8 bytes each after rbT");
     const int t32 = rows_tile_offset<P>() + rows32 * factor_ld<float>(NB) * 4;
     const int t64 = rows_tile_offset<P>() + rows64 * factor_ld<double>(NB) * 8;
     return std::max(batch, std::max(t32, t64));
