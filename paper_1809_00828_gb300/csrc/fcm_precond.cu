@@ -631,6 +631,12 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     };
     int rows32 = 0, rows64 = 0;
     schwarz_default_rows(p, rule, &rows32, &rows64);
+    // small blocks (p <= 2) fit one tile whole: then the default is one item per block, and the
+    // autotuner's candidates split it in two and four
+    if (maxn > 0 && (int64_t)maxn * factor_ld<float>(maxn) * 4 <= kTileBudget)
+        rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
+    if (maxn > 0 && (int64_t)maxn * factor_ld<double>(maxn) * 8 <= kTileBudget)
+        rows64 = std::max(rows64, (maxn + 1) / 2 * 2);
     // candidate row-tile sizes: the default (4 rows per warp, tile within kTileBudget), half and a
     // quarter of it (more, shorter work items)
     std::vector<std::pair<int, int>> cand = {{rows32, rows64}};
