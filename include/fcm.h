@@ -110,7 +110,8 @@ typedef struct {
     double coarse_seconds;    /* assembly time of the coarse operator K_H (0 until built) */
     int64_t n_jacobi;         /* free DOFs in no block (diagonal part of S), last build   */
     int rows32, rows64;       /* rows per work item of a cut block's FP32 / FP64 factor  */
-    double tune_seconds[4];   /* S-apply time of each tried row-tile size (0: not tried) */
+    int tiles_persistent;     /* 1: one persistent launch per colour with two tile stages */
+    double tune_seconds[8];   /* S-apply time of each tried launch shape (0: not tried)  */
     int device_error;         /* 1 if a Schwarz kernel gave up waiting for its factor copy
                                  since the last fcm_precond_build (its output is then wrong) */
 } fcm_info_t;
@@ -138,9 +139,12 @@ enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
  *        (Sec. 5.2's end points; eta_T is clamped to 1 against rounding).
  *   eta_bar: threshold of FCM_BLOCKS_ELEMENT (ignored by FCM_BLOCKS_VERTEX).
  *   fixed_tiles: 0 (default) lets the build time the Schwarz apply for up to
- *        three row-tile sizes of the cut blocks (the rows of a factor handled
- *        by one CTA) and keep the fastest; 1 keeps the default size.  The
- *        result of S r does not depend on the tile size.
+ *        six launch shapes (three row-tile sizes of the cut blocks, the rows of
+ *        a factor handled by one work item, each with one CTA per work item or
+ *        a persistent launch per colour that prefetches the next tile) and keep
+ *        the fastest; 1 keeps the default tile with one CTA per work item; 2 the
+ *        default tile with the persistent launch.  S r does not depend on the
+ *        choice.
  * A zero-initialised struct with eps, precision and cond_fp64 set selects
  * vertex patches and the autotuned tiles. */
 typedef struct {

@@ -368,7 +368,8 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->n_jacobi = C->n_jacobi;
     out->rows32 = C->plan.rows;
     out->rows64 = C->plan.rows64;
-    for (int k = 0; k < 4; ++k) out->tune_seconds[k] = C->tune_seconds[k];
+    out->tiles_persistent = C->plan.persistent;
+    for (int k = 0; k < 8; ++k) out->tune_seconds[k] = C->tune_seconds[k];
     out->device_error = 0;
     if (C->d_err) {
         int e = 0;
@@ -412,7 +413,7 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     if (opts) o = *opts;
     if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED) || !(o.cond_fp64 > 0.0) ||
         (o.block_rule != FCM_BLOCKS_VERTEX && o.block_rule != FCM_BLOCKS_ELEMENT) ||
-        (o.block_rule == FCM_BLOCKS_ELEMENT && !(o.eta_bar >= 0.0))) {
+        (o.block_rule == FCM_BLOCKS_ELEMENT && !(o.eta_bar >= 0.0)) || o.fixed_tiles < 0 || o.fixed_tiles > 2) {
         C->err = "fcm_precond_build: invalid options";
         return FCM_EINVAL;
     }

@@ -73,6 +73,9 @@ struct SchwarzPlan {
     int rows64;               // the same for FP64 factors
     int smem;                 // dynamic shared memory of a Schwarz CTA (schwarz_smem_bytes)
     int *err;                 // device flag, set to 1 by a bulk-copy wait that ran out
+    int persistent;           // 1: one persistent launch per colour with two tile stages
+    int tile_bytes;           // bytes of one tile stage (persistent launches)
+    int grid_cap;             // CTAs of a persistent launch (resident CTAs of the GPU)
     const double *jac;        // 1 / K_ll for the free DOFs in no block, 0 elsewhere (lattice); null if none
 };
 
@@ -89,8 +92,12 @@ void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, con
 constexpr int kTileBudget = 72 * 1024;
 void schwarz_default_rows(int p, int rule, int *rows32, int *rows64);
 int schwarz_smem_bytes(int p, int rows32, int rows64);
-// blocks per FP32 shared-factor batch (the register tiles of the batch kernel)
+// blocks per FP32 shared-factor batch
 int schwarz_f32_batch_cap(int p);
+// persistent launches: dynamic shared memory (and the bytes of one tile stage) for given row counts,
+// and the resident CTAs of the GPU at that size (sets the kernel's shared-memory attribute)
+int schwarz_persistent_smem_bytes(int p, int rows32, int rows64, int *tile_bytes);
+cudaError_t schwarz_persistent_grid(int p, int rule, int smem, int *grid);
 cudaError_t schwarz_prepare(int p, int smem_bytes);
 // nr <= 8 right-hand sides stored nlat apart (p = 4 needs FP32 factors)
 void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,
@@ -178,7 +185,7 @@ struct fcm_ctx {
     double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
     int *d_err = nullptr;            // set by a Schwarz CTA whose bulk-copy wait ran out
     int fcg_window = 100;            // stall window of the flexible CG (fcm_fpcg_set_stall_window)
-    double tune_seconds[4] = {0, 0, 0, 0};  // S-apply times of the row-tile sizes tried
+    double tune_seconds[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // S-apply times of the launch shapes tried
     int64_t n_jacobi = 0;
     fcm::SchwarzPlan plan = {};
     int64_t n_factors = 0, factor_bytes = 0, n_fp32_factors = 0;

@@ -365,62 +365,71 @@ __host__ __device__ constexpr int f32_batch_cap()
     return 8;
 }
 
-// Rows [row0, row0 + rows) of z_B += F r_B for a block with its own factor (cut blocks stream
-// their factor from DRAM).  The rows of the tile are contiguous in the factor pool (the
+// Row tiles of a block with its own factor (cut blocks stream their factor from DRAM): rows
+// [row0, row0 + rows) of z_B += F r_B.  The rows of a tile are contiguous in the factor pool (the
 // factor is symmetric, rows padded to 16 bytes), so one thread starts them on their way into
-// shared memory as bulk copies before the CTA gathers r_B; the CTA then waits on the
-// copies' mbarrier.  Each warp takes 4 rows at a time, its lanes split a row into 16-byte
-// vectors (r_B's vectors stay in registers across rows), and warp shuffles finish the sums.
-// Every CTA holds one tile in flight, so a colour's launch keeps the DRAM queue full without
-// per-thread loads.  (FP64 tiles: 2 rows per warp and pass, half as many rows per tile.)  A wait that runs out sets *err and the CTA returns without writing.
+// shared memory as bulk copies completed on an mbarrier (tile_issue); the CTA gathers r_B
+// meanwhile (tile_gather), waits, and applies the rows (tile_apply): each warp takes 4 (FP32)
+// or 2 (FP64) rows at a time, its lanes split a row into 16-byte vectors (r_B's vectors stay in
+// registers across rows), and warp shuffles finish the sums.
+
+struct TileGeom {
+    int lo[3], d[3], n, ld, row1;
+};
+
 template <int P, typename T>
-__device__ __forceinline__ void apply_rows(const double *__restrict__ r, double *__restrict__ z,
-                                           const T *__restrict__ pool, const PatchRec *__restrict__ patches,
-                                           int first, int row0, int rows, const Grid3 &g, int rule,
-                                           unsigned char *smem, int *err)
+__device__ __forceinline__ TileGeom tile_geom(const PatchRec &pr, int row0, int rows, const Grid3 &g, int rule)
+{
+    TileGeom t;
+    block_box(rule, P, g, pr.v, t.lo, t.d);
+    t.n = 3 * t.d[0] * t.d[1] * t.d[2];
+    t.ld = factor_ld<T>(t.n);
+    t.row1 = min(t.n, row0 + rows);
+    return t;
+}
+
+__device__ __forceinline__ int64_t tile_gidx(const TileGeom &tg, const Grid3 &g, int t)
+{
+    const int nl = t / 3;
+    const int ix = nl % tg.d[0], iy = (nl / tg.d[0]) % tg.d[1], iz = nl / (tg.d[0] * tg.d[1]);
+    return 3 * ((tg.lo[0] + ix) + (int64_t)g.M[0] * ((tg.lo[1] + iy) + (int64_t)g.M[1] * (tg.lo[2] + iz))) + t % 3;
+}
+
+// One thread: announce and start the bulk copies of the tile's rows into `tile`.
+template <int P, typename T>
+__device__ __forceinline__ void tile_issue(const T *__restrict__ pool, const PatchRec &pr, int row0, const TileGeom &tg,
+                                           unsigned char *tile, uint64_t *bar)
+{
+    const uint32_t bytes = (uint32_t)((tg.row1 - row0) * tg.ld * (int)sizeof(T));
+    const char *src = reinterpret_cast<const char *>(pool + pr.off + (size_t)row0 * tg.ld);
+    mbar_expect(bar, bytes);
+    constexpr uint32_t kChunk = 16384;
+    for (uint32_t o = 0; o < bytes; o += kChunk)
+        bulk_load(tile + o, src + o, bytes - o < kChunk ? bytes - o : kChunk, bar);
+}
+
+// All threads: r_B into rb, zero-padded to the row length.
+template <typename T>
+__device__ __forceinline__ void tile_gather(const double *__restrict__ r, const TileGeom &tg, const Grid3 &g, T *rb)
+{
+    for (int t = threadIdx.x; t < tg.ld; t += blockDim.x) rb[t] = t < tg.n ? (T)r[tile_gidx(tg, g, t)] : (T)0;
+}
+
+// All threads, once the tile has landed: z_B[rows] += F[rows, :] r_B.
+template <int P, typename T>
+__device__ __forceinline__ void tile_apply(double *__restrict__ z, const TileGeom &tg, const Grid3 &g, int row0,
+                                           const T *rb, const T *tile)
 {
     using VT = typename Vec16<T>::type;
     constexpr int W = box_width(P), NB = 3 * W * W * W, V = 16 / (int)sizeof(T);
     constexpr int KV = (factor_ld<T>(NB) / V + 31) / 32;  // 16-byte vectors per lane and row
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    T *rb = reinterpret_cast<T *>(smem + 16);
-    T *tile = reinterpret_cast<T *>(smem + rows_tile_offset<P>());
-    const PatchRec pr = patches[first];
-    int lo[3], d[3];
-    block_box(rule, P, g, pr.v, lo, d);
-    const int n = 3 * d[0] * d[1] * d[2], ld = factor_ld<T>(n);
-    const int row1 = min(n, row0 + rows);
-    if (threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)((row1 - row0) * ld * (int)sizeof(T));
-        const char *src = reinterpret_cast<const char *>(pool + pr.off + (size_t)row0 * ld);
-        mbar_init(bar);
-        mbar_expect(bar, bytes);
-        constexpr uint32_t kChunk = 16384;
-        for (uint32_t o = 0; o < bytes; o += kChunk)
-            bulk_load(reinterpret_cast<char *>(tile) + o, src + o, bytes - o < kChunk ? bytes - o : kChunk, bar);
-    }
-    auto gidx = [&](int t) -> int64_t {
-        const int nl = t / 3;
-        const int ix = nl % d[0], iy = (nl / d[0]) % d[1], iz = nl / (d[0] * d[1]);
-        return 3 * ((lo[0] + ix) + (int64_t)g.M[0] * ((lo[1] + iy) + (int64_t)g.M[1] * (lo[2] + iz))) + t % 3;
-    };
-    for (int t = threadIdx.x; t < ld; t += blockDim.x) rb[t] = t < n ? (T)r[gidx(t)] : (T)0;
-    __syncthreads();  // r_B gathered; the barrier is initialised
-    if (!__syncthreads_and(mbar_wait(bar, 0))) {
-        if (threadIdx.x == 0) {
-            atomicExch(err, 1);
-            mbar_wait(bar, 0);  // let the copies still in flight land before the CTA leaves
-        }
-        __syncthreads();
-        return;
-    }
+    constexpr int RPW = sizeof(T) == 8 ? 2 : 4;          // rows per warp and pass
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nv = ld / V;
+    const int nv = tg.ld / V, row1 = tg.row1, ld = tg.ld;
     const VT *rbv = reinterpret_cast<const VT *>(rb);
     VT xr[KV];
 #pragma unroll
     for (int k = 0; k < KV; ++k) xr[k] = lane + 32 * k < nv ? rbv[lane + 32 * k] : Vec16<T>::zero();
-    constexpr int RPW = sizeof(T) == 8 ? 2 : 4;  // rows per warp and pass (FP64 tiles are half as tall)
     for (int t = row0 + RPW * w; t < row1; t += RPW * nw) {
         T a[RPW];
 #pragma unroll
@@ -442,9 +451,39 @@ __device__ __forceinline__ void apply_rows(const double *__restrict__ r, double 
 #pragma unroll
             for (int q = 1; q < RPW; ++q)
                 if (lane == q) v = a[q];
-            z[gidx(t + lane)] += (double)v;
+            z[tile_gidx(tg, g, t + lane)] += (double)v;
         }
     }
+}
+
+// One row tile as one work item of a CTA: issue, gather while the copies fly, wait, apply.  A
+// wait that runs out sets *err and the CTA returns without writing.
+template <int P, typename T>
+__device__ __forceinline__ void apply_rows(const double *__restrict__ r, double *__restrict__ z,
+                                           const T *__restrict__ pool, const PatchRec *__restrict__ patches,
+                                           int first, int row0, int rows, const Grid3 &g, int rule,
+                                           unsigned char *smem, int *err)
+{
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *rb = reinterpret_cast<T *>(smem + 16);
+    unsigned char *tile = smem + rows_tile_offset<P>();
+    const PatchRec pr = patches[first];
+    const TileGeom tg = tile_geom<P, T>(pr, row0, rows, g, rule);
+    if (threadIdx.x == 0) {
+        mbar_init(bar);
+        tile_issue<P, T>(pool, pr, row0, tg, tile, bar);
+    }
+    tile_gather<T>(r, tg, g, rb);
+    __syncthreads();  // r_B gathered; the barrier is initialised
+    if (!__syncthreads_and(mbar_wait(bar, 0))) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            mbar_wait(bar, 0);  // let the copies still in flight land before the CTA leaves
+        }
+        __syncthreads();
+        return;
+    }
+    tile_apply<P, T>(z, tg, g, row0, rb, reinterpret_cast<const T *>(tile));
 }
 
 // Rows [row0, row0 + rows) of z_k,B += F r_k,B for nr <= 8 right-hand sides (vectors nlat
@@ -610,6 +649,100 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     }
 }
 
+// One colour of the Schwarz apply as a persistent launch: CTA b takes work items b, b + G,
+// b + 2G, ... (G = gridDim.x) and pipelines the row tiles of cut blocks through two shared-memory
+// stages: while it works on item i, the bulk copies of its next row tile (item i + G) are already
+// in flight, so the gather, compute and scatter phases of one tile overlap the DRAM transfer of
+// the next and the CTAs of a launch do not fall into step.  Shared-factor batches use a separate
+// area.  Each stage's mbarrier flips phase on every use.  The arithmetic is tile_apply /
+// apply_batch, so S r is bit-identical to schwarz_colour_kernel's.  Dynamic shared memory:
+// rows_tile_offset + 2 tile_bytes + the batch area (schwarz_persistent_smem_bytes).
+template <int P>
+__global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * box_width(P)), P == 3 ? 3 : 1)
+    schwarz_persistent_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ f64,
+                              const float *__restrict__ f32, const PatchRec *__restrict__ patches,
+                              const int2 *__restrict__ items, int nitems, Grid3 g, int rule, int rows32, int rows64,
+                              int tile_bytes, int *err, const int *__restrict__ done)
+{
+    constexpr int GD = (P == 4 ? 4 : 8);
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (done && *done) return;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // bar[0], bar[1]
+    unsigned char *rb = smem + 16;
+    unsigned char *tiles = smem + rows_tile_offset<P>();
+    unsigned char *area = tiles + 2 * (size_t)tile_bytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    auto single = [&](int i) {
+        const int k = items[i].y >> 8;
+        return k == kF32Single || k == kF64Single;
+    };
+    int issued = 0, used = 0;
+    unsigned phase = 0u;  // bit s: parity of the next completion of stage s
+    auto issue = [&](int i) {
+        if (threadIdx.x == 0) {
+            const int2 it = items[i];
+            const int kind = it.y >> 8, tile = it.y & 255;
+            unsigned char *dst = tiles + (size_t)(issued & 1) * tile_bytes;
+            uint64_t *b = &bar[issued & 1];
+            const PatchRec pr = patches[it.x];
+            // the stage was last read through the generic proxy; order those reads before the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (kind == kF32Single)
+                tile_issue<P, float>(f32, pr, tile * rows32, tile_geom<P, float>(pr, tile * rows32, rows32, g, rule), dst, b);
+            else
+                tile_issue<P, double>(f64, pr, tile * rows64, tile_geom<P, double>(pr, tile * rows64, rows64, g, rule), dst, b);
+        }
+        ++issued;
+    };
+    int i = blockIdx.x;
+    if (i < nitems && single(i)) issue(i);
+    for (; i < nitems; i += gridDim.x) {
+        const int nx = i + gridDim.x;
+        if (nx < nitems && single(nx)) issue(nx);
+        const int2 it = items[i];
+        const int kind = it.y >> 8, count = it.y & 255;
+        if (kind == kF32Shared) {
+            apply_batch<P, f32_batch_cap<P>(), float, 16>(r, z, f32, patches, it.x, count, g, rule, area);
+        } else if (kind == kF64Shared) {
+            apply_batch<P, GD, double, 4>(r, z, f64, patches, it.x, count, g, rule, area);
+        } else {
+            const int s = used & 1;
+            ++used;
+            const PatchRec pr = patches[it.x];
+            const bool f = kind == kF32Single;
+            const int rows = f ? rows32 : rows64, row0 = count * rows;
+            const TileGeom tg = f ? tile_geom<P, float>(pr, row0, rows, g, rule) : tile_geom<P, double>(pr, row0, rows, g, rule);
+            if (f)
+                tile_gather<float>(r, tg, g, reinterpret_cast<float *>(rb));
+            else
+                tile_gather<double>(r, tg, g, reinterpret_cast<double *>(rb));
+            __syncthreads();
+            const bool ok = __syncthreads_and(mbar_wait(&bar[s], (phase >> s) & 1u));
+            phase ^= 1u << s;
+            if (!ok) {
+                if (threadIdx.x == 0) {
+                    atomicExch(err, 1);
+                    mbar_wait(&bar[s], (phase >> s) & 1u ^ 1u);  // the copies still in flight land first
+                    if (issued > used) mbar_wait(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+                }
+                __syncthreads();
+                return;
+            }
+            if (f)
+                tile_apply<P, float>(z, tg, g, row0, reinterpret_cast<const float *>(rb),
+                                     reinterpret_cast<const float *>(tiles + (size_t)s * tile_bytes));
+            else
+                tile_apply<P, double>(z, tg, g, row0, reinterpret_cast<const double *>(rb),
+                                      reinterpret_cast<const double *>(tiles + (size_t)s * tile_bytes));
+        }
+        __syncthreads();  // the item's shared memory is free again
+    }
+}
+
 // Start of z = S r for nr vectors nlat apart: z = D r with D = 1 / K_ll for the DOFs in no
 // block (Algorithm 1's diagonal part) and 0 elsewhere, or z = 0 when the blocks cover every
 // free DOF (jac == nullptr).
@@ -659,7 +792,11 @@ void schwarz_launch(const Grid3 &g, const double *r, double *z, const double *f6
     const int threads = schwarz_threads(P, plan.rule);
     for (int i = 0; i < plan.nseg; ++i) {
         const SchwarzSeg &sg = plan.seg[i];
-        if (sg.count > 0)
+        if (sg.count > 0 && plan.persistent)
+            schwarz_persistent_kernel<P><<<std::min(sg.count, plan.grid_cap), threads, plan.smem, s>>>(
+                r, z, f64, f32, plan.patches, plan.batches + sg.first, sg.count, g, plan.rule, plan.rows, plan.rows64,
+                plan.tile_bytes, plan.err, done);
+        else if (sg.count > 0)
             schwarz_colour_kernel<P><<<sg.count, threads, plan.smem, s>>>(
                 r, z, f64, f32, plan.patches, plan.batches + sg.first, g, plan.rule, plan.rows, plan.rows64, plan.err, done);
     }
@@ -741,6 +878,55 @@ int schwarz_smem_bytes(int p, int rows32, int rows64)
     case 2: return smem_bytes_p<2>(rows32, rows64);
     case 3: return smem_bytes_p<3>(rows32, rows64);
     default: return smem_bytes_p<4>(rows32, rows64);
+    }
+}
+
+namespace {
+
+template <int P>
+int persistent_smem_p(int rows32, int rows64, int *tile_bytes)
+{
+    constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
+    const int tb = (std::max(rows32 * factor_ld<float>(NB) * 4, rows64 * factor_ld<double>(NB) * 8) + 15) / 16 * 16;
+    *tile_bytes = tb;
+    return rows_tile_offset<P>() + 2 * tb + NB * ROW + 64 + 4 * NB;
+}
+
+template <int P>
+cudaError_t persistent_grid_p(int threads, int smem, int *grid)
+{
+    cudaError_t e = cudaFuncSetAttribute(schwarz_persistent_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(schwarz_persistent_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_persistent_kernel<P>, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *grid = std::max(1, per_sm) * std::max(1, sms);
+    return e;
+}
+
+}  // namespace
+
+int schwarz_persistent_smem_bytes(int p, int rows32, int rows64, int *tile_bytes)
+{
+    switch (p) {
+    case 1: return persistent_smem_p<1>(rows32, rows64, tile_bytes);
+    case 2: return persistent_smem_p<2>(rows32, rows64, tile_bytes);
+    case 3: return persistent_smem_p<3>(rows32, rows64, tile_bytes);
+    default: return persistent_smem_p<4>(rows32, rows64, tile_bytes);
+    }
+}
+
+cudaError_t schwarz_persistent_grid(int p, int rule, int smem, int *grid)
+{
+    const int threads = schwarz_threads(p, rule);
+    switch (p) {
+    case 1: return persistent_grid_p<1>(threads, smem, grid);
+    case 2: return persistent_grid_p<2>(threads, smem, grid);
+    case 3: return persistent_grid_p<3>(threads, smem, grid);
+    default: return persistent_grid_p<4>(threads, smem, grid);
     }
 }
 

@@ -637,25 +637,50 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
     if (maxn > 0 && (int64_t)maxn * factor_ld<double>(maxn) * 8 <= kTileBudget)
         rows64 = std::max(rows64, (maxn + 1) / 2 * 2);
-    // candidate row-tile sizes: the default (4 rows per warp, tile within kTileBudget), half and a
-    // quarter of it (more, shorter work items)
-    std::vector<std::pair<int, int>> cand = {{rows32, rows64}};
-    if (!o.fixed_tiles)
-        for (int dv : {2, 4}) {
-            const std::pair<int, int> c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(2, rows64 / dv / 2 * 2)};
-            if (c2 != cand.back()) cand.push_back(c2);
-        }
+    // candidates: the default row tiles (4 rows per warp, a tile within kTileBudget), half and a
+    // quarter of them (more, shorter work items), each launched one CTA per work item or as a
+    // persistent launch with two tile stages
+    struct Cand {
+        int r32, r64, pers;
+    };
+    std::vector<Cand> cand;
+    if (o.fixed_tiles == 1 || o.fixed_tiles == 2) {
+        cand.push_back({rows32, rows64, o.fixed_tiles - 1});
+    } else {
+        for (int pers = 0; pers < 2; ++pers)
+            for (int dv : {1, 2, 4}) {
+                const Cand c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(2, rows64 / dv / 2 * 2), pers};
+                if (cand.empty() || c2.r32 != cand.back().r32 || c2.r64 != cand.back().r64 || c2.pers != cand.back().pers)
+                    cand.push_back(c2);
+            }
+    }
     std::vector<int2> batches;
     size_t max_items = 0;
+    int max_smem = 0, max_psmem = 0;
     for (const auto &c2 : cand) {
-        make_items(c2.first, c2.second, batches, plan);
+        make_items(c2.r32, c2.r64, batches, plan);
         max_items = std::max(max_items, batches.size());
+        int tb = 0;
+        if (c2.pers) max_psmem = std::max(max_psmem, schwarz_persistent_smem_bytes(p, c2.r32, c2.r64, &tb));
+        else max_smem = std::max(max_smem, plan.smem);
     }
-    make_items(rows32, rows64, batches, plan);
     if (!C->d_err) PC_CUDA(cudaMalloc(&C->d_err, sizeof(int)));
     PC_CUDA(cudaMemsetAsync(C->d_err, 0, sizeof(int), st));
-    plan.err = C->d_err;
-    PC_CUDA(schwarz_prepare(p, schwarz_smem_bytes(p, rows32, rows64)));  // the largest tile of the candidates
+    if (max_smem > 0) PC_CUDA(schwarz_prepare(p, max_smem));
+    // the kernel attributes, then per candidate the resident CTAs of a persistent launch
+    int grid_dummy = 0;
+    if (max_psmem > 0) PC_CUDA(schwarz_persistent_grid(p, rule, max_psmem, &grid_dummy));
+    auto configure = [&](const Cand &c2) -> std::string {
+        make_items(c2.r32, c2.r64, batches, plan);
+        plan.err = C->d_err;
+        plan.persistent = c2.pers;
+        if (c2.pers) {
+            plan.smem = schwarz_persistent_smem_bytes(p, c2.r32, c2.r64, &plan.tile_bytes);
+            if (schwarz_persistent_grid(p, rule, plan.smem, &plan.grid_cap) != cudaSuccess) return "persistent grid";
+            schwarz_persistent_grid(p, rule, max_psmem, &grid_dummy);  // keep the attribute at the largest size
+        }
+        return std::string();
+    };
     if (C->d_patches) cudaFree(C->d_patches);
     if (C->d_batches) cudaFree(C->d_batches);
     C->d_patches = nullptr;
@@ -663,11 +688,10 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     PC_CUDA(cudaMalloc(&C->d_patches, sizeof(PatchRec) * std::max<size_t>(all.size(), 1)));
     PC_CUDA(cudaMalloc(&C->d_batches, sizeof(int2) * std::max<size_t>(max_items, 1)));
     PC_CUDA(cudaMemcpyAsync(C->d_patches, all.data(), sizeof(PatchRec) * all.size(), cudaMemcpyHostToDevice, st));
-    PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
-    PC_CUDA(cudaStreamSynchronize(st));
     plan.patches = C->d_patches;
     plan.batches = C->d_batches;
-    for (int k = 0; k < 4; ++k) C->tune_seconds[k] = 0.0;
+    for (int k = 0; k < 8; ++k) C->tune_seconds[k] = 0.0;
+    size_t best_k = 0;
     if (cand.size() > 1) {
         // autotuner: S applied to the load vector (a field with the problem's own structure) into
         // the z work vector, 2 warm-up and 5 timed applies per candidate on the context's stream
@@ -675,10 +699,10 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         PC_CUDA(cudaEventCreate(&e0));
         PC_CUDA(cudaEventCreate(&e1));
         double best = 1e300;
-        size_t best_k = 0;
         std::string fail;
-        for (size_t k = 0; k < cand.size() && fail.empty(); ++k) {
-            make_items(cand[k].first, cand[k].second, batches, plan);
+        for (size_t k = 0; k < cand.size() && k < 8 && fail.empty(); ++k) {
+            fail = configure(cand[k]);
+            if (!fail.empty()) break;
             if (cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st) !=
                 cudaSuccess) {
                 fail = "autotune upload";
@@ -703,10 +727,13 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (!fail.empty()) return fail + ": " + cudaGetErrorString(cudaGetLastError());
-        make_items(cand[best_k].first, cand[best_k].second, batches, plan);
-        PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
-        PC_CUDA(cudaStreamSynchronize(st));
     }
+    {
+        const std::string e = configure(cand[best_k]);
+        if (!e.empty()) return e;
+    }
+    PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
     plan.patches = C->d_patches;
     plan.batches = C->d_batches;
     plan.rule = rule;

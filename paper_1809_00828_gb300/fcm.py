@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("n_blocks", ctypes.c_int64), ("n_blocks_fp32", ctypes.c_int64), ("kapply_fmas", ctypes.c_int64),
                 ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double),
                 ("coarse_seconds", ctypes.c_double), ("n_jacobi", ctypes.c_int64),
-                ("rows32", ctypes.c_int), ("rows64", ctypes.c_int), ("tune_seconds", ctypes.c_double * 4),
+                ("rows32", ctypes.c_int), ("rows64", ctypes.c_int), ("tiles_persistent", ctypes.c_int),
+                ("tune_seconds", ctypes.c_double * 8),
                 ("device_error", ctypes.c_int)]
 
 
@@ -171,11 +172,12 @@ class Solver:
         return b
 
     def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0,
-                      autotune=True):
+                      autotune=True, launch=None):
         """blocks: "vertex" (vertex patches) or "element" (element blocks of the cells with
         eta_T <= eta_bar, diagonal scaling for the DOFs in no block).  autotune: time the
-        Schwarz apply for a few row-tile sizes and keep the fastest (results do not depend
-        on the choice)."""
+        Schwarz apply for a few launch shapes and keep the fastest (results do not depend
+        on the choice).  launch ("items" or "persistent") fixes the default tile with that
+        launch instead."""
         if blocks not in ("vertex", "element"):
             raise ValueError(f"unknown block rule {blocks!r}")
         o = PrecondOpts()
@@ -184,7 +186,7 @@ class Solver:
         o.cond_fp64 = cond_fp64
         o.block_rule = BLOCKS_ELEMENT if blocks == "element" else BLOCKS_VERTEX
         o.eta_bar = eta_bar
-        o.fixed_tiles = 0 if autotune else 1
+        o.fixed_tiles = {None: 0 if autotune else 1, "items": 1, "persistent": 2}[launch]
         self._check(load().fcm_precond_build(self.ctx, ctypes.byref(o)))
         self.info = self.get_info()
 

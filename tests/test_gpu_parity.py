@@ -232,7 +232,18 @@ def test_row_tile_autotuner_leaves_S_unchanged(precision):
     z1 = s.apply_S(x)
     info1 = s.get_info()
     assert torch.equal(z0, z1)
-    assert info0["tune_seconds"] == [0.0] * 4 and sum(t > 0 for t in info1["tune_seconds"]) >= 2
+    assert info0["tune_seconds"] == [0.0] * 8 and sum(t > 0 for t in info1["tune_seconds"]) >= 2
     assert info0["device_error"] == 0 and info1["device_error"] == 0
     assert info1["rows32"] <= info0["rows32"] and info1["rows64"] <= info0["rows64"]
+    # the persistent launch (two tile stages, the next tile prefetched) gives the same S r
+    s.precond_build(precision=precision, launch="persistent")
+    info2 = s.get_info()
+    assert info2["tiles_persistent"] == 1 and info0["tiles_persistent"] == 0
+    z2 = s.apply_S(x)
+    assert torch.equal(z0, z2) and s.get_info()["device_error"] == 0
+    # and inside a solve, where the colour launches sit in the captured graph
+    u1, its1, _, _ = s.pcg_solve(s.rhs(), w.tol, 5000)
+    s.precond_build(precision=precision, launch="items")
+    u0, its0, _, _ = s.pcg_solve(s.rhs(), w.tol, 5000)
+    assert its0 == its1 and torch.equal(u0, u1)
     s.close()
