@@ -459,6 +459,9 @@ def run_fcm(args, rank, world, local_rank):
                              f"element matrices {info['element_bytes'] / 2**30:.2f} GiB",
                        "n_blocks": info["n_blocks"], "n_factors": info["n_factors"],
                        "n_factors_fp32": info["n_blocks_fp32"], "n_jacobi_dofs": info["n_jacobi"],
+                       "schwarz_launch": {"rows_fp32": info["rows32"], "rows_fp64": info["rows64"],
+                                          "persistent": bool(info["tiles_persistent"]),
+                                          "autotune_ms": [round(t * 1e3, 4) for t in info["tune_seconds"] if t > 0]},
                        "setup_s": info["setup_seconds"], "precond_s": info["precond_seconds"],
                        "coarse_operator_s": info["coarse_seconds"],
                        "load_cases": cases},
