@@ -340,7 +340,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 }
 
 // Waits for phase `parity` of the barrier; gives up (false) after a bounded number of tries.
-constexpr int kWaitTries = 1 << 22;
+constexpr int kWaitTries = 1 << 21;
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     for (int i = 0; i < kWaitTries; ++i)
@@ -701,6 +701,12 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     int i = blockIdx.x;
     if (i < nitems && single(i)) issue(i);
     for (; i < nitems; i += gridDim.x) {
+        // a CTA that gave up on a copy has flagged the apply as failed: stop early
+        if (__syncthreads_or(*reinterpret_cast<volatile int *>(err) != 0)) {
+            if (threadIdx.x == 0 && issued > used) mbar_wait(&bar[used & 1], (phase >> (used & 1)) & 1u);
+            __syncthreads();
+            return;
+        }
         const int nx = i + gridDim.x;
         if (nx < nitems && single(nx)) issue(nx);
         const int2 it = items[i];
