@@ -285,16 +285,8 @@ __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double
 #pragma unroll UNROLL
         for (int j = 0; j < n; ++j) {
             const T f = __ldg(F + (size_t)j * ld + t);
-            // the G residuals of row j as 16-byte shared loads (the same address for the warp)
-            using VT = typename Vec16<T>::type;
-            constexpr int V = 16 / (int)sizeof(T);
-            const VT *rv = reinterpret_cast<const VT *>(&rbT[j][0]);
 #pragma unroll
-            for (int q = 0; q < G / V; ++q) {
-                const VT x = rv[q];
-#pragma unroll
-                for (int e = 0; e < V; ++e) acc[q * V + e] = fma(f, Vec16<T>::get(x, e), acc[q * V + e]);
-            }
+            for (int k = 0; k < G; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
         }
         const int rt = rel[t];
 #pragma unroll
