@@ -275,6 +275,17 @@ def _unet_launches(net):
     return (L - 1) + 4 * L + 6 * (L - 1) + 1
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (the job ends with its slowest replica); `value` itself
+    without a process group."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_fcm(args, rank, world, local_rank):
     import torch
     from paper_1809_00828_gb300 import fcm
@@ -344,10 +355,7 @@ def run_fcm(args, rank, world, local_rank):
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     ms_per_step = elapsed / args.steps * 1e3
     last = s.last_solve()
 
