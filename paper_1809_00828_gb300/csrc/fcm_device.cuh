@@ -94,6 +94,8 @@ void schwarz_default_rows(int p, int rule, int *rows32, int *rows64);
 int schwarz_smem_bytes(int p, int rows32, int rows64);
 // blocks per FP32 shared-factor batch
 int schwarz_f32_batch_cap(int p);
+// true when blocks with their own factor are applied whole with direct loads (one item per block)
+bool schwarz_direct_singles(int p);
 // persistent launches: dynamic shared memory (and the bytes of one tile stage) for given row counts,
 // and the resident CTAs of the GPU at that size (sets the kernel's shared-memory attribute)
 int schwarz_persistent_smem_bytes(int p, int rows32, int rows64, int *tile_bytes);

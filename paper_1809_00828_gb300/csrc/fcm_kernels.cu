@@ -348,6 +348,15 @@ __host__ __device__ constexpr int rows_tile_offset()
     return 16 + (factor_ld<double>(3 * box_width(P) * box_width(P) * box_width(P)) * 8 + 15) / 16 * 16;
 }
 
+// Small blocks (p <= 2: 81 DOFs at most) are applied whole, one item each, with each thread
+// streaming its row straight from the factor pool: their few kilobytes do not amortise a staged
+// bulk copy.  Larger blocks go through row tiles.
+template <int P>
+__host__ __device__ constexpr bool direct_singles()
+{
+    return P <= 2;
+}
+
 // Blocks per FP32 shared-factor batch: each load of a factor entry (from L2: shared factors are
 // few) feeds that many multiply-adds.  (16 measured slower than 8 at p = 3: more registers, no
 // less time.)
@@ -605,8 +614,13 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     if (done && *done) return;
     const int2 bt = batches[blockIdx.x];
     const int count = bt.y & 255, kind = bt.y >> 8;
-    // single-factor items carry a row tile index in place of the block count
-    if (kind == kF32Single)
+    // single-factor items carry a row tile index in place of the block count (small blocks: one
+    // item each, in the order of the direct single-vector path)
+    if (direct_singles<P>() && kind == kF32Single)
+        apply_multi<P, float, 8>(r, z, nlat, nr, f32, patches, bt.x, 1, g, rule, smem);
+    else if (direct_singles<P>() && kind == kF64Single)
+        apply_multi<P, double, 8>(r, z, nlat, nr, f64, patches, bt.x, 1, g, rule, smem);
+    else if (kind == kF32Single)
         apply_multi_rows<P, float>(r, z, nlat, nr, f32, patches, bt.x, count * rows32, rows32, g, rule, smem);
     else if (kind == kF64Single && P < 4)
         apply_multi_rows<P, double>(r, z, nlat, nr, f64, patches, bt.x, count * rows64, rows64, g, rule, smem);
@@ -634,10 +648,17 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     const int count = bt.y & 255, kind = bt.y >> 8;
     switch (kind) {
     case kF32Shared: apply_batch<P, f32_batch_cap<P>(), float, 16>(r, z, f32, patches, bt.x, count, g, rule, smem); break;
-    // single-factor items carry a row tile index in place of the block count
-    case kF32Single: apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows32, rows32, g, rule, smem, err); break;
     case kF64Shared: apply_batch<P, GD, double, 4>(r, z, f64, patches, bt.x, count, g, rule, smem); break;
-    default: apply_rows<P, double>(r, z, f64, patches, bt.x, count * rows64, rows64, g, rule, smem, err); break;
+    // single-factor items carry a row tile index in place of the block count; small blocks (p <= 2)
+    // are one item each, applied with direct loads (no staging pays off for them)
+    case kF32Single:
+        if (direct_singles<P>()) apply_batch<P, 1, float, 16>(r, z, f32, patches, bt.x, 1, g, rule, smem);
+        else apply_rows<P, float>(r, z, f32, patches, bt.x, count * rows32, rows32, g, rule, smem, err);
+        break;
+    default:
+        if (direct_singles<P>()) apply_batch<P, 1, double, 16>(r, z, f64, patches, bt.x, 1, g, rule, smem);
+        else apply_rows<P, double>(r, z, f64, patches, bt.x, count * rows64, rows64, g, rule, smem, err);
+        break;
     }
 }
 
@@ -670,7 +691,7 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
     __syncthreads();
     auto single = [&](int i) {
         const int k = items[i].y >> 8;
-        return k == kF32Single || k == kF64Single;
+        return !direct_singles<P>() && (k == kF32Single || k == kF64Single);
     };
     int issued = 0, used = 0;
     unsigned phase = 0u;  // bit s: parity of the next completion of stage s
@@ -707,6 +728,10 @@ __global__ void __launch_bounds__(threads_for(3 * box_width(P) * box_width(P) * 
             apply_batch<P, f32_batch_cap<P>(), float, 16>(r, z, f32, patches, it.x, count, g, rule, area);
         } else if (kind == kF64Shared) {
             apply_batch<P, GD, double, 4>(r, z, f64, patches, it.x, count, g, rule, area);
+        } else if (direct_singles<P>() && kind == kF32Single) {
+            apply_batch<P, 1, float, 16>(r, z, f32, patches, it.x, 1, g, rule, area);
+        } else if (direct_singles<P>()) {
+            apply_batch<P, 1, double, 16>(r, z, f64, patches, it.x, 1, g, rule, area);
         } else {
             const int s = used & 1;
             ++used;
@@ -843,6 +868,7 @@ int smem_bytes_p(int rows32, int rows64)
     constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
     const int batch = std::max(NB * ROW + 64 + 4 * NB, NB * f32_batch_cap<P>() * 4 + 8 * f32_batch_cap<P>() + 4 * NB);
     static_assert(f32_batch_cap<P>() <= 16, "the batch's block bases take 8 bytes each after rbT");
+    if (direct_singles<P>()) return batch;  // no row tiles
     const int t32 = rows_tile_offset<P>() + rows32 * factor_ld<float>(NB) * 4;
     const int t64 = rows_tile_offset<P>() + rows64 * factor_ld<double>(NB) * 8;
     return std::max(batch, std::max(t32, t64));
@@ -885,7 +911,8 @@ template <int P>
 int persistent_smem_p(int rows32, int rows64, int *tile_bytes)
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
-    const int tb = (std::max(rows32 * factor_ld<float>(NB) * 4, rows64 * factor_ld<double>(NB) * 8) + 15) / 16 * 16;
+    const int tb = direct_singles<P>() ? 0
+                                       : (std::max(rows32 * factor_ld<float>(NB) * 4, rows64 * factor_ld<double>(NB) * 8) + 15) / 16 * 16;
     *tile_bytes = tb;
     return rows_tile_offset<P>() + 2 * tb + NB * ROW + 64 + 4 * NB;
 }
@@ -927,6 +954,8 @@ cudaError_t schwarz_persistent_grid(int p, int rule, int smem, int *grid)
     default: return persistent_grid_p<4>(threads, smem, grid);
     }
 }
+
+bool schwarz_direct_singles(int p) { return p <= 2 ? direct_singles<2>() : direct_singles<3>(); }
 
 int schwarz_f32_batch_cap(int p) { return p == 4 ? f32_batch_cap<4>() : f32_batch_cap<3>(); }
 

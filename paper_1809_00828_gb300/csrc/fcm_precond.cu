@@ -637,6 +637,12 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
     if (maxn > 0 && (int64_t)maxn * factor_ld<double>(maxn) * 8 <= kTileBudget)
         rows64 = std::max(rows64, (maxn + 1) / 2 * 2);
+    // blocks applied whole with direct loads: exactly one item per block
+    const bool whole = schwarz_direct_singles(p);
+    if (whole) {
+        rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
+        rows64 = std::max(rows64, (maxn + 3) / 4 * 4);
+    }
     // candidates: the default row tiles (4 rows per warp, a tile within kTileBudget), half and a
     // quarter of them (more, shorter work items), each launched one CTA per work item or as a
     // persistent launch with two tile stages
@@ -649,6 +655,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     } else {
         for (int pers = 0; pers < 2; ++pers)
             for (int dv : {1, 2, 4}) {
+                if (whole && dv > 1) continue;  // whole blocks only
                 const Cand c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(2, rows64 / dv / 2 * 2), pers};
                 if (cand.empty() || c2.r32 != cand.back().r32 || c2.r64 != cand.back().r64 || c2.pers != cand.back().pers)
                     cand.push_back(c2);
