@@ -249,8 +249,9 @@ __device__ __forceinline__ void apply_batch(const double *__restrict__ r, double
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W;
     T(*rbT)[G] = reinterpret_cast<T(*)[G]>(smem);
-    int64_t *base = reinterpret_cast<int64_t *>(smem + sizeof(T) * NB * G);  // G entries, -1: no block
-    int *rel = reinterpret_cast<int *>(base + G);                            // NB entries
+    // G entries, -1: no block; 16-byte aligned after rbT (4 NB bytes for one FP32 block)
+    int64_t *base = reinterpret_cast<int64_t *>(smem + (sizeof(T) * NB * G + 15) / 16 * 16);
+    int *rel = reinterpret_cast<int *>(base + G);  // NB entries
     const PatchRec p0 = patches[first];
     int lo0[3], d[3];
     block_box(rule, P, g, p0.v, lo0, d);
@@ -866,7 +867,8 @@ template <int P>
 int smem_bytes_p(int rows32, int rows64)
 {
     constexpr int W = box_width(P), NB = 3 * W * W * W, GD = (P == 4 ? 4 : 8), ROW = (GD * 8 > 32 ? GD * 8 : 32);
-    const int batch = std::max(NB * ROW + 64 + 4 * NB, NB * f32_batch_cap<P>() * 4 + 8 * f32_batch_cap<P>() + 4 * NB);
+    // rbT, the block bases (16-byte aligned) and the box offsets, for the largest batch of either precision
+    const int batch = std::max(NB * ROW + 16 + 64 + 4 * NB, NB * f32_batch_cap<P>() * 4 + 16 + 8 * f32_batch_cap<P>() + 4 * NB);
     static_assert(f32_batch_cap<P>() <= 16, "the batch's block bases take 8 bytes each after rbT");
     if (direct_singles<P>()) return batch;  // no row tiles
     const int t32 = rows_tile_offset<P>() + rows32 * factor_ld<float>(NB) * 4;
@@ -914,7 +916,7 @@ int persistent_smem_p(int rows32, int rows64, int *tile_bytes)
     const int tb = direct_singles<P>() ? 0
                                        : (std::max(rows32 * factor_ld<float>(NB) * 4, rows64 * factor_ld<double>(NB) * 8) + 15) / 16 * 16;
     *tile_bytes = tb;
-    return rows_tile_offset<P>() + 2 * tb + NB * ROW + 64 + 4 * NB;
+    return rows_tile_offset<P>() + 2 * tb + NB * ROW + 16 + 64 + 4 * NB;
 }
 
 template <int P>
