@@ -537,7 +537,6 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
 
     // ---- launch plan: per colour and precision, batches of blocks sharing a factor (up to 8; 4
     // for FP64 at p = 4) and row tiles of the blocks with their own factor
-    std::vector<int> users(fac.size(), 0);
     std::vector<std::vector<int>> by_colour_factor[8];
     for (int c = 0; c < 8; ++c) by_colour_factor[c].resize(fac.size());
     C->n_blocks = 0;
