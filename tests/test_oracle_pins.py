@@ -5,6 +5,7 @@ exact symbolic integration, textbook results, invariants, and the paper's
 qualitative statements (Sec. 3.1 remark on Jacobi, Sec. 3.1 single-block
 case, Additive-Schwarz lemma of Sec. 3.1/3.2).  No GPU is needed.
 """
+import os
 import numpy as np
 import numpy.polynomial.legendre as npleg
 import pytest
@@ -426,3 +427,24 @@ def test_unit_strain_loads_equal_minus_K_times_the_linear_field():
         b = P.load(k + 1)
         assert np.abs(b + K @ u).max() < 1e-12 * np.abs(b).max()
         assert np.abs(b).max() > 0
+
+
+def test_paper_dof_table_is_the_trunk_space_not_the_full_tensor_product():
+    # Reading 1 (basis): the paper's DOF table for the 8^3, p = 3 cube (Sec. 5.1, k = 0) counts the trunk
+    # space: per component, every vertex, p - 1 modes per edge, and no face or interior modes at p = 3
+    # (trunk face modes need i + j <= p with i, j >= 2).  The build uses the full tensor product, whose count
+    # is 3 (p n + 1)^3 -- the oracle's lattice size for the same grid.
+    rows = [line.split() for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec5_1_dofs.txt"))
+            if line.strip() and not line.startswith("#")]
+    k0 = {int(k): int(v) for k, v in rows}[0]
+    n, p = 8, 3
+    vertices = (n + 1) ** 3
+    edges = 3 * n * (n + 1) ** 2
+    faces = 3 * n * n * (n + 1)
+    face_modes = sum(1 for i in range(2, p + 1) for j in range(2, p + 1) if i + j <= p)
+    cell_modes = sum(1 for i in range(2, p + 1) for j in range(2, p + 1) for l in range(2, p + 1) if i + j + l <= p)
+    trunk = 3 * (vertices + (p - 1) * edges + face_modes * faces + cell_modes * n ** 3)
+    assert trunk == k0 == 13851
+    w = I.Workload("table", (n, n, n), p, 1e-8, I.single_sphere_void(0, 0.01, 0.0, octree_depth=1), 1e-8, bc=-1)
+    d, keep = O.desc_for(w)
+    assert O.Problem(d, keep).nlat == 3 * (p * n + 1) ** 3 == 46875
