@@ -389,7 +389,8 @@ def run_fcm(args, rank, world, local_rank):
     fp64_peak = fp64_peak_tflops(sm_mhz)
     achieved_tf = s_flops / t_s / 1e12
     achieved_gbs = s_bytes / t_s / 1e9
-    kernel = f"schwarz_colour_kernel<{w.p}> (8 colour launches per S apply)"
+    kernel = (f"schwarz_persistent_kernel<{w.p}>" if info["tiles_persistent"] else f"schwarz_colour_kernel<{w.p}>") + \
+        " (8 colour launches per S apply, the shape the build's autotuner kept)"
     if args.precision == "fp64":
         # FP64 factors: one FP64 multiply-add per 8-byte entry; the FP64 pipe saturates first
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
