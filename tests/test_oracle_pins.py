@@ -448,3 +448,17 @@ def test_paper_dof_table_is_the_trunk_space_not_the_full_tensor_product():
     w = I.Workload("table", (n, n, n), p, 1e-8, I.single_sphere_void(0, 0.01, 0.0, octree_depth=1), 1e-8, bc=-1)
     d, keep = O.desc_for(w)
     assert O.Problem(d, keep).nlat == 3 * (p * n + 1) ** 3 == 46875
+
+
+def test_element_blocks_on_cut_cells_beat_diagonal_scaling():
+    # Sec. 3.2 "Optimizing the number of blocks" / Sec. 5.2: diagonal scaling alone (eta_bar = 0) is not
+    # robust to a thin cut; blocks on the cut cells (0 < eta_T <= eta_bar) recover most of the loss, and a
+    # block for every element (eta_bar = 1) does at least as well.
+    g = I.halfspace(1.0, 0.0, 0.0, 0.75 + 0.25 * 0.01, octree_depth=5)
+    P = O.Problem.from_workload(I.Workload("sliver", (4, 4, 4), 2, 1e-12, g, 1e-8))
+    its = {}
+    for eta_bar in (0.0, 0.5, 1.0):
+        P.precond_build(3, 1e-13, eta_bar)
+        _, its[eta_bar], _ = P.pcg(tol=1e-8, maxit=30000)
+    assert its[0.5] * 5 < its[0.0]
+    assert its[1.0] <= its[0.5]
