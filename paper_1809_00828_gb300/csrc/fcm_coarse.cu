@@ -474,7 +474,7 @@ fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
     return FCM_OK;
 }
 
-// one iteration: q = K p, x and r, zS = S r and the judge, c = P y, the next direction
+// one iteration: q = K p, x and r, zS = S r and its norm (the convergence test), c = P y, the next direction
 fcm_status fcg_iteration(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
 {
     FcgState *F = C->fcg;
