@@ -630,8 +630,7 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     };
     int rows32 = 0, rows64 = 0;
     schwarz_default_rows(p, rule, &rows32, &rows64);
-    // small blocks (p <= 2) fit one tile whole: then the default is one item per block, and the
-    // autotuner's candidates split it in two and four
+    // a largest block that fits one tile whole (p <= 2) is one item per block by default
     if (maxn > 0 && (int64_t)maxn * factor_ld<float>(maxn) * 4 <= kTileBudget)
         rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
     if (maxn > 0 && (int64_t)maxn * factor_ld<double>(maxn) * 8 <= kTileBudget)
@@ -656,6 +655,10 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
             for (int dv : {1, 2, 4}) {
                 if (whole && dv > 1) continue;  // whole blocks only
                 const Cand c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(2, rows64 / dv / 2 * 2), pers};
+                // a work item carries its tile index in the 8 bits below its kind: candidates with more
+                // than 255 tiles per block (p = 4 vertex patches at a half or a quarter of the default
+                // tile) are not formed
+                if ((maxn + c2.r32 - 1) / c2.r32 > 255 || (maxn + c2.r64 - 1) / c2.r64 > 255) continue;
                 if (cand.empty() || c2.r32 != cand.back().r32 || c2.r64 != cand.back().r64 || c2.pers != cand.back().pers)
                     cand.push_back(c2);
             }
