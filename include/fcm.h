@@ -330,6 +330,55 @@ fcm_status fcm_fpcg_solve_host(fcm_ctx *ctx, fcm_unet *net, double gamma, int co
  *     (cudaGetSymbolAddress); make it before any stream capture. */
 fcm_status fcm_apply_S_noalloc(fcm_ctx *ctx, const double *r_dev, double *z_dev);
 
+/* ---- Multi-level hp overlays (Sec. 2.2) and their leaf blocks (Sec. 3.2): host-side plan ----------------
+ *
+ * A base grid (grid->n cells on [grid->lo, grid->hi]) refined k times toward the sphere surfaces of geom
+ * (geom->kind must be 0): a level-l cell that a sphere surface crosses (min distance < r < max distance from
+ * the centre) carries an overlay of its 8 children on level l + 1.  Every level has its own integrated-
+ * Legendre basis of order p, one set of modes per topological component.  A level-l component is active iff
+ * every in-domain level-l cell position around it exists (homogeneous Dirichlet conditions on the overlay's
+ * boundary) and at least one of them is a leaf (covered components are deactivated).
+ *
+ * Blocks are per leaf cell (Sec. 3.2 "Selecting suitable blocks"):
+ *   kind 0, full: every active scalar function supported on the leaf;
+ *   kind 1, truncated: the leaf's own-level functions plus, for each corner whose own-level vertex function
+ *           is inactive, the vertex function of the highest coarser level at which the corner point is an
+ *           active vertex.  No scalar function is in more than 2^3 truncated blocks.
+ * Scalar function f carries 3 displacement DOFs.  Orders: functions level by level, components (doubled
+ * coordinates: even = on a grid plane, odd = inside a cell interval) sorted by (z, y, x), modes with the
+ * bubble index of the lowest odd axis slowest; leaves by level, then (x, y, z) lexicographically.
+ *
+ * The plan is host memory only (no device work); the library owns it until fcm_mlhp_destroy. */
+typedef struct fcm_mlhp fcm_mlhp;
+typedef struct {
+    int levels;                 /* levels of the hierarchy, 1 = the base grid only */
+    int64_t n_leaves;           /* leaf cells over all levels */
+    int64_t n_functions;        /* active scalar functions, full tensor-product modes */
+    int64_t n_functions_trunk;  /* the same in the trunk space (face and cell bubble indices sum to <= p) */
+    int n_max_full;             /* most full blocks one scalar function belongs to (over all leaves) */
+    int n_max_truncated;        /* the same for truncated blocks */
+    int max_block_full;         /* most scalar functions in one full block */
+    int max_block_truncated;    /* the same for truncated blocks */
+} fcm_mlhp_info;
+
+/* Build the plan.  1 <= p <= 4, 0 <= k <= 10, grid->n[a] << k < 2^20.  FCM_EINVAL on bad arguments,
+ * FCM_ENOMEM when host memory runs out. */
+fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p, int k, fcm_mlhp **out);
+fcm_status fcm_mlhp_get_info(const fcm_mlhp *plan, fcm_mlhp_info *info);
+/* Level and cell index (on the level's grid of n * 2^level cells) of leaf `leaf`. */
+fcm_status fcm_mlhp_leaf(const fcm_mlhp *plan, int64_t leaf, int *level, int cell[3]);
+/* Level, component (doubled coordinates on the level's grid) and mode of scalar function f: mode[a] is 0
+ * on an axis where the component is a vertex coordinate (linear factor), else the bubble index 2..p. */
+fcm_status fcm_mlhp_function(const fcm_mlhp *plan, int64_t f, int *level, int comp[3], int mode[3]);
+/* Scalar functions of leaf `leaf`'s block (kind 0 full, 1 truncated) into fids[0 .. *count).  *count is
+ * always set; FCM_EINVAL (nothing copied) when it exceeds cap. */
+fcm_status fcm_mlhp_block(const fcm_mlhp *plan, int64_t leaf, int kind, int64_t *fids, int cap, int *count);
+/* Function f restricted to leaf `leaf` (f must be supported there: FCM_EINVAL otherwise) is the tensor
+ * product over the axes a of sum_j coef[a (p+1) + j] b_j(t_a), with b = (N0, N1, phi_2 .. phi_p) the
+ * leaf's own 1D shape functions in its local coordinate t_a in [-1, 1]. */
+fcm_status fcm_mlhp_restriction(const fcm_mlhp *plan, int64_t leaf, int64_t f, double *coef);
+void fcm_mlhp_destroy(fcm_mlhp *plan);
+
 /* Message of the last failure on ctx (ctx may be NULL for setup failures). */
 const char *fcm_last_error(const fcm_ctx *ctx);
 

@@ -1,0 +1,407 @@
+// Multi-level hp hierarchy and its leaf blocks: the host-side plan (Sec. 2.2, Sec. 3.2).
+//
+// A base grid of cells is refined toward sphere surfaces by superposed overlays: level l + 1 holds the 8
+// children of every refined level-l cell.  Every level carries its own integrated-Legendre basis, one
+// set of modes per topological component (vertex, edge, face, cell) of the level's grid.  A level-l
+// component is active iff every in-domain level-l cell position around it exists (the overlay's
+// homogeneous Dirichlet boundary, Sec. 2.2) and at least one of them is a leaf (components a finer
+// overlay covers are deactivated for linear independence).
+//
+// Blocks are per leaf (Sec. 3.2 "Selecting suitable blocks"): the full block holds every active function
+// supported on the leaf; the truncated block holds the leaf's own-level functions plus, for each leaf
+// corner whose own-level vertex function is inactive, the vertex function of the highest coarser level
+// at which the corner point is a vertex and is active (the 1D rule of Sec. 3.2 applied to the trilinear
+// functions).
+//
+// A level-l function restricted to a level-L leaf is a polynomial of the leaf's own tensor-product space:
+// fcm_mlhp_restriction gives its 1D coefficients per axis in the leaf's basis (N0, N1, phi_2..phi_p), so
+// a leaf's stiffness is C K_leaf C^T with the leaf's standard element matrix K_leaf.
+//
+// Enumeration orders (binding for callers that compare with other implementations): functions level by
+// level, components sorted by (z, y, x), modes with the bubble index of the lowest odd axis slowest;
+// leaves by level, then by (x, y, z) lexicographically; a leaf's full block level by level from 0, the
+// components of the ancestor's closure with x fastest.
+#include "fcm.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <tuple>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace {
+
+using I3 = std::array<int, 3>;
+
+uint64_t key3(const I3 &c) { return (uint64_t)c[0] | ((uint64_t)c[1] << 21) | ((uint64_t)c[2] << 42); }
+
+// A sphere surface crosses the closed box [lo, hi]: min distance < r < max distance from the centre.
+bool box_cut(const std::vector<std::array<double, 4>> &sph, const double lo[3], const double hi[3])
+{
+    for (const auto &s : sph) {
+        double dn = 0.0, df = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double c = s[a];
+            const double nr = std::min(std::max(c, lo[a]), hi[a]);
+            const double fr = std::fabs(c - lo[a]) > std::fabs(c - hi[a]) ? lo[a] : hi[a];
+            dn += (c - nr) * (c - nr);
+            df += (c - fr) * (c - fr);
+        }
+        if (std::sqrt(dn) < s[3] && s[3] < std::sqrt(df)) return true;
+    }
+    return false;
+}
+
+// 1D shape functions on [-1, 1] in the order N0, N1, phi_2..phi_p (Sec. 2.1 integrated Legendre).
+void shape1d(int p, double xi, double *f)
+{
+    double P[6];
+    P[0] = 1.0;
+    P[1] = xi;
+    for (int k = 1; k < p; ++k) P[k + 1] = ((2 * k + 1) * xi * P[k] - k * P[k - 1]) / (k + 1);
+    f[0] = 0.5 * (1.0 - xi);
+    f[1] = 0.5 * (1.0 + xi);
+    for (int j = 2; j <= p; ++j) f[j] = (P[j] - P[j - 2]) / std::sqrt(2.0 * (2 * j - 1));
+}
+
+}  // namespace
+
+struct fcm_mlhp {
+    int n[3] = {0, 0, 0};
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int p = 0, levels = 0;
+    std::vector<std::unordered_set<uint64_t>> cells, refined;
+    std::vector<std::pair<int, I3>> leaves;
+    // functions: level, component (doubled coordinates), mode (0 on vertex axes, 2..p on bubble axes)
+    std::vector<int> f_level;
+    std::vector<I3> f_comp, f_mode;
+    std::vector<std::unordered_map<uint64_t, int64_t>> first;  // per level: component -> its first function
+    int64_t n_trunk = 0;
+    int nmax_full = 0, nmax_trunc = 0, maxb_full = 0, maxb_trunc = 0;
+
+    int ext(int l, int a) const { return n[a] << l; }
+
+    bool has(int l, const I3 &c) const { return cells[l].count(key3(c)) != 0; }
+    bool is_refined(int l, const I3 &c) const { return refined[l].count(key3(c)) != 0; }
+
+    bool active(int l, const I3 &q) const
+    {
+        int lists[3][2], cnt[3];
+        for (int a = 0; a < 3; ++a) {
+            cnt[a] = 0;
+            if (q[a] % 2) {
+                lists[a][cnt[a]++] = (q[a] - 1) / 2;
+            } else {
+                for (int i : {q[a] / 2 - 1, q[a] / 2})
+                    if (i >= 0 && i < ext(l, a)) lists[a][cnt[a]++] = i;
+            }
+        }
+        bool any_leaf = false;
+        for (int i = 0; i < cnt[0]; ++i)
+            for (int j = 0; j < cnt[1]; ++j)
+                for (int k = 0; k < cnt[2]; ++k) {
+                    const I3 c = {lists[0][i], lists[1][j], lists[2][k]};
+                    if (!has(l, c)) return false;
+                    if (!is_refined(l, c)) any_leaf = true;
+                }
+        return any_leaf;
+    }
+
+    int64_t nmodes(const I3 &q) const
+    {
+        int64_t m = 1;
+        for (int a = 0; a < 3; ++a)
+            if (q[a] & 1) m *= p - 1;
+        return m;
+    }
+
+    // append the functions of active component q of level l
+    void append_component(int l, const I3 &q, std::vector<int64_t> &out) const
+    {
+        const auto it = first[l].find(key3(q));
+        const int64_t m = nmodes(q);
+        for (int64_t i = 0; i < m; ++i) out.push_back(it->second + i);
+    }
+
+    static std::array<I3, 27> closure(const I3 &c)
+    {
+        std::array<I3, 27> out;
+        int t = 0;
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) out[t++] = {2 * c[0] + i, 2 * c[1] + j, 2 * c[2] + k};
+        return out;
+    }
+
+    void full_block(int L, const I3 &c, std::vector<int64_t> &out) const
+    {
+        for (int l = 0; l <= L; ++l) {
+            const I3 A = {c[0] >> (L - l), c[1] >> (L - l), c[2] >> (L - l)};
+            for (const I3 &q : closure(A))
+                if (active(l, q)) append_component(l, q, out);
+        }
+    }
+
+    void truncated_block(int L, const I3 &c, std::vector<int64_t> &out) const
+    {
+        for (const I3 &q : closure(c))
+            if (active(L, q)) append_component(L, q, out);
+        for (int cx : {0, 2})
+            for (int cy : {0, 2})
+                for (int cz : {0, 2}) {
+                    const I3 q = {2 * c[0] + cx, 2 * c[1] + cy, 2 * c[2] + cz};
+                    if (active(L, q)) continue;
+                    for (int l = L - 1; l >= 0; --l) {
+                        const int s = 1 << (L - l);
+                        if (q[0] % (2 * s) || q[1] % (2 * s) || q[2] % (2 * s)) break;  // not a vertex of level l
+                        const I3 ql = {q[0] / s, q[1] / s, q[2] / s};
+                        if (active(l, ql)) {
+                            out.push_back(first[l].find(key3(ql))->second);
+                            break;
+                        }
+                    }
+                }
+    }
+
+    void build(const std::vector<std::array<double, 4>> &sph, int k)
+    {
+        std::unordered_set<uint64_t> base;
+        for (int z = 0; z < n[2]; ++z)
+            for (int y = 0; y < n[1]; ++y)
+                for (int x = 0; x < n[0]; ++x) base.insert(key3({x, y, z}));
+        cells.push_back(base);
+        for (int l = 0; l < k; ++l) {
+            std::unordered_set<uint64_t> R, next;
+            double h[3];
+            for (int a = 0; a < 3; ++a) h[a] = (hi[a] - lo[a]) / (double)(n[a] << l);
+            for (uint64_t key : cells[l]) {
+                const I3 c = {(int)(key & 0x1fffff), (int)((key >> 21) & 0x1fffff), (int)(key >> 42)};
+                double blo[3], bhi[3];
+                for (int a = 0; a < 3; ++a) {
+                    blo[a] = lo[a] + c[a] * h[a];
+                    bhi[a] = lo[a] + (c[a] + 1) * h[a];
+                }
+                if (!box_cut(sph, blo, bhi)) continue;
+                R.insert(key);
+                for (int i = 0; i < 8; ++i) next.insert(key3({2 * c[0] + (i & 1), 2 * c[1] + ((i >> 1) & 1), 2 * c[2] + (i >> 2)}));
+            }
+            refined.push_back(R);
+            if (R.empty()) break;
+            cells.push_back(next);
+        }
+        while (refined.size() < cells.size()) refined.emplace_back();
+        levels = (int)cells.size();
+        // leaves, by level and then (x, y, z) lexicographically
+        for (int l = 0; l < levels; ++l) {
+            std::vector<I3> lv;
+            for (uint64_t key : cells[l])
+                if (!refined[l].count(key)) lv.push_back({(int)(key & 0x1fffff), (int)((key >> 21) & 0x1fffff), (int)(key >> 42)});
+            std::sort(lv.begin(), lv.end());
+            for (const I3 &c : lv) leaves.push_back({l, c});
+        }
+        // functions, level by level, components sorted by (z, y, x)
+        first.resize(levels);
+        for (int l = 0; l < levels; ++l) {
+            std::unordered_set<uint64_t> seen;
+            std::vector<I3> comps;
+            for (uint64_t key : cells[l]) {
+                const I3 c = {(int)(key & 0x1fffff), (int)((key >> 21) & 0x1fffff), (int)(key >> 42)};
+                for (const I3 &q : closure(c))
+                    if (seen.insert(key3(q)).second) comps.push_back(q);
+            }
+            std::sort(comps.begin(), comps.end(), [](const I3 &a, const I3 &b) {
+                return std::make_tuple(a[2], a[1], a[0]) < std::make_tuple(b[2], b[1], b[0]);
+            });
+            for (const I3 &q : comps) {
+                if (!active(l, q)) continue;
+                first[l][key3(q)] = (int64_t)f_level.size();
+                int odd[3], no = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (q[a] & 1) odd[no++] = a;
+                const int64_t m = nmodes(q);
+                for (int64_t i = 0; i < m; ++i) {
+                    I3 mode = {0, 0, 0};
+                    int64_t r = i;
+                    for (int t = no - 1; t >= 0; --t) {  // lowest odd axis slowest
+                        mode[odd[t]] = 2 + (int)(r % (p - 1));
+                        r /= p - 1;
+                    }
+                    f_level.push_back(l);
+                    f_comp.push_back(q);
+                    f_mode.push_back(mode);
+                }
+                // trunk space: the bubble indices of a face or cell sum to at most p
+                if (no <= 1) {
+                    n_trunk += m;
+                } else {
+                    for (int64_t i = 0; i < m; ++i) {
+                        int64_t r = i, sum = 0;
+                        for (int t = 0; t < no; ++t) {
+                            sum += 2 + r % (p - 1);
+                            r /= p - 1;
+                        }
+                        if (sum <= p) ++n_trunk;
+                    }
+                }
+            }
+        }
+        // block overlap and sizes over all leaves
+        std::vector<int> cf(f_level.size(), 0), ct(f_level.size(), 0);
+        std::vector<int64_t> b;
+        for (const auto &lf : leaves) {
+            b.clear();
+            full_block(lf.first, lf.second, b);
+            maxb_full = std::max(maxb_full, (int)b.size());
+            for (int64_t f : b) ++cf[f];
+            b.clear();
+            truncated_block(lf.first, lf.second, b);
+            maxb_trunc = std::max(maxb_trunc, (int)b.size());
+            for (int64_t f : b) ++ct[f];
+        }
+        for (size_t f = 0; f < cf.size(); ++f) {
+            nmax_full = std::max(nmax_full, cf[f]);
+            nmax_trunc = std::max(nmax_trunc, ct[f]);
+        }
+    }
+
+    // 1D factor of function f along axis a on leaf (L, c), as coefficients in the leaf's 1D basis
+    bool restriction(int64_t leaf, int64_t f, double *coef) const
+    {
+        const int L = leaves[leaf].first;
+        const I3 &c = leaves[leaf].second;
+        const int l = f_level[f];
+        if (l > L) return false;
+        const int s = 1 << (L - l);
+        const I3 A = {c[0] >> (L - l), c[1] >> (L - l), c[2] >> (L - l)};
+        const I3 &q = f_comp[f];
+        for (int a = 0; a < 3; ++a) {  // supported on the leaf: q in the closure of the ancestor
+            if (q[a] < 2 * A[a] || q[a] > 2 * A[a] + 2) return false;
+        }
+        const int np = p + 1;
+        for (int a = 0; a < 3; ++a) {
+            const int off = c[a] - A[a] * s;
+            // collocation at p + 1 equispaced leaf points: V coef = g(xi(t))
+            double V[5][6];
+            for (int k = 0; k < np; ++k) {
+                const double t = -1.0 + 2.0 * k / p;
+                shape1d(p, t, V[k]);
+                double g[5];
+                shape1d(p, -1.0 + (2 * off + 1 + t) / s, g);
+                const int which = (q[a] & 1) ? f_mode[f][a] : (q[a] / 2 == A[a] ? 0 : 1);
+                V[k][np] = g[which];
+            }
+            for (int col = 0; col < np; ++col) {  // Gaussian elimination with partial pivoting
+                int piv = col;
+                for (int r = col + 1; r < np; ++r)
+                    if (std::fabs(V[r][col]) > std::fabs(V[piv][col])) piv = r;
+                for (int j = 0; j <= np; ++j) std::swap(V[col][j], V[piv][j]);
+                for (int r = 0; r < np; ++r) {
+                    if (r == col) continue;
+                    const double m = V[r][col] / V[col][col];
+                    for (int j = col; j <= np; ++j) V[r][j] -= m * V[col][j];
+                }
+            }
+            for (int j = 0; j < np; ++j) coef[a * np + j] = V[j][np] / V[j][j];
+        }
+        return true;
+    }
+};
+
+extern "C" {
+
+fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p, int k, fcm_mlhp **out)
+{
+    if (!out) return FCM_EINVAL;
+    *out = nullptr;
+    if (!grid || !geom || p < 1 || p > 4 || k < 0 || k > 10 || geom->kind != 0 || geom->nsph < 0 ||
+        (geom->nsph > 0 && !geom->sph))
+        return FCM_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (grid->n[a] < 1 || ((int64_t)grid->n[a] << k) >= (1 << 20) || !(grid->hi[a] > grid->lo[a])) return FCM_EINVAL;
+    }
+    fcm_mlhp *h = new (std::nothrow) fcm_mlhp;
+    if (!h) return FCM_ENOMEM;
+    try {
+        for (int a = 0; a < 3; ++a) {
+            h->n[a] = grid->n[a];
+            h->lo[a] = grid->lo[a];
+            h->hi[a] = grid->hi[a];
+        }
+        h->p = p;
+        std::vector<std::array<double, 4>> sph(geom->nsph);
+        for (int i = 0; i < geom->nsph; ++i)
+            for (int j = 0; j < 4; ++j) sph[i][j] = geom->sph[4 * i + j];
+        h->build(sph, k);
+    } catch (const std::bad_alloc &) {
+        delete h;
+        return FCM_ENOMEM;
+    }
+    *out = h;
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_get_info(const fcm_mlhp *h, fcm_mlhp_info *info)
+{
+    if (!h || !info) return FCM_EINVAL;
+    info->levels = h->levels;
+    info->n_leaves = (int64_t)h->leaves.size();
+    info->n_functions = (int64_t)h->f_level.size();
+    info->n_functions_trunk = h->n_trunk;
+    info->n_max_full = h->nmax_full;
+    info->n_max_truncated = h->nmax_trunc;
+    info->max_block_full = h->maxb_full;
+    info->max_block_truncated = h->maxb_trunc;
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_leaf(const fcm_mlhp *h, int64_t leaf, int *level, int cell[3])
+{
+    if (!h || !level || !cell || leaf < 0 || leaf >= (int64_t)h->leaves.size()) return FCM_EINVAL;
+    *level = h->leaves[leaf].first;
+    for (int a = 0; a < 3; ++a) cell[a] = h->leaves[leaf].second[a];
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_function(const fcm_mlhp *h, int64_t f, int *level, int comp[3], int mode[3])
+{
+    if (!h || !level || !comp || !mode || f < 0 || f >= (int64_t)h->f_level.size()) return FCM_EINVAL;
+    *level = h->f_level[f];
+    for (int a = 0; a < 3; ++a) {
+        comp[a] = h->f_comp[f][a];
+        mode[a] = h->f_mode[f][a];
+    }
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_block(const fcm_mlhp *h, int64_t leaf, int kind, int64_t *fids, int cap, int *count)
+{
+    if (!h || !count || leaf < 0 || leaf >= (int64_t)h->leaves.size() || (kind != 0 && kind != 1) || cap < 0 ||
+        (cap > 0 && !fids))
+        return FCM_EINVAL;
+    std::vector<int64_t> b;
+    try {
+        if (kind == 0) h->full_block(h->leaves[leaf].first, h->leaves[leaf].second, b);
+        else h->truncated_block(h->leaves[leaf].first, h->leaves[leaf].second, b);
+    } catch (const std::bad_alloc &) {
+        return FCM_ENOMEM;
+    }
+    *count = (int)b.size();
+    if ((int)b.size() > cap) return FCM_EINVAL;
+    std::copy(b.begin(), b.end(), fids);
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_restriction(const fcm_mlhp *h, int64_t leaf, int64_t f, double *coef)
+{
+    if (!h || !coef || leaf < 0 || leaf >= (int64_t)h->leaves.size() || f < 0 || f >= (int64_t)h->f_level.size())
+        return FCM_EINVAL;
+    return h->restriction(leaf, f, coef) ? FCM_OK : FCM_EINVAL;
+}
+
+void fcm_mlhp_destroy(fcm_mlhp *h) { delete h; }
+
+}  // extern "C"

@@ -25,7 +25,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
-            "fcm_fpcg_set_stall_window")
+            "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
+            "fcm_mlhp_block", "fcm_mlhp_restriction", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -76,6 +77,12 @@ class SolveInfo(ctypes.Structure):
                 ("fallback", ctypes.c_int)]
 
 
+class MLHPInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("n_leaves", ctypes.c_int64), ("n_functions", ctypes.c_int64),
+                ("n_functions_trunk", ctypes.c_int64), ("n_max_full", ctypes.c_int), ("n_max_truncated", ctypes.c_int),
+                ("max_block_full", ctypes.c_int), ("max_block_truncated", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -104,8 +111,18 @@ def load(path: str = LIB_PATH):
     L.fcm_last_error.argtypes = [P]
     L.fcm_last_error.restype = ctypes.c_char_p
     L.fcm_destroy.argtypes = [P]
+    i64 = ctypes.c_int64
+    L.fcm_mlhp_create.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Geometry), ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(P)]
+    L.fcm_mlhp_get_info.argtypes = [P, ctypes.POINTER(MLHPInfo)]
+    L.fcm_mlhp_leaf.argtypes = [P, i64, ip, ip]
+    L.fcm_mlhp_function.argtypes = [P, i64, ip, ip, ip]
+    L.fcm_mlhp_block.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int, ip]
+    L.fcm_mlhp_restriction.argtypes = [P, i64, i64, dp]
+    L.fcm_mlhp_destroy.argtypes = [P]
+    L.fcm_mlhp_destroy.restype = None
     for f in EXPORTED:
-        if f not in ("fcm_last_error", "fcm_destroy", "fcm_unet_destroy"):
+        if f not in ("fcm_last_error", "fcm_destroy", "fcm_unet_destroy", "fcm_mlhp_destroy"):
             getattr(L, f).restype = ctypes.c_int
     L.fcm_destroy.restype = None
     _lib = L
@@ -413,3 +430,76 @@ Solver.coarse_prolong = _solver_coarse_prolong
 Solver.coarse_apply = _solver_coarse_apply
 Solver.fpcg_solve = _solver_fpcg_solve
 Solver.fpcg_solve_host = _solver_fpcg_solve_host
+
+
+# ----------------------------------------------------------------------------------------------
+# Multi-level hp overlays: the host-side plan of the hierarchy, its basis and its leaf blocks.
+# ----------------------------------------------------------------------------------------------
+class MLHPPlan:
+    """fcm_mlhp plan: base grid n on [lo, hi] refined k times toward the surfaces of `spheres`
+    (rows cx, cy, cz, r), basis order p.  Host memory only; no device is needed."""
+
+    def __init__(self, n, lo, hi, spheres, p, k):
+        L = load()
+        g = Grid()
+        g.n[:] = list(n)
+        g.lo[:] = list(lo)
+        g.hi[:] = list(hi)
+        geo = Geometry()
+        geo.kind = 0
+        self._sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+        geo.nsph = self._sph.shape[0]
+        geo.sph = self._sph.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.p = p
+        self.h = ctypes.c_void_p()
+        st = L.fcm_mlhp_create(ctypes.byref(g), ctypes.byref(geo), p, k, ctypes.byref(self.h))
+        if st != FCM_OK:
+            raise FcmError(st, "fcm_mlhp_create")
+        inf = MLHPInfo()
+        self._check(L.fcm_mlhp_get_info(self.h, ctypes.byref(inf)))
+        self.info = {k2: getattr(inf, k2) for k2, _ in MLHPInfo._fields_}
+
+    @staticmethod
+    def _check(st):
+        if st != FCM_OK:
+            raise FcmError(st, "fcm_mlhp")
+
+    def leaf(self, i):
+        lv = ctypes.c_int()
+        c = (ctypes.c_int * 3)()
+        self._check(load().fcm_mlhp_leaf(self.h, i, ctypes.byref(lv), c))
+        return lv.value, tuple(c)
+
+    def function(self, f):
+        lv = ctypes.c_int()
+        q = (ctypes.c_int * 3)()
+        m = (ctypes.c_int * 3)()
+        self._check(load().fcm_mlhp_function(self.h, f, ctypes.byref(lv), q, m))
+        return lv.value, tuple(q), tuple(m)
+
+    def block(self, leaf, kind):
+        """kind "full" or "truncated": the scalar functions of the leaf's block."""
+        cnt = ctypes.c_int()
+        k = {"full": 0, "truncated": 1}[kind]
+        load().fcm_mlhp_block(self.h, leaf, k, None, 0, ctypes.byref(cnt))
+        out = np.zeros(max(cnt.value, 1), dtype=np.int64)
+        self._check(load().fcm_mlhp_block(self.h, leaf, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          cnt.value, ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def restriction(self, leaf, f):
+        """(3, p+1) coefficients of function f on the leaf in the leaf's basis (N0, N1, phi_2..phi_p)."""
+        c = np.zeros(3 * (self.p + 1))
+        self._check(load().fcm_mlhp_restriction(self.h, leaf, f, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return c.reshape(3, self.p + 1)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().fcm_mlhp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

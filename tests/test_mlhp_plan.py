@@ -1,0 +1,91 @@
+"""The library's multi-level hp plan (host side of Sec. 2.2 / Sec. 3.2) against the multi-level oracle.
+
+The plan is host memory only, so these run without a GPU: DOF counts against the paper's table,
+and the hierarchy, the basis, every leaf's full and truncated block and the restriction of functions
+to leaves against `oracle/mlhp_oracle.py`, element by element.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlhp_oracle as M
+
+fcm = pytest.importorskip("paper_1809_00828_gb300.fcm")
+if not os.path.exists(fcm.LIB_PATH):
+    pytest.skip("libfcm.so is not built", allow_module_level=True)
+
+CASES = [
+    ((8, 8, 8), [(0.5, 0.5, 0.5, 0.01)], 3, 2),            # the Sec. 5.1 cube, two levels
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 3),             # a cavity that cuts many cells per level
+    ((3, 2, 4), [(0.2, 0.3, 0.4, 0.25), (0.9, 0.1, 0.7, 0.3)], 4, 2),  # odd grid, two spheres, p = 4
+    ((2, 2, 2), [(0.0, 0.0, 0.0, 0.3)], 1, 3),             # refinement into a domain corner, p = 1
+]
+
+
+def test_paper_dof_table_from_the_library_plan():
+    rows = [line.split() for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec5_1_dofs.txt"))
+            if line.strip() and not line.startswith("#")]
+    for k, dofs in ((int(a), int(b)) for a, b in rows):
+        P = fcm.MLHPPlan((8, 8, 8), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.01)], 3, k)
+        assert 3 * P.info["n_functions_trunk"] == dofs
+        assert P.info["n_max_truncated"] == 8
+        P.close()
+
+
+@pytest.mark.parametrize("n,spheres,p,k", CASES)
+def test_plan_matches_the_oracle_hierarchy_basis_and_blocks(n, spheres, p, k):
+    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k)
+    H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), spheres, k)
+    B = M.Basis(H, p)
+    assert P.info["levels"] == H.levels
+    assert P.info["n_leaves"] == len(H.leaves)
+    assert [P.leaf(i) for i in range(len(H.leaves))] == [(l, tuple(c)) for l, c in H.leaves]
+    assert P.info["n_functions"] == len(B.funcs)
+    assert [P.function(f) for f in range(len(B.funcs))] == [(l, tuple(q), tuple(m)) for l, q, m in B.funcs]
+    assert 3 * P.info["n_functions_trunk"] == M.count_dofs(H, p, "trunk")
+    for i, (L, c) in enumerate(H.leaves):
+        assert P.block(i, "full").tolist() == B.leaf_functions(L, c)
+        assert P.block(i, "truncated").tolist() == B.truncated_functions(L, c)
+    assert P.info["n_max_full"] == B.overlap("full")
+    assert P.info["n_max_truncated"] == B.overlap("truncated") <= 8
+    P.close()
+
+
+@pytest.mark.parametrize("n,spheres,p,k", CASES[1:])
+def test_restriction_reproduces_the_function_on_the_leaf(n, spheres, p, k):
+    # fcm_mlhp_restriction: the tensor product of the 1D coefficients in the leaf's own basis must give
+    # the values the oracle evaluates through the leaf's ancestors, at random points of the leaf.
+    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k)
+    H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), spheres, k)
+    B = M.Basis(H, p)
+    rng = np.random.default_rng(4)
+    t = rng.uniform(-1, 1, (12, 3))
+    leaves = [i for i, (L, _) in enumerate(H.leaves) if L == H.levels - 1][:6] + list(range(3))
+    for i in leaves:
+        L, c = H.leaves[i]
+        fids = B.leaf_functions(L, c)
+        ref, _ = B.eval_on_leaf(L, c, fids, t)
+        for r, f in enumerate(fids):
+            coef = P.restriction(i, f)
+            val = np.ones(len(t))
+            for a in range(3):
+                F, _ = M.shape1d(p, t[:, a])
+                val *= coef[a] @ F
+            assert np.abs(val - ref[r]).max() < 1e-13
+    # a function not supported on the leaf is refused
+    L, c = H.leaves[0]
+    outside = sorted(set(range(len(B.funcs))) - set(B.leaf_functions(L, c)))
+    with pytest.raises(fcm.FcmError):
+        P.restriction(0, outside[0])
+    P.close()
+
+
+def test_plan_rejects_bad_arguments():
+    with pytest.raises(fcm.FcmError):
+        fcm.MLHPPlan((2, 2, 2), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 5, 1)
+    with pytest.raises(fcm.FcmError):
+        fcm.MLHPPlan((0, 2, 2), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, 1)
+    with pytest.raises(fcm.FcmError):
+        fcm.MLHPPlan((2, 2, 2), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, -1)
