@@ -4,7 +4,6 @@ The plan is host memory only, so these run without a GPU: DOF counts against the
 and the hierarchy, the basis, every leaf's full and truncated block and the restriction of functions
 to leaves against `oracle/mlhp_oracle.py`, element by element.
 """
-import itertools
 import os
 
 import numpy as np
@@ -89,3 +88,41 @@ def test_plan_rejects_bad_arguments():
         fcm.MLHPPlan((0, 2, 2), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, 1)
     with pytest.raises(fcm.FcmError):
         fcm.MLHPPlan((2, 2, 2), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, -1)
+
+
+def test_leaf_stiffness_is_the_standard_cell_matrix_through_the_restriction():
+    # The multi-level path's K apply per leaf: gather the leaf's functions, map them with the plan's
+    # restriction C onto the leaf's own basis, apply the standard element matrix of a cell of the leaf's
+    # size (the uniform-grid C oracle's, cut cells included), map back.  C K_cell C^T must be the
+    # multi-level oracle's leaf matrix.
+    from oracle import oracle as O
+    from paper_1809_00828_gb300 import inputs as I
+    p, k, depth, alpha = 2, 2, 2, 1e-6
+    sph = np.array([[0.5, 0.5, 0.5, 0.1]])
+    P = fcm.MLHPPlan((4, 4, 4), (0, 0, 0), (1, 1, 1), sph, p, k)
+    H = M.refine_toward_spheres((4, 4, 4), (0, 0, 0), (1, 1, 1), sph, k)
+    Q = M.MLProblem(H, p, sph, alpha=alpha, depth=depth)
+    g = I.Geometry(I.GEOM_SPHERE_VOIDS, spheres=sph, octree_depth=depth)
+    order = [0] + list(range(2, p + 1)) + [1]          # plan's (N0, N1, phi_2..) -> lattice order within a cell
+    descs = {}
+    checked = cut = 0
+    for i, (L, c) in enumerate(H.leaves):
+        if Q.eta[(L, c)] == 0.0 or (i % 7 and L < H.levels - 1):
+            continue
+        if L not in descs:
+            descs[L] = O.make_desc([4 << L] * 3, p, alpha, g)
+        Kc, eta = O.cell_matrix(descs[L][0], c)
+        assert abs(eta - Q.eta[(L, c)]) < 1e-13
+        fids = P.block(i, "full")
+        C = np.zeros((len(fids), (p + 1) ** 3))
+        for r, f in enumerate(fids):
+            cf = P.restriction(i, int(f))[:, order]
+            C[r] = np.einsum("z,y,x->zyx", cf[2], cf[1], cf[0]).reshape(-1)
+        C3 = np.kron(C, np.eye(3))
+        Kml = C3 @ Kc @ C3.T
+        _, Kref = Q.leaf_matrix(L, c)
+        assert np.abs(Kml - Kref).max() <= 1e-12 * np.abs(Kref).max()
+        checked += 1
+        cut += 0.0 < eta < 1.0
+    assert checked >= 20 and cut >= 5
+    P.close()
