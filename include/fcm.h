@@ -287,8 +287,8 @@ fcm_status fcm_coarse_apply(fcm_ctx *ctx, const float *x_cells_dev, float *y_cel
  * CG on K_H (coarse_iters = 0: the prediction alone; net == NULL needs
  * coarse_iters >= 1).  Since z depends nonlinearly on r, every new direction
  * is K-orthogonalised against the previous four (truncated flexible CG,
- * FCG(4), Notay 2000).  Convergence is judged by the plain Schwarz residual
- * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the judged residual grows
+ * FCG(4), Notay 2000).  Convergence is tested on the plain Schwarz residual
+ * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the stopping residual grows
  * 100-fold over its best value, has not halved within the stall window
  * (100 iterations unless set by fcm_fpcg_set_stall_window), or a
  * scalar breaks down, the solve falls back to plain Schwarz-PCG on the
@@ -300,8 +300,8 @@ fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, int coarse_
                           double tol, int maxit, double *u_dev, int *iterations, double *final_relres);
 
 /* Stall window of fcm_fpcg_solve: the flexible phase gives way to plain
- * Schwarz-PCG when the judged residual has not halved within this many
- * iterations (default 100).  The judged residual of CG is not monotone, so on
+ * Schwarz-PCG when the stopping residual has not halved within this many
+ * iterations (default 100).  The stopping residual of CG is not monotone, so on
  * slowly converging problems a longer window keeps the coarse correction in
  * use through plateaus.  Returns FCM_EINVAL for window < 1. */
 fcm_status fcm_fpcg_set_stall_window(fcm_ctx *ctx, int window);

@@ -13,9 +13,9 @@
 // refined by a few coarse CG steps (or those steps from zero without a
 // network).  z depends nonlinearly on r, so each new search direction is
 // K-orthogonalised explicitly against the last four (truncated flexible CG,
-// FCG(4), Notay, SIAM J. Sci. Comput. 22, 2000).  Convergence is judged on
+// FCG(4), Notay, SIAM J. Sci. Comput. 22, 2000).  Convergence is tested on
 // ||S r|| / ||S b|| (Sec. 5 Eq. (14)) with the plain Schwarz part, so the
-// judge is the same as for plain PCG.
+// stopping test is the same as for plain PCG.
 //
 // The iteration runs on the device: every scalar (alpha, the
 // orthogonalisation coefficients, the convergence and stall tests) is
@@ -42,7 +42,7 @@ constexpr int kFcgChunk = 4;   // iterations per captured graph
 struct FcgScalars {
     double pq[kM];     // p_j . K p_j, by ring slot
     double beta[kM];   // z . K p_j / pq_j for the j-th previous direction
-    double alpha, judge0, rel, best, mark, tol, sigma;
+    double alpha, sb_norm, rel, best, mark, tol, sigma;
     int it, maxit, mark_it, window, stop, status, fallback, pad;
 };
 
@@ -182,7 +182,7 @@ __device__ bool grid_sums(double (&v)[K], double *partial, unsigned *counter)
     return true;
 }
 
-// judge0 = ||S b||; resets the iteration state
+// sb_norm = ||S b||; resets the iteration state
 __global__ void __launch_bounds__(RT) fk_first_kernel(const double *zS, int64_t n, double *partial, unsigned *counter,
                                                        FcgScalars *F)
 {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(RT) fk_first_kernel(const double *zS, int64_t 
     for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) v[0] = fma(zS[i], zS[i], v[0]);
     if (!grid_sums<1>(v, partial, counter) || threadIdx.x) return;
     const double j0 = sqrt(v[0]);
-    F->judge0 = j0;
+    F->sb_norm = j0;
     F->it = 0;
     F->rel = 1.0;
     F->best = 1.0;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(RT) fk_xr_kernel(double *x, double *r, const d
     }
 }
 
-// judged residual ||S r|| / ||S b|| (Eq. (14)); convergence, growth, stall and iteration-limit tests
+// stopping residual ||S r|| / ||S b|| (Eq. (14)); convergence, growth, stall and iteration-limit tests
 __global__ void __launch_bounds__(RT) fk_conv_kernel(const double *zS, int64_t n, double *partial, unsigned *counter,
                                                       FcgScalars *F)
 {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(RT) fk_conv_kernel(const double *zS, int64_t n
     if (!grid_sums<1>(v, partial, counter) || threadIdx.x) return;
     const int it = F->it + 1;
     F->it = it;
-    const double rel = sqrt(v[0]) / F->judge0;
+    const double rel = sqrt(v[0]) / F->sb_norm;
     F->rel = rel;
     if (!isfinite(rel)) {
         F->fallback = 1;
@@ -632,12 +632,12 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     }
     const int it = h.it;
     const bool fallback = h.fallback != 0;
-    const double judge0 = h.judge0;
+    const double sb_norm = h.sb_norm;
     double rel = h.rel;
     int total = it;
     fcm_status status = (fcm_status)h.status;
     if (fallback && it < maxit) {
-        // plain Schwarz-PCG on K dx = b - K x, to the same absolute judged residual
+        // plain Schwarz-PCG on K dx = b - K x, to the same absolute stopping residual
         double *res = F->c, *keep = F->ring;
         ctx_apply_K_flag(C, x, q, nullptr);
         sub_kernel<<<nblk(n), 256, 0, st>>>(res, b, q, n);
@@ -646,13 +646,13 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
         const double jr = std::sqrt(h2[0]);
         CO_CUDA(C, cudaMemcpyAsync(keep, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         fcm_solve_info inner = {};
-        const double tol2 = jr > 0.0 ? std::min(1.0, tol * judge0 / jr) : 1.0;
+        const double tol2 = jr > 0.0 ? std::min(1.0, tol * sb_norm / jr) : 1.0;
         // the plain solve copies its right-hand side first, so `res` also receives dx
         fcm_status s2 = ctx_solve_one(C, res, tol2, maxit - it, res, inner);
         if (s2 == FCM_EINVAL || s2 == FCM_ECUDA || s2 == FCM_ENOMEM) return s2;
         add_kernel<<<nblk(n), 256, 0, st>>>(x, keep, res, n);
         total += inner.iterations;
-        rel = inner.relres * (jr / judge0);
+        rel = inner.relres * (jr / sb_norm);
         status = (fcm_status)inner.status;
         // the plain solve left b = masked res; restore the caller's b for the true residual
         launch_mask_copy(rhs, b, C->d_mask, n, st);

@@ -419,7 +419,7 @@ def _solver_fpcg_solve_host(self, net, gamma, b_host, tol, maxit=100000, out=Non
 
 
 def _solver_set_stall_window(self, window):
-    """Iterations without halving of the judged residual after which fpcg_solve falls back."""
+    """Iterations without halving of the stopping residual after which fpcg_solve falls back."""
     _bind_unet(load())
     self._check(load().fcm_fpcg_set_stall_window(self.ctx, int(window)))
 
