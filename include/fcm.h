@@ -377,6 +377,21 @@ fcm_status fcm_mlhp_block(const fcm_mlhp *plan, int64_t leaf, int kind, int64_t 
  * product over the axes a of sum_j coef[a (p+1) + j] b_j(t_a), with b = (N0, N1, phi_2 .. phi_p) the
  * leaf's own 1D shape functions in its local coordinate t_a in [-1, 1]. */
 fcm_status fcm_mlhp_restriction(const fcm_mlhp *plan, int64_t leaf, int64_t f, double *coef);
+/* Assemble the elasticity system of Eq. (1) on the hierarchy (host memory), with the plan's spheres as
+ * voids (alpha inside them) and their octree_depth, material and conditions from bc (FCM_BC_* as for
+ * fcm_setup; Dirichlet DOFs are removed: a function is fixed in component a when its component lies on the
+ * plane of that condition), and the traction bc->traction on the top face z = hi[2].  Each leaf with eta > 0
+ * contributes C K_cell C^T, with K_cell the cell matrix of the leaf's box (the same moment quadrature as
+ * fcm_setup, octree depth counted from the leaf) and C the restriction above; a function is kept when some
+ * leaf in its support has eta > 0.  FCM_EINVAL on bad arguments (alpha in (0, 1]). */
+fcm_status fcm_mlhp_assemble(fcm_mlhp *plan, double alpha, const fcm_bc *bc);
+/* Sizes of the assembled system: free DOFs and CSR nonzeros.  FCM_ESTATE before fcm_mlhp_assemble. */
+fcm_status fcm_mlhp_system_size(const fcm_mlhp *plan, int64_t *n_free, int64_t *nnz);
+/* Copy the assembled system to caller-owned host arrays (any may be NULL): free_dofs[n_free] (3 f + comp,
+ * ascending), the CSR rowptr[n_free + 1], cols[nnz], vals[nnz] over the free DOFs, the load rhs[n_free] and
+ * the volume fraction of every leaf leaf_eta[n_leaves]. */
+fcm_status fcm_mlhp_system(const fcm_mlhp *plan, int64_t *free_dofs, int64_t *rowptr, int64_t *cols, double *vals,
+                           double *rhs, double *leaf_eta);
 void fcm_mlhp_destroy(fcm_mlhp *plan);
 
 /* Message of the last failure on ctx (ctx may be NULL for setup failures). */

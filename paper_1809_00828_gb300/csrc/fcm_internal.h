@@ -65,6 +65,13 @@ void make_sf_tables(const HostProblem &P, SfTables &T);
 std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, int p, double alpha,
                                const fcm_bc &bc, HostProblem &out, int nthreads = 0);
 
+// One cell on the box [clo, chi] with the grid cells' moment quadrature (octree depth counted from the
+// cell): alpha-weighted element matrix K (3 (p+1)^3 square, lattice order), volume fraction eta and, if
+// face != nullptr, the solid-part integrals face[i1 (p+1) + i0] of N_i0 N_i1 over the top face z = chi[2].
+// Voxel images span the domain box [dlo, dhi].
+void box_cell_setup(const fcm_geometry &geom, const double *dlo, const double *dhi, int p, double alpha, double E,
+                    double nu, const double *clo, const double *chi, double *K, double *eta, double *face);
+
 // Gauss-Legendre rule with n points on [-1, 1].
 void gauss_legendre(int n, double *x, double *w);
 

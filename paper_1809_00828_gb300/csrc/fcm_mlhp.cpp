@@ -22,8 +22,13 @@
 // leaves by level, then by (x, y, z) lexicographically; a leaf's full block level by level from 0, the
 // components of the ancestor's closure with x fastest.
 #include "fcm.h"
+#include "fcm_internal.h"
 
 #include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <string>
+#include <thread>
 #include <array>
 #include <cmath>
 #include <cstdint>
@@ -82,6 +87,14 @@ struct fcm_mlhp {
     std::vector<std::unordered_map<uint64_t, int64_t>> first;  // per level: component -> its first function
     int64_t n_trunk = 0;
     int nmax_full = 0, nmax_trunc = 0, maxb_full = 0, maxb_trunc = 0;
+    // geometry of the refinement, kept for the assembly
+    std::vector<double> sph;
+    int depth = 0;
+    // assembled system (fcm_mlhp_assemble): free DOFs 3 f + comp ascending, CSR over them, load
+    bool assembled = false;
+    std::vector<double> leaf_eta;
+    std::vector<int64_t> free_dofs, rowptr, cols;
+    std::vector<double> vals, rhs;
 
     int ext(int l, int a) const { return n[a] << l; }
 
@@ -268,6 +281,146 @@ struct fcm_mlhp {
         }
     }
 
+    // Eq. (1) on the leaves: K = sum over leaves with eta > 0 of C K_cell C^T, C the restriction of the
+    // leaf's functions to its own lattice-ordered basis and K_cell the cell matrix of the leaf's box; the
+    // traction on the top face z = hi[2] the same way.  Returns an error message or "".
+    std::string assemble(double alpha, const fcm_bc &bc)
+    {
+        const int q = p + 1, nl = q * q * q, ne = 3 * nl;
+        fcm_geometry g;
+        std::memset(&g, 0, sizeof g);
+        g.kind = FCM_GEOM_SPHERE_VOIDS;
+        g.nsph = (int)(sph.size() / 4);
+        g.sph = sph.data();
+        g.octree_depth = depth;
+        const int64_t nleaf = (int64_t)leaves.size();
+        leaf_eta.assign(nleaf, 0.0);
+        std::vector<std::vector<double>> Kc(nleaf), face(nleaf);
+        std::atomic<int64_t> next(0);
+        auto work = [&]() {
+            for (int64_t i = next++; i < nleaf; i = next++) {
+                const int L = leaves[i].first;
+                const I3 &c = leaves[i].second;
+                double clo[3], chi[3];
+                for (int a = 0; a < 3; ++a) {
+                    const double h = (hi[a] - lo[a]) / (double)(n[a] << L);
+                    clo[a] = lo[a] + c[a] * h;
+                    chi[a] = clo[a] + h;
+                }
+                const bool top = c[2] == ext(L, 2) - 1;
+                Kc[i].assign((size_t)ne * ne, 0.0);
+                if (top) face[i].assign((size_t)q * q, 0.0);
+                fcm::box_cell_setup(g, lo, hi, p, alpha, bc.E, bc.nu, clo, chi, Kc[i].data(), &leaf_eta[i],
+                                    top ? face[i].data() : nullptr);
+                if (!(leaf_eta[i] > 0.0)) {
+                    std::vector<double>().swap(Kc[i]);
+                    std::vector<double>().swap(face[i]);
+                }
+            }
+        };
+        const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+        work();
+        for (auto &t : pool) t.join();
+        // kept functions (some active leaf in their support) and free DOFs
+        const int64_t nf = (int64_t)f_level.size();
+        std::vector<uint8_t> kept(nf, 0);
+        std::vector<std::vector<int64_t>> blocks(nleaf);
+        for (int64_t i = 0; i < nleaf; ++i) {
+            if (!(leaf_eta[i] > 0.0)) continue;
+            full_block(leaves[i].first, leaves[i].second, blocks[i]);
+            for (int64_t f : blocks[i]) kept[f] = 1;
+        }
+        std::vector<int64_t> pos(3 * nf, -1);
+        free_dofs.clear();
+        for (int64_t f = 0; f < nf; ++f) {
+            if (!kept[f]) continue;
+            for (int a = 0; a < 3; ++a) {
+                bool fixed = false;
+                if (bc.bc == FCM_BC_CLAMP_ZLO) fixed = f_comp[f][2] == 0;
+                if (bc.bc == FCM_BC_ROLLERS) fixed = f_comp[f][a] == 0;
+                if (!fixed) {
+                    pos[3 * f + a] = (int64_t)free_dofs.size();
+                    free_dofs.push_back(3 * f + a);
+                }
+            }
+        }
+        const int64_t nfree = (int64_t)free_dofs.size();
+        // leaf matrices through the restriction, gathered as (row, col, value)
+        std::vector<std::vector<std::pair<int64_t, double>>> rows(nfree);
+        rhs.assign(nfree, 0.0);
+        std::vector<double> coef(3 * q), C, T;
+        for (int64_t i = 0; i < nleaf; ++i) {
+            if (!(leaf_eta[i] > 0.0)) continue;
+            const std::vector<int64_t> &fb = blocks[i];
+            const int m = (int)fb.size();
+            C.assign((size_t)m * nl, 0.0);
+            std::vector<double> ztop(m, 0.0);
+            for (int r = 0; r < m; ++r) {
+                restriction(i, fb[r], coef.data());
+                double cl[3][5];  // lattice order (N0, phi_2 .. phi_p, N1) from (N0, N1, phi_2 .. phi_p)
+                for (int a = 0; a < 3; ++a)
+                    for (int j = 0; j < q; ++j) cl[a][j] = coef[a * q + (j == p ? 1 : (j == 0 ? 0 : j + 1))];
+                for (int iz = 0; iz < q; ++iz)
+                    for (int iy = 0; iy < q; ++iy)
+                        for (int ix = 0; ix < q; ++ix) C[(size_t)r * nl + ix + q * (iy + q * iz)] = cl[0][ix] * cl[1][iy] * cl[2][iz];
+                if (!face[i].empty()) {
+                    double s = 0.0;
+                    for (int iy = 0; iy < q; ++iy)
+                        for (int ix = 0; ix < q; ++ix) s += cl[0][ix] * cl[1][iy] * face[i][iy * q + ix];
+                    ztop[r] = s * cl[2][p];  // only N1 is nonzero on the top face
+                }
+            }
+            // T[(I,a)][(g,b)] = sum_J K_cell[(I,a)][(J,b)] C[g][J]
+            T.assign((size_t)ne * 3 * m, 0.0);
+            for (int I3i = 0; I3i < ne; ++I3i)
+                for (int gI = 0; gI < m; ++gI)
+                    for (int b = 0; b < 3; ++b) {
+                        double s = 0.0;
+                        const double *krow = Kc[i].data() + (size_t)I3i * ne;
+                        const double *cg = C.data() + (size_t)gI * nl;
+                        for (int J = 0; J < nl; ++J) s += krow[3 * J + b] * cg[J];
+                        T[(size_t)I3i * 3 * m + 3 * gI + b] = s;
+                    }
+            for (int fI = 0; fI < m; ++fI)
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t r = pos[3 * fb[fI] + a];
+                    if (r < 0) continue;
+                    if (!face[i].empty()) rhs[r] += bc.traction[a] * ztop[fI];
+                    const double *cf = C.data() + (size_t)fI * nl;
+                    for (int gI = 0; gI < m; ++gI)
+                        for (int b = 0; b < 3; ++b) {
+                            const int64_t col = pos[3 * fb[gI] + b];
+                            if (col < 0) continue;
+                            double s = 0.0;
+                            for (int I = 0; I < nl; ++I) s += cf[I] * T[(size_t)(3 * I + a) * 3 * m + 3 * gI + b];
+                            rows[r].push_back({col, s});
+                        }
+                }
+        }
+        rowptr.assign(nfree + 1, 0);
+        cols.clear();
+        vals.clear();
+        for (int64_t r = 0; r < nfree; ++r) {
+            auto &v = rows[r];
+            std::sort(v.begin(), v.end(), [](const std::pair<int64_t, double> &x, const std::pair<int64_t, double> &y) {
+                return x.first < y.first;
+            });
+            for (size_t k = 0; k < v.size(); ++k) {
+                if (!cols.empty() && (int64_t)cols.size() > rowptr[r] && cols.back() == v[k].first) vals.back() += v[k].second;
+                else {
+                    cols.push_back(v[k].first);
+                    vals.push_back(v[k].second);
+                }
+            }
+            std::vector<std::pair<int64_t, double>>().swap(v);
+            rowptr[r + 1] = (int64_t)cols.size();
+        }
+        assembled = true;
+        return std::string();
+    }
+
     // 1D factor of function f along axis a on leaf (L, c), as coefficients in the leaf's 1D basis
     bool restriction(int64_t leaf, int64_t f, double *coef) const
     {
@@ -318,7 +471,7 @@ fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p
     if (!out) return FCM_EINVAL;
     *out = nullptr;
     if (!grid || !geom || p < 1 || p > 4 || k < 0 || k > 10 || geom->kind != 0 || geom->nsph < 0 ||
-        (geom->nsph > 0 && !geom->sph))
+        (geom->nsph > 0 && !geom->sph) || geom->octree_depth < 0 || geom->octree_depth > 12)
         return FCM_EINVAL;
     for (int a = 0; a < 3; ++a) {
         if (grid->n[a] < 1 || ((int64_t)grid->n[a] << k) >= (1 << 20) || !(grid->hi[a] > grid->lo[a])) return FCM_EINVAL;
@@ -335,6 +488,8 @@ fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p
         std::vector<std::array<double, 4>> sph(geom->nsph);
         for (int i = 0; i < geom->nsph; ++i)
             for (int j = 0; j < 4; ++j) sph[i][j] = geom->sph[4 * i + j];
+        h->sph.assign(geom->sph, geom->sph + 4 * (size_t)geom->nsph);
+        h->depth = geom->octree_depth;
         h->build(sph, k);
     } catch (const std::bad_alloc &) {
         delete h;
@@ -400,6 +555,45 @@ fcm_status fcm_mlhp_restriction(const fcm_mlhp *h, int64_t leaf, int64_t f, doub
     if (!h || !coef || leaf < 0 || leaf >= (int64_t)h->leaves.size() || f < 0 || f >= (int64_t)h->f_level.size())
         return FCM_EINVAL;
     return h->restriction(leaf, f, coef) ? FCM_OK : FCM_EINVAL;
+}
+
+fcm_status fcm_mlhp_assemble(fcm_mlhp *h, double alpha, const fcm_bc *bc)
+{
+    if (!h || !bc || !(alpha > 0.0 && alpha <= 1.0) || !(bc->E > 0.0) || !(bc->nu > -1.0 && bc->nu < 0.5) ||
+        bc->bc < FCM_BC_NONE || bc->bc > FCM_BC_ROLLERS)
+        return FCM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(bc->traction[a])) return FCM_EINVAL;
+    try {
+        h->assembled = false;
+        if (!h->assemble(alpha, *bc).empty()) return FCM_EINVAL;
+    } catch (const std::bad_alloc &) {
+        return FCM_ENOMEM;
+    }
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_system_size(const fcm_mlhp *h, int64_t *n_free, int64_t *nnz)
+{
+    if (!h || !n_free || !nnz) return FCM_EINVAL;
+    if (!h->assembled) return FCM_ESTATE;
+    *n_free = (int64_t)h->free_dofs.size();
+    *nnz = (int64_t)h->cols.size();
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_system(const fcm_mlhp *h, int64_t *free_dofs, int64_t *rowptr, int64_t *cols, double *vals,
+                           double *rhs, double *leaf_eta)
+{
+    if (!h) return FCM_EINVAL;
+    if (!h->assembled) return FCM_ESTATE;
+    if (free_dofs) std::copy(h->free_dofs.begin(), h->free_dofs.end(), free_dofs);
+    if (rowptr) std::copy(h->rowptr.begin(), h->rowptr.end(), rowptr);
+    if (cols) std::copy(h->cols.begin(), h->cols.end(), cols);
+    if (vals) std::copy(h->vals.begin(), h->vals.end(), vals);
+    if (rhs) std::copy(h->rhs.begin(), h->rhs.end(), rhs);
+    if (leaf_eta) std::copy(h->leaf_eta.begin(), h->leaf_eta.end(), leaf_eta);
+    return FCM_OK;
 }
 
 void fcm_mlhp_destroy(fcm_mlhp *h) { delete h; }

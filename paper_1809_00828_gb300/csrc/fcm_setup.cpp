@@ -736,3 +736,75 @@ std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, i
 }
 
 }  // namespace fcm
+
+namespace fcm {
+
+// One cell on the box [clo, chi]: its alpha-weighted element matrix (lattice order, 3 (p+1)^3 rows), its
+// volume fraction eta, and, if face != nullptr, the solid-part integrals face[i1 (p+1) + i0] of
+// N_i0(x) N_i1(y) over its top face z = chi[2] (physical area).  The same moment quadrature as the grid's
+// cells, with the octree depth counted from this cell.  Voxel images span the domain box [dlo, dhi].
+void box_cell_setup(const fcm_geometry &geom, const double *dlo, const double *dhi, int p, double alpha, double E,
+                    double nu, const double *clo, const double *chi, double *K, double *eta, double *face)
+{
+    HostProblem P;
+    P.p = p;
+    P.alpha = alpha;
+    P.E = E;
+    P.nu = nu;
+    P.bc = FCM_BC_NONE;
+    for (int a = 0; a < 3; ++a) {
+        P.n[a] = 1;
+        P.lo[a] = clo[a];
+        P.hi[a] = chi[a];
+        P.h[a] = chi[a] - clo[a];
+        P.M[a] = p + 1;
+        P.traction[a] = 0.0;
+    }
+    P.gkind = geom.kind;
+    P.depth = geom.octree_depth;
+    std::memcpy(P.plane, geom.plane, sizeof P.plane);
+    Setup S;
+    S.P = &P;
+    S.geo.kind = geom.kind;
+    S.geo.sph = geom.sph;
+    S.geo.nsph = geom.kind == FCM_GEOM_SPHERE_VOIDS ? geom.nsph : 0;
+    S.geo.vox = geom.vox;
+    for (int a = 0; a < 3; ++a) {
+        S.geo.vdim[a] = geom.vdim[a];
+        S.geo.lo[a] = dlo[a];
+        S.geo.hi[a] = dhi[a];
+    }
+    std::memcpy(S.geo.plane, geom.plane, sizeof S.geo.plane);
+    make_tables(p, S.T);
+    const int L = S.T.L, L3 = L * L * L;
+    std::vector<double> mu(L3, 0.0);
+    if (!S.geo.crossed(clo, chi)) {
+        double ctr[3];
+        for (int a = 0; a < 3; ++a) ctr[a] = 0.5 * (clo[a] + chi[a]);
+        const bool solid = S.geo.solid(ctr);
+        *eta = solid ? 1.0 : 0.0;
+        mu[0] = solid ? 8.0 : 8.0 * alpha;
+    } else {
+        bool any = false;
+        cell_moments_rec(S, clo, clo, chi, 0, mu.data(), any);
+        *eta = mu[0] / 8.0;
+        for (int m = 0; m < L3; ++m) mu[m] *= (1.0 - alpha);
+        mu[0] += 8.0 * alpha;
+    }
+    element_from_moments(S, mu.data(), K);
+    if (face) {
+        std::vector<double> fm(L * L, 0.0);
+        const double flo[2] = {clo[0], clo[1]}, fhi[2] = {chi[0], chi[1]};
+        face_moments_rec(S, clo, flo, fhi, 0, fm.data());
+        const double area = P.h[0] * P.h[1] / 4.0;
+        for (int i1 = 0; i1 <= p; ++i1)
+            for (int i0 = 0; i0 <= p; ++i0) {
+                double s = 0.0;
+                for (int m0 = 0; m0 < L; ++m0)
+                    for (int m1 = 0; m1 < L; ++m1) s += S.T.face[i0][m0] * S.T.face[i1][m1] * fm[m0 * L + m1];
+                face[i1 * (p + 1) + i0] = area * s;
+            }
+    }
+}
+
+}  // namespace fcm

@@ -26,7 +26,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
             "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
-            "fcm_mlhp_block", "fcm_mlhp_restriction", "fcm_mlhp_destroy")
+            "fcm_mlhp_block", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size", "fcm_mlhp_system",
+            "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -119,6 +120,9 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_function.argtypes = [P, i64, ip, ip, ip]
     L.fcm_mlhp_block.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int, ip]
     L.fcm_mlhp_restriction.argtypes = [P, i64, i64, dp]
+    L.fcm_mlhp_assemble.argtypes = [P, ctypes.c_double, ctypes.POINTER(BC)]
+    L.fcm_mlhp_system_size.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.fcm_mlhp_system.argtypes = [P, P, P, P, P, P, P]
     L.fcm_mlhp_destroy.argtypes = [P]
     L.fcm_mlhp_destroy.restype = None
     for f in EXPORTED:
@@ -354,6 +358,28 @@ class UNet:
     def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         _unet_check(load().fcm_unet_adam(self.h, lr, beta1, beta2, eps, step))
 
+    def assemble(self, alpha, bc_kind="clamp", E=1.0, nu=0.3, traction=(0.0, 0.0, -1.0)):
+        """Assemble the system on the host; returns (free_dofs, K as scipy CSR, rhs, leaf_eta)."""
+        import scipy.sparse as sp
+        bc = BC()
+        bc.E, bc.nu = E, nu
+        bc.bc = {"none": -1, "clamp": 0, "roller": 1}[bc_kind]
+        bc.traction[:] = list(traction)
+        L = load()
+        self._check(L.fcm_mlhp_assemble(self.h, alpha, ctypes.byref(bc)))
+        nf, nnz = ctypes.c_int64(), ctypes.c_int64()
+        self._check(L.fcm_mlhp_system_size(self.h, ctypes.byref(nf), ctypes.byref(nnz)))
+        free = np.zeros(nf.value, dtype=np.int64)
+        rowptr = np.zeros(nf.value + 1, dtype=np.int64)
+        cols = np.zeros(nnz.value, dtype=np.int64)
+        vals = np.zeros(nnz.value)
+        rhs = np.zeros(nf.value)
+        eta = np.zeros(self.info["n_leaves"])
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        self._check(L.fcm_mlhp_system(self.h, ptr(free), ptr(rowptr), ptr(cols), ptr(vals), ptr(rhs), ptr(eta)))
+        K = sp.csr_matrix((vals, cols, rowptr), shape=(nf.value, nf.value))
+        return free, K, rhs, eta
+
     def close(self):
         if getattr(self, "h", None) and self.h.value:
             load().fcm_unet_destroy(self.h)
@@ -437,9 +463,10 @@ Solver.fpcg_solve_host = _solver_fpcg_solve_host
 # ----------------------------------------------------------------------------------------------
 class MLHPPlan:
     """fcm_mlhp plan: base grid n on [lo, hi] refined k times toward the surfaces of `spheres`
-    (rows cx, cy, cz, r), basis order p.  Host memory only; no device is needed."""
+    (rows cx, cy, cz, r), basis order p; the spheres are also the voids of `assemble`, integrated with
+    an octree of `octree_depth` levels per leaf.  Host memory only; no device is needed."""
 
-    def __init__(self, n, lo, hi, spheres, p, k):
+    def __init__(self, n, lo, hi, spheres, p, k, octree_depth=3):
         L = load()
         g = Grid()
         g.n[:] = list(n)
@@ -447,6 +474,7 @@ class MLHPPlan:
         g.hi[:] = list(hi)
         geo = Geometry()
         geo.kind = 0
+        geo.octree_depth = octree_depth
         self._sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
         geo.nsph = self._sph.shape[0]
         geo.sph = self._sph.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -492,6 +520,28 @@ class MLHPPlan:
         c = np.zeros(3 * (self.p + 1))
         self._check(load().fcm_mlhp_restriction(self.h, leaf, f, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return c.reshape(3, self.p + 1)
+
+    def assemble(self, alpha, bc_kind="clamp", E=1.0, nu=0.3, traction=(0.0, 0.0, -1.0)):
+        """Assemble the system on the host; returns (free_dofs, K as scipy CSR, rhs, leaf_eta)."""
+        import scipy.sparse as sp
+        bc = BC()
+        bc.E, bc.nu = E, nu
+        bc.bc = {"none": -1, "clamp": 0, "roller": 1}[bc_kind]
+        bc.traction[:] = list(traction)
+        L = load()
+        self._check(L.fcm_mlhp_assemble(self.h, alpha, ctypes.byref(bc)))
+        nf, nnz = ctypes.c_int64(), ctypes.c_int64()
+        self._check(L.fcm_mlhp_system_size(self.h, ctypes.byref(nf), ctypes.byref(nnz)))
+        free = np.zeros(nf.value, dtype=np.int64)
+        rowptr = np.zeros(nf.value + 1, dtype=np.int64)
+        cols = np.zeros(nnz.value, dtype=np.int64)
+        vals = np.zeros(nnz.value)
+        rhs = np.zeros(nf.value)
+        eta = np.zeros(self.info["n_leaves"])
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        self._check(L.fcm_mlhp_system(self.h, ptr(free), ptr(rowptr), ptr(cols), ptr(vals), ptr(rhs), ptr(eta)))
+        K = sp.csr_matrix((vals, cols, rowptr), shape=(nf.value, nf.value))
+        return free, K, rhs, eta
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

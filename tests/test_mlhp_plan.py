@@ -126,3 +126,22 @@ def test_leaf_stiffness_is_the_standard_cell_matrix_through_the_restriction():
         cut += 0.0 < eta < 1.0
     assert checked >= 20 and cut >= 5
     P.close()
+
+
+@pytest.mark.parametrize("n,spheres,p,k,depth,alpha,bc", [
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 2, 2, 1e-6, "clamp"),
+    ((3, 2, 4), [(0.2, 0.3, 0.4, 0.25), (0.9, 0.1, 0.97, 0.3)], 3, 1, 2, 1e-3, "roller"),  # a void through z = 1
+    ((2, 2, 2), [(0.0, 0.0, 0.0, 0.3)], 1, 3, 3, 1e-8, "clamp"),
+])
+def test_assembled_system_matches_the_oracle(n, spheres, p, k, depth, alpha, bc):
+    # fcm_mlhp_assemble (moment quadrature per leaf box, C K_cell C^T, quadtree traction) against the
+    # oracle's point-wise assembly on the same hierarchy: same free DOFs, K and b to rounding.
+    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k, octree_depth=depth)
+    free, K, rhs, eta = P.assemble(alpha, bc)
+    H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), spheres, k)
+    Q = M.MLProblem(H, p, spheres, alpha=alpha, depth=depth, bc=bc)
+    assert np.array_equal(free, Q.free)
+    assert abs(K - Q.K).max() <= 1e-13 * abs(Q.K).max()
+    assert np.abs(rhs - Q.b).max() <= 1e-13 * np.abs(Q.b).max()
+    assert max(abs(eta[i] - Q.eta[lc]) for i, lc in enumerate(H.leaves)) < 1e-13
+    P.close()
