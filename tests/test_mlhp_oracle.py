@@ -228,16 +228,20 @@ def test_span_reading_fills_every_block_but_breaks_the_overlap_bound():
 
 
 def test_truncated_blocks_converge_faster_than_full_blocks_under_refinement():
-    # Sec. 5.1: with full blocks the iteration count grows with the refinement depth much faster than with
-    # truncated blocks.  Cavity r = 0.1 in a 4^3 base grid, p = 2, alpha = 1e-10, k = 0..2.
+    # Sec. 5.1: the cube with a small spherical cavity at its centre, refined toward the cavity's surface.
+    # With full blocks the iteration count grows with the depth k much faster than with truncated blocks.
+    # The paper's set-up scaled to a 4^3 base grid (r / h = 0.08 as for r = 0.01 on 8^3), p = 2,
+    # alpha = 1e-8, k = 0..3.
     its = {}
-    for k in range(3):
-        H = M.refine_toward_spheres((4, 4, 4), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], k)
-        Q = M.MLProblem(H, 2, [(0.5, 0.5, 0.5, 0.1)], alpha=1e-10, depth=2)
+    ball = [(0.5, 0.5, 0.5, 0.02)]
+    for k in range(4):
+        H = M.refine_toward_spheres((4, 4, 4), (0, 0, 0), (1, 1, 1), ball, k)
+        Q = M.MLProblem(H, 2, ball, alpha=1e-8, depth=3)
         for kind in ("full", "truncated"):
             Q.build_blocks(kind)
             its[kind, k] = Q.pcg(tol=1e-8, maxit=3000)[1]
     assert its["full", 0] == its["truncated", 0]               # no overlay: the blocks coincide
-    for k in (1, 2):
+    for k in (1, 2, 3):
         assert its["truncated", k] < its["full", k]
-    assert its["truncated", 2] < 0.75 * its["full", 2]
+    assert its["full", 3] > 2.5 * its["full", 0]
+    assert its["truncated", 3] < 1.6 * its["truncated", 0]

@@ -130,7 +130,7 @@ def test_leaf_stiffness_is_the_standard_cell_matrix_through_the_restriction():
 
 @pytest.mark.parametrize("n,spheres,p,k,depth,alpha,bc", [
     ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 2, 2, 1e-6, "clamp"),
-    ((3, 2, 4), [(0.2, 0.3, 0.4, 0.25), (0.9, 0.1, 0.97, 0.3)], 3, 1, 2, 1e-3, "roller"),  # a void through z = 1
+    ((3, 2, 2), [(0.2, 0.3, 0.4, 0.25), (0.9, 0.1, 0.97, 0.3)], 3, 1, 2, 1e-3, "roller"),  # a void through z = 1
     ((2, 2, 2), [(0.0, 0.0, 0.0, 0.3)], 1, 3, 3, 1e-8, "clamp"),
 ])
 def test_assembled_system_matches_the_oracle(n, spheres, p, k, depth, alpha, bc):
