@@ -373,6 +373,11 @@ fcm_status fcm_mlhp_function(const fcm_mlhp *plan, int64_t f, int *level, int co
 /* Scalar functions of leaf `leaf`'s block (kind 0 full, 1 truncated) into fids[0 .. *count).  *count is
  * always set; FCM_EINVAL (nothing copied) when it exceeds cap. */
 fcm_status fcm_mlhp_block(const fcm_mlhp *plan, int64_t leaf, int kind, int64_t *fids, int cap, int *count);
+/* Colour classes of the leaf blocks (kind 0 full, 1 truncated): colour[n_leaves] such that two leaves of one
+ * colour share no scalar function, so a launch per colour can scatter without atomics.  Greedy in leaf
+ * order.  Truncated blocks take about 13 colours on refined hierarchies (8 on a uniform grid); full blocks
+ * need at least n_max_full colours, and FCM_EINVAL is returned beyond 64. */
+fcm_status fcm_mlhp_colour(const fcm_mlhp *plan, int kind, int *colour, int *n_colours);
 /* Function f restricted to leaf `leaf` (f must be supported there: FCM_EINVAL otherwise) is the tensor
  * product over the axes a of sum_j coef[a (p+1) + j] b_j(t_a), with b = (N0, N1, phi_2 .. phi_p) the
  * leaf's own 1D shape functions in its local coordinate t_a in [-1, 1]. */

@@ -550,6 +550,35 @@ fcm_status fcm_mlhp_block(const fcm_mlhp *h, int64_t leaf, int kind, int64_t *fi
     return FCM_OK;
 }
 
+fcm_status fcm_mlhp_colour(const fcm_mlhp *h, int kind, int *colour, int *n_colours)
+{
+    if (!h || !colour || !n_colours || (kind != 0 && kind != 1)) return FCM_EINVAL;
+    // greedy, leaves in plan order: the lowest colour that no block sharing a function already has
+    std::vector<uint64_t> used;
+    try {
+        used.assign(h->f_level.size(), 0);
+        std::vector<int64_t> b;
+        int nc = 0;
+        for (size_t i = 0; i < h->leaves.size(); ++i) {
+            b.clear();
+            if (kind == 0) h->full_block(h->leaves[i].first, h->leaves[i].second, b);
+            else h->truncated_block(h->leaves[i].first, h->leaves[i].second, b);
+            uint64_t taken = 0;
+            for (int64_t f : b) taken |= used[f];
+            if (taken == ~0ull) return FCM_EINVAL;  // more than 64 colours
+            int c = 0;
+            while (taken >> c & 1ull) ++c;
+            colour[i] = c;
+            nc = std::max(nc, c + 1);
+            for (int64_t f : b) used[f] |= 1ull << c;
+        }
+        *n_colours = nc;
+    } catch (const std::bad_alloc &) {
+        return FCM_ENOMEM;
+    }
+    return FCM_OK;
+}
+
 fcm_status fcm_mlhp_restriction(const fcm_mlhp *h, int64_t leaf, int64_t f, double *coef)
 {
     if (!h || !coef || leaf < 0 || leaf >= (int64_t)h->leaves.size() || f < 0 || f >= (int64_t)h->f_level.size())

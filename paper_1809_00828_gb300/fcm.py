@@ -26,7 +26,7 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
             "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
-            "fcm_mlhp_block", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size", "fcm_mlhp_system",
+            "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size", "fcm_mlhp_system",
             "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_leaf.argtypes = [P, i64, ip, ip]
     L.fcm_mlhp_function.argtypes = [P, i64, ip, ip, ip]
     L.fcm_mlhp_block.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int, ip]
+    L.fcm_mlhp_colour.argtypes = [P, ctypes.c_int, ip, ip]
     L.fcm_mlhp_restriction.argtypes = [P, i64, i64, dp]
     L.fcm_mlhp_assemble.argtypes = [P, ctypes.c_double, ctypes.POINTER(BC)]
     L.fcm_mlhp_system_size.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -514,6 +515,14 @@ class MLHPPlan:
         self._check(load().fcm_mlhp_block(self.h, leaf, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                           cnt.value, ctypes.byref(cnt)))
         return out[:cnt.value]
+
+    def colour(self, kind):
+        """Colour of every leaf's block (kind "full" or "truncated"); blocks of one colour share no function."""
+        c = np.zeros(self.info["n_leaves"], dtype=np.int32)
+        nc = ctypes.c_int()
+        self._check(load().fcm_mlhp_colour(self.h, {"full": 0, "truncated": 1}[kind],
+                                           c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(nc)))
+        return c, nc.value
 
     def restriction(self, leaf, f):
         """(3, p+1) coefficients of function f on the leaf in the leaf's basis (N0, N1, phi_2..phi_p)."""

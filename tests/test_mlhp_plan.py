@@ -145,3 +145,22 @@ def test_assembled_system_matches_the_oracle(n, spheres, p, k, depth, alpha, bc)
     assert np.abs(rhs - Q.b).max() <= 1e-13 * np.abs(Q.b).max()
     assert max(abs(eta[i] - Q.eta[lc]) for i, lc in enumerate(H.leaves)) < 1e-13
     P.close()
+
+
+def test_truncated_block_colours_share_no_function():
+    # fcm_mlhp_colour: blocks of one colour are disjoint in their functions (one launch per colour can
+    # scatter without atomics); the uniform grid needs the 8 parity colours.
+    for n, spheres, p, k in CASES[:3]:
+        P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k)
+        colour, nc = P.colour("truncated")
+        assert nc == colour.max() + 1 <= 16
+        for c in range(nc):
+            seen = set()
+            for i in np.flatnonzero(colour == c):
+                f = set(P.block(int(i), "truncated").tolist())
+                assert not (f & seen)
+                seen |= f
+        P.close()
+    P = fcm.MLHPPlan((4, 4, 4), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, 0)
+    assert P.colour("truncated")[1] == P.colour("full")[1] == 8
+    P.close()
