@@ -491,7 +491,7 @@ fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p
         h->sph.assign(geom->sph, geom->sph + 4 * (size_t)geom->nsph);
         h->depth = geom->octree_depth;
         h->build(sph, k);
-    } catch (const std::bad_alloc &) {
+    } catch (...) {
         delete h;
         return FCM_ENOMEM;
     }
@@ -541,7 +541,7 @@ fcm_status fcm_mlhp_block(const fcm_mlhp *h, int64_t leaf, int kind, int64_t *fi
     try {
         if (kind == 0) h->full_block(h->leaves[leaf].first, h->leaves[leaf].second, b);
         else h->truncated_block(h->leaves[leaf].first, h->leaves[leaf].second, b);
-    } catch (const std::bad_alloc &) {
+    } catch (...) {
         return FCM_ENOMEM;
     }
     *count = (int)b.size();
@@ -573,7 +573,7 @@ fcm_status fcm_mlhp_colour(const fcm_mlhp *h, int kind, int *colour, int *n_colo
             for (int64_t f : b) used[f] |= 1ull << c;
         }
         *n_colours = nc;
-    } catch (const std::bad_alloc &) {
+    } catch (...) {
         return FCM_ENOMEM;
     }
     return FCM_OK;
@@ -597,6 +597,8 @@ fcm_status fcm_mlhp_assemble(fcm_mlhp *h, double alpha, const fcm_bc *bc)
         h->assembled = false;
         if (!h->assemble(alpha, *bc).empty()) return FCM_EINVAL;
     } catch (const std::bad_alloc &) {
+        return FCM_ENOMEM;
+    } catch (...) {  // e.g. std::system_error from thread creation: no exception crosses the C ABI
         return FCM_ENOMEM;
     }
     return FCM_OK;
