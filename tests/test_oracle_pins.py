@@ -462,3 +462,51 @@ def test_element_blocks_on_cut_cells_beat_diagonal_scaling():
         _, its[eta_bar], _ = P.pcg(tol=1e-8, maxit=30000)
     assert its[0.5] * 5 < its[0.0]
     assert its[1.0] <= its[0.5]
+
+
+def test_schwarz_pcg_iterates_do_not_depend_on_the_basis_scaling(single_void):
+    # Rescaling basis functions (K' = D K D, b' = D b) maps every block to D_B A_B D_B, whose inverse is
+    # D_B^-1 A_B^-1 D_B^-1, so the Schwarz-PCG iterates are the same functions: x_i = D x'_i.  The paper does
+    # not fix the normalisation of its integrated-Legendre functions (reading 1); this shows that the
+    # iterates, and so the energy errors, do not depend on it.  The scaled run is an independent PCG on
+    # K', with each block inverted by the oracle's pseudo inverse.
+    w, P = single_void
+    P.precond_build(0)
+    K = P.csr()
+    b = P.rhs()
+    d = np.random.default_rng(8).uniform(0.5, 2.0, P.nfree)
+    Ks = (K.multiply(d[:, None]).multiply(d[None, :])).tocsr()
+    bs = d * b
+    blocks = []
+    for k in range(P.nblocks()):
+        idx, F, _ = P.block(k)
+        Fs, _, _, nfilt = O.pseudo_inverse(Ks[idx][:, idx].toarray())
+        _, _, _, nfilt0 = O.pseudo_inverse(K[idx][:, idx].toarray())
+        assert nfilt == nfilt0 == 0          # no eigenvalue near the cut-off: the inverse is exact
+        blocks.append((idx, Fs))
+
+    def S(r):
+        z = np.zeros_like(r)
+        for idx, F in blocks:
+            z[idx] += F @ r[idx]
+        return z
+
+    x = np.zeros(P.nfree)
+    r = bs.copy()
+    z = S(r)
+    p = z.copy()
+    rz = r @ z
+    for i in range(1, 11):
+        q = Ks @ p
+        a = rz / (p @ q)
+        x += a * p
+        r -= a * q
+        if i in (1, 3, 10):
+            xi, its, _ = P.pcg(b, tol=0.0, maxit=i)
+            assert its == i + 1                   # stopped by maxit, x is the i-th iterate
+            e = d * x - xi
+            assert np.sqrt(e @ (K @ e) / (xi @ (K @ xi))) < 1e-9
+        z = S(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
