@@ -73,6 +73,49 @@ void shape1d(int p, double xi, double *f)
     for (int j = 2; j <= p; ++j) f[j] = (P[j] - P[j - 2]) / std::sqrt(2.0 * (2 * j - 1));
 }
 
+// Eigen-decomposition of a symmetric n x n matrix by cyclic Jacobi rotations (Golub & Van Loan,
+// Matrix Computations, Sec. 8.5): A (row-major) is overwritten, lam[k] and column k of V (row-major) are the
+// eigenpairs.  Sweeps until the off-diagonal part is below 1e-15 of the Frobenius norm (at most 100).
+void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V)
+{
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    double fro = 0.0;
+    for (double v : A) fro += v * v;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += 2.0 * A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        if (off <= 1e-30 * fro) break;
+        for (int pp = 0; pp < n - 1; ++pp)
+            for (int qq = pp + 1; qq < n; ++qq) {
+                const double apq = A[(size_t)pp * n + qq];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)pp * n + pp], aqq = A[(size_t)qq * n + qq];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // columns pp, qq of A
+                    const double akp = A[(size_t)k * n + pp], akq = A[(size_t)k * n + qq];
+                    A[(size_t)k * n + pp] = c * akp - s * akq;
+                    A[(size_t)k * n + qq] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows pp, qq of A
+                    const double apk = A[(size_t)pp * n + k], aqk = A[(size_t)qq * n + k];
+                    A[(size_t)pp * n + k] = c * apk - s * aqk;
+                    A[(size_t)qq * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {  // columns pp, qq of V
+                    const double vkp = V[(size_t)k * n + pp], vkq = V[(size_t)k * n + qq];
+                    V[(size_t)k * n + pp] = c * vkp - s * vkq;
+                    V[(size_t)k * n + qq] = s * vkp + c * vkq;
+                }
+            }
+    }
+    lam.resize(n);
+    for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+}
+
 }  // namespace
 
 struct fcm_mlhp {
@@ -95,6 +138,11 @@ struct fcm_mlhp {
     std::vector<double> leaf_eta;
     std::vector<int64_t> free_dofs, rowptr, cols;
     std::vector<double> vals, rhs;
+    // Schwarz factors (fcm_mlhp_factorize): blocks over free DOFs in colour order, their pseudo inverses
+    // (row-major, one after the other), the colour ranges of blocks, and 1 / K_ll for free DOFs in no block
+    bool factorized = false;
+    std::vector<int64_t> blk_ptr, blk_dofs, fac_ptr, colour_ptr;
+    std::vector<double> factors, jacobi;
 
     int ext(int l, int a) const { return n[a] << l; }
 
@@ -421,6 +469,118 @@ struct fcm_mlhp {
         return std::string();
     }
 
+    // Sec. 3.2 / Algorithm 1 on the assembled system: a block per leaf with eta > 0 (its full or truncated
+    // functions, the free DOFs among them), A_B^+ = V diag(1/lambda, lambda > eps lambda_max) V^T, and the
+    // diagonal part for free DOFs in no block.  Blocks are coloured greedily (no two blocks of one colour
+    // share a DOF) and stored colour by colour.
+    void factorize(int kind, double eps)
+    {
+        const int64_t nfree = (int64_t)free_dofs.size();
+        std::vector<int64_t> pos(3 * f_level.size(), -1);
+        for (int64_t i = 0; i < nfree; ++i) pos[free_dofs[i]] = i;
+        std::vector<std::vector<int64_t>> blocks;
+        std::vector<int64_t> fb;
+        for (size_t i = 0; i < leaves.size(); ++i) {
+            if (!(leaf_eta[i] > 0.0)) continue;
+            fb.clear();
+            if (kind == 0) full_block(leaves[i].first, leaves[i].second, fb);
+            else truncated_block(leaves[i].first, leaves[i].second, fb);
+            std::vector<int64_t> loc;
+            for (int64_t f : fb)
+                for (int a = 0; a < 3; ++a)
+                    if (pos[3 * f + a] >= 0) loc.push_back(pos[3 * f + a]);
+            std::sort(loc.begin(), loc.end());
+            loc.erase(std::unique(loc.begin(), loc.end()), loc.end());
+            if (!loc.empty()) blocks.push_back(std::move(loc));
+        }
+        // greedy colours over free DOFs
+        std::vector<int> colour(blocks.size(), 0);
+        std::vector<std::vector<uint8_t>> used;
+        int nc = 0;
+        for (size_t b = 0; b < blocks.size(); ++b) {
+            int c = 0;
+            for (;; ++c) {
+                if (c >= nc) break;
+                bool clash = false;
+                for (int64_t d : blocks[b])
+                    if (used[c][d]) {
+                        clash = true;
+                        break;
+                    }
+                if (!clash) break;
+            }
+            if (c == nc) {
+                used.emplace_back(nfree, 0);
+                ++nc;
+            }
+            colour[b] = c;
+            for (int64_t d : blocks[b]) used[c][d] = 1;
+        }
+        std::vector<size_t> order(blocks.size());
+        for (size_t b = 0; b < order.size(); ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return colour[x] < colour[y]; });
+        colour_ptr.assign(nc + 1, 0);
+        for (size_t b = 0; b < blocks.size(); ++b) ++colour_ptr[colour[b] + 1];
+        for (int c = 0; c < nc; ++c) colour_ptr[c + 1] += colour_ptr[c];
+        blk_ptr.assign(1, 0);
+        blk_dofs.clear();
+        fac_ptr.assign(1, 0);
+        for (size_t b : order) {
+            blk_dofs.insert(blk_dofs.end(), blocks[b].begin(), blocks[b].end());
+            blk_ptr.push_back((int64_t)blk_dofs.size());
+            fac_ptr.push_back(fac_ptr.back() + (int64_t)blocks[b].size() * (int64_t)blocks[b].size());
+        }
+        factors.assign(fac_ptr.back(), 0.0);
+        // pseudo inverses, in parallel over blocks
+        std::atomic<size_t> next(0);
+        auto work = [&]() {
+            std::vector<int64_t> where(nfree, -1);
+            std::vector<double> A, lam, V;
+            for (size_t k = next++; k < order.size(); k = next++) {
+                const int64_t *B = blk_dofs.data() + blk_ptr[k];
+                const int m = (int)(blk_ptr[k + 1] - blk_ptr[k]);
+                for (int i = 0; i < m; ++i) where[B[i]] = i;
+                A.assign((size_t)m * m, 0.0);
+                for (int i = 0; i < m; ++i)
+                    for (int64_t e = rowptr[B[i]]; e < rowptr[B[i] + 1]; ++e)
+                        if (where[cols[e]] >= 0) A[(size_t)i * m + where[cols[e]]] = vals[e];
+                for (int i = 0; i < m; ++i) where[B[i]] = -1;
+                for (int i = 0; i < m; ++i)  // exact symmetry
+                    for (int j = i + 1; j < m; ++j) {
+                        const double v = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
+                        A[(size_t)i * m + j] = A[(size_t)j * m + i] = v;
+                    }
+                jacobi_eigen(m, A, lam, V);
+                double lmax = 0.0;
+                for (double l : lam) lmax = std::max(lmax, l);
+                double *F = factors.data() + fac_ptr[k];
+                for (int t = 0; t < m; ++t) {
+                    if (!(lam[t] > eps * lmax)) continue;
+                    const double inv = 1.0 / lam[t];
+                    for (int i = 0; i < m; ++i) {
+                        const double vi = V[(size_t)i * m + t] * inv;
+                        for (int j = 0; j < m; ++j) F[(size_t)i * m + j] += vi * V[(size_t)j * m + t];
+                    }
+                }
+            }
+        };
+        const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+        work();
+        for (auto &t : pool) t.join();
+        // diagonal part for free DOFs in no block
+        std::vector<uint8_t> covered(nfree, 0);
+        for (int64_t d : blk_dofs) covered[d] = 1;
+        jacobi.assign(nfree, 0.0);
+        for (int64_t i = 0; i < nfree; ++i) {
+            if (covered[i]) continue;
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+                if (cols[e] == i) jacobi[i] = 1.0 / vals[e];
+        }
+        factorized = true;
+    }
+
     // 1D factor of function f along axis a on leaf (L, c), as coefficients in the leaf's 1D basis
     bool restriction(int64_t leaf, int64_t f, double *coef) const
     {
@@ -595,6 +755,7 @@ fcm_status fcm_mlhp_assemble(fcm_mlhp *h, double alpha, const fcm_bc *bc)
         if (!std::isfinite(bc->traction[a])) return FCM_EINVAL;
     try {
         h->assembled = false;
+        h->factorized = false;
         if (!h->assemble(alpha, *bc).empty()) return FCM_EINVAL;
     } catch (const std::bad_alloc &) {
         return FCM_ENOMEM;
@@ -624,6 +785,43 @@ fcm_status fcm_mlhp_system(const fcm_mlhp *h, int64_t *free_dofs, int64_t *rowpt
     if (vals) std::copy(h->vals.begin(), h->vals.end(), vals);
     if (rhs) std::copy(h->rhs.begin(), h->rhs.end(), rhs);
     if (leaf_eta) std::copy(h->leaf_eta.begin(), h->leaf_eta.end(), leaf_eta);
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_factorize(fcm_mlhp *h, int kind, double eps)
+{
+    if (!h || (kind != 0 && kind != 1) || !(eps < 1.0)) return FCM_EINVAL;
+    if (!h->assembled) return FCM_ESTATE;
+    try {
+        h->factorized = false;
+        h->factorize(kind, eps);
+    } catch (...) {
+        return FCM_ENOMEM;
+    }
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_factor_info(const fcm_mlhp *h, int *n_blocks, int *n_colours, int64_t *factor_entries)
+{
+    if (!h || !n_blocks || !n_colours || !factor_entries) return FCM_EINVAL;
+    if (!h->factorized) return FCM_ESTATE;
+    *n_blocks = (int)(h->blk_ptr.size() - 1);
+    *n_colours = (int)(h->colour_ptr.size() - 1);
+    *factor_entries = h->fac_ptr.back();
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_factors(const fcm_mlhp *h, int64_t *blk_ptr, int64_t *blk_dofs, int64_t *fac_ptr, double *factors,
+                            int64_t *colour_ptr, double *jacobi)
+{
+    if (!h) return FCM_EINVAL;
+    if (!h->factorized) return FCM_ESTATE;
+    if (blk_ptr) std::copy(h->blk_ptr.begin(), h->blk_ptr.end(), blk_ptr);
+    if (blk_dofs) std::copy(h->blk_dofs.begin(), h->blk_dofs.end(), blk_dofs);
+    if (fac_ptr) std::copy(h->fac_ptr.begin(), h->fac_ptr.end(), fac_ptr);
+    if (factors) std::copy(h->factors.begin(), h->factors.end(), factors);
+    if (colour_ptr) std::copy(h->colour_ptr.begin(), h->colour_ptr.end(), colour_ptr);
+    if (jacobi) std::copy(h->jacobi.begin(), h->jacobi.end(), jacobi);
     return FCM_OK;
 }
 

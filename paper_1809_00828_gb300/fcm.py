@@ -27,7 +27,7 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
             "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size", "fcm_mlhp_system",
-            "fcm_mlhp_destroy")
+            "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -124,6 +124,9 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_assemble.argtypes = [P, ctypes.c_double, ctypes.POINTER(BC)]
     L.fcm_mlhp_system_size.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.fcm_mlhp_system.argtypes = [P, P, P, P, P, P, P]
+    L.fcm_mlhp_factorize.argtypes = [P, ctypes.c_int, ctypes.c_double]
+    L.fcm_mlhp_factor_info.argtypes = [P, ip, ip, ctypes.POINTER(i64)]
+    L.fcm_mlhp_factors.argtypes = [P, P, P, P, P, P, P]
     L.fcm_mlhp_destroy.argtypes = [P]
     L.fcm_mlhp_destroy.restype = None
     for f in EXPORTED:
@@ -551,6 +554,29 @@ class MLHPPlan:
         self._check(L.fcm_mlhp_system(self.h, ptr(free), ptr(rowptr), ptr(cols), ptr(vals), ptr(rhs), ptr(eta)))
         K = sp.csr_matrix((vals, cols, rowptr), shape=(nf.value, nf.value))
         return free, K, rhs, eta
+
+    def factorize(self, kind="truncated", eps=1e-13):
+        """Schwarz factors on the host; returns (blocks, factors, colour_ptr, jacobi): block b's free DOFs and
+        its pseudo inverse, blocks of colour c at colour_ptr[c] .. colour_ptr[c+1]."""
+        L = load()
+        self._check(L.fcm_mlhp_factorize(self.h, {"full": 0, "truncated": 1}[kind], eps))
+        nb, nc, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        self._check(L.fcm_mlhp_factor_info(self.h, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(ne)))
+        nfree = ctypes.c_int64()
+        nnz = ctypes.c_int64()
+        self._check(L.fcm_mlhp_system_size(self.h, ctypes.byref(nfree), ctypes.byref(nnz)))
+        bptr = np.zeros(nb.value + 1, dtype=np.int64)
+        fptr = np.zeros(nb.value + 1, dtype=np.int64)
+        cptr = np.zeros(nc.value + 1, dtype=np.int64)
+        fac = np.zeros(ne.value)
+        jac = np.zeros(nfree.value)
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        self._check(L.fcm_mlhp_factors(self.h, ptr(bptr), None, None, None, None, None))
+        dofs = np.zeros(bptr[-1], dtype=np.int64)
+        self._check(L.fcm_mlhp_factors(self.h, ptr(bptr), ptr(dofs), ptr(fptr), ptr(fac), ptr(cptr), ptr(jac)))
+        blocks = [dofs[bptr[b]:bptr[b + 1]] for b in range(nb.value)]
+        factors = [fac[fptr[b]:fptr[b + 1]].reshape(len(blocks[b]), len(blocks[b])) for b in range(nb.value)]
+        return blocks, factors, cptr, jac
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

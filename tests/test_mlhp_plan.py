@@ -164,3 +164,32 @@ def test_truncated_block_colours_share_no_function():
     P = fcm.MLHPPlan((4, 4, 4), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, 0)
     assert P.colour("truncated")[1] == P.colour("full")[1] == 8
     P.close()
+
+
+@pytest.mark.parametrize("n,spheres,p,k,depth,alpha,kind", [
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 2, 2, 1e-6, "truncated"),
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 1, 2, 1e-6, "full"),
+    ((2, 2, 2), [(0.0, 0.0, 0.0, 0.3)], 3, 2, 2, 1e-8, "truncated"),
+])
+def test_schwarz_factors_match_the_oracle_blocks_and_pseudo_inverses(n, spheres, p, k, depth, alpha, kind):
+    # fcm_mlhp_factorize: the same blocks as the oracle (as sets of free DOFs), colour classes without a
+    # shared DOF, and each factor the pseudo inverse of its block (numpy's eigensolver on the assembled K):
+    # two eigensolvers agree on A_B^+ to about cond(A_B) times the rounding unit.
+    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k, octree_depth=depth)
+    free, K, rhs, eta = P.assemble(alpha, "clamp")
+    blocks, F, cptr, jac = P.factorize(kind)
+    H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), spheres, k)
+    Q = M.MLProblem(H, p, spheres, alpha=alpha, depth=depth)
+    Q.build_blocks(kind)
+    assert sorted(tuple(b) for b in blocks) == sorted(tuple(b) for b in Q.blocks)
+    assert np.array_equal(jac == 0.0, Q.jacobi == 0.0)
+    for c in range(len(cptr) - 1):
+        members = np.concatenate([blocks[b] for b in range(cptr[c], cptr[c + 1])])
+        assert len(members) == len(np.unique(members))
+    for B, Fb in zip(blocks, F):
+        lam, V = np.linalg.eigh(K[B][:, B].toarray())
+        keep = lam > 1e-13 * lam.max()
+        Fn = (V[:, keep] / lam[keep]) @ V[:, keep].T
+        cond = lam.max() / lam[keep].min()
+        assert np.abs(Fb - Fn).max() <= max(1e-12, 64 * cond * 2.2e-16) * np.abs(Fn).max()
+    P.close()
