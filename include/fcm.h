@@ -411,6 +411,20 @@ fcm_status fcm_mlhp_factor_info(const fcm_mlhp *plan, int *n_blocks, int *n_colo
  * c are colour_ptr[c] .. colour_ptr[c+1]) and jacobi[n_free] (0 on DOFs inside blocks). */
 fcm_status fcm_mlhp_factors(const fcm_mlhp *plan, int64_t *blk_ptr, int64_t *blk_dofs, int64_t *fac_ptr, double *factors,
                             int64_t *colour_ptr, double *jacobi);
+/* Upload the assembled system and the factors to the current device (after fcm_mlhp_factorize, else
+ * FCM_ESTATE); every index is checked on the host first (FCM_EINVAL).  The device arrays belong to the plan
+ * until fcm_mlhp_destroy or the next assemble / factorize.  Work is queued on cuda_stream. */
+fcm_status fcm_mlhp_device_setup(fcm_mlhp *plan, void *cuda_stream);
+/* y_dev = K x_dev over the free DOFs (device arrays of n_free doubles; one warp per CSR row). */
+fcm_status fcm_mlhp_apply_K(fcm_mlhp *plan, const double *x_dev, double *y_dev);
+/* z_dev = S r_dev (Eq. (5)): the diagonal part, then one launch per colour of blocks, z_B += A_B^+ r_B.
+ * r_dev and z_dev must differ. */
+fcm_status fcm_mlhp_apply_S(fcm_mlhp *plan, const double *r_dev, double *z_dev);
+/* PCG on K u = b (x0 = 0), stopped when ||S r_i|| / ||S b|| <= tol (Eq. (14)) or after maxit iterations;
+ * *iterations counts the K applications.  FCM_OK, FCM_ENOTCONV (u = the last iterate), FCM_EBREAKDOWN
+ * (p.Kp <= 0 or a non-finite scalar).  Synchronises the stream. */
+fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *plan, const double *b_dev, double tol, int maxit, double *u_dev, int *iterations,
+                              double *relres);
 void fcm_mlhp_destroy(fcm_mlhp *plan);
 
 /* Message of the last failure on ctx (ctx may be NULL for setup failures). */

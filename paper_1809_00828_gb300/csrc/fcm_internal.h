@@ -72,6 +72,21 @@ std::string build_host_problem(const fcm_grid &grid, const fcm_geometry &geom, i
 void box_cell_setup(const fcm_geometry &geom, const double *dlo, const double *dhi, int p, double alpha, double E,
                     double nu, const double *clo, const double *chi, double *K, double *eta, double *face);
 
+// The multi-level system on the device (fcm_mlhp_device.cu): CSR K over the free DOFs, the Schwarz blocks
+// (free-DOF lists, row-major pseudo inverses, colour ranges) and the diagonal part.  create() checks every
+// index on the host, uploads and synchronises; the vectors of the other calls are device arrays of n.
+struct MlhpDevice;
+std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, const int64_t *cols, const double *vals,
+                               int64_t nblocks, const int64_t *bptr, const int64_t *bdofs, const int64_t *fptr,
+                               const double *fac, int ncolours, const int64_t *cptr, const double *jac,
+                               MlhpDevice **out);
+void mlhp_device_destroy(MlhpDevice *d);
+std::string mlhp_device_apply_K(MlhpDevice *d, const double *x, double *y);
+std::string mlhp_device_apply_S(MlhpDevice *d, const double *r, double *z);
+// status: 0 converged, 1 not converged within maxit, 2 breakdown.
+std::string mlhp_device_pcg(MlhpDevice *d, const double *b, double tol, int maxit, double *u, int *its, double *relres,
+                            int *status);
+
 // Gauss-Legendre rule with n points on [-1, 1].
 void gauss_legendre(int n, double *x, double *w);
 

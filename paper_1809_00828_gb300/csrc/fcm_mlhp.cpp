@@ -141,6 +141,10 @@ struct fcm_mlhp {
     // Schwarz factors (fcm_mlhp_factorize): blocks over free DOFs in colour order, their pseudo inverses
     // (row-major, one after the other), the colour ranges of blocks, and 1 / K_ll for free DOFs in no block
     bool factorized = false;
+    // device copy (fcm_mlhp_device_setup)
+    fcm::MlhpDevice *dev = nullptr;
+
+    ~fcm_mlhp() { fcm::mlhp_device_destroy(dev); }
     std::vector<int64_t> blk_ptr, blk_dofs, fac_ptr, colour_ptr;
     std::vector<double> factors, jacobi;
 
@@ -756,6 +760,8 @@ fcm_status fcm_mlhp_assemble(fcm_mlhp *h, double alpha, const fcm_bc *bc)
     try {
         h->assembled = false;
         h->factorized = false;
+        fcm::mlhp_device_destroy(h->dev);
+        h->dev = nullptr;
         if (!h->assemble(alpha, *bc).empty()) return FCM_EINVAL;
     } catch (const std::bad_alloc &) {
         return FCM_ENOMEM;
@@ -794,6 +800,8 @@ fcm_status fcm_mlhp_factorize(fcm_mlhp *h, int kind, double eps)
     if (!h->assembled) return FCM_ESTATE;
     try {
         h->factorized = false;
+        fcm::mlhp_device_destroy(h->dev);
+        h->dev = nullptr;
         h->factorize(kind, eps);
     } catch (...) {
         return FCM_ENOMEM;
@@ -823,6 +831,48 @@ fcm_status fcm_mlhp_factors(const fcm_mlhp *h, int64_t *blk_ptr, int64_t *blk_do
     if (colour_ptr) std::copy(h->colour_ptr.begin(), h->colour_ptr.end(), colour_ptr);
     if (jacobi) std::copy(h->jacobi.begin(), h->jacobi.end(), jacobi);
     return FCM_OK;
+}
+
+fcm_status fcm_mlhp_device_setup(fcm_mlhp *h, void *cuda_stream)
+{
+    if (!h) return FCM_EINVAL;
+    if (!h->factorized) return FCM_ESTATE;
+    fcm::mlhp_device_destroy(h->dev);
+    h->dev = nullptr;
+    try {
+        const std::string e = fcm::mlhp_device_create(
+            cuda_stream, (int64_t)h->free_dofs.size(), h->rowptr.data(), h->cols.data(), h->vals.data(),
+            (int64_t)h->blk_ptr.size() - 1, h->blk_ptr.data(), h->blk_dofs.data(), h->fac_ptr.data(), h->factors.data(),
+            (int)h->colour_ptr.size() - 1, h->colour_ptr.data(), h->jacobi.data(), &h->dev);
+        if (!e.empty()) return e.rfind("upload", 0) == 0 || e.rfind("cudaMalloc", 0) == 0 ? FCM_ECUDA : FCM_EINVAL;
+    } catch (...) {
+        return FCM_ENOMEM;
+    }
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_apply_K(fcm_mlhp *h, const double *x_dev, double *y_dev)
+{
+    if (!h || !x_dev || !y_dev) return FCM_EINVAL;
+    if (!h->dev) return FCM_ESTATE;
+    return fcm::mlhp_device_apply_K(h->dev, x_dev, y_dev).empty() ? FCM_OK : FCM_ECUDA;
+}
+
+fcm_status fcm_mlhp_apply_S(fcm_mlhp *h, const double *r_dev, double *z_dev)
+{
+    if (!h || !r_dev || !z_dev || r_dev == z_dev) return FCM_EINVAL;
+    if (!h->dev) return FCM_ESTATE;
+    return fcm::mlhp_device_apply_S(h->dev, r_dev, z_dev).empty() ? FCM_OK : FCM_ECUDA;
+}
+
+fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *h, const double *b_dev, double tol, int maxit, double *u_dev, int *iterations,
+                              double *relres)
+{
+    if (!h || !b_dev || !u_dev || !iterations || !relres || maxit < 0 || !(tol >= 0.0)) return FCM_EINVAL;
+    if (!h->dev) return FCM_ESTATE;
+    int status = 0;
+    if (!fcm::mlhp_device_pcg(h->dev, b_dev, tol, maxit, u_dev, iterations, relres, &status).empty()) return FCM_ECUDA;
+    return status == 0 ? FCM_OK : status == 1 ? FCM_ENOTCONV : FCM_EBREAKDOWN;
 }
 
 void fcm_mlhp_destroy(fcm_mlhp *h) { delete h; }

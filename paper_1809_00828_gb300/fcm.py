@@ -27,7 +27,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
             "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size", "fcm_mlhp_system",
-            "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_destroy")
+            "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
+            "fcm_mlhp_apply_K", "fcm_mlhp_apply_S", "fcm_mlhp_pcg_solve", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -127,6 +128,10 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_factorize.argtypes = [P, ctypes.c_int, ctypes.c_double]
     L.fcm_mlhp_factor_info.argtypes = [P, ip, ip, ctypes.POINTER(i64)]
     L.fcm_mlhp_factors.argtypes = [P, P, P, P, P, P, P]
+    L.fcm_mlhp_device_setup.argtypes = [P, P]
+    L.fcm_mlhp_apply_K.argtypes = [P, P, P]
+    L.fcm_mlhp_apply_S.argtypes = [P, P, P]
+    L.fcm_mlhp_pcg_solve.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
     L.fcm_mlhp_destroy.argtypes = [P]
     L.fcm_mlhp_destroy.restype = None
     for f in EXPORTED:
@@ -577,6 +582,36 @@ class MLHPPlan:
         blocks = [dofs[bptr[b]:bptr[b + 1]] for b in range(nb.value)]
         factors = [fac[fptr[b]:fptr[b + 1]].reshape(len(blocks[b]), len(blocks[b])) for b in range(nb.value)]
         return blocks, factors, cptr, jac
+
+    def device_setup(self, stream=None):
+        """Upload the assembled system and factors to the current CUDA device (torch's current stream)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._stream = stream
+        self._check(load().fcm_mlhp_device_setup(self.h, ctypes.c_void_p(stream)))
+
+    def apply_K(self, x, out=None):
+        import torch
+        y = out if out is not None else torch.empty_like(x)
+        self._check(load().fcm_mlhp_apply_K(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_S(self, r, out=None):
+        import torch
+        z = out if out is not None else torch.empty_like(r)
+        self._check(load().fcm_mlhp_apply_S(self.h, _ptr(r), _ptr(z)))
+        return z
+
+    def pcg_solve(self, b, tol, maxit=100000, out=None, check=True):
+        import torch
+        u = out if out is not None else torch.empty_like(b)
+        its = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = load().fcm_mlhp_pcg_solve(self.h, _ptr(b), tol, maxit, _ptr(u), ctypes.byref(its), ctypes.byref(rel))
+        if check:
+            self._check(st)
+        return u, its.value, rel.value, st
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
