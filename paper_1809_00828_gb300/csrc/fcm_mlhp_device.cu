@@ -3,9 +3,9 @@
 // The host plan assembles K over the free DOFs (CSR) and the Schwarz factors of the leaf blocks
 // (fcm_mlhp.cpp); this file uploads them and runs:
 //   - K x: one warp per CSR row;
-//   - S r (Eq. (5)): z = D r for the DOFs in no block, then one launch per colour, one CTA per block:
-//     gather r_B into shared memory, z_B += A_B^+ r_B, scatter (the blocks of one colour share no DOF, so no
-//     atomics);
+//   - S r (Eq. (5)): z = D r for the DOFs in no block, then one launch per colour, each block's rows split
+//     over a few CTAs: gather r_B into shared memory, z_B += A_B^+ r_B with a warp per row, scatter (the
+//     blocks of one colour share no DOF, so no atomics);
 //   - PCG with x0 = 0, stopped on ||S r_i|| / ||S b|| <= tol (Eq. (14)): the dot products are two-level
 //     reductions in a fixed order (deterministic), the scalars go to the host each iteration.
 // Every index the kernels use is checked on the host before the upload.
@@ -52,25 +52,34 @@ __global__ void __launch_bounds__(kThreads) mlhp_diag_kernel(int n, const double
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) z[i] = jac[i] * r[i];
 }
 
-// One CTA per block of one colour: z_B += A_B^+ r_B.
-__global__ void __launch_bounds__(128) mlhp_block_kernel(int64_t first, const int64_t *__restrict__ bptr,
-                                                         const int *__restrict__ bdofs,
-                                                         const int64_t *__restrict__ fptr,
-                                                         const double *__restrict__ fac,
-                                                         const double *__restrict__ r, double *__restrict__ z)
+// z_B += A_B^+ r_B for the blocks of one colour.  A block's rows are split over `splits` CTAs of
+// kRowsPerCta rows (more CTAs in flight than blocks in a colour); every CTA gathers r_B into shared memory,
+// then each warp takes one row at a time and reads it coalesced, lanes striding over the columns.
+constexpr int kRowsPerCta = 32;
+
+__global__ void __launch_bounds__(kThreads) mlhp_block_kernel(int64_t first, int splits, const int64_t *__restrict__ bptr,
+                                                              const int *__restrict__ bdofs,
+                                                              const int64_t *__restrict__ fptr,
+                                                              const double *__restrict__ fac,
+                                                              const double *__restrict__ r, double *__restrict__ z)
 {
     extern __shared__ double rb[];
-    const int64_t b = first + blockIdx.x;
+    const int64_t b = first + blockIdx.x / splits;
+    const int row0 = (int)(blockIdx.x % splits) * kRowsPerCta;
     const int64_t o = bptr[b];
     const int m = (int)(bptr[b + 1] - o);
+    if (row0 >= m) return;  // uniform across the CTA, before any barrier
     const double *F = fac + fptr[b];
-    for (int j = threadIdx.x; j < m; j += blockDim.x) rb[j] = r[bdofs[o + j]];
+    for (int j = threadIdx.x; j < m; j += kThreads) rb[j] = r[bdofs[o + j]];
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row_end = min(m, row0 + kRowsPerCta);
+    for (int i = row0 + warp; i < row_end; i += kThreads / 32) {  // warp-uniform bounds
         const double *Fi = F + (int64_t)i * m;
         double s = 0.0;
-        for (int j = 0; j < m; ++j) s += Fi[j] * rb[j];
-        z[bdofs[o + i]] += s;
+        for (int j = lane; j < m; j += 32) s += Fi[j] * rb[j];
+        s = warp_sum(s);
+        if (lane == 0) z[bdofs[o + i]] += s;
     }
 }
 
@@ -237,10 +246,12 @@ std::string mlhp_device_apply_S(MlhpDevice *d, const double *r, double *z)
     mlhp_diag_kernel<<<d->grid_n, kThreads, 0, d->st>>>(d->n, d->jac, r, z);
     MLHP_CUDA(cudaGetLastError());
     const size_t smem = (size_t)d->max_block * sizeof(double);
+    const int splits = (d->max_block + kRowsPerCta - 1) / kRowsPerCta;
     for (int c = 0; c < d->ncolours; ++c) {
         const int64_t nb = d->colour_ptr[c + 1] - d->colour_ptr[c];
         if (nb == 0) continue;
-        mlhp_block_kernel<<<(unsigned)nb, 128, smem, d->st>>>(d->colour_ptr[c], d->bptr, d->bdofs, d->fptr, d->fac, r, z);
+        mlhp_block_kernel<<<(unsigned)(nb * splits), kThreads, smem, d->st>>>(d->colour_ptr[c], splits, d->bptr, d->bdofs,
+                                                                            d->fptr, d->fac, r, z);
         MLHP_CUDA(cudaGetLastError());
     }
     return std::string();
