@@ -398,12 +398,13 @@ fcm_status fcm_mlhp_system_size(const fcm_mlhp *plan, int64_t *n_free, int64_t *
 fcm_status fcm_mlhp_system(const fcm_mlhp *plan, int64_t *free_dofs, int64_t *rowptr, int64_t *cols, double *vals,
                            double *rhs, double *leaf_eta);
 /* Schwarz factors of the assembled system (Sec. 3.2, Algorithm 1), on the host: one block per leaf with
- * eta > 0 (kind 0 full, 1 truncated: the free DOFs of its functions), its pseudo inverse A_B^+ (eigenpairs
+ * 0 < eta_T <= eta_bar (eta_T clamped to 1; eta_bar in [0, 1], 1 = every leaf) (kind 0 full, 1 truncated:
+ * the free DOFs of its functions), its pseudo inverse A_B^+ (eigenpairs
  * with lambda > eps lambda_max of the block, Eq. (13); cyclic Jacobi eigen-decomposition), and 1 / K_ll for
  * free DOFs in no block.  Blocks are coloured greedily (no two blocks of one colour share a DOF) and stored
  * colour by colour.  Host time grows as the cube of the block size: meant for truncated blocks.
  * FCM_ESTATE before fcm_mlhp_assemble. */
-fcm_status fcm_mlhp_factorize(fcm_mlhp *plan, int kind, double eps);
+fcm_status fcm_mlhp_factorize(fcm_mlhp *plan, int kind, double eps, double eta_bar);
 fcm_status fcm_mlhp_factor_info(const fcm_mlhp *plan, int *n_blocks, int *n_colours, int64_t *factor_entries);
 /* Copy the factors to caller-owned host arrays (any may be NULL): blk_ptr[n_blocks + 1] and blk_dofs (free
  * DOF indices of block b in blk_dofs[blk_ptr[b] .. blk_ptr[b+1]), ascending), fac_ptr[n_blocks + 1] and

@@ -457,12 +457,14 @@ class MLProblem:
         return b
 
     # -- Sec. 3.2: blocks on leaves --------------------------------------------------------------------
-    def build_blocks(self, kind="truncated", eps=1e-13):
-        """Blocks (free DOF index arrays, one per leaf with eta > 0) and their pseudo inverses; the
-        diagonal part of Algorithm 1 (1 / K_ll) for free DOFs in no block.  kind: 'full', 'truncated'
-        or 'span'."""
+    def build_blocks(self, kind="truncated", eps=1e-13, eta_bar=1.0):
+        """Blocks (free DOF index arrays, one per leaf with 0 < eta_T <= eta_bar, Sec. 3.2 "Optimizing the
+        number of blocks", eta_T clamped to 1) and their pseudo inverses; the diagonal part of Algorithm 1
+        (1 / K_ll) for free DOFs in no block.  kind: 'full', 'truncated' or 'span'."""
         blocks = []
         for (L, c) in self.active_leaves:
+            if min(self.eta[(L, c)], 1.0) > eta_bar:
+                continue
             fids = self.basis.block_functions(kind, L, c)
             dofs = (3 * np.array(sorted(set(fids)))[:, None] + np.arange(3)[None, :]).reshape(-1)
             loc = self.pos[dofs]

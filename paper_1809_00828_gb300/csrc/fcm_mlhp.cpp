@@ -473,11 +473,11 @@ struct fcm_mlhp {
         return std::string();
     }
 
-    // Sec. 3.2 / Algorithm 1 on the assembled system: a block per leaf with eta > 0 (its full or truncated
-    // functions, the free DOFs among them), A_B^+ = V diag(1/lambda, lambda > eps lambda_max) V^T, and the
+    // Sec. 3.2 / Algorithm 1 on the assembled system: a block per leaf with 0 < eta <= eta_bar (its full or
+    // truncated functions, the free DOFs among them), A_B^+ = V diag(1/lambda, lambda > eps lambda_max) V^T, and the
     // diagonal part for free DOFs in no block.  Blocks are coloured greedily (no two blocks of one colour
     // share a DOF) and stored colour by colour.
-    void factorize(int kind, double eps)
+    void factorize(int kind, double eps, double eta_bar)
     {
         const int64_t nfree = (int64_t)free_dofs.size();
         std::vector<int64_t> pos(3 * f_level.size(), -1);
@@ -485,7 +485,7 @@ struct fcm_mlhp {
         std::vector<std::vector<int64_t>> blocks;
         std::vector<int64_t> fb;
         for (size_t i = 0; i < leaves.size(); ++i) {
-            if (!(leaf_eta[i] > 0.0)) continue;
+            if (!(leaf_eta[i] > 0.0) || std::min(leaf_eta[i], 1.0) > eta_bar) continue;  // Sec. 3.2 threshold
             fb.clear();
             if (kind == 0) full_block(leaves[i].first, leaves[i].second, fb);
             else truncated_block(leaves[i].first, leaves[i].second, fb);
@@ -794,15 +794,15 @@ fcm_status fcm_mlhp_system(const fcm_mlhp *h, int64_t *free_dofs, int64_t *rowpt
     return FCM_OK;
 }
 
-fcm_status fcm_mlhp_factorize(fcm_mlhp *h, int kind, double eps)
+fcm_status fcm_mlhp_factorize(fcm_mlhp *h, int kind, double eps, double eta_bar)
 {
-    if (!h || (kind != 0 && kind != 1) || !(eps < 1.0)) return FCM_EINVAL;
+    if (!h || (kind != 0 && kind != 1) || !(eps < 1.0) || !(eta_bar >= 0.0 && eta_bar <= 1.0)) return FCM_EINVAL;
     if (!h->assembled) return FCM_ESTATE;
     try {
         h->factorized = false;
         fcm::mlhp_device_destroy(h->dev);
         h->dev = nullptr;
-        h->factorize(kind, eps);
+        h->factorize(kind, eps, eta_bar);
     } catch (...) {
         return FCM_ENOMEM;
     }

@@ -125,7 +125,7 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_assemble.argtypes = [P, ctypes.c_double, ctypes.POINTER(BC)]
     L.fcm_mlhp_system_size.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.fcm_mlhp_system.argtypes = [P, P, P, P, P, P, P]
-    L.fcm_mlhp_factorize.argtypes = [P, ctypes.c_int, ctypes.c_double]
+    L.fcm_mlhp_factorize.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double]
     L.fcm_mlhp_factor_info.argtypes = [P, ip, ip, ctypes.POINTER(i64)]
     L.fcm_mlhp_factors.argtypes = [P, P, P, P, P, P, P]
     L.fcm_mlhp_device_setup.argtypes = [P, P]
@@ -560,11 +560,12 @@ class MLHPPlan:
         K = sp.csr_matrix((vals, cols, rowptr), shape=(nf.value, nf.value))
         return free, K, rhs, eta
 
-    def factorize(self, kind="truncated", eps=1e-13):
-        """Schwarz factors on the host; returns (blocks, factors, colour_ptr, jacobi): block b's free DOFs and
-        its pseudo inverse, blocks of colour c at colour_ptr[c] .. colour_ptr[c+1]."""
+    def factorize(self, kind="truncated", eps=1e-13, eta_bar=1.0):
+        """Schwarz factors on the host for the leaves with eta_T <= eta_bar; returns (blocks, factors,
+        colour_ptr, jacobi): block b's free DOFs and its pseudo inverse, blocks of colour c at
+        colour_ptr[c] .. colour_ptr[c+1], and 1 / K_ll on the DOFs in no block."""
         L = load()
-        self._check(L.fcm_mlhp_factorize(self.h, {"full": 0, "truncated": 1}[kind], eps))
+        self._check(L.fcm_mlhp_factorize(self.h, {"full": 0, "truncated": 1}[kind], eps, eta_bar))
         nb, nc, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
         self._check(L.fcm_mlhp_factor_info(self.h, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(ne)))
         nfree = ctypes.c_int64()

@@ -166,23 +166,25 @@ def test_truncated_block_colours_share_no_function():
     P.close()
 
 
-@pytest.mark.parametrize("n,spheres,p,k,depth,alpha,kind", [
-    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 2, 2, 1e-6, "truncated"),
-    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 1, 2, 1e-6, "full"),
-    ((2, 2, 2), [(0.0, 0.0, 0.0, 0.3)], 3, 2, 2, 1e-8, "truncated"),
+@pytest.mark.parametrize("n,spheres,p,k,depth,alpha,kind,eta_bar", [
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 2, 2, 1e-6, "truncated", 1.0),
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 2, 2, 1e-6, "truncated", 0.5),   # blocks on the cut leaves only
+    ((4, 4, 4), [(0.5, 0.5, 0.5, 0.1)], 2, 1, 2, 1e-6, "full", 1.0),
+    ((2, 2, 2), [(0.0, 0.0, 0.0, 0.3)], 3, 2, 2, 1e-8, "truncated", 1.0),
 ])
-def test_schwarz_factors_match_the_oracle_blocks_and_pseudo_inverses(n, spheres, p, k, depth, alpha, kind):
+def test_schwarz_factors_match_the_oracle_blocks_and_pseudo_inverses(n, spheres, p, k, depth, alpha, kind, eta_bar):
     # fcm_mlhp_factorize: the same blocks as the oracle (as sets of free DOFs), colour classes without a
     # shared DOF, and each factor the pseudo inverse of its block (numpy's eigensolver on the assembled K):
     # two eigensolvers agree on A_B^+ to about cond(A_B) times the rounding unit.
     P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k, octree_depth=depth)
     free, K, rhs, eta = P.assemble(alpha, "clamp")
-    blocks, F, cptr, jac = P.factorize(kind)
+    blocks, F, cptr, jac = P.factorize(kind, eta_bar=eta_bar)
     H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), spheres, k)
     Q = M.MLProblem(H, p, spheres, alpha=alpha, depth=depth)
-    Q.build_blocks(kind)
+    Q.build_blocks(kind, eta_bar=eta_bar)
     assert sorted(tuple(b) for b in blocks) == sorted(tuple(b) for b in Q.blocks)
     assert np.array_equal(jac == 0.0, Q.jacobi == 0.0)
+    assert np.abs(jac - Q.jacobi).max() <= 1e-13 * np.abs(Q.jacobi).max(initial=1.0)
     for c in range(len(cptr) - 1):
         members = np.concatenate([blocks[b] for b in range(cptr[c], cptr[c + 1])])
         assert len(members) == len(np.unique(members))
@@ -192,4 +194,15 @@ def test_schwarz_factors_match_the_oracle_blocks_and_pseudo_inverses(n, spheres,
         Fn = (V[:, keep] / lam[keep]) @ V[:, keep].T
         cond = lam.max() / lam[keep].min()
         assert np.abs(Fb - Fn).max() <= max(1e-12, 64 * cond * 2.2e-16) * np.abs(Fn).max()
+    P.close()
+
+
+def test_eta_bar_zero_leaves_only_the_diagonal_part():
+    # eta_bar = 0: no leaf gets a block (Sec. 3.2, "eta_bar = 0 results in a Jacobi preconditioner"), so S is
+    # 1 / K_ll on every free DOF.
+    P = fcm.MLHPPlan((4, 4, 4), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.1)], 2, 1, octree_depth=2)
+    free, K, rhs, eta = P.assemble(1e-6, "clamp")
+    blocks, F, cptr, jac = P.factorize("truncated", eta_bar=0.0)
+    assert blocks == [] and len(cptr) == 1
+    assert np.array_equal(jac, 1.0 / K.diagonal())
     P.close()
