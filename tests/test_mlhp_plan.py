@@ -206,3 +206,19 @@ def test_eta_bar_zero_leaves_only_the_diagonal_part():
     assert blocks == [] and len(cptr) == 1
     assert np.array_equal(jac, 1.0 / K.diagonal())
     P.close()
+
+
+def test_porous_hierarchy_overlap_grows_like_the_paper_table_for_full_blocks_only():
+    # Sec. 5.3 table of n_max (gearbox, refined toward internal pores, k = 0..3): full blocks 8, 64, 274, 810;
+    # truncated blocks 8 at every depth.  A porous cube (40 voids, 8^3 base, p = 3) refined toward the void
+    # surfaces shows the same pattern: 8, 57, 323, 1450 for full blocks, 8 for truncated ones.
+    from paper_1809_00828_gb300 import inputs as I
+    sph = I.random_sphere_voids(11, 40, 0.02, 0.08).sphere_array()
+    full = []
+    for k in range(4):
+        P = fcm.MLHPPlan((8, 8, 8), (0, 0, 0), (1, 1, 1), sph, 3, k)
+        assert P.info["n_max_truncated"] == 8
+        full.append(P.info["n_max_full"])
+        P.close()
+    assert full[0] == 8
+    assert all(b > 2.5 * a for a, b in zip(full, full[1:]))
