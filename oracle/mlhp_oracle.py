@@ -428,8 +428,8 @@ class MLProblem:
             pts, wts = [], []
 
             def rec(blo, bhi, d):  # face-local coordinates [-1, 1]^2
-                plo = np.array([lo[0] + (blo[0] + 1) * 0.5 * (hi[0] - lo[0]), lo[1] + (blo[1] + 1) * 0.5 * (hi[1] - lo[1]), hi[2]])
-                phi = np.array([lo[0] + (bhi[0] + 1) * 0.5 * (hi[0] - lo[0]), lo[1] + (bhi[1] + 1) * 0.5 * (hi[1] - lo[1]), hi[2]])
+                plo = np.append(lo[:2] + (blo + 1) * 0.5 * (hi[:2] - lo[:2]), hi[2])
+                phi = np.append(lo[:2] + (bhi + 1) * 0.5 * (hi[:2] - lo[:2]), hi[2])
                 if d < self.depth and _box_cut(self.spheres, plo, phi):
                     mid = 0.5 * (blo + bhi)
                     for o in itertools.product((0, 1), repeat=2):

@@ -252,7 +252,8 @@ struct fcm_mlhp {
                 }
                 if (!box_cut(sph, blo, bhi)) continue;
                 R.insert(key);
-                for (int i = 0; i < 8; ++i) next.insert(key3({2 * c[0] + (i & 1), 2 * c[1] + ((i >> 1) & 1), 2 * c[2] + (i >> 2)}));
+                for (int i = 0; i < 8; ++i)
+                    next.insert(key3({2 * c[0] + (i & 1), 2 * c[1] + ((i >> 1) & 1), 2 * c[2] + (i >> 2)}));
             }
             refined.push_back(R);
             if (R.empty()) break;
@@ -264,7 +265,8 @@ struct fcm_mlhp {
         for (int l = 0; l < levels; ++l) {
             std::vector<I3> lv;
             for (uint64_t key : cells[l])
-                if (!refined[l].count(key)) lv.push_back({(int)(key & 0x1fffff), (int)((key >> 21) & 0x1fffff), (int)(key >> 42)});
+                if (!refined[l].count(key))
+                    lv.push_back({(int)(key & 0x1fffff), (int)((key >> 21) & 0x1fffff), (int)(key >> 42)});
             std::sort(lv.begin(), lv.end());
             for (const I3 &c : lv) leaves.push_back({l, c});
         }
@@ -416,7 +418,8 @@ struct fcm_mlhp {
                     for (int j = 0; j < q; ++j) cl[a][j] = coef[a * q + (j == p ? 1 : (j == 0 ? 0 : j + 1))];
                 for (int iz = 0; iz < q; ++iz)
                     for (int iy = 0; iy < q; ++iy)
-                        for (int ix = 0; ix < q; ++ix) C[(size_t)r * nl + ix + q * (iy + q * iz)] = cl[0][ix] * cl[1][iy] * cl[2][iz];
+                        for (int ix = 0; ix < q; ++ix)
+                            C[(size_t)r * nl + ix + q * (iy + q * iz)] = cl[0][ix] * cl[1][iy] * cl[2][iz];
                 if (!face[i].empty()) {
                     double s = 0.0;
                     for (int iy = 0; iy < q; ++iy)
@@ -460,8 +463,9 @@ struct fcm_mlhp {
                 return x.first < y.first;
             });
             for (size_t k = 0; k < v.size(); ++k) {
-                if (!cols.empty() && (int64_t)cols.size() > rowptr[r] && cols.back() == v[k].first) vals.back() += v[k].second;
-                else {
+                if (!cols.empty() && (int64_t)cols.size() > rowptr[r] && cols.back() == v[k].first) {
+                    vals.back() += v[k].second;
+                } else {
                     cols.push_back(v[k].first);
                     vals.push_back(v[k].second);
                 }

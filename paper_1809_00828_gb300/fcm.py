@@ -26,7 +26,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
             "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
-            "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size", "fcm_mlhp_system",
+            "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size",
+            "fcm_mlhp_system",
             "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
             "fcm_mlhp_apply_K", "fcm_mlhp_apply_S", "fcm_mlhp_pcg_solve", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
