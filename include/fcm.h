@@ -330,7 +330,7 @@ fcm_status fcm_fpcg_solve_host(fcm_ctx *ctx, fcm_unet *net, double gamma, int co
  *     (cudaGetSymbolAddress); make it before any stream capture. */
 fcm_status fcm_apply_S_noalloc(fcm_ctx *ctx, const double *r_dev, double *z_dev);
 
-/* ---- Multi-level hp overlays (Sec. 2.2) and their leaf blocks (Sec. 3.2): host-side plan ----------------
+/* ---- Multi-level hp overlays (Sec. 2.2) and their leaf blocks (Sec. 3.2) -------------------------------
  *
  * A base grid (grid->n cells on [grid->lo, grid->hi]) refined k times toward the sphere surfaces of geom
  * (geom->kind must be 0): a level-l cell that a sphere surface crosses (min distance < r < max distance from
@@ -348,7 +348,9 @@ fcm_status fcm_apply_S_noalloc(fcm_ctx *ctx, const double *r_dev, double *z_dev)
  * coordinates: even = on a grid plane, odd = inside a cell interval) sorted by (z, y, x), modes with the
  * bubble index of the lowest odd axis slowest; leaves by level, then (x, y, z) lexicographically.
  *
- * The plan is host memory only (no device work); the library owns it until fcm_mlhp_destroy. */
+ * The plan, the assembled system and the factors live in host memory; fcm_mlhp_device_setup adds a device
+ * copy for the K and S applies and the PCG.  The library owns everything until fcm_mlhp_destroy.  Device
+ * calls return FCM_ECUDA when a CUDA call fails. */
 typedef struct fcm_mlhp fcm_mlhp;
 typedef struct {
     int levels;                 /* levels of the hierarchy, 1 = the base grid only */
@@ -398,10 +400,10 @@ fcm_status fcm_mlhp_system_size(const fcm_mlhp *plan, int64_t *n_free, int64_t *
 fcm_status fcm_mlhp_system(const fcm_mlhp *plan, int64_t *free_dofs, int64_t *rowptr, int64_t *cols, double *vals,
                            double *rhs, double *leaf_eta);
 /* Schwarz factors of the assembled system (Sec. 3.2, Algorithm 1), on the host: one block per leaf with
- * 0 < eta_T <= eta_bar (eta_T clamped to 1; eta_bar in [0, 1], 1 = every leaf) (kind 0 full, 1 truncated:
- * the free DOFs of its functions), its pseudo inverse A_B^+ (eigenpairs
- * with lambda > eps lambda_max of the block, Eq. (13); cyclic Jacobi eigen-decomposition), and 1 / K_ll for
- * free DOFs in no block.  Blocks are coloured greedily (no two blocks of one colour share a DOF) and stored
+ * 0 < eta_T <= eta_bar (eta_T clamped to 1; eta_bar in [0, 1], 1 = every leaf), holding the free DOFs of the
+ * leaf's functions (kind 0 full, 1 truncated); its pseudo inverse A_B^+ (eigenpairs with lambda > eps
+ * lambda_max of the block, Eq. (13); cyclic Jacobi eigen-decomposition); and 1 / K_ll for free DOFs in no
+ * block.  Blocks are coloured greedily (no two blocks of one colour share a DOF) and stored
  * colour by colour.  Host time grows as the cube of the block size: meant for truncated blocks.
  * FCM_ESTATE before fcm_mlhp_assemble. */
 fcm_status fcm_mlhp_factorize(fcm_mlhp *plan, int kind, double eps, double eta_bar);
