@@ -332,9 +332,10 @@ fcm_status fcm_apply_S_noalloc(fcm_ctx *ctx, const double *r_dev, double *z_dev)
 
 /* ---- Multi-level hp overlays (Sec. 2.2) and their leaf blocks (Sec. 3.2) -------------------------------
  *
- * A base grid (grid->n cells on [grid->lo, grid->hi]) refined k times toward the sphere surfaces of geom
- * (geom->kind must be 0): a level-l cell that a sphere surface crosses (min distance < r < max distance from
- * the centre) carries an overlay of its 8 children on level l + 1.  Every level has its own integrated-
+ * A base grid (grid->n cells on [grid->lo, grid->hi]) refined k times toward the boundary of geom: a level-l
+ * cell that the boundary crosses carries an overlay of its 8 children on level l + 1.  Crossing: spheres,
+ * min distance < r < max distance from the centre; voxels (an image spanning the grid box), the voxels the
+ * cell overlaps are not all equal; half space, min a.x < d < max a.x over the cell.  Every level has its own integrated-
  * Legendre basis of order p, one set of modes per topological component.  A level-l component is active iff
  * every in-domain level-l cell position around it exists (homogeneous Dirichlet conditions on the overlay's
  * boundary) and at least one of them is a leaf (covered components are deactivated).
@@ -384,8 +385,8 @@ fcm_status fcm_mlhp_colour(const fcm_mlhp *plan, int kind, int *colour, int *n_c
  * product over the axes a of sum_j coef[a (p+1) + j] b_j(t_a), with b = (N0, N1, phi_2 .. phi_p) the
  * leaf's own 1D shape functions in its local coordinate t_a in [-1, 1]. */
 fcm_status fcm_mlhp_restriction(const fcm_mlhp *plan, int64_t leaf, int64_t f, double *coef);
-/* Assemble the elasticity system of Eq. (1) on the hierarchy (host memory), with the plan's spheres as
- * voids (alpha inside them) and their octree_depth, material and conditions from bc (FCM_BC_* as for
+/* Assemble the elasticity system of Eq. (1) on the hierarchy (host memory), with the plan's geometry
+ * (alpha in the void) and its octree_depth, material and conditions from bc (FCM_BC_* as for
  * fcm_setup; Dirichlet DOFs are removed: a function is fixed in component a when its component lies on the
  * plane of that condition), and the traction bc->traction on the top face z = hi[2].  Each leaf with eta > 0
  * contributes C K_cell C^T, with K_cell the cell matrix of the leaf's box (the same moment quadrature as

@@ -23,8 +23,8 @@ Readings where the paper is silent (each is binding for any implementation compa
   Dirichlet boundary; it applies only where the overlay borders unrefined cells, not on the domain
   boundary.  The second deactivates components that finer overlays cover.  In 1D this keeps, on a leaf
   at the domain end, both vertex functions on the finest level, as the paper's Fig. 4 discussion says.
-- Refinement toward a surface: a level-l cell is refined (l < k) when a sphere surface crosses its
-  closed box (min distance < r < max distance from the centre), the octree's cut test.
+- Refinement toward a surface: a level-l cell is refined (l < k) when the domain boundary crosses its
+  closed box, the octree's cut test (Shape.cut: sphere surfaces, voxel interfaces or a plane).
 - Truncation in 3D: the paper states the 1D rule (p - 1 higher-order functions of the leaf and two
   linear functions, the missing one found by traversing down the hierarchy) and says 3D follows by
   the tensor product.  Read here: every non-vertex function comes from the leaf's own level; only
@@ -40,7 +40,7 @@ import numpy as np
 import numpy.polynomial.legendre as npleg
 import scipy.sparse as sp
 
-__all__ = ["Hierarchy", "refine_toward_spheres", "Basis", "MLProblem", "count_dofs", "shape1d"]
+__all__ = ["Shape", "Hierarchy", "refine_toward_spheres", "Basis", "MLProblem", "count_dofs", "shape1d"]
 
 
 # ----------------------------------------------------------------------------- 1D basis (Sec. 2.1)
@@ -65,23 +65,83 @@ def shape1d(p, xi):
 
 
 # ----------------------------------------------------------------------------- geometry
-def _void(spheres, x):
-    """True where x (m, 3) lies inside some sphere (cx, cy, cz, r): the fictitious domain."""
-    out = np.zeros(len(x), dtype=bool)
-    for c0, c1, c2, r in spheres:
-        out |= (x[:, 0] - c0) ** 2 + (x[:, 1] - c1) ** 2 + (x[:, 2] - c2) ** 2 < r * r
-    return out
+class Shape:
+    """The physical domain, as for the uniform grid: the box minus sphere voids (kind 0), the solid voxels of
+    an image spanning the box (kind 1, array [z][y][x]), or the half space a.x < d (kind 2).
+
+    void(x): the fictitious domain at points x (m, 3).  cut(lo, hi): the boundary crosses the closed box:
+    spheres, min distance < r < max distance from the centre; voxels, the voxels the box overlaps are not all
+    equal; half space, min a.x < d < max a.x over the box."""
+
+    def __init__(self, kind=0, spheres=(), voxels=None, plane=(0.0, 0.0, 1.0, 2.0), lo=(0, 0, 0), hi=(1, 1, 1)):
+        self.kind = int(kind)
+        self.spheres = [tuple(float(v) for v in s) for s in spheres]
+        self.voxels = None if voxels is None else np.asarray(voxels, dtype=np.uint8)
+        self.plane = tuple(float(v) for v in plane)
+        self.lo = np.asarray(lo, dtype=np.float64)
+        self.hi = np.asarray(hi, dtype=np.float64)
+
+    @classmethod
+    def of(cls, geometry, lo=(0, 0, 0), hi=(1, 1, 1)):
+        """From a sphere list (cx, cy, cz, r) or an object with kind, spheres, voxels, plane."""
+        if isinstance(geometry, Shape):
+            return geometry
+        if hasattr(geometry, "kind"):
+            sph = geometry.spheres if geometry.spheres is not None else ()
+            return cls(geometry.kind, sph, geometry.voxels, geometry.plane, lo, hi)
+        return cls(0, geometry, lo=lo, hi=hi)
+
+    def _vox_index(self, x):
+        dims = np.array(self.voxels.shape[::-1])
+        t = (x - self.lo) / (self.hi - self.lo) * dims
+        return np.clip(np.floor(t).astype(np.int64), 0, dims - 1)
+
+    def void(self, x):
+        x = np.atleast_2d(x)
+        if self.kind == 0:
+            out = np.zeros(len(x), dtype=bool)
+            for c0, c1, c2, r in self.spheres:
+                out |= (x[:, 0] - c0) ** 2 + (x[:, 1] - c1) ** 2 + (x[:, 2] - c2) ** 2 < r * r
+            return out
+        if self.kind == 1:
+            i = self._vox_index(x)
+            return self.voxels[i[:, 2], i[:, 1], i[:, 0]] == 0
+        a = np.array(self.plane[:3])
+        return ~(x @ a < self.plane[3])
+
+    def cut(self, lo, hi):
+        lo = np.asarray(lo, dtype=np.float64)
+        hi = np.asarray(hi, dtype=np.float64)
+        if self.kind == 0:
+            for c0, c1, c2, r in self.spheres:
+                c = np.array([c0, c1, c2])
+                near = np.clip(c, lo, hi)
+                far = np.where(np.abs(c - lo) > np.abs(c - hi), lo, hi)
+                if np.linalg.norm(c - near) < r < np.linalg.norm(c - far):
+                    return True
+            return False
+        if self.kind == 1:
+            dims = np.array(self.voxels.shape[::-1])
+            h = (self.hi - self.lo) / dims
+            i0 = np.floor((lo - self.lo) / h).astype(np.int64)
+            i1 = np.ceil((hi - self.lo) / h).astype(np.int64) - 1
+            i1 = np.maximum(i1, i0)
+            i0 = np.clip(i0, 0, dims - 1)
+            i1 = np.clip(i1, 0, dims - 1)
+            sub = self.voxels[i0[2]:i1[2] + 1, i0[1]:i1[1] + 1, i0[0]:i1[0] + 1] != 0
+            return bool(sub.any() and not sub.all())
+        a = np.array(self.plane[:3])
+        mn = np.sum(np.minimum(a * lo, a * hi))
+        mx = np.sum(np.maximum(a * lo, a * hi))
+        return bool(mn < self.plane[3] < mx)
 
 
-def _box_cut(spheres, lo, hi):
-    """A sphere surface crosses the closed box [lo, hi]: min distance < r < max distance."""
-    for c0, c1, c2, r in spheres:
-        c = np.array([c0, c1, c2])
-        near = np.clip(c, lo, hi)
-        far = np.where(np.abs(c - lo) > np.abs(c - hi), lo, hi)
-        if np.linalg.norm(c - near) < r < np.linalg.norm(c - far):
-            return True
-    return False
+def _void(shape, x):
+    return shape.void(x)
+
+
+def _box_cut(shape, lo, hi):
+    return shape.cut(lo, hi)
 
 
 # ----------------------------------------------------------------------------- the hierarchy
@@ -142,9 +202,11 @@ class Hierarchy:
 
 
 def refine_toward_spheres(n, lo, hi, spheres, k):
-    """Hierarchy refined k times toward the sphere surfaces (cells the surface crosses)."""
+    """Hierarchy refined k times toward the boundary of the domain (cells the boundary crosses); `spheres` is
+    a sphere list or a geometry (see Shape.of)."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
+    spheres = Shape.of(spheres, lo, hi)
     refined = []
     cells = set(itertools.product(*[range(v) for v in n]))
     for l in range(k):
@@ -315,8 +377,9 @@ class MLProblem:
 
     def __init__(self, H, p, spheres=(), alpha=1e-8, depth=2, E=1.0, nu=0.3, traction=(0.0, 0.0, -1.0),
                  bc="clamp"):
+        """spheres: the voids (cx, cy, cz, r), or any geometry Shape.of accepts."""
         self.H, self.p, self.depth = H, int(p), int(depth)
-        self.spheres = [tuple(float(v) for v in s) for s in spheres]
+        self.spheres = Shape.of(spheres, H.lo, H.hi)
         self.alpha = float(alpha)
         self.lam = E * nu / ((1 + nu) * (1 - nu * 2))
         self.mu = E / (2 * (1 + nu))

@@ -1,6 +1,7 @@
 // Multi-level hp hierarchy and its leaf blocks: the host-side plan (Sec. 2.2, Sec. 3.2).
 //
-// A base grid of cells is refined toward sphere surfaces by superposed overlays: level l + 1 holds the 8
+// A base grid of cells is refined toward the domain boundary (sphere surfaces, a voxel image's solid-void
+// interfaces or a plane) by superposed overlays: level l + 1 holds the 8
 // children of every refined level-l cell.  Every level carries its own integrated-Legendre basis, one
 // set of modes per topological component (vertex, edge, face, cell) of the level's grid.  A level-l
 // component is active iff every in-domain level-l cell position around it exists (the overlay's
@@ -43,23 +44,6 @@ namespace {
 using I3 = std::array<int, 3>;
 
 uint64_t key3(const I3 &c) { return (uint64_t)c[0] | ((uint64_t)c[1] << 21) | ((uint64_t)c[2] << 42); }
-
-// A sphere surface crosses the closed box [lo, hi]: min distance < r < max distance from the centre.
-bool box_cut(const std::vector<std::array<double, 4>> &sph, const double lo[3], const double hi[3])
-{
-    for (const auto &s : sph) {
-        double dn = 0.0, df = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            const double c = s[a];
-            const double nr = std::min(std::max(c, lo[a]), hi[a]);
-            const double fr = std::fabs(c - lo[a]) > std::fabs(c - hi[a]) ? lo[a] : hi[a];
-            dn += (c - nr) * (c - nr);
-            df += (c - fr) * (c - fr);
-        }
-        if (std::sqrt(dn) < s[3] && s[3] < std::sqrt(df)) return true;
-    }
-    return false;
-}
 
 // 1D shape functions on [-1, 1] in the order N0, N1, phi_2..phi_p (Sec. 2.1 integrated Legendre).
 void shape1d(int p, double xi, double *f)
@@ -131,8 +115,60 @@ struct fcm_mlhp {
     int64_t n_trunk = 0;
     int nmax_full = 0, nmax_trunc = 0, maxb_full = 0, maxb_trunc = 0;
     // geometry of the refinement, kept for the assembly
+    // the physical domain: spheres (kind 0), a voxel image over the box (kind 1) or a half space (kind 2)
+    int gkind = 0;
     std::vector<double> sph;
+    std::vector<uint8_t> vox;
+    int vdim[3] = {1, 1, 1};
+    double plane[4] = {0.0, 0.0, 1.0, 2.0};
     int depth = 0;
+
+    // The boundary crosses the closed box [blo, bhi] (the refinement test): spheres, min distance < r < max
+    // distance from the centre; voxels, the voxels the box overlaps are not all equal; half space,
+    // min a.x < d < max a.x over the box.
+    bool crossed(const double *blo, const double *bhi) const
+    {
+        if (gkind == FCM_GEOM_SPHERE_VOIDS) {
+            for (size_t s4 = 0; s4 + 3 < sph.size(); s4 += 4) {
+                double dn = 0.0, df = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double c = sph[s4 + a];
+                    const double nr = std::min(std::max(c, blo[a]), bhi[a]);
+                    const double fr = std::fabs(c - blo[a]) > std::fabs(c - bhi[a]) ? blo[a] : bhi[a];
+                    dn += (c - nr) * (c - nr);
+                    df += (c - fr) * (c - fr);
+                }
+                if (std::sqrt(dn) < sph[s4 + 3] && sph[s4 + 3] < std::sqrt(df)) return true;
+            }
+            return false;
+        }
+        if (gkind == FCM_GEOM_VOXELS) {
+            int i0[3], i1[3];
+            for (int a = 0; a < 3; ++a) {
+                const double h = (hi[a] - lo[a]) / vdim[a];
+                i0[a] = (int)std::floor((blo[a] - lo[a]) / h);
+                i1[a] = (int)std::ceil((bhi[a] - lo[a]) / h) - 1;
+                if (i1[a] < i0[a]) i1[a] = i0[a];
+                i0[a] = std::min(std::max(i0[a], 0), vdim[a] - 1);
+                i1[a] = std::min(std::max(i1[a], 0), vdim[a] - 1);
+            }
+            int first = -1;
+            for (int z = i0[2]; z <= i1[2]; ++z)
+                for (int y = i0[1]; y <= i1[1]; ++y)
+                    for (int x = i0[0]; x <= i1[0]; ++x) {
+                        const int v = vox[x + (size_t)vdim[0] * (y + (size_t)vdim[1] * z)] != 0;
+                        if (first < 0) first = v;
+                        else if (v != first) return true;
+                    }
+            return false;
+        }
+        double mn = 0.0, mx = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            mn += std::min(plane[a] * blo[a], plane[a] * bhi[a]);
+            mx += std::max(plane[a] * blo[a], plane[a] * bhi[a]);
+        }
+        return mn < plane[3] && plane[3] < mx;
+    }
     // assembled system (fcm_mlhp_assemble): free DOFs 3 f + comp ascending, CSR over them, load
     bool assembled = false;
     std::vector<double> leaf_eta;
@@ -232,7 +268,7 @@ struct fcm_mlhp {
                 }
     }
 
-    void build(const std::vector<std::array<double, 4>> &sph, int k)
+    void build(int k)
     {
         std::unordered_set<uint64_t> base;
         for (int z = 0; z < n[2]; ++z)
@@ -250,7 +286,7 @@ struct fcm_mlhp {
                     blo[a] = lo[a] + c[a] * h[a];
                     bhi[a] = lo[a] + (c[a] + 1) * h[a];
                 }
-                if (!box_cut(sph, blo, bhi)) continue;
+                if (!crossed(blo, bhi)) continue;
                 R.insert(key);
                 for (int i = 0; i < 8; ++i)
                     next.insert(key3({2 * c[0] + (i & 1), 2 * c[1] + ((i >> 1) & 1), 2 * c[2] + (i >> 2)}));
@@ -343,9 +379,12 @@ struct fcm_mlhp {
         const int q = p + 1, nl = q * q * q, ne = 3 * nl;
         fcm_geometry g;
         std::memset(&g, 0, sizeof g);
-        g.kind = FCM_GEOM_SPHERE_VOIDS;
+        g.kind = gkind;
         g.nsph = (int)(sph.size() / 4);
         g.sph = sph.data();
+        g.vox = vox.data();
+        for (int a = 0; a < 3; ++a) g.vdim[a] = vdim[a];
+        for (int a = 0; a < 4; ++a) g.plane[a] = plane[a];
         g.octree_depth = depth;
         const int64_t nleaf = (int64_t)leaves.size();
         leaf_eta.assign(nleaf, 0.0);
@@ -638,9 +677,15 @@ fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p
 {
     if (!out) return FCM_EINVAL;
     *out = nullptr;
-    if (!grid || !geom || p < 1 || p > 4 || k < 0 || k > 10 || geom->kind != 0 || geom->nsph < 0 ||
-        (geom->nsph > 0 && !geom->sph) || geom->octree_depth < 0 || geom->octree_depth > 12)
+    if (!grid || !geom || p < 1 || p > 4 || k < 0 || k > 10 || geom->octree_depth < 0 || geom->octree_depth > 12)
         return FCM_EINVAL;
+    if (geom->kind == FCM_GEOM_SPHERE_VOIDS) {
+        if (geom->nsph < 0 || (geom->nsph > 0 && !geom->sph)) return FCM_EINVAL;
+    } else if (geom->kind == FCM_GEOM_VOXELS) {
+        if (!geom->vox || geom->vdim[0] < 1 || geom->vdim[1] < 1 || geom->vdim[2] < 1) return FCM_EINVAL;
+    } else if (geom->kind != FCM_GEOM_HALFSPACE) {
+        return FCM_EINVAL;
+    }
     for (int a = 0; a < 3; ++a) {
         if (grid->n[a] < 1 || ((int64_t)grid->n[a] << k) >= (1 << 20) || !(grid->hi[a] > grid->lo[a])) return FCM_EINVAL;
     }
@@ -653,12 +698,15 @@ fcm_status fcm_mlhp_create(const fcm_grid *grid, const fcm_geometry *geom, int p
             h->hi[a] = grid->hi[a];
         }
         h->p = p;
-        std::vector<std::array<double, 4>> sph(geom->nsph);
-        for (int i = 0; i < geom->nsph; ++i)
-            for (int j = 0; j < 4; ++j) sph[i][j] = geom->sph[4 * i + j];
-        h->sph.assign(geom->sph, geom->sph + 4 * (size_t)geom->nsph);
+        h->gkind = geom->kind;
+        if (geom->kind == FCM_GEOM_SPHERE_VOIDS) h->sph.assign(geom->sph, geom->sph + 4 * (size_t)geom->nsph);
+        if (geom->kind == FCM_GEOM_VOXELS) {
+            for (int a = 0; a < 3; ++a) h->vdim[a] = geom->vdim[a];
+            h->vox.assign(geom->vox, geom->vox + (size_t)geom->vdim[0] * geom->vdim[1] * geom->vdim[2]);
+        }
+        for (int a = 0; a < 4; ++a) h->plane[a] = geom->plane[a];
         h->depth = geom->octree_depth;
-        h->build(sph, k);
+        h->build(k);
     } catch (...) {
         delete h;
         return FCM_ENOMEM;

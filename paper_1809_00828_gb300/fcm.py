@@ -476,18 +476,26 @@ class MLHPPlan:
     (rows cx, cy, cz, r), basis order p; the spheres are also the voids of `assemble`, integrated with
     an octree of `octree_depth` levels per leaf.  Host memory only; no device is needed."""
 
-    def __init__(self, n, lo, hi, spheres, p, k, octree_depth=3):
+    def __init__(self, n, lo, hi, spheres, p, k, octree_depth=3, geometry=None):
+        """geometry (an inputs.Geometry: spheres, voxels or a half space) replaces `spheres` when given."""
         L = load()
         g = Grid()
         g.n[:] = list(n)
         g.lo[:] = list(lo)
         g.hi[:] = list(hi)
         geo = Geometry()
-        geo.kind = 0
+        geo.kind = 0 if geometry is None else geometry.kind
         geo.octree_depth = octree_depth
-        self._sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+        sph = spheres if geometry is None else geometry.sphere_array()
+        self._sph = np.ascontiguousarray(np.asarray(sph, dtype=np.float64).reshape(-1, 4))
         geo.nsph = self._sph.shape[0]
         geo.sph = self._sph.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if geometry is not None and geometry.voxels is not None:
+            self._vox = np.ascontiguousarray(geometry.voxels, dtype=np.uint8)
+            geo.vdim[:] = [self._vox.shape[2], self._vox.shape[1], self._vox.shape[0]]
+            geo.vox = self._vox.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        if geometry is not None:
+            geo.plane[:] = list(geometry.plane)
         self.p = p
         self.h = ctypes.c_void_p()
         st = L.fcm_mlhp_create(ctypes.byref(g), ctypes.byref(geo), p, k, ctypes.byref(self.h))

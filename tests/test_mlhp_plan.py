@@ -222,3 +222,32 @@ def test_porous_hierarchy_overlap_grows_like_the_paper_table_for_full_blocks_onl
         P.close()
     assert full[0] == 8
     assert all(b > 2.5 * a for a, b in zip(full, full[1:]))
+
+
+@pytest.mark.parametrize("which", ["voxels", "halfspace"])
+def test_voxel_and_halfspace_hierarchies_match_the_oracle(which):
+    # The plan refines toward any boundary the uniform grid supports: a voxel image's solid-void interfaces
+    # (a 16^3 Gaussian random field, as for the trabecular workloads) or a tilted plane.  Hierarchy, blocks
+    # and the assembled system against the oracle.
+    from paper_1809_00828_gb300 import inputs as I
+    if which == "voxels":
+        g = I.gaussian_random_field_voxels(3, m=16, corr_len=0.15, solid_fraction=0.5, octree_depth=2)
+        n, k = (4, 4, 4), 2
+    else:
+        g = I.halfspace(1.0, 0.3, 0.2, 0.81, octree_depth=2)
+        n, k = (3, 3, 3), 1
+    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), None, 2, k, octree_depth=2, geometry=g)
+    H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), g, k)
+    assert all(len(r) > 0 for r in H.refined[:k])
+    B = M.Basis(H, 2)
+    assert [P.leaf(i) for i in range(len(H.leaves))] == [(l, tuple(c)) for l, c in H.leaves]
+    for i, (L, c) in enumerate(H.leaves):
+        assert P.block(i, "truncated").tolist() == B.truncated_functions(L, c)
+    assert P.info["n_max_truncated"] <= 8
+    free, K, rhs, eta = P.assemble(1e-6, "clamp")
+    Q = M.MLProblem(H, 2, g, alpha=1e-6, depth=2)
+    assert np.array_equal(free, Q.free)
+    assert abs(K - Q.K).max() <= 1e-13 * abs(Q.K).max()
+    assert np.abs(rhs - Q.b).max() <= 1e-13 * np.abs(Q.b).max()
+    assert max(abs(eta[i] - Q.eta[lc]) for i, lc in enumerate(H.leaves)) < 1e-13
+    P.close()
