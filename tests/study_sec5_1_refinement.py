@@ -4,7 +4,8 @@ full and with truncated leaf blocks, and their overlap n_max.
 
 Not a test (it takes minutes): run it with `python tests/study_sec5_1_refinement.py [K] [alpha] [porous]`;
 `porous` swaps the cube for a porous cube (10 voids, 4^3 base cells, p = 2) refined toward its void
-surfaces, the analogue of the paper's gearbox study (Sec. 5.3).  The
+surfaces, the analogue of the paper's gearbox study (Sec. 5.3); `voxels` for a trabecular-like voxel image
+(32^3 Gaussian random field, half solid, 4^3 base cells, p = 2) refined toward its surface.  The
 system comes from the library's host assembly (fcm_mlhp_assemble) and its block lists (fcm_mlhp_block);
 the pseudo inverses and the PCG are plain numpy, as in the multi-level oracle.  Differences from the
 paper's set-up: the full tensor-product basis instead of the trunk space, a clamped base and a traction
@@ -30,8 +31,11 @@ CUBE = ((8, 8, 8), [(0.5, 0.5, 0.5, 0.01)], 3)
 
 
 def study(k, alpha=1e-8, setup=CUBE, tol=1e-8, maxit=5000):
-    n, spheres, p = setup
-    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), spheres, p, k, octree_depth=3)
+    n, geometry, p = setup
+    if hasattr(geometry, "kind"):
+        P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), None, p, k, octree_depth=3, geometry=geometry)
+    else:
+        P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), geometry, p, k, octree_depth=3)
     free, K, b, eta = P.assemble(alpha, "clamp")
     pos = -np.ones(3 * P.info["n_functions"], dtype=np.int64)
     pos[free] = np.arange(len(free))
@@ -92,6 +96,10 @@ if __name__ == "__main__":
         # a porous cube refined toward its void surfaces, as the paper's gearbox is refined toward its pores
         from paper_1809_00828_gb300 import inputs as I
         setup = ((4, 4, 4), I.random_sphere_voids(11, 10, 0.05, 0.15).sphere_array(), 2)
+    if len(sys.argv) > 3 and sys.argv[3] == "voxels":
+        # a trabecular-like voxel image (32^3 Gaussian random field, half solid) refined toward its surface
+        from paper_1809_00828_gb300 import inputs as I
+        setup = ((4, 4, 4), I.gaussian_random_field_voxels(3, m=32, corr_len=0.1, solid_fraction=0.5), 2)
     for k in range(K + 1):
         t = time.time()
         print(study(k, alpha, setup), f"{time.time() - t:.0f} s", flush=True)
