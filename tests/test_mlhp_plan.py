@@ -251,3 +251,26 @@ def test_voxel_and_halfspace_hierarchies_match_the_oracle(which):
     assert np.abs(rhs - Q.b).max() <= 1e-13 * np.abs(Q.b).max()
     assert max(abs(eta[i] - Q.eta[lc]) for i, lc in enumerate(H.leaves)) < 1e-13
     P.close()
+
+
+def test_random_hierarchies_match_the_oracle():
+    # Seeded random cases: boxes that are not cubes, spheres that cross the domain boundary, p = 1..4,
+    # k = 0..3.  Leaves, functions, every full and truncated block, and n_max against the oracle.
+    rng = np.random.default_rng(123)
+    for _ in range(25):
+        n = tuple(int(v) for v in rng.integers(1, 4, 3))
+        p = int(rng.integers(1, 5))
+        k = int(rng.integers(0, 4))
+        sph = [tuple(float(v) for v in (*rng.uniform(-0.2, 1.2, 3), rng.uniform(0.05, 0.5)))
+               for _ in range(int(rng.integers(1, 4)))]
+        hi = tuple(float(v) for v in rng.uniform(0.5, 2.0, 3))
+        P = fcm.MLHPPlan(n, (0, 0, 0), hi, sph, p, k)
+        H = M.refine_toward_spheres(n, (0, 0, 0), hi, sph, k)
+        B = M.Basis(H, p)
+        assert [P.leaf(i) for i in range(P.info["n_leaves"])] == [(l, tuple(c)) for l, c in H.leaves]
+        assert P.info["n_functions"] == len(B.funcs)
+        for i, (L, c) in enumerate(H.leaves):
+            assert P.block(i, "full").tolist() == B.leaf_functions(L, c)
+            assert P.block(i, "truncated").tolist() == B.truncated_functions(L, c)
+        assert P.info["n_max_truncated"] == B.overlap("truncated") <= 8
+        P.close()
