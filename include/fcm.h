@@ -325,9 +325,12 @@ fcm_status fcm_fpcg_solve_host(fcm_ctx *ctx, fcm_unet *net, double gamma, int co
  *   - Returns FCM_EINVAL when n_lattice > FCM_NOALLOC_MAX_LATTICE, FCM_ESTATE
  *     before fcm_precond_build.
  *   - All calls on a device share the one array; calls that overlap on the
- *     GPU (different streams or contexts) race on it.
- *   - The first call on each device looks up the array's address
- *     (cudaGetSymbolAddress); make it before any stream capture. */
+ *     GPU (different streams or contexts) race on it.  Each call overwrites
+ *     every entry it reads, so nothing needs clearing between calls.
+ *   - fcm_precond_build looks the array's device address up
+ *     (cudaGetSymbolAddress, with the context's device current, outside any
+ *     capture) and keeps it in the context; this call only launches work.
+ *     FCM_ECUDA if that lookup failed. */
 fcm_status fcm_apply_S_noalloc(fcm_ctx *ctx, const double *r_dev, double *z_dev);
 
 /* ---- Multi-level hp overlays (Sec. 2.2) and their leaf blocks (Sec. 3.2) -------------------------------
@@ -419,7 +422,8 @@ fcm_status fcm_mlhp_factors(const fcm_mlhp *plan, int64_t *blk_ptr, int64_t *blk
  * FCM_ESTATE); every index is checked on the host first (FCM_EINVAL).  The device arrays belong to the plan
  * until fcm_mlhp_destroy or the next assemble / factorize.  Work is queued on cuda_stream. */
 fcm_status fcm_mlhp_device_setup(fcm_mlhp *plan, void *cuda_stream);
-/* y_dev = K x_dev over the free DOFs (device arrays of n_free doubles; one warp per CSR row). */
+/* y_dev = K x_dev over the free DOFs (device arrays of n_free doubles; one warp per CSR row).
+ * x_dev and y_dev must differ (FCM_EINVAL): warps write y while others still read x. */
 fcm_status fcm_mlhp_apply_K(fcm_mlhp *plan, const double *x_dev, double *y_dev);
 /* z_dev = S r_dev (Eq. (5)): the diagonal part, then one launch per colour of blocks, z_B += A_B^+ r_B.
  * r_dev and z_dev must differ. */
@@ -429,6 +433,10 @@ fcm_status fcm_mlhp_apply_S(fcm_mlhp *plan, const double *r_dev, double *z_dev);
  * (p.Kp <= 0 or a non-finite scalar).  Synchronises the stream. */
 fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *plan, const double *b_dev, double tol, int maxit, double *u_dev, int *iterations,
                               double *relres);
+/* Message of the last failed device call on the plan (fcm_mlhp_device_setup, the applies, the PCG): the
+ * CUDA error or the rejected input; "" when none.  Device set-up returns FCM_ENOMEM when an allocation
+ * fails, FCM_ECUDA for other CUDA failures and FCM_EINVAL for a rejected index. */
+const char *fcm_mlhp_last_error(const fcm_mlhp *plan);
 void fcm_mlhp_destroy(fcm_mlhp *plan);
 
 /* Message of the last failure on ctx (ctx may be NULL for setup failures). */

@@ -235,6 +235,7 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
         C->g.M[a] = hp.M[a];
     }
     C->ustream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&C->device);
     auto fail = [&](cudaError_t ce, const char *what) {
         g_setup_error = std::string("fcm_setup: ") + what + ": " + cudaGetErrorString(ce);
         free_ctx(C);
@@ -431,6 +432,19 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     if (!e.empty()) {
         C->err = "fcm_precond_build: " + e;
         return e.find("out of memory") != std::string::npos ? FCM_ENOMEM : FCM_ECUDA;
+    }
+    // address of fcm_apply_S_noalloc's static scratch on this context's device (looked up here, at
+    // set-up and outside any capture, so that the allocation-free call itself only launches)
+    C->noalloc_scratch = nullptr;
+    C->noalloc_err.clear();
+    int dev = -1;
+    if (C->nlat > (int64_t)FCM_NOALLOC_MAX_LATTICE) {
+        C->noalloc_err = "problem larger than FCM_NOALLOC_MAX_LATTICE";
+    } else if (cudaGetDevice(&dev) != cudaSuccess || dev != C->device) {
+        C->noalloc_err = "the context's device is not current";
+    } else {
+        const cudaError_t ce = fcm::noalloc_scratch_address(&C->noalloc_scratch);
+        if (ce != cudaSuccess) C->noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ce);
     }
     return FCM_OK;
 }

@@ -106,6 +106,8 @@ void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *
                                 const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
                                 cudaStream_t s);
 void launch_mask_copy(const double *in, double *out, const uint8_t *mask, int64_t n, cudaStream_t s);
+// fcm_noalloc.cu: device address of the static scratch of fcm_apply_S_noalloc on the current device
+cudaError_t noalloc_scratch_address(double **out);
 void launch_zero(double *v, int64_t n, const int *done, cudaStream_t s);
 
 // CG building blocks (fcm_solver.cu)
@@ -186,6 +188,9 @@ struct fcm_ctx {
     int2 *d_batches = nullptr;
     double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
     int *d_err = nullptr;            // set by a Schwarz CTA whose bulk-copy wait ran out
+    double *noalloc_scratch = nullptr;  // device address of fcm_apply_S_noalloc's static scratch
+    std::string noalloc_err;            // why it is null (problem too large, or the lookup failed)
+    int device = 0;                     // CUDA device current at fcm_setup
     int fcg_window = 100;            // stall window of the flexible CG (fcm_fpcg_set_stall_window)
     double tune_seconds[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // S-apply times of the launch shapes tried
     int64_t n_jacobi = 0;

@@ -103,6 +103,7 @@ void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &lam, std::
 }  // namespace
 
 struct fcm_mlhp {
+    std::string err;  // message of the last failed device call (fcm_mlhp_last_error)
     int n[3] = {0, 0, 0};
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     int p = 0, levels = 0;
@@ -888,7 +889,11 @@ fcm_status fcm_mlhp_factors(const fcm_mlhp *h, int64_t *blk_ptr, int64_t *blk_do
 fcm_status fcm_mlhp_device_setup(fcm_mlhp *h, void *cuda_stream)
 {
     if (!h) return FCM_EINVAL;
-    if (!h->factorized) return FCM_ESTATE;
+    h->err.clear();
+    if (!h->factorized) {
+        h->err = "fcm_mlhp_device_setup: call fcm_mlhp_factorize first";
+        return FCM_ESTATE;
+    }
     fcm::mlhp_device_destroy(h->dev);
     h->dev = nullptr;
     try {
@@ -896,9 +901,18 @@ fcm_status fcm_mlhp_device_setup(fcm_mlhp *h, void *cuda_stream)
             cuda_stream, (int64_t)h->free_dofs.size(), h->rowptr.data(), h->cols.data(), h->vals.data(),
             (int64_t)h->blk_ptr.size() - 1, h->blk_ptr.data(), h->blk_dofs.data(), h->fac_ptr.data(), h->factors.data(),
             (int)h->colour_ptr.size() - 1, h->colour_ptr.data(), h->jacobi.data(), &h->dev);
-        if (!e.empty()) return e.rfind("upload", 0) == 0 || e.rfind("cudaMalloc", 0) == 0 ? FCM_ECUDA : FCM_EINVAL;
-    } catch (...) {
+        if (!e.empty()) {
+            h->err = "fcm_mlhp_device_setup: " + e;
+            // CUDA failures carry the call's name in front; an allocation failure reads "out of memory"
+            if (e.find("out of memory") != std::string::npos) return FCM_ENOMEM;
+            return e.rfind("upload", 0) == 0 || e.rfind("cudaMalloc", 0) == 0 ? FCM_ECUDA : FCM_EINVAL;
+        }
+    } catch (const std::bad_alloc &) {
+        h->err = "fcm_mlhp_device_setup: out of host memory";
         return FCM_ENOMEM;
+    } catch (...) {
+        h->err = "fcm_mlhp_device_setup: host failure";
+        return FCM_ECUDA;
     }
     return FCM_OK;
 }
@@ -906,15 +920,27 @@ fcm_status fcm_mlhp_device_setup(fcm_mlhp *h, void *cuda_stream)
 fcm_status fcm_mlhp_apply_K(fcm_mlhp *h, const double *x_dev, double *y_dev)
 {
     if (!h || !x_dev || !y_dev) return FCM_EINVAL;
+    if (x_dev == y_dev) {
+        h->err = "fcm_mlhp_apply_K: x_dev and y_dev must differ";
+        return FCM_EINVAL;
+    }
     if (!h->dev) return FCM_ESTATE;
-    return fcm::mlhp_device_apply_K(h->dev, x_dev, y_dev).empty() ? FCM_OK : FCM_ECUDA;
+    const std::string e = fcm::mlhp_device_apply_K(h->dev, x_dev, y_dev);
+    if (!e.empty()) h->err = "fcm_mlhp_apply_K: " + e;
+    return e.empty() ? FCM_OK : FCM_ECUDA;
 }
 
 fcm_status fcm_mlhp_apply_S(fcm_mlhp *h, const double *r_dev, double *z_dev)
 {
-    if (!h || !r_dev || !z_dev || r_dev == z_dev) return FCM_EINVAL;
+    if (!h || !r_dev || !z_dev) return FCM_EINVAL;
+    if (r_dev == z_dev) {
+        h->err = "fcm_mlhp_apply_S: r_dev and z_dev must differ";
+        return FCM_EINVAL;
+    }
     if (!h->dev) return FCM_ESTATE;
-    return fcm::mlhp_device_apply_S(h->dev, r_dev, z_dev).empty() ? FCM_OK : FCM_ECUDA;
+    const std::string e = fcm::mlhp_device_apply_S(h->dev, r_dev, z_dev);
+    if (!e.empty()) h->err = "fcm_mlhp_apply_S: " + e;
+    return e.empty() ? FCM_OK : FCM_ECUDA;
 }
 
 fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *h, const double *b_dev, double tol, int maxit, double *u_dev, int *iterations,
@@ -923,9 +949,15 @@ fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *h, const double *b_dev, double tol, int 
     if (!h || !b_dev || !u_dev || !iterations || !relres || maxit < 0 || !(tol >= 0.0)) return FCM_EINVAL;
     if (!h->dev) return FCM_ESTATE;
     int status = 0;
-    if (!fcm::mlhp_device_pcg(h->dev, b_dev, tol, maxit, u_dev, iterations, relres, &status).empty()) return FCM_ECUDA;
+    const std::string e = fcm::mlhp_device_pcg(h->dev, b_dev, tol, maxit, u_dev, iterations, relres, &status);
+    if (!e.empty()) {
+        h->err = "fcm_mlhp_pcg_solve: " + e;
+        return FCM_ECUDA;
+    }
     return status == 0 ? FCM_OK : status == 1 ? FCM_ENOTCONV : FCM_EBREAKDOWN;
 }
+
+const char *fcm_mlhp_last_error(const fcm_mlhp *h) { return h ? h->err.c_str() : ""; }
 
 void fcm_mlhp_destroy(fcm_mlhp *h) { delete h; }
 

@@ -17,12 +17,12 @@
 //     call's contents; each call overwrites every entry it reads, so nothing
 //     has to be cleared, but calls that overlap on the GPU (two streams, or
 //     two contexts on different streams) race on it;
-//   * the first call on each device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current); make that first call
-//     before any stream capture.
+//   * host code cannot use the array's name as a device address (in host code
+//     it names a host-side shadow).  fcm_precond_build looks the device
+//     address up with cudaGetSymbolAddress, with the context's device current
+//     and outside any stream capture, and keeps it in the context, so the
+//     address lives exactly as long as the context's own device allocations.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "fcm_device.cuh"
 
@@ -30,29 +30,20 @@ namespace {
 
 static __device__ __align__(256) double g_noalloc_scratch[FCM_NOALLOC_MAX_LATTICE];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+}  // namespace
 
-// Device address of the scratch array on the current device (looked up once per device).
-cudaError_t scratch_for_current_device(double **out)
+namespace fcm {
+
+// Device address of the scratch array on the current device.
+cudaError_t noalloc_scratch_address(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_ptr[dev];
-    return cudaSuccess;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    *out = e == cudaSuccess ? static_cast<double *>(p) : nullptr;
+    return e;
 }
 
-}  // namespace
+}  // namespace fcm
 
 extern "C" fcm_status fcm_apply_S_noalloc(fcm_ctx *C, const double *r_dev, double *z_dev)
 {
@@ -67,10 +58,10 @@ extern "C" fcm_status fcm_apply_S_noalloc(fcm_ctx *C, const double *r_dev, doubl
                  std::to_string((long long)FCM_NOALLOC_MAX_LATTICE) + "); use fcm_apply_S";
         return FCM_EINVAL;
     }
-    double *scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
-    if (e != cudaSuccess) {
-        C->err = std::string("fcm_apply_S_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    double *scratch = C->noalloc_scratch;
+    if (!scratch) {
+        C->err = "fcm_apply_S_noalloc: the static scratch address was not found at fcm_precond_build (" +
+                 C->noalloc_err + ")";
         return FCM_ECUDA;
     }
     cudaEventRecord(C->ev_in, C->ustream);
@@ -78,7 +69,7 @@ extern "C" fcm_status fcm_apply_S_noalloc(fcm_ctx *C, const double *r_dev, doubl
     fcm::launch_mask_copy(r_dev, scratch, C->d_mask, C->nlat, C->stream);
     fcm::launch_schwarz_apply(C->p, C->g, scratch, z_dev, C->d_f64, C->d_f32, C->plan,
                               nullptr, C->stream);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     cudaEventRecord(C->ev_out, C->stream);
     cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
     if (e != cudaSuccess) {

@@ -29,7 +29,7 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size",
             "fcm_mlhp_system",
             "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
-            "fcm_mlhp_apply_K", "fcm_mlhp_apply_S", "fcm_mlhp_pcg_solve", "fcm_mlhp_destroy")
+            "fcm_mlhp_apply_K", "fcm_mlhp_apply_S", "fcm_mlhp_pcg_solve", "fcm_mlhp_last_error", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -135,16 +135,52 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_pcg_solve.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
     L.fcm_mlhp_destroy.argtypes = [P]
     L.fcm_mlhp_destroy.restype = None
+    L.fcm_mlhp_last_error.argtypes = [P]
     for f in EXPORTED:
-        if f not in ("fcm_last_error", "fcm_destroy", "fcm_unet_destroy", "fcm_mlhp_destroy"):
+        if f not in ("fcm_last_error", "fcm_destroy", "fcm_unet_destroy", "fcm_mlhp_destroy", "fcm_mlhp_last_error"):
             getattr(L, f).restype = ctypes.c_int
     L.fcm_destroy.restype = None
+    L.fcm_mlhp_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
 
-def _ptr(t):
+def _dev(t, n, dtype="float64", device=None, what="vector", multiple=False):
+    """Device pointer of tensor t, after checking what the kernels will index through it.
+
+    The C ABI receives a bare pointer and cannot see a tensor's type or extent, so a wrong
+    tensor would be read or written out of bounds on the device.  Checked here: a torch
+    tensor of `dtype`, contiguous, with exactly n elements (a positive multiple of n when
+    `multiple`), on the CUDA device `device` (any CUDA device when None).  ValueError otherwise.
+    """
+    import torch
+    want = getattr(torch, dtype)
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{what}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != want:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {want}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor is not contiguous")
+    k = t.numel()
+    if (multiple and (k == 0 or k % n != 0)) or (not multiple and k != n):
+        raise ValueError(f"{what}: {k} elements, expected {'a positive multiple of ' if multiple else ''}{n}")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: a CUDA tensor is required, got one on {t.device}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{what}: tensor on cuda:{t.device.index}, the context lives on cuda:{device}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_vec(a, n, what, multiple=False, writable=False):
+    """The same checks for a host numpy buffer handed to a *_host entry point: float64,
+    C-contiguous, n elements (or a positive multiple), writable for outputs."""
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what}: expected a C-contiguous float64 numpy array")
+    if (multiple and (a.size == 0 or a.size % n != 0)) or (not multiple and a.size != n):
+        raise ValueError(f"{what}: {a.size} elements, expected {'a positive multiple of ' if multiple else ''}{n}")
+    if writable and not a.flags["WRITEABLE"]:
+        raise ValueError(f"{what}: array is read-only")
+    return a
 
 
 class Solver:
@@ -182,8 +218,12 @@ class Solver:
         if st != FCM_OK:
             raise FcmError(st, L.fcm_last_error(None).decode())
         self.workload = w
+        self.device = torch.cuda.current_device()
         self.info = self.get_info()
         self.n = self.info["n_lattice"]
+
+    def _vec(self, t, what, nrhs=1, multiple=False):
+        return _dev(t, self.n * nrhs, device=self.device, what=what, multiple=multiple)
 
     def _check(self, st):
         if st != FCM_OK:
@@ -199,7 +239,7 @@ class Solver:
 
     def rhs(self, load_case=0):
         b = self.empty()
-        self._check(load().fcm_rhs(self.ctx, load_case, _ptr(b)))
+        self._check(load().fcm_rhs(self.ctx, load_case, self._vec(b, "b")))
         return b
 
     def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0,
@@ -222,18 +262,22 @@ class Solver:
         self.info = self.get_info()
 
     def pcg_solve(self, b, tol, maxit=100000, out=None, check=True):
+        pb = self._vec(b, "b", multiple=True)
         nrhs = b.numel() // self.n
         u = out if out is not None else self.empty(nrhs)
+        pu = self._vec(u, "out", nrhs)
         its = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
-        st = load().fcm_pcg_solve(self.ctx, _ptr(b), nrhs, tol, maxit, _ptr(u), ctypes.byref(its), ctypes.byref(rel))
+        st = load().fcm_pcg_solve(self.ctx, pb, nrhs, tol, maxit, pu, ctypes.byref(its), ctypes.byref(rel))
         if check:
             self._check(st)
         return u, its.value, rel.value, st
 
     def pcg_solve_host(self, b_host: np.ndarray, tol, maxit=100000, out: np.ndarray | None = None):
+        b_host = _host_vec(b_host, self.n, "b_host", multiple=True)
         nrhs = b_host.size // self.n
         u = out if out is not None else np.empty_like(b_host)
+        u = _host_vec(u, self.n * nrhs, "out", writable=True)
         its = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
         st = load().fcm_pcg_solve_host(self.ctx, ctypes.c_void_p(b_host.ctypes.data), nrhs, tol, maxit,
@@ -248,12 +292,12 @@ class Solver:
 
     def apply_K(self, x, out=None):
         y = out if out is not None else self.empty()
-        self._check(load().fcm_apply_K(self.ctx, _ptr(x), _ptr(y)))
+        self._check(load().fcm_apply_K(self.ctx, self._vec(x, "x"), self._vec(y, "out")))
         return y
 
     def apply_S(self, r, out=None):
         z = out if out is not None else self.empty()
-        self._check(load().fcm_apply_S(self.ctx, _ptr(r), _ptr(z)))
+        self._check(load().fcm_apply_S(self.ctx, self._vec(r, "r"), self._vec(z, "out")))
         return z
 
     def close(self):
@@ -347,19 +391,24 @@ class UNet:
         _unet_check(load().fcm_unet_set(self.h, ctypes.c_void_p(w.ctypes.data)))
 
     def forward(self, x, out=None):
+        if x.dim() != 5 or x.shape[1] != self.desc[0]:
+            raise ValueError(f"input: expected [batch][{self.desc[0]}][z][y][x], got shape {tuple(x.shape)}")
         B, C, Z, Y, X = x.shape
         if out is None:
             out = self._torch.empty((B, self.desc[1], Z, Y, X), dtype=self._torch.float32, device=x.device)
-        _unet_check(load().fcm_unet_forward(self.h, _ptr(x), B, X, Y, Z, _ptr(out)))
+        px = _dev(x, x.numel(), "float32", what="input")
+        po = _dev(out, B * self.desc[1] * Z * Y * X, "float32", device=x.device.index, what="out")
+        self._shape = (B, Z, Y, X)
+        _unet_check(load().fcm_unet_forward(self.h, px, B, X, Y, Z, po))
         return out
 
     def backward(self, gout, want_din=False):
+        B, Z, Y, X = getattr(self, "_shape", (0, 0, 0, 0))
+        pg = _dev(gout, B * self.desc[1] * Z * Y * X, "float32", what="gradient of the output (after forward)")
         din = None
         if want_din:
-            shp = list(gout.shape)
-            shp[1] = self.desc[0]
-            din = self._torch.empty(shp, dtype=self._torch.float32, device=gout.device)
-        _unet_check(load().fcm_unet_backward(self.h, _ptr(gout), _ptr(din) if want_din else None))
+            din = self._torch.empty((B, self.desc[0], Z, Y, X), dtype=self._torch.float32, device=gout.device)
+        _unet_check(load().fcm_unet_backward(self.h, pg, _dev(din, din.numel(), "float32") if want_din else None))
         return din
 
     def zero_grad(self):
@@ -367,28 +416,6 @@ class UNet:
 
     def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         _unet_check(load().fcm_unet_adam(self.h, lr, beta1, beta2, eps, step))
-
-    def assemble(self, alpha, bc_kind="clamp", E=1.0, nu=0.3, traction=(0.0, 0.0, -1.0)):
-        """Assemble the system on the host; returns (free_dofs, K as scipy CSR, rhs, leaf_eta)."""
-        import scipy.sparse as sp
-        bc = BC()
-        bc.E, bc.nu = E, nu
-        bc.bc = {"none": -1, "clamp": 0, "roller": 1}[bc_kind]
-        bc.traction[:] = list(traction)
-        L = load()
-        self._check(L.fcm_mlhp_assemble(self.h, alpha, ctypes.byref(bc)))
-        nf, nnz = ctypes.c_int64(), ctypes.c_int64()
-        self._check(L.fcm_mlhp_system_size(self.h, ctypes.byref(nf), ctypes.byref(nnz)))
-        free = np.zeros(nf.value, dtype=np.int64)
-        rowptr = np.zeros(nf.value + 1, dtype=np.int64)
-        cols = np.zeros(nnz.value, dtype=np.int64)
-        vals = np.zeros(nnz.value)
-        rhs = np.zeros(nf.value)
-        eta = np.zeros(self.info["n_leaves"])
-        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
-        self._check(L.fcm_mlhp_system(self.h, ptr(free), ptr(rowptr), ptr(cols), ptr(vals), ptr(rhs), ptr(eta)))
-        K = sp.csr_matrix((vals, cols, rowptr), shape=(nf.value, nf.value))
-        return free, K, rhs, eta
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
@@ -407,14 +434,19 @@ def _solver_coarse_restrict(self, v, s=1.0, eta_channel=True, out=None):
     nc = self.workload.n[0] * self.workload.n[1] * self.workload.n[2]
     if out is None:
         out = self._torch.empty((4 if eta_channel else 3) * nc, dtype=self._torch.float32, device="cuda")
-    self._check(load().fcm_coarse_restrict(self.ctx, _ptr(v), s, 1 if eta_channel else 0, _ptr(out)))
+    po = _dev(out, (4 if eta_channel else 3) * nc, "float32", device=self.device, what="out")
+    self._check(load().fcm_coarse_restrict(self.ctx, self._vec(v, "v"), s, 1 if eta_channel else 0, po))
     return out
 
 
 def _solver_coarse_prolong(self, cells, s=1.0, out=None):
     _bind_unet(load())
     y = out if out is not None else self.empty()
-    self._check(load().fcm_coarse_prolong(self.ctx, _ptr(cells), s, _ptr(y)))
+    nc = self.workload.n[0] * self.workload.n[1] * self.workload.n[2]
+    pc = _dev(cells, 3 * nc, "float32", device=self.device, what="cells", multiple=True)
+    if cells.numel() not in (3 * nc, 4 * nc):
+        raise ValueError(f"cells: {cells.numel()} elements, expected {3 * nc} (or {4 * nc} with the eta channel)")
+    self._check(load().fcm_coarse_prolong(self.ctx, pc, s, self._vec(y, "out")))
     return y
 
 
@@ -422,7 +454,9 @@ def _solver_coarse_apply(self, x, out=None):
     """y = K_H x on cell vectors (3 * n_cells floats, component-major)."""
     _bind_unet(load())
     y = out if out is not None else self._torch.empty_like(x)
-    self._check(load().fcm_coarse_apply(self.ctx, _ptr(x), _ptr(y)))
+    nc = self.workload.n[0] * self.workload.n[1] * self.workload.n[2]
+    px = _dev(x, 3 * nc, "float32", device=self.device, what="x")
+    self._check(load().fcm_coarse_apply(self.ctx, px, _dev(y, 3 * nc, "float32", device=self.device, what="out")))
     return y
 
 
@@ -432,8 +466,9 @@ def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=T
     u = out if out is not None else self.empty()
     its = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
-    st = load().fcm_fpcg_solve(self.ctx, net.h if net is not None else None, gamma, coarse_iters, _ptr(b), tol,
-                               maxit, _ptr(u), ctypes.byref(its), ctypes.byref(rel))
+    st = load().fcm_fpcg_solve(self.ctx, net.h if net is not None else None, gamma, coarse_iters,
+                               self._vec(b, "b"), tol, maxit, self._vec(u, "out"), ctypes.byref(its),
+                               ctypes.byref(rel))
     if check:
         self._check(st)
     return u, its.value, rel.value, st
@@ -442,8 +477,8 @@ def _solver_fpcg_solve(self, net, gamma, b, tol, maxit=100000, out=None, check=T
 def _solver_fpcg_solve_host(self, net, gamma, b_host, tol, maxit=100000, out=None, check=True, coarse_iters=0):
     """fpcg_solve with host numpy buffers (float64, n_lattice); copies are inside the call."""
     _bind_unet(load())
-    b_host = np.ascontiguousarray(b_host, dtype=np.float64)
-    u = out if out is not None else np.empty_like(b_host)
+    b_host = _host_vec(np.ascontiguousarray(b_host, dtype=np.float64), self.n, "b_host")
+    u = _host_vec(out if out is not None else np.empty_like(b_host), self.n, "out", writable=True)
     its = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
     st = load().fcm_fpcg_solve_host(self.ctx, net.h if net is not None else None, gamma, coarse_iters,
@@ -505,10 +540,10 @@ class MLHPPlan:
         self._check(L.fcm_mlhp_get_info(self.h, ctypes.byref(inf)))
         self.info = {k2: getattr(inf, k2) for k2, _ in MLHPInfo._fields_}
 
-    @staticmethod
-    def _check(st):
+    def _check(self, st):
         if st != FCM_OK:
-            raise FcmError(st, "fcm_mlhp")
+            msg = load().fcm_mlhp_last_error(self.h) if getattr(self, "h", None) else b""
+            raise FcmError(st, "fcm_mlhp: " + (msg.decode() if msg else "failed"))
 
     def leaf(self, i):
         lv = ctypes.c_int()
@@ -600,17 +635,26 @@ class MLHPPlan:
             stream = torch.cuda.current_stream().cuda_stream
         self._stream = stream
         self._check(load().fcm_mlhp_device_setup(self.h, ctypes.c_void_p(stream)))
+        nf, nnz = ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().fcm_mlhp_system_size(self.h, ctypes.byref(nf), ctypes.byref(nnz)))
+        self._nfree = nf.value
+        self._device = torch.cuda.current_device()
+
+    def _vec(self, t, what):
+        if getattr(self, "_nfree", None) is None:
+            raise RuntimeError("call device_setup first")
+        return _dev(t, self._nfree, device=self._device, what=what)
 
     def apply_K(self, x, out=None):
         import torch
         y = out if out is not None else torch.empty_like(x)
-        self._check(load().fcm_mlhp_apply_K(self.h, _ptr(x), _ptr(y)))
+        self._check(load().fcm_mlhp_apply_K(self.h, self._vec(x, "x"), self._vec(y, "out")))
         return y
 
     def apply_S(self, r, out=None):
         import torch
         z = out if out is not None else torch.empty_like(r)
-        self._check(load().fcm_mlhp_apply_S(self.h, _ptr(r), _ptr(z)))
+        self._check(load().fcm_mlhp_apply_S(self.h, self._vec(r, "r"), self._vec(z, "out")))
         return z
 
     def pcg_solve(self, b, tol, maxit=100000, out=None, check=True):
@@ -618,7 +662,8 @@ class MLHPPlan:
         u = out if out is not None else torch.empty_like(b)
         its = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
-        st = load().fcm_mlhp_pcg_solve(self.h, _ptr(b), tol, maxit, _ptr(u), ctypes.byref(its), ctypes.byref(rel))
+        st = load().fcm_mlhp_pcg_solve(self.h, self._vec(b, "b"), tol, maxit, self._vec(u, "out"),
+                                       ctypes.byref(its), ctypes.byref(rel))
         if check:
             self._check(st)
         return u, its.value, rel.value, st
