@@ -389,8 +389,10 @@ def run_fcm(args, rank, world, local_rank):
     fp64_peak = fp64_peak_tflops(sm_mhz)
     achieved_tf = s_flops / t_s / 1e12
     achieved_gbs = s_bytes / t_s / 1e9
-    kernel = (f"schwarz_persistent_kernel<{w.p}>" if info["tiles_persistent"] else f"schwarz_colour_kernel<{w.p}>") + \
-        " (8 colour launches per S apply, the shape the build's autotuner kept)"
+    kernel = (f"S apply: schwarz_gemm_kernel<{w.p}> (shared factors) + "
+              f"{'schwarz_rows_kernel' if w.p == 3 else 'schwarz_cols_kernel'}<{w.p}> (streamed factors) + "
+              f"schwarz_sum_kernel<{w.p}>, "
+              f"{'concurrent' if info['schwarz_concurrent'] else 'serial'} (the shape the build's autotuner kept)")
     if args.precision == "fp64":
         # FP64 factors: one FP64 multiply-add per 8-byte entry; the FP64 pipe saturates first
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -468,8 +470,9 @@ def run_fcm(args, rank, world, local_rank):
                              f"element matrices {info['element_bytes'] / 2**30:.2f} GiB",
                        "n_blocks": info["n_blocks"], "n_factors": info["n_factors"],
                        "n_factors_fp32": info["n_blocks_fp32"], "n_jacobi_dofs": info["n_jacobi"],
-                       "schwarz_launch": {"rows_fp32": info["rows32"], "rows_fp64": info["rows64"],
-                                          "persistent": bool(info["tiles_persistent"]),
+                       "n_factors_double_float": info["n_factors_ff"], "n_gemm_blocks": info["n_gemm_blocks"],
+                       "schwarz_launch": {"stream_rows": info["stream_rows"],
+                                          "concurrent": bool(info["schwarz_concurrent"]),
                                           "autotune_ms": [round(t * 1e3, 4) for t in info["tune_seconds"] if t > 0]},
                        "setup_s": info["setup_seconds"], "precond_s": info["precond_seconds"],
                        "coarse_operator_s": info["coarse_seconds"],
@@ -534,8 +537,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
-                    help="mixed: FP32 block factors (FP64 for cond > 1e7), compared with plain FP64 in the same run")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_fp64"],
+                    help="mixed: FP32 block factors, double-float pairs for cond > 1e7 (mixed_fp64: FP64 there), "
+                         "compared with plain FP64 in the same run")
     ap.add_argument("--form", default="coarse", choices=["coarse", "pcg"],
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
     ap.add_argument("--coarse-iters", type=int, default=20)

@@ -109,14 +109,17 @@ typedef struct {
     double max_block_cond;    /* largest retained condition number of a block          */
     double coarse_seconds;    /* assembly time of the coarse operator K_H (0 until built) */
     int64_t n_jacobi;         /* free DOFs in no block (diagonal part of S), last build   */
-    int rows32, rows64;       /* rows per work item of a cut block's FP32 / FP64 factor  */
-    int tiles_persistent;     /* 1: one persistent launch per colour with two tile stages */
+    int stream_rows;          /* rows per work item of a block that streams its own factor (p = 3) */
+    int schwarz_concurrent;   /* 1: shared-factor products run on a second stream beside the
+                                 streamed factors; 0: after them                          */
     double tune_seconds[8];   /* S-apply time of each tried launch shape (0: not tried)  */
     int device_error;         /* 1 if a Schwarz kernel gave up waiting for its factor copy
-                                 since the last fcm_precond_build (its output is then wrong) */
+                                 since the last fcm_precond_build or solve (its output is then wrong) */
+    int64_t n_factors_ff;     /* factors stored as double-float pairs (FCM_PREC_MIXED, cond > cond_fp64) */
+    int64_t n_gemm_blocks;    /* blocks applied by the shared-factor dense product        */
 } fcm_info_t;
 
-enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1 };
+enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1, FCM_PREC_MIXED_FP64 = 2 };
 
 enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
 
@@ -126,7 +129,12 @@ enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
  *        unstabilised inverse S* (every nonzero eigenvalue inverted).
  *   precision: FCM_PREC_FP64 stores and applies every factor in FP64;
  *        FCM_PREC_MIXED stores factors in FP32 except blocks whose retained
- *        condition number exceeds cond_fp64 (kept in FP64).
+ *        condition number exceeds cond_fp64: those keep their FP64 values as
+ *        double-float pairs (hi = fl32(f), lo = fl32(f - hi), 2^-48 relative)
+ *        applied with error-free FP32 transformations (compensated products
+ *        and sums; ~1e-14 relative per dot product), or in FP64 when the factor
+ *        is shared by many blocks; FCM_PREC_MIXED_FP64 is the same with FP64
+ *        storage and arithmetic for every factor above the threshold.
  *   cond_fp64: threshold for FCM_PREC_MIXED (default 1e7).
  *   block_rule: FCM_BLOCKS_VERTEX (0, default): one block per grid vertex,
  *        the free functions carried by the vertex and by the edges, faces and
@@ -139,12 +147,11 @@ enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
  *        (Sec. 5.2's end points; eta_T is clamped to 1 against rounding).
  *   eta_bar: threshold of FCM_BLOCKS_ELEMENT (ignored by FCM_BLOCKS_VERTEX).
  *   fixed_tiles: 0 (default) lets the build time the Schwarz apply for up to
- *        six launch shapes (three row-tile sizes of the cut blocks, the rows of
- *        a factor handled by one work item, each with one CTA per work item or
- *        a persistent launch per colour that prefetches the next tile) and keep
- *        the fastest; 1 keeps the default tile with one CTA per work item; 2 the
- *        default tile with the persistent launch.  S r does not depend on the
- *        choice.
+ *        six launch shapes (three row-tile sizes of the blocks that stream their
+ *        own factor, each with the shared-factor products after the streamed
+ *        factors or beside them on a second stream) and keep the fastest; 1 keeps
+ *        the default tile, products after the streamed factors; 2 the default
+ *        tile, both at once.  S r does not depend on the choice.
  * A zero-initialised struct with eps, precision and cond_fp64 set selects
  * vertex patches and the autotuned tiles. */
 typedef struct {
@@ -223,6 +230,20 @@ fcm_status fcm_apply_K(fcm_ctx *ctx, const double *x_dev, double *y_dev);
 /* z_dev = S r_dev, S = sum_B R_B^T A_B+^-1 R_B (Sec. 3.1 Eq. (5)); device.
  * FCM_ESTATE before fcm_precond_build. */
 fcm_status fcm_apply_S(fcm_ctx *ctx, const double *r_dev, double *z_dev);
+
+/* z_dev = S r_dev for nrhs (1..8) vectors stored n_lattice apart (device);
+ * the block factors are read once for all of them.  Column k equals
+ * fcm_apply_S of column k.  FCM_EINVAL for nrhs outside 1..8. */
+fcm_status fcm_apply_S_many(fcm_ctx *ctx, const double *r_dev, int nrhs, double *z_dev);
+
+/* Failure detection: polls of the bounded mbarrier wait with which a Schwarz
+ * kernel waits for a bulk copy of a shared factor into shared memory (default
+ * 2^21).  A wait that runs out lets the copies in flight land, marks the apply
+ * as failed and returns; the solves then stop with FCM_ETIMEOUT (and
+ * fcm_info.device_error reports it after fcm_apply_S).  tries = 0 gives up at
+ * the first poll (for tests); tries < 0 restores the default.  Captured solver
+ * graphs are dropped (captured again by the next solve). */
+fcm_status fcm_set_wait_limit(fcm_ctx *ctx, int tries);
 
 /* ------------------------------------------------------------------------ */
 /* Learned coarse correction (not in the paper: the paper's preconditioner   */

@@ -136,9 +136,15 @@ fcm_status solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, doubl
         fcm_status s = build_graph(C);
         if (s != FCM_OK) return s;
     }
+    bool timed_out = false;
     for (;;) {
         API_CUDA(C, cudaMemcpyAsync(&h, C->d_s, sizeof h, cudaMemcpyDeviceToHost, st));
+        API_CUDA(C, cudaMemcpyAsync(C->h_err, C->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         API_CUDA(C, cudaStreamSynchronize(st));
+        if (*C->h_err) {
+            timed_out = true;  // a Schwarz apply gave up waiting for a factor copy: its z is wrong
+            break;
+        }
         if (h.done) break;
         API_CUDA(C, cudaGraphLaunch(C->graph, st));
     }
@@ -154,29 +160,36 @@ fcm_status solve_one(fcm_ctx *C, const double *rhs, double tol, int maxit, doubl
     info.iterations = h.it;
     info.relres = h.relres;
     info.true_relres = bb[1] > 0.0 ? std::sqrt(bb[0] / bb[1]) : 0.0;
-    info.status = h.status;
+    info.status = timed_out ? FCM_ETIMEOUT : h.status;
     info.seconds = ms * 1e-3;
-    return (fcm_status)h.status;
+    if (timed_out) {
+        API_CUDA(C, cudaMemsetAsync(C->d_err, 0, sizeof(int), st));
+        C->err = "a Schwarz apply gave up waiting for a factor copy (bounded mbarrier wait); the iterate is not valid";
+    }
+    return (fcm_status)info.status;
 }
 
 void free_ctx(fcm_ctx *C)
 {
     if (!C) return;
     destroy_graph(C);
-    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32, C->d_patches, C->d_batches, C->d_eta, C->d_jac, C->d_err,
+    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32,
+                    C->d_slots, C->d_slot_of, C->d_items, C->d_zb, C->d_mzb, C->d_eta, C->d_jac, C->d_err,
                     C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
                     C->d_out2};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (C->h_s) cudaFreeHost(C->h_s);
+    if (C->h_err) cudaFreeHost(C->h_err);
     if (C->d_m) cudaFree(C->d_m);
     if (C->d_ms) cudaFree(C->d_ms);
     if (C->h_ms) cudaFreeHost(C->h_ms);
     fcm::fcg_free(C->fcg);
     fcm::coarse_free(C->coarse);
-    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1};
+    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1, C->ev_fork, C->ev_join};
     for (auto e : evs)
         if (e) cudaEventDestroy(e);
+    if (C->side) cudaStreamDestroy(C->side);
     if (C->stream) cudaStreamDestroy(C->stream);
     delete C;
 }
@@ -311,6 +324,7 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     SETUP_CUDA(cudaMemsetAsync(C->d_s, 0, sizeof(CgScalars), st));
     SETUP_CUDA(dalloc(&C->d_out2, 2));
     SETUP_CUDA(cudaMallocHost((void **)&C->h_s, sizeof(CgScalars)));
+    SETUP_CUDA(cudaMallocHost((void **)&C->h_err, sizeof(int)));
     SETUP_CUDA(cudaStreamSynchronize(st));
 #undef SETUP_CUDA
     // diagonal of K (Algorithm 1's diagonal scaling for DOFs in no block), then the element
@@ -367,9 +381,10 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->max_block_cond = C->max_cond;
     out->coarse_seconds = fcm::coarse_seconds(C->coarse);
     out->n_jacobi = C->n_jacobi;
-    out->rows32 = C->plan.rows;
-    out->rows64 = C->plan.rows64;
-    out->tiles_persistent = C->plan.persistent;
+    out->stream_rows = C->plan.rows;
+    out->schwarz_concurrent = C->plan.concurrent;
+    out->n_factors_ff = C->n_ff_factors;
+    out->n_gemm_blocks = C->n_gemm_blocks;
     for (int k = 0; k < 8; ++k) out->tune_seconds[k] = C->tune_seconds[k];
     out->device_error = 0;
     if (C->d_err) {
@@ -412,7 +427,7 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     o.eta_bar = 1.0;
     o.fixed_tiles = 0;
     if (opts) o = *opts;
-    if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED) || !(o.cond_fp64 > 0.0) ||
+    if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED && o.precision != FCM_PREC_MIXED_FP64) || !(o.cond_fp64 > 0.0) ||
         (o.block_rule != FCM_BLOCKS_VERTEX && o.block_rule != FCM_BLOCKS_ELEMENT) ||
         (o.block_rule == FCM_BLOCKS_ELEMENT && !(o.eta_bar >= 0.0)) || o.fixed_tiles < 0 || o.fixed_tiles > 2) {
         C->err = "fcm_precond_build: invalid options";
@@ -461,13 +476,16 @@ static fcm_status solve_multi(fcm_ctx *C, const double *rhs, int nr, double tol,
         if (C->d_m) cudaFree(C->d_m);
         if (C->d_ms) cudaFree(C->d_ms);
         if (C->h_ms) cudaFreeHost(C->h_ms);
+        if (C->d_mzb) cudaFree(C->d_mzb);
         C->d_m = nullptr;
         C->d_ms = nullptr;
         C->h_ms = nullptr;
+        C->d_mzb = nullptr;
         C->m_nr = 0;
         API_CUDA(C, cudaMalloc(&C->d_m, sizeof(double) * 6 * (size_t)nr * n));
         API_CUDA(C, cudaMalloc(&C->d_ms, sizeof(CgScalars) * nr));
         API_CUDA(C, cudaMallocHost((void **)&C->h_ms, sizeof(CgScalars) * nr));
+        API_CUDA(C, cudaMalloc(&C->d_mzb, sizeof(double) * (size_t)nr * C->plan.nslots * C->plan.zs));
         C->m_nr = nr;
     }
     double *X = C->d_m, *R = X + (size_t)nr * n, *Z = R + (size_t)nr * n, *Pd = Z + (size_t)nr * n,
@@ -498,19 +516,26 @@ static fcm_status solve_multi(fcm_ctx *C, const double *rhs, int nr, double tol,
     API_CUDA(C, cudaMemcpyAsync(C->d_ms, C->h_ms, sizeof(CgScalars) * nr, cudaMemcpyHostToDevice, st));
     API_CUDA(C, cudaEventRecord(C->ev_t0, st));
     for (int k = 0; k < nr; ++k) fcm::cg_init_kernels(w[k], st);
-    fcm::launch_schwarz_apply_multi(C->p, C->g, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, nullptr, st);
+    fcm::launch_schwarz_apply_multi(C->p, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, C->d_mzb, nullptr, st);
     for (int k = 0; k < nr; ++k) fcm::cg_after_first_S(w[k], st);
     for (int it = 0;; ++it) {
         if (it % 8 == 0) {
             API_CUDA(C, cudaMemcpyAsync(C->h_ms, C->d_ms, sizeof(CgScalars) * nr, cudaMemcpyDeviceToHost, st));
+            API_CUDA(C, cudaMemcpyAsync(C->h_err, C->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             API_CUDA(C, cudaStreamSynchronize(st));
+            if (*C->h_err) {
+                API_CUDA(C, cudaMemsetAsync(C->d_err, 0, sizeof(int), st));
+                C->err = "a Schwarz apply gave up waiting for a factor copy (bounded mbarrier wait); the iterates are not valid";
+                agg.status = FCM_ETIMEOUT;
+                return FCM_ETIMEOUT;
+            }
             bool all = true;
             for (int k = 0; k < nr; ++k) all = all && C->h_ms[k].done;
             if (all) break;
         }
         for (int k = 0; k < nr; ++k) apply_K_dev(C, w[k].p, w[k].q, &C->d_ms[k].done);
         for (int k = 0; k < nr; ++k) fcm::cg_after_K(w[k], st);
-        fcm::launch_schwarz_apply_multi(C->p, C->g, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, nullptr, st);
+        fcm::launch_schwarz_apply_multi(C->p, R, Z, n, nr, C->d_f64, C->d_f32, C->plan, C->d_mzb, nullptr, st);
         for (int k = 0; k < nr; ++k) fcm::cg_after_S(w[k], st);
         API_CUDA(C, cudaGetLastError());
     }
@@ -547,13 +572,19 @@ static fcm_status solve_many(fcm_ctx *C, const double *rhs, int nrhs, double tol
         return FCM_ESTATE;
     }
     StreamScope sc(C);
+    // a failed wait of an earlier fcm_apply_S (reported by fcm_info) does not belong to this solve
+    API_CUDA(C, cudaMemsetAsync(C->d_err, 0, sizeof(int), C->stream));
     fcm_solve_info agg = {};
     agg.status = FCM_OK;
     fcm_status worst = FCM_OK;
     const bool fp64_p4 = C->p == 4 && C->d_f64;
     if (!host && nrhs > 1 && nrhs <= 8 && !fp64_p4) {
         worst = solve_multi(C, rhs, nrhs, tol, maxit, u, agg);
-        if (worst == FCM_EINVAL || worst == FCM_ECUDA || worst == FCM_ENOMEM) return worst;
+        if (worst == FCM_EINVAL || worst == FCM_ECUDA || worst == FCM_ENOMEM || worst == FCM_ETIMEOUT) {
+            agg.status = worst;
+            C->last = agg;
+            return worst;
+        }
         nrhs = 0;  // done
     }
     for (int k = 0; k < nrhs; ++k) {
@@ -570,6 +601,10 @@ static fcm_status solve_many(fcm_ctx *C, const double *rhs, int nrhs, double tol
             API_CUDA(C, cudaStreamSynchronize(C->stream));
         }
         if (s == FCM_EINVAL || s == FCM_ECUDA || s == FCM_ENOMEM) return s;
+        if (s == FCM_ETIMEOUT) {
+            C->last = one;
+            return s;
+        }
         agg.iterations = std::max(agg.iterations, one.iterations);
         agg.relres = std::max(agg.relres, one.relres);
         agg.true_relres = std::max(agg.true_relres, one.true_relres);
@@ -625,6 +660,54 @@ fcm_status fcm_apply_S(fcm_ctx *C, const double *r_dev, double *z_dev)
     fcm::launch_mask_copy(r_dev, C->d_t, C->d_mask, C->nlat, C->stream);
     apply_S_dev(C, C->d_t, z_dev, nullptr);
     API_CUDA(C, cudaGetLastError());
+    return FCM_OK;
+}
+
+fcm_status fcm_apply_S_many(fcm_ctx *C, const double *r_dev, int nrhs, double *z_dev)
+{
+    if (!C || !r_dev || !z_dev || nrhs < 1 || nrhs > 8) {
+        if (C) C->err = "fcm_apply_S_many: invalid argument (1 <= nrhs <= 8)";
+        return FCM_EINVAL;
+    }
+    if (!C->have_precond) {
+        C->err = "fcm_apply_S_many: call fcm_precond_build first";
+        return FCM_ESTATE;
+    }
+    if (nrhs == 1) return fcm_apply_S(C, r_dev, z_dev);
+    StreamScope sc(C);
+    const int64_t n = C->nlat;
+    if (C->m_nr != nrhs) {
+        // the multi-RHS workspace of the solver, shaped for nrhs vectors
+        if (C->d_m) cudaFree(C->d_m);
+        if (C->d_ms) cudaFree(C->d_ms);
+        if (C->h_ms) cudaFreeHost(C->h_ms);
+        if (C->d_mzb) cudaFree(C->d_mzb);
+        C->d_m = nullptr;
+        C->d_ms = nullptr;
+        C->h_ms = nullptr;
+        C->d_mzb = nullptr;
+        C->m_nr = 0;
+        API_CUDA(C, cudaMalloc(&C->d_m, sizeof(double) * 6 * (size_t)nrhs * n));
+        API_CUDA(C, cudaMalloc(&C->d_ms, sizeof(CgScalars) * nrhs));
+        API_CUDA(C, cudaMallocHost((void **)&C->h_ms, sizeof(CgScalars) * nrhs));
+        API_CUDA(C, cudaMalloc(&C->d_mzb, sizeof(double) * (size_t)nrhs * C->plan.nslots * C->plan.zs));
+        C->m_nr = nrhs;
+    }
+    double *R = C->d_m;  // masked copies of the inputs
+    for (int k = 0; k < nrhs; ++k) fcm::launch_mask_copy(r_dev + (size_t)k * n, R + (size_t)k * n, C->d_mask, n, C->stream);
+    fcm::launch_schwarz_apply_multi(C->p, R, z_dev, n, nrhs, C->d_f64, C->d_f32, C->plan, C->d_mzb, nullptr, C->stream);
+    API_CUDA(C, cudaGetLastError());
+    return FCM_OK;
+}
+
+fcm_status fcm_set_wait_limit(fcm_ctx *C, int tries)
+{
+    if (!C) return FCM_EINVAL;
+    C->wait_tries = tries < 0 ? fcm::kWaitTries : tries;
+    C->plan.wait_tries = C->wait_tries;
+    // the captured graphs hold the plan's launch parameters
+    destroy_graph(C);
+    fcm::fcg_forget_graph(C->fcg);
     return FCM_OK;
 }
 

@@ -601,6 +601,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     } restore{net, net ? unet_set_stream(net, st) : nullptr};
 
     double *x = C->d_x, *r = C->d_r, *zS = C->d_z, *q = C->d_q, *b = C->d_b;
+    CO_CUDA(C, cudaMemsetAsync(C->d_err, 0, sizeof(int), st));  // earlier fcm_apply_S failures are not this solve's
     launch_mask_copy(rhs, b, C->d_mask, n, st);
     double h2[2];
     if ((s = dot2(C, b, b, nullptr, nullptr, h2)) != FCM_OK) return s;
@@ -626,7 +627,17 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     if ((s = fcg_graph(C, net, gamma, coarse_iters)) != FCM_OK) return s;
     for (;;) {
         CO_CUDA(C, cudaMemcpyAsync(&h, F->d, sizeof h, cudaMemcpyDeviceToHost, st));
+        CO_CUDA(C, cudaMemcpyAsync(C->h_err, C->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CO_CUDA(C, cudaStreamSynchronize(st));
+        if (*C->h_err) {
+            // a Schwarz apply gave up waiting for a factor copy: the iterate is not valid
+            CO_CUDA(C, cudaMemsetAsync(C->d_err, 0, sizeof(int), st));
+            C->err = "fcm_fpcg_solve: a Schwarz apply gave up waiting for a factor copy (bounded mbarrier wait)";
+            C->last.status = FCM_ETIMEOUT;
+            cudaEventRecord(C->ev_out, st);
+            cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
+            return FCM_ETIMEOUT;
+        }
         if (h.stop) break;
         CO_CUDA(C, cudaGraphLaunch(F->graph, st));
     }
@@ -649,7 +660,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
         const double tol2 = jr > 0.0 ? std::min(1.0, tol * sb_norm / jr) : 1.0;
         // the plain solve copies its right-hand side first, so `res` also receives dx
         fcm_status s2 = ctx_solve_one(C, res, tol2, maxit - it, res, inner);
-        if (s2 == FCM_EINVAL || s2 == FCM_ECUDA || s2 == FCM_ENOMEM) return s2;
+        if (s2 == FCM_EINVAL || s2 == FCM_ECUDA || s2 == FCM_ENOMEM || s2 == FCM_ETIMEOUT) return s2;
         add_kernel<<<nblk(n), 256, 0, st>>>(x, keep, res, n);
         total += inner.iterations;
         rel = inner.relres * (jr / sb_norm);

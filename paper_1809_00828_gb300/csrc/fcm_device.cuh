@@ -51,60 +51,54 @@ struct KCells {
     SfTables sf;
 };
 
-// Launch plan of the Schwarz apply.  Blocks are grouped into batches that
-// share one stored factor (up to 8 blocks, same colour and precision); a block
-// with its own factor is split into row tiles, one work item each.  A segment
-// is a run of work items launched together; segments are ordered by colour,
-// so the colours run one after another.
-struct SchwarzSeg {
-    int colour;   // parity colour 0..7 of the vertex or cell
-    int prec;     // 0 FP64 factors, 1 FP32 factors
-    int G;        // 8: shared-factor batches, 1: single patches
-    int first;    // first batch of the segment
-    int count;    // batches in the segment
-};
+// Launch plan of the Schwarz apply (fcm_schwarz.cu).  Every block has a slot: its record
+// (factor offset, vertex or cell id, storage: 0 FP64, 1 FP32, 2 double-float) and nslots * zs
+// doubles of Zb for its product.  Slots of blocks that share a factor are consecutive (GEMM tiles
+// of up to NC blocks: (first slot, count), the FP32 tiles first); the other blocks stream their
+// own factor in row tiles ((slot, first row) work items), with a warp per row (row_items, `rows`
+// rows each; p = 3, one right-hand side) or a thread per row (col_items, schwarz_col_rows(p) rows
+// each).  slot_of maps a vertex (or cell) id to its slot, -1 when the block has no free DOF.
 struct SchwarzPlan {
-    const PatchRec *patches;  // patch records, batch by batch
-    const int2 *batches;      // (first block, count or row tile | kind << 8)
-    int nseg;
-    SchwarzSeg seg[32];
+    Grid3 g;
     int rule;                 // 0 vertex patches, 3 element blocks (FCM_BLOCKS_*)
-    int rows;                 // rows per work item of a block with its own FP32 factor (row tiles)
-    int rows64;               // the same for FP64 factors
-    int smem;                 // dynamic shared memory of a Schwarz CTA (schwarz_smem_bytes)
-    int *err;                 // device flag, set to 1 by a bulk-copy wait that ran out
-    int persistent;           // 1: one persistent launch per colour with two tile stages
-    int tile_bytes;           // bytes of one tile stage (persistent launches)
-    int grid_cap;             // CTAs of a persistent launch (resident CTAs of the GPU)
+    int zs;                   // Zb rows per slot (largest block, rounded up to 8)
+    int64_t nslots;
+    const PatchRec *slots;
+    const int *slot_of;
+    const int2 *row_items;
+    int n_row_items, rows;
+    const int2 *col_items;
+    int n_col_items;
+    const int2 *tiles;        // n_tiles32 FP32 tiles, then n_tiles64 FP64 tiles
+    int n_tiles32, n_tiles64;
+    double *zb;               // Zb for one right-hand side
     const double *jac;        // 1 / K_ll for the free DOFs in no block, 0 elsewhere (lattice); null if none
+    int *err;                 // device flag, set to 1 by a bulk-copy wait that ran out
+    int wait_tries;           // polls of a bulk-copy wait before it gives up
+    int concurrent;           // 1: the GEMM tiles run on `side` beside the streamed factors
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 };
 
 // Launchers (all asynchronous on `s`).  `done` may be null.  The Schwarz launchers overwrite z
-// with S r (its diagonal part first, then the blocks colour by colour).
+// with S r.  The multi-RHS form takes nr <= 8 vectors nlat apart and a Zb of nr * nslots * zs doubles.
 void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
                     const KCells &kc, const int *done, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
                           const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
-// Row tiles of the blocks with their own factor: default rows per work item for FP32 and FP64
-// factors (4 per warp of the launch, a tile of at most kTileBudget bytes), the dynamic shared
-// memory a Schwarz CTA needs for given row counts, and the kernel attributes for it (host
-// calls, outside stream capture).
-constexpr int kTileBudget = 72 * 1024;
-void schwarz_default_rows(int p, int rule, int *rows32, int *rows64);
-int schwarz_smem_bytes(int p, int rows32, int rows64);
-// blocks per FP32 shared-factor batch
-int schwarz_f32_batch_cap(int p);
-// true when blocks with their own factor are applied whole with direct loads (one item per block)
-bool schwarz_direct_singles(int p);
-// persistent launches: dynamic shared memory (and the bytes of one tile stage) for given row counts,
-// and the resident CTAs of the GPU at that size (sets the kernel's shared-memory attribute)
-int schwarz_persistent_smem_bytes(int p, int rows32, int rows64, int *tile_bytes);
-cudaError_t schwarz_persistent_grid(int p, int rule, int smem, int *grid);
-cudaError_t schwarz_prepare(int p, int smem_bytes);
-// nr <= 8 right-hand sides stored nlat apart (p = 4 needs FP32 factors)
-void launch_schwarz_apply_multi(int p, const Grid3 &g, const double *r, double *z, int64_t nlat, int nr,
-                                const double *f64, const float *f32, const SchwarzPlan &plan, const int *done,
+void launch_schwarz_apply_multi(int p, const double *r, double *z, int64_t nlat, int nr, const double *f64,
+                                const float *f32, const SchwarzPlan &plan, double *zb, const int *done,
                                 cudaStream_t s);
+// columns of a GEMM tile for FP32 (prec 1) or FP64 (prec 0) factors; rows per col_items work item;
+// whether single right-hand sides stream through row_items; threads of a row_items CTA
+int schwarz_gemm_cols(int p, int prec);
+int schwarz_col_rows(int p);
+bool schwarz_uses_rows_kernel(int p);
+int schwarz_rows_threads();
+// kernel attributes (dynamic shared memory); host call, outside stream capture
+cudaError_t schwarz_prepare(int p);
+// polls of a bulk-copy wait before it gives up (default)
+constexpr int kWaitTries = 1 << 21;
 void launch_mask_copy(const double *in, double *out, const uint8_t *mask, int64_t n, cudaStream_t s);
 // fcm_noalloc.cu: device address of the static scratch of fcm_apply_S_noalloc on the current device
 cudaError_t noalloc_scratch_address(double **out);
@@ -184,8 +178,14 @@ struct fcm_ctx {
     bool have_precond = false;
     double *d_f64 = nullptr;         // FP64 factor pool
     float *d_f32 = nullptr;          // FP32 factor pool (mixed precision)
-    fcm::PatchRec *d_patches = nullptr;
-    int2 *d_batches = nullptr;
+    fcm::PatchRec *d_slots = nullptr;
+    int *d_slot_of = nullptr;
+    int2 *d_items = nullptr;         // row items, column items, GEMM tiles
+    double *d_zb = nullptr;          // block products of one S apply
+    cudaStream_t side = nullptr;     // second stream of the Schwarz apply (shared-factor products)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int64_t n_ff_factors = 0;        // factors stored as double-float pairs
+    int64_t n_gemm_blocks = 0;       // blocks applied by the shared-factor GEMM
     double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
     int *d_err = nullptr;            // set by a Schwarz CTA whose bulk-copy wait ran out
     double *noalloc_scratch = nullptr;  // device address of fcm_apply_S_noalloc's static scratch
@@ -193,6 +193,7 @@ struct fcm_ctx {
     int device = 0;                     // CUDA device current at fcm_setup
     int fcg_window = 100;            // stall window of the flexible CG (fcm_fpcg_set_stall_window)
     double tune_seconds[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // S-apply times of the launch shapes tried
+    int wait_tries = fcm::kWaitTries;  // fcm_set_wait_limit
     int64_t n_jacobi = 0;
     fcm::SchwarzPlan plan = {};
     int64_t n_factors = 0, factor_bytes = 0, n_fp32_factors = 0;
@@ -207,6 +208,7 @@ struct fcm_ctx {
     unsigned *d_counter = nullptr;
     fcm::CgScalars *d_s = nullptr;
     fcm::CgScalars *h_s = nullptr;   // pinned
+    int *h_err = nullptr;            // pinned copy of d_err, read with the scalars
     double *d_out2 = nullptr;
     int red_blocks = 0;
     cudaGraphExec_t graph = nullptr;
@@ -215,6 +217,7 @@ struct fcm_ctx {
     // multi-RHS workspace: x, r, z, p, q, b for m_nr right-hand sides, and their CG scalars
     double *d_m = nullptr;
     fcm::CgScalars *d_ms = nullptr, *h_ms = nullptr;
+    double *d_mzb = nullptr;         // block products of the multi-RHS Schwarz apply
     int m_nr = 0;
     // coarse operator of the learned correction (built on first use)
     fcm::CoarseOp *coarse = nullptr;

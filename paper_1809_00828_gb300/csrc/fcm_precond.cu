@@ -250,6 +250,24 @@ __global__ void to_f32_kernel(const double *in, float *out, int n)
     }
 }
 
+// FP64 factor -> double-float pairs: entry j of row i at floats 2 (i ld + j) (hi) and +1 (lo),
+// hi = fl32(f), lo = fl32(f - hi); rows of ld = factor_ld<double>(n) entries, padding zero
+__global__ void to_ff_kernel(const double *in, float *out, int n)
+{
+    const int ld = factor_ld<double>(n);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * ld; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % ld);
+        const double x = j < n ? in[e] : 0.0;
+        const float h = __double2float_rn(x);
+        out[2 * e] = h;
+        out[2 * e + 1] = __double2float_rn(x - (double)h);
+    }
+}
+
+// A factor shared by at least this many blocks is applied as a dense product over its blocks
+// (GEMM tiles); factors with fewer blocks stream once per block.
+constexpr int kGemmMinBlocks = 8;
+
 struct FactorInfo {
     int rep;      // representative vertex
     int n;        // box size
@@ -492,19 +510,34 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         }
     }
 
-    // ---- final pools (FP64 only, or FP32 + FP64 for the ill-conditioned blocks)
-    const bool mixed = o.precision == FCM_PREC_MIXED;
+    // ---- blocks of each factor, in vertex (or cell) order
+    std::vector<std::vector<int>> blocks_of(fac.size());
+    for (int64_t v = 0; v < npatch; ++v)
+        if (patch_factor[v] >= 0) blocks_of[patch_factor[v]].push_back((int)v);
+    std::vector<char> shared(fac.size(), 0);
+    for (size_t f = 0; f < fac.size(); ++f) shared[f] = (int)blocks_of[f].size() >= kGemmMinBlocks;
+
+    // ---- final pools.  FP64 form: every factor FP64 (the staging layout is final).  Mixed forms: FP32
+    // where the retained condition number is at most cond_fp64; above it double-float pairs (FCM_PREC_MIXED)
+    // or FP64 (FCM_PREC_MIXED_FP64); a shared factor above it stays FP64 (the dense product runs in FP32
+    // or FP64).  prec: 0 FP64, 1 FP32, 2 double-float.
+    const bool mixed = o.precision != FCM_PREC_FP64;
     std::vector<int> prec(fac.size(), 0);
     std::vector<int64_t> off(fac.size(), 0);
     int64_t n64 = 0, n32 = 0, alg_bytes = 0;
     for (size_t f = 0; f < fac.size(); ++f) {
         const int n = fac[f].n;
-        if (mixed && fac[f].cond <= o.cond_fp64) {
-            prec[f] = 1;
+        if (mixed) prec[f] = fac[f].cond <= o.cond_fp64 ? 1 : (o.precision == FCM_PREC_MIXED && !shared[f] ? 2 : 0);
+        if (prec[f] == 1) {
             n32 = (n32 + 3) / 4 * 4;
             off[f] = n32;
             n32 += (int64_t)n * factor_ld<float>(n);
             alg_bytes += (int64_t)n * n * 4;
+        } else if (prec[f] == 2) {
+            n32 = (n32 + 3) / 4 * 4;
+            off[f] = n32;
+            n32 += 2 * (int64_t)n * factor_ld<double>(n);
+            alg_bytes += (int64_t)n * n * 8;
         } else {
             n64 = (n64 + 1) / 2 * 2;
             off[f] = n64;
@@ -519,234 +552,169 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     if (!mixed) {
         C->d_f64 = stage;  // staging layout is final
         guard.ptrs.erase(std::find(guard.ptrs.begin(), guard.ptrs.end(), (void *)stage));
+        for (size_t f = 0; f < fac.size(); ++f) off[f] = fac[f].off;
     } else {
         if (n64 > 0) PC_CUDA(cudaMalloc(&C->d_f64, sizeof(double) * n64));
         if (n32 > 0) PC_CUDA(cudaMalloc(&C->d_f32, sizeof(float) * n32));
         for (size_t f = 0; f < fac.size(); ++f) {
             const int64_t sz = (int64_t)fac[f].n * factor_ld<double>(fac[f].n);
+            const int grid = (int)std::min<int64_t>((sz + 255) / 256, 1024);
             if (prec[f] == 1)
-                to_f32_kernel<<<(int)std::min<int64_t>((sz + 255) / 256, 1024), 256, 0, st>>>(stage + fac[f].off, C->d_f32 + off[f], fac[f].n);
+                to_f32_kernel<<<grid, 256, 0, st>>>(stage + fac[f].off, C->d_f32 + off[f], fac[f].n);
+            else if (prec[f] == 2)
+                to_ff_kernel<<<grid, 256, 0, st>>>(stage + fac[f].off, C->d_f32 + off[f], fac[f].n);
             else
                 PC_CUDA(cudaMemcpyAsync(C->d_f64 + off[f], stage + fac[f].off, sizeof(double) * sz, cudaMemcpyDeviceToDevice, st));
         }
         PC_CUDA(cudaGetLastError());
         PC_CUDA(cudaStreamSynchronize(st));
     }
-    if (!mixed)
-        for (size_t f = 0; f < fac.size(); ++f) off[f] = fac[f].off;
 
-    // ---- launch plan: per colour and precision, batches of blocks sharing a factor (up to 8; 4
-    // for FP64 at p = 4) and row tiles of the blocks with their own factor
-    std::vector<std::vector<int>> by_colour_factor[8];
-    for (int c = 0; c < 8; ++c) by_colour_factor[c].resize(fac.size());
+    // ---- slots: the blocks of shared factors first (FP32 factors, then FP64), consecutive per factor,
+    // then the blocks streaming their own factor
+    std::vector<PatchRec> slots;
+    std::vector<int> slot_of(npatch, -1);
+    std::vector<int2> tiles32, tiles64;
+    int64_t gemm_blocks = 0;
+    for (int want = 1; want >= 0; --want)
+        for (size_t f = 0; f < fac.size(); ++f) {
+            if (!shared[f] || prec[f] != want) continue;
+            const int nc = schwarz_gemm_cols(p, want);
+            const int first = (int)slots.size();
+            for (int v : blocks_of[f]) {
+                slot_of[v] = (int)slots.size();
+                slots.push_back({off[f], v, prec[f]});
+            }
+            const int cnt = (int)blocks_of[f].size();
+            for (int s0 = 0; s0 < cnt; s0 += nc) (want == 1 ? tiles32 : tiles64).push_back(make_int2(first + s0, std::min(nc, cnt - s0)));
+            gemm_blocks += cnt;
+        }
+    std::vector<int> own_slots[3];  // by storage
+    for (size_t f = 0; f < fac.size(); ++f) {
+        if (shared[f]) continue;
+        for (int v : blocks_of[f]) {
+            slot_of[v] = (int)slots.size();
+            own_slots[prec[f]].push_back((int)slots.size());
+            slots.push_back({off[f], v, prec[f]});
+        }
+    }
     C->n_blocks = 0;
     C->sapply_fmas = 0;
-    // colours: parity of the vertex (rule 0) or of the cell (rule 3); blocks of one colour are DOF-disjoint
-    for (int vz = 0; vz < nid[2]; ++vz)
-        for (int vy = 0; vy < nid[1]; ++vy)
-            for (int vx = 0; vx < nid[0]; ++vx) {
-                const int v = vx + nid[0] * (vy + nid[1] * vz);
-                const int f = patch_factor[v];
-                if (f < 0) continue;
-                by_colour_factor[(vx & 1) + 2 * (vy & 1) + 4 * (vz & 1)][f].push_back(v);
-                C->n_blocks += 1;
-                C->sapply_fmas += (int64_t)fac[f].n * fac[f].n;
-            }
-    // One launch per colour.  Units by kind, heaviest first: FP64 shared-factor batches, FP64 single
-    // blocks, FP32 single blocks (DRAM-bound), FP32 batches; their work items are interleaved below.
-    // Kinds as in fcm_kernels.cu: 0 FP32 shared, 1 FP32 single, 2 FP64 shared, 3 FP64 single.
-    // `units` lists, colour by colour, a batch (first record, count) or a single block (record,
-    // rows); the work items follow from them once the row-tile sizes are chosen.
-    struct Unit {
-        int rec, kind, size;  // size: block count of a batch, rows of a single block
-    };
-    std::vector<PatchRec> all;
-    std::vector<Unit> units;
-    int unit_colour_end[8];
-    const int order[4][2] = {{0, 1}, {0, 0}, {1, 0}, {1, 1}};  // (precision 0 = FP64 / 1 = FP32, shared?)
-    for (int c = 0; c < 8; ++c) {
-        for (const auto &o : order) {
-            const int pr = o[0], shared = o[1];
-            const int kind = pr == 1 ? (shared ? 0 : 1) : (shared ? 2 : 3);
-            const int cap = !shared ? 1 : pr == 1 ? schwarz_f32_batch_cap(p) : (p == 4 ? 4 : 8);
-            for (size_t f = 0; f < fac.size(); ++f) {
-                const std::vector<int> &vs = by_colour_factor[c][f];
-                if (prec[f] != pr || vs.empty() || ((vs.size() > 1) != (shared == 1))) continue;
-                for (size_t s0 = 0; s0 < vs.size(); s0 += cap) {
-                    const int cnt = (int)std::min<size_t>(cap, vs.size() - s0);
-                    units.push_back({(int)all.size(), kind, shared ? cnt : fac[f].n});
-                    for (int k = 0; k < cnt; ++k) all.push_back({off[f], vs[s0 + k], prec[f]});
-                }
-            }
-        }
-        unit_colour_end[c] = (int)units.size();
+    for (size_t f = 0; f < fac.size(); ++f) {
+        C->n_blocks += (int64_t)blocks_of[f].size();
+        C->sapply_fmas += (int64_t)blocks_of[f].size() * fac[f].n * fac[f].n;
     }
-    SchwarzPlan plan = {};
-    plan.rule = rule;
-    // a block with its own factor is split into row tiles of rows32 (FP32) or rows64 (FP64) rows;
-    // its items carry the tile index in place of the count
-    auto make_items = [&](int rows32, int rows64, std::vector<int2> &items, SchwarzPlan &pl) {
+    // work items of the streamed factors, (slot, first row): the three storages interleaved by relative
+    // position, so that every part of a launch mixes FP64-pipe, FP32-pipe and DRAM-bound work
+    auto make_items = [&](int rows, std::vector<int2> &items) {
+        std::vector<int2> lists[3];
+        for (int k = 0; k < 3; ++k)
+            for (int sl : own_slots[k])
+                for (int r0 = 0; r0 < fac[patch_factor[slots[sl].v]].n; r0 += rows) lists[k].push_back(make_int2(sl, r0));
         items.clear();
-        pl.nseg = 0;
-        int u = 0;
-        for (int c = 0; c < 8; ++c) {
-            SchwarzSeg sg = {c, -1, 0, (int)items.size(), 0};
-            // three streams of work items: FP64 (FP64 pipe), FP32 single-factor tiles (DRAM), FP32
-            // batches (FP32 pipe, factor in L2); each heaviest first
-            std::vector<int2> lists[3];
-            for (; u < unit_colour_end[c]; ++u) {
-                const Unit &un = units[u];
-                const int li = un.kind >= 2 ? 0 : un.kind == 1 ? 1 : 2;
-                if (un.kind == 0 || un.kind == 2) {
-                    lists[li].push_back(make_int2(un.rec, un.size | (un.kind << 8)));
-                } else {
-                    const int rws = un.kind == 1 ? rows32 : rows64;
-                    for (int t = 0; t * rws < un.size; ++t) lists[li].push_back(make_int2(un.rec, t | (un.kind << 8)));
-                }
-            }
-            // interleaved by relative position, so that every part of the launch mixes the three
-            // kinds and the SMs run compute-bound and DRAM-bound items side by side
-            size_t pos[3] = {0, 0, 0};
-            for (;;) {
-                int best = -1;
-                double key = 2.0;
-                for (int l = 0; l < 3; ++l)
-                    if (pos[l] < lists[l].size()) {
-                        const double k = (pos[l] + 0.5) / (double)lists[l].size();
-                        if (k < key) {
-                            key = k;
-                            best = l;
-                        }
+        size_t pos[3] = {0, 0, 0};
+        for (;;) {
+            int best = -1;
+            double key = 2.0;
+            for (int l = 0; l < 3; ++l)
+                if (pos[l] < lists[l].size()) {
+                    const double k = (pos[l] + 0.5) / (double)lists[l].size();
+                    if (k < key) {
+                        key = k;
+                        best = l;
                     }
-                if (best < 0) break;
-                items.push_back(lists[best][pos[best]++]);
-            }
-            sg.count = (int)items.size() - sg.first;
-            if (sg.count > 0) pl.seg[pl.nseg++] = sg;
+                }
+            if (best < 0) break;
+            items.push_back(lists[best][pos[best]++]);
         }
-        pl.rows = rows32;
-        pl.rows64 = rows64;
-        pl.smem = schwarz_smem_bytes(p, rows32, rows64);
     };
-    int rows32 = 0, rows64 = 0;
-    schwarz_default_rows(p, rule, &rows32, &rows64);
-    // a largest block that fits one tile whole (p <= 2) is one item per block by default
-    if (maxn > 0 && (int64_t)maxn * factor_ld<float>(maxn) * 4 <= kTileBudget)
-        rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
-    if (maxn > 0 && (int64_t)maxn * factor_ld<double>(maxn) * 8 <= kTileBudget)
-        rows64 = std::max(rows64, (maxn + 1) / 2 * 2);
-    // blocks applied whole with direct loads: exactly one item per block
-    const bool whole = schwarz_direct_singles(p);
-    if (whole) {
-        rows32 = std::max(rows32, (maxn + 3) / 4 * 4);
-        rows64 = std::max(rows64, (maxn + 3) / 4 * 4);
-    }
-    // candidates: the default row tiles (4 rows per warp, a tile within kTileBudget), half and a
-    // quarter of them (more, shorter work items), each launched one CTA per work item or as a
-    // persistent launch with two tile stages
+    const bool rows_kernel = schwarz_uses_rows_kernel(p);
+    std::vector<int2> col_items;
+    make_items(schwarz_col_rows(p), col_items);
+    // candidates: rows per row item (p = 3: 64, 128, the whole block), each with the shared-factor products
+    // after the streamed factors or beside them on a second stream
     struct Cand {
-        int r32, r64, pers;
+        int rows, conc;
     };
     std::vector<Cand> cand;
+    const int whole = (maxn + 31) / 32 * 32;
+    std::vector<int> row_opts = rows_kernel ? std::vector<int>{128, 64, whole} : std::vector<int>{0};
     if (o.fixed_tiles == 1 || o.fixed_tiles == 2) {
-        cand.push_back({rows32, rows64, o.fixed_tiles - 1});
+        cand.push_back({row_opts[0], o.fixed_tiles - 1});
     } else {
-        for (int pers = 0; pers < 2; ++pers)
-            for (int dv : {1, 2, 4}) {
-                if (whole && dv > 1) continue;  // whole blocks only
-                const Cand c2 = {std::max(4, rows32 / dv / 4 * 4), std::max(2, rows64 / dv / 2 * 2), pers};
-                // a work item carries its tile index in the 8 bits below its kind: candidates with more
-                // than 255 tiles per block (p = 4 vertex patches at a half or a quarter of the default
-                // tile) are not formed
-                if ((maxn + c2.r32 - 1) / c2.r32 > 255 || (maxn + c2.r64 - 1) / c2.r64 > 255) continue;
-                if (cand.empty() || c2.r32 != cand.back().r32 || c2.r64 != cand.back().r64 || c2.pers != cand.back().pers)
-                    cand.push_back(c2);
-            }
+        for (int conc = 0; conc < 2; ++conc)
+            for (int ro : row_opts) cand.push_back({ro, conc});
     }
-    std::vector<int2> batches;
-    size_t max_items = 0;
-    int max_smem = 0, max_psmem = 0;
-    for (const auto &c2 : cand) {
-        make_items(c2.r32, c2.r64, batches, plan);
-        max_items = std::max(max_items, batches.size());
-        int tb = 0;
-        if (c2.pers) max_psmem = std::max(max_psmem, schwarz_persistent_smem_bytes(p, c2.r32, c2.r64, &tb));
-        else max_smem = std::max(max_smem, plan.smem);
-    }
+    std::vector<int2> row_items;
+    size_t max_rows_items = 0;
+    for (const auto &c2 : cand)
+        if (rows_kernel) {
+            make_items(c2.rows, row_items);
+            max_rows_items = std::max(max_rows_items, row_items.size());
+        }
+
+    // ---- device arrays: slots, slot_of, [row items | column items | tiles], Zb
+    auto reup = [&](auto **d, size_t count) -> cudaError_t {
+        if (*d) cudaFree(*d);
+        *d = nullptr;
+        return cudaMalloc((void **)d, sizeof(**d) * std::max<size_t>(count, 1));
+    };
+    PC_CUDA(reup(&C->d_slots, slots.size()));
+    PC_CUDA(reup(&C->d_slot_of, slot_of.size()));
+    const size_t n_tiles = tiles32.size() + tiles64.size();
+    PC_CUDA(reup(&C->d_items, max_rows_items + col_items.size() + n_tiles));
+    const int zs = (maxn + 7) / 8 * 8;
+    PC_CUDA(reup(&C->d_zb, (size_t)slots.size() * zs));
+    PC_CUDA(cudaMemcpyAsync(C->d_slots, slots.data(), sizeof(PatchRec) * slots.size(), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(C->d_slot_of, slot_of.data(), sizeof(int) * slot_of.size(), cudaMemcpyHostToDevice, st));
+    int2 *d_col = C->d_items + max_rows_items, *d_tiles = d_col + col_items.size();
+    PC_CUDA(cudaMemcpyAsync(d_col, col_items.data(), sizeof(int2) * col_items.size(), cudaMemcpyHostToDevice, st));
+    std::vector<int2> tiles(tiles32);
+    tiles.insert(tiles.end(), tiles64.begin(), tiles64.end());
+    PC_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st));
     if (!C->d_err) PC_CUDA(cudaMalloc(&C->d_err, sizeof(int)));
     PC_CUDA(cudaMemsetAsync(C->d_err, 0, sizeof(int), st));
-    if (max_smem > 0) PC_CUDA(schwarz_prepare(p, max_smem));
-    // the kernel attributes, then per candidate the resident CTAs of a persistent launch
-    int grid_dummy = 0;
-    if (max_psmem > 0) PC_CUDA(schwarz_persistent_grid(p, rule, max_psmem, &grid_dummy));
-    auto configure = [&](const Cand &c2) -> std::string {
-        make_items(c2.r32, c2.r64, batches, plan);
-        plan.err = C->d_err;
-        plan.persistent = c2.pers;
-        if (c2.pers) {
-            plan.smem = schwarz_persistent_smem_bytes(p, c2.r32, c2.r64, &plan.tile_bytes);
-            if (schwarz_persistent_grid(p, rule, plan.smem, &plan.grid_cap) != cudaSuccess) return "persistent grid";
-            schwarz_persistent_grid(p, rule, max_psmem, &grid_dummy);  // keep the attribute at the largest size
-        }
-        return std::string();
-    };
-    if (C->d_patches) cudaFree(C->d_patches);
-    if (C->d_batches) cudaFree(C->d_batches);
-    C->d_patches = nullptr;
-    C->d_batches = nullptr;
-    PC_CUDA(cudaMalloc(&C->d_patches, sizeof(PatchRec) * std::max<size_t>(all.size(), 1)));
-    PC_CUDA(cudaMalloc(&C->d_batches, sizeof(int2) * std::max<size_t>(max_items, 1)));
-    PC_CUDA(cudaMemcpyAsync(C->d_patches, all.data(), sizeof(PatchRec) * all.size(), cudaMemcpyHostToDevice, st));
-    plan.patches = C->d_patches;
-    plan.batches = C->d_batches;
-    for (int k = 0; k < 8; ++k) C->tune_seconds[k] = 0.0;
-    size_t best_k = 0;
-    if (cand.size() > 1) {
-        // autotuner: S applied to the load vector (a field with the problem's own structure) into
-        // the z work vector, 2 warm-up and 5 timed applies per candidate on the context's stream
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        PC_CUDA(cudaEventCreate(&e0));
-        PC_CUDA(cudaEventCreate(&e1));
-        double best = 1e300;
-        std::string fail;
-        for (size_t k = 0; k < cand.size() && k < 8 && fail.empty(); ++k) {
-            fail = configure(cand[k]);
-            if (!fail.empty()) break;
-            if (cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess) {
-                fail = "autotune upload";
-                break;
-            }
-            for (int w = 0; w < 2; ++w) launch_schwarz_apply(p, g, C->d_rhs, C->d_z, C->d_f64, C->d_f32, plan, nullptr, st);
-            cudaEventRecord(e0, st);
-            for (int w = 0; w < 5; ++w) launch_schwarz_apply(p, g, C->d_rhs, C->d_z, C->d_f64, C->d_f32, plan, nullptr, st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-                fail = "autotune run";
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            C->tune_seconds[k] = ms / 5e3;
-            if (C->tune_seconds[k] < best) {
-                best = C->tune_seconds[k];
-                best_k = k;
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (!fail.empty()) return fail + ": " + cudaGetErrorString(cudaGetLastError());
+    if (!C->side) {
+        PC_CUDA(cudaStreamCreateWithFlags(&C->side, cudaStreamNonBlocking));
+        PC_CUDA(cudaEventCreateWithFlags(&C->ev_fork, cudaEventDisableTiming));
+        PC_CUDA(cudaEventCreateWithFlags(&C->ev_join, cudaEventDisableTiming));
     }
-    {
-        const std::string e = configure(cand[best_k]);
-        if (!e.empty()) return e;
-    }
-    PC_CUDA(cudaMemcpyAsync(C->d_batches, batches.data(), sizeof(int2) * batches.size(), cudaMemcpyHostToDevice, st));
-    PC_CUDA(cudaStreamSynchronize(st));
-    plan.patches = C->d_patches;
-    plan.batches = C->d_batches;
-    plan.rule = rule;
+    PC_CUDA(schwarz_prepare(p));
+    if (C->d_mzb) cudaFree(C->d_mzb);  // multi-RHS products: sized again by the next multi-RHS solve
+    C->d_mzb = nullptr;
+    C->m_nr = 0;
 
+    SchwarzPlan plan = {};
+    plan.g = g;
+    plan.rule = rule;
+    plan.zs = zs;
+    plan.nslots = (int64_t)slots.size();
+    plan.slots = C->d_slots;
+    plan.slot_of = C->d_slot_of;
+    plan.row_items = C->d_items;
+    plan.col_items = d_col;
+    plan.n_col_items = (int)col_items.size();
+    plan.tiles = d_tiles;
+    plan.n_tiles32 = (int)tiles32.size();
+    plan.n_tiles64 = (int)tiles64.size();
+    plan.zb = C->d_zb;
+    plan.err = C->d_err;
+    plan.wait_tries = C->wait_tries;
+    plan.side = C->side;
+    plan.ev_fork = C->ev_fork;
+    plan.ev_join = C->ev_join;
+    plan.jac = nullptr;  // set below, with the diagonal part
+    auto configure = [&](const Cand &c2) -> cudaError_t {
+        plan.concurrent = c2.conc;
+        plan.rows = c2.rows;
+        plan.n_row_items = 0;
+        if (rows_kernel) {
+            make_items(c2.rows, row_items);
+            plan.n_row_items = (int)row_items.size();
+            return cudaMemcpyAsync(C->d_items, row_items.data(), sizeof(int2) * row_items.size(), cudaMemcpyHostToDevice, st);
+        }
+        return cudaSuccess;
+    };
     // ---- Algorithm 1's diagonal part: 1 / K_ll for the free DOFs in no block
     std::vector<uint8_t> covered(hp.nlat, 0);
     for (int64_t v = 0; v < npatch; ++v) {
@@ -773,14 +741,56 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         PC_CUDA(cudaStreamSynchronize(st));
     }
     plan.jac = C->d_jac;
+
+    // ---- autotuner: S applied to the load vector (a field with the problem's own structure) into the z
+    // work vector, 2 warm-up and 5 timed applies per candidate on the context's stream; S r does not depend
+    // on the choice
+    for (int k = 0; k < 8; ++k) C->tune_seconds[k] = 0.0;
+    size_t best_k = 0;
+    if (cand.size() > 1) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        PC_CUDA(cudaEventCreate(&e0));
+        PC_CUDA(cudaEventCreate(&e1));
+        double best = 1e300;
+        std::string fail;
+        for (size_t k = 0; k < cand.size() && k < 8; ++k) {
+            if (configure(cand[k]) != cudaSuccess) {
+                fail = "autotune upload";
+                break;
+            }
+            for (int w = 0; w < 2; ++w) launch_schwarz_apply(p, g, C->d_rhs, C->d_z, C->d_f64, C->d_f32, plan, nullptr, st);
+            cudaEventRecord(e0, st);
+            for (int w = 0; w < 5; ++w) launch_schwarz_apply(p, g, C->d_rhs, C->d_z, C->d_f64, C->d_f32, plan, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+                fail = "autotune run";
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            C->tune_seconds[k] = ms / 5e3;
+            if (C->tune_seconds[k] < best) {
+                best = C->tune_seconds[k];
+                best_k = k;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (!fail.empty()) return fail + ": " + cudaGetErrorString(cudaGetLastError());
+    }
+    PC_CUDA(configure(cand[best_k]));
+    PC_CUDA(cudaStreamSynchronize(st));
     C->plan = plan;
+    C->n_ff_factors = 0;
+    for (size_t f = 0; f < fac.size(); ++f) C->n_ff_factors += prec[f] == 2;
+    C->n_gemm_blocks = gemm_blocks;
     C->n_factors = (int64_t)fac.size();
     C->factor_bytes = alg_bytes;  // n^2 entries per factor (the stored rows carry < 16 bytes of padding)
     C->max_block = maxn;
     C->n_fp32_factors = 0;
     C->max_cond = 0.0;
     for (size_t f = 0; f < fac.size(); ++f) {
-        C->n_fp32_factors += prec[f];
+        C->n_fp32_factors += prec[f] == 1;
         if (std::isfinite(fac[f].cond)) C->max_cond = std::max(C->max_cond, fac[f].cond);
     }
     C->have_precond = true;

@@ -1,0 +1,787 @@
+// Additive-Schwarz apply z = D r + sum_B R_B^T F_B R_B r on sm_103a (Sec. 3.1 Eq. (5), Algorithm 1;
+// F_B the eigenvalue-filtered pseudo inverse of Sec. 3.2 Eqs. (11)-(13), D Algorithm 1's diagonal
+// scaling of the DOFs in no block).
+//
+// Two phases, so that no block waits for another:
+//   1. block products Zb[B] = F_B r_B for every block at once, each written to its own slot of a
+//      buffer (no scatter, no colours):
+//        - blocks with their own factor (cut blocks) stream the factor from HBM once; a work item is
+//          a tile of rows of one block (schwarz_rows_kernel: a warp per row, the lanes split the row
+//          into 16-byte vectors; schwarz_cols_kernel: a thread per row, for small blocks and for
+//          several right-hand sides);
+//        - blocks that share a factor (uncut patches with equal boundary patterns) form a dense
+//          product F [r_B1 ... r_Bm]: schwarz_gemm_kernel stages the factor through shared memory
+//          by bulk copies (cp.async.bulk, completed on mbarriers, double-buffered) and keeps an
+//          8 x 8 register tile of outputs per thread, so one shared-memory read of a factor entry
+//          feeds 8 multiply-adds;
+//   2. schwarz_sum_kernel: z_l = D_l r_l + the Zb rows of the blocks that contain DOF l, summed in
+//      a fixed order of the blocks: deterministic, and every launch shape gives the same bits.
+//
+// Factor storage per block: FP64; FP32; or "double-float" (each FP64 entry f stored as the float
+// pair hi = fl32(f), lo = fl32(f - hi), relative error 2^-48) for the ill-conditioned blocks of
+// the mixed form.  Double-float products run on the FP32 pipe with error-free transformations
+// (Dekker's product by FMA, Knuth's TwoSum; Ogita, Rump & Oishi's compensated dot product), which
+// GB300's FP64 pipe (2 fused multiply-adds per clock per SM) could not do at HBM rate.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fcm_device.cuh"
+
+namespace fcm {
+
+namespace {
+
+__host__ __device__ constexpr int sbox_width(int P) { return 2 * P - 1 > P + 1 ? 2 * P - 1 : P + 1; }
+// rows of the largest block box of either rule
+__host__ __device__ constexpr int sbox_max(int P) { return 3 * sbox_width(P) * sbox_width(P) * sbox_width(P); }
+__host__ __device__ constexpr int rnd32(int v) { return (v + 31) / 32 * 32; }
+
+struct SBox {
+    int lo[3], d[3], n;
+};
+
+// Lattice box of block `id`: rule 0, the vertex patch of vertex id, [p v - (p-1), p v + (p-1)] clipped to
+// the lattice; rule 3, the element block of cell id, [p c, p c + p].
+__device__ __forceinline__ SBox sbox(int rule, int P, const Grid3 &g, int id)
+{
+    SBox b;
+    if (rule == 3) {
+        const int c[3] = {id % g.n[0], (id / g.n[0]) % g.n[1], id / (g.n[0] * g.n[1])};
+        for (int a = 0; a < 3; ++a) {
+            b.lo[a] = P * c[a];
+            b.d[a] = P + 1;
+        }
+    } else {
+        const int nvx = g.n[0] + 1, nvy = g.n[1] + 1;
+        const int v[3] = {id % nvx, (id / nvx) % nvy, id / (nvx * nvy)};
+        for (int a = 0; a < 3; ++a) {
+            b.lo[a] = max(0, P * v[a] - (P - 1));
+            b.d[a] = min(g.M[a] - 1, P * v[a] + (P - 1)) - b.lo[a] + 1;
+        }
+    }
+    b.n = 3 * b.d[0] * b.d[1] * b.d[2];
+    return b;
+}
+
+// offset of box entry t from the box's first lattice DOF
+__device__ __forceinline__ int box_rel(const SBox &b, const Grid3 &g, int t)
+{
+    const int nl = t / 3;
+    const int ix = nl % b.d[0], iy = (nl / b.d[0]) % b.d[1], iz = nl / (b.d[0] * b.d[1]);
+    return 3 * (ix + g.M[0] * (iy + g.M[1] * iz)) + t % 3;
+}
+
+__device__ __forceinline__ int64_t box_base(const SBox &b, const Grid3 &g)
+{
+    return 3 * (b.lo[0] + (int64_t)g.M[0] * (b.lo[1] + (int64_t)g.M[1] * b.lo[2]));
+}
+
+// ---- double-float arithmetic (FP32 pipe)
+
+// fl32(x) and fl32(x - fl32(x)): x = hi + lo to 2^-48 relative
+__device__ __forceinline__ float2 split_ff(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// S + C += (fh + fl)(xh + xl): the product fh xh exactly as p + e (FMA), the cross terms in FP32,
+// fl xl (2^-48 relative) dropped; S accumulates by TwoSum, its rounding errors go to C.  The
+// intrinsics keep the compiler from contracting or reassociating these steps.
+__device__ __forceinline__ void ff_fma(float fh, float fl, float xh, float xl, float &S, float &C)
+{
+    const float p = __fmul_rn(fh, xh);
+    const float e = __fmaf_rn(fh, xh, -p);
+    C = __fmaf_rn(fh, xl, C);
+    C = __fmaf_rn(fl, xh, C);
+    C = __fadd_rn(C, e);
+    const float s = __fadd_rn(S, p);
+    const float bb = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    S = s;
+    C = __fadd_rn(C, err);
+}
+
+// (S, C) += (S2, C2) with S by TwoSum (symmetric in the two operands)
+__device__ __forceinline__ void ff_add(float &S, float &C, float S2, float C2)
+{
+    const float s = __fadd_rn(S, S2);
+    const float bb = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(S2, bb));
+    S = s;
+    C = __fadd_rn(__fadd_rn(C, C2), err);
+}
+
+// 16-byte vectors of float (4) or double (2)
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using type = float4;
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float dot(float4 a, float4 b, float c)
+    {
+        return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
+    }
+};
+template <> struct V16<double> {
+    using type = double2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double dot(double2 a, double2 b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
+};
+
+// ---- phase 1a: own factors, a warp per row (blocks of p = 3, one right-hand side)
+
+constexpr int kRowsThreads = 256;
+
+// rows [row0, row0 + rows) of Zb = F r_B, F in T (FP32 or FP64), rows of ld entries padded to 16 bytes
+template <int P, typename T>
+__device__ __forceinline__ void rows_plain(const double *__restrict__ r, const T *__restrict__ F, const SBox &b,
+                                           const Grid3 &g, int row0, int rows, double *__restrict__ zout,
+                                           unsigned char *smem)
+{
+    using VT = typename V16<T>::type;
+    constexpr int V = 16 / (int)sizeof(T);
+    constexpr int KV = (factor_ld<T>(sbox_max(P)) / V + 31) / 32;  // 16-byte vectors per lane and row
+    constexpr int RPW = sizeof(T) == 8 ? 2 : 4;                     // rows per warp and pass
+    T *rb = reinterpret_cast<T *>(smem);
+    const int n = b.n, ld = factor_ld<T>(n), nv = ld / V;
+    const int64_t base = box_base(b, g);
+    for (int t = threadIdx.x; t < ld; t += blockDim.x) rb[t] = t < n ? (T)r[base + box_rel(b, g, t)] : (T)0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    VT xr[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) xr[k] = lane + 32 * k < nv ? reinterpret_cast<const VT *>(rb)[lane + 32 * k] : V16<T>::zero();
+    const int row1 = min(n, row0 + rows);
+    for (int t = row0 + RPW * w; t < row1; t += RPW * nw) {
+        VT fv[RPW][KV];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            // rows past row1 repeat the last row (in bounds) and are not written
+            const VT *fr = reinterpret_cast<const VT *>(F + (size_t)min(t + q, row1 - 1) * ld);
+#pragma unroll
+            for (int k = 0; k < KV; ++k) fv[q][k] = lane + 32 * k < nv ? __ldcs(fr + lane + 32 * k) : V16<T>::zero();
+        }
+        T a[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            a[q] = (T)0;
+#pragma unroll
+            for (int k = 0; k < KV; ++k) a[q] = V16<T>::dot(fv[q][k], xr[k], a[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+        if (lane < RPW && t + lane < row1) {
+            T v = a[0];
+#pragma unroll
+            for (int q = 1; q < RPW; ++q)
+                if (lane == q) v = a[q];
+            zout[t + lane] = (double)v;
+        }
+    }
+}
+
+// the same for a double-float factor: entry j of a row is the float pair at 2j, 2j+1
+template <int P>
+__device__ __forceinline__ void rows_ff(const double *__restrict__ r, const float *__restrict__ F, const SBox &b,
+                                        const Grid3 &g, int row0, int rows, double *__restrict__ zout,
+                                        unsigned char *smem)
+{
+    constexpr int KV = (factor_ld<double>(sbox_max(P)) / 2 + 31) / 32;  // float4 = two entries
+    constexpr int RPW = 2;
+    float2 *rb = reinterpret_cast<float2 *>(smem);
+    const int n = b.n, ld = factor_ld<double>(n), nv = ld / 2;
+    const int64_t base = box_base(b, g);
+    for (int t = threadIdx.x; t < ld; t += blockDim.x)
+        rb[t] = t < n ? split_ff(r[base + box_rel(b, g, t)]) : make_float2(0.f, 0.f);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float4 xr[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k)
+        xr[k] = lane + 32 * k < nv ? reinterpret_cast<const float4 *>(rb)[lane + 32 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int row1 = min(n, row0 + rows);
+    for (int t = row0 + RPW * w; t < row1; t += RPW * nw) {
+        float4 fv[RPW][KV];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const float4 *fr = reinterpret_cast<const float4 *>(F + (size_t)min(t + q, row1 - 1) * 2 * ld);
+#pragma unroll
+            for (int k = 0; k < KV; ++k)
+                fv[q][k] = lane + 32 * k < nv ? __ldcs(fr + lane + 32 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float S[RPW], C[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            S[q] = 0.f;
+            C[q] = 0.f;
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+                ff_fma(fv[q][k].x, fv[q][k].y, xr[k].x, xr[k].y, S[q], C[q]);
+                ff_fma(fv[q][k].z, fv[q][k].w, xr[k].z, xr[k].w, S[q], C[q]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, S[q], o), c2 = __shfl_xor_sync(0xffffffffu, C[q], o);
+                ff_add(S[q], C[q], s2, c2);
+            }
+        if (lane < RPW && t + lane < row1) {
+            float s = S[0], c = C[0];
+#pragma unroll
+            for (int q = 1; q < RPW; ++q)
+                if (lane == q) {
+                    s = S[q];
+                    c = C[q];
+                }
+            zout[t + lane] = (double)s + (double)c;
+        }
+    }
+}
+
+// One work item per CTA: (slot, first row) of a block with its own factor; the slot's record
+// gives the factor's offset and storage (0 FP64, 1 FP32, 2 double-float).
+template <int P>
+__global__ void __launch_bounds__(kRowsThreads)
+    schwarz_rows_kernel(const double *__restrict__ r, const double *__restrict__ f64, const float *__restrict__ f32,
+                        const PatchRec *__restrict__ slots, const int2 *__restrict__ items, int rows, Grid3 g, int rule,
+                        double *__restrict__ zb, int zs, const int *__restrict__ done)
+{
+    __shared__ __align__(16) double smem_d[factor_ld<double>(sbox_max(P))];
+    if (done && *done) return;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(smem_d);
+    const int2 it = items[blockIdx.x];
+    const PatchRec pr = slots[it.x];
+    const SBox b = sbox(rule, P, g, pr.v);
+    double *zout = zb + (size_t)it.x * zs;
+    if (pr.prec == 1) rows_plain<P, float>(r, f32 + pr.off, b, g, it.y, rows, zout, smem);
+    else if (pr.prec == 2) rows_ff<P>(r, f32 + pr.off, b, g, it.y, rows, zout, smem);
+    else rows_plain<P, double>(r, f64 + pr.off, b, g, it.y, rows, zout, smem);
+}
+
+// ---- phase 1b: own factors, a thread per row (small blocks; several right-hand sides)
+//
+// Thread t of the item owns row row0 + t and walks the columns j: F[j][row] = F[row][j] (F is
+// symmetric) is read coalesced across the threads, and the NR residual entries r_k,B[j] are one
+// broadcast shared-memory read for the whole CTA.  nr <= NR right-hand sides are nlat apart in r, and
+// zsize apart in Zb.
+
+__host__ __device__ constexpr int cols_threads(int P) { return P >= 3 ? 128 : rnd32(sbox_max(P)); }
+
+template <int P, int NR, typename T>
+__device__ __forceinline__ void cols_plain(const double *__restrict__ r, int64_t nlat, int nr, const T *__restrict__ F,
+                                           const SBox &b, const Grid3 &g, int row0, double *__restrict__ zout,
+                                           int64_t zsize, unsigned char *smem)
+{
+    T(*rbT)[NR] = reinterpret_cast<T(*)[NR]>(smem);
+    const int n = b.n, ld = factor_ld<T>(n);
+    const int64_t base = box_base(b, g);
+    for (int e = threadIdx.x; e < n * NR; e += blockDim.x) {
+        const int t = e / NR, k = e % NR;
+        rbT[t][k] = k < nr ? (T)r[(int64_t)k * nlat + base + box_rel(b, g, t)] : (T)0;
+    }
+    __syncthreads();
+    const int row = row0 + threadIdx.x;
+    if (row >= n) return;
+    T acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = (T)0;
+    const T *__restrict__ col = F + row;
+#pragma unroll 8
+    for (int j = 0; j < n; ++j) {
+        const T f = __ldcs(col + (size_t)j * ld);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) acc[k] = fma(f, rbT[j][k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+        if (k < nr) zout[(int64_t)k * zsize + row] = (double)acc[k];
+}
+
+template <int P, int NR>
+__device__ __forceinline__ void cols_ff(const double *__restrict__ r, int64_t nlat, int nr, const float *__restrict__ F,
+                                        const SBox &b, const Grid3 &g, int row0, double *__restrict__ zout, int64_t zsize,
+                                        unsigned char *smem)
+{
+    float2(*rbT)[NR] = reinterpret_cast<float2(*)[NR]>(smem);
+    const int n = b.n, ld = factor_ld<double>(n);
+    const int64_t base = box_base(b, g);
+    for (int e = threadIdx.x; e < n * NR; e += blockDim.x) {
+        const int t = e / NR, k = e % NR;
+        rbT[t][k] = k < nr ? split_ff(r[(int64_t)k * nlat + base + box_rel(b, g, t)]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int row = row0 + threadIdx.x;
+    if (row >= n) return;
+    float S[NR], C[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) S[k] = C[k] = 0.f;
+    const float2 *__restrict__ col = reinterpret_cast<const float2 *>(F) + row;
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) {
+        const float2 f = __ldcs(col + (size_t)j * ld);
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+            if (k < nr) ff_fma(f.x, f.y, rbT[j][k].x, rbT[j][k].y, S[k], C[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+        if (k < nr) zout[(int64_t)k * zsize + row] = (double)S[k] + (double)C[k];
+}
+
+template <int P, int NR>
+__global__ void __launch_bounds__(cols_threads(P))
+    schwarz_cols_kernel(const double *__restrict__ r, int64_t nlat, int nr, const double *__restrict__ f64,
+                        const float *__restrict__ f32, const PatchRec *__restrict__ slots,
+                        const int2 *__restrict__ items, Grid3 g, int rule, double *__restrict__ zb, int zs,
+                        int64_t zsize, const int *__restrict__ done)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (done && *done) return;
+    const int2 it = items[blockIdx.x];
+    const PatchRec pr = slots[it.x];
+    const SBox b = sbox(rule, P, g, pr.v);
+    double *zout = zb + (size_t)it.x * zs;
+    if (pr.prec == 1) cols_plain<P, NR, float>(r, nlat, nr, f32 + pr.off, b, g, it.y, zout, zsize, smem);
+    else if (pr.prec == 2) cols_ff<P, NR>(r, nlat, nr, f32 + pr.off, b, g, it.y, zout, zsize, smem);
+    else cols_plain<P, NR, double>(r, nlat, nr, f64 + pr.off, b, g, it.y, zout, zsize, smem);
+}
+
+// ---- phase 1c: blocks sharing a factor, Zb[B_1 .. B_m] = F [r_B1 .. r_Bm] (m = count of the tile)
+//
+// Columns of the tile are (block, right-hand side) pairs, NC per group; the residual panel R[k][col]
+// (the gathered r_B, converted to T) sits in shared memory for the whole group.  The factor streams
+// through two shared-memory stages of KC rows: F[k0 .. k0 + KC)[0 .. ld) is one contiguous bulk copy
+// (F is symmetric, so these rows are the columns k0 .. k0 + KC of the product).  Thread (rg, cg)
+// accumulates rows 8 rg .. 8 rg + 7 for 8 columns (NC/8): two 16-byte reads of the stage and two of
+// the panel feed 64 multiply-adds.  Blocks with more rows than 8 x (threads / 8) take several passes
+// over the factor.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// dst, src and bytes multiples of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier, giving up (false) after `tries` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int tries)
+{
+    for (int i = 0; i < tries; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// Polls of the wait that lets copies still in flight land before a CTA that gave up leaves.
+constexpr int kDrainTries = 1 << 22;
+
+// m consecutive values from shared memory at a pointer aligned to min(16, m sizeof(T)) bytes, in
+// 16-byte (or 8-byte) vector reads
+template <typename T, int m>
+__device__ __forceinline__ void load_vec(const T *p, T *out)
+{
+    if constexpr (sizeof(T) * m % 16 == 0) {
+        using VT = typename V16<T>::type;
+        constexpr int V = 16 / (int)sizeof(T);
+#pragma unroll
+        for (int i = 0; i < m / V; ++i) {
+            const VT v = reinterpret_cast<const VT *>(p)[i];
+            if constexpr (V == 4) {
+                out[4 * i] = v.x;
+                out[4 * i + 1] = v.y;
+                out[4 * i + 2] = v.z;
+                out[4 * i + 3] = v.w;
+            } else {
+                out[2 * i] = v.x;
+                out[2 * i + 1] = v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < m; ++i) out[i] = p[i];
+    }
+}
+
+__host__ __device__ constexpr int gemm_threads(int P)
+{
+    return 8 * ((sbox_max(P) + 7) / 8) < 512 ? rnd32(8 * ((sbox_max(P) + 7) / 8)) : 512;
+}
+template <typename T, int P> struct GemmCfg {
+    static constexpr int NC = sizeof(T) == 4 ? (P == 4 ? 32 : 64) : (P == 4 ? 16 : 32);  // columns per group
+    static constexpr int KC = (sizeof(T) == 4 ? 16 : 8) / (P == 4 ? 2 : 1);            // factor rows per stage
+};
+
+// shared memory: 2 mbarriers | column sources and destinations | box offsets | panel | 2 stages
+template <int P, typename T>
+__host__ __device__ constexpr int gemm_stage_elems()
+{
+    return (GemmCfg<T, P>::KC * factor_ld<T>(sbox_max(P)) + 8 + 15) / 16 * 16;
+}
+template <int P, typename T>
+__host__ __device__ constexpr int gemm_panel_off()
+{
+    return (16 + 16 * GemmCfg<T, P>::NC + 4 * sbox_max(P) + 127) / 128 * 128;
+}
+template <int P, typename T>
+__host__ __device__ constexpr int gemm_smem_bytes()
+{
+    return gemm_panel_off<P, T>() + (int)sizeof(T) * (sbox_max(P) * GemmCfg<T, P>::NC + 2 * gemm_stage_elems<P, T>());
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(gemm_threads(P))
+    schwarz_gemm_kernel(const double *__restrict__ r, int64_t nlat, int nr, const T *__restrict__ pool,
+                        const PatchRec *__restrict__ slots, const int2 *__restrict__ tiles, Grid3 g, int rule,
+                        double *__restrict__ zb, int zs, int64_t zsize, int *err, int wait_tries,
+                        const int *__restrict__ done)
+{
+    constexpr int NC = GemmCfg<T, P>::NC, KC = GemmCfg<T, P>::KC, CPT = NC / 8, HALF = CPT / 2;
+    constexpr int SE = gemm_stage_elems<P, T>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (done && *done) return;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int64_t *src = reinterpret_cast<int64_t *>(smem + 16);   // NC: first lattice DOF of the column's r_B, -1 none
+    int64_t *dst = src + NC;                                  // NC: the column's Zb row 0, -1 none
+    int *rel = reinterpret_cast<int *>(smem + 16 + 16 * NC);  // box offsets
+    T *panel = reinterpret_cast<T *>(smem + gemm_panel_off<P, T>());
+    T *stage = panel + sbox_max(P) * NC;
+    const int2 tl = tiles[blockIdx.x];
+    const int first = tl.x, count = tl.y;
+    const PatchRec p0 = slots[first];
+    const SBox b0 = sbox(rule, P, g, p0.v);
+    const int n = b0.n, ld = factor_ld<T>(n);
+    const T *F = pool + p0.off;
+    const int tid = threadIdx.x, rg = tid >> 3, cg = tid & 7, nrg = blockDim.x >> 3;
+    const int per_group = NC / nr;                               // blocks per column group
+    const int groups = (count + per_group - 1) / per_group;
+    const int passes = (n + 8 * nrg - 1) / (8 * nrg);
+    const int nch = (n + KC - 1) / KC;
+    const int Q = groups * passes * nch;                         // factor chunks streamed by this CTA
+    for (int t = tid; t < n; t += blockDim.x) rel[t] = box_rel(b0, g, t);
+    if (tid == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    auto issue = [&](int q) {  // thread 0: chunk q into stage q & 1
+        const int c = q % nch, k0 = c * KC, kc = min(KC, n - k0);
+        const uint32_t bytes = (uint32_t)(kc * ld * (int)sizeof(T));
+        unsigned char *d = reinterpret_cast<unsigned char *>(stage + (size_t)(q & 1) * SE);
+        const unsigned char *s = reinterpret_cast<const unsigned char *>(F + (size_t)k0 * ld);
+        // the stage was last read through the generic proxy: order those reads before the copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect(&bar[q & 1], bytes);
+        for (uint32_t o = 0; o < bytes; o += 16384u) bulk_g2s(d + o, s + o, min(16384u, bytes - o), &bar[q & 1]);
+    };
+    if (tid == 0) {
+        issue(0);
+        if (Q > 1) issue(1);
+    }
+    int q = 0;
+    for (int grp = 0; grp < groups; ++grp) {
+        // columns of this group and their gathered residuals
+        for (int c = tid; c < NC; c += blockDim.x) {
+            const int pj = grp * per_group + c / nr, k = c % nr;
+            int64_t s = -1, d = -1;
+            if (c < per_group * nr && pj < count) {
+                const PatchRec pr = slots[first + pj];
+                s = (int64_t)k * nlat + box_base(sbox(rule, P, g, pr.v), g);
+                d = (int64_t)k * zsize + (int64_t)(first + pj) * zs;
+            }
+            src[c] = s;
+            dst[c] = d;
+        }
+        __syncthreads();
+        for (int e = tid; e < n * NC; e += blockDim.x) {
+            const int t = e / NC, c = e % NC;
+            const int64_t s = src[c];
+            panel[e] = s >= 0 ? (T)r[s + rel[t]] : (T)0;
+        }
+        __syncthreads();
+        for (int pass = 0; pass < passes; ++pass) {
+            const int row0 = pass * 8 * nrg + 8 * rg;
+            T acc[8][CPT];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) acc[i][j] = (T)0;
+            for (int c = 0; c < nch; ++c, ++q) {
+                const int s = q & 1;
+                const bool ok = __syncthreads_and(mbar_wait(&bar[s], (q >> 1) & 1, wait_tries));
+                if (!ok) {
+                    // flag the apply as failed; the copies still in flight land before the CTA leaves
+                    if (tid == 0) {
+                        atomicExch(err, 1);
+                        mbar_wait(&bar[s], (q >> 1) & 1, kDrainTries);
+                        if (q + 1 < Q) mbar_wait(&bar[s ^ 1], ((q + 1) >> 1) & 1, kDrainTries);
+                    }
+                    __syncthreads();
+                    return;
+                }
+                const int k0 = c * KC, kc = min(KC, n - k0);
+                if (row0 < n) {
+                    const T *fs = stage + (size_t)s * SE + row0;
+                    const T *pk = panel + (size_t)k0 * NC + cg * HALF;
+                    for (int kk = 0; kk < kc; ++kk) {
+                        T fv[8], rv[CPT];
+                        load_vec<T, 8>(fs + (size_t)kk * ld, fv);
+                        load_vec<T, HALF>(pk + (size_t)kk * NC, rv);
+                        load_vec<T, HALF>(pk + (size_t)kk * NC + NC / 2, rv + HALF);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+#pragma unroll
+                            for (int j = 0; j < CPT; ++j) acc[i][j] = fma(fv[i], rv[j], acc[i][j]);
+                    }
+                }
+                __syncthreads();  // every thread is done with stage s
+                if (tid == 0 && q + 2 < Q) issue(q + 2);
+            }
+            if (row0 < n) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    const int c = j < HALF ? cg * HALF + j : NC / 2 + cg * HALF + (j - HALF);
+                    const int64_t d = dst[c];
+                    if (d < 0) continue;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (row0 + i < n) zb[d + row0 + i] = (double)acc[i][j];
+                }
+            }
+        }
+        __syncthreads();  // the next group overwrites the columns and the panel
+    }
+}
+
+// ---- phase 2: z = D r + sum over the blocks containing each DOF of their Zb rows
+
+template <int P>
+__global__ void schwarz_sum_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ jac,
+                                   const double *__restrict__ zb, const int *__restrict__ slot_of, Grid3 g, int rule,
+                                   int zs, int64_t zsize, int64_t nlat, int nr, const int *__restrict__ done)
+{
+    if (done && *done) return;
+    const int64_t nnode = nlat / 3;
+    const int nid0 = rule == 3 ? g.n[0] : g.n[0] + 1, nid1 = rule == 3 ? g.n[1] : g.n[1] + 1;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nnode;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        const int L[3] = {(int)(node % g.M[0]), (int)((node / g.M[0]) % g.M[1]), (int)(node / ((int64_t)g.M[0] * g.M[1]))};
+        // per axis: the blocks whose box contains the node, ascending, with the node's offset in the box
+        int cid[3][2], cloc[3][2], cdim[3][2], cm[3];
+        for (int a = 0; a < 3; ++a) {
+            const int i = L[a], c = i / P, s = i - P * c;
+            int m = 0;
+            if (rule == 3) {
+                // element boxes [P c, P c + P]
+                if (s == 0 && c >= 1) {
+                    cid[a][m] = c - 1;
+                    cloc[a][m] = i - P * (c - 1);
+                    cdim[a][m++] = P + 1;
+                }
+                if (c < g.n[a]) {
+                    cid[a][m] = c;
+                    cloc[a][m] = s;
+                    cdim[a][m++] = P + 1;
+                }
+            } else {
+                // vertex patches [P v - (P-1), P v + (P-1)] clipped: the vertex c itself, or (inside a
+                // cell) both of its vertices
+                for (int v = c; v <= (s == 0 ? c : c + 1); ++v) {
+                    const int lo = max(0, P * v - (P - 1)), hi = min(g.M[a] - 1, P * v + (P - 1));
+                    cid[a][m] = v;
+                    cloc[a][m] = i - lo;
+                    cdim[a][m++] = hi - lo + 1;
+                }
+            }
+            cm[a] = m;
+        }
+        for (int k = 0; k < nr; ++k) {
+            const int64_t gi = (int64_t)k * nlat + 3 * node;
+            double acc[3];
+            for (int c = 0; c < 3; ++c) acc[c] = jac ? jac[3 * node + c] * r[gi + c] : 0.0;
+            for (int az = 0; az < cm[2]; ++az)
+                for (int ay = 0; ay < cm[1]; ++ay)
+                    for (int ax = 0; ax < cm[0]; ++ax) {
+                        const int slot = slot_of[cid[0][ax] + nid0 * (cid[1][ay] + nid1 * cid[2][az])];
+                        if (slot < 0) continue;
+                        const double *zr = zb + (int64_t)k * zsize + (int64_t)slot * zs +
+                                           3 * (cloc[0][ax] + cdim[0][ax] * (cloc[1][ay] + cdim[1][ay] * cloc[2][az]));
+                        for (int c = 0; c < 3; ++c) acc[c] += zr[c];
+                    }
+            for (int c = 0; c < 3; ++c) z[gi + c] = acc[c];
+        }
+    }
+}
+
+int sum_grid(int64_t nnode)
+{
+    int64_t b = (nnode + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)std::max<int64_t>(b, 1);
+}
+
+template <int P>
+void gemm_launch(const double *r, int64_t nlat, int nr, const double *f64, const float *f32, const SchwarzPlan &pl,
+                 double *zb, int64_t zsize, const int *done, cudaStream_t s)
+{
+    const Grid3 &g = pl.g;
+    if (pl.n_tiles32 > 0)
+        schwarz_gemm_kernel<P, float><<<pl.n_tiles32, gemm_threads(P), gemm_smem_bytes<P, float>(), s>>>(
+            r, nlat, nr, f32, pl.slots, pl.tiles, g, pl.rule, zb, pl.zs, zsize, pl.err, pl.wait_tries, done);
+    if (pl.n_tiles64 > 0)
+        schwarz_gemm_kernel<P, double><<<pl.n_tiles64, gemm_threads(P), gemm_smem_bytes<P, double>(), s>>>(
+            r, nlat, nr, f64, pl.slots, pl.tiles + pl.n_tiles32, g, pl.rule, zb, pl.zs, zsize, pl.err, pl.wait_tries,
+            done);
+}
+
+template <int P, int NR>
+void cols_launch(const double *r, int64_t nlat, int nr, const double *f64, const float *f32, const SchwarzPlan &pl,
+                 double *zb, int64_t zsize, const int *done, cudaStream_t s)
+{
+    const int smem = factor_ld<double>(sbox_max(P)) * NR * 8;
+    schwarz_cols_kernel<P, NR><<<pl.n_col_items, cols_threads(P), smem, s>>>(
+        r, nlat, nr, f64, f32, pl.slots, pl.col_items, pl.g, pl.rule, zb, pl.zs, zsize, done);
+}
+
+template <int P>
+void apply_p(const double *r, double *z, int64_t nlat, int nr, const double *f64, const float *f32,
+             const SchwarzPlan &pl, double *zb, const int *done, cudaStream_t s)
+{
+    const int64_t zsize = (int64_t)pl.nslots * pl.zs;
+    const bool gemm = pl.n_tiles32 + pl.n_tiles64 > 0;
+    const bool own = nr == 1 && P == 3 ? pl.n_row_items > 0 : pl.n_col_items > 0;
+    const bool side = pl.concurrent && gemm && own && pl.side;
+    if (side) {
+        // the shared-factor products on the second stream, beside the streamed factors
+        cudaEventRecord(pl.ev_fork, s);
+        cudaStreamWaitEvent(pl.side, pl.ev_fork, 0);
+        gemm_launch<P>(r, nlat, nr, f64, f32, pl, zb, zsize, done, pl.side);
+        cudaEventRecord(pl.ev_join, pl.side);
+    } else if (gemm) {
+        gemm_launch<P>(r, nlat, nr, f64, f32, pl, zb, zsize, done, s);
+    }
+    if (own) {
+        if constexpr (P == 3) {
+            if (nr == 1)
+                schwarz_rows_kernel<P><<<pl.n_row_items, kRowsThreads, 0, s>>>(r, f64, f32, pl.slots, pl.row_items,
+                                                                               pl.rows, pl.g, pl.rule, zb, pl.zs, done);
+            else
+                cols_launch<P, 8>(r, nlat, nr, f64, f32, pl, zb, zsize, done, s);
+        } else if (nr == 1)
+            cols_launch<P, 1>(r, nlat, nr, f64, f32, pl, zb, zsize, done, s);
+        else
+            cols_launch<P, 8>(r, nlat, nr, f64, f32, pl, zb, zsize, done, s);
+    }
+    if (side) cudaStreamWaitEvent(s, pl.ev_join, 0);
+    schwarz_sum_kernel<P><<<sum_grid(nlat / 3), 256, 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule, pl.zs,
+                                                             zsize, nlat, nr, done);
+}
+
+template <int P>
+cudaError_t prepare_p()
+{
+    cudaError_t e = cudaFuncSetAttribute(schwarz_gemm_kernel<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         gemm_smem_bytes<P, float>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(schwarz_gemm_kernel<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 gemm_smem_bytes<P, double>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(schwarz_cols_kernel<P, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 factor_ld<double>(sbox_max(P)) * 8 * 8);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(schwarz_cols_kernel<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 factor_ld<double>(sbox_max(P)) * 8);
+    return e;
+}
+
+static_assert(gemm_smem_bytes<3, float>() <= 227 * 1024, "GEMM tile exceeds shared memory");
+static_assert(gemm_smem_bytes<3, double>() <= 227 * 1024, "GEMM tile exceeds shared memory");
+static_assert(gemm_smem_bytes<4, float>() <= 227 * 1024, "GEMM tile exceeds shared memory");
+static_assert(gemm_smem_bytes<4, double>() <= 227 * 1024, "GEMM tile exceeds shared memory");
+static_assert(factor_ld<double>(sbox_max(4)) * 8 * 8 <= 227 * 1024, "multi-RHS panel exceeds shared memory");
+
+}  // namespace
+
+int schwarz_gemm_cols(int p, int prec)
+{
+    switch (p) {
+    case 1: return prec == 1 ? GemmCfg<float, 1>::NC : GemmCfg<double, 1>::NC;
+    case 2: return prec == 1 ? GemmCfg<float, 2>::NC : GemmCfg<double, 2>::NC;
+    case 3: return prec == 1 ? GemmCfg<float, 3>::NC : GemmCfg<double, 3>::NC;
+    default: return prec == 1 ? GemmCfg<float, 4>::NC : GemmCfg<double, 4>::NC;
+    }
+}
+
+int schwarz_col_rows(int p)
+{
+    switch (p) {
+    case 1: return cols_threads(1);
+    case 2: return cols_threads(2);
+    case 3: return cols_threads(3);
+    default: return cols_threads(4);
+    }
+}
+
+bool schwarz_uses_rows_kernel(int p) { return p == 3; }
+
+int schwarz_rows_threads() { return kRowsThreads; }
+
+cudaError_t schwarz_prepare(int p)
+{
+    switch (p) {
+    case 1: return prepare_p<1>();
+    case 2: return prepare_p<2>();
+    case 3: return prepare_p<3>();
+    default: return prepare_p<4>();
+    }
+}
+
+void launch_schwarz_apply_multi(int p, const double *r, double *z, int64_t nlat, int nr, const double *f64,
+                                const float *f32, const SchwarzPlan &plan, double *zb, const int *done, cudaStream_t s)
+{
+    switch (p) {
+    case 1: apply_p<1>(r, z, nlat, nr, f64, f32, plan, zb, done, s); break;
+    case 2: apply_p<2>(r, z, nlat, nr, f64, f32, plan, zb, done, s); break;
+    case 3: apply_p<3>(r, z, nlat, nr, f64, f32, plan, zb, done, s); break;
+    case 4: apply_p<4>(r, z, nlat, nr, f64, f32, plan, zb, done, s); break;
+    default: break;
+    }
+}
+
+void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *f64, const float *f32,
+                          const SchwarzPlan &plan, const int *done, cudaStream_t s)
+{
+    const int64_t nlat = 3 * (int64_t)g.M[0] * g.M[1] * g.M[2];
+    launch_schwarz_apply_multi(p, r, z, nlat, 1, f64, f32, plan, plan.zb, done, s);
+}
+
+}  // namespace fcm

@@ -17,11 +17,12 @@ LIB_PATH = os.path.join(_HERE, "libfcm.so")
 FCM_OK, FCM_EINVAL, FCM_ENOMEM, FCM_ECUDA, FCM_ENOTCONV, FCM_EBREAKDOWN, FCM_ETIMEOUT, FCM_ESTATE = range(8)
 STATUS_NAMES = ["FCM_OK", "FCM_EINVAL", "FCM_ENOMEM", "FCM_ECUDA", "FCM_ENOTCONV", "FCM_EBREAKDOWN",
                 "FCM_ETIMEOUT", "FCM_ESTATE"]
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_FP64 = 0, 1, 2
 
 # Every symbol include/fcm.h declares (checked by the tests).
 EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_solve", "fcm_pcg_solve_host",
-            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_last_error", "fcm_destroy",
+            "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_apply_S_many",
+            "fcm_set_wait_limit", "fcm_last_error", "fcm_destroy",
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
@@ -61,9 +62,9 @@ class Info(ctypes.Structure):
                 ("n_blocks", ctypes.c_int64), ("n_blocks_fp32", ctypes.c_int64), ("kapply_fmas", ctypes.c_int64),
                 ("sapply_fmas", ctypes.c_int64), ("max_block_cond", ctypes.c_double),
                 ("coarse_seconds", ctypes.c_double), ("n_jacobi", ctypes.c_int64),
-                ("rows32", ctypes.c_int), ("rows64", ctypes.c_int), ("tiles_persistent", ctypes.c_int),
+                ("stream_rows", ctypes.c_int), ("schwarz_concurrent", ctypes.c_int),
                 ("tune_seconds", ctypes.c_double * 8),
-                ("device_error", ctypes.c_int)]
+                ("device_error", ctypes.c_int), ("n_factors_ff", ctypes.c_int64), ("n_gemm_blocks", ctypes.c_int64)]
 
 
 class PrecondOpts(ctypes.Structure):
@@ -111,6 +112,8 @@ def load(path: str = LIB_PATH):
     L.fcm_apply_K.argtypes = [P, P, P]
     L.fcm_apply_S.argtypes = [P, P, P]
     L.fcm_apply_S_noalloc.argtypes = [P, P, P]
+    L.fcm_apply_S_many.argtypes = [P, P, ctypes.c_int, P]
+    L.fcm_set_wait_limit.argtypes = [P, ctypes.c_int]
     L.fcm_last_error.argtypes = [P]
     L.fcm_last_error.restype = ctypes.c_char_p
     L.fcm_destroy.argtypes = [P]
@@ -244,20 +247,22 @@ class Solver:
 
     def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0,
                       autotune=True, launch=None):
-        """blocks: "vertex" (vertex patches) or "element" (element blocks of the cells with
-        eta_T <= eta_bar, diagonal scaling for the DOFs in no block).  autotune: time the
-        Schwarz apply for a few launch shapes and keep the fastest (results do not depend
-        on the choice).  launch ("items" or "persistent") fixes the default tile with that
-        launch instead."""
+        """precision: "fp64", "mixed" (FP32 factors, double-float pairs above cond_fp64) or
+        "mixed_fp64" (FP32 factors, FP64 above cond_fp64).  blocks: "vertex" (vertex patches)
+        or "element" (element blocks of the cells with eta_T <= eta_bar, diagonal scaling for
+        the DOFs in no block).  autotune: time the Schwarz apply for a few launch shapes and
+        keep the fastest (results do not depend on the choice).  launch ("serial" or
+        "concurrent": the shared-factor products after or beside the streamed factors) fixes
+        the default shape instead."""
         if blocks not in ("vertex", "element"):
             raise ValueError(f"unknown block rule {blocks!r}")
         o = PrecondOpts()
         o.eps = eps
-        o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        o.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED, "mixed_fp64": PREC_MIXED_FP64}[precision]
         o.cond_fp64 = cond_fp64
         o.block_rule = BLOCKS_ELEMENT if blocks == "element" else BLOCKS_VERTEX
         o.eta_bar = eta_bar
-        o.fixed_tiles = {None: 0 if autotune else 1, "items": 1, "persistent": 2}[launch]
+        o.fixed_tiles = {None: 0 if autotune else 1, "serial": 1, "concurrent": 2}[launch]
         self._check(load().fcm_precond_build(self.ctx, ctypes.byref(o)))
         self.info = self.get_info()
 
@@ -296,9 +301,20 @@ class Solver:
         return y
 
     def apply_S(self, r, out=None):
-        z = out if out is not None else self.empty()
-        self._check(load().fcm_apply_S(self.ctx, self._vec(r, "r"), self._vec(z, "out")))
+        """z = S r; r may hold 1..8 vectors (n_lattice apart), applied in one call."""
+        pr = self._vec(r, "r", multiple=True)
+        nr = r.numel() // self.n
+        z = out if out is not None else self.empty(nr)
+        pz = self._vec(z, "out", nr)
+        if nr == 1:
+            self._check(load().fcm_apply_S(self.ctx, pr, pz))
+        else:
+            self._check(load().fcm_apply_S_many(self.ctx, pr, nr, pz))
         return z
+
+    def set_wait_limit(self, tries):
+        """Polls of the Schwarz kernels' bounded bulk-copy wait (0: give up at once; < 0: default)."""
+        self._check(load().fcm_set_wait_limit(self.ctx, int(tries)))
 
     def close(self):
         if getattr(self, "ctx", None) and self.ctx.value:

@@ -20,7 +20,11 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.mark.parametrize("levels,base,shape", [(3, 4, (8, 8, 8)), (2, 3, (4, 6, 2)), (1, 2, (3, 2, 5))])
+# the last case is the network of the learned correction's workload (4 levels, channels 16/32/64/64):
+# its inner levels have Cin = 32, 64 and 128 (decoder concatenation), beyond one 16-channel chunk of
+# the conv kernels' input loop
+@pytest.mark.parametrize("levels,base,shape", [(3, 4, (8, 8, 8)), (2, 3, (4, 6, 2)), (1, 2, (3, 2, 5)),
+                                               (4, 16, (16, 16, 16))])
 def test_unet_forward_backward_match_oracle(levels, base, shape):
     from paper_1809_00828_gb300 import fcm
     net = fcm.UNet(in_ch=4, out_ch=3, base=base, levels=levels, seed=7)
