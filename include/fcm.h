@@ -152,6 +152,10 @@ enum { FCM_BLOCKS_VERTEX = 0, FCM_BLOCKS_ELEMENT = 3 };
  *        factors or beside them on a second stream) and keep the fastest; 1 keeps
  *        the default tile, products after the streamed factors; 2 the default
  *        tile, both at once.  S r does not depend on the choice.
+ *   simt_shared: 0 (default) applies the FP32 shared factors of the mixed
+ *        forms (p = 2, 3; one right-hand side) on the tensor cores (tcgen05,
+ *        TF32 three-pass products, ~2^-22 relative); 1 applies them on the
+ *        CUDA cores in FP32.
  * A zero-initialised struct with eps, precision and cond_fp64 set selects
  * vertex patches and the autotuned tiles. */
 typedef struct {
@@ -161,6 +165,7 @@ typedef struct {
     int block_rule;
     double eta_bar;
     int fixed_tiles;
+    int simt_shared;
 } fcm_precond_opts;
 
 /* Solver result details. */

@@ -174,7 +174,8 @@ void free_ctx(fcm_ctx *C)
     if (!C) return;
     destroy_graph(C);
     void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32,
-                    C->d_slots, C->d_slot_of, C->d_items, C->d_zb, C->d_mzb, C->d_eta, C->d_jac, C->d_err,
+                    C->d_slots, C->d_slot_of, C->d_items, C->d_zb, C->d_mzb, C->d_tc_tiles, C->d_tc_ft,
+                    C->d_eta, C->d_jac, C->d_err,
                     C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
                     C->d_out2};
     for (void *q : ptrs)
@@ -426,10 +427,12 @@ fcm_status fcm_precond_build(fcm_ctx *C, const fcm_precond_opts *opts)
     o.block_rule = FCM_BLOCKS_VERTEX;
     o.eta_bar = 1.0;
     o.fixed_tiles = 0;
+    o.simt_shared = 0;
     if (opts) o = *opts;
     if (!(o.eps == o.eps) || (o.precision != FCM_PREC_FP64 && o.precision != FCM_PREC_MIXED && o.precision != FCM_PREC_MIXED_FP64) || !(o.cond_fp64 > 0.0) ||
         (o.block_rule != FCM_BLOCKS_VERTEX && o.block_rule != FCM_BLOCKS_ELEMENT) ||
-        (o.block_rule == FCM_BLOCKS_ELEMENT && !(o.eta_bar >= 0.0)) || o.fixed_tiles < 0 || o.fixed_tiles > 2) {
+        (o.block_rule == FCM_BLOCKS_ELEMENT && !(o.eta_bar >= 0.0)) || o.fixed_tiles < 0 || o.fixed_tiles > 2 ||
+        o.simt_shared < 0 || o.simt_shared > 1) {
         C->err = "fcm_precond_build: invalid options";
         return FCM_EINVAL;
     }

@@ -58,6 +58,14 @@ struct KCells {
 // own factor in row tiles ((slot, first row) work items), with a warp per row (row_items, `rows`
 // rows each; p = 3, one right-hand side) or a thread per row (col_items, schwarz_col_rows(p) rows
 // each).  slot_of maps a vertex (or cell) id to its slot, -1 when the block has no free DOF.
+// A tile of the tensor-core product: 128 consecutive slots (`count` used) sharing one FP32 factor, its
+// factor tiles at ft_off (floats), nch chunks of 16 K values.
+struct TcTile {
+    int first, count;
+    int64_t ft_off;
+    int nch, pad;
+};
+
 struct SchwarzPlan {
     Grid3 g;
     int rule;                 // 0 vertex patches, 3 element blocks (FCM_BLOCKS_*)
@@ -71,7 +79,12 @@ struct SchwarzPlan {
     int n_col_items;
     const int2 *tiles;        // n_tiles32 FP32 tiles, then n_tiles64 FP64 tiles
     int n_tiles32, n_tiles64;
+    int n_tiles32_plain;      // FP32 tiles of the factors without tensor-core tiles (listed first)
+    const TcTile *tc_tiles;   // tensor-core tiles (one right-hand side), same blocks as the rest of the FP32 tiles
+    int n_tc_tiles;
+    const float *tc_ft;       // factor tiles (hi, lo) in the tensor core's layout
     double *zb;               // Zb for one right-hand side
+    int pairs;                // 1: Zb entries are float pairs (mixed forms), 0: FP64 values
     const double *jac;        // 1 / K_ll for the free DOFs in no block, 0 elsewhere (lattice); null if none
     int *err;                 // device flag, set to 1 by a bulk-copy wait that ran out
     int wait_tries;           // polls of a bulk-copy wait before it gives up
@@ -94,6 +107,11 @@ void launch_schwarz_apply_multi(int p, const double *r, double *z, int64_t nlat,
 int schwarz_gemm_cols(int p, int prec);
 int schwarz_col_rows(int p);
 bool schwarz_uses_rows_kernel(int p);
+// tensor-core products (p = 2, 3): floats of one factor's tiles, and the kernel that builds them from an
+// FP64 factor (rows padded to factor_ld<double>(n))
+bool schwarz_tc_supported(int p);
+int64_t schwarz_tc_factor_floats(int p, int n);
+cudaError_t schwarz_tc_factor(int p, const double *F, int n, float *ft, cudaStream_t s);
 int schwarz_rows_threads();
 // kernel attributes (dynamic shared memory); host call, outside stream capture
 cudaError_t schwarz_prepare(int p);
@@ -181,6 +199,8 @@ struct fcm_ctx {
     fcm::PatchRec *d_slots = nullptr;
     int *d_slot_of = nullptr;
     int2 *d_items = nullptr;         // row items, column items, GEMM tiles
+    fcm::TcTile *d_tc_tiles = nullptr;
+    float *d_tc_ft = nullptr;        // tensor-core factor tiles
     double *d_zb = nullptr;          // block products of one S apply
     cudaStream_t side = nullptr;     // second stream of the Schwarz apply (shared-factor products)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -268,6 +268,11 @@ __global__ void to_ff_kernel(const double *in, float *out, int n)
 // (GEMM tiles); factors with fewer blocks stream once per block.
 constexpr int kGemmMinBlocks = 8;
 
+// Largest retained condition number of an FP32 shared factor applied by the tensor cores (TF32
+// three-pass products, ~2^-22 relative): the perturbation stays below ~1e-1 of the smallest retained
+// eigenvalue.  Shared factors belong to uncut patches, whose condition numbers are far below it.
+constexpr double kTcCondMax = 1e5;
+
 struct FactorInfo {
     int rep;      // representative vertex
     int n;        // box size
@@ -570,15 +575,26 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
         PC_CUDA(cudaStreamSynchronize(st));
     }
 
-    // ---- slots: the blocks of shared factors first (FP32 factors, then FP64), consecutive per factor,
-    // then the blocks streaming their own factor
+    // ---- slots: the blocks of shared factors first (FP32 factors without, then with tensor-core tiles,
+    // then FP64), consecutive per factor, then the blocks streaming their own factor.  FP32 shared factors
+    // of the mixed form with a retained condition number up to kTcCondMax also get tensor-core tiles
+    // (TF32 three-pass products, about 2^-22 relative); the SIMT tiles of the same blocks serve the
+    // multi-RHS applies.
+    std::vector<char> tc(fac.size(), 0);
+    for (size_t f = 0; f < fac.size(); ++f)
+        tc[f] = mixed && !o.simt_shared && shared[f] && prec[f] == 1 && schwarz_tc_supported(p) &&
+                fac[f].cond <= kTcCondMax;
     std::vector<PatchRec> slots;
     std::vector<int> slot_of(npatch, -1);
     std::vector<int2> tiles32, tiles64;
-    int64_t gemm_blocks = 0;
-    for (int want = 1; want >= 0; --want)
+    std::vector<TcTile> tc_tiles;
+    std::vector<int64_t> ft_off(fac.size(), -1);
+    int64_t gemm_blocks = 0, ft_floats = 0;
+    int n_tiles32_plain = 0;
+    for (int pass = 0; pass < 3; ++pass) {
+        const int want = pass < 2 ? 1 : 0;
         for (size_t f = 0; f < fac.size(); ++f) {
-            if (!shared[f] || prec[f] != want) continue;
+            if (!shared[f] || prec[f] != want || (want == 1 && tc[f] != (pass == 1))) continue;
             const int nc = schwarz_gemm_cols(p, want);
             const int first = (int)slots.size();
             for (int v : blocks_of[f]) {
@@ -588,7 +604,28 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
             const int cnt = (int)blocks_of[f].size();
             for (int s0 = 0; s0 < cnt; s0 += nc) (want == 1 ? tiles32 : tiles64).push_back(make_int2(first + s0, std::min(nc, cnt - s0)));
             gemm_blocks += cnt;
+            if (pass == 1) {
+                ft_off[f] = ft_floats;
+                ft_floats += schwarz_tc_factor_floats(p, fac[f].n);
+                const int nch = (fac[f].n + 15) / 16;
+                for (int s0 = 0; s0 < cnt; s0 += 128) tc_tiles.push_back({first + s0, std::min(128, cnt - s0), ft_off[f], nch, 0});
+            }
         }
+        if (pass == 0) n_tiles32_plain = (int)tiles32.size();
+    }
+    // factor tiles of the tensor-core products, from the FP64 staging copy
+    if (C->d_tc_ft) cudaFree(C->d_tc_ft);
+    if (C->d_tc_tiles) cudaFree(C->d_tc_tiles);
+    C->d_tc_ft = nullptr;
+    C->d_tc_tiles = nullptr;
+    if (!tc_tiles.empty()) {
+        PC_CUDA(cudaMalloc(&C->d_tc_ft, sizeof(float) * ft_floats));
+        PC_CUDA(cudaMalloc(&C->d_tc_tiles, sizeof(TcTile) * tc_tiles.size()));
+        PC_CUDA(cudaMemcpyAsync(C->d_tc_tiles, tc_tiles.data(), sizeof(TcTile) * tc_tiles.size(), cudaMemcpyHostToDevice, st));
+        for (size_t f = 0; f < fac.size(); ++f)
+            if (ft_off[f] >= 0) PC_CUDA(schwarz_tc_factor(p, stage + fac[f].off, fac[f].n, C->d_tc_ft + ft_off[f], st));
+        PC_CUDA(cudaStreamSynchronize(st));
+    }
     std::vector<int> own_slots[3];  // by storage
     for (size_t f = 0; f < fac.size(); ++f) {
         if (shared[f]) continue;
@@ -697,7 +734,12 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     plan.tiles = d_tiles;
     plan.n_tiles32 = (int)tiles32.size();
     plan.n_tiles64 = (int)tiles64.size();
+    plan.n_tiles32_plain = n_tiles32_plain;
+    plan.tc_tiles = C->d_tc_tiles;
+    plan.n_tc_tiles = (int)tc_tiles.size();
+    plan.tc_ft = C->d_tc_ft;
     plan.zb = C->d_zb;
+    plan.pairs = mixed ? 1 : 0;
     plan.err = C->d_err;
     plan.wait_tries = C->wait_tries;
     plan.side = C->side;

@@ -77,14 +77,111 @@ __device__ __forceinline__ int64_t box_base(const SBox &b, const Grid3 &g)
     return 3 * (b.lo[0] + (int64_t)g.M[0] * (b.lo[1] + (int64_t)g.M[1] * b.lo[2]));
 }
 
-// ---- double-float arithmetic (FP32 pipe)
+// ---- FP64 -> FP32 splits by integer operations
+//
+// GB300's FP64 pipe, which also converts between FP64 and FP32, does 2 operations per clock per SM, so
+// the kernels never convert a gathered FP64 value with it.  split_bits<MB> reads the value's bits:
+// hi = x with its significand cut to MB fraction bits (exact in a format with MB fraction bits), lo =
+// x - hi (a 42 to 52 - MB bit integer times a power of two) rounded to MB + 1 significant bits, half
+// up in magnitude.  MB = 23: a float pair with |x - hi - lo| <= 2^-48 |x|; MB = 10: two TF32 values
+// with |x - hi - lo| <= 2^-22 |x|.  |x| below 2^-126 gives +-0; beyond the FP32 range +-inf (NaN
+// stays NaN), as a conversion would; a lo below 2^-126 is dropped.
+template <int MB>
+__device__ __forceinline__ void split_bits(double x, float &hi, float &lo)
+{
+    constexpr int CUT = 52 - MB;  // fraction bits of x below hi
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const int E = (int)(u >> 52) & 0x7FF;
+    const unsigned long long M = u & 0xFFFFFFFFFFFFFull;
+    const int ef = E - 896;  // FP32 exponent field of x: E - 1023 + 127
+    lo = 0.f;
+    if (ef <= 0) {
+        hi = __uint_as_float(sign);
+        return;
+    }
+    if (ef >= 255) {
+        hi = __uint_as_float(sign | (E == 0x7FF && M ? 0x7FC00000u : 0x7F800000u));
+        return;
+    }
+    hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((unsigned)(M >> CUT) << (23 - MB)));
+    const unsigned long long R = M & ((1ull << CUT) - 1);  // x - hi = R 2^(E - 1075)
+    if (R == 0) return;
+    const int t = 63 - __clzll((long long)R);               // leading one of R
+    int e = ef - 52 + t;                                    // FP32 exponent field of lo
+    unsigned q;                                             // MB + 1 significant bits
+    if (t > MB) {
+        q = (unsigned)(((R >> (t - MB - 1)) + 1) >> 1);
+        if (q == (2u << MB)) {
+            q = 1u << MB;
+            ++e;
+        }
+    } else {
+        q = (unsigned)(R << (MB - t));
+    }
+    if (e > 0) lo = __uint_as_float(sign | ((unsigned)e << 23) | ((q & ((1u << MB) - 1)) << (23 - MB)));
+}
 
-// fl32(x) and fl32(x - fl32(x)): x = hi + lo to 2^-48 relative
+// x as a float pair, x = hi + lo to 2^-48 relative
 __device__ __forceinline__ float2 split_ff(double x)
 {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
+    float h, l;
+    split_bits<23>(x, h, l);
+    return make_float2(h, l);
 }
+
+// x rounded to FP32 (the pair's sum: within half an ulp but for ties)
+__device__ __forceinline__ float to_f32(double x)
+{
+    float h, l;
+    split_bits<23>(x, h, l);
+    return __fadd_rn(h, l);
+}
+
+// a gathered residual value in the factor's type
+template <typename T> __device__ __forceinline__ T gathered(double x);
+template <> __device__ __forceinline__ float gathered<float>(double x) { return to_f32(x); }
+template <> __device__ __forceinline__ double gathered<double>(double x) { return x; }
+
+// FP32 -> FP64 from the bits (exact; FP32 subnormals become zero)
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long frac = (unsigned long long)(b & 0x7FFFFFu) << 29;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    if (e == 0xFF) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | frac));
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896) << 52) | frac));
+}
+
+// Block products Zb.  With `pairs` (the mixed forms) an entry is a float pair (hi, lo) whose sum is
+// the value: FP32 results (v, 0), double-float results (S, C), FP64 results split by split_bits<23>;
+// the sum kernel then adds them on the FP32 pipe.  Otherwise (FP64 form) an entry is an FP64 value.
+__device__ __forceinline__ void put_f32(double *zb, int64_t i, float v, bool pairs)
+{
+    if (pairs) reinterpret_cast<float2 *>(zb)[i] = make_float2(v, 0.f);
+    else zb[i] = f2d(v);
+}
+__device__ __forceinline__ void put_ff(double *zb, int64_t i, float s, float c, bool pairs)
+{
+    if (pairs) reinterpret_cast<float2 *>(zb)[i] = make_float2(s, c);
+    else zb[i] = f2d(s) + f2d(c);
+}
+__device__ __forceinline__ void put_f64(double *zb, int64_t i, double v, bool pairs)
+{
+    if (pairs) {
+        float h, l;
+        split_bits<23>(v, h, l);
+        reinterpret_cast<float2 *>(zb)[i] = make_float2(h, l);
+    } else {
+        zb[i] = v;
+    }
+}
+__device__ __forceinline__ void put_val(double *zb, int64_t i, float v, bool pairs) { put_f32(zb, i, v, pairs); }
+__device__ __forceinline__ void put_val(double *zb, int64_t i, double v, bool pairs) { put_f64(zb, i, v, pairs); }
+
+// ---- double-float arithmetic (FP32 pipe)
 
 // S + C += (fh + fl)(xh + xl): the product fh xh exactly as p + e (FMA), the cross terms in FP32,
 // fl xl (2^-48 relative) dropped; S accumulates by TwoSum, its rounding errors go to C.  The
@@ -137,7 +234,7 @@ constexpr int kRowsThreads = 256;
 template <int P, typename T>
 __device__ __forceinline__ void rows_plain(const double *__restrict__ r, const T *__restrict__ F, const SBox &b,
                                            const Grid3 &g, int row0, int rows, double *__restrict__ zout,
-                                           unsigned char *smem)
+                                           bool pairs, unsigned char *smem)
 {
     using VT = typename V16<T>::type;
     constexpr int V = 16 / (int)sizeof(T);
@@ -146,7 +243,7 @@ __device__ __forceinline__ void rows_plain(const double *__restrict__ r, const T
     T *rb = reinterpret_cast<T *>(smem);
     const int n = b.n, ld = factor_ld<T>(n), nv = ld / V;
     const int64_t base = box_base(b, g);
-    for (int t = threadIdx.x; t < ld; t += blockDim.x) rb[t] = t < n ? (T)r[base + box_rel(b, g, t)] : (T)0;
+    for (int t = threadIdx.x; t < ld; t += blockDim.x) rb[t] = t < n ? gathered<T>(r[base + box_rel(b, g, t)]) : (T)0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     VT xr[KV];
@@ -178,7 +275,7 @@ __device__ __forceinline__ void rows_plain(const double *__restrict__ r, const T
 #pragma unroll
             for (int q = 1; q < RPW; ++q)
                 if (lane == q) v = a[q];
-            zout[t + lane] = (double)v;
+            put_val(zout, t + lane, v, pairs);
         }
     }
 }
@@ -186,7 +283,7 @@ __device__ __forceinline__ void rows_plain(const double *__restrict__ r, const T
 // the same for a double-float factor: entry j of a row is the float pair at 2j, 2j+1
 template <int P>
 __device__ __forceinline__ void rows_ff(const double *__restrict__ r, const float *__restrict__ F, const SBox &b,
-                                        const Grid3 &g, int row0, int rows, double *__restrict__ zout,
+                                        const Grid3 &g, int row0, int rows, double *__restrict__ zout, bool pairs,
                                         unsigned char *smem)
 {
     constexpr int KV = (factor_ld<double>(sbox_max(P)) / 2 + 31) / 32;  // float4 = two entries
@@ -238,7 +335,7 @@ __device__ __forceinline__ void rows_ff(const double *__restrict__ r, const floa
                     s = S[q];
                     c = C[q];
                 }
-            zout[t + lane] = (double)s + (double)c;
+            put_ff(zout, t + lane, s, c, pairs);
         }
     }
 }
@@ -249,7 +346,7 @@ template <int P>
 __global__ void __launch_bounds__(kRowsThreads)
     schwarz_rows_kernel(const double *__restrict__ r, const double *__restrict__ f64, const float *__restrict__ f32,
                         const PatchRec *__restrict__ slots, const int2 *__restrict__ items, int rows, Grid3 g, int rule,
-                        double *__restrict__ zb, int zs, const int *__restrict__ done)
+                        double *__restrict__ zb, int zs, int pairs, const int *__restrict__ done)
 {
     __shared__ __align__(16) double smem_d[factor_ld<double>(sbox_max(P))];
     if (done && *done) return;
@@ -258,9 +355,9 @@ __global__ void __launch_bounds__(kRowsThreads)
     const PatchRec pr = slots[it.x];
     const SBox b = sbox(rule, P, g, pr.v);
     double *zout = zb + (size_t)it.x * zs;
-    if (pr.prec == 1) rows_plain<P, float>(r, f32 + pr.off, b, g, it.y, rows, zout, smem);
-    else if (pr.prec == 2) rows_ff<P>(r, f32 + pr.off, b, g, it.y, rows, zout, smem);
-    else rows_plain<P, double>(r, f64 + pr.off, b, g, it.y, rows, zout, smem);
+    if (pr.prec == 1) rows_plain<P, float>(r, f32 + pr.off, b, g, it.y, rows, zout, pairs, smem);
+    else if (pr.prec == 2) rows_ff<P>(r, f32 + pr.off, b, g, it.y, rows, zout, pairs, smem);
+    else rows_plain<P, double>(r, f64 + pr.off, b, g, it.y, rows, zout, pairs, smem);
 }
 
 // ---- phase 1b: own factors, a thread per row (small blocks; several right-hand sides)
@@ -275,14 +372,14 @@ __host__ __device__ constexpr int cols_threads(int P) { return P >= 3 ? 128 : rn
 template <int P, int NR, typename T>
 __device__ __forceinline__ void cols_plain(const double *__restrict__ r, int64_t nlat, int nr, const T *__restrict__ F,
                                            const SBox &b, const Grid3 &g, int row0, double *__restrict__ zout,
-                                           int64_t zsize, unsigned char *smem)
+                                           int64_t zsize, bool pairs, unsigned char *smem)
 {
     T(*rbT)[NR] = reinterpret_cast<T(*)[NR]>(smem);
     const int n = b.n, ld = factor_ld<T>(n);
     const int64_t base = box_base(b, g);
     for (int e = threadIdx.x; e < n * NR; e += blockDim.x) {
         const int t = e / NR, k = e % NR;
-        rbT[t][k] = k < nr ? (T)r[(int64_t)k * nlat + base + box_rel(b, g, t)] : (T)0;
+        rbT[t][k] = k < nr ? gathered<T>(r[(int64_t)k * nlat + base + box_rel(b, g, t)]) : (T)0;
     }
     __syncthreads();
     const int row = row0 + threadIdx.x;
@@ -299,13 +396,13 @@ __device__ __forceinline__ void cols_plain(const double *__restrict__ r, int64_t
     }
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-        if (k < nr) zout[(int64_t)k * zsize + row] = (double)acc[k];
+        if (k < nr) put_val(zout, (int64_t)k * zsize + row, acc[k], pairs);
 }
 
 template <int P, int NR>
 __device__ __forceinline__ void cols_ff(const double *__restrict__ r, int64_t nlat, int nr, const float *__restrict__ F,
                                         const SBox &b, const Grid3 &g, int row0, double *__restrict__ zout, int64_t zsize,
-                                        unsigned char *smem)
+                                        bool pairs, unsigned char *smem)
 {
     float2(*rbT)[NR] = reinterpret_cast<float2(*)[NR]>(smem);
     const int n = b.n, ld = factor_ld<double>(n);
@@ -330,7 +427,7 @@ __device__ __forceinline__ void cols_ff(const double *__restrict__ r, int64_t nl
     }
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-        if (k < nr) zout[(int64_t)k * zsize + row] = (double)S[k] + (double)C[k];
+        if (k < nr) put_ff(zout, (int64_t)k * zsize + row, S[k], C[k], pairs);
 }
 
 template <int P, int NR>
@@ -338,7 +435,7 @@ __global__ void __launch_bounds__(cols_threads(P))
     schwarz_cols_kernel(const double *__restrict__ r, int64_t nlat, int nr, const double *__restrict__ f64,
                         const float *__restrict__ f32, const PatchRec *__restrict__ slots,
                         const int2 *__restrict__ items, Grid3 g, int rule, double *__restrict__ zb, int zs,
-                        int64_t zsize, const int *__restrict__ done)
+                        int64_t zsize, int pairs, const int *__restrict__ done)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if (done && *done) return;
@@ -346,9 +443,9 @@ __global__ void __launch_bounds__(cols_threads(P))
     const PatchRec pr = slots[it.x];
     const SBox b = sbox(rule, P, g, pr.v);
     double *zout = zb + (size_t)it.x * zs;
-    if (pr.prec == 1) cols_plain<P, NR, float>(r, nlat, nr, f32 + pr.off, b, g, it.y, zout, zsize, smem);
-    else if (pr.prec == 2) cols_ff<P, NR>(r, nlat, nr, f32 + pr.off, b, g, it.y, zout, zsize, smem);
-    else cols_plain<P, NR, double>(r, nlat, nr, f64 + pr.off, b, g, it.y, zout, zsize, smem);
+    if (pr.prec == 1) cols_plain<P, NR, float>(r, nlat, nr, f32 + pr.off, b, g, it.y, zout, zsize, pairs, smem);
+    else if (pr.prec == 2) cols_ff<P, NR>(r, nlat, nr, f32 + pr.off, b, g, it.y, zout, zsize, pairs, smem);
+    else cols_plain<P, NR, double>(r, nlat, nr, f64 + pr.off, b, g, it.y, zout, zsize, pairs, smem);
 }
 
 // ---- phase 1c: blocks sharing a factor, Zb[B_1 .. B_m] = F [r_B1 .. r_Bm] (m = count of the tile)
@@ -462,7 +559,7 @@ template <int P, typename T>
 __global__ void __launch_bounds__(gemm_threads(P))
     schwarz_gemm_kernel(const double *__restrict__ r, int64_t nlat, int nr, const T *__restrict__ pool,
                         const PatchRec *__restrict__ slots, const int2 *__restrict__ tiles, Grid3 g, int rule,
-                        double *__restrict__ zb, int zs, int64_t zsize, int *err, int wait_tries,
+                        double *__restrict__ zb, int zs, int64_t zsize, int pairs, int *err, int wait_tries,
                         const int *__restrict__ done)
 {
     constexpr int NC = GemmCfg<T, P>::NC, KC = GemmCfg<T, P>::KC, CPT = NC / 8, HALF = CPT / 2;
@@ -525,7 +622,7 @@ __global__ void __launch_bounds__(gemm_threads(P))
         for (int e = tid; e < n * NC; e += blockDim.x) {
             const int t = e / NC, c = e % NC;
             const int64_t s = src[c];
-            panel[e] = s >= 0 ? (T)r[s + rel[t]] : (T)0;
+            panel[e] = s >= 0 ? gathered<T>(r[s + rel[t]]) : (T)0;
         }
         __syncthreads();
         for (int pass = 0; pass < passes; ++pass) {
@@ -574,7 +671,7 @@ __global__ void __launch_bounds__(gemm_threads(P))
                     if (d < 0) continue;
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        if (row0 + i < n) zb[d + row0 + i] = (double)acc[i][j];
+                        if (row0 + i < n) put_val(zb, d + row0 + i, acc[i][j], pairs);
                 }
             }
         }
@@ -584,7 +681,7 @@ __global__ void __launch_bounds__(gemm_threads(P))
 
 // ---- phase 2: z = D r + sum over the blocks containing each DOF of their Zb rows
 
-template <int P>
+template <int P, bool PAIRS>
 __global__ void schwarz_sum_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ jac,
                                    const double *__restrict__ zb, const int *__restrict__ slot_of, Grid3 g, int rule,
                                    int zs, int64_t zsize, int64_t nlat, int nr, const int *__restrict__ done)
@@ -626,20 +723,312 @@ __global__ void schwarz_sum_kernel(const double *__restrict__ r, double *__restr
         }
         for (int k = 0; k < nr; ++k) {
             const int64_t gi = (int64_t)k * nlat + 3 * node;
-            double acc[3];
-            for (int c = 0; c < 3; ++c) acc[c] = jac ? jac[3 * node + c] * r[gi + c] : 0.0;
+            // FP64 entries: FP64 sums; float pairs: TwoSum on the FP32 pipe, one FP64 add per DOF at the end
+            double acc[3] = {0.0, 0.0, 0.0};
+            float S[3] = {0.f, 0.f, 0.f}, C[3] = {0.f, 0.f, 0.f};
             for (int az = 0; az < cm[2]; ++az)
                 for (int ay = 0; ay < cm[1]; ++ay)
                     for (int ax = 0; ax < cm[0]; ++ax) {
                         const int slot = slot_of[cid[0][ax] + nid0 * (cid[1][ay] + nid1 * cid[2][az])];
                         if (slot < 0) continue;
-                        const double *zr = zb + (int64_t)k * zsize + (int64_t)slot * zs +
-                                           3 * (cloc[0][ax] + cdim[0][ax] * (cloc[1][ay] + cdim[1][ay] * cloc[2][az]));
-                        for (int c = 0; c < 3; ++c) acc[c] += zr[c];
+                        const int64_t e = (int64_t)k * zsize + (int64_t)slot * zs +
+                                          3 * (cloc[0][ax] + cdim[0][ax] * (cloc[1][ay] + cdim[1][ay] * cloc[2][az]));
+                        if constexpr (PAIRS) {
+                            const float2 *zr = reinterpret_cast<const float2 *>(zb) + e;
+                            for (int c = 0; c < 3; ++c) {
+                                const float2 v = zr[c];
+                                ff_add(S[c], C[c], v.x, v.y);
+                            }
+                        } else {
+                            for (int c = 0; c < 3; ++c) acc[c] += zb[e + c];
+                        }
                     }
-            for (int c = 0; c < 3; ++c) z[gi + c] = acc[c];
+            for (int c = 0; c < 3; ++c) {
+                double v = PAIRS ? f2d(S[c]) + f2d(C[c]) : acc[c];
+                if (jac) v = fma(jac[3 * node + c], r[gi + c], v);
+                z[gi + c] = v;
+            }
         }
     }
+}
+
+// ---- phase 1c on the tensor cores: tcgen05 products for the FP32 shared factors (p = 2, 3; one
+// right-hand side)
+//
+// D[m][i] = sum_k R[m][k] F[i][k] for the 128 columns m of a tile (blocks sharing the factor F) and
+// the rows i of F, as tcgen05.mma kind::tf32 with M = 128 columns, N = the factor's rows (pieces of
+// at most 256) and K = 8 per instruction, the accumulators in tensor memory (TMEM).  TF32 keeps 10
+// mantissa bits, so each operand is split, x = hi + lo with hi = x with its low 13 bits cleared
+// (exact in TF32) and lo = x - hi rounded to TF32, and the products hi*hi + hi*lo + lo*hi are
+// accumulated in FP32: about 2^-22 relative, which the shared (uncut, well-conditioned) factors
+// tolerate.
+//
+// Operands in shared memory use the tensor core's canonical K-major layout without swizzle: 8 rows x
+// 16 bytes per core matrix, core matrices 128 B apart along K and 512 B apart along M or N, in chunks
+// of 16 K values.  The factor's hi/lo tiles are built once at fcm_precond_build (tc_factor_kernel) in
+// that layout, so a chunk of them is one run of bytes, moved by bulk copies completed on the stage's
+// mbarrier.  The residual panel is gathered from r by eight producer warps straight into the stage
+// (FP64 -> hi/lo), each thread one column and 8 K values, loading the next chunk while it stores the
+// current one.  One thread issues the copies and the MMAs; tcgen05.commit on a stage's `empty`
+// barrier hands the stage back to the producers and the copy engine.  The producer warps then read
+// the accumulators (tcgen05.ld) and write the rows to Zb through a shared-memory transpose, so that
+// each store covers consecutive rows of one block.
+
+template <int P> struct TcCfg {
+    static constexpr int NRP = (sbox_max(P) + 15) / 16 * 16;          // factor rows, padded (384 at p = 3)
+    static constexpr int NPIECE = NRP > 256 ? NRP / 2 : NRP;         // N of one MMA (192 or 96)
+    static constexpr int NPIECES = NRP / NPIECE;
+    static constexpr int TMEM_COLS = NRP > 256 ? 512 : NRP > 128 ? 256 : 128;
+    static constexpr int A_BYTES = 2 * 128 * 16 * 4;                 // hi and lo of 128 columns x 16 K
+    static constexpr int B_BYTES = 2 * NRP * 16 * 4;                 // hi and lo of NRP rows x 16 K
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = STAGE * 4 <= 196 * 1024 ? 4 : 3;
+    static constexpr int HEAD = 4096;                                // barriers, TMEM address, column bases, box offsets
+    static constexpr int SMEM = HEAD + STAGES * STAGE;
+    static constexpr int THREADS = 32 * 9;                           // warp 0: copies and MMAs; warps 1-8: producers
+};
+static_assert(TcCfg<3>::NPIECE % 16 == 0 && TcCfg<3>::NPIECE <= 256 && TcCfg<2>::NPIECE % 16 == 0, "MMA N");
+static_assert(TcCfg<3>::SMEM <= 227 * 1024 && TcCfg<2>::SMEM <= 227 * 1024, "tensor-core tile exceeds shared memory");
+static_assert((TcCfg<3>::NRP / 2) % 16 == 0 && (TcCfg<2>::NRP / 2) % 16 == 0, "epilogue column split");
+
+// float offset of element (row, kk) (kk < 16) in one hi or lo part of a chunk, canonical K-major layout
+__host__ __device__ __forceinline__ int tc_off(int row, int kk)
+{
+    return (row >> 3) * 128 + (kk >> 2) * 32 + (row & 7) * 4 + (kk & 3);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (ties away from zero), so that the tensor core's reading of the
+// low part drops nothing
+__device__ __forceinline__ float tf32_rn(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+
+// 64-bit shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_count(uint64_t *bar, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Factor tiles of one shared factor (built once): chunk c = [hi | lo], NRP rows x 16 K each.
+template <int P>
+__global__ void tc_factor_kernel(const double *__restrict__ F, int n, float *__restrict__ ft)
+{
+    using Cfg = TcCfg<P>;
+    const int ld = factor_ld<double>(n), nch = (n + 15) / 16;
+    const int64_t total = (int64_t)nch * Cfg::NRP * 16;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / (Cfg::NRP * 16)), rem = (int)(e % (Cfg::NRP * 16));
+        const int row = rem / 16, kk = rem % 16, k = 16 * c + kk;
+        const double x = row < n && k < n ? F[(size_t)row * ld + k] : 0.0;
+        const float h = tf32_hi((float)x);
+        float *hi = ft + (int64_t)c * 2 * Cfg::NRP * 16;
+        hi[tc_off(row, kk)] = h;
+        hi[Cfg::NRP * 16 + tc_off(row, kk)] = tf32_rn((float)(x - (double)h));
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(TcCfg<P>::THREADS, 1)
+    tc_gemm_kernel(const double *__restrict__ r, const PatchRec *__restrict__ slots, const TcTile *__restrict__ tiles,
+                   Grid3 g, int rule, const float *__restrict__ ft, double *__restrict__ zb, int zs, int pairs,
+                   int *err, int wait_tries, const int *__restrict__ done)
+{
+    using Cfg = TcCfg<P>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (done && *done) return;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);   // S: panel written and factor chunk landed
+    uint64_t *empty = full + S;                            // S: the stage's MMAs completed
+    uint64_t *fin = empty + S;                             // every MMA completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
+    int *flag = reinterpret_cast<int *>(tmem_slot + 1);    // a producer gave up waiting
+    int64_t *base = reinterpret_cast<int64_t *>(smem + 128);  // 128 column bases (-1: no block)
+    int *rel = reinterpret_cast<int *>(smem + 128 + 1024);     // box offsets, NRP entries
+    unsigned char *stages = smem + Cfg::HEAD;
+    const TcTile tl = tiles[blockIdx.x];
+    const SBox b0 = sbox(rule, P, g, slots[tl.first].v);
+    const int n = b0.n, nch = tl.nch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < 128; t += blockDim.x)
+        base[t] = t < tl.count ? box_base(sbox(rule, P, g, slots[tl.first + t].v), g) : -1;
+    for (int t = threadIdx.x; t < Cfg::NRP; t += blockDim.x) rel[t] = t < n ? box_rel(b0, g, t) : -1;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init_count(&full[i], 256 + 1);  // 256 producer arrivals + the copy's expect_tx
+            mbar_init(&empty[i]);
+        }
+        mbar_init(fin);
+        *flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(Cfg::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool failed = false;
+    if (warp == 0) {
+        if (lane == 0) {
+            const char *bsrc = reinterpret_cast<const char *>(ft + tl.ft_off);
+            auto issue = [&](int c) {  // factor chunk c into stage c % S
+                unsigned char *st = stages + (size_t)(c % S) * Cfg::STAGE + Cfg::A_BYTES;
+                mbar_expect(&full[c % S], (uint32_t)Cfg::B_BYTES);
+                for (int o = 0; o < Cfg::B_BYTES; o += 16384)
+                    bulk_g2s(st + o, bsrc + (size_t)c * Cfg::B_BYTES + o, min(16384, Cfg::B_BYTES - o), &full[c % S]);
+            };
+            int issued = 0;
+            for (; issued < min(S, nch); ++issued) issue(issued);
+            constexpr uint32_t idesc = tc_idesc(128, Cfg::NPIECE);
+            int c = 0;
+            for (; c < nch; ++c) {
+                const int s = c % S;
+                if (!mbar_wait(&full[s], (c / S) & 1, wait_tries)) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_hi = smem_u32(stages + (size_t)s * Cfg::STAGE), a_lo = a_hi + 128 * 16 * 4;
+                const uint32_t b_hi = a_hi + Cfg::A_BYTES, b_lo = b_hi + Cfg::NRP * 16 * 4;
+                for (int ks = 0; ks < 2; ++ks)
+                    for (int h = 0; h < Cfg::NPIECES; ++h) {
+                        const uint32_t d = tmem + h * Cfg::NPIECE;
+                        const uint32_t bo = h * (Cfg::NPIECE / 8) * 512 + ks * 256;
+                        const uint64_t ah = smem_desc(a_hi + ks * 256, 128, 512), al = smem_desc(a_lo + ks * 256, 128, 512);
+                        const uint64_t bh = smem_desc(b_hi + bo, 128, 512), bl = smem_desc(b_lo + bo, 128, 512);
+                        tc_mma(d, ah, bh, idesc, (c | ks) != 0);
+                        tc_mma(d, ah, bl, idesc, 1);
+                        tc_mma(d, al, bh, idesc, 1);
+                    }
+                tc_commit(&empty[s]);
+                // refill the stage of the previous chunk once its MMAs are done (this chunk's are queued)
+                if (c >= 1 && issued < nch) {
+                    const int sp = (c - 1) % S;
+                    if (!mbar_wait(&empty[sp], ((c - 1) / S) & 1, wait_tries)) {
+                        failed = true;
+                        ++c;
+                        break;
+                    }
+                    issue(issued++);
+                }
+            }
+            tc_commit(fin);  // arrives once every MMA issued above has completed
+            if (failed) {
+                // factor copies issued but not consumed land before the CTA leaves
+                for (int q = c; q < issued; ++q) mbar_wait(&full[q % S], (q / S) & 1, kDrainTries);
+            }
+        }
+    } else {
+        // producers: column m, K values 8 kh .. 8 kh + 7 of each chunk
+        const int p = threadIdx.x - 32, m = p & 127, kh = p >> 7;
+        const int64_t bm = base[m];
+        double cur[8], nxt[8];
+        auto load = [&](int c, double *v) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = 16 * c + 8 * kh + i;
+                const int rk = k < Cfg::NRP ? rel[k] : -1;
+                v[i] = (bm >= 0 && rk >= 0) ? r[bm + rk] : 0.0;
+            }
+        };
+        load(0, cur);
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) load(c + 1, nxt);
+            const int s = c % S;
+            if (c >= S && !mbar_wait(&empty[s], ((c / S) - 1) & 1, wait_tries)) {
+                failed = true;
+                break;
+            }
+            float *hi = reinterpret_cast<float *>(stages + (size_t)s * Cfg::STAGE), *lo = hi + 128 * 16;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {  // two groups of 4 K values: one 16-byte store each
+                float4 vh, vl;
+                float *ph = &vh.x, *pl = &vl.x;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split_bits<10>(cur[4 * q + i], ph[i], pl[i]);
+                const int o = tc_off(m, 8 * kh + 4 * q);
+                *reinterpret_cast<float4 *>(hi + o) = vh;
+                *reinterpret_cast<float4 *>(lo + o) = vl;
+            }
+            // the tensor core reads the panel through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[s]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cur[i] = nxt[i];
+        }
+        if (failed) atomicExch(flag, 1);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(fin, 0, kDrainTries);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    failed = __syncthreads_or(failed || !ok || *reinterpret_cast<volatile int *>(flag));
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (warp >= 1) {
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (columns m) and half (w - 1) / 4 of the rows, 16 at
+        // a time, and writes them through a 32 x 17 transpose buffer: each store covers 16 rows of a block
+        const int q4 = warp & 3, half = (warp - 1) >> 2;
+        float *tb = reinterpret_cast<float *>(stages) + (warp - 1) * 32 * 17;
+        const int m = 32 * q4 + lane;
+        for (int j0 = half * (Cfg::NRP / 2); j0 < (half + 1) * (Cfg::NRP / 2); j0 += 16) {
+            uint32_t v[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + j0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+                "%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) tb[lane * 17 + i] = __uint_as_float(v[i]);
+            __syncwarp();
+            for (int i = 0; i < 16; ++i) {  // columns 2 i, 2 i + 1: 16 rows each
+                const int ml = 2 * i + (lane >> 4), row = j0 + (lane & 15), mm = 32 * q4 + ml;
+                if (mm < tl.count && row < n) put_f32(zb, (int64_t)(tl.first + mm) * zs + row, tb[ml * 17 + (lane & 15)], pairs);
+            }
+            __syncwarp();
+        }
+        (void)m;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS) : "memory");
 }
 
 int sum_grid(int64_t nnode)
@@ -654,13 +1043,21 @@ void gemm_launch(const double *r, int64_t nlat, int nr, const double *f64, const
                  double *zb, int64_t zsize, const int *done, cudaStream_t s)
 {
     const Grid3 &g = pl.g;
-    if (pl.n_tiles32 > 0)
-        schwarz_gemm_kernel<P, float><<<pl.n_tiles32, gemm_threads(P), gemm_smem_bytes<P, float>(), s>>>(
-            r, nlat, nr, f32, pl.slots, pl.tiles, g, pl.rule, zb, pl.zs, zsize, pl.err, pl.wait_tries, done);
+    // one right-hand side: the FP32 shared factors that have tensor-core tiles go through tcgen05
+    const bool tc = nr == 1 && pl.n_tc_tiles > 0;
+    if constexpr (P == 2 || P == 3) {
+        if (tc)
+            tc_gemm_kernel<P><<<pl.n_tc_tiles, TcCfg<P>::THREADS, TcCfg<P>::SMEM, s>>>(
+                r, pl.slots, pl.tc_tiles, g, pl.rule, pl.tc_ft, zb, pl.zs, pl.pairs, pl.err, pl.wait_tries, done);
+    }
+    const int n32 = tc ? pl.n_tiles32_plain : pl.n_tiles32;
+    if (n32 > 0)
+        schwarz_gemm_kernel<P, float><<<n32, gemm_threads(P), gemm_smem_bytes<P, float>(), s>>>(
+            r, nlat, nr, f32, pl.slots, pl.tiles, g, pl.rule, zb, pl.zs, zsize, pl.pairs, pl.err, pl.wait_tries, done);
     if (pl.n_tiles64 > 0)
         schwarz_gemm_kernel<P, double><<<pl.n_tiles64, gemm_threads(P), gemm_smem_bytes<P, double>(), s>>>(
-            r, nlat, nr, f64, pl.slots, pl.tiles + pl.n_tiles32, g, pl.rule, zb, pl.zs, zsize, pl.err, pl.wait_tries,
-            done);
+            r, nlat, nr, f64, pl.slots, pl.tiles + pl.n_tiles32, g, pl.rule, zb, pl.zs, zsize, pl.pairs, pl.err,
+            pl.wait_tries, done);
 }
 
 template <int P, int NR>
@@ -669,7 +1066,7 @@ void cols_launch(const double *r, int64_t nlat, int nr, const double *f64, const
 {
     const int smem = factor_ld<double>(sbox_max(P)) * NR * 8;
     schwarz_cols_kernel<P, NR><<<pl.n_col_items, cols_threads(P), smem, s>>>(
-        r, nlat, nr, f64, f32, pl.slots, pl.col_items, pl.g, pl.rule, zb, pl.zs, zsize, done);
+        r, nlat, nr, f64, f32, pl.slots, pl.col_items, pl.g, pl.rule, zb, pl.zs, zsize, pl.pairs, done);
 }
 
 template <int P>
@@ -677,7 +1074,7 @@ void apply_p(const double *r, double *z, int64_t nlat, int nr, const double *f64
              const SchwarzPlan &pl, double *zb, const int *done, cudaStream_t s)
 {
     const int64_t zsize = (int64_t)pl.nslots * pl.zs;
-    const bool gemm = pl.n_tiles32 + pl.n_tiles64 > 0;
+    const bool gemm = pl.n_tiles32 + pl.n_tiles64 + (nr == 1 ? pl.n_tc_tiles : 0) > 0;
     const bool own = nr == 1 && P == 3 ? pl.n_row_items > 0 : pl.n_col_items > 0;
     const bool side = pl.concurrent && gemm && own && pl.side;
     if (side) {
@@ -692,8 +1089,8 @@ void apply_p(const double *r, double *z, int64_t nlat, int nr, const double *f64
     if (own) {
         if constexpr (P == 3) {
             if (nr == 1)
-                schwarz_rows_kernel<P><<<pl.n_row_items, kRowsThreads, 0, s>>>(r, f64, f32, pl.slots, pl.row_items,
-                                                                               pl.rows, pl.g, pl.rule, zb, pl.zs, done);
+                schwarz_rows_kernel<P><<<pl.n_row_items, kRowsThreads, 0, s>>>(
+                    r, f64, f32, pl.slots, pl.row_items, pl.rows, pl.g, pl.rule, zb, pl.zs, pl.pairs, done);
             else
                 cols_launch<P, 8>(r, nlat, nr, f64, f32, pl, zb, zsize, done, s);
         } else if (nr == 1)
@@ -702,8 +1099,12 @@ void apply_p(const double *r, double *z, int64_t nlat, int nr, const double *f64
             cols_launch<P, 8>(r, nlat, nr, f64, f32, pl, zb, zsize, done, s);
     }
     if (side) cudaStreamWaitEvent(s, pl.ev_join, 0);
-    schwarz_sum_kernel<P><<<sum_grid(nlat / 3), 256, 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule, pl.zs,
-                                                             zsize, nlat, nr, done);
+    if (pl.pairs)
+        schwarz_sum_kernel<P, true><<<sum_grid(nlat / 3), 256, 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule,
+                                                                       pl.zs, zsize, nlat, nr, done);
+    else
+        schwarz_sum_kernel<P, false><<<sum_grid(nlat / 3), 256, 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule,
+                                                                        pl.zs, zsize, nlat, nr, done);
 }
 
 template <int P>
@@ -711,6 +1112,9 @@ cudaError_t prepare_p()
 {
     cudaError_t e = cudaFuncSetAttribute(schwarz_gemm_kernel<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          gemm_smem_bytes<P, float>());
+    if constexpr (P == 2 || P == 3)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tc_gemm_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<P>::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(schwarz_gemm_kernel<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  gemm_smem_bytes<P, double>());
@@ -752,6 +1156,24 @@ int schwarz_col_rows(int p)
 }
 
 bool schwarz_uses_rows_kernel(int p) { return p == 3; }
+
+bool schwarz_tc_supported(int p) { return p == 2 || p == 3; }
+
+int64_t schwarz_tc_factor_floats(int p, int n)
+{
+    const int nrp = p == 3 ? TcCfg<3>::NRP : TcCfg<2>::NRP;
+    return (int64_t)((n + 15) / 16) * 2 * nrp * 16;
+}
+
+cudaError_t schwarz_tc_factor(int p, const double *F, int n, float *ft, cudaStream_t s)
+{
+    const int64_t total = schwarz_tc_factor_floats(p, n) / 2;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 1024);
+    if (p == 3) tc_factor_kernel<3><<<grid, 256, 0, s>>>(F, n, ft);
+    else if (p == 2) tc_factor_kernel<2><<<grid, 256, 0, s>>>(F, n, ft);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 int schwarz_rows_threads() { return kRowsThreads; }
 

@@ -69,7 +69,8 @@ class Info(ctypes.Structure):
 
 class PrecondOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("cond_fp64", ctypes.c_double),
-                ("block_rule", ctypes.c_int), ("eta_bar", ctypes.c_double), ("fixed_tiles", ctypes.c_int)]
+                ("block_rule", ctypes.c_int), ("eta_bar", ctypes.c_double), ("fixed_tiles", ctypes.c_int),
+                ("simt_shared", ctypes.c_int)]
 
 
 BLOCKS_VERTEX, BLOCKS_ELEMENT = 0, 3
@@ -246,14 +247,15 @@ class Solver:
         return b
 
     def precond_build(self, eps=1e-13, precision="fp64", cond_fp64=1e7, blocks="vertex", eta_bar=1.0,
-                      autotune=True, launch=None):
+                      autotune=True, launch=None, tensor_cores=True):
         """precision: "fp64", "mixed" (FP32 factors, double-float pairs above cond_fp64) or
         "mixed_fp64" (FP32 factors, FP64 above cond_fp64).  blocks: "vertex" (vertex patches)
         or "element" (element blocks of the cells with eta_T <= eta_bar, diagonal scaling for
         the DOFs in no block).  autotune: time the Schwarz apply for a few launch shapes and
         keep the fastest (results do not depend on the choice).  launch ("serial" or
         "concurrent": the shared-factor products after or beside the streamed factors) fixes
-        the default shape instead."""
+        the default shape instead.  tensor_cores: FP32 shared factors on tcgen05 (TF32 three-pass)
+        or, when False, on the CUDA cores."""
         if blocks not in ("vertex", "element"):
             raise ValueError(f"unknown block rule {blocks!r}")
         o = PrecondOpts()
@@ -263,6 +265,7 @@ class Solver:
         o.block_rule = BLOCKS_ELEMENT if blocks == "element" else BLOCKS_VERTEX
         o.eta_bar = eta_bar
         o.fixed_tiles = {None: 0 if autotune else 1, "serial": 1, "concurrent": 2}[launch]
+        o.simt_shared = 0 if tensor_cores else 1
         self._check(load().fcm_precond_build(self.ctx, ctypes.byref(o)))
         self.info = self.get_info()
 

@@ -5,7 +5,8 @@ A porous 4^3-cell cube with 3 voids: cut patches stream their own factors (FP32 
 build, double-float pairs), uncut interior patches share factors and go through the dense product,
 and 375-row blocks cross several row tiles with a ragged tail.  Bounds: S r per DOF by the
 eigensolver perturbation of the blocks that contain it (tests/schwarz_bounds.py; FP32 factors add
-their 2^-24 storage rounding), and 1e-9 (FP64) or 1e-5 (FP32 factors) in the energy norm of K; the
+their storage rounding, 2^-24, and the tensor-core products of shared factors theirs, ~2^-22: 2^-20
+covers both), and 1e-9 (FP64) or 1e-5 (FP32 factors) in the energy norm of K; the
 PCG solutions within 1e-8 of a sparse direct solve in the energy norm (Eq. (15)), iteration counts
 within 2 of the oracle's PCG on each load case.
 """
@@ -41,7 +42,8 @@ def test_multi_rhs_S_columns_match_oracle(porous4, precision):
     R = np.concatenate([I.random_vector(40 + k, s.n) for k in range(6)])
     Z = s.apply_S(torch.from_numpy(R).cuda()).cpu().numpy()
     K = P.csr()
-    u = 2.0 ** -24 if precision == "mixed" else 0.0
+    # FP32 factors round to 2^-24; the tensor-core products of shared factors (TF32, three passes) to ~2^-22
+    u = 2.0 ** -20 if precision == "mixed" else 0.0
     for k in range(6):
         rk = R[k * s.n:(k + 1) * s.n]
         zk = Z[k * s.n:(k + 1) * s.n]
