@@ -117,6 +117,7 @@ typedef struct {
                                  since the last fcm_precond_build or solve (its output is then wrong) */
     int64_t n_factors_ff;     /* factors stored as double-float pairs (FCM_PREC_MIXED, cond > cond_fp64) */
     int64_t n_gemm_blocks;    /* blocks applied by the shared-factor dense product        */
+    int k_double_float;       /* 1: K applied in double-float arithmetic (fcm_set_k_precision) */
 } fcm_info_t;
 
 enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1, FCM_PREC_MIXED_FP64 = 2 };
@@ -235,6 +236,18 @@ fcm_status fcm_apply_K(fcm_ctx *ctx, const double *x_dev, double *y_dev);
 /* z_dev = S r_dev, S = sum_B R_B^T A_B+^-1 R_B (Sec. 3.1 Eq. (5)); device.
  * FCM_ESTATE before fcm_precond_build. */
 fcm_status fcm_apply_S(fcm_ctx *ctx, const double *r_dev, double *z_dev);
+
+enum { FCM_K_FP64 = 0, FCM_K_DOUBLE_FLOAT = 1 };
+
+/* Arithmetic of K x (Eq. (1); every K apply of the context, solves included).
+ * FCM_K_FP64 (default): FP64 multiply-adds.  FCM_K_DOUBLE_FLOAT: the same
+ * steps with double-float values (float pairs) and compensated products and
+ * sums on the FP32 pipe, about 2^-46 relative per contraction (K x within
+ * ~1e-13 of the FP64 result); GB300's FP32 pipe is 64 times wider than its
+ * FP64 pipe.  The first switch to double-float stores a float-pair copy of
+ * the element matrices (fcm_info.element_bytes more device memory).  Captured
+ * solver graphs are dropped.  FCM_EINVAL for another mode. */
+fcm_status fcm_set_k_precision(fcm_ctx *ctx, int mode);
 
 /* z_dev = S r_dev for nrhs (1..8) vectors stored n_lattice apart (device);
  * the block factors are read once for all of them.  Column k equals

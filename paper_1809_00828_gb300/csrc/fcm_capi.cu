@@ -69,7 +69,10 @@ struct StreamScope {
 void apply_K_dev(fcm_ctx *C, const double *x, double *y, const int *done)
 {
     fcm::launch_zero(y, C->nlat, done, C->stream);
-    fcm::launch_k_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->kc, done, C->stream);
+    if (C->k_ff)
+        fcm::launch_k_apply_ff(C->p, C->g, x, y, C->d_mask, C->d_elem_ff, C->kc, done, C->stream);
+    else
+        fcm::launch_k_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->kc, done, C->stream);
 }
 
 void apply_S_dev(fcm_ctx *C, const double *r, double *z, const int *done)
@@ -173,7 +176,7 @@ void free_ctx(fcm_ctx *C)
 {
     if (!C) return;
     destroy_graph(C);
-    void *ptrs[] = {C->d_elem, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32,
+    void *ptrs[] = {C->d_elem, C->d_elem_ff, C->d_cell_elem, C->d_mask, C->d_rhs, C->d_cells, C->d_uncut, C->d_f64, C->d_f32,
                     C->d_slots, C->d_slot_of, C->d_items, C->d_zb, C->d_mzb, C->d_tc_tiles, C->d_tc_ft,
                     C->d_eta, C->d_jac, C->d_err,
                     C->d_x, C->d_r, C->d_z, C->d_p, C->d_q, C->d_b, C->d_t, C->d_partial, C->d_counter, C->d_s,
@@ -310,6 +313,7 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     C->kc.cut = C->d_cells;
     C->kc.uncut = C->d_uncut;
     fcm::make_sf_tables(hp, C->kc.sf);
+    fcm::make_sf_tables_ff(C->kc.sf, C->kc.sff);
     // solver workspace
     double **vecs[] = {&C->d_x, &C->d_r, &C->d_z, &C->d_p, &C->d_q, &C->d_b, &C->d_t};
     for (double **v : vecs) {
@@ -385,6 +389,7 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->stream_rows = C->plan.rows;
     out->schwarz_concurrent = C->plan.concurrent;
     out->n_factors_ff = C->n_ff_factors;
+    out->k_double_float = C->k_ff;
     out->n_gemm_blocks = C->n_gemm_blocks;
     for (int k = 0; k < 8; ++k) out->tune_seconds[k] = C->tune_seconds[k];
     out->device_error = 0;
@@ -700,6 +705,29 @@ fcm_status fcm_apply_S_many(fcm_ctx *C, const double *r_dev, int nrhs, double *z
     for (int k = 0; k < nrhs; ++k) fcm::launch_mask_copy(r_dev + (size_t)k * n, R + (size_t)k * n, C->d_mask, n, C->stream);
     fcm::launch_schwarz_apply_multi(C->p, R, z_dev, n, nrhs, C->d_f64, C->d_f32, C->plan, C->d_mzb, nullptr, C->stream);
     API_CUDA(C, cudaGetLastError());
+    return FCM_OK;
+}
+
+fcm_status fcm_set_k_precision(fcm_ctx *C, int mode)
+{
+    if (!C || (mode != FCM_K_FP64 && mode != FCM_K_DOUBLE_FLOAT)) {
+        if (C) C->err = "fcm_set_k_precision: unknown mode";
+        return FCM_EINVAL;
+    }
+    StreamScope sc(C);
+    if (mode == FCM_K_DOUBLE_FLOAT && !C->d_elem_ff) {
+        const int64_t n = C->element_bytes / (int64_t)sizeof(double);
+        API_CUDA(C, cudaMalloc(&C->d_elem_ff, sizeof(float2) * (size_t)std::max<int64_t>(n, 1)));
+        fcm::launch_to_ff_pairs(C->d_elem, C->d_elem_ff, n, C->stream);
+        API_CUDA(C, cudaGetLastError());
+        API_CUDA(C, cudaStreamSynchronize(C->stream));
+    }
+    if (C->k_ff != (mode == FCM_K_DOUBLE_FLOAT)) {
+        C->k_ff = mode == FCM_K_DOUBLE_FLOAT;
+        // the captured graphs hold the K launches of the other mode
+        destroy_graph(C);
+        fcm::fcg_forget_graph(C->fcg);
+    }
     return FCM_OK;
 }
 

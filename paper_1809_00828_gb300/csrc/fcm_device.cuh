@@ -41,6 +41,13 @@ struct Grid3 {
     int M[3];   // lattice nodes per axis
 };
 
+// The sum-factorisation tables as double-float pairs (hi = fl32(v), lo = fl32(v - hi)).
+struct SfTablesFF {
+    float2 B[5][5], G[3][5][5], W[5];
+    float2 detJ, lam, mu;
+};
+void make_sf_tables_ff(const SfTables &T, SfTablesFF &F);
+
 // Active cells of the K apply, grouped by parity colour: uncut cells (matrix-free,
 // sum-factorised) and cut cells (their own dense element matrix).
 struct KCells {
@@ -49,6 +56,7 @@ struct KCells {
     int uncut_off[9];
     int cut_off[9];
     SfTables sf;
+    SfTablesFF sff;
 };
 
 // Launch plan of the Schwarz apply (fcm_schwarz.cu).  Every block has a slot: its record
@@ -97,6 +105,11 @@ struct SchwarzPlan {
 // with S r.  The multi-RHS form takes nr <= 8 vectors nlat apart and a Zb of nr * nslots * zs doubles.
 void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
                     const KCells &kc, const int *done, cudaStream_t s);
+// the same in double-float arithmetic on the FP32 pipe (fcm_kapply_ff.cu); elem: the element matrices as
+// float pairs
+void launch_k_apply_ff(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const float2 *elem,
+                       const KCells &kc, const int *done, cudaStream_t s);
+void launch_to_ff_pairs(const double *in, float2 *out, int64_t n, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
                           const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
 void launch_schwarz_apply_multi(int p, const double *r, double *z, int64_t nlat, int nr, const double *f64,
@@ -183,6 +196,8 @@ struct fcm_ctx {
     int64_t nlat = 0;
     // problem on the device
     double *d_elem = nullptr;        // [Kref | Kcut_1 | ...], ne*ne each, row-major (symmetric)
+    float2 *d_elem_ff = nullptr;     // the same as double-float pairs (allocated by fcm_set_k_precision)
+    int k_ff = 0;                    // 1: K applied in double-float arithmetic
     int32_t *d_cell_elem = nullptr;  // per cell
     uint8_t *d_mask = nullptr;       // per lattice DOF
     double *d_rhs = nullptr;         // load case 0

@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "fcm_device.cuh"
+#include "fcm_ff.cuh"
 
 namespace fcm {
 
@@ -77,84 +78,6 @@ __device__ __forceinline__ int64_t box_base(const SBox &b, const Grid3 &g)
     return 3 * (b.lo[0] + (int64_t)g.M[0] * (b.lo[1] + (int64_t)g.M[1] * b.lo[2]));
 }
 
-// ---- FP64 -> FP32 splits by integer operations
-//
-// GB300's FP64 pipe, which also converts between FP64 and FP32, does 2 operations per clock per SM, so
-// the kernels never convert a gathered FP64 value with it.  split_bits<MB> reads the value's bits:
-// hi = x with its significand cut to MB fraction bits (exact in a format with MB fraction bits), lo =
-// x - hi (a 42 to 52 - MB bit integer times a power of two) rounded to MB + 1 significant bits, half
-// up in magnitude.  MB = 23: a float pair with |x - hi - lo| <= 2^-48 |x|; MB = 10: two TF32 values
-// with |x - hi - lo| <= 2^-22 |x|.  |x| below 2^-126 gives +-0; beyond the FP32 range +-inf (NaN
-// stays NaN), as a conversion would; a lo below 2^-126 is dropped.
-template <int MB>
-__device__ __forceinline__ void split_bits(double x, float &hi, float &lo)
-{
-    constexpr int CUT = 52 - MB;  // fraction bits of x below hi
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
-    const int E = (int)(u >> 52) & 0x7FF;
-    const unsigned long long M = u & 0xFFFFFFFFFFFFFull;
-    const int ef = E - 896;  // FP32 exponent field of x: E - 1023 + 127
-    lo = 0.f;
-    if (ef <= 0) {
-        hi = __uint_as_float(sign);
-        return;
-    }
-    if (ef >= 255) {
-        hi = __uint_as_float(sign | (E == 0x7FF && M ? 0x7FC00000u : 0x7F800000u));
-        return;
-    }
-    hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((unsigned)(M >> CUT) << (23 - MB)));
-    const unsigned long long R = M & ((1ull << CUT) - 1);  // x - hi = R 2^(E - 1075)
-    if (R == 0) return;
-    const int t = 63 - __clzll((long long)R);               // leading one of R
-    int e = ef - 52 + t;                                    // FP32 exponent field of lo
-    unsigned q;                                             // MB + 1 significant bits
-    if (t > MB) {
-        q = (unsigned)(((R >> (t - MB - 1)) + 1) >> 1);
-        if (q == (2u << MB)) {
-            q = 1u << MB;
-            ++e;
-        }
-    } else {
-        q = (unsigned)(R << (MB - t));
-    }
-    if (e > 0) lo = __uint_as_float(sign | ((unsigned)e << 23) | ((q & ((1u << MB) - 1)) << (23 - MB)));
-}
-
-// x as a float pair, x = hi + lo to 2^-48 relative
-__device__ __forceinline__ float2 split_ff(double x)
-{
-    float h, l;
-    split_bits<23>(x, h, l);
-    return make_float2(h, l);
-}
-
-// x rounded to FP32 (the pair's sum: within half an ulp but for ties)
-__device__ __forceinline__ float to_f32(double x)
-{
-    float h, l;
-    split_bits<23>(x, h, l);
-    return __fadd_rn(h, l);
-}
-
-// a gathered residual value in the factor's type
-template <typename T> __device__ __forceinline__ T gathered(double x);
-template <> __device__ __forceinline__ float gathered<float>(double x) { return to_f32(x); }
-template <> __device__ __forceinline__ double gathered<double>(double x) { return x; }
-
-// FP32 -> FP64 from the bits (exact; FP32 subnormals become zero)
-__device__ __forceinline__ double f2d(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xFFu;
-    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    const unsigned long long frac = (unsigned long long)(b & 0x7FFFFFu) << 29;
-    if (e == 0) return __longlong_as_double((long long)sign);
-    if (e == 0xFF) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | frac));
-    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896) << 52) | frac));
-}
-
 // Block products Zb.  With `pairs` (the mixed forms) an entry is a float pair (hi, lo) whose sum is
 // the value: FP32 results (v, 0), double-float results (S, C), FP64 results split by split_bits<23>;
 // the sum kernel then adds them on the FP32 pipe.  Otherwise (FP64 form) an entry is an FP64 value.
@@ -180,35 +103,6 @@ __device__ __forceinline__ void put_f64(double *zb, int64_t i, double v, bool pa
 }
 __device__ __forceinline__ void put_val(double *zb, int64_t i, float v, bool pairs) { put_f32(zb, i, v, pairs); }
 __device__ __forceinline__ void put_val(double *zb, int64_t i, double v, bool pairs) { put_f64(zb, i, v, pairs); }
-
-// ---- double-float arithmetic (FP32 pipe)
-
-// S + C += (fh + fl)(xh + xl): the product fh xh exactly as p + e (FMA), the cross terms in FP32,
-// fl xl (2^-48 relative) dropped; S accumulates by TwoSum, its rounding errors go to C.  The
-// intrinsics keep the compiler from contracting or reassociating these steps.
-__device__ __forceinline__ void ff_fma(float fh, float fl, float xh, float xl, float &S, float &C)
-{
-    const float p = __fmul_rn(fh, xh);
-    const float e = __fmaf_rn(fh, xh, -p);
-    C = __fmaf_rn(fh, xl, C);
-    C = __fmaf_rn(fl, xh, C);
-    C = __fadd_rn(C, e);
-    const float s = __fadd_rn(S, p);
-    const float bb = __fsub_rn(s, S);
-    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    S = s;
-    C = __fadd_rn(C, err);
-}
-
-// (S, C) += (S2, C2) with S by TwoSum (symmetric in the two operands)
-__device__ __forceinline__ void ff_add(float &S, float &C, float S2, float C2)
-{
-    const float s = __fadd_rn(S, S2);
-    const float bb = __fsub_rn(s, S);
-    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(S2, bb));
-    S = s;
-    C = __fadd_rn(__fadd_rn(C, C2), err);
-}
 
 // 16-byte vectors of float (4) or double (2)
 template <typename T> struct V16;
@@ -437,7 +331,7 @@ __global__ void __launch_bounds__(cols_threads(P))
                         const int2 *__restrict__ items, Grid3 g, int rule, double *__restrict__ zb, int zs,
                         int64_t zsize, int pairs, const int *__restrict__ done)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     if (done && *done) return;
     const int2 it = items[blockIdx.x];
     const PatchRec pr = slots[it.x];
@@ -564,7 +458,7 @@ __global__ void __launch_bounds__(gemm_threads(P))
 {
     constexpr int NC = GemmCfg<T, P>::NC, KC = GemmCfg<T, P>::KC, CPT = NC / 8, HALF = CPT / 2;
     constexpr int SE = gemm_stage_elems<P, T>();
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     if (done && *done) return;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     int64_t *src = reinterpret_cast<int64_t *>(smem + 16);   // NC: first lattice DOF of the column's r_B, -1 none
@@ -681,71 +575,94 @@ __global__ void __launch_bounds__(gemm_threads(P))
 
 // ---- phase 2: z = D r + sum over the blocks containing each DOF of their Zb rows
 
+// Along one axis, the blocks whose box contains lattice index i (at most two, ascending), with i's
+// offset in the box and the box width: vertex patches [P v - (P-1), P v + (P-1)] clipped (the vertex
+// i / P itself when i is a vertex node, else both vertices of the cell), element boxes [P c, P c + P]
+// (at a vertex node the cells on both sides that exist).
+struct AxisCand {
+    int id[2], loc[2], dim[2];
+    bool on[2];
+};
+
+template <int P>
+__device__ __forceinline__ AxisCand axis_cand(int rule, int i, int ncell, int M)
+{
+    AxisCand a;
+    const int c = i / P, s = i - P * c;
+    if (rule == 3) {
+        a.on[0] = s == 0 && c >= 1;
+        a.id[0] = c - 1;
+        a.loc[0] = i - P * (c - 1);
+        a.on[1] = c < ncell;
+        a.id[1] = c;
+        a.loc[1] = s;
+        a.dim[0] = a.dim[1] = P + 1;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int v = c + k, lo = max(0, P * v - (P - 1)), hi = min(M - 1, P * v + (P - 1));
+            a.id[k] = v;
+            a.loc[k] = i - lo;
+            a.dim[k] = hi - lo + 1;
+        }
+        a.on[0] = true;
+        a.on[1] = s != 0;
+    }
+    return a;
+}
+
 template <int P, bool PAIRS>
-__global__ void schwarz_sum_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ jac,
-                                   const double *__restrict__ zb, const int *__restrict__ slot_of, Grid3 g, int rule,
-                                   int zs, int64_t zsize, int64_t nlat, int nr, const int *__restrict__ done)
+__global__ void __launch_bounds__(256)
+    schwarz_sum_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ jac,
+                       const double *__restrict__ zb, const int *__restrict__ slot_of, Grid3 g, int rule, int zs,
+                       int64_t zsize, int64_t nlat, int nr, const int *__restrict__ done)
 {
     if (done && *done) return;
-    const int64_t nnode = nlat / 3;
+    const int nnode = (int)(nlat / 3);
     const int nid0 = rule == 3 ? g.n[0] : g.n[0] + 1, nid1 = rule == 3 ? g.n[1] : g.n[1] + 1;
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nnode;
-         node += (int64_t)gridDim.x * blockDim.x) {
-        const int L[3] = {(int)(node % g.M[0]), (int)((node / g.M[0]) % g.M[1]), (int)(node / ((int64_t)g.M[0] * g.M[1]))};
-        // per axis: the blocks whose box contains the node, ascending, with the node's offset in the box
-        int cid[3][2], cloc[3][2], cdim[3][2], cm[3];
-        for (int a = 0; a < 3; ++a) {
-            const int i = L[a], c = i / P, s = i - P * c;
-            int m = 0;
-            if (rule == 3) {
-                // element boxes [P c, P c + P]
-                if (s == 0 && c >= 1) {
-                    cid[a][m] = c - 1;
-                    cloc[a][m] = i - P * (c - 1);
-                    cdim[a][m++] = P + 1;
-                }
-                if (c < g.n[a]) {
-                    cid[a][m] = c;
-                    cloc[a][m] = s;
-                    cdim[a][m++] = P + 1;
-                }
-            } else {
-                // vertex patches [P v - (P-1), P v + (P-1)] clipped: the vertex c itself, or (inside a
-                // cell) both of its vertices
-                for (int v = c; v <= (s == 0 ? c : c + 1); ++v) {
-                    const int lo = max(0, P * v - (P - 1)), hi = min(g.M[a] - 1, P * v + (P - 1));
-                    cid[a][m] = v;
-                    cloc[a][m] = i - lo;
-                    cdim[a][m++] = hi - lo + 1;
-                }
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nnode; node += gridDim.x * blockDim.x) {
+        const int i0 = node % g.M[0], i1 = (node / g.M[0]) % g.M[1], i2 = node / (g.M[0] * g.M[1]);
+        const AxisCand ax = axis_cand<P>(rule, i0, g.n[0], g.M[0]);
+        const AxisCand ay = axis_cand<P>(rule, i1, g.n[1], g.M[1]);
+        const AxisCand az = axis_cand<P>(rule, i2, g.n[2], g.M[2]);
+        // the (up to 8) blocks in a fixed order: their slot and the node's entry in it
+        int64_t ent[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int kx = q & 1, ky = (q >> 1) & 1, kz = q >> 2;
+            int64_t e = -1;
+            if (ax.on[kx] && ay.on[ky] && az.on[kz]) {
+                const int slot = slot_of[ax.id[kx] + nid0 * (ay.id[ky] + nid1 * az.id[kz])];
+                if (slot >= 0)
+                    e = (int64_t)slot * zs + 3 * (ax.loc[kx] + ax.dim[kx] * (ay.loc[ky] + ay.dim[ky] * az.loc[kz]));
             }
-            cm[a] = m;
+            ent[q] = e;
         }
         for (int k = 0; k < nr; ++k) {
-            const int64_t gi = (int64_t)k * nlat + 3 * node;
+            const int64_t gi = (int64_t)k * nlat + 3 * (int64_t)node;
             // FP64 entries: FP64 sums; float pairs: TwoSum on the FP32 pipe, one FP64 add per DOF at the end
             double acc[3] = {0.0, 0.0, 0.0};
             float S[3] = {0.f, 0.f, 0.f}, C[3] = {0.f, 0.f, 0.f};
-            for (int az = 0; az < cm[2]; ++az)
-                for (int ay = 0; ay < cm[1]; ++ay)
-                    for (int ax = 0; ax < cm[0]; ++ax) {
-                        const int slot = slot_of[cid[0][ax] + nid0 * (cid[1][ay] + nid1 * cid[2][az])];
-                        if (slot < 0) continue;
-                        const int64_t e = (int64_t)k * zsize + (int64_t)slot * zs +
-                                          3 * (cloc[0][ax] + cdim[0][ax] * (cloc[1][ay] + cdim[1][ay] * cloc[2][az]));
-                        if constexpr (PAIRS) {
-                            const float2 *zr = reinterpret_cast<const float2 *>(zb) + e;
-                            for (int c = 0; c < 3; ++c) {
-                                const float2 v = zr[c];
-                                ff_add(S[c], C[c], v.x, v.y);
-                            }
-                        } else {
-                            for (int c = 0; c < 3; ++c) acc[c] += zb[e + c];
-                        }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (ent[q] < 0) continue;
+                const int64_t e = (int64_t)k * zsize + ent[q];
+                if constexpr (PAIRS) {
+                    const float2 *zr = reinterpret_cast<const float2 *>(zb) + e;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 v = zr[c];
+                        ff_add(S[c], C[c], v.x, v.y);
                     }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[c] += zb[e + c];
+                }
+            }
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double v = PAIRS ? f2d(S[c]) + f2d(C[c]) : acc[c];
-                if (jac) v = fma(jac[3 * node + c], r[gi + c], v);
+                if (jac) v = fma(jac[3 * (int64_t)node + c], r[gi + c], v);
                 z[gi + c] = v;
             }
         }

@@ -22,7 +22,7 @@ PREC_FP64, PREC_MIXED, PREC_MIXED_FP64 = 0, 1, 2
 # Every symbol include/fcm.h declares (checked by the tests).
 EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_solve", "fcm_pcg_solve_host",
             "fcm_last_solve", "fcm_apply_K", "fcm_apply_S", "fcm_apply_S_noalloc", "fcm_apply_S_many",
-            "fcm_set_wait_limit", "fcm_last_error", "fcm_destroy",
+            "fcm_set_wait_limit", "fcm_set_k_precision", "fcm_last_error", "fcm_destroy",
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
@@ -64,7 +64,8 @@ class Info(ctypes.Structure):
                 ("coarse_seconds", ctypes.c_double), ("n_jacobi", ctypes.c_int64),
                 ("stream_rows", ctypes.c_int), ("schwarz_concurrent", ctypes.c_int),
                 ("tune_seconds", ctypes.c_double * 8),
-                ("device_error", ctypes.c_int), ("n_factors_ff", ctypes.c_int64), ("n_gemm_blocks", ctypes.c_int64)]
+                ("device_error", ctypes.c_int), ("n_factors_ff", ctypes.c_int64), ("n_gemm_blocks", ctypes.c_int64),
+                ("k_double_float", ctypes.c_int)]
 
 
 class PrecondOpts(ctypes.Structure):
@@ -115,6 +116,7 @@ def load(path: str = LIB_PATH):
     L.fcm_apply_S_noalloc.argtypes = [P, P, P]
     L.fcm_apply_S_many.argtypes = [P, P, ctypes.c_int, P]
     L.fcm_set_wait_limit.argtypes = [P, ctypes.c_int]
+    L.fcm_set_k_precision.argtypes = [P, ctypes.c_int]
     L.fcm_last_error.argtypes = [P]
     L.fcm_last_error.restype = ctypes.c_char_p
     L.fcm_destroy.argtypes = [P]
@@ -314,6 +316,11 @@ class Solver:
         else:
             self._check(load().fcm_apply_S_many(self.ctx, pr, nr, pz))
         return z
+
+    def set_k_precision(self, mode):
+        """K x in "fp64" or "double_float" arithmetic (every K apply of the context, solves included)."""
+        self._check(load().fcm_set_k_precision(self.ctx, {"fp64": 0, "double_float": 1}[mode]))
+        self.info = self.get_info()
 
     def set_wait_limit(self, tries):
         """Polls of the Schwarz kernels' bounded bulk-copy wait (0: give up at once; < 0: default)."""

@@ -253,3 +253,39 @@ def test_launch_shapes_leave_S_unchanged(precision):
     u0, its0, _, _ = s.pcg_solve(s.rhs(), w.tol, 5000)
     assert its0 == its1 and torch.equal(u0, u1)
     s.close()
+
+
+@pytest.mark.parametrize("p,n", [(1, (3, 2, 2)), (2, (4, 4, 4)), (3, (2, 2, 3)), (4, (2, 1, 2))])
+def test_apply_K_double_float_matches_oracle(p, n):
+    # K x in double-float arithmetic on the FP32 pipe: every contraction to ~2^-46, so the result agrees
+    # with the oracle's FP64 K x to the same 1e-12 (max norm) as the FP64 kernels
+    g = I.random_sphere_voids(9, 3, 0.15, 0.3, octree_depth=2)
+    w = I.Workload("orders_ff", n, p, 1e-6, g, 1e-9, hi=(0.3 * n[0], 0.25 * n[1], 0.2 * n[2]))
+    P = O.Problem.from_workload(w)
+    s = _solver(w)
+    s.set_k_precision("double_float")
+    assert s.info["k_double_float"] == 1
+    for seed in (7, 8):
+        x = I.random_vector(seed + p, s.n)
+        y = s.apply_K(_lat(x)).cpu().numpy()
+        y_ref = P.apply_K(x[P.free_lat])
+        assert np.abs(y[P.free_lat] - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+        mask = np.zeros(s.n, dtype=bool)
+        mask[P.free_lat] = True
+        assert not y[~mask].any()
+    s.close()
+
+
+def test_pcg_with_double_float_K(porous8):
+    w, P, x_ref, its_o = porous8
+    s = _solver(w)
+    s.set_k_precision("double_float")
+    s.precond_build()
+    u, its, rel, st = s.pcg_solve(s.rhs(), w.tol, 5000)
+    assert abs(its - its_o) <= 2
+    assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
+    # back to FP64 K: the graphs are captured again
+    s.set_k_precision("fp64")
+    u2, its2, _, _ = s.pcg_solve(s.rhs(), w.tol, 5000)
+    assert abs(its2 - its_o) <= 2 and s.get_info()["k_double_float"] == 0
+    s.close()
