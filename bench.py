@@ -1,9 +1,10 @@
 """Benchmark: PCG time-to-solution of the finite cell Schwarz-PCG on one GB300.
 
 A step is one complete preconditioned CG solve (x0 = 0 to ||S r|| / ||S b|| <=
-tol) of the 32^3-cell, p=3 porous cube (40 seeded spherical voids, alpha 1e-10,
-octree depth 4) with the set-up, the preconditioner and the coarse operator
-built once beforehand.  Forms:
+tol) of the default workload, the 80^3-cell, p=2 porous cube with 300 seeded
+spherical voids (alpha 1e-10, octree depth 3, 11.4M free DOFs; the largest
+configuration that fits one GPU), with the set-up, the preconditioner and the
+coarse operator built once beforehand.  Forms:
 
   coarse (default): flexible CG, z = S r + P y with y from `--coarse-iters`
                     coarse CG steps on K_H = P^T K P (optionally started from a
@@ -38,7 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PCG time-to-solution (s) and GB/s vs HBM roofline at 1e-8, learned/mixed vs plain FP64"
-DEFAULT_WORKLOAD = "porous40_32_p3"
+DEFAULT_WORKLOAD = "porous300_80_p2"
 
 
 def _peaks():
@@ -56,7 +57,7 @@ FP64_FLOP_PER_CLK_PER_SM = 4
 N_SM = 152
 
 
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "schwarz_colour_kernel_traffic_porous40_32_p3.md")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "schwarz_apply_traffic_porous300_80_p2.md")
 
 
 def _schwarz_traffic(workload_name, precision):
@@ -64,7 +65,7 @@ def _schwarz_traffic(workload_name, precision):
 
     The capture (dram__bytes_read.sum + dram__bytes_write.sum over the 8 colour launches of one S
     apply) holds for the kernel source it was taken with: the profile records the SHA-256 of
-    fcm_kernels.cu, and any other source gives None.
+    fcm_schwarz.cu, and any other source gives None.
     """
     import hashlib
     import re
@@ -75,7 +76,7 @@ def _schwarz_traffic(workload_name, precision):
     m_h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
     if not m_b or not m_h:
         return None
-    src = os.path.join(ROOT, "paper_1809_00828_gb300", "csrc", "fcm_kernels.cu")
+    src = os.path.join(ROOT, "paper_1809_00828_gb300", "csrc", "fcm_schwarz.cu")
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != m_h.group(1):
         return None
     return float(m_b.group(1))
@@ -180,6 +181,52 @@ def oracle_sample(w, gpu_iterations, sapply_fmas, kapply_fmas, min_seconds=10.0)
     return value, sample, t_total
 
 
+# iterations of plain FP64 Schwarz-PCG (the oracle's algorithm) measured on the GPU for these workloads
+REF_ITERATIONS = {"porous40_32_p3": 877, "porous300_80_p2": 2706}
+
+FULL_SOLVE_WORKLOAD = ("porous40_8_p2", 11, 8, 2, 40, 1e-10, 3, 1e-8)
+
+
+def full_solve_comparison(fcm=None, repeats=3):
+    """A complete solve the oracle finishes in seconds, timed on the host and on the GPU.
+
+    The 8^3-cell, p = 2 member of the porous family (40 seeded voids, seed 11, 13,872 free DOFs): the
+    oracle's plain FP64 Schwarz-PCG (one thread, as it stands; set-up and preconditioner timed apart,
+    solve only, median of `repeats`) beside this library's plain FP64 Schwarz-PCG on the same problem
+    (device time of fcm_pcg_solve, median of `repeats`), when `fcm` is given.
+    """
+    from oracle import oracle as O
+    from paper_1809_00828_gb300 import inputs
+    name, seed, nc, p, cnt, alpha, depth, tol = FULL_SOLVE_WORKLOAD
+    w = inputs.workload_porous(seed, nc, p, cnt, alpha, depth, tol)
+    t0 = time.perf_counter()
+    P = O.Problem.from_workload(w)
+    t1 = time.perf_counter()
+    P.precond_build(0)
+    t2 = time.perf_counter()
+    times, its = [], 0
+    for _ in range(repeats):
+        ts = time.perf_counter()
+        _, its, _ = P.pcg(tol=tol, maxit=20000)
+        times.append(time.perf_counter() - ts)
+    out = {"workload": f"{name}: {nc}^3 cells, p={p}, {cnt} spherical voids (seed {seed}), alpha={alpha:g}, "
+                       f"octree depth {depth}, tol {tol:g}, {P.nfree} free DOFs",
+           "oracle_threads": 1, "oracle_setup_s": t1 - t0, "oracle_precond_s": t2 - t1,
+           "oracle_solve_s": statistics.median(times), "oracle_iterations": its}
+    if fcm is not None:
+        s = fcm.Solver(w)
+        s.precond_build(precision="fp64")
+        b = s.rhs()
+        gt = []
+        for _ in range(repeats + 1):
+            _, gits, _, _ = s.pcg_solve(b, tol, 20000)
+            gt.append(s.last_solve()["seconds"])
+        out.update({"gpu_solve_s": statistics.median(gt[1:]), "gpu_iterations": gits,
+                    "solve_speedup": statistics.median(times) / statistics.median(gt[1:])})
+        s.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -189,18 +236,23 @@ def run_reference(args, rank, world):
     # take hours)
     gpu_like_iters = args.ref_iterations
     kf, sf = _host_work_counts(w)
-    steps = []
+    steps, walls = [], []
     sample = ""
     for i in range(args.warmup + args.steps):
-        v, sample, _ = oracle_sample(w, gpu_like_iters, sf, kf, min_seconds=2.0 if i < args.warmup else 10.0)
+        v, sample, wall = oracle_sample(w, gpu_like_iters, sf, kf, min_seconds=1.0 if i < args.warmup else 5.0)
         if i >= args.warmup:
             steps.append(v)
+            walls.append(wall)
     value = statistics.median(steps)
+    # a step is a bounded sample (the corner window) whose per-iteration time is scaled to the whole
+    # workload; ms_per_step is the wall time a sample actually took
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": _describe(w, args), "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(walls) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _describe(w, args), "precision": "fp64",
+                       "value_kind": "time-to-solution of the whole workload, scaled from each step's sample"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "full_solve_measured": full_solve_comparison(None)},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -253,20 +305,20 @@ def _form(args, net):
             f"coarse operator K_H = P^T K P starting from {start}")
 
 
-def _launches_per_solve(args, its, net):
-    """Kernels of one solve (device-side loop, so the count follows the iterations)."""
-    k_apply = 1 + 2 * 8        # zero q, uncut and cut launches of the 8 colours
-    s_apply = 1 + 8            # zero z, one launch per colour
+def _launches_per_solve(args, info, its, flex_its, net):
+    """Kernels of one solve (device-side loop, so the count follows the iterations): K and S applies
+    from the library's own counts, plus the CG vector kernels, the coarse solve and the network."""
+    k_apply, s_apply = info["k_apply_launches"], info["s_apply_launches"]
+    plain = k_apply + 2 + s_apply + 2                   # K, pq, xr, S, rz, p
+    start = 3 + 1 + s_apply + 1 + k_apply + 2           # mask copy, norms, init, first S, first kernel, true residual
     if args.form == "pcg":
-        graphs = -(-its // 8)
-        return 4 + s_apply + 1 + graphs * 8 * (k_apply + 2 + s_apply + 2) + k_apply + 1
+        return start + its * plain
     k = args.coarse_iters
     coarse = 1 + (1 + 2 * k) + 1                        # restrict, coarse start + 2 per step, prolong
     if net is not None:
         coarse += 2 + 1 + 2 + _unet_launches(net)       # sigma, prep, post, start apply + line search
-    per_it = k_apply + 2 + s_apply + 1 + coarse + 2    # pq, xr, conv, dots, newp
-    graphs = -(-its // 4)
-    return 1 + s_apply + 1 + coarse + 1 + graphs * 4 * per_it + k_apply + 3
+    flex = k_apply + 2 + s_apply + 1 + coarse + 2       # pq, xr, conv, dots, newp
+    return start + coarse + flex_its * flex + (its - flex_its) * plain
 
 
 def _unet_launches(net):
@@ -297,6 +349,8 @@ def run_fcm(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = _workload(args.workload)
     s = fcm.Solver(w)
+    k_prec = args.k_precision if args.precision != "fp64" else "fp64"
+    s.set_k_precision(k_prec)
     s.precond_build(precision=args.precision, blocks=args.blocks, eta_bar=args.eta_bar)
     n = s.n
     # load cases: 0 = traction on z = 1; 1..6 = unit Voigt strains (one solve of all six)
@@ -324,6 +378,23 @@ def run_fcm(args, rank, world, local_rank):
             _, its, rel, _ = s.pcg_solve(b, w.tol, args.maxit, out=out)
         return its, rel
 
+    if args.profile_apply:
+        # apply S (or K) a few times between cudaProfilerStart / Stop, after 3 warm-up applies, for
+        # `ncu --profile-from-start off`; no JSON line
+        r = b[:n].clone()
+        z = s.empty()
+        op = s.apply_S if args.profile_apply == "S" else s.apply_K
+        for _ in range(3):
+            op(r, out=z)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.profile_reps):
+            op(r, out=z)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"profiled {args.profile_reps} {args.profile_apply} applies of {w.name}")
+        s.close()
+        return 0
     for _ in range(args.warmup):
         its, rel = solve(u)
     if args.profile_one_step:
@@ -359,7 +430,7 @@ def run_fcm(args, rank, world, local_rank):
     ms_per_step = elapsed / args.steps * 1e3
     last = s.last_solve()
 
-    # dominant kernel: the Schwarz block apply (8 colour launches), timed live on the stream
+    # the Schwarz apply (all its launches, block products and sum) and the K apply, timed live on the stream
     r = b[:n].clone()
     z = s.empty()
     for _ in range(3):
@@ -389,10 +460,13 @@ def run_fcm(args, rank, world, local_rank):
     fp64_peak = fp64_peak_tflops(sm_mhz)
     achieved_tf = s_flops / t_s / 1e12
     achieved_gbs = s_bytes / t_s / 1e9
-    kernel = (f"S apply: schwarz_gemm_kernel<{w.p}> (shared factors) + "
+    shared = (f"tc_gemm_kernel<{w.p}> (tcgen05, shared factors)" if args.precision != "fp64" and w.p in (2, 3)
+              else f"schwarz_gemm_kernel<{w.p}> (shared factors)")
+    kernel = (f"S apply, {info['s_apply_launches']} launches: {shared} + "
               f"{'schwarz_rows_kernel' if w.p == 3 else 'schwarz_cols_kernel'}<{w.p}> (streamed factors) + "
-              f"schwarz_sum_kernel<{w.p}>, "
-              f"{'concurrent' if info['schwarz_concurrent'] else 'serial'} (the shape the build's autotuner kept)")
+              f"schwarz_sum_kernel<{w.p}>, shared-factor products "
+              f"{'beside' if info['schwarz_concurrent'] else 'before'} the streamed ones (the shape the build's "
+              f"autotuner kept)")
     if args.precision == "fp64":
         # FP64 factors: one FP64 multiply-add per 8-byte entry; the FP64 pipe saturates first
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -428,8 +502,8 @@ def run_fcm(args, rank, world, local_rank):
                          "kh_note": f"K_H ({nc * 63 * 9 * 4 / 1e6:.0f} MB) "
                                     + ("stays in L2 (129 MB) across a coarse solve, so this rate can exceed the "
                                        "HBM copy peak" if nc * 63 * 9 * 4 < 100e6 else "streams from HBM")})
-    roofline.update({"s_apply_ms": t_s * 1e3, "k_apply_ms": t_k * 1e3,
-                     "k_apply_fp64_tflops": 2.0 * info["kapply_fmas"] / t_k / 1e12,
+    roofline.update({"s_apply_ms": t_s * 1e3, "k_apply_ms": t_k * 1e3, "k_precision": k_prec,
+                     "k_apply_multiply_adds_per_s": info["kapply_fmas"] / t_k,
                      "k_apply_fp64_frac": 2.0 * info["kapply_fmas"] / t_k / 1e12 / fp64_peak,
                      "algorithmic_bytes_per_s_apply": s_bytes})
 
@@ -456,12 +530,13 @@ def run_fcm(args, rank, world, local_rank):
     e2e = (time.perf_counter() - t0) / e2e_steps
 
     its_med = int(statistics.median(iters))
-    launches_per_solve = _launches_per_solve(args, its_med, net) * (nrhs if args.form == "coarse" else 1)
+    flex_its = last["flexible_iterations"] if args.form == "coarse" else 0
+    launches_per_solve = _launches_per_solve(args, info, its_med, flex_its, net) * (nrhs if args.form == "coarse" else 1)
     line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
             "config": {"workload": _describe(w, args), "loads": args.loads, "form": _form(args, net),
-                       "precision": args.precision, "n_free": info["n_free"],
+                       "precision": args.precision, "k_precision": k_prec, "n_free": info["n_free"],
                        "iterations": its_med, "relres": rel, "true_relres": last["true_relres"],
                        "fell_back_to_plain_pcg": bool(last["fallback"]) if args.form == "coarse" else None,
                        "flexible_iterations": last["flexible_iterations"] if args.form == "coarse" else None,
@@ -496,6 +571,7 @@ def run_fcm(args, rank, world, local_rank):
                 tm.append(s.last_solve()["seconds"])  # device time of the call (all right-hand sides)
             line["config"]["plain_mixed"] = {"seconds": statistics.median(tm), "iterations": itsm,
                                              "speedup_of_this_form": statistics.median(tm) / (ms_per_step / 1e3)}
+        s.set_k_precision("fp64")
         s.precond_build(precision="fp64", blocks=args.blocks, eta_bar=args.eta_bar)
         x64, its64, _, _ = s.pcg_solve(b, w.tol, args.maxit)
         t64 = []
@@ -519,7 +595,8 @@ def run_fcm(args, rank, world, local_rank):
         if nrhs > 1:
             v *= nrhs
             sample += f"; times {nrhs} right-hand sides"
-        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                                "full_solve_measured": full_solve_comparison(fcm)}
     if net is not None:
         net.close()
     s.close()
@@ -542,7 +619,9 @@ def main():
                          "compared with plain FP64 in the same run")
     ap.add_argument("--form", default="coarse", choices=["coarse", "pcg"],
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
-    ap.add_argument("--coarse-iters", type=int, default=20)
+    ap.add_argument("--coarse-iters", type=int, default=10)
+    ap.add_argument("--k-precision", default="double_float", choices=["double_float", "fp64"],
+                    help="arithmetic of K x in the forms with FP32 factors (plain FP64 always uses FP64 K)")
     ap.add_argument("--stall-window", type=int, default=100,
                     help="iterations without halving after which the flexible CG falls back to plain PCG")
     ap.add_argument("--net", default=None, help="U-Net checkpoint whose prediction starts the coarse solve")
@@ -555,9 +634,13 @@ def main():
                     help="element blocks for the cells with volume fraction at most this (1: every cell); "
                          "the DOFs in no block diagonal")
     ap.add_argument("--ref-iterations", type=int, default=None,
-                    help="iteration count that scales the reference arm's per-iteration time (default 877, the plain "
-                         "FP64 Schwarz-PCG count of porous40_32_p3, which the oracle's algorithm shares)")
+                    help="iteration count that scales the reference arm's per-iteration time (default: the plain "
+                         "FP64 Schwarz-PCG count measured on the GPU for the workload, which the oracle's "
+                         "algorithm shares)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-apply", default=None, choices=["S", "K"],
+                    help="apply S or K --profile-reps times between cudaProfilerStart/Stop and exit (for ncu)")
+    ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="after the warm-up, run one step between cudaProfilerStart/Stop and exit (for ncu)")
     args = ap.parse_args()
@@ -565,10 +648,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if args.ref_iterations is None and args.workload not in REF_ITERATIONS:
+            print(json.dumps({"impl": "reference", "unavailable": f"no plain FP64 iteration count recorded for "
+                                                                  f"{args.workload}; pass --ref-iterations"}))
+            return 0
         if args.ref_iterations is None:
-            # iterations of the plain FP64 Schwarz-PCG on porous40_32_p3 (the oracle runs the same
-            # algorithm; its iteration count at this size is taken from the GPU runs, 876-877)
-            args.ref_iterations = 877
+            args.ref_iterations = REF_ITERATIONS[args.workload]
         return run_reference(args, rank, world)
     return run_fcm(args, rank, world, local_rank)
 

@@ -118,6 +118,8 @@ typedef struct {
     int64_t n_factors_ff;     /* factors stored as double-float pairs (FCM_PREC_MIXED, cond > cond_fp64) */
     int64_t n_gemm_blocks;    /* blocks applied by the shared-factor dense product        */
     int k_double_float;       /* 1: K applied in double-float arithmetic (fcm_set_k_precision) */
+    int s_apply_launches;     /* kernel launches of one fcm_apply_S (one right-hand side, masked copy excluded) */
+    int k_apply_launches;     /* kernel launches of one fcm_apply_K (masked copy excluded)  */
 } fcm_info_t;
 
 enum { FCM_PREC_FP64 = 0, FCM_PREC_MIXED = 1, FCM_PREC_MIXED_FP64 = 2 };

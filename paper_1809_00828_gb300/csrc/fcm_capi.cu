@@ -190,7 +190,7 @@ void free_ctx(fcm_ctx *C)
     if (C->h_ms) cudaFreeHost(C->h_ms);
     fcm::fcg_free(C->fcg);
     fcm::coarse_free(C->coarse);
-    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1, C->ev_fork, C->ev_join};
+    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1, C->ev_f0, C->ev_f1, C->ev_fork, C->ev_join};
     for (auto e : evs)
         if (e) cudaEventDestroy(e);
     if (C->side) cudaStreamDestroy(C->side);
@@ -268,6 +268,8 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     SETUP_CUDA(cudaEventCreateWithFlags(&C->ev_out, cudaEventDisableTiming));
     SETUP_CUDA(cudaEventCreate(&C->ev_t0));
     SETUP_CUDA(cudaEventCreate(&C->ev_t1));
+    SETUP_CUDA(cudaEventCreate(&C->ev_f0));
+    SETUP_CUDA(cudaEventCreate(&C->ev_f1));
     const size_t ne2 = (size_t)hp.ne * hp.ne;
     const int64_t nelem = 1 + hp.ncut;
     SETUP_CUDA(dalloc(&C->d_elem, ne2 * nelem));
@@ -390,6 +392,18 @@ fcm_status fcm_info(const fcm_ctx *C, fcm_info_t *out)
     out->schwarz_concurrent = C->plan.concurrent;
     out->n_factors_ff = C->n_ff_factors;
     out->k_double_float = C->k_ff;
+    {
+        const fcm::SchwarzPlan &pl = C->plan;
+        const bool tc = pl.n_tc_tiles > 0;
+        const int own = (fcm::schwarz_uses_rows_kernel(C->p) ? pl.n_row_items : pl.n_col_items) > 0;
+        out->s_apply_launches = C->have_precond ? (tc ? 1 : 0) + ((tc ? pl.n_tiles32_plain : pl.n_tiles32) > 0) +
+                                                      (pl.n_tiles64 > 0) + own + 1
+                                                : 0;
+        int k = 1;  // zero y
+        for (int c = 0; c < 8; ++c)
+            k += (C->kc.uncut_off[c + 1] > C->kc.uncut_off[c]) + (C->kc.cut_off[c + 1] > C->kc.cut_off[c]);
+        out->k_apply_launches = k;
+    }
     out->n_gemm_blocks = C->n_gemm_blocks;
     for (int k = 0; k < 8; ++k) out->tune_seconds[k] = C->tune_seconds[k];
     out->device_error = 0;

@@ -615,7 +615,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     h.maxit = maxit;
     h.window = C->fcg_window;
     CO_CUDA(C, cudaMemcpyAsync(F->d, &h, sizeof h, cudaMemcpyHostToDevice, st));
-    CO_CUDA(C, cudaEventRecord(C->ev_t0, st));
+    CO_CUDA(C, cudaEventRecord(C->ev_f0, st));
     CO_CUDA(C, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     CO_CUDA(C, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     ctx_apply_S_flag(C, r, zS, nullptr);
@@ -670,7 +670,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     } else if (fallback) {
         status = FCM_ENOTCONV;
     }
-    cudaEventRecord(C->ev_t1, st);
+    cudaEventRecord(C->ev_f1, st);
     CO_CUDA(C, cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     ctx_apply_K_flag(C, x, q, nullptr);
     if ((s = dot2(C, b, b, nullptr, nullptr, h2)) != FCM_OK) return s;
@@ -678,7 +678,7 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     sub_kernel<<<nblk(n), 256, 0, st>>>(F->c, b, q, n);
     if ((s = dot2(C, F->c, F->c, nullptr, nullptr, h2)) != FCM_OK) return s;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, C->ev_t0, C->ev_t1);
+    cudaEventElapsedTime(&ms, C->ev_f0, C->ev_f1);
     C->last.iterations = total;
     C->last.relres = rel;
     C->last.true_relres = bb > 0.0 ? std::sqrt(h2[0] / bb) : 0.0;

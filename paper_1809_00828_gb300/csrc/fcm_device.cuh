@@ -190,6 +190,7 @@ struct fcm_ctx {
     cudaStream_t ustream = nullptr;  // caller's stream (ordering with the caller)
     cudaStream_t stream = nullptr;   // the library's own work stream (capturable)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;  // start and end of a flexible solve (ev_t0/ev_t1 time its inner plain solve)
     fcm::HostProblem hp;
     fcm::Grid3 g;
     int p = 0, ne = 0;

@@ -701,8 +701,14 @@ std::string build_preconditioner(fcm_ctx *C, const fcm_precond_opts &o)
     const size_t n_tiles = tiles32.size() + tiles64.size();
     PC_CUDA(reup(&C->d_items, max_rows_items + col_items.size() + n_tiles));
     const int zs = (maxn + 7) / 8 * 8;
+    // the sum kernel addresses Zb in 32-bit float offsets
+    if (2 * (int64_t)slots.size() * zs >= ((int64_t)1 << 31)) return "too many blocks for the block-product buffer";
     PC_CUDA(reup(&C->d_zb, (size_t)slots.size() * zs));
     PC_CUDA(cudaMemcpyAsync(C->d_slots, slots.data(), sizeof(PatchRec) * slots.size(), cudaMemcpyHostToDevice, st));
+    // the pair format stores FP32 slots as floats: their slot_of entries carry the flag the sum kernel reads
+    if (mixed)
+        for (int64_t v = 0; v < npatch; ++v)
+            if (slot_of[v] >= 0 && slots[slot_of[v]].prec == 1) slot_of[v] |= 1 << 30;
     PC_CUDA(cudaMemcpyAsync(C->d_slot_of, slot_of.data(), sizeof(int) * slot_of.size(), cudaMemcpyHostToDevice, st));
     int2 *d_col = C->d_items + max_rows_items, *d_tiles = d_col + col_items.size();
     PC_CUDA(cudaMemcpyAsync(d_col, col_items.data(), sizeof(int2) * col_items.size(), cudaMemcpyHostToDevice, st));

@@ -78,31 +78,36 @@ __device__ __forceinline__ int64_t box_base(const SBox &b, const Grid3 &g)
     return 3 * (b.lo[0] + (int64_t)g.M[0] * (b.lo[1] + (int64_t)g.M[1] * b.lo[2]));
 }
 
-// Block products Zb.  With `pairs` (the mixed forms) an entry is a float pair (hi, lo) whose sum is
-// the value: FP32 results (v, 0), double-float results (S, C), FP64 results split by split_bits<23>;
-// the sum kernel then adds them on the FP32 pipe.  Otherwise (FP64 form) an entry is an FP64 value.
-__device__ __forceinline__ void put_f32(double *zb, int64_t i, float v, bool pairs)
+// Block products Zb: nslots * zs entries of 8 bytes per right-hand side, slot by slot.  With `pairs`
+// (the mixed forms) a slot of an FP32 factor holds its rows as floats (the first half of the slot's
+// bytes), any other slot as float pairs (hi, lo) whose sum is the value: double-float results (S, C),
+// FP64 results split by split_bits<23>; the sum kernel adds them on the FP32 pipe.  Otherwise (FP64
+// form) a slot holds FP64 values.  `zslot` points at the slot's first entry.
+__device__ __forceinline__ void put_f32(double *zslot, int row, float v, bool pairs)
 {
-    if (pairs) reinterpret_cast<float2 *>(zb)[i] = make_float2(v, 0.f);
-    else zb[i] = f2d(v);
+    if (pairs) reinterpret_cast<float *>(zslot)[row] = v;
+    else zslot[row] = f2d(v);
 }
-__device__ __forceinline__ void put_ff(double *zb, int64_t i, float s, float c, bool pairs)
+__device__ __forceinline__ void put_ff(double *zslot, int row, float s, float c, bool pairs)
 {
-    if (pairs) reinterpret_cast<float2 *>(zb)[i] = make_float2(s, c);
-    else zb[i] = f2d(s) + f2d(c);
+    if (pairs) reinterpret_cast<float2 *>(zslot)[row] = make_float2(s, c);
+    else zslot[row] = f2d(s) + f2d(c);
 }
-__device__ __forceinline__ void put_f64(double *zb, int64_t i, double v, bool pairs)
+__device__ __forceinline__ void put_f64(double *zslot, int row, double v, bool pairs)
 {
     if (pairs) {
         float h, l;
         split_bits<23>(v, h, l);
-        reinterpret_cast<float2 *>(zb)[i] = make_float2(h, l);
+        reinterpret_cast<float2 *>(zslot)[row] = make_float2(h, l);
     } else {
-        zb[i] = v;
+        zslot[row] = v;
     }
 }
-__device__ __forceinline__ void put_val(double *zb, int64_t i, float v, bool pairs) { put_f32(zb, i, v, pairs); }
-__device__ __forceinline__ void put_val(double *zb, int64_t i, double v, bool pairs) { put_f64(zb, i, v, pairs); }
+__device__ __forceinline__ void put_val(double *zslot, int row, float v, bool pairs) { put_f32(zslot, row, v, pairs); }
+__device__ __forceinline__ void put_val(double *zslot, int row, double v, bool pairs) { put_f64(zslot, row, v, pairs); }
+
+// slot_of entries of FP32 slots in the pair format carry this flag
+constexpr int kSlotF32 = 1 << 30;
 
 // 16-byte vectors of float (4) or double (2)
 template <typename T> struct V16;
@@ -290,7 +295,7 @@ __device__ __forceinline__ void cols_plain(const double *__restrict__ r, int64_t
     }
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-        if (k < nr) put_val(zout, (int64_t)k * zsize + row, acc[k], pairs);
+        if (k < nr) put_val(zout + (int64_t)k * zsize, row, acc[k], pairs);
 }
 
 template <int P, int NR>
@@ -321,7 +326,7 @@ __device__ __forceinline__ void cols_ff(const double *__restrict__ r, int64_t nl
     }
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-        if (k < nr) put_ff(zout, (int64_t)k * zsize + row, S[k], C[k], pairs);
+        if (k < nr) put_ff(zout + (int64_t)k * zsize, row, S[k], C[k], pairs);
 }
 
 template <int P, int NR>
@@ -565,7 +570,7 @@ __global__ void __launch_bounds__(gemm_threads(P))
                     if (d < 0) continue;
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        if (row0 + i < n) put_val(zb, d + row0 + i, acc[i][j], pairs);
+                        if (row0 + i < n) put_val(zb + d, row0 + i, acc[i][j], pairs);
                 }
             }
         }
@@ -611,6 +616,8 @@ __device__ __forceinline__ AxisCand axis_cand(int rule, int i, int ncell, int M)
     return a;
 }
 
+// One thread per lattice node: blockDim (32, 8), grid (ceil(M0 / 32), ceil(M1 / 8), M2), so a warp is 32
+// consecutive nodes along x with the same y and z (coalesced Zb rows, warp-uniform y/z candidates).
 template <int P, bool PAIRS>
 __global__ void __launch_bounds__(256)
     schwarz_sum_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ jac,
@@ -618,51 +625,65 @@ __global__ void __launch_bounds__(256)
                        int64_t zsize, int64_t nlat, int nr, const int *__restrict__ done)
 {
     if (done && *done) return;
-    const int nnode = (int)(nlat / 3);
     const int nid0 = rule == 3 ? g.n[0] : g.n[0] + 1, nid1 = rule == 3 ? g.n[1] : g.n[1] + 1;
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nnode; node += gridDim.x * blockDim.x) {
-        const int i0 = node % g.M[0], i1 = (node / g.M[0]) % g.M[1], i2 = node / (g.M[0] * g.M[1]);
+    const int i0 = blockIdx.x * 32 + threadIdx.x, i1 = blockIdx.y * 8 + threadIdx.y, i2 = blockIdx.z;
+    if (i0 < g.M[0] && i1 < g.M[1]) {
+        const int64_t node = i0 + (int64_t)g.M[0] * (i1 + (int64_t)g.M[1] * i2);
         const AxisCand ax = axis_cand<P>(rule, i0, g.n[0], g.M[0]);
         const AxisCand ay = axis_cand<P>(rule, i1, g.n[1], g.M[1]);
         const AxisCand az = axis_cand<P>(rule, i2, g.n[2], g.M[2]);
-        // the (up to 8) blocks in a fixed order: their slot and the node's entry in it
-        int64_t ent[8];
+        // the (up to 8) blocks in a fixed order: the node's first entry in the block's slot (entries of
+        // 8 bytes from the start of Zb; nslots * zs < 2^31), -1 for none, and the slot's format
+        int ent[8];
+        bool f32[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int kx = q & 1, ky = (q >> 1) & 1, kz = q >> 2;
-            int64_t e = -1;
-            if (ax.on[kx] && ay.on[ky] && az.on[kz]) {
-                const int slot = slot_of[ax.id[kx] + nid0 * (ay.id[ky] + nid1 * az.id[kz])];
-                if (slot >= 0)
-                    e = (int64_t)slot * zs + 3 * (ax.loc[kx] + ax.dim[kx] * (ay.loc[ky] + ay.dim[ky] * az.loc[kz]));
-            }
-            ent[q] = e;
+            int sv = -1;
+            if (ax.on[kx] && ay.on[ky] && az.on[kz]) sv = slot_of[ax.id[kx] + nid0 * (ay.id[ky] + nid1 * az.id[kz])];
+            f32[q] = sv >= 0 && (sv & kSlotF32);
+            ent[q] = sv < 0 ? -1 : (sv & (kSlotF32 - 1)) * zs;
+            // within the slot: FP32 slots count floats, the others 8-byte entries
+            const int loc = 3 * (ax.loc[kx] + ax.dim[kx] * (ay.loc[ky] + ay.dim[ky] * az.loc[kz]));
+            ent[q] = sv < 0 ? -1 : 2 * ent[q] + (f32[q] ? loc : 2 * loc);  // in floats
         }
         for (int k = 0; k < nr; ++k) {
-            const int64_t gi = (int64_t)k * nlat + 3 * (int64_t)node;
-            // FP64 entries: FP64 sums; float pairs: TwoSum on the FP32 pipe, one FP64 add per DOF at the end
+            const int64_t gi = (int64_t)k * nlat + 3 * node;
+            const float *zk = reinterpret_cast<const float *>(zb + (int64_t)k * zsize);
+            // FP64 entries: FP64 sums.  Pair format: FP32 results summed in FP32 (they carry FP32 accuracy),
+            // float pairs by TwoSum; one FP64 add per DOF at the end.
             double acc[3] = {0.0, 0.0, 0.0};
-            float S[3] = {0.f, 0.f, 0.f}, C[3] = {0.f, 0.f, 0.f};
+            float S[3] = {0.f, 0.f, 0.f}, C[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (ent[q] < 0) continue;
-                const int64_t e = (int64_t)k * zsize + ent[q];
+                const float *zf = zk + ent[q];
                 if constexpr (PAIRS) {
-                    const float2 *zr = reinterpret_cast<const float2 *>(zb) + e;
+                    if (f32[q]) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float2 v = zr[c];
-                        ff_add(S[c], C[c], v.x, v.y);
+                        for (int c = 0; c < 3; ++c) F[c] = __fadd_rn(F[c], zf[c]);
+                    } else {
+                        const float2 *zp = reinterpret_cast<const float2 *>(zf);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float2 v = zp[c];
+                            ff_add(S[c], C[c], v.x, v.y);
+                        }
                     }
                 } else {
+                    const double *zd = reinterpret_cast<const double *>(zf);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) acc[c] += zb[e + c];
+                    for (int c = 0; c < 3; ++c) acc[c] += zd[c];
                 }
+            }
+            if constexpr (PAIRS) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ff_add(S[c], C[c], F[c], 0.f);
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double v = PAIRS ? f2d(S[c]) + f2d(C[c]) : acc[c];
-                if (jac) v = fma(jac[3 * (int64_t)node + c], r[gi + c], v);
+                if (jac) v = fma(jac[3 * node + c], r[gi + c], v);
                 z[gi + c] = v;
             }
         }
@@ -699,10 +720,11 @@ template <int P> struct TcCfg {
     static constexpr int A_BYTES = 2 * 128 * 16 * 4;                 // hi and lo of 128 columns x 16 K
     static constexpr int B_BYTES = 2 * NRP * 16 * 4;                 // hi and lo of NRP rows x 16 K
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = STAGE * 4 <= 196 * 1024 ? 4 : 3;
+    static constexpr int STAGES = 3;
     static constexpr int HEAD = 4096;                                // barriers, TMEM address, column bases, box offsets
     static constexpr int SMEM = HEAD + STAGES * STAGE;
     static constexpr int THREADS = 32 * 9;                           // warp 0: copies and MMAs; warps 1-8: producers
+    static constexpr int CTAS_PER_SM = 2 * SMEM <= 227 * 1024 ? 2 : 1;
 };
 static_assert(TcCfg<3>::NPIECE % 16 == 0 && TcCfg<3>::NPIECE <= 256 && TcCfg<2>::NPIECE % 16 == 0, "MMA N");
 static_assert(TcCfg<3>::SMEM <= 227 * 1024 && TcCfg<2>::SMEM <= 227 * 1024, "tensor-core tile exceeds shared memory");
@@ -776,7 +798,7 @@ __global__ void tc_factor_kernel(const double *__restrict__ F, int n, float *__r
 }
 
 template <int P>
-__global__ void __launch_bounds__(TcCfg<P>::THREADS, 1)
+__global__ void __launch_bounds__(TcCfg<P>::THREADS, TcCfg<P>::CTAS_PER_SM)
     tc_gemm_kernel(const double *__restrict__ r, const PatchRec *__restrict__ slots, const TcTile *__restrict__ tiles,
                    Grid3 g, int rule, const float *__restrict__ ft, double *__restrict__ zb, int zs, int pairs,
                    int *err, int wait_tries, const int *__restrict__ done)
@@ -936,7 +958,8 @@ __global__ void __launch_bounds__(TcCfg<P>::THREADS, 1)
             __syncwarp();
             for (int i = 0; i < 16; ++i) {  // columns 2 i, 2 i + 1: 16 rows each
                 const int ml = 2 * i + (lane >> 4), row = j0 + (lane & 15), mm = 32 * q4 + ml;
-                if (mm < tl.count && row < n) put_f32(zb, (int64_t)(tl.first + mm) * zs + row, tb[ml * 17 + (lane & 15)], pairs);
+                if (mm < tl.count && row < n)
+                    put_f32(zb + (int64_t)(tl.first + mm) * zs, row, tb[ml * 17 + (lane & 15)], pairs);
             }
             __syncwarp();
         }
@@ -948,12 +971,7 @@ __global__ void __launch_bounds__(TcCfg<P>::THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS) : "memory");
 }
 
-int sum_grid(int64_t nnode)
-{
-    int64_t b = (nnode + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    return (int)std::max<int64_t>(b, 1);
-}
+dim3 sum_grid(const Grid3 &g) { return dim3((g.M[0] + 31) / 32, (g.M[1] + 7) / 8, g.M[2]); }
 
 template <int P>
 void gemm_launch(const double *r, int64_t nlat, int nr, const double *f64, const float *f32, const SchwarzPlan &pl,
@@ -1017,10 +1035,10 @@ void apply_p(const double *r, double *z, int64_t nlat, int nr, const double *f64
     }
     if (side) cudaStreamWaitEvent(s, pl.ev_join, 0);
     if (pl.pairs)
-        schwarz_sum_kernel<P, true><<<sum_grid(nlat / 3), 256, 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule,
+        schwarz_sum_kernel<P, true><<<sum_grid(pl.g), dim3(32, 8), 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule,
                                                                        pl.zs, zsize, nlat, nr, done);
     else
-        schwarz_sum_kernel<P, false><<<sum_grid(nlat / 3), 256, 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule,
+        schwarz_sum_kernel<P, false><<<sum_grid(pl.g), dim3(32, 8), 0, s>>>(r, z, pl.jac, zb, pl.slot_of, pl.g, pl.rule,
                                                                         pl.zs, zsize, nlat, nr, done);
 }
 

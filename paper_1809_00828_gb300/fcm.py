@@ -65,7 +65,8 @@ class Info(ctypes.Structure):
                 ("stream_rows", ctypes.c_int), ("schwarz_concurrent", ctypes.c_int),
                 ("tune_seconds", ctypes.c_double * 8),
                 ("device_error", ctypes.c_int), ("n_factors_ff", ctypes.c_int64), ("n_gemm_blocks", ctypes.c_int64),
-                ("k_double_float", ctypes.c_int)]
+                ("k_double_float", ctypes.c_int), ("s_apply_launches", ctypes.c_int),
+                ("k_apply_launches", ctypes.c_int)]
 
 
 class PrecondOpts(ctypes.Structure):
