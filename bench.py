@@ -184,6 +184,9 @@ def oracle_sample(w, gpu_iterations, sapply_fmas, kapply_fmas, min_seconds=10.0)
 # iterations of plain FP64 Schwarz-PCG (the oracle's algorithm) measured on the GPU for these workloads
 REF_ITERATIONS = {"porous40_32_p3": 877, "porous300_80_p2": 2706}
 
+MODEL_NOTE = ("model: the oracle's measured per-iteration time on the corner window, scaled by multiply-adds to "
+              "the whole workload; full_solve_measured is a complete oracle solve, measured")
+
 FULL_SOLVE_WORKLOAD = ("porous40_8_p2", 11, 8, 2, 40, 1e-10, 3, 1e-8)
 
 
@@ -252,7 +255,7 @@ def run_reference(args, rank, world):
             "config": {"workload": _describe(w, args), "precision": "fp64",
                        "value_kind": "time-to-solution of the whole workload, scaled from each step's sample"},
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
-                             "full_solve_measured": full_solve_comparison(None)},
+                             "value_kind": MODEL_NOTE, "full_solve_measured": full_solve_comparison(None)},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -596,7 +599,7 @@ def run_fcm(args, rank, world, local_rank):
             v *= nrhs
             sample += f"; times {nrhs} right-hand sides"
         line["cpu_baseline"] = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
-                                "full_solve_measured": full_solve_comparison(fcm)}
+                                "value_kind": MODEL_NOTE, "full_solve_measured": full_solve_comparison(fcm)}
     if net is not None:
         net.close()
     s.close()
@@ -604,6 +607,66 @@ def run_fcm(args, rank, world, local_rank):
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_mlhp(args):
+    """Multi-level hp path on the Sec. 5.1 cube: 8^3 base cells, p = 3, a cavity of radius 0.01 at the
+    centre refined `args.mlhp_k` times toward its surface, alpha = 1e-8, truncated blocks.  One JSON line:
+    host set-up times, the device K and S applies (CUDA events on the plan's stream, median of 20 after 3
+    warm-ups) with their algorithmic bytes and bandwidth, and the PCG solve to 1e-8.  Algorithmic bytes: K x
+    reads 12 B per CSR nonzero plus the row pointers and writes y; S r reads every factor entry once (8 B)
+    plus the gathers and the read-modify-write of z on the block DOFs."""
+    import numpy as np
+    import torch
+    from paper_1809_00828_gb300 import fcm
+
+    t0 = time.time()
+    P = fcm.MLHPPlan((8, 8, 8), (0, 0, 0), (1, 1, 1), [(0.5, 0.5, 0.5, 0.01)], 3, args.mlhp_k, octree_depth=3)
+    free, K, b, eta = P.assemble(1e-8, "clamp")
+    t1 = time.time()
+    blocks, F, cptr, jac = P.factorize("truncated")
+    t2 = time.time()
+    P.device_setup()
+    n = len(free)
+    x = torch.from_numpy(np.random.default_rng(1).standard_normal(n)).cuda()
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps=20, warm=3):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return float(np.median(ts))
+
+    tk = timed(lambda: P.apply_K(x, y))
+    ts = timed(lambda: P.apply_S(x, y))
+    bk = 12 * K.nnz + 8 * (n + 1) + 16 * n
+    nb_dofs = sum(len(B) for B in blocks)
+    bs = 8 * sum(len(B) ** 2 for B in blocks) + 4 * nb_dofs + 8 * nb_dofs * 3 + 24 * n
+    bd = torch.from_numpy(b).cuda()
+    torch.cuda.synchronize()
+    t3 = time.time()
+    _, its, _, status = P.pcg_solve(bd, 1e-8, 20000, check=False)
+    torch.cuda.synchronize()
+    t4 = time.time()
+    hbm = _peaks()[0]["hbm_gbs"]
+    print(json.dumps({"workload": f"mlhp cube: 8^3 base cells, p=3, cavity r=0.01, k={args.mlhp_k}, truncated blocks",
+                      "dofs": n, "nnz": int(K.nnz), "blocks": len(blocks), "colours": len(cptr) - 1,
+                      "assemble_s": round(t1 - t0, 2), "factorize_s": round(t2 - t1, 2),
+                      "apply_K_ms": round(tk * 1e3, 4), "apply_K_GBs": round(bk / tk * 1e-9, 1),
+                      "apply_K_frac": round(bk / tk * 1e-9 / hbm, 3),
+                      "apply_S_ms": round(ts * 1e3, 4), "apply_S_GBs": round(bs / ts * 1e-9, 1),
+                      "apply_S_frac": round(bs / ts * 1e-9 / hbm, 3),
+                      "pcg_iterations": its, "pcg_status": status, "pcg_s": round(t4 - t3, 4)}))
+    P.close()
     return 0
 
 
@@ -643,7 +706,11 @@ def main():
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="after the warm-up, run one step between cudaProfilerStart/Stop and exit (for ncu)")
+    ap.add_argument("--mlhp-k", type=int, default=None,
+                    help="instead of the bench line: time the multi-level hp path on the Sec. 5.1 cube refined k times")
     args = ap.parse_args()
+    if args.mlhp_k is not None:
+        return run_mlhp(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

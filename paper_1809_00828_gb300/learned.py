@@ -163,3 +163,94 @@ def load(path, seed=0):
     net = fcm.UNet(in_ch, out_ch, base, levels, seed)
     net.set(w)
     return net, gamma
+
+
+def train_cubes(net, seeds, n=32, p=2, count=40, group=8, steps_per_group=100, batch=4, lr=1e-3,
+                snapshots=SNAPSHOTS, log=print):
+    """Train on many seeded porous cubes, `group` cubes at a time: their snapshots are generated (one
+    FP64 Schwarz-PCG per cube), the network takes `steps_per_group` Adam steps on them, and the group's
+    contexts are released before the next group.  gamma is the median RMS(R e) / RMS(R r) of the first
+    group.  Returns (gamma, loss history)."""
+    gamma = None
+    history = []
+    seeds = list(seeds)
+    for g0 in range(0, len(seeds), group):
+        ws = training_workloads(seeds[g0:g0 + group], n=n, p=p, count=count)
+        samples, solvers, g = generate(ws, snapshots, log=None)
+        if gamma is None:
+            gamma = g
+        history += train(net, samples, gamma, steps=steps_per_group, batch=batch, lr=lr, seed=g0, log=None)
+        for s in solvers:
+            s.close()
+        if log:
+            log(f"  cubes {g0}..{g0 + len(ws) - 1}: {len(samples)} pairs, mean loss {np.mean(history[-steps_per_group:]):.4f}")
+    return gamma, history
+
+
+def solve_gain(net, gamma, workload, coarse_iters, tol=None, maxit=20000):
+    """Flexible PCG on `workload` with the network's start and without it (zero start), the same coarse
+    steps: (iterations with, iterations without, seconds with, seconds without)."""
+    s = fcm.Solver(workload)
+    s.set_k_precision("double_float")
+    s.precond_build(precision="mixed")
+    b = s.rhs()
+    tol = tol or workload.tol
+    out = []
+    for nn in (net, None):
+        if nn is None and coarse_iters == 0:
+            _, its, _, _ = s.pcg_solve(b, tol, maxit)
+        else:
+            _, its, _, _ = s.fpcg_solve(nn, gamma if nn is not None else 0.0, b, tol, maxit, coarse_iters=coarse_iters)
+        out.append((its, s.last_solve()["seconds"]))
+    s.close()
+    return out[0][0], out[1][0], out[0][1], out[1][1]
+
+
+def main(argv=None):
+    """python -m paper_1809_00828_gb300.learned train|gain ...
+
+    train: the configured training set (seeded 32^3, p = 2 porous cubes with 40 voids; seeds 1000..1199 by
+    default), a 4-level U-Net (channels 16/32/64/64), checkpoint to --out.
+    gain: flexible PCG on a held-out workload with the checkpoint's start and without it.
+    """
+    import argparse
+    ap = argparse.ArgumentParser(prog="python -m paper_1809_00828_gb300.learned")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--seeds", default="1000-1199", help="first-last seed of the training cubes")
+    t.add_argument("--n", type=int, default=32)
+    t.add_argument("--p", type=int, default=2)
+    t.add_argument("--count", type=int, default=40)
+    t.add_argument("--group", type=int, default=8)
+    t.add_argument("--steps-per-group", type=int, default=100)
+    t.add_argument("--batch", type=int, default=4)
+    t.add_argument("--lr", type=float, default=1e-3)
+    t.add_argument("--base", type=int, default=16)
+    t.add_argument("--levels", type=int, default=4)
+    t.add_argument("--out", required=True)
+    g = sub.add_parser("gain")
+    g.add_argument("--net", required=True)
+    g.add_argument("--workload", default="porous300_80_p2")
+    g.add_argument("--coarse-iters", type=int, default=10)
+    a = ap.parse_args(argv)
+    if a.cmd == "train":
+        lo, hi = (int(v) for v in a.seeds.split("-"))
+        net = fcm.UNet(in_ch=4, out_ch=3, base=a.base, levels=a.levels, seed=0)
+        t0 = time.perf_counter()
+        gamma, hist = train_cubes(net, range(lo, hi + 1), n=a.n, p=a.p, count=a.count, group=a.group,
+                                  steps_per_group=a.steps_per_group, batch=a.batch, lr=a.lr)
+        save(a.out, net, gamma)
+        print(f"trained on seeds {lo}..{hi} in {time.perf_counter() - t0:.0f} s, gamma {gamma:.4f}, "
+              f"final mean loss {np.mean(hist[-a.steps_per_group:]):.4f} -> {a.out}")
+        net.close()
+    else:
+        net, gamma = load(a.net)
+        w = inputs.WORKLOADS[a.workload]()
+        iw, io, sw, so = solve_gain(net, gamma, w, a.coarse_iters)
+        print(f"{w.name}, {a.coarse_iters} coarse steps: with the network {iw} iterations {sw:.3f} s, "
+              f"without {io} iterations {so:.3f} s")
+        net.close()
+
+
+if __name__ == "__main__":
+    main()
