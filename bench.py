@@ -7,8 +7,11 @@ configuration that fits one GPU), with the set-up, the preconditioner and the
 coarse operator built once beforehand.  Forms:
 
   coarse (default): flexible CG, z = S r + P y with y from `--coarse-iters`
-                    coarse CG steps on K_H = P^T K P (optionally started from a
-                    trained U-Net, `--net`), FP32 block factors (`--precision`)
+                    coarse CG steps on K_H = P^T K P, preconditioned by block
+                    Jacobi or by a V-cycle of the cell-grid multigrid hierarchy
+                    (`--coarse-prec`; both defaults per workload), optionally
+                    started from a trained U-Net (`--net`); FP32 / double-float
+                    block factors (`--precision`)
   pcg:              plain Schwarz-PCG
 
 The same run also times plain FP64 Schwarz-PCG and reports the energy-norm
@@ -16,7 +19,8 @@ error of this form against it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcm|reference]
                   [--workload NAME] [--form coarse|pcg] [--precision fp64|mixed]
-                  [--coarse-iters K] [--net CHECKPOINT] [--loads traction|strain6]
+                  [--coarse-iters K] [--coarse-prec jacobi|vcycle] [--net CHECKPOINT]
+                  [--loads traction|strain6] [--mlhp-k K]
                   [--blocks vertex|element] [--eta-bar X]
 
 N > 1 runs independent replicas (one per GPU, launched by torchrun); the
@@ -58,6 +62,13 @@ N_SM = 152
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "schwarz_apply_traffic_porous300_80_p2.md")
+
+# Coarse CG of the flexible PCG per workload (preconditioner, steps), the fastest measured: while K_H fits
+# the 129 MB L2 (32^3 cells: 74 MB) block-Jacobi steps are cheap and 20 of them solve the coarse grid
+# well; at 80^3 cells K_H (1.16 GB) streams from HBM and two V-cycle-preconditioned steps win (3.2 s
+# against 6.4 s for 10 block-Jacobi steps, which stall into the plain-PCG fallback).
+COARSE_DEFAULTS = {"porous40_32_p3": ("jacobi", 20), "porous40_32_p2": ("jacobi", 20),
+                   "porous300_80_p2": ("vcycle", 2)}
 
 
 def _schwarz_traffic(workload_name, precision):
@@ -304,11 +315,14 @@ def _form(args, net):
     if args.form == "pcg":
         return "plain Schwarz-PCG"
     start = "trained U-Net prediction scaled by the coarse line search" if net is not None else "zero"
-    return (f"flexible CG(4), z = S r + P y, y from {args.coarse_iters} block-Jacobi CG steps on the Galerkin "
+    prec = ("block-Jacobi" if args.coarse_prec == "jacobi" else
+            "V-cycle-preconditioned (cell-grid multigrid, Galerkin levels, damped block-Jacobi smoothing, dense "
+            "coarsest level)")
+    return (f"flexible CG(4), z = S r + P y, y from {args.coarse_iters} {prec} CG steps on the Galerkin "
             f"coarse operator K_H = P^T K P starting from {start}")
 
 
-def _launches_per_solve(args, info, its, flex_its, net):
+def _launches_per_solve(args, info, its, flex_its, net, mg_levels=0):
     """Kernels of one solve (device-side loop, so the count follows the iterations): K and S applies
     from the library's own counts, plus the CG vector kernels, the coarse solve and the network."""
     k_apply, s_apply = info["k_apply_launches"], info["s_apply_launches"]
@@ -318,6 +332,9 @@ def _launches_per_solve(args, info, its, flex_its, net):
         return start + its * plain
     k = args.coarse_iters
     coarse = 1 + (1 + 2 * k) + 1                        # restrict, coarse start + 2 per step, prolong
+    if args.coarse_prec == "vcycle" and k > 0:
+        # a V-cycle (5 launches per level above the last, 1 for the last) and r.z, once per step
+        coarse += k * (5 * (mg_levels - 1) + 1 + 1)
     if net is not None:
         coarse += 2 + 1 + 2 + _unet_launches(net)       # sigma, prep, post, start apply + line search
     flex = k_apply + 2 + s_apply + 1 + coarse + 2       # pq, xr, conv, dots, newp
@@ -365,6 +382,7 @@ def run_fcm(args, rank, world, local_rank):
     net, gamma = None, 0.0
     if args.form == "coarse":
         s.set_stall_window(args.stall_window)
+        s.set_coarse_preconditioner(args.coarse_prec)
     if args.form == "coarse" and args.net:
         from paper_1809_00828_gb300 import learned
         net, gamma = learned.load(args.net)
@@ -534,7 +552,9 @@ def run_fcm(args, rank, world, local_rank):
 
     its_med = int(statistics.median(iters))
     flex_its = last["flexible_iterations"] if args.form == "coarse" else 0
-    launches_per_solve = _launches_per_solve(args, info, its_med, flex_its, net) * (nrhs if args.form == "coarse" else 1)
+    mg = s.coarse_levels() if args.form == "coarse" else {"levels": 0, "dims": [], "seconds": 0.0}
+    launches_per_solve = (_launches_per_solve(args, info, its_med, flex_its, net, mg["levels"]) *
+                          (nrhs if args.form == "coarse" else 1))
     line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
@@ -554,6 +574,8 @@ def run_fcm(args, rank, world, local_rank):
                                           "autotune_ms": [round(t * 1e3, 4) for t in info["tune_seconds"] if t > 0]},
                        "setup_s": info["setup_seconds"], "precond_s": info["precond_seconds"],
                        "coarse_operator_s": info["coarse_seconds"],
+                       "coarse_multigrid": ({"levels": mg["dims"], "build_s": mg["seconds"]}
+                                            if mg["levels"] else None),
                        "load_cases": cases},
             "roofline": roofline,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs},
@@ -682,7 +704,11 @@ def main():
                          "compared with plain FP64 in the same run")
     ap.add_argument("--form", default="coarse", choices=["coarse", "pcg"],
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
-    ap.add_argument("--coarse-iters", type=int, default=10)
+    ap.add_argument("--coarse-iters", type=int, default=None,
+                    help="coarse CG steps per preconditioner apply (default: per workload, COARSE_DEFAULTS)")
+    ap.add_argument("--coarse-prec", default=None, choices=["jacobi", "vcycle"],
+                    help="preconditioner of the coarse CG: 3x3 diagonal blocks of K_H, or one V-cycle of the "
+                         "cell-grid multigrid hierarchy (default: per workload, COARSE_DEFAULTS)")
     ap.add_argument("--k-precision", default="double_float", choices=["double_float", "fp64"],
                     help="arithmetic of K x in the forms with FP32 factors (plain FP64 always uses FP64 K)")
     ap.add_argument("--stall-window", type=int, default=100,
@@ -709,6 +735,9 @@ def main():
     ap.add_argument("--mlhp-k", type=int, default=None,
                     help="instead of the bench line: time the multi-level hp path on the Sec. 5.1 cube refined k times")
     args = ap.parse_args()
+    prec, iters = COARSE_DEFAULTS.get(args.workload, ("vcycle", 2))
+    args.coarse_prec = args.coarse_prec or prec
+    args.coarse_iters = iters if args.coarse_iters is None else args.coarse_iters
     if args.mlhp_k is not None:
         return run_mlhp(args)
     rank = int(os.environ.get("RANK", "0"))

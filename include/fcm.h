@@ -347,6 +347,35 @@ fcm_status fcm_fpcg_solve(fcm_ctx *ctx, fcm_unet *net, double gamma, int coarse_
  * use through plateaus.  Returns FCM_EINVAL for window < 1. */
 fcm_status fcm_fpcg_set_stall_window(fcm_ctx *ctx, int window);
 
+/* Preconditioner of the coarse CG inside fcm_fpcg_solve.
+ *   FCM_COARSE_JACOBI (the default): the inverses of the 3x3 diagonal blocks of K_H.
+ *   FCM_COARSE_VCYCLE: one V-cycle of a geometric multigrid hierarchy on the cell grid.  Level l+1
+ *     halves the cells of level l along every axis with more than one cell (n' = (n + 1) / 2); the
+ *     interpolation P2 is cell-centred trilinear (3/4 from the coarse cell containing the fine one,
+ *     1/4 from its neighbour on the fine cell's side, all of it at the boundary); K_{l+1} =
+ *     P2^T K_l P2, assembled on the device by probing like K_H; one block-Jacobi step damped by
+ *     4 / (3.3 lambda_max(D^-1 K_l)) before and one after the coarse correction; the coarsest level
+ *     (at most 512 cells) by its dense pseudo-inverse (eigenvalues below 1e-12 of the largest
+ *     dropped).  The cycle is a fixed symmetric linear operator, so the coarse CG stays a
+ *     preconditioned CG.  Not part of the paper's method: a coarse space for its Sec. 6 limitation.
+ * The hierarchy is built on the first coarse solve after the choice (FCM_ENOMEM if it does not fit).
+ * Changing the choice drops the flexible CG's captured graph.  FCM_EINVAL for another kind. */
+#define FCM_COARSE_JACOBI 0
+#define FCM_COARSE_VCYCLE 1
+fcm_status fcm_coarse_set_preconditioner(fcm_ctx *ctx, int kind);
+
+/* The multigrid hierarchy after it is built: *levels (0 before), the cell grid of each level in
+ * dims[3 * l + axis] (room for 3 * 12 ints, may be null), the smoother's lambda_max estimate per
+ * level but the last in lambdas (room for 12, may be null) and the build time in *seconds (may be
+ * null). */
+fcm_status fcm_coarse_levels(fcm_ctx *ctx, int *levels, int *dims, double *lambdas, double *seconds);
+
+/* x_cells_dev = one V-cycle of that hierarchy applied to f_cells_dev (cell vectors, 3 * n_cells floats,
+ * component-major, distinct device buffers), whatever the coarse preconditioner in use; builds K_H
+ * and the hierarchy if needed.  Ordered on the caller's stream like fcm_coarse_apply.  A fixed
+ * symmetric linear operator: on a grid of at most 512 cells it is the pseudo-inverse of K_H. */
+fcm_status fcm_coarse_vcycle(fcm_ctx *ctx, const float *f_cells_dev, float *x_cells_dev);
+
 /* Same as fcm_fpcg_solve with host buffers: rhs_host (n_lattice doubles) is
  * copied to the device, solved, and the solution copied back into u_host
  * before returning (pinned host memory makes the copies asynchronous DMA). */

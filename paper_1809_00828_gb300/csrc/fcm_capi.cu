@@ -70,9 +70,9 @@ void apply_K_dev(fcm_ctx *C, const double *x, double *y, const int *done)
 {
     fcm::launch_zero(y, C->nlat, done, C->stream);
     if (C->k_ff)
-        fcm::launch_k_apply_ff(C->p, C->g, x, y, C->d_mask, C->d_elem_ff, C->kc, done, C->stream);
+        fcm::launch_k_apply_ff(C->p, C->g, x, y, C->d_mask, C->d_elem_ff, C->kc, done, C->stream, C->ks);
     else
-        fcm::launch_k_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->kc, done, C->stream);
+        fcm::launch_k_apply(C->p, C->g, x, y, C->d_mask, C->d_elem, C->kc, done, C->stream, C->ks);
 }
 
 void apply_S_dev(fcm_ctx *C, const double *r, double *z, const int *done)
@@ -190,10 +190,12 @@ void free_ctx(fcm_ctx *C)
     if (C->h_ms) cudaFreeHost(C->h_ms);
     fcm::fcg_free(C->fcg);
     fcm::coarse_free(C->coarse);
-    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1, C->ev_f0, C->ev_f1, C->ev_fork, C->ev_join};
+    cudaEvent_t evs[] = {C->ev_in, C->ev_out, C->ev_t0, C->ev_t1, C->ev_f0, C->ev_f1, C->ev_fork, C->ev_join,
+                         C->ks.fork, C->ks.join};
     for (auto e : evs)
         if (e) cudaEventDestroy(e);
     if (C->side) cudaStreamDestroy(C->side);
+    if (C->ks.side) cudaStreamDestroy(C->ks.side);
     if (C->stream) cudaStreamDestroy(C->stream);
     delete C;
 }
@@ -270,6 +272,9 @@ fcm_status fcm_setup(const fcm_grid *grid, const fcm_geometry *geom, int p, doub
     SETUP_CUDA(cudaEventCreate(&C->ev_t1));
     SETUP_CUDA(cudaEventCreate(&C->ev_f0));
     SETUP_CUDA(cudaEventCreate(&C->ev_f1));
+    SETUP_CUDA(cudaStreamCreateWithFlags(&C->ks.side, cudaStreamNonBlocking));
+    SETUP_CUDA(cudaEventCreateWithFlags(&C->ks.fork, cudaEventDisableTiming));
+    SETUP_CUDA(cudaEventCreateWithFlags(&C->ks.join, cudaEventDisableTiming));
     const size_t ne2 = (size_t)hp.ne * hp.ne;
     const int64_t nelem = 1 + hp.ncut;
     SETUP_CUDA(dalloc(&C->d_elem, ne2 * nelem));

@@ -101,14 +101,21 @@ struct SchwarzPlan {
     cudaEvent_t ev_fork, ev_join;
 };
 
+// Second stream of the K apply: per colour, the cut cells run on `side` beside the uncut cells on the
+// main stream (the two sets are DOF-disjoint within a colour); null side: one stream.
+struct KStreams {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
 // Launchers (all asynchronous on `s`).  `done` may be null.  The Schwarz launchers overwrite z
 // with S r.  The multi-RHS form takes nr <= 8 vectors nlat apart and a Zb of nr * nslots * zs doubles.
 void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
-                    const KCells &kc, const int *done, cudaStream_t s);
+                    const KCells &kc, const int *done, cudaStream_t s, const KStreams &ks);
 // the same in double-float arithmetic on the FP32 pipe (fcm_kapply_ff.cu); elem: the element matrices as
 // float pairs
 void launch_k_apply_ff(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const float2 *elem,
-                       const KCells &kc, const int *done, cudaStream_t s);
+                       const KCells &kc, const int *done, cudaStream_t s, const KStreams &ks);
 void launch_to_ff_pairs(const double *in, float2 *out, int64_t n, cudaStream_t s);
 void launch_schwarz_apply(int p, const Grid3 &g, const double *r, double *z, const double *fpool64,
                           const float *fpool32, const SchwarzPlan &plan, const int *done, cudaStream_t s);
@@ -220,6 +227,7 @@ struct fcm_ctx {
     double *d_zb = nullptr;          // block products of one S apply
     cudaStream_t side = nullptr;     // second stream of the Schwarz apply (shared-factor products)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    fcm::KStreams ks{};              // second stream of the K apply (cut cells beside uncut ones)
     int64_t n_ff_factors = 0;        // factors stored as double-float pairs
     int64_t n_gemm_blocks = 0;       // blocks applied by the shared-factor GEMM
     double *d_jac = nullptr;         // diagonal part of S (element blocks), lattice; null if none
@@ -257,5 +265,6 @@ struct fcm_ctx {
     int m_nr = 0;
     // coarse operator of the learned correction (built on first use)
     fcm::CoarseOp *coarse = nullptr;
+    int coarse_prec = FCM_COARSE_JACOBI;  // fcm_coarse_set_preconditioner
     fcm::FcgState *fcg = nullptr;
 };

@@ -20,6 +20,17 @@ namespace {
 __host__ __device__ constexpr int rnd32k(int v) { return (v + 31) / 32 * 32; }
 __host__ __device__ constexpr int ebe_threads(int rows) { return rnd32k(rows) < 512 ? rnd32k(rows) : 512; }
 
+// Barrier among the threads of one cell: a warp when the cell's points fit one warp (p <= 2), else
+// the CTA.  Only the table load at the start needs the whole CTA.
+template <int TPC>
+__device__ __forceinline__ void cell_sync()
+{
+    if constexpr (TPC == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // S + C += sum over k < n of a_k b_k for double-float operands
 struct FFAcc {
     float S = 0.f, C = 0.f;
@@ -98,14 +109,14 @@ __global__ void __launch_bounds__(256)
             for (int k = 0; k < Q; ++k) s.add(sB[tx][k], U[lc][c][k + Q * (ty + Q * tz)]);
             A[lc][t] = s.get();
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {
             FFAcc s;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s.add(sB[ty][k], A[lc][tx + Q * (k + Q * tz)]);
             Bq[lc][t] = s.get();
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {
             FFAcc s;
 #pragma unroll
@@ -113,10 +124,10 @@ __global__ void __launch_bounds__(256)
             uq[c] = s.get();
         }
     }
-    __syncthreads();  // every point has read the nodal values of its cell
+    cell_sync<TPC>();  // every point has read the nodal values of its cell
     if (on)
         for (int c = 0; c < 3; ++c) U[lc][c][t] = uq[c];
-    __syncthreads();
+    cell_sync<TPC>();
     // gradients at the point by the collocation derivative along each axis
     float2 gr[3][3];
     if (on) {
@@ -147,10 +158,10 @@ __global__ void __launch_bounds__(256)
     }
     float2 out[3];
     for (int c = 0; c < 3; ++c) {
-        __syncthreads();  // the previous readers of U and A are done
+        cell_sync<TPC>();  // the previous readers of U and A are done
         if (on)
             for (int j = 0; j < 3; ++j) U[lc][j][t] = F[c][j];
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // transposed collocation derivative: point values of component c's force
             FFAcc v;
 #pragma unroll
@@ -161,21 +172,21 @@ __global__ void __launch_bounds__(256)
             }
             A[lc][t] = v.get();
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // z^T: (qx, qy, iz)
             FFAcc s;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s.add(sB[k][tz], A[lc][tx + Q * (ty + Q * k)]);
             Bq[lc][t] = s.get();
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // y^T: (qx, iy, iz)
             FFAcc s;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s.add(sB[k][ty], Bq[lc][tx + Q * (k + Q * tz)]);
             A[lc][t] = s.get();
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // x^T: nodal force (ix, iy, iz)
             FFAcc s;
 #pragma unroll
@@ -190,18 +201,30 @@ __global__ void __launch_bounds__(256)
 
 template <int P>
 void k_launch_ff(const Grid3 &g, const double *x, double *y, const uint8_t *mask, const float2 *elem,
-                 const KCells &kc, const int *done, cudaStream_t s)
+                 const KCells &kc, const int *done, cudaStream_t s, const KStreams &ks)
 {
     constexpr int NE = 3 * (P + 1) * (P + 1) * (P + 1);
     constexpr int CPC = 256 / rnd32k((P + 1) * (P + 1) * (P + 1));
     for (int c = 0; c < 8; ++c) {
         const int nu = kc.uncut_off[c + 1] - kc.uncut_off[c];
+        const int nc = kc.cut_off[c + 1] - kc.cut_off[c];
+        // cut and uncut cells of one colour share no DOF: the cut cells (HBM-bound) run beside the uncut
+        // ones (FP32-pipe and latency bound)
+        const bool fork = ks.side && nu > 0 && nc > 0;
+        if (fork) {
+            cudaEventRecord(ks.fork, s);
+            cudaStreamWaitEvent(ks.side, ks.fork, 0);
+        }
+        if (nc > 0)
+            ebe_apply_ff_kernel<P><<<nc, ebe_threads(NE), 0, fork ? ks.side : s>>>(x, y, mask, elem,
+                                                                                  kc.cut + kc.cut_off[c], g, done);
         if (nu > 0)
             sf_apply_ff_kernel<P><<<(nu + CPC - 1) / CPC, 256, 0, s>>>(x, y, mask, kc.uncut + kc.uncut_off[c], nu, g,
                                                                       kc.sff, done);
-        const int nc = kc.cut_off[c + 1] - kc.cut_off[c];
-        if (nc > 0)
-            ebe_apply_ff_kernel<P><<<nc, ebe_threads(NE), 0, s>>>(x, y, mask, elem, kc.cut + kc.cut_off[c], g, done);
+        if (fork) {
+            cudaEventRecord(ks.join, ks.side);
+            cudaStreamWaitEvent(s, ks.join, 0);
+        }
     }
 }
 
@@ -215,13 +238,13 @@ __global__ void to_ff_pairs_kernel(const double *__restrict__ in, float2 *__rest
 }  // namespace
 
 void launch_k_apply_ff(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const float2 *elem,
-                       const KCells &kc, const int *done, cudaStream_t s)
+                       const KCells &kc, const int *done, cudaStream_t s, const KStreams &ks)
 {
     switch (p) {
-    case 1: k_launch_ff<1>(g, x, y, mask, elem, kc, done, s); break;
-    case 2: k_launch_ff<2>(g, x, y, mask, elem, kc, done, s); break;
-    case 3: k_launch_ff<3>(g, x, y, mask, elem, kc, done, s); break;
-    case 4: k_launch_ff<4>(g, x, y, mask, elem, kc, done, s); break;
+    case 1: k_launch_ff<1>(g, x, y, mask, elem, kc, done, s, ks); break;
+    case 2: k_launch_ff<2>(g, x, y, mask, elem, kc, done, s, ks); break;
+    case 3: k_launch_ff<3>(g, x, y, mask, elem, kc, done, s, ks); break;
+    case 4: k_launch_ff<4>(g, x, y, mask, elem, kc, done, s, ks); break;
     default: break;
     }
 }

@@ -46,6 +46,17 @@ __global__ void __launch_bounds__(threads_for(3 * (P + 1) * (P + 1) * (P + 1)))
     }
 }
 
+// Barrier among the threads of one cell: a warp when the cell's points fit one warp (p <= 2), else
+// the CTA.  Only the table load at the start needs the whole CTA.
+template <int TPC>
+__device__ __forceinline__ void cell_sync()
+{
+    if constexpr (TPC == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // y += K_ref x_e for uncut cells of one colour, without the matrix.  Each displacement
 // component is interpolated to the (p+1)^3 Gauss points by one-dimensional contractions along
 // x, y, z (sum factorisation); its gradient there follows from the collocation derivative on
@@ -91,14 +102,14 @@ __global__ void __launch_bounds__(256)
             for (int k = 0; k < Q; ++k) s0 = fma(sB[tx][k], U[lc][c][k + Q * (ty + Q * tz)], s0);
             A[lc][t] = s0;
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {
             double s1 = 0.0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s1 = fma(sB[ty][k], A[lc][tx + Q * (k + Q * tz)], s1);
             Bq[lc][t] = s1;
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {
             double s2 = 0.0;
 #pragma unroll
@@ -106,10 +117,10 @@ __global__ void __launch_bounds__(256)
             uq[c] = s2;
         }
     }
-    __syncthreads();  // every point has read the nodal values of its cell
+    cell_sync<TPC>();  // every point has read the nodal values of its cell
     if (on)
         for (int c = 0; c < 3; ++c) U[lc][c][t] = uq[c];
-    __syncthreads();
+    cell_sync<TPC>();
     // gradients at the point by the collocation derivative along each axis
     double gr[3][3];
     if (on) {
@@ -136,10 +147,10 @@ __global__ void __launch_bounds__(256)
     }
     double out[3];
     for (int c = 0; c < 3; ++c) {
-        __syncthreads();  // the previous readers of U and A are done
+        cell_sync<TPC>();  // the previous readers of U and A are done
         if (on)
             for (int j = 0; j < 3; ++j) U[lc][j][t] = F[c][j];
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // transposed collocation derivative: point values of component c's force
             double v = 0.0;
 #pragma unroll
@@ -150,21 +161,21 @@ __global__ void __launch_bounds__(256)
             }
             A[lc][t] = v;
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // z^T: (qx, qy, iz)
             double s2 = 0.0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s2 = fma(sB[k][tz], A[lc][tx + Q * (ty + Q * k)], s2);
             Bq[lc][t] = s2;
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // y^T: (qx, iy, iz)
             double s1 = 0.0;
 #pragma unroll
             for (int k = 0; k < Q; ++k) s1 = fma(sB[k][ty], Bq[lc][tx + Q * (k + Q * tz)], s1);
             A[lc][t] = s1;
         }
-        __syncthreads();
+        cell_sync<TPC>();
         if (on) {  // x^T: nodal force (ix, iy, iz)
             double o = 0.0;
 #pragma unroll
@@ -193,17 +204,29 @@ __global__ void zero_kernel(double *__restrict__ v, int64_t n, const int *__rest
 
 template <int P>
 void k_launch(const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem, const KCells &kc,
-              const int *done, cudaStream_t s)
+              const int *done, cudaStream_t s, const KStreams &ks)
 {
     constexpr int NE = 3 * (P + 1) * (P + 1) * (P + 1);
     constexpr int CPC = 256 / round32((P + 1) * (P + 1) * (P + 1));
     for (int c = 0; c < 8; ++c) {
         const int nu = kc.uncut_off[c + 1] - kc.uncut_off[c];
+        const int nc = kc.cut_off[c + 1] - kc.cut_off[c];
+        // cut and uncut cells of one colour share no DOF: the cut cells may run beside the uncut ones
+        const bool fork = ks.side && nu > 0 && nc > 0;
+        if (fork) {
+            cudaEventRecord(ks.fork, s);
+            cudaStreamWaitEvent(ks.side, ks.fork, 0);
+        }
+        if (nc > 0)
+            ebe_apply_kernel<P><<<nc, threads_for(NE), 0, fork ? ks.side : s>>>(x, y, mask, elem, kc.cut + kc.cut_off[c],
+                                                                               g, done);
         if (nu > 0)
             sf_apply_kernel<P><<<(nu + CPC - 1) / CPC, 256, 0, s>>>(x, y, mask, kc.uncut + kc.uncut_off[c], nu, g, kc.sf,
                                                                    done);
-        const int nc = kc.cut_off[c + 1] - kc.cut_off[c];
-        if (nc > 0) ebe_apply_kernel<P><<<nc, threads_for(NE), 0, s>>>(x, y, mask, elem, kc.cut + kc.cut_off[c], g, done);
+        if (fork) {
+            cudaEventRecord(ks.join, ks.side);
+            cudaStreamWaitEvent(s, ks.join, 0);
+        }
     }
 }
 
@@ -217,13 +240,13 @@ int grid_for(int64_t n, int threads)
 }  // namespace
 
 void launch_k_apply(int p, const Grid3 &g, const double *x, double *y, const uint8_t *mask, const double *elem,
-                    const KCells &kc, const int *done, cudaStream_t s)
+                    const KCells &kc, const int *done, cudaStream_t s, const KStreams &ks)
 {
     switch (p) {
-    case 1: k_launch<1>(g, x, y, mask, elem, kc, done, s); break;
-    case 2: k_launch<2>(g, x, y, mask, elem, kc, done, s); break;
-    case 3: k_launch<3>(g, x, y, mask, elem, kc, done, s); break;
-    case 4: k_launch<4>(g, x, y, mask, elem, kc, done, s); break;
+    case 1: k_launch<1>(g, x, y, mask, elem, kc, done, s, ks); break;
+    case 2: k_launch<2>(g, x, y, mask, elem, kc, done, s, ks); break;
+    case 3: k_launch<3>(g, x, y, mask, elem, kc, done, s, ks); break;
+    case 4: k_launch<4>(g, x, y, mask, elem, kc, done, s, ks); break;
     default: break;
     }
 }

@@ -3,26 +3,29 @@
 // The host plan assembles K over the free DOFs (CSR) and the Schwarz factors of the leaf blocks
 // (fcm_mlhp.cpp); this file uploads them and runs:
 //   - K x: one warp per CSR row;
-//   - S r (Eq. (5)): z = D r for the DOFs in no block, then one launch per colour, each block's rows split
-//     over a few CTAs: gather r_B into shared memory, z_B += A_B^+ r_B with a warp per row, scatter (the
-//     blocks of one colour share no DOF, so no atomics);
-//   - PCG with x0 = 0, stopped on ||S r_i|| / ||S b|| <= tol (Eq. (14)): the dot products are two-level
-//     reductions in a fixed order (deterministic), the scalars go to the host each iteration.
+//   - S r (Eq. (5)) in two launches, as on the uniform grid: every block's product Zb = A_B^+ r_B goes
+//     into a slot of its own (one CTA per 32 rows of a block: gather r_B into shared memory, a warp per
+//     row reading the factor row coalesced), then one thread per DOF adds the diagonal part and the
+//     slots of the blocks containing it, in block order (no colours, no atomics, a fixed order);
+//   - PCG with x0 = 0, stopped on ||S r_i|| / ||S b|| <= tol (Eq. (14)), with the uniform grid's fused
+//     CG kernels: every scalar stays on the device (deterministic two-level reductions), eight
+//     iterations are captured in one CUDA graph, and the host polls the scalars once per graph.
 // Every index the kernels use is checked on the host before the upload.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <cstring>
 #include <string>
 #include <vector>
 
-#include "fcm_internal.h"
+#include "fcm_device.cuh"
 
 namespace fcm {
 
 namespace {
 
-constexpr int kDotGrid = 304;  // 2 CTAs per SM of a 152-SM GB300
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -35,8 +38,10 @@ __device__ __forceinline__ double warp_sum(double v)
 __global__ void __launch_bounds__(kThreads) mlhp_spmv_kernel(int n, const int64_t *__restrict__ rowptr,
                                                              const int *__restrict__ cols,
                                                              const double *__restrict__ vals,
-                                                             const double *__restrict__ x, double *__restrict__ y)
+                                                             const double *__restrict__ x, double *__restrict__ y,
+                                                             const int *done)
 {
+    if (done && *done) return;
     const int row = (int)((blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;  // uniform across the warp
@@ -46,83 +51,48 @@ __global__ void __launch_bounds__(kThreads) mlhp_spmv_kernel(int n, const int64_
     if (lane == 0) y[row] = s;
 }
 
-__global__ void __launch_bounds__(kThreads) mlhp_diag_kernel(int n, const double *__restrict__ jac,
-                                                             const double *__restrict__ r, double *__restrict__ z)
-{
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) z[i] = jac[i] * r[i];
-}
-
-// z_B += A_B^+ r_B for the blocks of one colour.  A block's rows are split over `splits` CTAs of
-// kRowsPerCta rows (more CTAs in flight than blocks in a colour); every CTA gathers r_B into shared memory,
-// then each warp takes one row at a time and reads it coalesced, lanes striding over the columns.
+// Zb[o_B + i] = (A_B^+ r_B)_i for the rows i of item (block, first row): a CTA per 32 rows of a block.
 constexpr int kRowsPerCta = 32;
 
-__global__ void __launch_bounds__(kThreads) mlhp_block_kernel(int64_t first, int splits, const int64_t *__restrict__ bptr,
-                                                              const int *__restrict__ bdofs,
-                                                              const int64_t *__restrict__ fptr,
-                                                              const double *__restrict__ fac,
-                                                              const double *__restrict__ r, double *__restrict__ z)
+__global__ void __launch_bounds__(kThreads) mlhp_block_rows_kernel(const int2 *__restrict__ items,
+                                                                   const int64_t *__restrict__ bptr,
+                                                                   const int *__restrict__ bdofs,
+                                                                   const int64_t *__restrict__ fptr,
+                                                                   const double *__restrict__ fac,
+                                                                   const double *__restrict__ r,
+                                                                   double *__restrict__ zb, const int *done)
 {
+    if (done && *done) return;
     extern __shared__ double rb[];
-    const int64_t b = first + blockIdx.x / splits;
-    const int row0 = (int)(blockIdx.x % splits) * kRowsPerCta;
-    const int64_t o = bptr[b];
-    const int m = (int)(bptr[b + 1] - o);
-    if (row0 >= m) return;  // uniform across the CTA, before any barrier
-    const double *F = fac + fptr[b];
+    const int2 it = items[blockIdx.x];
+    const int64_t o = bptr[it.x];
+    const int m = (int)(bptr[it.x + 1] - o);
+    const double *F = fac + fptr[it.x];
     for (int j = threadIdx.x; j < m; j += kThreads) rb[j] = r[bdofs[o + j]];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row_end = min(m, row0 + kRowsPerCta);
-    for (int i = row0 + warp; i < row_end; i += kThreads / 32) {  // warp-uniform bounds
+    const int row_end = min(m, it.y + kRowsPerCta);
+    for (int i = it.y + warp; i < row_end; i += kThreads / 32) {  // warp-uniform bounds
         const double *Fi = F + (int64_t)i * m;
         double s = 0.0;
         for (int j = lane; j < m; j += 32) s += Fi[j] * rb[j];
         s = warp_sum(s);
-        if (lane == 0) z[bdofs[o + i]] += s;
+        if (lane == 0) zb[o + i] = s;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) mlhp_dot_partial_kernel(int n, const double *__restrict__ a,
-                                                                    const double *__restrict__ b,
-                                                                    double *__restrict__ partial)
+// z_d = jac_d r_d + sum of the slots of the blocks containing d, in block order
+__global__ void __launch_bounds__(kThreads) mlhp_sum_kernel(int n, const int64_t *__restrict__ occ_ptr,
+                                                            const int *__restrict__ occ, const double *__restrict__ zb,
+                                                            const double *__restrict__ jac, const double *__restrict__ r,
+                                                            double *__restrict__ z, const int *done)
 {
-    __shared__ double sh[kThreads / 32];
-    double s = 0.0;
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) s += a[i] * b[i];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        s = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
-        s = warp_sum(s);
-        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (done && *done) return;
+    for (int d = blockIdx.x * kThreads + threadIdx.x; d < n; d += gridDim.x * kThreads) {
+        double s = jac[d] * r[d];
+        for (int64_t k = occ_ptr[d]; k < occ_ptr[d + 1]; ++k) s += zb[occ[k]];
+        z[d] = s;
     }
-}
-
-__global__ void mlhp_dot_final_kernel(int g, const double *__restrict__ partial, double *__restrict__ out)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < g; ++i) s += partial[i];
-        *out = s;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) mlhp_xr_kernel(int n, double a, const double *__restrict__ p,
-                                                           const double *__restrict__ q, double *__restrict__ x,
-                                                           double *__restrict__ r)
-{
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-        x[i] += a * p[i];
-        r[i] -= a * q[i];
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) mlhp_p_kernel(int n, double beta, const double *__restrict__ z,
-                                                          double *__restrict__ p)
-{
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) p[i] = z[i] + beta * p[i];
 }
 
 template <class T>
@@ -136,24 +106,38 @@ cudaError_t upload(T **d, const T *h, size_t count, cudaStream_t st)
 
 }  // namespace
 
+constexpr int kChunk = 8;  // PCG iterations per captured graph
+
 struct MlhpDevice {
-    cudaStream_t st = nullptr;
-    int n = 0, ncolours = 0, max_block = 0;
-    std::vector<int64_t> colour_ptr;
-    int64_t *rowptr = nullptr, *bptr = nullptr, *fptr = nullptr;
-    int *cols = nullptr, *bdofs = nullptr;
-    double *vals = nullptr, *fac = nullptr, *jac = nullptr;
-    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *partial = nullptr, *scalar = nullptr;
-    int grid_n = 1;
+    cudaStream_t st = nullptr;    // the caller's stream (applies; the solve is ordered after it)
+    cudaStream_t own = nullptr;   // the solve's stream (capturable)
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    int n = 0, max_block = 0, nitems = 0;
+    int64_t nslots = 0;
+    int64_t *rowptr = nullptr, *bptr = nullptr, *fptr = nullptr, *occ_ptr = nullptr;
+    int *cols = nullptr, *bdofs = nullptr, *occ = nullptr;
+    int2 *items = nullptr;
+    double *vals = nullptr, *fac = nullptr, *jac = nullptr, *zb = nullptr;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *partial = nullptr;
+    unsigned *counter = nullptr;
+    CgScalars *s = nullptr, *hs = nullptr;  // device scalars, pinned host copy
+    int grid_n = 1, red_blocks = 1;
+    cudaGraphExec_t graph = nullptr;
 };
 
 void mlhp_device_destroy(MlhpDevice *d)
 {
     if (!d) return;
-    for (void *ptr : {(void *)d->rowptr, (void *)d->bptr, (void *)d->fptr, (void *)d->cols, (void *)d->bdofs,
-                      (void *)d->vals, (void *)d->fac, (void *)d->jac, (void *)d->x, (void *)d->r, (void *)d->z,
-                      (void *)d->p, (void *)d->q, (void *)d->partial, (void *)d->scalar})
+    if (d->graph) cudaGraphExecDestroy(d->graph);
+    for (void *ptr : {(void *)d->rowptr, (void *)d->bptr, (void *)d->fptr, (void *)d->occ_ptr, (void *)d->cols,
+                      (void *)d->bdofs, (void *)d->occ, (void *)d->items, (void *)d->vals, (void *)d->fac,
+                      (void *)d->jac, (void *)d->zb, (void *)d->x, (void *)d->r, (void *)d->z, (void *)d->p,
+                      (void *)d->q, (void *)d->b, (void *)d->partial, (void *)d->counter, (void *)d->s})
         if (ptr) cudaFree(ptr);
+    if (d->hs) cudaFreeHost(d->hs);
+    if (d->ev_a) cudaEventDestroy(d->ev_a);
+    if (d->ev_b) cudaEventDestroy(d->ev_b);
+    if (d->own) cudaStreamDestroy(d->own);
     delete d;
 }
 
@@ -177,40 +161,47 @@ std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, c
     const int64_t nnz = rowptr[n];
     for (int64_t e = 0; e < nnz; ++e)
         if (cols[e] < 0 || cols[e] >= n) return "CSR column out of range";
-    if (nblocks < 0 || bptr[0] != 0 || fptr[0] != 0) return "bad block pointers";
+    if (nblocks < 0 || nblocks > ((int64_t)1 << 30) || bptr[0] != 0 || fptr[0] != 0) return "bad block pointers";
     int max_block = 0;
     for (int64_t b = 0; b < nblocks; ++b) {
         const int64_t m = bptr[b + 1] - bptr[b];
         if (m < 1 || m > 4096 || fptr[b + 1] - fptr[b] != m * m) return "bad block pointers";
         max_block = std::max(max_block, (int)m);
     }
-    for (int64_t k = 0; k < bptr[nblocks]; ++k)
+    const int64_t nslots = bptr[nblocks];
+    if (nslots >= ((int64_t)1 << 31)) return "too many block rows";
+    for (int64_t k = 0; k < nslots; ++k)
         if (bdofs[k] < 0 || bdofs[k] >= n) return "block DOF out of range";
     if (ncolours < 0 || cptr[0] != 0 || cptr[ncolours] != nblocks) return "bad colour pointers";
     for (int c = 0; c < ncolours; ++c)
         if (cptr[c + 1] < cptr[c]) return "bad colour pointers";
-    {  // blocks of one colour share no DOF
-        std::vector<int> seen(n, -1);
-        for (int c = 0; c < ncolours; ++c)
-            for (int64_t b = cptr[c]; b < cptr[c + 1]; ++b)
-                for (int64_t k = bptr[b]; k < bptr[b + 1]; ++k) {
-                    if (seen[bdofs[k]] == c) return "blocks of one colour share a DOF";
-                    seen[bdofs[k]] = c;
-                }
-    }
+    // work items (block, first row) and, per DOF, its slots in block order
+    std::vector<int2> items;
+    for (int64_t b = 0; b < nblocks; ++b)
+        for (int64_t i = 0; i < bptr[b + 1] - bptr[b]; i += kRowsPerCta) items.push_back(make_int2((int)b, (int)i));
+    std::vector<int64_t> occ_ptr(n + 1, 0);
+    for (int64_t k = 0; k < nslots; ++k) occ_ptr[bdofs[k] + 1] += 1;
+    for (int64_t i = 0; i < n; ++i) occ_ptr[i + 1] += occ_ptr[i];
+    std::vector<int> occ(nslots), fill(occ_ptr.begin(), occ_ptr.end() - 1);
+    for (int64_t k = 0; k < nslots; ++k) occ[fill[bdofs[k]]++] = (int)k;  // k grows with the block index
     MlhpDevice *d = new MlhpDevice;
     d->st = static_cast<cudaStream_t>(stream);
     d->n = (int)n;
-    d->ncolours = ncolours;
     d->max_block = max_block;
-    d->colour_ptr.assign(cptr, cptr + ncolours + 1);
+    d->nitems = (int)items.size();
+    d->nslots = nslots;
     d->grid_n = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 8 * 152);
-    std::vector<int> cols32(cols, cols + nnz), bdofs32(bdofs, bdofs + bptr[nblocks]);
+    d->red_blocks = d->grid_n;
+    std::vector<int> cols32(cols, cols + nnz), bdofs32(bdofs, bdofs + nslots);
     auto fail = [&](const std::string &m) {
         mlhp_device_destroy(d);
         return m;
     };
     cudaError_t e = cudaSuccess;
+    if ((e = cudaStreamCreateWithFlags(&d->own, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&d->ev_a, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&d->ev_b, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
     if ((e = upload(&d->rowptr, rowptr, (size_t)n + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->cols, cols32.data(), cols32.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->vals, vals, (size_t)nnz, d->st)) != cudaSuccess ||
@@ -218,113 +209,144 @@ std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, c
         (e = upload(&d->bdofs, bdofs32.data(), bdofs32.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->fptr, fptr, (size_t)nblocks + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->fac, fac, (size_t)fptr[nblocks], d->st)) != cudaSuccess ||
-        (e = upload(&d->jac, jac, (size_t)n, d->st)) != cudaSuccess)
+        (e = upload(&d->jac, jac, (size_t)n, d->st)) != cudaSuccess ||
+        (e = upload(&d->items, items.data(), items.size(), d->st)) != cudaSuccess ||
+        (e = upload(&d->occ_ptr, occ_ptr.data(), occ_ptr.size(), d->st)) != cudaSuccess ||
+        (e = upload(&d->occ, occ.data(), occ.size(), d->st)) != cudaSuccess)
         return fail(std::string("upload: ") + cudaGetErrorString(e));
-    for (double **v : {&d->x, &d->r, &d->z, &d->p, &d->q})
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&d->zb), std::max<int64_t>(nslots, 1) * sizeof(double))) != cudaSuccess)
+        return fail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    for (double **v : {&d->x, &d->r, &d->z, &d->p, &d->q, &d->b})
         if ((e = cudaMalloc(reinterpret_cast<void **>(v), (size_t)n * sizeof(double))) != cudaSuccess)
             return fail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    if ((e = cudaMalloc(reinterpret_cast<void **>(&d->partial), kDotGrid * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void **>(&d->scalar), sizeof(double))) != cudaSuccess)
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&d->partial), 2 * (size_t)d->red_blocks * sizeof(double))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void **>(&d->counter), sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void **>(&d->s), sizeof(CgScalars))) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void **>(&d->hs), sizeof(CgScalars))) != cudaSuccess)
         return fail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    if ((e = cudaMemsetAsync(d->counter, 0, sizeof(unsigned), d->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d->s, 0, sizeof(CgScalars), d->st)) != cudaSuccess)
+        return fail(std::string("cudaMemset: ") + cudaGetErrorString(e));
     // the host copies above come from pageable memory owned by the caller: finish them before returning
     if ((e = cudaStreamSynchronize(d->st)) != cudaSuccess) return fail(std::string("upload: ") + cudaGetErrorString(e));
     *out = d;
     return std::string();
 }
 
-std::string mlhp_device_apply_K(MlhpDevice *d, const double *x, double *y)
+namespace {
+
+void apply_K(MlhpDevice *d, const double *x, double *y, const int *done, cudaStream_t st)
 {
     const int64_t warps_per_cta = kThreads / 32;
     const unsigned grid = (unsigned)((d->n + warps_per_cta - 1) / warps_per_cta);
-    mlhp_spmv_kernel<<<grid, kThreads, 0, d->st>>>(d->n, d->rowptr, d->cols, d->vals, x, y);
+    mlhp_spmv_kernel<<<grid, kThreads, 0, st>>>(d->n, d->rowptr, d->cols, d->vals, x, y, done);
+}
+
+void apply_S(MlhpDevice *d, const double *r, double *z, const int *done, cudaStream_t st)
+{
+    if (d->nitems > 0)
+        mlhp_block_rows_kernel<<<d->nitems, kThreads, (size_t)d->max_block * sizeof(double), st>>>(
+            d->items, d->bptr, d->bdofs, d->fptr, d->fac, r, d->zb, done);
+    mlhp_sum_kernel<<<d->grid_n, kThreads, 0, st>>>(d->n, d->occ_ptr, d->occ, d->zb, d->jac, r, z, done);
+}
+
+CgWork work_of(MlhpDevice *d)
+{
+    CgWork w;
+    w.x = d->x;
+    w.r = d->r;
+    w.z = d->z;
+    w.p = d->p;
+    w.q = d->q;
+    w.b = d->b;
+    w.partial = d->partial;
+    w.counter = d->counter;
+    w.s = d->s;
+    w.n = d->n;
+    w.red_blocks = d->red_blocks;
+    return w;
+}
+
+const int *done_flag(MlhpDevice *d)
+{
+    return reinterpret_cast<const int *>(reinterpret_cast<const char *>(d->s) + offsetof(CgScalars, done));
+}
+
+}  // namespace
+
+std::string mlhp_device_apply_K(MlhpDevice *d, const double *x, double *y)
+{
+    apply_K(d, x, y, nullptr, d->st);
     MLHP_CUDA(cudaGetLastError());
     return std::string();
 }
 
 std::string mlhp_device_apply_S(MlhpDevice *d, const double *r, double *z)
 {
-    mlhp_diag_kernel<<<d->grid_n, kThreads, 0, d->st>>>(d->n, d->jac, r, z);
+    apply_S(d, r, z, nullptr, d->st);
     MLHP_CUDA(cudaGetLastError());
-    const size_t smem = (size_t)d->max_block * sizeof(double);
-    const int splits = (d->max_block + kRowsPerCta - 1) / kRowsPerCta;
-    for (int c = 0; c < d->ncolours; ++c) {
-        const int64_t nb = d->colour_ptr[c + 1] - d->colour_ptr[c];
-        if (nb == 0) continue;
-        mlhp_block_kernel<<<(unsigned)(nb * splits), kThreads, smem, d->st>>>(d->colour_ptr[c], splits, d->bptr, d->bdofs,
-                                                                            d->fptr, d->fac, r, z);
-        MLHP_CUDA(cudaGetLastError());
-    }
     return std::string();
 }
-
-namespace {
-
-std::string dot(MlhpDevice *d, const double *a, const double *b, double *out)
-{
-    mlhp_dot_partial_kernel<<<kDotGrid, kThreads, 0, d->st>>>(d->n, a, b, d->partial);
-    MLHP_CUDA(cudaGetLastError());
-    mlhp_dot_final_kernel<<<1, 32, 0, d->st>>>(kDotGrid, d->partial, d->scalar);
-    MLHP_CUDA(cudaGetLastError());
-    MLHP_CUDA(cudaMemcpyAsync(out, d->scalar, sizeof(double), cudaMemcpyDeviceToHost, d->st));
-    MLHP_CUDA(cudaStreamSynchronize(d->st));
-    return std::string();
-}
-
-}  // namespace
 
 // status: 0 converged, 1 not converged within maxit, 2 breakdown (p.Kp <= 0 or a non-finite scalar).
 std::string mlhp_device_pcg(MlhpDevice *d, const double *b, double tol, int maxit, double *u, int *its, double *relres,
                             int *status)
 {
-    std::string err;
+    cudaStream_t st = d->own;
+    const CgWork w = work_of(d);
     const size_t bytes = (size_t)d->n * sizeof(double);
-    MLHP_CUDA(cudaMemsetAsync(d->x, 0, bytes, d->st));
-    MLHP_CUDA(cudaMemcpyAsync(d->r, b, bytes, cudaMemcpyDeviceToDevice, d->st));
-    if (!(err = mlhp_device_apply_S(d, d->r, d->z)).empty()) return err;
-    MLHP_CUDA(cudaMemcpyAsync(d->p, d->z, bytes, cudaMemcpyDeviceToDevice, d->st));
-    double rz = 0.0, zz = 0.0;
-    if (!(err = dot(d, d->r, d->z, &rz)).empty()) return err;
-    if (!(err = dot(d, d->z, d->z, &zz)).empty()) return err;
-    const double zn0 = std::sqrt(zz);
-    *its = 0;
-    *relres = 1.0;
-    *status = 1;
-    if (zn0 == 0.0) {
-        *status = 0;
-        *relres = 0.0;
+    // ordered after the caller's stream, and the caller's stream after the solve
+    MLHP_CUDA(cudaEventRecord(d->ev_a, d->st));
+    MLHP_CUDA(cudaStreamWaitEvent(st, d->ev_a, 0));
+    CgScalars &h = *d->hs;
+    std::memset(&h, 0, sizeof h);
+    h.tol = tol;
+    h.maxit = std::max(maxit, 1);
+    MLHP_CUDA(cudaMemcpyAsync(d->s, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    MLHP_CUDA(cudaMemcpyAsync(d->b, b, bytes, cudaMemcpyDeviceToDevice, st));
+    cg_init_kernels(w, st);
+    apply_S(d, d->r, d->z, nullptr, st);
+    cg_after_first_S(w, st);
+    MLHP_CUDA(cudaGetLastError());
+    MLHP_CUDA(cudaMemcpyAsync(&h, d->s, sizeof h, cudaMemcpyDeviceToHost, st));
+    MLHP_CUDA(cudaStreamSynchronize(st));
+    if (!h.done && maxit > 0) {
+        if (!d->graph) {
+            MLHP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int *done = done_flag(d);
+            for (int i = 0; i < kChunk; ++i) {
+                apply_K(d, d->p, d->q, done, st);
+                cg_after_K(w, st);
+                apply_S(d, d->r, d->z, done, st);
+                cg_after_S(w, st);
+            }
+            cudaGraph_t g = nullptr;
+            MLHP_CUDA(cudaStreamEndCapture(st, &g));
+            const cudaError_t e = cudaGraphInstantiate(&d->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                d->graph = nullptr;
+                return std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+            }
+        }
+        while (!h.done) {
+            MLHP_CUDA(cudaGraphLaunch(d->graph, st));
+            MLHP_CUDA(cudaMemcpyAsync(&h, d->s, sizeof h, cudaMemcpyDeviceToHost, st));
+            MLHP_CUDA(cudaStreamSynchronize(st));
+        }
     }
-    for (int it = 1; it <= maxit && *status == 1; ++it) {
-        if (!(err = mlhp_device_apply_K(d, d->p, d->q)).empty()) return err;
-        double pq = 0.0;
-        if (!(err = dot(d, d->p, d->q, &pq)).empty()) return err;
-        *its = it;
-        if (!(pq > 0.0)) {
-            *status = 2;
-            break;
-        }
-        const double a = rz / pq;
-        mlhp_xr_kernel<<<d->grid_n, kThreads, 0, d->st>>>(d->n, a, d->p, d->q, d->x, d->r);
-        MLHP_CUDA(cudaGetLastError());
-        if (!(err = mlhp_device_apply_S(d, d->r, d->z)).empty()) return err;
-        double rz_new = 0.0;
-        if (!(err = dot(d, d->r, d->z, &rz_new)).empty()) return err;
-        if (!(err = dot(d, d->z, d->z, &zz)).empty()) return err;
-        const double rel = std::sqrt(zz) / zn0;
-        *relres = rel;
-        if (!std::isfinite(rel) || !std::isfinite(rz_new)) {
-            *status = 2;
-            break;
-        }
-        if (rel <= tol) {
-            *status = 0;
-            break;
-        }
-        mlhp_p_kernel<<<d->grid_n, kThreads, 0, d->st>>>(d->n, rz_new / rz, d->z, d->p);
-        MLHP_CUDA(cudaGetLastError());
-        rz = rz_new;
+    MLHP_CUDA(cudaMemcpyAsync(u, d->x, bytes, cudaMemcpyDeviceToDevice, st));
+    MLHP_CUDA(cudaEventRecord(d->ev_b, st));
+    MLHP_CUDA(cudaStreamWaitEvent(d->st, d->ev_b, 0));
+    MLHP_CUDA(cudaStreamSynchronize(st));
+    *its = h.it;
+    *relres = h.relres;
+    if (!h.done) {  // maxit == 0 and not converged at the start
+        *status = 1;
+    } else {
+        *status = h.status == FCM_OK ? 0 : h.status == FCM_ENOTCONV ? 1 : 2;
     }
-    MLHP_CUDA(cudaMemcpyAsync(u, d->x, bytes, cudaMemcpyDeviceToDevice, d->st));
-    MLHP_CUDA(cudaStreamSynchronize(d->st));
     return std::string();
 }
 

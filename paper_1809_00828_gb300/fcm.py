@@ -26,7 +26,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
-            "fcm_fpcg_set_stall_window", "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
+            "fcm_fpcg_set_stall_window", "fcm_coarse_set_preconditioner", "fcm_coarse_levels", "fcm_coarse_vcycle",
+            "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size",
             "fcm_mlhp_system",
             "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
@@ -374,9 +375,13 @@ def _bind_unet(L):
     L.fcm_fpcg_solve_host.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ip,
                                       dp]
     L.fcm_fpcg_set_stall_window.argtypes = [P, ctypes.c_int]
+    L.fcm_coarse_set_preconditioner.argtypes = [P, ctypes.c_int]
+    L.fcm_coarse_levels.argtypes = [P, ip, ip, dp, dp]
+    L.fcm_coarse_vcycle.argtypes = [P, P, P]
     for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
               "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
-              "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host", "fcm_fpcg_set_stall_window"):
+              "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host", "fcm_fpcg_set_stall_window",
+              "fcm_coarse_set_preconditioner", "fcm_coarse_levels", "fcm_coarse_vcycle"):
         getattr(L, f).restype = ctypes.c_int
     _unet_bound = True
 
@@ -522,6 +527,46 @@ def _solver_set_stall_window(self, window):
     self._check(load().fcm_fpcg_set_stall_window(self.ctx, int(window)))
 
 
+COARSE_PREC = {"jacobi": 0, "vcycle": 1}  # FCM_COARSE_JACOBI, FCM_COARSE_VCYCLE
+
+
+def _solver_set_coarse_preconditioner(self, kind):
+    """Preconditioner of the coarse CG in fpcg_solve: "jacobi" (3x3 diagonal blocks of K_H) or "vcycle"
+    (one V-cycle of the cell-grid multigrid hierarchy, built on the next coarse solve)."""
+    _bind_unet(load())
+    if kind not in COARSE_PREC:
+        raise ValueError(f"coarse preconditioner {kind!r}: expected one of {sorted(COARSE_PREC)}")
+    self._check(load().fcm_coarse_set_preconditioner(self.ctx, COARSE_PREC[kind]))
+
+
+def _solver_coarse_levels(self):
+    """The multigrid hierarchy: {"levels": n, "dims": [(nx, ny, nz), ...], "lambda_max": [...], "seconds": s}."""
+    _bind_unet(load())
+    n = ctypes.c_int(0)
+    dims = (ctypes.c_int * 36)()
+    lam = (ctypes.c_double * 12)()
+    sec = ctypes.c_double(0.0)
+    self._check(load().fcm_coarse_levels(self.ctx, ctypes.byref(n), dims, lam, ctypes.byref(sec)))
+    return {"levels": n.value, "dims": [tuple(dims[3 * i:3 * i + 3]) for i in range(n.value)],
+            "lambda_max": [lam[i] for i in range(max(0, n.value - 1))], "seconds": sec.value}
+
+
+def _solver_coarse_vcycle(self, f, out=None):
+    """x = one V-cycle of the cell-grid multigrid hierarchy applied to f (3 * n_cells floats, component-major)."""
+    _bind_unet(load())
+    nc = self.workload.n[0] * self.workload.n[1] * self.workload.n[2]
+    x = out if out is not None else self._torch.empty_like(f)
+    pf = _dev(f, 3 * nc, "float32", device=self.device, what="f")
+    px = _dev(x, 3 * nc, "float32", device=self.device, what="out")
+    if pf == px:
+        raise ValueError("coarse_vcycle: f and out must be distinct buffers")
+    self._check(load().fcm_coarse_vcycle(self.ctx, pf, px))
+    return x
+
+
+Solver.coarse_vcycle = _solver_coarse_vcycle
+Solver.set_coarse_preconditioner = _solver_set_coarse_preconditioner
+Solver.coarse_levels = _solver_coarse_levels
 Solver.set_stall_window = _solver_set_stall_window
 Solver.coarse_restrict = _solver_coarse_restrict
 Solver.coarse_prolong = _solver_coarse_prolong

@@ -31,3 +31,33 @@ def test_training_reduces_the_error_left_on_held_out_residuals():
     net.close()
     for s in solvers + held_solvers:
         s.close()
+
+
+def test_trained_start_inside_the_flexible_pcg_on_a_held_out_cube():
+    """The trained network's prediction as the start of the coarse solve, inside flexible PCG on a cube it
+    has not seen: the solve reaches the solution of the plain FP64 solve.  The iteration counts with and
+    without the network are printed, not asserted: on these cubes the learned start saves no iterations
+    (the coarse CG from zero does better), which is the measured result this test keeps visible."""
+    from paper_1809_00828_gb300 import fcm, learned
+    net = fcm.UNet(in_ch=4, out_ch=3, base=8, levels=3, seed=0)
+    gamma, _ = learned.train_cubes(net, [1000, 1001, 1002], n=16, p=2, count=12, group=3, steps_per_group=200,
+                                   batch=4, lr=2e-3, snapshots=(3, 6, 12, 25, 50, 100), log=None)
+    held = learned.training_workloads([1100], n=16, p=2, count=12)[0]
+    s = fcm.Solver(held)
+    try:
+        s.precond_build()
+        b = s.rhs()
+        x64, _, _, _ = s.pcg_solve(b, 1e-10, 20000)
+        kx = s.apply_K(x64)
+        den = float(torch.dot(x64, kx))
+        for k in (2, 5):
+            with_net, its_n, rel_n, st_n = s.fpcg_solve(net, gamma, b, held.tol, 20000, coarse_iters=k)
+            without, its_0, rel_0, st_0 = s.fpcg_solve(None, 0.0, b, held.tol, 20000, coarse_iters=k)
+            assert st_n == 0 and st_0 == 0
+            for u in (with_net, without):
+                e = u - x64
+                assert (float(torch.dot(e, s.apply_K(e))) / den) ** 0.5 < 1e-6
+            print(f"{k} coarse steps: {its_n} iterations with the trained start, {its_0} from zero")
+    finally:
+        s.close()
+        net.close()

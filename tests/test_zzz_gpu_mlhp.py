@@ -5,8 +5,10 @@ scaled to a 4^3 base grid) and a larger cavity that cuts many leaves.
 - K x: the device CSR product against the oracle's assembled K, 1e-12 of max |y| (assembly and product
   differ only by rounding).
 - S r: against the same factors applied on the host, 1e-12 of max |z| (summation order only).  Against
-  the oracle's own pseudo inverses in the energy norm, 1e-6: two eigensolvers agree on A_B^+ to about
-  cond(A_B) times the rounding unit, and cut leaves reach cond ~ 1e10.
+  the oracle's own pseudo inverses per DOF: two backward-stable eigensolvers agree on A_B^+ to
+  c n eps (cond(A_B) + 1) ||A_B^+|| (cond over the retained spectrum), so a DOF may differ by the sum of
+  that times ||r_B|| over the blocks containing it (c = 10); sliver leaves reach cond ~ 1e10 and loosen
+  the bound on their own DOFs only.
 - PCG with truncated blocks: iterations within 5 % of the oracle's (its factors come from another
   eigensolver), energy error below 1e-6 against a sparse direct solve.
 """
@@ -58,8 +60,14 @@ def test_mlhp_apply_S_matches_the_factors_and_the_oracle(case):
         zh[B] += Fb @ r[B]
     assert np.abs(z - zh).max() <= 1e-12 * np.abs(zh).max()
     zo = Q.apply_S(r)
-    d = z - zo
-    assert np.sqrt(abs(d @ (Q.K @ d)) / (zo @ (Q.K @ zo))) < 1e-6
+    bound = np.zeros(Q.n)
+    for B in Q.blocks:
+        lam = np.linalg.eigvalsh(Q.K[B][:, B].toarray())
+        keep = lam[lam > 1e-13 * lam.max()]
+        cond = keep.max() / keep.min()
+        bound[B] += 10.0 * len(B) * 2.0 ** -52 * (cond + 1.0) / keep.min() * np.linalg.norm(r[B])
+    bound += np.abs(jac * r) * 2.0 ** -52 * 4  # the diagonal part, rounding only
+    assert (np.abs(z - zo) <= bound).all(), float(np.max(np.abs(z - zo) / np.maximum(bound, 1e-300)))
 
 
 def test_mlhp_pcg_matches_the_oracle(case):
