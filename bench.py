@@ -315,9 +315,11 @@ def _form(args, net):
     if args.form == "pcg":
         return "plain Schwarz-PCG"
     start = "trained U-Net prediction scaled by the coarse line search" if net is not None else "zero"
-    prec = ("block-Jacobi" if args.coarse_prec == "jacobi" else
-            "V-cycle-preconditioned (cell-grid multigrid, Galerkin levels, damped block-Jacobi smoothing, dense "
-            "coarsest level)")
+    prec = {"jacobi": "block-Jacobi",
+            "vcycle": "V-cycle-preconditioned (cell-grid multigrid, Galerkin levels, damped block-Jacobi "
+                      "smoothing, dense coarsest level)",
+            "hybrid": "hybrid-V-cycle-preconditioned (cell-grid multigrid, additive block Jacobi on the finest "
+                      "cell grid, V-cycle below)"}[args.coarse_prec]
     return (f"flexible CG(4), z = S r + P y, y from {args.coarse_iters} {prec} CG steps on the Galerkin "
             f"coarse operator K_H = P^T K P starting from {start}")
 
@@ -335,6 +337,9 @@ def _launches_per_solve(args, info, its, flex_its, net, mg_levels=0):
     if args.coarse_prec == "vcycle" and k > 0:
         # a V-cycle (5 launches per level above the last, 1 for the last) and r.z, once per step
         coarse += k * (5 * (mg_levels - 1) + 1 + 1)
+    elif args.coarse_prec == "hybrid" and k > 0:
+        # level 0: Jacobi, restrict, interpolate; 5 per level between; 1 for the last; r.z
+        coarse += k * ((3 + 5 * (mg_levels - 2) if mg_levels > 1 else 0) + 1 + 1)
     if net is not None:
         coarse += 2 + 1 + 2 + _unet_launches(net)       # sigma, prep, post, start apply + line search
     flex = k_apply + 2 + s_apply + 1 + coarse + 2       # pq, xr, conv, dots, newp
@@ -706,7 +711,7 @@ def main():
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
     ap.add_argument("--coarse-iters", type=int, default=None,
                     help="coarse CG steps per preconditioner apply (default: per workload, COARSE_DEFAULTS)")
-    ap.add_argument("--coarse-prec", default=None, choices=["jacobi", "vcycle"],
+    ap.add_argument("--coarse-prec", default=None, choices=["jacobi", "vcycle", "hybrid"],
                     help="preconditioner of the coarse CG: 3x3 diagonal blocks of K_H, or one V-cycle of the "
                          "cell-grid multigrid hierarchy (default: per workload, COARSE_DEFAULTS)")
     ap.add_argument("--k-precision", default="double_float", choices=["double_float", "fp64"],

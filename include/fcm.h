@@ -358,10 +358,15 @@ fcm_status fcm_fpcg_set_stall_window(fcm_ctx *ctx, int window);
  *     (at most 512 cells) by its dense pseudo-inverse (eigenvalues below 1e-12 of the largest
  *     dropped).  The cycle is a fixed symmetric linear operator, so the coarse CG stays a
  *     preconditioned CG.  Not part of the paper's method: a coarse space for its Sec. 6 limitation.
+ *   FCM_COARSE_HYBRID: the same hierarchy, but on the finest cell grid (level 0) the damped block-Jacobi
+ *     step and the coarse correction are added, x = omega D^-1 f + P2 V_1(P2^T f), V_1 the V-cycle of
+ *     the levels below: symmetric and linear too, and it applies K_H itself no more (the level-0
+ *     apply is the costly one when K_H streams from HBM).
  * The hierarchy is built on the first coarse solve after the choice (FCM_ENOMEM if it does not fit).
  * Changing the choice drops the flexible CG's captured graph.  FCM_EINVAL for another kind. */
 #define FCM_COARSE_JACOBI 0
 #define FCM_COARSE_VCYCLE 1
+#define FCM_COARSE_HYBRID 2
 fcm_status fcm_coarse_set_preconditioner(fcm_ctx *ctx, int kind);
 
 /* The multigrid hierarchy after it is built: *levels (0 before), the cell grid of each level in
@@ -370,11 +375,12 @@ fcm_status fcm_coarse_set_preconditioner(fcm_ctx *ctx, int kind);
  * null). */
 fcm_status fcm_coarse_levels(fcm_ctx *ctx, int *levels, int *dims, double *lambdas, double *seconds);
 
-/* x_cells_dev = one V-cycle of that hierarchy applied to f_cells_dev (cell vectors, 3 * n_cells floats,
- * component-major, distinct device buffers), whatever the coarse preconditioner in use; builds K_H
- * and the hierarchy if needed.  Ordered on the caller's stream like fcm_coarse_apply.  A fixed
- * symmetric linear operator: on a grid of at most 512 cells it is the pseudo-inverse of K_H. */
-fcm_status fcm_coarse_vcycle(fcm_ctx *ctx, const float *f_cells_dev, float *x_cells_dev);
+/* x_cells_dev = one cycle of that hierarchy, kind FCM_COARSE_VCYCLE or FCM_COARSE_HYBRID, applied to
+ * f_cells_dev (cell vectors, 3 * n_cells floats, component-major, distinct device buffers), whatever
+ * the coarse preconditioner in use; builds K_H and the hierarchy if needed.  Ordered on the caller's
+ * stream like fcm_coarse_apply.  A fixed symmetric linear operator: on a grid of at most 512 cells it
+ * is the pseudo-inverse of K_H.  FCM_EINVAL for another kind. */
+fcm_status fcm_coarse_vcycle(fcm_ctx *ctx, int kind, const float *f_cells_dev, float *x_cells_dev);
 
 /* Same as fcm_fpcg_solve with host buffers: rhs_host (n_lattice doubles) is
  * copied to the device, solved, and the solution copied back into u_host

@@ -672,13 +672,13 @@ int tiles(int64_t ncell) { return (int)((ncell + kTileCells - 1) / kTileCells); 
 namespace {
 fcm_status mg_build(fcm_ctx *C);
 void mg_free_levels(CoarseOp *op);
-void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int *stop);
+void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int *stop, bool hybrid);
 }  // namespace
 
 fcm_status coarse_ensure(fcm_ctx *C)
 {
     if (C->coarse) {
-        if (C->coarse_prec == FCM_COARSE_VCYCLE && C->coarse->nlev == 0) return mg_build(C);
+        if (C->coarse_prec != FCM_COARSE_JACOBI && C->coarse->nlev == 0) return mg_build(C);
         return FCM_OK;
     }
     const int64_t ncell = C->hp.ncells, n3 = 3 * ncell;
@@ -732,7 +732,7 @@ fcm_status coarse_ensure(fcm_ctx *C)
     cudaFree(ecell);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return fail(e);
     C->coarse = op;
-    if (C->coarse_prec == FCM_COARSE_VCYCLE) return mg_build(C);
+    if (C->coarse_prec != FCM_COARSE_JACOBI) return mg_build(C);
     return FCM_OK;
 }
 
@@ -937,7 +937,11 @@ fcm_status mg_build(fcm_ctx *C)
 // block-Jacobi step from zero, the residual restricted to the next level, the correction
 // interpolated back and one more damped block-Jacobi step; the last level by its dense
 // pseudo-inverse.  Symmetric in its smoothing, so a fixed linear operator (for the coarse CG).
-void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int *stop)
+//
+// hybrid: on level 0 the damped block-Jacobi step and the coarse correction are added instead of
+// multiplied, x0 = omega Dinv f0 + P2 V_1(P2^T f0) with V_1 the V-cycle of the levels below: symmetric as
+// well, and without a K_H apply on the finest cell grid (the expensive one).
+void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int *stop, bool hybrid)
 {
     const int L = op->nlev - 1;
     if (L == 0) {
@@ -945,7 +949,13 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
                                                                                            op->n3last, stop);
         return;
     }
-    for (int l = 0; l < L; ++l) {
+    const int l0 = hybrid ? 1 : 0;
+    if (hybrid) {
+        MgLevel &v = op->lev[0];
+        jacobi0_kernel<<<nb(v.ncell), RT, 0, st>>>(f0, v.Dinv, v.omega, x0, v.ncell, stop);
+        mg_restrict_kernel<<<nb(op->lev[1].ncell), RT, 0, st>>>(f0, op->lev[1].f, dims_down(v, op->lev[1]), stop);
+    }
+    for (int l = l0; l < L; ++l) {
         MgLevel &v = op->lev[l];
         const float *f = l == 0 ? f0 : v.f;
         jacobi0_kernel<<<nb(v.ncell), RT, 0, st>>>(f, v.Dinv, v.omega, v.xa, v.ncell, stop);
@@ -956,7 +966,7 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
     }
     dense_mv_kernel<<<std::max(1, std::min((op->n3last + 7) / 8, 152 * 8)), RT, 0, st>>>(op->Apinv, op->lev[L].f,
                                                                                        op->lev[L].x, op->n3last, stop);
-    for (int l = L - 1; l >= 0; --l) {
+    for (int l = L - 1; l >= l0; --l) {
         MgLevel &v = op->lev[l];
         const float *f = l == 0 ? f0 : v.f;
         float *out = l == 0 ? x0 : v.x;
@@ -964,6 +974,9 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
         kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, out, nullptr, v.g, v.ncell, 4, op->partial, op->counter,
                                                  op->sc, stop, v.Dinv, v.omega);
     }
+    if (hybrid)
+        mg_interp_kernel<<<nb(op->lev[0].ncell), RT, 0, st>>>(op->lev[1].x, x0, dims_down(op->lev[0], op->lev[1]), 1,
+                                                               stop);
 }
 
 }  // namespace
@@ -980,7 +993,8 @@ void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, co
     CoarseOp *op = C->coarse;
     const int64_t n3 = 3 * op->ncell, nc = op->ncell;
     cudaStream_t st = C->stream;
-    const bool mg = C->coarse_prec == FCM_COARSE_VCYCLE && op->nlev > 0;
+    const bool mg = C->coarse_prec != FCM_COARSE_JACOBI && op->nlev > 0;
+    const bool hybrid = C->coarse_prec == FCM_COARSE_HYBRID;
     if (start != 0)
         kh_kernel<<<tiles(nc), RT, 0, st>>>(op->KH, y, nullptr, nullptr, op->q, C->g, nc, 0, op->partial, op->counter,
                                             op->sc, stop);
@@ -988,7 +1002,7 @@ void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, co
     cstart_kernel<<<nb(nc), RT, 0, st>>>(f, y, op->r, op->z, op->q, op->Dinv, nc, start, !mg && iters > 0 ? 1 : 0,
                                          op->partial, op->counter, op->sc, stop);
     if (mg && iters > 0) {
-        vcycle(op, op->r, op->z, st, stop);
+        vcycle(op, op->r, op->z, st, stop, hybrid);
         rz_kernel<<<nb(n3), RT, 0, st>>>(op->r, op->z, n3, 1, op->partial, op->counter, op->sc, stop);
     }
     for (int i = 0; i < iters; ++i) {
@@ -1001,7 +1015,7 @@ void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, co
         cupd_kernel<<<nb(nc), RT, 0, st>>>(y, op->r, op->z, pn, op->q, op->Dinv, nc, last || mg ? 1 : 0, op->partial,
                                            op->counter, op->sc, stop);
         if (mg && !last) {
-            vcycle(op, op->r, op->z, st, stop);
+            vcycle(op, op->r, op->z, st, stop, hybrid);
             rz_kernel<<<nb(n3), RT, 0, st>>>(op->r, op->z, n3, 0, op->partial, op->counter, op->sc, stop);
         }
     }
@@ -1035,25 +1049,25 @@ extern "C" fcm_status fcm_coarse_apply(fcm_ctx *C, const float *x_dev, float *y_
 }
 
 namespace fcm {
-fcm_status coarse_vcycle_apply(fcm_ctx *C, const float *f, float *x)
+fcm_status coarse_vcycle_apply(fcm_ctx *C, int kind, const float *f, float *x)
 {
     fcm_status s = coarse_ensure(C);
     if (s == FCM_OK && C->coarse->nlev == 0) s = mg_build(C);
     if (s != FCM_OK) return s;
-    vcycle(C->coarse, f, x, C->stream, nullptr);
+    vcycle(C->coarse, f, x, C->stream, nullptr, kind == FCM_COARSE_HYBRID);
     return FCM_OK;
 }
 }  // namespace fcm
 
-extern "C" fcm_status fcm_coarse_vcycle(fcm_ctx *C, const float *f_dev, float *x_dev)
+extern "C" fcm_status fcm_coarse_vcycle(fcm_ctx *C, int kind, const float *f_dev, float *x_dev)
 {
-    if (!C || !f_dev || !x_dev || f_dev == x_dev) {
+    if (!C || !f_dev || !x_dev || f_dev == x_dev || (kind != FCM_COARSE_VCYCLE && kind != FCM_COARSE_HYBRID)) {
         if (C) C->err = "fcm_coarse_vcycle: invalid argument";
         return FCM_EINVAL;
     }
     cudaEventRecord(C->ev_in, C->ustream);
     cudaStreamWaitEvent(C->stream, C->ev_in, 0);
-    fcm_status s = fcm::coarse_vcycle_apply(C, f_dev, x_dev);
+    fcm_status s = fcm::coarse_vcycle_apply(C, kind, f_dev, x_dev);
     cudaEventRecord(C->ev_out, C->stream);
     cudaStreamWaitEvent(C->ustream, C->ev_out, 0);
     if (s != FCM_OK) return s;
@@ -1068,8 +1082,8 @@ extern "C" fcm_status fcm_coarse_vcycle(fcm_ctx *C, const float *f_dev, float *x
 extern "C" fcm_status fcm_coarse_set_preconditioner(fcm_ctx *C, int kind)
 {
     if (!C) return FCM_EINVAL;
-    if (kind != FCM_COARSE_JACOBI && kind != FCM_COARSE_VCYCLE) {
-        C->err = "fcm_coarse_set_preconditioner: kind must be FCM_COARSE_JACOBI or FCM_COARSE_VCYCLE";
+    if (kind != FCM_COARSE_JACOBI && kind != FCM_COARSE_VCYCLE && kind != FCM_COARSE_HYBRID) {
+        C->err = "fcm_coarse_set_preconditioner: kind must be FCM_COARSE_JACOBI, FCM_COARSE_VCYCLE or FCM_COARSE_HYBRID";
         return FCM_EINVAL;
     }
     if (kind != C->coarse_prec) fcm::fcg_forget_graph(C->fcg);

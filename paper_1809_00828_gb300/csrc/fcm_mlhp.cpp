@@ -905,7 +905,7 @@ fcm_status fcm_mlhp_device_setup(fcm_mlhp *h, void *cuda_stream)
             h->err = "fcm_mlhp_device_setup: " + e;
             // CUDA failures carry the call's name in front; an allocation failure reads "out of memory"
             if (e.find("out of memory") != std::string::npos) return FCM_ENOMEM;
-            return e.rfind("upload", 0) == 0 || e.rfind("cudaMalloc", 0) == 0 ? FCM_ECUDA : FCM_EINVAL;
+            return e.rfind("upload", 0) == 0 || e.rfind("cuda", 0) == 0 ? FCM_ECUDA : FCM_EINVAL;
         }
     } catch (const std::bad_alloc &) {
         h->err = "fcm_mlhp_device_setup: out of host memory";

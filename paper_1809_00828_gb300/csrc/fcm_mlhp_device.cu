@@ -71,13 +71,28 @@ __global__ void __launch_bounds__(kThreads) mlhp_block_rows_kernel(const int2 *_
     for (int j = threadIdx.x; j < m; j += kThreads) rb[j] = r[bdofs[o + j]];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the warp's four rows it.y + warp + 8 t at once: four independent streams of factor loads in flight
+    constexpr int kRowsPerWarp = kRowsPerCta / (kThreads / 32);
     const int row_end = min(m, it.y + kRowsPerCta);
-    for (int i = it.y + warp; i < row_end; i += kThreads / 32) {  // warp-uniform bounds
-        const double *Fi = F + (int64_t)i * m;
-        double s = 0.0;
-        for (int j = lane; j < m; j += 32) s += Fi[j] * rb[j];
-        s = warp_sum(s);
-        if (lane == 0) zb[o + i] = s;
+    const double *Fi[kRowsPerWarp];
+    bool on[kRowsPerWarp];
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int i = it.y + warp + t * (kThreads / 32);
+        on[t] = i < row_end;  // warp-uniform
+        Fi[t] = F + (int64_t)(on[t] ? i : it.y) * m;
+    }
+    double s[kRowsPerWarp] = {};
+    for (int j = lane; j < m; j += 32) {
+        const double rj = rb[j];
+#pragma unroll
+        for (int t = 0; t < kRowsPerWarp; ++t)
+            if (on[t]) s[t] = fma(__ldcs(Fi[t] + j), rj, s[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        const double v = warp_sum(s[t]);
+        if (on[t] && lane == 0) zb[o + it.y + warp + t * (kThreads / 32)] = v;
     }
 }
 

@@ -377,7 +377,7 @@ def _bind_unet(L):
     L.fcm_fpcg_set_stall_window.argtypes = [P, ctypes.c_int]
     L.fcm_coarse_set_preconditioner.argtypes = [P, ctypes.c_int]
     L.fcm_coarse_levels.argtypes = [P, ip, ip, dp, dp]
-    L.fcm_coarse_vcycle.argtypes = [P, P, P]
+    L.fcm_coarse_vcycle.argtypes = [P, ctypes.c_int, P, P]
     for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
               "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
               "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host", "fcm_fpcg_set_stall_window",
@@ -527,12 +527,13 @@ def _solver_set_stall_window(self, window):
     self._check(load().fcm_fpcg_set_stall_window(self.ctx, int(window)))
 
 
-COARSE_PREC = {"jacobi": 0, "vcycle": 1}  # FCM_COARSE_JACOBI, FCM_COARSE_VCYCLE
+COARSE_PREC = {"jacobi": 0, "vcycle": 1, "hybrid": 2}  # FCM_COARSE_JACOBI, FCM_COARSE_VCYCLE, FCM_COARSE_HYBRID
 
 
 def _solver_set_coarse_preconditioner(self, kind):
-    """Preconditioner of the coarse CG in fpcg_solve: "jacobi" (3x3 diagonal blocks of K_H) or "vcycle"
-    (one V-cycle of the cell-grid multigrid hierarchy, built on the next coarse solve)."""
+    """Preconditioner of the coarse CG in fpcg_solve: "jacobi" (3x3 diagonal blocks of K_H), "vcycle" (one
+    V-cycle of the cell-grid multigrid hierarchy, built on the next coarse solve) or "hybrid" (the same,
+    additive on the finest cell grid)."""
     _bind_unet(load())
     if kind not in COARSE_PREC:
         raise ValueError(f"coarse preconditioner {kind!r}: expected one of {sorted(COARSE_PREC)}")
@@ -551,8 +552,9 @@ def _solver_coarse_levels(self):
             "lambda_max": [lam[i] for i in range(max(0, n.value - 1))], "seconds": sec.value}
 
 
-def _solver_coarse_vcycle(self, f, out=None):
-    """x = one V-cycle of the cell-grid multigrid hierarchy applied to f (3 * n_cells floats, component-major)."""
+def _solver_coarse_vcycle(self, f, out=None, kind="vcycle"):
+    """x = one cycle ("vcycle" or "hybrid") of the cell-grid multigrid hierarchy applied to f (3 * n_cells
+    floats, component-major)."""
     _bind_unet(load())
     nc = self.workload.n[0] * self.workload.n[1] * self.workload.n[2]
     x = out if out is not None else self._torch.empty_like(f)
@@ -560,7 +562,9 @@ def _solver_coarse_vcycle(self, f, out=None):
     px = _dev(x, 3 * nc, "float32", device=self.device, what="out")
     if pf == px:
         raise ValueError("coarse_vcycle: f and out must be distinct buffers")
-    self._check(load().fcm_coarse_vcycle(self.ctx, pf, px))
+    if kind not in ("vcycle", "hybrid"):
+        raise ValueError(f"coarse_vcycle: kind {kind!r}, expected 'vcycle' or 'hybrid'")
+    self._check(load().fcm_coarse_vcycle(self.ctx, COARSE_PREC[kind], pf, px))
     return x
 
 

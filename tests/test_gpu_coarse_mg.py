@@ -123,7 +123,13 @@ def _reference_vcycle(KH, n, lambdas):
         x = x + P2 @ vc(P2.T @ r, l + 1)
         return x + om * (Di @ (f - A @ x))
 
-    return vc, dims, cond, levels
+    def hybrid(f):
+        if not levels:
+            return pinv @ f
+        _, P2, Di, om = levels[0]
+        return om * (Di @ f) + P2 @ vc(P2.T @ f, 1)
+
+    return {"vcycle": vc, "hybrid": hybrid}, dims, cond, levels
 
 
 def _workload(kind):
@@ -134,8 +140,9 @@ def _workload(kind):
     return I.Workload("porous_24_p1", (24, 24, 24), 1, 1e-3, geo, 1e-8)
 
 
+@pytest.mark.parametrize("cycle", ["vcycle", "hybrid"])
 @pytest.mark.parametrize("kind,levels", [("odd", 2), ("cube", 3)])
-def test_vcycle_matches_its_definition(kind, levels):
+def test_vcycle_matches_its_definition(kind, levels, cycle):
     from paper_1809_00828_gb300 import fcm
     w = _workload(kind)
     P = O.Problem.from_workload(w)
@@ -145,12 +152,13 @@ def test_vcycle_matches_its_definition(kind, levels):
         nc = int(np.prod(w.n))
         rng = np.random.default_rng(5)
         f = rng.standard_normal(3 * nc).astype(np.float32)
-        x_dev = s.coarse_vcycle(torch.from_numpy(f).cuda()).cpu().numpy().astype(np.float64)
+        x_dev = s.coarse_vcycle(torch.from_numpy(f).cuda(), kind=cycle).cpu().numpy().astype(np.float64)
         info = s.coarse_levels()
         assert info["levels"] == levels
         Pf = _prolongation(w, P.free_lat)
         KH = (Pf.T @ P.csr() @ Pf).tocsr()
-        vc, dims, cond, lv = _reference_vcycle(KH, w.n, info["lambda_max"])
+        cycles, dims, cond, lv = _reference_vcycle(KH, w.n, info["lambda_max"])
+        vc = cycles[cycle]
         assert [tuple(d) for d in info["dims"]] == dims
         # the smoother's lambda: 15 power steps approach lambda_max(Dinv K_l) from below
         for l, (A, _, Di, _) in enumerate(lv):
@@ -161,11 +169,11 @@ def test_vcycle_matches_its_definition(kind, levels):
         e = x_dev - x_ref
         err = np.sqrt(e @ (KH @ e)) / np.sqrt(x_ref @ (KH @ x_ref))
         bound = 64 * 2.0 ** -24 * cond + 1e-5
-        print(f"{kind}: levels {dims}, cond(K_L) {cond:.3g}, energy difference {err:.3g} (bound {bound:.3g})")
+        print(f"{kind} {cycle}: levels {dims}, cond(K_L) {cond:.3g}, energy difference {err:.3g} (bound {bound:.3g})")
         assert err <= bound
         # a symmetric positive semi-definite operator, as the coarse CG needs
         g = rng.standard_normal(3 * nc).astype(np.float32)
-        y_dev = s.coarse_vcycle(torch.from_numpy(g).cuda()).cpu().numpy().astype(np.float64)
+        y_dev = s.coarse_vcycle(torch.from_numpy(g).cuda(), kind=cycle).cpu().numpy().astype(np.float64)
         a, b = g.astype(np.float64) @ x_dev, f.astype(np.float64) @ y_dev
         assert abs(a - b) <= max(1e-4, bound) * max(abs(a), abs(b))
         assert f.astype(np.float64) @ x_dev > 0.0
@@ -213,8 +221,12 @@ def test_fpcg_with_vcycle_coarse_cg():
         assert s.last_solve()["fallback"] == 0
         x_ref = spla.spsolve(P.csr().tocsc(), P.rhs())
         assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
-        print(f"flexible PCG, 2 coarse steps: block Jacobi {its_j} iterations, V-cycle {its_v}")
         assert its_v < its_j
+        s.set_coarse_preconditioner("hybrid")
+        u, its_h, rel, st = s.fpcg_solve(None, 0.0, b, w.tol, 4000, coarse_iters=2)
+        assert st == 0 and rel <= w.tol * 1.0001
+        assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
+        print(f"flexible PCG, 2 coarse steps: block Jacobi {its_j} iterations, V-cycle {its_v}, hybrid {its_h}")
         # back to block Jacobi: the captured iteration is rebuilt and gives the first count again
         s.set_coarse_preconditioner("jacobi")
         _, its_j2, _, _ = s.fpcg_solve(None, 0.0, b, w.tol, 4000, coarse_iters=2)
