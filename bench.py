@@ -67,8 +67,8 @@ TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "schwarz_apply_traffic_porous30
 # the 129 MB L2 (32^3 cells: 74 MB) block-Jacobi steps are cheap and 20 of them solve the coarse grid
 # well; at 80^3 cells K_H (1.16 GB) streams from HBM and two V-cycle-preconditioned steps win (3.2 s
 # against 6.4 s for 10 block-Jacobi steps, which stall into the plain-PCG fallback).
-COARSE_DEFAULTS = {"porous40_32_p3": ("jacobi", 20), "porous40_32_p2": ("jacobi", 20),
-                   "porous300_80_p2": ("vcycle", 2)}
+COARSE_DEFAULTS = {"porous40_32_p3": ("jacobi", 20, "fp32"), "porous40_32_p2": ("jacobi", 20, "fp32"),
+                   "porous300_80_p2": ("vcycle", 2, "fp32")}
 
 
 def _schwarz_traffic(workload_name, precision):
@@ -321,7 +321,7 @@ def _form(args, net):
             "hybrid": "hybrid-V-cycle-preconditioned (cell-grid multigrid, additive block Jacobi on the finest "
                       "cell grid, V-cycle below)"}[args.coarse_prec]
     return (f"flexible CG(4), z = S r + P y, y from {args.coarse_iters} {prec} CG steps on the Galerkin "
-            f"coarse operator K_H = P^T K P starting from {start}")
+            f"coarse operator K_H = P^T K P ({args.coarse_storage} storage) starting from {start}")
 
 
 def _launches_per_solve(args, info, its, flex_its, net, mg_levels=0):
@@ -388,6 +388,7 @@ def run_fcm(args, rank, world, local_rank):
     if args.form == "coarse":
         s.set_stall_window(args.stall_window)
         s.set_coarse_preconditioner(args.coarse_prec)
+        s.set_coarse_storage(args.coarse_storage)
     if args.form == "coarse" and args.net:
         from paper_1809_00828_gb300 import learned
         net, gamma = learned.load(args.net)
@@ -711,6 +712,8 @@ def main():
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
     ap.add_argument("--coarse-iters", type=int, default=None,
                     help="coarse CG steps per preconditioner apply (default: per workload, COARSE_DEFAULTS)")
+    ap.add_argument("--coarse-storage", default=None, choices=["fp32", "fp16"],
+                    help="storage of K_H: FP32, or symmetrically scaled FP16 (default: per workload)")
     ap.add_argument("--coarse-prec", default=None, choices=["jacobi", "vcycle", "hybrid"],
                     help="preconditioner of the coarse CG: 3x3 diagonal blocks of K_H, or one V-cycle of the "
                          "cell-grid multigrid hierarchy (default: per workload, COARSE_DEFAULTS)")
@@ -740,8 +743,9 @@ def main():
     ap.add_argument("--mlhp-k", type=int, default=None,
                     help="instead of the bench line: time the multi-level hp path on the Sec. 5.1 cube refined k times")
     args = ap.parse_args()
-    prec, iters = COARSE_DEFAULTS.get(args.workload, ("vcycle", 2))
+    prec, iters, storage = COARSE_DEFAULTS.get(args.workload, ("vcycle", 2, "fp32"))
     args.coarse_prec = args.coarse_prec or prec
+    args.coarse_storage = args.coarse_storage or storage
     args.coarse_iters = iters if args.coarse_iters is None else args.coarse_iters
     if args.mlhp_k is not None:
         return run_mlhp(args)

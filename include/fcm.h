@@ -369,6 +369,21 @@ fcm_status fcm_fpcg_set_stall_window(fcm_ctx *ctx, int window);
 #define FCM_COARSE_HYBRID 2
 fcm_status fcm_coarse_set_preconditioner(fcm_ctx *ctx, int kind);
 
+/* Storage of K_H on its own cell grid, used by every K_H product (fcm_coarse_apply, the coarse CG and
+ * the finest level of the cycles; the coarser levels are built from the FP32 operator and stay FP32):
+ *   FCM_COARSE_STORE_FP32 (the default): the 63 stored 3x3 blocks per cell in FP32, 2,268 B per cell;
+ *   FCM_COARSE_STORE_FP16: symmetrically scaled, K~_cj = s_c K_cj s_j with s_c = (tr K_cc / 3)^(-1/2),
+ *     in FP16 rounded to nearest, 1,134 B per cell (+ 4 B for s).  For the positive semi-definite K_H
+ *     every scaled entry is at most 3 in magnitude, so FP16 keeps 11 significant bits of each entry
+ *     above 6e-5 and an absolute 3e-8 below: a perturbation of K_H of relative size ~5e-4 in the scaled
+ *     norm, which the coarse part of the flexible CG's preconditioner tolerates; the copy halves the
+ *     bytes of each product where K_H streams from HBM.
+ * The FP16 copy is made on the next coarse call (FCM_ENOMEM if it does not fit); changing the storage
+ * drops the flexible CG's captured graph.  FCM_EINVAL for another value. */
+#define FCM_COARSE_STORE_FP32 0
+#define FCM_COARSE_STORE_FP16 1
+fcm_status fcm_coarse_set_storage(fcm_ctx *ctx, int storage);
+
 /* The multigrid hierarchy after it is built: *levels (0 before), the cell grid of each level in
  * dims[3 * l + axis] (room for 3 * 12 ints, may be null), the smoother's lambda_max estimate per
  * level but the last in lambdas (room for 12, may be null) and the build time in *seconds (may be

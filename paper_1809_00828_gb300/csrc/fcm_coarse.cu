@@ -55,6 +55,9 @@ struct FcgState {
     float *cin = nullptr, *cout = nullptr, *f = nullptr;
     FcgScalars *d = nullptr, *h = nullptr;
     cudaGraphExec_t graph = nullptr;
+    // the coarse correction without a network runs on `side`, beside the Schwarz apply (both read r only)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_r = nullptr, ev_c = nullptr;
     // what the graph was captured for
     uint64_t net_serial = 0, net_gen = 0;
     const fcm_unet *net = nullptr;
@@ -84,6 +87,9 @@ void fcg_free(FcgState *F)
     for (void *q : ps)
         if (q) cudaFree(q);
     if (F->h) cudaFreeHost(F->h);
+    if (F->ev_r) cudaEventDestroy(F->ev_r);
+    if (F->ev_c) cudaEventDestroy(F->ev_c);
+    if (F->side) cudaStreamDestroy(F->side);
     delete F;
 }
 
@@ -133,6 +139,30 @@ __global__ void prolong_kernel(const float *__restrict__ cells, const uint8_t *_
             }
         }
         for (int a = 0; a < 3; ++a) y[3 * node + a] = mask[3 * node + a] ? 0.125 * s * acc[a] : 0.0;
+    }
+}
+
+// z += P cells on the free vertex DOFs (the only DOFs P reaches): one thread per vertex node, the 8
+// cells around it summed in the same fixed order as prolong_kernel, so z + P y here equals the sum
+// zS[i] + (P y)[i] formed from a separate prolongation
+__global__ void prolong_add_kernel(const float *__restrict__ cells, const uint8_t *__restrict__ mask,
+                                   double *__restrict__ z, Grid3 g, int p, const int *stop)
+{
+    STOP_RETURN;
+    const int vx = g.n[0] + 1, vy = g.n[1] + 1, vz = g.n[2] + 1;
+    const int64_t nv = (int64_t)vx * vy * vz, ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        const int vi = (int)(v % vx), vj = (int)((v / vx) % vy), vk = (int)(v / ((int64_t)vx * vy));
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int t = 0; t < 8; ++t) {
+            const int cx = vi - 1 + (t & 1), cy = vj - 1 + ((t >> 1) & 1), cz = vk - 1 + (t >> 2);
+            if (cx < 0 || cy < 0 || cz < 0 || cx >= g.n[0] || cy >= g.n[1] || cz >= g.n[2]) continue;
+            const int64_t c = cx + (int64_t)g.n[0] * (cy + (int64_t)g.n[1] * cz);
+            for (int a = 0; a < 3; ++a) acc[a] += cells[a * ncell + c];
+        }
+        const int64_t node = (int64_t)p * vi + (int64_t)g.M[0] * ((int64_t)p * vj + (int64_t)g.M[1] * p * vk);
+        for (int a = 0; a < 3; ++a)
+            if (mask[3 * node + a]) z[3 * node + a] += 0.125 * acc[a];
     }
 }
 
@@ -286,8 +316,8 @@ __global__ void __launch_bounds__(RT) fk_conv_kernel(const double *zS, int64_t n
     }
 }
 
-// beta_j = (zS + c) . q_j / pq_j over the last min(it, kM) directions
-__global__ void __launch_bounds__(RT) fk_dots_kernel(const double *zS, const double *c, const double *ring, int64_t n,
+// beta_j = z . q_j / pq_j over the last min(it, kM) directions (z = S r + P y)
+__global__ void __launch_bounds__(RT) fk_dots_kernel(const double *zv, const double *ring, int64_t n,
                                                       double *partial, unsigned *counter, FcgScalars *F)
 {
     const int *stop = &F->stop;
@@ -298,7 +328,7 @@ __global__ void __launch_bounds__(RT) fk_dots_kernel(const double *zS, const dou
     for (int j = 0; j < kM; ++j) Q[j] = ring + (int64_t)(kM + (it - 1 - j + 2 * kM) % kM) * n;
     double v[kM] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
-        const double z = zS[i] + c[i];
+        const double z = zv[i];
 #pragma unroll
         for (int j = 0; j < kM; ++j)
             if (j < np) v[j] = fma(z, Q[j][i], v[j]);
@@ -308,9 +338,9 @@ __global__ void __launch_bounds__(RT) fk_dots_kernel(const double *zS, const dou
     for (int j = 0; j < kM; ++j) F->beta[j] = j < np ? v[j] / F->pq[(it - 1 - j + 2 * kM) % kM] : 0.0;
 }
 
-// p = zS + c - sum_j beta_j p_j
-__global__ void __launch_bounds__(RT) fk_newp_kernel(double *p, const double *zS, const double *c, const double *ring,
-                                                      int64_t n, const FcgScalars *F)
+// p = z - sum_j beta_j p_j (z = S r + P y)
+__global__ void __launch_bounds__(RT) fk_newp_kernel(double *p, const double *zv, const double *ring, int64_t n,
+                                                      const FcgScalars *F)
 {
     const int *stop = &F->stop;
     STOP_RETURN;
@@ -323,7 +353,7 @@ __global__ void __launch_bounds__(RT) fk_newp_kernel(double *p, const double *zS
         b[j] = j < np ? F->beta[j] : 0.0;
     }
     for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
-        double z = zS[i] + c[i];
+        double z = zv[i];
 #pragma unroll
         for (int j = 0; j < kM; ++j)
             if (j < np) z = fma(-b[j], P[j][i], z);
@@ -433,6 +463,9 @@ fcm_status fcg_ensure(fcm_ctx *C)
         return e == cudaErrorMemoryAllocation ? FCM_ENOMEM : FCM_ECUDA;
     };
     cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&F->side, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&F->ev_r, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&F->ev_c, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&F->ring, sizeof(double) * 2 * kM * F->n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&F->c, sizeof(double) * F->n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&F->partial, sizeof(double) * kM * 152 * 8)) != cudaSuccess) return fail(e);
@@ -448,7 +481,7 @@ fcm_status fcg_ensure(fcm_ctx *C)
     return FCM_OK;
 }
 
-// c = P y, y ~ K_H^-1 R r (see the file comment); every launch is stream-ordered and capturable
+// z += P y, y ~ K_H^-1 R r (see the file comment); every launch is stream-ordered and capturable
 fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
 {
     FcgState *F = C->fcg;
@@ -470,7 +503,9 @@ fcm_status coarse_correction(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
         restrict_kernel<<<nblk(ncell), 256, 0, st>>>(C->d_r, C->d_mask, C->d_eta, F->f, C->g, C->p, 1.0f, 0, ncell, stop);
         coarse_solve(C, F->f, F->cout, iters, 0, stop);
     }
-    prolong_kernel<<<nblk(C->nlat / 3), 256, 0, st>>>(F->cout, C->d_mask, F->c, C->g, C->p, 1.0, C->nlat / 3, stop);
+    // z = zS + P y in place (zS's norm has been taken for the convergence test)
+    const int64_t nv = (int64_t)(C->g.n[0] + 1) * (C->g.n[1] + 1) * (C->g.n[2] + 1);
+    prolong_add_kernel<<<nblk(nv), 256, 0, st>>>(F->cout, C->d_mask, C->d_z, C->g, C->p, stop);
     return FCM_OK;
 }
 
@@ -485,12 +520,29 @@ fcm_status fcg_iteration(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
     ctx_apply_K_flag(C, C->d_p, C->d_q, stop);
     fk_pq_kernel<<<rb, RT, 0, st>>>(C->d_p, C->d_q, C->d_r, F->ring, n, F->partial, F->counter, F->d);
     fk_xr_kernel<<<rb, RT, 0, st>>>(C->d_x, C->d_r, C->d_p, C->d_q, n, F->d);
-    ctx_apply_S_flag(C, C->d_r, C->d_z, stop);
-    fk_conv_kernel<<<rb, RT, 0, st>>>(C->d_z, n, F->partial, F->counter, F->d);
-    fcm_status s = coarse_correction(C, net, gamma, iters);
-    if (s != FCM_OK) return s;
-    fk_dots_kernel<<<rb, RT, 0, st>>>(C->d_z, F->c, F->ring, n, F->partial, F->counter, F->d);
-    fk_newp_kernel<<<rb, RT, 0, st>>>(C->d_p, C->d_z, F->c, F->ring, n, F->d);
+    if (!net) {
+        // R r and the coarse solve on the side stream while the Schwarz apply streams its factors; both
+        // only read r, and they share no scratch (separate reduction buffers)
+        const int64_t ncell = F->ncell;
+        CO_CUDA(C, cudaEventRecord(F->ev_r, st));
+        CO_CUDA(C, cudaStreamWaitEvent(F->side, F->ev_r, 0));
+        restrict_kernel<<<nblk(ncell), 256, 0, F->side>>>(C->d_r, C->d_mask, C->d_eta, F->f, C->g, C->p, 1.0f, 0, ncell,
+                                                          stop);
+        coarse_solve(C, F->f, F->cout, iters, 0, stop, F->side);
+        CO_CUDA(C, cudaEventRecord(F->ev_c, F->side));
+        ctx_apply_S_flag(C, C->d_r, C->d_z, stop);
+        fk_conv_kernel<<<rb, RT, 0, st>>>(C->d_z, n, F->partial, F->counter, F->d);
+        CO_CUDA(C, cudaStreamWaitEvent(st, F->ev_c, 0));
+        const int64_t nv = (int64_t)(C->g.n[0] + 1) * (C->g.n[1] + 1) * (C->g.n[2] + 1);
+        prolong_add_kernel<<<nblk(nv), 256, 0, st>>>(F->cout, C->d_mask, C->d_z, C->g, C->p, stop);
+    } else {
+        ctx_apply_S_flag(C, C->d_r, C->d_z, stop);
+        fk_conv_kernel<<<rb, RT, 0, st>>>(C->d_z, n, F->partial, F->counter, F->d);
+        fcm_status s = coarse_correction(C, net, gamma, iters);
+        if (s != FCM_OK) return s;
+    }
+    fk_dots_kernel<<<rb, RT, 0, st>>>(C->d_z, F->ring, n, F->partial, F->counter, F->d);
+    fk_newp_kernel<<<rb, RT, 0, st>>>(C->d_p, C->d_z, F->ring, n, F->d);
     return FCM_OK;
 }
 
@@ -620,9 +672,9 @@ fcm_status fcm_fpcg_solve(fcm_ctx *C, fcm_unet *net, double gamma, int coarse_it
     CO_CUDA(C, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     ctx_apply_S_flag(C, r, zS, nullptr);
     fk_first_kernel<<<C->red_blocks, RT, 0, st>>>(zS, n, F->partial, F->counter, F->d);
-    // first direction p = S r + c (also the warm-up of the network's buffers before any capture)
+    // first direction p = S r + P y (also the warm-up of the network's buffers before any capture)
     if ((s = coarse_correction(C, net, gamma, coarse_iters)) != FCM_OK) return s;
-    fk_newp_kernel<<<C->red_blocks, RT, 0, st>>>(C->d_p, zS, F->c, F->ring, n, F->d);
+    fk_newp_kernel<<<C->red_blocks, RT, 0, st>>>(C->d_p, zS, F->ring, n, F->d);
     CO_CUDA(C, cudaGetLastError());
     if ((s = fcg_graph(C, net, gamma, coarse_iters)) != FCM_OK) return s;
     for (;;) {

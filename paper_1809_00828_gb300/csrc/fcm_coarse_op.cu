@@ -23,6 +23,7 @@
 // 74 MB stay in L2 across the steps of a coarse solve.  Every kernel returns at
 // once when the device flag `stop` (may be null) is set, so the solve can be
 // captured in a CUDA graph that runs past the end of the outer iteration.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
@@ -60,6 +61,11 @@ struct CoarseOp {
     unsigned *counter = nullptr;
     double *sc = nullptr;    // rz, pq, alpha, beta, t
     double seconds = 0.0;    // assembly time
+    // K_H stored in scaled FP16 (fcm_coarse_set_storage): K~_cj = s_c K_cj s_j, s_c = (tr K_cc / 3)^-1/2
+    __half *KH16 = nullptr;
+    float *scale = nullptr, *iscale = nullptr;  // s and 1 / s
+    bool use_half = false;   // KH16 in use (the storage chosen at the last coarse_ensure)
+    Grid3 g{};               // the cell grid of K_H
     // multigrid hierarchy (built on first use of the V-cycle preconditioner)
     int nlev = 0;
     MgLevel lev[kMaxLevels];
@@ -225,12 +231,22 @@ __device__ bool grid_sums2(double &x, double &y, double *partial, unsigned *coun
 //   mode 2: v = x;                          v is written to pout; pq = v.y, alpha = rz / pq
 //   mode 3: y = xb - K_H x                  (residual of K_H x = xb)
 //   mode 4: pout = x + omega Dinv (xb - K_H x)  (one damped block-Jacobi step; pout must not alias x)
-__global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, const float *__restrict__ x,
+//
+// T = __half: the blocks are stored symmetrically scaled, K~_cj = s_c K_cj s_j, so that every stored
+// value is O(1) and FP16 keeps 11 significant bits; K_H x = S^-1 K~ S^-1 x, so the kernel multiplies the
+// vector values by `scale` = 1 / s before the product and the result by 1 / s_c after it.
+__device__ __forceinline__ float ldk(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldk(const __half *p) { return __half2float(__ldg(p)); }
+
+template <class T>
+__global__ void __launch_bounds__(RT) kh_kernel(const T *__restrict__ KH, const float *__restrict__ x,
                                                  const float *__restrict__ xb, float *__restrict__ pout,
                                                  float *__restrict__ y, Grid3 g, int64_t ncell, int mode,
                                                  double *partial, unsigned *counter, double *sc, const int *stop,
-                                                 const float *__restrict__ Dinv = nullptr, float omega = 0.f)
+                                                 const float *__restrict__ Dinv = nullptr, float omega = 0.f,
+                                                 const float *__restrict__ scale = nullptr)
 {
+    constexpr bool kScaled = sizeof(T) == 2;
     STOP_RETURN;
     __shared__ float red[kTileWarps][3][kTileCells];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -258,8 +274,8 @@ __global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, co
             const bool vm = s > 0 && ((mx >> (2 - dx)) & (my >> (2 - dy)) & (mz >> (2 - dz)) & 1u);
             const int64_t n = vd ? c + d : c, m = vm ? c - d : c;
             const float wd = vd ? 1.f : 0.f, wm = vm ? 1.f : 0.f;
-            const float *Bc = KH + (int64_t)s * 9 * ncell + c;
-            const float *Bm = KH + (int64_t)s * 9 * ncell + m;
+            const T *Bc = KH + (int64_t)s * 9 * ncell + c;
+            const T *Bm = KH + (int64_t)s * 9 * ncell + m;
             float u0 = __ldg(x + n), u1 = __ldg(x + ncell + n), u2 = __ldg(x + 2 * ncell + n);
             float v0 = __ldg(x + m), v1 = __ldg(x + ncell + m), v2 = __ldg(x + 2 * ncell + m);
             if (mode == 1) {
@@ -270,18 +286,23 @@ __global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, co
                 v1 = fmaf(beta, __ldg(xb + ncell + m), v1);
                 v2 = fmaf(beta, __ldg(xb + 2 * ncell + m), v2);
             }
-            u0 *= wd;
-            u1 *= wd;
-            u2 *= wd;
-            v0 *= wm;
-            v1 *= wm;
-            v2 *= wm;
-            a0 = fmaf(__ldg(Bc), u0, fmaf(__ldg(Bc + ncell), u1, fmaf(__ldg(Bc + 2 * ncell), u2, a0)));
-            a1 = fmaf(__ldg(Bc + 3 * ncell), u0, fmaf(__ldg(Bc + 4 * ncell), u1, fmaf(__ldg(Bc + 5 * ncell), u2, a1)));
-            a2 = fmaf(__ldg(Bc + 6 * ncell), u0, fmaf(__ldg(Bc + 7 * ncell), u1, fmaf(__ldg(Bc + 8 * ncell), u2, a2)));
-            a0 = fmaf(__ldg(Bm), v0, fmaf(__ldg(Bm + 3 * ncell), v1, fmaf(__ldg(Bm + 6 * ncell), v2, a0)));
-            a1 = fmaf(__ldg(Bm + ncell), v0, fmaf(__ldg(Bm + 4 * ncell), v1, fmaf(__ldg(Bm + 7 * ncell), v2, a1)));
-            a2 = fmaf(__ldg(Bm + 2 * ncell), v0, fmaf(__ldg(Bm + 5 * ncell), v1, fmaf(__ldg(Bm + 8 * ncell), v2, a2)));
+            float sd = wd, sm = wm;
+            if constexpr (kScaled) {
+                sd *= __ldg(scale + n);
+                sm *= __ldg(scale + m);
+            }
+            u0 *= sd;
+            u1 *= sd;
+            u2 *= sd;
+            v0 *= sm;
+            v1 *= sm;
+            v2 *= sm;
+            a0 = fmaf(ldk(Bc), u0, fmaf(ldk(Bc + ncell), u1, fmaf(ldk(Bc + 2 * ncell), u2, a0)));
+            a1 = fmaf(ldk(Bc + 3 * ncell), u0, fmaf(ldk(Bc + 4 * ncell), u1, fmaf(ldk(Bc + 5 * ncell), u2, a1)));
+            a2 = fmaf(ldk(Bc + 6 * ncell), u0, fmaf(ldk(Bc + 7 * ncell), u1, fmaf(ldk(Bc + 8 * ncell), u2, a2)));
+            a0 = fmaf(ldk(Bm), v0, fmaf(ldk(Bm + 3 * ncell), v1, fmaf(ldk(Bm + 6 * ncell), v2, a0)));
+            a1 = fmaf(ldk(Bm + ncell), v0, fmaf(ldk(Bm + 4 * ncell), v1, fmaf(ldk(Bm + 7 * ncell), v2, a1)));
+            a2 = fmaf(ldk(Bm + 2 * ncell), v0, fmaf(ldk(Bm + 5 * ncell), v1, fmaf(ldk(Bm + 8 * ncell), v2, a2)));
         }
     }
     red[w][0][lane] = a0;
@@ -291,12 +312,13 @@ __global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, co
     if (mode >= 3) {
         if (w == 0 && live) {
             float res[3];
+            const float sc_c = kScaled ? scale[c] : 1.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < kTileWarps; ++k) acc += red[k][a][lane];
-                res[a] = xb[a * ncell + c] - acc;
+                res[a] = xb[a * ncell + c] - sc_c * acc;
             }
             if (mode == 3) {
 #pragma unroll
@@ -318,6 +340,7 @@ __global__ void __launch_bounds__(RT) kh_kernel(const float *__restrict__ KH, co
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < kTileWarps; ++k) acc += red[k][w][lane];
+        if (kScaled) acc *= scale[c];
         if (live) {
             y[w * ncell + c] = acc;
             if (mode != 0) {
@@ -664,7 +687,49 @@ __global__ void __launch_bounds__(RT) rz_kernel(const float *r, const float *z, 
     sc[0] = a;
 }
 
+// s_c = (tr K_cc / 3)^-1/2 from the centre block, and 1 / s_c (both 0 where the trace is 0)
+__global__ void kh_scale_kernel(const float *__restrict__ KH, float *__restrict__ scale, float *__restrict__ iscale,
+                                int64_t ncell)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const double tr = (double)KH[c] + (double)KH[4 * ncell + c] + (double)KH[8 * ncell + c];
+        scale[c] = tr > 0.0 ? (float)(1.0 / sqrt(tr / 3.0)) : 0.f;
+        iscale[c] = tr > 0.0 ? (float)sqrt(tr / 3.0) : 0.f;
+    }
+}
+
+// K~ = s K s in FP16, rounded to nearest; a block whose column cell lies outside the grid is 0
+__global__ void kh_to_half_kernel(const float *__restrict__ KH, const float *__restrict__ scale,
+                                  __half *__restrict__ KH16, Grid3 g, int64_t ncell)
+{
+    const int64_t total = ncell * kStored * 9;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % ncell;
+        const int s = (int)(t / ncell / 9), oi = kCenter + s;
+        const int cx = (int)(c % g.n[0]) + oi % 5 - 2, cy = (int)((c / g.n[0]) % g.n[1]) + (oi / 5) % 5 - 2,
+                  cz = (int)(c / ((int64_t)g.n[0] * g.n[1])) + oi / 25 - 2;
+        float v = 0.f;
+        if (cx >= 0 && cy >= 0 && cz >= 0 && cx < g.n[0] && cy < g.n[1] && cz < g.n[2]) {
+            const int64_t j = cx + (int64_t)g.n[0] * (cy + (int64_t)g.n[1] * cz);
+            v = KH[t] * scale[c] * scale[j];
+        }
+        KH16[t] = __float2half_rn(v);
+    }
+}
+
 int tiles(int64_t ncell) { return (int)((ncell + kTileCells - 1) / kTileCells); }
+
+// K_H apply on the cell grid of K_H in the stored precision: FP32, or the scaled FP16 copy when in use
+void kh0(const CoarseOp *op, const float *x, const float *xb, float *pout, float *y, int mode, cudaStream_t st,
+         const int *stop, const float *Dinv = nullptr, float omega = 0.f)
+{
+    if (op->use_half)
+        kh_kernel<__half><<<tiles(op->ncell), RT, 0, st>>>(op->KH16, x, xb, pout, y, op->g, op->ncell, mode, op->partial,
+                                                           op->counter, op->sc, stop, Dinv, omega, op->iscale);
+    else
+        kh_kernel<float><<<tiles(op->ncell), RT, 0, st>>>(op->KH, x, xb, pout, y, op->g, op->ncell, mode, op->partial,
+                                                          op->counter, op->sc, stop, Dinv, omega);
+}
 
 }  // namespace
 
@@ -675,15 +740,46 @@ void mg_free_levels(CoarseOp *op);
 void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int *stop, bool hybrid);
 }  // namespace
 
+namespace {
+// the scaled FP16 copy of K_H (outside any capture), or FCM_ENOMEM
+fcm_status half_build(fcm_ctx *C)
+{
+    CoarseOp *op = C->coarse;
+    const int64_t nc = op->ncell;
+    cudaError_t e;
+    if ((e = cudaMalloc(&op->scale, sizeof(float) * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&op->iscale, sizeof(float) * nc)) != cudaSuccess ||
+        (e = cudaMalloc(&op->KH16, sizeof(__half) * (size_t)nc * kStored * 9)) != cudaSuccess) {
+        if (op->scale) cudaFree(op->scale);
+        if (op->iscale) cudaFree(op->iscale);
+        op->scale = op->iscale = nullptr;
+        op->KH16 = nullptr;
+        C->err = std::string("coarse operator FP16 copy: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? FCM_ENOMEM : FCM_ECUDA;
+    }
+    kh_scale_kernel<<<nb(nc), 256, 0, C->stream>>>(op->KH, op->scale, op->iscale, nc);
+    kh_to_half_kernel<<<nb(nc * kStored * 9), 256, 0, C->stream>>>(op->KH, op->scale, op->KH16, op->g, nc);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        C->err = std::string("coarse operator FP16 copy: ") + cudaGetErrorString(e);
+        return FCM_ECUDA;
+    }
+    return FCM_OK;
+}
+}  // namespace
+
 fcm_status coarse_ensure(fcm_ctx *C)
 {
     if (C->coarse) {
-        if (C->coarse_prec != FCM_COARSE_JACOBI && C->coarse->nlev == 0) return mg_build(C);
-        return FCM_OK;
+        fcm_status s = FCM_OK;
+        if (C->coarse_half && !C->coarse->KH16) s = half_build(C);
+        C->coarse->use_half = C->coarse_half && C->coarse->KH16;
+        if (s == FCM_OK && C->coarse_prec != FCM_COARSE_JACOBI && C->coarse->nlev == 0) s = mg_build(C);
+        return s;
     }
     const int64_t ncell = C->hp.ncells, n3 = 3 * ncell;
     CoarseOp *op = new CoarseOp();
     op->ncell = ncell;
+    op->g = C->g;
     auto fail = [&](cudaError_t e) {
         C->err = std::string("coarse operator: ") + cudaGetErrorString(e);
         coarse_free(op);
@@ -732,14 +828,16 @@ fcm_status coarse_ensure(fcm_ctx *C)
     cudaFree(ecell);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return fail(e);
     C->coarse = op;
-    if (C->coarse_prec != FCM_COARSE_JACOBI) return mg_build(C);
-    return FCM_OK;
+    return coarse_ensure(C);  // the FP16 copy and the hierarchy, where asked for
 }
 
 void coarse_free(CoarseOp *op)
 {
     if (!op) return;
     mg_free_levels(op);
+    if (op->KH16) cudaFree(op->KH16);
+    if (op->scale) cudaFree(op->scale);
+    if (op->iscale) cudaFree(op->iscale);
     void *ps[] = {op->KH, op->Dinv, op->r, op->z, op->q, op->p[0], op->p[1], op->partial, op->counter, op->sc};
     for (void *q : ps)
         if (q) cudaFree(q);
@@ -959,8 +1057,11 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
         MgLevel &v = op->lev[l];
         const float *f = l == 0 ? f0 : v.f;
         jacobi0_kernel<<<nb(v.ncell), RT, 0, st>>>(f, v.Dinv, v.omega, v.xa, v.ncell, stop);
-        kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, nullptr, v.r, v.g, v.ncell, 3, op->partial, op->counter,
-                                                 op->sc, stop);
+        if (l == 0)
+            kh0(op, v.xa, f, nullptr, v.r, 3, st, stop);
+        else
+            kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, nullptr, v.r, v.g, v.ncell, 3, op->partial,
+                                                     op->counter, op->sc, stop);
         mg_restrict_kernel<<<nb(op->lev[l + 1].ncell), RT, 0, st>>>(v.r, op->lev[l + 1].f, dims_down(v, op->lev[l + 1]),
                                                                     stop);
     }
@@ -971,8 +1072,11 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
         const float *f = l == 0 ? f0 : v.f;
         float *out = l == 0 ? x0 : v.x;
         mg_interp_kernel<<<nb(v.ncell), RT, 0, st>>>(op->lev[l + 1].x, v.xa, dims_down(v, op->lev[l + 1]), 1, stop);
-        kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, out, nullptr, v.g, v.ncell, 4, op->partial, op->counter,
-                                                 op->sc, stop, v.Dinv, v.omega);
+        if (l == 0)
+            kh0(op, v.xa, f, out, nullptr, 4, st, stop, v.Dinv, v.omega);
+        else
+            kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, out, nullptr, v.g, v.ncell, 4, op->partial,
+                                                     op->counter, op->sc, stop, v.Dinv, v.omega);
     }
     if (hybrid)
         mg_interp_kernel<<<nb(op->lev[0].ncell), RT, 0, st>>>(op->lev[1].x, x0, dims_down(op->lev[0], op->lev[1]), 1,
@@ -988,16 +1092,15 @@ double coarse_seconds(const CoarseOp *op) { return op ? op->seconds : 0.0; }
 // energy-minimising step); asynchronous on the context's stream, capturable.  Two launches
 // per step: the K_H apply (which also forms the new direction and alpha) and the update
 // (which also applies Dinv and forms beta).
-void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, const int *stop)
+void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, const int *stop, cudaStream_t st)
 {
     CoarseOp *op = C->coarse;
     const int64_t n3 = 3 * op->ncell, nc = op->ncell;
-    cudaStream_t st = C->stream;
+    if (!st) st = C->stream;
     const bool mg = C->coarse_prec != FCM_COARSE_JACOBI && op->nlev > 0;
     const bool hybrid = C->coarse_prec == FCM_COARSE_HYBRID;
     if (start != 0)
-        kh_kernel<<<tiles(nc), RT, 0, st>>>(op->KH, y, nullptr, nullptr, op->q, C->g, nc, 0, op->partial, op->counter,
-                                            op->sc, stop);
+        kh0(op, y, nullptr, nullptr, op->q, 0, st, stop);
     if (start == 2) line_kernel<<<nb(n3), RT, 0, st>>>(f, y, op->q, n3, op->partial, op->counter, op->sc, stop);
     cstart_kernel<<<nb(nc), RT, 0, st>>>(f, y, op->r, op->z, op->q, op->Dinv, nc, start, !mg && iters > 0 ? 1 : 0,
                                          op->partial, op->counter, op->sc, stop);
@@ -1009,8 +1112,7 @@ void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, co
         float *pn = op->p[i & 1];
         const float *po = op->p[(i + 1) & 1];
         const bool last = i + 1 == iters;
-        kh_kernel<<<tiles(nc), RT, 0, st>>>(op->KH, op->z, i == 0 ? nullptr : po, pn, op->q, C->g, nc, i == 0 ? 2 : 1,
-                                            op->partial, op->counter, op->sc, stop);
+        kh0(op, op->z, i == 0 ? nullptr : po, pn, op->q, i == 0 ? 2 : 1, st, stop);
         // with the V-cycle the update kernel only moves y and r; z and beta follow from the cycle
         cupd_kernel<<<nb(nc), RT, 0, st>>>(y, op->r, op->z, pn, op->q, op->Dinv, nc, last || mg ? 1 : 0, op->partial,
                                            op->counter, op->sc, stop);
@@ -1024,8 +1126,7 @@ void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, co
 void coarse_apply(fcm_ctx *C, const float *x, float *y)
 {
     CoarseOp *op = C->coarse;
-    kh_kernel<<<tiles(op->ncell), RT, 0, C->stream>>>(op->KH, x, nullptr, nullptr, y, C->g, op->ncell, 0, op->partial,
-                                                      op->counter, op->sc, nullptr);
+    kh0(op, x, nullptr, nullptr, y, 0, C->stream, nullptr);
 }
 
 }  // namespace fcm
@@ -1088,6 +1189,19 @@ extern "C" fcm_status fcm_coarse_set_preconditioner(fcm_ctx *C, int kind)
     }
     if (kind != C->coarse_prec) fcm::fcg_forget_graph(C->fcg);
     C->coarse_prec = kind;
+    return FCM_OK;
+}
+
+extern "C" fcm_status fcm_coarse_set_storage(fcm_ctx *C, int storage)
+{
+    if (!C) return FCM_EINVAL;
+    if (storage != FCM_COARSE_STORE_FP32 && storage != FCM_COARSE_STORE_FP16) {
+        C->err = "fcm_coarse_set_storage: storage must be FCM_COARSE_STORE_FP32 or FCM_COARSE_STORE_FP16";
+        return FCM_EINVAL;
+    }
+    const int half = storage == FCM_COARSE_STORE_FP16;
+    if (half != C->coarse_half) fcm::fcg_forget_graph(C->fcg);
+    C->coarse_half = half;
     return FCM_OK;
 }
 

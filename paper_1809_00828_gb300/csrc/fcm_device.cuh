@@ -178,7 +178,9 @@ struct CoarseOp;
 fcm_status coarse_ensure(fcm_ctx *C);
 void coarse_free(CoarseOp *op);
 // start: 0 from zero, 1 from the given y, 2 from the given y scaled by the energy-minimising step
-void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, const int *stop);
+// st: the stream to run on (null: the context's work stream)
+void coarse_solve(fcm_ctx *C, const float *f, float *y, int iters, int start, const int *stop,
+                  cudaStream_t st = nullptr);
 void coarse_apply(fcm_ctx *C, const float *x, float *y);
 double coarse_seconds(const CoarseOp *op);
 
@@ -266,5 +268,6 @@ struct fcm_ctx {
     // coarse operator of the learned correction (built on first use)
     fcm::CoarseOp *coarse = nullptr;
     int coarse_prec = FCM_COARSE_JACOBI;  // fcm_coarse_set_preconditioner
+    int coarse_half = 0;                  // fcm_coarse_set_storage
     fcm::FcgState *fcg = nullptr;
 };

@@ -7,6 +7,9 @@
 //     into a slot of its own (one CTA per 32 rows of a block: gather r_B into shared memory, a warp per
 //     row reading the factor row coalesced), then one thread per DOF adds the diagonal part and the
 //     slots of the blocks containing it, in block order (no colours, no atomics, a fixed order);
+//   - K values and factors are stored as float pairs (8 B, as FP64) and both products run in
+//     double-float arithmetic on the FP32 pipe, each result within ~2^-44 of the sum of the products'
+//     magnitudes, leaving the FP64 pipe one add per row;
 //   - PCG with x0 = 0, stopped on ||S r_i|| / ||S b|| <= tol (Eq. (14)), with the uniform grid's fused
 //     CG kernels: every scalar stays on the device (deterministic two-level reductions), eight
 //     iterations are captured in one CUDA graph, and the host polls the scalars once per graph.
@@ -21,6 +24,7 @@
 #include <vector>
 
 #include "fcm_device.cuh"
+#include "fcm_ff.cuh"
 
 namespace fcm {
 
@@ -28,53 +32,75 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double warp_sum(double v)
+// (S, C) summed over the warp, every lane holding the result (ff_add is symmetric in its operands)
+__device__ __forceinline__ void ff_warp_sum(float &S, float &C)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float S2 = __shfl_xor_sync(0xffffffffu, S, o), C2 = __shfl_xor_sync(0xffffffffu, C, o);
+        ff_add(S, C, S2, C2);
+    }
 }
 
+// x2 = x as float pairs (split by integer operations), once per product instead of once per nonzero
+__global__ void __launch_bounds__(kThreads) mlhp_split_kernel(int n, const double *__restrict__ x,
+                                                              float2 *__restrict__ x2, const int *done)
+{
+    if (done && *done) return;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) x2[i] = split_ff(x[i]);
+}
+
+// y = K x, a warp per CSR row.  The values are stored as float pairs (hi, lo; |v - hi - lo| <= 2^-48 |v|),
+// x arrives split (mlhp_split_kernel), and every product and sum runs in double-float arithmetic on the
+// FP32 pipe (GB300's FP64 pipe does 2 operations per clock per SM; a FP64 multiply-add per nonzero plus
+// the row reductions kept it busy 77 % of the time).  One FP64 add per row.
 __global__ void __launch_bounds__(kThreads) mlhp_spmv_kernel(int n, const int64_t *__restrict__ rowptr,
                                                              const int *__restrict__ cols,
-                                                             const double *__restrict__ vals,
-                                                             const double *__restrict__ x, double *__restrict__ y,
+                                                             const float2 *__restrict__ vals,
+                                                             const float2 *__restrict__ x, double *__restrict__ y,
                                                              const int *done)
 {
     if (done && *done) return;
     const int row = (int)((blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;  // uniform across the warp
-    double s = 0.0;
-    for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) s += vals[e] * x[cols[e]];
-    s = warp_sum(s);
-    if (lane == 0) y[row] = s;
+    float S = 0.f, C = 0.f;
+    const int64_t e1 = rowptr[row + 1];
+#pragma unroll 4
+    for (int64_t e = rowptr[row] + lane; e < e1; e += 32) {
+        const float2 v = __ldcs(vals + e);
+        const float2 xv = x[cols[e]];
+        ff_fma(v.x, v.y, xv.x, xv.y, S, C);
+    }
+    ff_warp_sum(S, C);
+    if (lane == 0) y[row] = ff_to_double(ff_norm(S, C));
 }
 
 // Zb[o_B + i] = (A_B^+ r_B)_i for the rows i of item (block, first row): a CTA per 32 rows of a block.
+// Factors as float pairs, r_B split once into shared memory, double-float products and sums.
 constexpr int kRowsPerCta = 32;
 
 __global__ void __launch_bounds__(kThreads) mlhp_block_rows_kernel(const int2 *__restrict__ items,
                                                                    const int64_t *__restrict__ bptr,
                                                                    const int *__restrict__ bdofs,
                                                                    const int64_t *__restrict__ fptr,
-                                                                   const double *__restrict__ fac,
+                                                                   const float2 *__restrict__ fac,
                                                                    const double *__restrict__ r,
                                                                    double *__restrict__ zb, const int *done)
 {
     if (done && *done) return;
-    extern __shared__ double rb[];
+    extern __shared__ float2 rb[];
     const int2 it = items[blockIdx.x];
     const int64_t o = bptr[it.x];
     const int m = (int)(bptr[it.x + 1] - o);
-    const double *F = fac + fptr[it.x];
-    for (int j = threadIdx.x; j < m; j += kThreads) rb[j] = r[bdofs[o + j]];
+    const float2 *F = fac + fptr[it.x];
+    for (int j = threadIdx.x; j < m; j += kThreads) rb[j] = split_ff(r[bdofs[o + j]]);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // the warp's four rows it.y + warp + 8 t at once: four independent streams of factor loads in flight
     constexpr int kRowsPerWarp = kRowsPerCta / (kThreads / 32);
     const int row_end = min(m, it.y + kRowsPerCta);
-    const double *Fi[kRowsPerWarp];
+    const float2 *Fi[kRowsPerWarp];
     bool on[kRowsPerWarp];
 #pragma unroll
     for (int t = 0; t < kRowsPerWarp; ++t) {
@@ -82,17 +108,21 @@ __global__ void __launch_bounds__(kThreads) mlhp_block_rows_kernel(const int2 *_
         on[t] = i < row_end;  // warp-uniform
         Fi[t] = F + (int64_t)(on[t] ? i : it.y) * m;
     }
-    double s[kRowsPerWarp] = {};
+    float S[kRowsPerWarp] = {}, C[kRowsPerWarp] = {};
+#pragma unroll 2
     for (int j = lane; j < m; j += 32) {
-        const double rj = rb[j];
+        const float2 rj = rb[j];
 #pragma unroll
         for (int t = 0; t < kRowsPerWarp; ++t)
-            if (on[t]) s[t] = fma(__ldcs(Fi[t] + j), rj, s[t]);
+            if (on[t]) {
+                const float2 f = __ldcs(Fi[t] + j);
+                ff_fma(f.x, f.y, rj.x, rj.y, S[t], C[t]);
+            }
     }
 #pragma unroll
     for (int t = 0; t < kRowsPerWarp; ++t) {
-        const double v = warp_sum(s[t]);
-        if (on[t] && lane == 0) zb[o + it.y + warp + t * (kThreads / 32)] = v;
+        ff_warp_sum(S[t], C[t]);
+        if (on[t] && lane == 0) zb[o + it.y + warp + t * (kThreads / 32)] = ff_to_double(ff_norm(S[t], C[t]));
     }
 }
 
@@ -132,7 +162,9 @@ struct MlhpDevice {
     int64_t *rowptr = nullptr, *bptr = nullptr, *fptr = nullptr, *occ_ptr = nullptr;
     int *cols = nullptr, *bdofs = nullptr, *occ = nullptr;
     int2 *items = nullptr;
-    double *vals = nullptr, *fac = nullptr, *jac = nullptr, *zb = nullptr;
+    float2 *vals = nullptr, *fac = nullptr;  // K values and factors as float pairs
+    float2 *x2 = nullptr;                    // the K apply's input as float pairs
+    double *jac = nullptr, *zb = nullptr;
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *partial = nullptr;
     unsigned *counter = nullptr;
     CgScalars *s = nullptr, *hs = nullptr;  // device scalars, pinned host copy
@@ -147,7 +179,8 @@ void mlhp_device_destroy(MlhpDevice *d)
     for (void *ptr : {(void *)d->rowptr, (void *)d->bptr, (void *)d->fptr, (void *)d->occ_ptr, (void *)d->cols,
                       (void *)d->bdofs, (void *)d->occ, (void *)d->items, (void *)d->vals, (void *)d->fac,
                       (void *)d->jac, (void *)d->zb, (void *)d->x, (void *)d->r, (void *)d->z, (void *)d->p,
-                      (void *)d->q, (void *)d->b, (void *)d->partial, (void *)d->counter, (void *)d->s})
+                      (void *)d->q, (void *)d->b, (void *)d->partial, (void *)d->counter, (void *)d->s,
+                      (void *)d->x2})
         if (ptr) cudaFree(ptr);
     if (d->hs) cudaFreeHost(d->hs);
     if (d->ev_a) cudaEventDestroy(d->ev_a);
@@ -217,18 +250,30 @@ std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, c
         (e = cudaEventCreateWithFlags(&d->ev_a, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&d->ev_b, cudaEventDisableTiming)) != cudaSuccess)
         return fail(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    // float pairs: hi = fl32(v), lo = fl32(v - hi), so |v - hi - lo| <= 2^-48 |v|
+    auto pairs = [](const double *v, int64_t cnt) {
+        std::vector<float2> out((size_t)cnt);
+        for (int64_t i = 0; i < cnt; ++i) {
+            const float h = (float)v[i];
+            out[(size_t)i] = make_float2(h, (float)(v[i] - (double)h));
+        }
+        return out;
+    };
+    const std::vector<float2> vals2 = pairs(vals, nnz), fac2 = pairs(fac, fptr[nblocks]);
     if ((e = upload(&d->rowptr, rowptr, (size_t)n + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->cols, cols32.data(), cols32.size(), d->st)) != cudaSuccess ||
-        (e = upload(&d->vals, vals, (size_t)nnz, d->st)) != cudaSuccess ||
+        (e = upload(&d->vals, vals2.data(), vals2.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->bptr, bptr, (size_t)nblocks + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->bdofs, bdofs32.data(), bdofs32.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->fptr, fptr, (size_t)nblocks + 1, d->st)) != cudaSuccess ||
-        (e = upload(&d->fac, fac, (size_t)fptr[nblocks], d->st)) != cudaSuccess ||
+        (e = upload(&d->fac, fac2.data(), fac2.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->jac, jac, (size_t)n, d->st)) != cudaSuccess ||
         (e = upload(&d->items, items.data(), items.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->occ_ptr, occ_ptr.data(), occ_ptr.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->occ, occ.data(), occ.size(), d->st)) != cudaSuccess)
         return fail(std::string("upload: ") + cudaGetErrorString(e));
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&d->x2), (size_t)n * sizeof(float2))) != cudaSuccess)
+        return fail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
     if ((e = cudaMalloc(reinterpret_cast<void **>(&d->zb), std::max<int64_t>(nslots, 1) * sizeof(double))) != cudaSuccess)
         return fail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
     for (double **v : {&d->x, &d->r, &d->z, &d->p, &d->q, &d->b})
@@ -255,13 +300,14 @@ void apply_K(MlhpDevice *d, const double *x, double *y, const int *done, cudaStr
 {
     const int64_t warps_per_cta = kThreads / 32;
     const unsigned grid = (unsigned)((d->n + warps_per_cta - 1) / warps_per_cta);
-    mlhp_spmv_kernel<<<grid, kThreads, 0, st>>>(d->n, d->rowptr, d->cols, d->vals, x, y, done);
+    mlhp_split_kernel<<<d->grid_n, kThreads, 0, st>>>(d->n, x, d->x2, done);
+    mlhp_spmv_kernel<<<grid, kThreads, 0, st>>>(d->n, d->rowptr, d->cols, d->vals, d->x2, y, done);
 }
 
 void apply_S(MlhpDevice *d, const double *r, double *z, const int *done, cudaStream_t st)
 {
     if (d->nitems > 0)
-        mlhp_block_rows_kernel<<<d->nitems, kThreads, (size_t)d->max_block * sizeof(double), st>>>(
+        mlhp_block_rows_kernel<<<d->nitems, kThreads, (size_t)d->max_block * sizeof(float2), st>>>(
             d->items, d->bptr, d->bdofs, d->fptr, d->fac, r, d->zb, done);
     mlhp_sum_kernel<<<d->grid_n, kThreads, 0, st>>>(d->n, d->occ_ptr, d->occ, d->zb, d->jac, r, z, done);
 }

@@ -26,7 +26,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
             "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_unet_destroy", "fcm_coarse_restrict",
             "fcm_coarse_prolong", "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host",
-            "fcm_fpcg_set_stall_window", "fcm_coarse_set_preconditioner", "fcm_coarse_levels", "fcm_coarse_vcycle",
+            "fcm_fpcg_set_stall_window", "fcm_coarse_set_preconditioner", "fcm_coarse_set_storage", "fcm_coarse_levels",
+            "fcm_coarse_vcycle",
             "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size",
             "fcm_mlhp_system",
@@ -376,12 +377,13 @@ def _bind_unet(L):
                                       dp]
     L.fcm_fpcg_set_stall_window.argtypes = [P, ctypes.c_int]
     L.fcm_coarse_set_preconditioner.argtypes = [P, ctypes.c_int]
+    L.fcm_coarse_set_storage.argtypes = [P, ctypes.c_int]
     L.fcm_coarse_levels.argtypes = [P, ip, ip, dp, dp]
     L.fcm_coarse_vcycle.argtypes = [P, ctypes.c_int, P, P]
     for f in ("fcm_unet_create", "fcm_unet_params", "fcm_unet_get", "fcm_unet_set", "fcm_unet_forward",
               "fcm_unet_backward", "fcm_unet_zero_grad", "fcm_unet_adam", "fcm_coarse_restrict", "fcm_coarse_prolong",
               "fcm_coarse_apply", "fcm_fpcg_solve", "fcm_fpcg_solve_host", "fcm_fpcg_set_stall_window",
-              "fcm_coarse_set_preconditioner", "fcm_coarse_levels", "fcm_coarse_vcycle"):
+              "fcm_coarse_set_preconditioner", "fcm_coarse_set_storage", "fcm_coarse_levels", "fcm_coarse_vcycle"):
         getattr(L, f).restype = ctypes.c_int
     _unet_bound = True
 
@@ -540,6 +542,15 @@ def _solver_set_coarse_preconditioner(self, kind):
     self._check(load().fcm_coarse_set_preconditioner(self.ctx, COARSE_PREC[kind]))
 
 
+def _solver_set_coarse_storage(self, storage):
+    """Storage of K_H: "fp32" (default) or "fp16" (symmetrically scaled FP16, half the bytes per product)."""
+    _bind_unet(load())
+    kinds = {"fp32": 0, "fp16": 1}  # FCM_COARSE_STORE_FP32, FCM_COARSE_STORE_FP16
+    if storage not in kinds:
+        raise ValueError(f"coarse storage {storage!r}: expected 'fp32' or 'fp16'")
+    self._check(load().fcm_coarse_set_storage(self.ctx, kinds[storage]))
+
+
 def _solver_coarse_levels(self):
     """The multigrid hierarchy: {"levels": n, "dims": [(nx, ny, nz), ...], "lambda_max": [...], "seconds": s}."""
     _bind_unet(load())
@@ -569,6 +580,7 @@ def _solver_coarse_vcycle(self, f, out=None, kind="vcycle"):
 
 
 Solver.coarse_vcycle = _solver_coarse_vcycle
+Solver.set_coarse_storage = _solver_set_coarse_storage
 Solver.set_coarse_preconditioner = _solver_set_coarse_preconditioner
 Solver.coarse_levels = _solver_coarse_levels
 Solver.set_stall_window = _solver_set_stall_window

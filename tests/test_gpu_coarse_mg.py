@@ -235,3 +235,54 @@ def test_fpcg_with_vcycle_coarse_cg():
             s.set_coarse_preconditioner("amg")
     finally:
         s.close()
+
+
+def test_fp16_storage_of_the_coarse_operator():
+    """K_H stored as K~ = s K s in FP16 (s_c = (tr K_cc / 3)^-1/2).  Each stored entry is rounded once to
+    FP16: relative error <= 2^-11 above FP16's normal range, absolute <= 2^-25 (half the subnormal spacing)
+    below it, i.e. |K'_cj - K_cj| <= 2^-11 |K_cj| + 2^-25 / (s_c s_j); FP32 scaling and accumulation add
+    ~1e-6 relative.  So per cell row |y - K_H x| <= (2^-11 + 1e-5) (|K_H| |x|) + 2^-25 / s_c (B (|x| / s))
+    with B the block pattern.  Then the flexible PCG with the FP16 operator reaches the direct solution."""
+    from paper_1809_00828_gb300 import fcm
+    w = _workload("cube")
+    P = O.Problem.from_workload(w)
+    s = fcm.Solver(w)
+    try:
+        s.precond_build()
+        nc = int(np.prod(w.n))
+        Pf = _prolongation(w, P.free_lat)
+        KH = (Pf.T @ P.csr() @ Pf).tocsr()
+        d = KH.diagonal()
+        tr = d[:nc] + d[nc:2 * nc] + d[2 * nc:]
+        sc = np.where(tr > 0, 1.0 / np.sqrt(np.maximum(tr, 1e-300) / 3.0), 0.0)
+        s3 = np.concatenate([sc, sc, sc])
+        s.set_coarse_storage("fp16")
+        rng = np.random.default_rng(8)
+        for trial in range(2):
+            x = rng.standard_normal(3 * nc).astype(np.float32)
+            y = s.coarse_apply(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+            xd = x.astype(np.float64)
+            ref = KH @ xd
+            absK = abs(KH)
+            pattern = (absK > 0).astype(np.float64)
+            inv_s = np.where(s3 > 0, 1.0 / np.where(s3 > 0, s3, 1.0), 0.0)
+            bound = (2.0 ** -11 + 1e-5) * (absK @ np.abs(xd)) + 2.0 ** -25 * inv_s * (pattern @ (np.abs(xd) * inv_s))
+            assert (np.abs(y - ref) <= bound + 1e-30).all(), float(np.max(np.abs(y - ref) / (bound + 1e-30)))
+            # and FP16 is not FP32: the products do differ (the copy is in use)
+            if trial == 0:
+                s.set_coarse_storage("fp32")
+                y32 = s.coarse_apply(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+                assert np.abs(y32 - ref).max() <= 1e-5 * np.abs(ref).max()
+                assert np.abs(y - y32).max() > 0.0
+                s.set_coarse_storage("fp16")
+        s.set_coarse_preconditioner("vcycle")
+        b = s.rhs()
+        u, its, rel, st = s.fpcg_solve(None, 0.0, b, w.tol, 4000, coarse_iters=2)
+        assert st == 0 and rel <= w.tol * 1.0001
+        x_ref = spla.spsolve(P.csr().tocsc(), P.rhs())
+        assert P.energy_error(x_ref, u.cpu().numpy()[P.free_lat]) < 1e-6
+        print(f"flexible PCG, 2 V-cycle steps, FP16 K_H: {its} iterations")
+        with pytest.raises(ValueError):
+            s.set_coarse_storage("bf16")
+    finally:
+        s.close()
