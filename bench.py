@@ -643,8 +643,8 @@ def run_mlhp(args):
     centre refined `args.mlhp_k` times toward its surface, alpha = 1e-8, truncated blocks.  One JSON line:
     host set-up times, the device K and S applies (CUDA events on the plan's stream, median of 20 after 3
     warm-ups) with their algorithmic bytes and bandwidth, and the PCG solve to 1e-8.  Algorithmic bytes: K x
-    reads 12 B per CSR nonzero plus the row pointers and writes y; S r reads every factor entry once (8 B)
-    plus the gathers and the read-modify-write of z on the block DOFs."""
+    reads 12 B per CSR nonzero plus the row pointers and writes y; S r reads every stored factor byte once
+    (8 B per entry as a float pair, 4 B in FP32) plus the gathers and the block-row sums."""
     import numpy as np
     import torch
     from paper_1809_00828_gb300 import fcm
@@ -655,7 +655,8 @@ def run_mlhp(args):
     t1 = time.time()
     blocks, F, cptr, jac = P.factorize("truncated")
     t2 = time.time()
-    P.device_setup()
+    P.device_setup(precision=args.mlhp_precision)
+    n32, fbytes = P.device_info()
     n = len(free)
     x = torch.from_numpy(np.random.default_rng(1).standard_normal(n)).cuda()
     y = torch.empty_like(x)
@@ -678,8 +679,9 @@ def run_mlhp(args):
     ts = timed(lambda: P.apply_S(x, y))
     bk = 12 * K.nnz + 8 * (n + 1) + 16 * n
     nb_dofs = sum(len(B) for B in blocks)
-    bs = 8 * sum(len(B) ** 2 for B in blocks) + 4 * nb_dofs + 8 * nb_dofs * 3 + 24 * n
+    bs = fbytes + 4 * nb_dofs + 8 * nb_dofs * 3 + 24 * n
     bd = torch.from_numpy(b).cuda()
+    P.pcg_solve(bd, 1e-8, 20000, check=False)  # warm-up: captures the iteration graph
     torch.cuda.synchronize()
     t3 = time.time()
     _, its, _, status = P.pcg_solve(bd, 1e-8, 20000, check=False)
@@ -688,6 +690,7 @@ def run_mlhp(args):
     hbm = _peaks()[0]["hbm_gbs"]
     print(json.dumps({"workload": f"mlhp cube: 8^3 base cells, p=3, cavity r=0.01, k={args.mlhp_k}, truncated blocks",
                       "dofs": n, "nnz": int(K.nnz), "blocks": len(blocks), "colours": len(cptr) - 1,
+                      "precision": args.mlhp_precision, "fp32_blocks": n32, "factor_bytes": fbytes,
                       "assemble_s": round(t1 - t0, 2), "factorize_s": round(t2 - t1, 2),
                       "apply_K_ms": round(tk * 1e3, 4), "apply_K_GBs": round(bk / tk * 1e-9, 1),
                       "apply_K_frac": round(bk / tk * 1e-9 / hbm, 3),
@@ -712,7 +715,7 @@ def main():
                     help="coarse: flexible CG with the Galerkin coarse correction; pcg: plain Schwarz-PCG")
     ap.add_argument("--coarse-iters", type=int, default=None,
                     help="coarse CG steps per preconditioner apply (default: per workload, COARSE_DEFAULTS)")
-    ap.add_argument("--coarse-storage", default=None, choices=["fp32", "fp16"],
+    ap.add_argument("--coarse-storage", default=None, choices=["fp32", "fp16", "fp16_cycles"],
                     help="storage of K_H: FP32, or symmetrically scaled FP16 (default: per workload)")
     ap.add_argument("--coarse-prec", default=None, choices=["jacobi", "vcycle", "hybrid"],
                     help="preconditioner of the coarse CG: 3x3 diagonal blocks of K_H, or one V-cycle of the "
@@ -740,6 +743,8 @@ def main():
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="after the warm-up, run one step between cudaProfilerStart/Stop and exit (for ncu)")
+    ap.add_argument("--mlhp-precision", default="mixed", choices=["fp64", "mixed"],
+                    help="factor storage of the multi-level path (mixed: FP32 where cond <= 1e7)")
     ap.add_argument("--mlhp-k", type=int, default=None,
                     help="instead of the bench line: time the multi-level hp path on the Sec. 5.1 cube refined k times")
     args = ap.parse_args()

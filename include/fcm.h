@@ -378,10 +378,13 @@ fcm_status fcm_coarse_set_preconditioner(fcm_ctx *ctx, int kind);
  *     above 6e-5 and an absolute 3e-8 below: a perturbation of K_H of relative size ~5e-4 in the scaled
  *     norm, which the coarse part of the flexible CG's preconditioner tolerates; the copy halves the
  *     bytes of each product where K_H streams from HBM.
+ *   FCM_COARSE_STORE_FP16_CYCLES: the FP16 copy only in the V-cycle's residual and smoothing products on
+ *     the finest cell grid; the coarse CG's own products and fcm_coarse_apply stay FP32.
  * The FP16 copy is made on the next coarse call (FCM_ENOMEM if it does not fit); changing the storage
  * drops the flexible CG's captured graph.  FCM_EINVAL for another value. */
 #define FCM_COARSE_STORE_FP32 0
 #define FCM_COARSE_STORE_FP16 1
+#define FCM_COARSE_STORE_FP16_CYCLES 2
 fcm_status fcm_coarse_set_storage(fcm_ctx *ctx, int storage);
 
 /* The multigrid hierarchy after it is built: *levels (0 before), the cell grid of each level in
@@ -513,15 +516,27 @@ fcm_status fcm_mlhp_factors(const fcm_mlhp *plan, int64_t *blk_ptr, int64_t *blk
  * FCM_ESTATE); every index is checked on the host first (FCM_EINVAL).  The device arrays belong to the plan
  * until fcm_mlhp_destroy or the next assemble / factorize.  Work is queued on cuda_stream. */
 fcm_status fcm_mlhp_device_setup(fcm_mlhp *plan, void *cuda_stream);
-/* y_dev = K x_dev over the free DOFs (device arrays of n_free doubles; one warp per CSR row).
- * x_dev and y_dev must differ (FCM_EINVAL): warps write y while others still read x. */
+/* Factor storage of the next fcm_mlhp_device_setup: FCM_PREC_FP64 (the default; every factor as a float
+ * pair, FP64 accuracy) or FCM_PREC_MIXED (FP32 for the blocks whose retained condition number
+ * lambda_max / lambda_min is at most 1e7, as on the uniform grid: half the bytes, products within 2^-24 of
+ * the factor's magnitude; float pairs for the others).  FCM_EINVAL for another value. */
+fcm_status fcm_mlhp_set_precision(fcm_mlhp *plan, int precision);
+/* After fcm_mlhp_device_setup (else FCM_ESTATE): blocks stored in FP32 and the device factor bytes. */
+fcm_status fcm_mlhp_device_info(const fcm_mlhp *plan, int64_t *n_fp32_blocks, int64_t *factor_bytes);
+/* y_dev = K x_dev over the free DOFs (device arrays of n_free doubles): x split into float pairs, then one
+ * warp per CSR row in double-float arithmetic (values stored as float pairs, 2^-48 relative), each entry
+ * of y within 2^-43 (|K| |x|) of the exact product.  x_dev and y_dev must differ (FCM_EINVAL): warps
+ * write y while others still read x. */
 fcm_status fcm_mlhp_apply_K(fcm_mlhp *plan, const double *x_dev, double *y_dev);
-/* z_dev = S r_dev (Eq. (5)): the diagonal part, then one launch per colour of blocks, z_B += A_B^+ r_B.
- * r_dev and z_dev must differ. */
+/* z_dev = S r_dev (Eq. (5)) in two launches: every block's product A_B^+ r_B into a slot of its own
+ * (double-float arithmetic on float-pair factors), then per DOF the diagonal part plus the slots of the
+ * blocks containing it in block order (deterministic, no atomics).  r_dev and z_dev must differ. */
 fcm_status fcm_mlhp_apply_S(fcm_mlhp *plan, const double *r_dev, double *z_dev);
 /* PCG on K u = b (x0 = 0), stopped when ||S r_i|| / ||S b|| <= tol (Eq. (14)) or after maxit iterations;
- * *iterations counts the K applications.  FCM_OK, FCM_ENOTCONV (u = the last iterate), FCM_EBREAKDOWN
- * (p.Kp <= 0 or a non-finite scalar).  Synchronises the stream. */
+ * *iterations counts the K applications.  The scalars stay on the device (deterministic reductions);
+ * eight iterations per captured CUDA graph on the plan's own stream, ordered after cuda_stream of
+ * fcm_mlhp_device_setup.  FCM_OK, FCM_ENOTCONV (u = the last iterate), FCM_EBREAKDOWN (p.Kp <= 0 or a
+ * non-finite scalar).  Synchronises the stream. */
 fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *plan, const double *b_dev, double tol, int maxit, double *u_dev, int *iterations,
                               double *relres);
 /* Message of the last failed device call on the plan (fcm_mlhp_device_setup, the applies, the PCG): the

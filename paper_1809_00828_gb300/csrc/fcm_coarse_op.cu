@@ -65,6 +65,7 @@ struct CoarseOp {
     __half *KH16 = nullptr;
     float *scale = nullptr, *iscale = nullptr;  // s and 1 / s
     bool use_half = false;   // KH16 in use (the storage chosen at the last coarse_ensure)
+    bool half_cycles = false;  // ... only in the cycles' residual and smoothing products
     Grid3 g{};               // the cell grid of K_H
     // multigrid hierarchy (built on first use of the V-cycle preconditioner)
     int nlev = 0;
@@ -721,9 +722,9 @@ int tiles(int64_t ncell) { return (int)((ncell + kTileCells - 1) / kTileCells); 
 
 // K_H apply on the cell grid of K_H in the stored precision: FP32, or the scaled FP16 copy when in use
 void kh0(const CoarseOp *op, const float *x, const float *xb, float *pout, float *y, int mode, cudaStream_t st,
-         const int *stop, const float *Dinv = nullptr, float omega = 0.f)
+         const int *stop, const float *Dinv = nullptr, float omega = 0.f, bool in_cycle = false)
 {
-    if (op->use_half)
+    if (op->use_half && (in_cycle || !op->half_cycles))
         kh_kernel<__half><<<tiles(op->ncell), RT, 0, st>>>(op->KH16, x, xb, pout, y, op->g, op->ncell, mode, op->partial,
                                                            op->counter, op->sc, stop, Dinv, omega, op->iscale);
     else
@@ -773,6 +774,7 @@ fcm_status coarse_ensure(fcm_ctx *C)
         fcm_status s = FCM_OK;
         if (C->coarse_half && !C->coarse->KH16) s = half_build(C);
         C->coarse->use_half = C->coarse_half && C->coarse->KH16;
+        C->coarse->half_cycles = C->coarse_half == FCM_COARSE_STORE_FP16_CYCLES;
         if (s == FCM_OK && C->coarse_prec != FCM_COARSE_JACOBI && C->coarse->nlev == 0) s = mg_build(C);
         return s;
     }
@@ -1058,7 +1060,7 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
         const float *f = l == 0 ? f0 : v.f;
         jacobi0_kernel<<<nb(v.ncell), RT, 0, st>>>(f, v.Dinv, v.omega, v.xa, v.ncell, stop);
         if (l == 0)
-            kh0(op, v.xa, f, nullptr, v.r, 3, st, stop);
+            kh0(op, v.xa, f, nullptr, v.r, 3, st, stop, nullptr, 0.f, true);
         else
             kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, nullptr, v.r, v.g, v.ncell, 3, op->partial,
                                                      op->counter, op->sc, stop);
@@ -1073,7 +1075,7 @@ void vcycle(CoarseOp *op, const float *f0, float *x0, cudaStream_t st, const int
         float *out = l == 0 ? x0 : v.x;
         mg_interp_kernel<<<nb(v.ncell), RT, 0, st>>>(op->lev[l + 1].x, v.xa, dims_down(v, op->lev[l + 1]), 1, stop);
         if (l == 0)
-            kh0(op, v.xa, f, out, nullptr, 4, st, stop, v.Dinv, v.omega);
+            kh0(op, v.xa, f, out, nullptr, 4, st, stop, v.Dinv, v.omega, true);
         else
             kh_kernel<<<tiles(v.ncell), RT, 0, st>>>(v.KH, v.xa, f, out, nullptr, v.g, v.ncell, 4, op->partial,
                                                      op->counter, op->sc, stop, v.Dinv, v.omega);
@@ -1195,11 +1197,11 @@ extern "C" fcm_status fcm_coarse_set_preconditioner(fcm_ctx *C, int kind)
 extern "C" fcm_status fcm_coarse_set_storage(fcm_ctx *C, int storage)
 {
     if (!C) return FCM_EINVAL;
-    if (storage != FCM_COARSE_STORE_FP32 && storage != FCM_COARSE_STORE_FP16) {
-        C->err = "fcm_coarse_set_storage: storage must be FCM_COARSE_STORE_FP32 or FCM_COARSE_STORE_FP16";
+    if (storage != FCM_COARSE_STORE_FP32 && storage != FCM_COARSE_STORE_FP16 && storage != FCM_COARSE_STORE_FP16_CYCLES) {
+        C->err = "fcm_coarse_set_storage: storage must be FCM_COARSE_STORE_FP32, _FP16 or _FP16_CYCLES";
         return FCM_EINVAL;
     }
-    const int half = storage == FCM_COARSE_STORE_FP16;
+    const int half = storage;
     if (half != C->coarse_half) fcm::fcg_forget_graph(C->fcg);
     C->coarse_half = half;
     return FCM_OK;

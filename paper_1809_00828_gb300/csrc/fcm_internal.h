@@ -76,10 +76,12 @@ void box_cell_setup(const fcm_geometry &geom, const double *dlo, const double *d
 // (free-DOF lists, row-major pseudo inverses, colour ranges) and the diagonal part.  create() checks every
 // index on the host, uploads and synchronises; the vectors of the other calls are device arrays of n.
 struct MlhpDevice;
+// fac_cond (may be null): the blocks whose retained condition number is at most 1e7 keep FP32 factors.
 std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, const int64_t *cols, const double *vals,
                                int64_t nblocks, const int64_t *bptr, const int64_t *bdofs, const int64_t *fptr,
                                const double *fac, int ncolours, const int64_t *cptr, const double *jac,
-                               MlhpDevice **out);
+                               const double *fac_cond, MlhpDevice **out);
+void mlhp_device_info(const MlhpDevice *d, int64_t *n_fp32_blocks, int64_t *factor_bytes);
 void mlhp_device_destroy(MlhpDevice *d);
 std::string mlhp_device_apply_K(MlhpDevice *d, const double *x, double *y);
 std::string mlhp_device_apply_S(MlhpDevice *d, const double *r, double *z);

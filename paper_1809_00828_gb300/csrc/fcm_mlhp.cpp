@@ -184,6 +184,8 @@ struct fcm_mlhp {
     ~fcm_mlhp() { fcm::mlhp_device_destroy(dev); }
     std::vector<int64_t> blk_ptr, blk_dofs, fac_ptr, colour_ptr;
     std::vector<double> factors, jacobi;
+    std::vector<double> fac_cond;  // retained condition number lambda_max / lambda_min of each block
+    int precision = FCM_PREC_FP64;  // fcm_mlhp_set_precision: factor storage of the next device set-up
 
     int ext(int l, int a) const { return n[a] << l; }
 
@@ -579,6 +581,7 @@ struct fcm_mlhp {
             fac_ptr.push_back(fac_ptr.back() + (int64_t)blocks[b].size() * (int64_t)blocks[b].size());
         }
         factors.assign(fac_ptr.back(), 0.0);
+        fac_cond.assign(order.size(), 1.0);
         // pseudo inverses, in parallel over blocks
         std::atomic<size_t> next(0);
         auto work = [&]() {
@@ -601,6 +604,10 @@ struct fcm_mlhp {
                 jacobi_eigen(m, A, lam, V);
                 double lmax = 0.0;
                 for (double l : lam) lmax = std::max(lmax, l);
+                double lmin = lmax;
+                for (double l : lam)
+                    if (l > eps * lmax) lmin = std::min(lmin, l);
+                fac_cond[k] = lmin > 0.0 ? lmax / lmin : 1.0;
                 double *F = factors.data() + fac_ptr[k];
                 for (int t = 0; t < m; ++t) {
                     if (!(lam[t] > eps * lmax)) continue;
@@ -900,7 +907,8 @@ fcm_status fcm_mlhp_device_setup(fcm_mlhp *h, void *cuda_stream)
         const std::string e = fcm::mlhp_device_create(
             cuda_stream, (int64_t)h->free_dofs.size(), h->rowptr.data(), h->cols.data(), h->vals.data(),
             (int64_t)h->blk_ptr.size() - 1, h->blk_ptr.data(), h->blk_dofs.data(), h->fac_ptr.data(), h->factors.data(),
-            (int)h->colour_ptr.size() - 1, h->colour_ptr.data(), h->jacobi.data(), &h->dev);
+            (int)h->colour_ptr.size() - 1, h->colour_ptr.data(), h->jacobi.data(),
+            h->precision == FCM_PREC_MIXED ? h->fac_cond.data() : nullptr, &h->dev);
         if (!e.empty()) {
             h->err = "fcm_mlhp_device_setup: " + e;
             // CUDA failures carry the call's name in front; an allocation failure reads "out of memory"
@@ -955,6 +963,25 @@ fcm_status fcm_mlhp_pcg_solve(fcm_mlhp *h, const double *b_dev, double tol, int 
         return FCM_ECUDA;
     }
     return status == 0 ? FCM_OK : status == 1 ? FCM_ENOTCONV : FCM_EBREAKDOWN;
+}
+
+fcm_status fcm_mlhp_set_precision(fcm_mlhp *h, int precision)
+{
+    if (!h) return FCM_EINVAL;
+    if (precision != FCM_PREC_FP64 && precision != FCM_PREC_MIXED) {
+        h->err = "fcm_mlhp_set_precision: precision must be FCM_PREC_FP64 or FCM_PREC_MIXED";
+        return FCM_EINVAL;
+    }
+    h->precision = precision;
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_device_info(const fcm_mlhp *h, int64_t *n_fp32_blocks, int64_t *factor_bytes)
+{
+    if (!h || !n_fp32_blocks || !factor_bytes) return FCM_EINVAL;
+    if (!h->dev) return FCM_ESTATE;
+    fcm::mlhp_device_info(h->dev, n_fp32_blocks, factor_bytes);
+    return FCM_OK;
 }
 
 const char *fcm_mlhp_last_error(const fcm_mlhp *h) { return h ? h->err.c_str() : ""; }

@@ -80,11 +80,69 @@ __global__ void __launch_bounds__(kThreads) mlhp_spmv_kernel(int n, const int64_
 // Factors as float pairs, r_B split once into shared memory, double-float products and sums.
 constexpr int kRowsPerCta = 32;
 
+// Blocks with `prec` 1 keep FP32 factors (retained condition number <= 1e7, the uniform grid's rule):
+// half the bytes, and plain FP32 products and sums (the factor's own rounding, 2^-24, already bounds the
+// accuracy; about (m / 32 + 8) 2^-24 of sum |F_ij r_j| per row).  fptr: offset in the block's own pool.
+template <class T>
+__device__ __forceinline__ void row_fma(const T *p, float2 rj, float &S, float &C);
+template <>
+__device__ __forceinline__ void row_fma<float2>(const float2 *p, float2 rj, float &S, float &C)
+{
+    const float2 f = __ldcs(p);
+    ff_fma(f.x, f.y, rj.x, rj.y, S, C);
+}
+template <>
+__device__ __forceinline__ void row_fma<float>(const float *p, float2 rj, float &S, float &)
+{
+    S = __fmaf_rn(__ldcs(p), __fadd_rn(rj.x, rj.y), S);
+}
+
+template <class T>
+__device__ __forceinline__ void block_rows(const T *__restrict__ F, int m, int row0, const float2 *rb, int64_t o,
+                                           double *__restrict__ zb)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the warp's four rows row0 + warp + 8 t at once: four independent streams of factor loads in flight
+    constexpr int kRowsPerWarp = kRowsPerCta / (kThreads / 32);
+    const int row_end = min(m, row0 + kRowsPerCta);
+    const T *Fi[kRowsPerWarp];
+    bool on[kRowsPerWarp];
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int i = row0 + warp + t * (kThreads / 32);
+        on[t] = i < row_end;  // warp-uniform
+        Fi[t] = F + (int64_t)(on[t] ? i : row0) * m;
+    }
+    float S[kRowsPerWarp] = {}, C[kRowsPerWarp] = {};
+#pragma unroll 2
+    for (int j = lane; j < m; j += 32) {
+        const float2 rj = rb[j];
+#pragma unroll
+        for (int t = 0; t < kRowsPerWarp; ++t)
+            if (on[t]) row_fma<T>(Fi[t] + j, rj, S[t], C[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        double v;
+        if constexpr (sizeof(T) == sizeof(float)) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) S[t] = __fadd_rn(S[t], __shfl_xor_sync(0xffffffffu, S[t], off));
+            v = f2d(S[t]);
+        } else {
+            ff_warp_sum(S[t], C[t]);
+            v = ff_to_double(ff_norm(S[t], C[t]));
+        }
+        if (on[t] && lane == 0) zb[o + row0 + warp + t * (kThreads / 32)] = v;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) mlhp_block_rows_kernel(const int2 *__restrict__ items,
                                                                    const int64_t *__restrict__ bptr,
                                                                    const int *__restrict__ bdofs,
                                                                    const int64_t *__restrict__ fptr,
+                                                                   const uint8_t *__restrict__ prec,
                                                                    const float2 *__restrict__ fac,
+                                                                   const float *__restrict__ fac32,
                                                                    const double *__restrict__ r,
                                                                    double *__restrict__ zb, const int *done)
 {
@@ -93,37 +151,12 @@ __global__ void __launch_bounds__(kThreads) mlhp_block_rows_kernel(const int2 *_
     const int2 it = items[blockIdx.x];
     const int64_t o = bptr[it.x];
     const int m = (int)(bptr[it.x + 1] - o);
-    const float2 *F = fac + fptr[it.x];
     for (int j = threadIdx.x; j < m; j += kThreads) rb[j] = split_ff(r[bdofs[o + j]]);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the warp's four rows it.y + warp + 8 t at once: four independent streams of factor loads in flight
-    constexpr int kRowsPerWarp = kRowsPerCta / (kThreads / 32);
-    const int row_end = min(m, it.y + kRowsPerCta);
-    const float2 *Fi[kRowsPerWarp];
-    bool on[kRowsPerWarp];
-#pragma unroll
-    for (int t = 0; t < kRowsPerWarp; ++t) {
-        const int i = it.y + warp + t * (kThreads / 32);
-        on[t] = i < row_end;  // warp-uniform
-        Fi[t] = F + (int64_t)(on[t] ? i : it.y) * m;
-    }
-    float S[kRowsPerWarp] = {}, C[kRowsPerWarp] = {};
-#pragma unroll 2
-    for (int j = lane; j < m; j += 32) {
-        const float2 rj = rb[j];
-#pragma unroll
-        for (int t = 0; t < kRowsPerWarp; ++t)
-            if (on[t]) {
-                const float2 f = __ldcs(Fi[t] + j);
-                ff_fma(f.x, f.y, rj.x, rj.y, S[t], C[t]);
-            }
-    }
-#pragma unroll
-    for (int t = 0; t < kRowsPerWarp; ++t) {
-        ff_warp_sum(S[t], C[t]);
-        if (on[t] && lane == 0) zb[o + it.y + warp + t * (kThreads / 32)] = ff_to_double(ff_norm(S[t], C[t]));
-    }
+    if (prec[it.x])  // CTA-uniform
+        block_rows<float>(fac32 + fptr[it.x], m, it.y, rb, o, zb);
+    else
+        block_rows<float2>(fac + fptr[it.x], m, it.y, rb, o, zb);
 }
 
 // z_d = jac_d r_d + sum of the slots of the blocks containing d, in block order
@@ -163,6 +196,9 @@ struct MlhpDevice {
     int *cols = nullptr, *bdofs = nullptr, *occ = nullptr;
     int2 *items = nullptr;
     float2 *vals = nullptr, *fac = nullptr;  // K values and factors as float pairs
+    float *fac32 = nullptr;                  // FP32 factors (mixed precision)
+    uint8_t *prec = nullptr;                 // per block: 1 when its factor is in fac32
+    int64_t n_fp32 = 0, factor_bytes = 0;
     float2 *x2 = nullptr;                    // the K apply's input as float pairs
     double *jac = nullptr, *zb = nullptr;
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *partial = nullptr;
@@ -180,7 +216,7 @@ void mlhp_device_destroy(MlhpDevice *d)
                       (void *)d->bdofs, (void *)d->occ, (void *)d->items, (void *)d->vals, (void *)d->fac,
                       (void *)d->jac, (void *)d->zb, (void *)d->x, (void *)d->r, (void *)d->z, (void *)d->p,
                       (void *)d->q, (void *)d->b, (void *)d->partial, (void *)d->counter, (void *)d->s,
-                      (void *)d->x2})
+                      (void *)d->x2, (void *)d->fac32, (void *)d->prec})
         if (ptr) cudaFree(ptr);
     if (d->hs) cudaFreeHost(d->hs);
     if (d->ev_a) cudaEventDestroy(d->ev_a);
@@ -198,7 +234,7 @@ void mlhp_device_destroy(MlhpDevice *d)
 std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, const int64_t *cols, const double *vals,
                                int64_t nblocks, const int64_t *bptr, const int64_t *bdofs, const int64_t *fptr,
                                const double *fac, int ncolours, const int64_t *cptr, const double *jac,
-                               MlhpDevice **out)
+                               const double *fac_cond, MlhpDevice **out)
 {
     *out = nullptr;
     // every index the kernels will use, checked here
@@ -259,14 +295,37 @@ std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, c
         }
         return out;
     };
-    const std::vector<float2> vals2 = pairs(vals, nnz), fac2 = pairs(fac, fptr[nblocks]);
+    const std::vector<float2> vals2 = pairs(vals, nnz);
+    // factors: FP32 for the blocks whose retained condition number is at most 1e7 (when fac_cond is
+    // given), float pairs for the others; each block's offset is into its own pool
+    std::vector<float2> fac2;
+    std::vector<float> fac32;
+    std::vector<int64_t> foff(nblocks + 1, 0);
+    std::vector<uint8_t> prec(std::max<int64_t>(nblocks, 1), 0);
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const int64_t cnt = fptr[b + 1] - fptr[b];
+        const bool f32 = fac_cond && fac_cond[b] <= 1e7;
+        prec[b] = f32 ? 1 : 0;
+        if (f32) {
+            foff[b] = (int64_t)fac32.size();
+            for (int64_t k = 0; k < cnt; ++k) fac32.push_back((float)fac[fptr[b] + k]);
+            d->n_fp32 += 1;
+        } else {
+            foff[b] = (int64_t)fac2.size();
+            const std::vector<float2> pb = pairs(fac + fptr[b], cnt);
+            fac2.insert(fac2.end(), pb.begin(), pb.end());
+        }
+    }
+    d->factor_bytes = (int64_t)(fac2.size() * sizeof(float2) + fac32.size() * sizeof(float));
     if ((e = upload(&d->rowptr, rowptr, (size_t)n + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->cols, cols32.data(), cols32.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->vals, vals2.data(), vals2.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->bptr, bptr, (size_t)nblocks + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->bdofs, bdofs32.data(), bdofs32.size(), d->st)) != cudaSuccess ||
-        (e = upload(&d->fptr, fptr, (size_t)nblocks + 1, d->st)) != cudaSuccess ||
+        (e = upload(&d->fptr, foff.data(), (size_t)nblocks + 1, d->st)) != cudaSuccess ||
         (e = upload(&d->fac, fac2.data(), fac2.size(), d->st)) != cudaSuccess ||
+        (e = upload(&d->fac32, fac32.data(), fac32.size(), d->st)) != cudaSuccess ||
+        (e = upload(&d->prec, prec.data(), prec.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->jac, jac, (size_t)n, d->st)) != cudaSuccess ||
         (e = upload(&d->items, items.data(), items.size(), d->st)) != cudaSuccess ||
         (e = upload(&d->occ_ptr, occ_ptr.data(), occ_ptr.size(), d->st)) != cudaSuccess ||
@@ -308,7 +367,7 @@ void apply_S(MlhpDevice *d, const double *r, double *z, const int *done, cudaStr
 {
     if (d->nitems > 0)
         mlhp_block_rows_kernel<<<d->nitems, kThreads, (size_t)d->max_block * sizeof(float2), st>>>(
-            d->items, d->bptr, d->bdofs, d->fptr, d->fac, r, d->zb, done);
+            d->items, d->bptr, d->bdofs, d->fptr, d->prec, d->fac, d->fac32, r, d->zb, done);
     mlhp_sum_kernel<<<d->grid_n, kThreads, 0, st>>>(d->n, d->occ_ptr, d->occ, d->zb, d->jac, r, z, done);
 }
 
@@ -335,6 +394,12 @@ const int *done_flag(MlhpDevice *d)
 }
 
 }  // namespace
+
+void mlhp_device_info(const MlhpDevice *d, int64_t *n_fp32_blocks, int64_t *factor_bytes)
+{
+    *n_fp32_blocks = d->n_fp32;
+    *factor_bytes = d->factor_bytes;
+}
 
 std::string mlhp_device_apply_K(MlhpDevice *d, const double *x, double *y)
 {

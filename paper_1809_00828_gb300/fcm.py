@@ -32,7 +32,8 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size",
             "fcm_mlhp_system",
             "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
-            "fcm_mlhp_apply_K", "fcm_mlhp_apply_S", "fcm_mlhp_pcg_solve", "fcm_mlhp_last_error", "fcm_mlhp_destroy")
+            "fcm_mlhp_set_precision", "fcm_mlhp_device_info", "fcm_mlhp_apply_K", "fcm_mlhp_apply_S",
+            "fcm_mlhp_pcg_solve", "fcm_mlhp_last_error", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
 
 
@@ -139,6 +140,8 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_factor_info.argtypes = [P, ip, ip, ctypes.POINTER(i64)]
     L.fcm_mlhp_factors.argtypes = [P, P, P, P, P, P, P]
     L.fcm_mlhp_device_setup.argtypes = [P, P]
+    L.fcm_mlhp_set_precision.argtypes = [P, ctypes.c_int]
+    L.fcm_mlhp_device_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.fcm_mlhp_apply_K.argtypes = [P, P, P]
     L.fcm_mlhp_apply_S.argtypes = [P, P, P]
     L.fcm_mlhp_pcg_solve.argtypes = [P, P, ctypes.c_double, ctypes.c_int, P, ip, dp]
@@ -543,11 +546,12 @@ def _solver_set_coarse_preconditioner(self, kind):
 
 
 def _solver_set_coarse_storage(self, storage):
-    """Storage of K_H: "fp32" (default) or "fp16" (symmetrically scaled FP16, half the bytes per product)."""
+    """Storage of K_H: "fp32" (default), "fp16" (symmetrically scaled FP16, half the bytes per product) or
+    "fp16_cycles" (FP16 only in the V-cycle's products on the finest cell grid)."""
     _bind_unet(load())
-    kinds = {"fp32": 0, "fp16": 1}  # FCM_COARSE_STORE_FP32, FCM_COARSE_STORE_FP16
+    kinds = {"fp32": 0, "fp16": 1, "fp16_cycles": 2}  # FCM_COARSE_STORE_FP32, _FP16, _FP16_CYCLES
     if storage not in kinds:
-        raise ValueError(f"coarse storage {storage!r}: expected 'fp32' or 'fp16'")
+        raise ValueError(f"coarse storage {storage!r}: expected one of {sorted(kinds)}")
     self._check(load().fcm_coarse_set_storage(self.ctx, kinds[storage]))
 
 
@@ -716,17 +720,27 @@ class MLHPPlan:
         factors = [fac[fptr[b]:fptr[b + 1]].reshape(len(blocks[b]), len(blocks[b])) for b in range(nb.value)]
         return blocks, factors, cptr, jac
 
-    def device_setup(self, stream=None):
-        """Upload the assembled system and factors to the current CUDA device (torch's current stream)."""
+    def device_setup(self, stream=None, precision="fp64"):
+        """Upload the assembled system and factors to the current CUDA device (torch's current stream).
+        precision "mixed": FP32 factors for the blocks with retained condition number <= 1e7."""
         import torch
+        if precision not in ("fp64", "mixed"):
+            raise ValueError(f"precision {precision!r}: expected 'fp64' or 'mixed'")
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self._stream = stream
+        self._check(load().fcm_mlhp_set_precision(self.h, PREC_FP64 if precision == "fp64" else PREC_MIXED))
         self._check(load().fcm_mlhp_device_setup(self.h, ctypes.c_void_p(stream)))
         nf, nnz = ctypes.c_int64(), ctypes.c_int64()
         self._check(load().fcm_mlhp_system_size(self.h, ctypes.byref(nf), ctypes.byref(nnz)))
         self._nfree = nf.value
         self._device = torch.cuda.current_device()
+
+    def device_info(self):
+        """(blocks stored in FP32, device factor bytes) after device_setup."""
+        n32, nb = ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().fcm_mlhp_device_info(self.h, ctypes.byref(n32), ctypes.byref(nb)))
+        return n32.value, nb.value
 
     def _vec(self, t, what):
         if getattr(self, "_nfree", None) is None:

@@ -84,3 +84,52 @@ def test_mlhp_pcg_matches_the_oracle(case):
     assert abs(its - its_o) <= max(3, 0.05 * its_o)
     xref = spla.spsolve(Q.K.tocsc(), Q.b)
     assert Q.energy_error(xref, u.cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_mlhp_mixed_precision_factors(ci):
+    """FP32 factors for the blocks whose retained condition number is at most 1e7 (fcm_mlhp_set_precision):
+    the blocks so stored are those; their products run in FP32 (factor, r_B, products and the row sum each
+    rounded: (m / 32 + 8) 2^-24 of sum_j |F_ij r_j| for a row of m entries, 32 lanes), so S r stays within
+    that, summed over the blocks containing a DOF, of the FP64 factors; and PCG reaches the direct
+    solution in the oracle's iteration count within 5 %."""
+    from paper_1809_00828_gb300 import fcm
+    n, sph, p, k, depth, alpha = CASES[ci]
+    P = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), sph, p, k, octree_depth=depth)
+    try:
+        free, K, b, eta = P.assemble(alpha, "clamp")
+        blocks, F, cptr, jac = P.factorize("truncated")
+        P.device_setup(precision="mixed")
+        n32, fbytes = P.device_info()
+        conds = []
+        for B in blocks:
+            lam = np.linalg.eigvalsh(K[B][:, B].toarray())
+            keep = lam[lam > 1e-13 * lam.max()]
+            conds.append(keep.max() / keep.min())
+        conds = np.array(conds)
+        sizes = np.array([len(B) for B in blocks])
+        sure32 = conds <= 0.99e7
+        sure64 = conds > 1.01e7
+        assert sure32.sum() <= n32 <= len(blocks) - sure64.sum()
+        assert 4 * (sizes[sure32] ** 2).sum() + 8 * (sizes[sure64] ** 2).sum() <= fbytes
+        assert fbytes <= 4 * (sizes[~sure64] ** 2).sum() + 8 * (sizes[~sure32] ** 2).sum()
+        r = np.random.default_rng(4).standard_normal(len(free))
+        z = P.apply_S(torch.from_numpy(r).cuda()).cpu().numpy()
+        zh = jac * r
+        mag = np.abs(jac * r) * 2.0 ** -50
+        for B, Fb in zip(blocks, F):
+            zh[B] += Fb @ r[B]
+            mag[B] += ((len(B) / 32 + 8) * 2.0 ** -24 + 2.0 ** -43) * (np.abs(Fb) @ np.abs(r[B]))
+        assert (np.abs(z - zh) <= mag).all(), float(np.max(np.abs(z - zh) / mag))
+        H = M.refine_toward_spheres(n, (0, 0, 0), (1, 1, 1), sph, k)
+        Q = M.MLProblem(H, p, sph, alpha=alpha, depth=depth)
+        Q.build_blocks("truncated")
+        _, its_o = Q.pcg(tol=1e-8, maxit=5000)
+        u, its, rel, st = P.pcg_solve(torch.from_numpy(b).cuda(), 1e-8, 5000)
+        assert st == fcm.FCM_OK and rel <= 1e-8
+        assert abs(its - its_o) <= max(3, 0.05 * its_o)
+        xref = spla.spsolve(Q.K.tocsc(), Q.b)
+        assert Q.energy_error(xref, u.cpu().numpy()) < 1e-6
+        print(f"case {ci}: {n32} of {len(blocks)} blocks in FP32, {fbytes} factor bytes, {its} iterations")
+    finally:
+        P.close()
