@@ -376,6 +376,23 @@ def run_fcm(args, rank, world, local_rank):
     s = fcm.Solver(w)
     k_prec = args.k_precision if args.precision != "fp64" else "fp64"
     s.set_k_precision(k_prec)
+    if args.profile_apply == "KH":
+        # the coarse operator alone (no preconditioner on the device): K_H products between
+        # cudaProfilerStart / Stop, after its assembly and 3 warm-up products
+        nc = w.n[0] * w.n[1] * w.n[2]
+        xc = torch.ones(3 * nc, dtype=torch.float32, device="cuda")
+        yc = torch.empty_like(xc)
+        for _ in range(3):
+            s.coarse_apply(xc, out=yc)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.profile_reps):
+            s.coarse_apply(xc, out=yc)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"profiled {args.profile_reps} K_H applies of {w.name}")
+        s.close()
+        return 0
     s.precond_build(precision=args.precision, blocks=args.blocks, eta_bar=args.eta_bar)
     n = s.n
     # load cases: 0 = traction on z = 1; 1..6 = unit Voigt strains (one solve of all six)
@@ -738,8 +755,9 @@ def main():
                          "FP64 Schwarz-PCG count measured on the GPU for the workload, which the oracle's "
                          "algorithm shares)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-apply", default=None, choices=["S", "K"],
-                    help="apply S or K --profile-reps times between cudaProfilerStart/Stop and exit (for ncu)")
+    ap.add_argument("--profile-apply", default=None, choices=["S", "K", "KH"],
+                    help="apply S, K or the coarse operator K_H (KH: without building the preconditioner) "
+                         "--profile-reps times between cudaProfilerStart/Stop and exit (for ncu)")
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="after the warm-up, run one step between cudaProfilerStart/Stop and exit (for ncu)")
