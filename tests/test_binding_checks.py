@@ -58,3 +58,15 @@ def test_host_buffers_of_the_host_entry_points():
         fcm._host_vec(ro, 8, "out", writable=True)
     a = np.zeros(16)
     assert fcm._host_vec(a, 8, "b", multiple=True) is a
+
+
+def test_choice_arguments_are_checked_before_any_call():
+    # the named choices of the coarse correction and of the multi-level factors are validated in the
+    # binding, before the object (here a stand-in) is used or the library is called
+    dummy = object()
+    with pytest.raises(ValueError):
+        fcm.Solver.set_coarse_preconditioner(dummy, "amg")
+    with pytest.raises(ValueError):
+        fcm.Solver.set_coarse_storage(dummy, "bf16")
+    with pytest.raises(ValueError):
+        fcm.MLHPPlan.device_setup(dummy, stream=0, precision="fp16")
