@@ -37,6 +37,7 @@
 namespace fcm {
 
 constexpr int kM = 4;          // FCG(m): directions kept for the explicit K-orthogonalisation
+constexpr double kL2Bytes = 129e6;  // GB300's L2
 constexpr int kFcgChunk = 4;   // iterations per captured graph
 
 struct FcgScalars {
@@ -520,9 +521,13 @@ fcm_status fcg_iteration(fcm_ctx *C, fcm_unet *net, double gamma, int iters)
     ctx_apply_K_flag(C, C->d_p, C->d_q, stop);
     fk_pq_kernel<<<rb, RT, 0, st>>>(C->d_p, C->d_q, C->d_r, F->ring, n, F->partial, F->counter, F->d);
     fk_xr_kernel<<<rb, RT, 0, st>>>(C->d_x, C->d_r, C->d_p, C->d_q, n, F->d);
-    if (!net) {
+    // K_H in bytes: 63 stored 3x3 FP32 blocks per cell
+    const double kh_bytes = (double)F->ncell * 63 * 9 * 4;
+    if (!net && kh_bytes > kL2Bytes) {
         // R r and the coarse solve on the side stream while the Schwarz apply streams its factors; both
-        // only read r, and they share no scratch (separate reduction buffers)
+        // only read r, and they share no scratch (separate reduction buffers).  Only where K_H streams
+        // from HBM anyway: a K_H that fits the L2 stays there across the coarse steps, and the Schwarz
+        // apply's stream beside them would evict it.
         const int64_t ncell = F->ncell;
         CO_CUDA(C, cudaEventRecord(F->ev_r, st));
         CO_CUDA(C, cudaStreamWaitEvent(F->side, F->ev_r, 0));
