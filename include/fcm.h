@@ -324,9 +324,12 @@ fcm_status fcm_coarse_apply(fcm_ctx *ctx, const float *x_cells_dev, float *y_cel
 /* Flexible PCG with a coarse correction: z = S r + P y, S the Additive-Schwarz
  * operator (Eq. (5)) and y an approximation of K_H^-1 R r.  y starts from the
  * U-Net's prediction gamma sigma N(R r / sigma, eta) (sigma the RMS of R r;
- * zero when net is NULL) and is refined by coarse_iters steps of block-Jacobi
- * CG on K_H (coarse_iters = 0: the prediction alone; net == NULL needs
- * coarse_iters >= 1).  Since z depends nonlinearly on r, every new direction
+ * zero when net is NULL) and is refined by coarse_iters steps of CG on K_H,
+ * preconditioned as fcm_coarse_set_preconditioner chose (block Jacobi by
+ * default, or the cell-grid multigrid cycle) (coarse_iters = 0: the prediction
+ * alone; net == NULL needs coarse_iters >= 1).  Without a network, and where
+ * K_H exceeds the 129 MB L2, R r and the coarse solve run on a second stream
+ * beside the Schwarz apply.  Since z depends nonlinearly on r, every new direction
  * is K-orthogonalised against the previous four (truncated flexible CG,
  * FCG(4), Notay 2000).  Convergence is tested on the plain Schwarz residual
  * ||S r|| / ||S b|| <= tol (Eq. (14)).  When the stopping residual grows
