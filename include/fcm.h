@@ -508,6 +508,12 @@ fcm_status fcm_mlhp_system(const fcm_mlhp *plan, int64_t *free_dofs, int64_t *ro
  * colour by colour.  Host time grows as the cube of the block size: meant for truncated blocks.
  * FCM_ESTATE before fcm_mlhp_assemble. */
 fcm_status fcm_mlhp_factorize(fcm_mlhp *plan, int kind, double eps, double eta_bar);
+/* fcm_mlhp_factorize with the blocks' eigensolves on the current CUDA device: the blocks are formed on the
+ * host as there, then solved by batched FP64 eigensolves (cuSOLVER, one batch per block size) on
+ * cuda_stream, with the same Eq. (13) cut-off and the same pseudo inverse up to the two eigensolvers'
+ * rounding; the factors land in host memory as with fcm_mlhp_factorize.  FCM_ECUDA (message in
+ * fcm_mlhp_last_error) when a device call fails, FCM_ENOMEM when memory runs out. */
+fcm_status fcm_mlhp_factorize_device(fcm_mlhp *plan, int kind, double eps, double eta_bar, void *cuda_stream);
 fcm_status fcm_mlhp_factor_info(const fcm_mlhp *plan, int *n_blocks, int *n_colours, int64_t *factor_entries);
 /* Copy the factors to caller-owned host arrays (any may be NULL): blk_ptr[n_blocks + 1] and blk_dofs (free
  * DOF indices of block b in blk_dofs[blk_ptr[b] .. blk_ptr[b+1]), ascending), fac_ptr[n_blocks + 1] and

@@ -82,6 +82,11 @@ std::string mlhp_device_create(void *stream, int64_t n, const int64_t *rowptr, c
                                const double *fac, int ncolours, const int64_t *cptr, const double *jac,
                                const double *fac_cond, MlhpDevice **out);
 void mlhp_device_info(const MlhpDevice *d, int64_t *n_fp32_blocks, int64_t *factor_bytes);
+// Pseudo inverses of nblocks symmetric blocks (A: row-major m_b x m_b at fac_ptr[b]) by batched eigensolves
+// on the device (stream), eigenvalues below eps * lambda_max dropped (Eq. (13)); F as A, cond[b] the retained
+// condition number.  "" on success, else the failure.
+std::string mlhp_device_pinv(void *stream, int64_t nblocks, const int64_t *fac_ptr, const double *A, double eps,
+                             double *F, double *cond);
 void mlhp_device_destroy(MlhpDevice *d);
 std::string mlhp_device_apply_K(MlhpDevice *d, const double *x, double *y);
 std::string mlhp_device_apply_S(MlhpDevice *d, const double *r, double *z);

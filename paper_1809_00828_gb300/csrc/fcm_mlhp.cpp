@@ -523,7 +523,9 @@ struct fcm_mlhp {
     // truncated functions, the free DOFs among them), A_B^+ = V diag(1/lambda, lambda > eps lambda_max) V^T, and the
     // diagonal part for free DOFs in no block.  Blocks are coloured greedily (no two blocks of one colour
     // share a DOF) and stored colour by colour.
-    void factorize(int kind, double eps, double eta_bar)
+    // on_device: the blocks' eigensolves run batched on the current CUDA device (stream); the result is the
+    // same pseudo inverse up to the two eigensolvers' rounding.  Returns "" or the device failure.
+    std::string factorize(int kind, double eps, double eta_bar, bool on_device = false, void *stream = nullptr)
     {
         const int64_t nfree = (int64_t)free_dofs.size();
         std::vector<int64_t> pos(3 * f_level.size(), -1);
@@ -582,7 +584,9 @@ struct fcm_mlhp {
         }
         factors.assign(fac_ptr.back(), 0.0);
         fac_cond.assign(order.size(), 1.0);
-        // pseudo inverses, in parallel over blocks
+        std::vector<double> dense;  // the blocks themselves, for the device eigensolves
+        if (on_device) dense.assign(fac_ptr.back(), 0.0);
+        // pseudo inverses (or, on_device, the dense blocks), in parallel over blocks
         std::atomic<size_t> next(0);
         auto work = [&]() {
             std::vector<int64_t> where(nfree, -1);
@@ -601,6 +605,10 @@ struct fcm_mlhp {
                         const double v = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
                         A[(size_t)i * m + j] = A[(size_t)j * m + i] = v;
                     }
+                if (on_device) {
+                    std::copy(A.begin(), A.end(), dense.begin() + fac_ptr[k]);
+                    continue;
+                }
                 jacobi_eigen(m, A, lam, V);
                 double lmax = 0.0;
                 for (double l : lam) lmax = std::max(lmax, l);
@@ -624,6 +632,11 @@ struct fcm_mlhp {
         for (int t = 1; t < nt; ++t) pool.emplace_back(work);
         work();
         for (auto &t : pool) t.join();
+        if (on_device) {
+            const std::string e = fcm::mlhp_device_pinv(stream, (int64_t)order.size(), fac_ptr.data(), dense.data(), eps,
+                                                        factors.data(), fac_cond.data());
+            if (!e.empty()) return e;
+        }
         // diagonal part for free DOFs in no block
         std::vector<uint8_t> covered(nfree, 0);
         for (int64_t d : blk_dofs) covered[d] = 1;
@@ -634,6 +647,7 @@ struct fcm_mlhp {
                 if (cols[e] == i) jacobi[i] = 1.0 / vals[e];
         }
         factorized = true;
+        return std::string();
     }
 
     // 1D factor of function f along axis a on leaf (L, c), as coefficients in the leaf's 1D basis
@@ -863,6 +877,26 @@ fcm_status fcm_mlhp_factorize(fcm_mlhp *h, int kind, double eps, double eta_bar)
         fcm::mlhp_device_destroy(h->dev);
         h->dev = nullptr;
         h->factorize(kind, eps, eta_bar);
+    } catch (...) {
+        return FCM_ENOMEM;
+    }
+    return FCM_OK;
+}
+
+fcm_status fcm_mlhp_factorize_device(fcm_mlhp *h, int kind, double eps, double eta_bar, void *cuda_stream)
+{
+    if (!h || (kind != 0 && kind != 1) || !(eps < 1.0) || !(eta_bar >= 0.0 && eta_bar <= 1.0)) return FCM_EINVAL;
+    if (!h->assembled) return FCM_ESTATE;
+    h->err.clear();
+    try {
+        h->factorized = false;
+        fcm::mlhp_device_destroy(h->dev);
+        h->dev = nullptr;
+        const std::string e = h->factorize(kind, eps, eta_bar, true, cuda_stream);
+        if (!e.empty()) {
+            h->err = "fcm_mlhp_factorize_device: " + e;
+            return e.find("out of memory") != std::string::npos ? FCM_ENOMEM : FCM_ECUDA;
+        }
     } catch (...) {
         return FCM_ENOMEM;
     }

@@ -14,12 +14,15 @@
 //     CG kernels: every scalar stays on the device (deterministic two-level reductions), eight
 //     iterations are captured in one CUDA graph, and the host polls the scalars once per graph.
 // Every index the kernels use is checked on the host before the upload.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -472,6 +475,164 @@ std::string mlhp_device_pcg(MlhpDevice *d, const double *b, double tol, int maxi
         *status = 1;
     } else {
         *status = h.status == FCM_OK ? 0 : h.status == FCM_ENOTCONV ? 1 : 2;
+    }
+    return std::string();
+}
+
+}  // namespace fcm
+
+// ---- pseudo inverses of the leaf blocks on the device (fcm_mlhp_factorize_device) ----
+namespace fcm {
+
+namespace {
+
+// per block (one CTA): U(:, k) = V(:, k) / lambda_k for lambda_k > eps lambda_max, else 0 (V column-major, the
+// eigenvectors from syev), and the retained condition number lambda_max / lambda_min
+__global__ void __launch_bounds__(kThreads) mlhp_pinv_scale_kernel(const double *__restrict__ V,
+                                                                   const double *__restrict__ W, int m, double eps,
+                                                                   double *__restrict__ U, double *__restrict__ cond)
+{
+    const double *v = V + (size_t)blockIdx.x * m * m;
+    const double *w = W + (size_t)blockIdx.x * m;
+    double *u = U + (size_t)blockIdx.x * m * m;
+    __shared__ double lmax_s, lmin_s;
+    if (threadIdx.x == 0) {
+        double lmax = 0.0;
+        for (int k = 0; k < m; ++k) lmax = fmax(lmax, w[k]);
+        double lmin = lmax;
+        for (int k = 0; k < m; ++k)
+            if (w[k] > eps * lmax) lmin = fmin(lmin, w[k]);
+        lmax_s = lmax;
+        lmin_s = lmin;
+        cond[blockIdx.x] = lmin > 0.0 ? lmax / lmin : 1.0;
+    }
+    __syncthreads();
+    const double cut = eps * lmax_s;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        const int k = t / m;  // column
+        u[t] = w[k] > cut ? v[t] / w[k] : 0.0;
+    }
+}
+
+}  // namespace
+
+#define PINV_CUDA(call)                                                                            \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return std::string(#call) + ": " + cudaGetErrorString(e_);          \
+    } while (0)
+#define PINV_SOLVER(call)                                                                          \
+    do {                                                                                           \
+        cusolverStatus_t e_ = (call);                                                              \
+        if (e_ != CUSOLVER_STATUS_SUCCESS) return std::string(#call) + ": cusolver status " + std::to_string((int)e_); \
+    } while (0)
+#define PINV_BLAS(call)                                                                            \
+    do {                                                                                           \
+        cublasStatus_t e_ = (call);                                                                \
+        if (e_ != CUBLAS_STATUS_SUCCESS) return std::string(#call) + ": cublas status " + std::to_string((int)e_); \
+    } while (0)
+
+std::string mlhp_device_pinv(void *stream, int64_t nblocks, const int64_t *fac_ptr, const double *A, double eps,
+                             double *F, double *cond)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // blocks by size: one batched eigensolve per size (and per chunk of at most ~1 GB of work arrays)
+    std::map<int, std::vector<int64_t>> groups;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const int64_t n2 = fac_ptr[b + 1] - fac_ptr[b];
+        const int m = (int)std::llround(std::sqrt((double)n2));
+        if ((int64_t)m * m != n2 || m < 1) return "factor sizes are not squares";
+        groups[m].push_back(b);
+    }
+    struct Res {
+        std::vector<void *> p;
+        cusolverDnHandle_t s = nullptr;
+        cublasHandle_t b = nullptr;
+        cusolverDnParams_t q = nullptr;
+        ~Res()
+        {
+            for (void *x : p) cudaFree(x);
+            if (q) cusolverDnDestroyParams(q);
+            if (s) cusolverDnDestroy(s);
+            if (b) cublasDestroy(b);
+        }
+    } res;
+    PINV_SOLVER(cusolverDnCreate(&res.s));
+    PINV_SOLVER(cusolverDnCreateParams(&res.q));
+    PINV_SOLVER(cusolverDnSetStream(res.s, st));
+    PINV_BLAS(cublasCreate(&res.b));
+    PINV_BLAS(cublasSetStream(res.b, st));
+    for (auto &kv : groups) {
+        const int m = kv.first;
+        const std::vector<int64_t> &ids = kv.second;
+        const size_t m2 = (size_t)m * m;
+        const int chunk = (int)std::max<size_t>(1, std::min<size_t>(ids.size(), (size_t)(1ull << 30) / (3 * m2 * 8)));
+        double *dA = nullptr, *dU = nullptr, *dC = nullptr, *dW = nullptr, *dcond = nullptr;
+        int *dinfo = nullptr;
+        PINV_CUDA(cudaMalloc(&dA, sizeof(double) * m2 * chunk));
+        res.p.push_back(dA);
+        PINV_CUDA(cudaMalloc(&dU, sizeof(double) * m2 * chunk));
+        res.p.push_back(dU);
+        PINV_CUDA(cudaMalloc(&dC, sizeof(double) * m2 * chunk));
+        res.p.push_back(dC);
+        PINV_CUDA(cudaMalloc(&dW, sizeof(double) * m * chunk));
+        res.p.push_back(dW);
+        PINV_CUDA(cudaMalloc(&dcond, sizeof(double) * chunk));
+        res.p.push_back(dcond);
+        PINV_CUDA(cudaMalloc(&dinfo, sizeof(int) * chunk));
+        res.p.push_back(dinfo);
+        bool batched = true;
+        size_t dws = 0, hws = 0;
+        if (cusolverDnXsyevBatched_bufferSize(res.s, res.q, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m,
+                                              CUDA_R_64F, dA, m, CUDA_R_64F, dW, CUDA_R_64F, &dws, &hws,
+                                              chunk) != CUSOLVER_STATUS_SUCCESS)
+            batched = false;
+        if (!batched)
+            PINV_SOLVER(cusolverDnXsyevd_bufferSize(res.s, res.q, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m,
+                                                    CUDA_R_64F, dA, m, CUDA_R_64F, dW, CUDA_R_64F, &dws, &hws));
+        void *dwork = nullptr;
+        PINV_CUDA(cudaMalloc(&dwork, std::max<size_t>(dws, 16)));
+        res.p.push_back(dwork);
+        std::vector<char> hwork(std::max<size_t>(hws, 1));
+        std::vector<double> stage(m2 * chunk), hcond(chunk);
+        std::vector<int> hinfo(chunk);
+        for (size_t s0 = 0; s0 < ids.size(); s0 += chunk) {
+            const int B = (int)std::min<size_t>(chunk, ids.size() - s0);
+            // the blocks are symmetric, so row-major host storage is their column-major form
+            for (int b = 0; b < B; ++b)
+                std::copy(A + fac_ptr[ids[s0 + b]], A + fac_ptr[ids[s0 + b]] + m2, stage.begin() + (size_t)b * m2);
+            PINV_CUDA(cudaMemcpyAsync(dA, stage.data(), sizeof(double) * m2 * B, cudaMemcpyHostToDevice, st));
+            if (batched) {
+                PINV_SOLVER(cusolverDnXsyevBatched(res.s, res.q, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m,
+                                                   CUDA_R_64F, dA, m, CUDA_R_64F, dW, CUDA_R_64F, dwork, dws,
+                                                   hwork.data(), hws, dinfo, B));
+            } else {
+                for (int b = 0; b < B; ++b)
+                    PINV_SOLVER(cusolverDnXsyevd(res.s, res.q, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m,
+                                                 CUDA_R_64F, dA + m2 * b, m, CUDA_R_64F, dW + (size_t)m * b, CUDA_R_64F,
+                                                 dwork, dws, hwork.data(), hws, dinfo + b));
+            }
+            mlhp_pinv_scale_kernel<<<B, kThreads, 0, st>>>(dA, dW, m, eps, dU, dcond);
+            PINV_CUDA(cudaGetLastError());
+            const double one = 1.0, zero = 0.0;
+            // C = U V^T: C(i, j) = sum_k V(i, k) V(j, k) / lambda_k, symmetric
+            PINV_BLAS(cublasDgemmStridedBatched(res.b, CUBLAS_OP_N, CUBLAS_OP_T, m, m, m, &one, dU, m, (long long)m2, dA,
+                                                m, (long long)m2, &zero, dC, m, (long long)m2, B));
+            PINV_CUDA(cudaMemcpyAsync(stage.data(), dC, sizeof(double) * m2 * B, cudaMemcpyDeviceToHost, st));
+            PINV_CUDA(cudaMemcpyAsync(hcond.data(), dcond, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+            PINV_CUDA(cudaMemcpyAsync(hinfo.data(), dinfo, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+            PINV_CUDA(cudaStreamSynchronize(st));
+            for (int b = 0; b < B; ++b) {
+                if (hinfo[b] != 0) return "eigensolver failed for a block (info " + std::to_string(hinfo[b]) + ")";
+                const int64_t id = ids[s0 + b];
+                // exact symmetry, as the host path makes it: the mean of C and its transpose
+                const double *c = stage.data() + (size_t)b * m2;
+                double *f = F + fac_ptr[id];
+                for (int i = 0; i < m; ++i)
+                    for (int j = 0; j < m; ++j) f[(size_t)i * m + j] = 0.5 * (c[(size_t)i * m + j] + c[(size_t)j * m + i]);
+                cond[id] = hcond[b];
+            }
+        }
     }
     return std::string();
 }

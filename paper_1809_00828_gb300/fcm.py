@@ -31,7 +31,7 @@ EXPORTED = ("fcm_setup", "fcm_info", "fcm_rhs", "fcm_precond_build", "fcm_pcg_so
             "fcm_mlhp_create", "fcm_mlhp_get_info", "fcm_mlhp_leaf", "fcm_mlhp_function",
             "fcm_mlhp_block", "fcm_mlhp_colour", "fcm_mlhp_restriction", "fcm_mlhp_assemble", "fcm_mlhp_system_size",
             "fcm_mlhp_system",
-            "fcm_mlhp_factorize", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
+            "fcm_mlhp_factorize", "fcm_mlhp_factorize_device", "fcm_mlhp_factor_info", "fcm_mlhp_factors", "fcm_mlhp_device_setup",
             "fcm_mlhp_set_precision", "fcm_mlhp_device_info", "fcm_mlhp_apply_K", "fcm_mlhp_apply_S",
             "fcm_mlhp_pcg_solve", "fcm_mlhp_last_error", "fcm_mlhp_destroy")
 NOALLOC_MAX_LATTICE = 1048576  # FCM_NOALLOC_MAX_LATTICE in include/fcm.h
@@ -140,6 +140,7 @@ def load(path: str = LIB_PATH):
     L.fcm_mlhp_factor_info.argtypes = [P, ip, ip, ctypes.POINTER(i64)]
     L.fcm_mlhp_factors.argtypes = [P, P, P, P, P, P, P]
     L.fcm_mlhp_device_setup.argtypes = [P, P]
+    L.fcm_mlhp_factorize_device.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, P]
     L.fcm_mlhp_set_precision.argtypes = [P, ctypes.c_int]
     L.fcm_mlhp_device_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.fcm_mlhp_apply_K.argtypes = [P, P, P]
@@ -696,12 +697,21 @@ class MLHPPlan:
         K = sp.csr_matrix((vals, cols, rowptr), shape=(nf.value, nf.value))
         return free, K, rhs, eta
 
-    def factorize(self, kind="truncated", eps=1e-13, eta_bar=1.0):
-        """Schwarz factors on the host for the leaves with eta_T <= eta_bar; returns (blocks, factors,
-        colour_ptr, jacobi): block b's free DOFs and its pseudo inverse, blocks of colour c at
-        colour_ptr[c] .. colour_ptr[c+1], and 1 / K_ll on the DOFs in no block."""
+    def factorize(self, kind="truncated", eps=1e-13, eta_bar=1.0, device=False):
+        """Schwarz factors for the leaves with eta_T <= eta_bar; returns (blocks, factors, colour_ptr,
+        jacobi): block b's free DOFs and its pseudo inverse, blocks of colour c at colour_ptr[c] ..
+        colour_ptr[c+1], and 1 / K_ll on the DOFs in no block.  device: the eigensolves batched on the
+        current CUDA device (torch's current stream) instead of the host."""
         L = load()
-        self._check(L.fcm_mlhp_factorize(self.h, {"full": 0, "truncated": 1}[kind], eps, eta_bar))
+        if kind not in ("full", "truncated"):
+            raise ValueError(f"kind {kind!r}: expected 'full' or 'truncated'")
+        k = {"full": 0, "truncated": 1}[kind]
+        if device:
+            import torch
+            st = torch.cuda.current_stream().cuda_stream
+            self._check(L.fcm_mlhp_factorize_device(self.h, k, eps, eta_bar, ctypes.c_void_p(st)))
+        else:
+            self._check(L.fcm_mlhp_factorize(self.h, k, eps, eta_bar))
         nb, nc, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
         self._check(L.fcm_mlhp_factor_info(self.h, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(ne)))
         nfree = ctypes.c_int64()

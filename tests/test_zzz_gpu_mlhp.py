@@ -133,3 +133,46 @@ def test_mlhp_mixed_precision_factors(ci):
         print(f"case {ci}: {n32} of {len(blocks)} blocks in FP32, {fbytes} factor bytes, {its} iterations")
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_mlhp_device_factorisation_matches_the_host(ci):
+    """fcm_mlhp_factorize_device (batched cuSOLVER eigensolves) against the host's cyclic-Jacobi factors: the
+    same blocks, and per block ||F_dev - F_host||_2 <= 10 m eps (cond(A_B) + 1) ||F_host||_2, the bound two
+    backward-stable eigensolvers satisfy when they keep the same eigenvalues; then the PCG on the device
+    factors takes the host factors' iteration count within 2 and reaches the direct solution."""
+    from paper_1809_00828_gb300 import fcm
+    n, sph, p, k, depth, alpha = CASES[ci]
+    P1 = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), sph, p, k, octree_depth=depth)
+    P2 = fcm.MLHPPlan(n, (0, 0, 0), (1, 1, 1), sph, p, k, octree_depth=depth)
+    try:
+        free, K, b, eta = P1.assemble(alpha, "clamp")
+        P2.assemble(alpha, "clamp")
+        blocks_h, F_h, _, jac_h = P1.factorize("truncated")
+        blocks_d, F_d, _, jac_d = P2.factorize("truncated", device=True)
+        assert len(blocks_h) == len(blocks_d)
+        assert all(np.array_equal(x, y) for x, y in zip(blocks_h, blocks_d))
+        assert np.array_equal(jac_h, jac_d)
+        worst = 0.0
+        for B, Fh, Fd in zip(blocks_h, F_h, F_d):
+            lam = np.linalg.eigvalsh(K[B][:, B].toarray())
+            keep = lam[lam > 1e-13 * lam.max()]
+            cond = keep.max() / keep.min()
+            bound = 10 * len(B) * 2.0 ** -52 * (cond + 1.0) * np.linalg.norm(Fh, 2)
+            err = np.linalg.norm(Fd - Fh, 2)
+            worst = max(worst, err / bound)
+            assert err <= bound, (len(B), cond, err, bound)
+        bd = torch.from_numpy(b).cuda()
+        P1.device_setup(precision="fp64")
+        P2.device_setup(precision="fp64")
+        _, its_h, _, st_h = P1.pcg_solve(bd, 1e-8, 5000)
+        u, its_d, rel, st_d = P2.pcg_solve(bd, 1e-8, 5000)
+        assert st_h == fcm.FCM_OK and st_d == fcm.FCM_OK and rel <= 1e-8
+        assert abs(its_d - its_h) <= 2
+        xref = spla.spsolve(K.tocsc(), b)
+        e = u.cpu().numpy() - xref
+        assert np.sqrt(e @ (K @ e) / (xref @ (K @ xref))) < 1e-6
+        print(f"case {ci}: worst factor difference {worst:.2g} of its bound; PCG {its_h} (host), {its_d} (device)")
+    finally:
+        P1.close()
+        P2.close()
