@@ -1,5 +1,5 @@
 """Slab decomposition of the Schwarz-PCG (Sec. 4.2 ghost layers, Sec. 5.3.3 distributed scaling) on
-CPU ranks: two gloo processes run the partitioned PCG of paper_1809_00828_gb300/slabs.py with the
+CPU ranks: two to four gloo processes run the partitioned PCG of paper_1809_00828_gb300/slabs.py with the
 oracle's operators cut to each slab (the K rows of the owned DOFs, the vertex-patch blocks of the
 owned vertices) and reproduce the single-domain oracle PCG: the same iteration count, the same first
 residual history steps and the same solution, up to the order of the summations.
@@ -115,18 +115,20 @@ def _worker(rank, world, port, name, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["single_void", "porous4"])
-def test_two_slab_ranks_reproduce_the_single_domain_pcg(name):
+@pytest.mark.parametrize("name,world", [("single_void", 2), ("porous4", 2), ("porous4", 3), ("porous4", 4)])
+def test_slab_ranks_reproduce_the_single_domain_pcg(name, world):
+    # world 4 on 4 cell layers: every rank owns one layer, so every halo and reverse addition crosses ranks
+    # (the plan test below covers the ghost planes of p = 1, 3 and 4)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, name, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, name, q)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(300)
         assert p.exitcode == 0
-    res = sorted(q.get(timeout=10) for _ in range(2))
+    res = sorted(q.get(timeout=10) for _ in range(world))
     for rank, its, its_ref, dx, xmax, dh, dh_all, e_energy in res:
         assert its == its_ref, (rank, its, its_ref)
         assert e_energy <= 1e-9, (rank, e_energy)  # both iterates stop at ||S r|| / ||S b|| <= 1e-8
